@@ -1,0 +1,189 @@
+/*
+ * bem.h - C interface of the GB300 Burton-Miller collocation BEM library (libbem).
+ *
+ * The library assembles and solves the collocation system A y = b of the Calderon-preconditioned
+ * Burton-Miller formulation for two-dimensional Helmholtz transmission problems
+ * (Matsumoto, Yoshiki, Isakari, arXiv 2312.12787):
+ *   - Sec. 2: domains Omega_d with wavenumber k_d and flux coefficient eps_d (w = (1/eps_d) du/dn,
+ *     eps_1 = 1), u and w continuous across interfaces, radiation condition in the host Omega_1.
+ *   - Sec. 3.3: operators S, D, D*, N with G = (i/4) H0^(1)(k r) (eqs. stmp .. ddtmp, fundamental_sol),
+ *     Burton-Miller coefficient alpha = -i/k_1.
+ *   - Sec. 5 (eq. calderon_bieb, beta = -alpha) and Sec. 6 (eq. 3dom_calderon_bie, gamma = alpha/eps;
+ *     the general recipe at the end of Sec. 6): placement of standard and Burton-Miller rows.
+ *   - Sec. 7: constant elements, collocation at element centres, Gauss-Legendre quadrature, GMRES
+ *     without restart from x0 = 0.
+ *
+ * Conventions for every entry point:
+ *   - Complex numbers are bem_c64 {re, im} (16 bytes, layout-compatible with double _Complex).
+ *   - Pointers named *_dev are CUDA device pointers on the current device; pointers named *_host are
+ *     host pointers.  The caller owns every buffer it passes; the library owns the assembled matrix,
+ *     the Krylov workspace and any scratch it allocates (freed by bem_problem_destroy).
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).  Device work is
+ *     stream-ordered on it.  Entry points that return host values (iteration counts, residuals,
+ *     host outputs) synchronise the stream before returning.
+ *   - Unknown order: y = [u_1 .. u_N, w_1 .. w_N], elements numbered segment by segment in the order
+ *     the segments were added, and along each segment in vertex order.  Multiple right-hand sides are
+ *     stored one after another: column r of a block X is X + r*2N.
+ *   - Every function returns a bem_status; on failure bem_last_error() gives a message (thread-local).
+ *     Nothing is written to outputs after an argument error.  BEM_ENOCONV still writes the best iterate.
+ *   - Not thread-safe on one bem_problem; distinct problems may be used from distinct threads.
+ */
+#ifndef BEM_H_
+#define BEM_H_
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(_WIN32)
+#define BEM_API
+#else
+#define BEM_API __attribute__((visibility("default")))
+#endif
+
+typedef struct { double re, im; } bem_c64;
+
+typedef enum {
+  BEM_OK = 0,
+  BEM_EINVAL = 1,     /* invalid argument or geometry */
+  BEM_ENOMEM = 2,     /* device allocation failed or a footprint limit was exceeded */
+  BEM_ENOCONV = 3,    /* GMRES / refinement hit its iteration limit; best iterate written */
+  BEM_ETIMEOUT = 4,   /* a bounded device-side wait expired */
+  BEM_ECUDA = 5,      /* a CUDA runtime call failed (message gives the call and error) */
+  BEM_ESTATE = 6      /* call out of order (e.g. solve before domains were set) */
+} bem_status;
+
+/* Row placement of the integral equations (see oracle and Sec. 5-6):
+ *  MOD   - the paper's proposal: upper row of each element = standard equation of the domain its normal
+ *          points into, times -alpha; lower row = Burton-Miller equation of the domain its normal points
+ *          out of, with coefficient alpha/eps (Sec. 6 recipe; eq. calderon_bieb, eq. 3dom_calderon_bie).
+ *  ORIG  - eq. 3dom_calderon_bie0: as MOD but interior domains keep standard lower rows (times -alpha).
+ *  BETA1 - eq. calderon_bie1: as MOD with the standard rows unscaled.
+ *  CONV  - eq. naive_bie / eq. 3dom_conv_bie (up to row order): Burton-Miller (host) or standard
+ *          equations of the outward domain first, standard equations of the inward domain second. */
+typedef enum { BEM_FORM_MOD = 0, BEM_FORM_ORIG = 1, BEM_FORM_BETA1 = 2, BEM_FORM_CONV = 3 } bem_form;
+
+/* Arithmetic of the solve.  Assembly is always evaluated in FP64.
+ *  FP64     - A stored as complex FP64; FP64 matvec, FP64 Arnoldi; one unrestarted GMRES to `tol`.
+ *  MIXED    - A stored as complex FP32 (hi) plus its FP32 rounding remainder (lo).  Inner GMRES runs on
+ *             hi with FP32 products and an FP32 Krylov basis to `inner_tol`; the outer loop refines
+ *             x in FP64 with residuals b - (hi + lo) x accumulated in double-float arithmetic.
+ *  MIXED_TC - as MIXED, but the inner matvec of a multi-right-hand-side block runs as one dense complex
+ *             GEMM on the tcgen05 tensor cores (3xTF32 split products, FP32 accumulation). */
+typedef enum { BEM_PREC_FP64 = 0, BEM_PREC_MIXED = 1, BEM_PREC_MIXED_TC = 2 } bem_prec;
+
+typedef struct {
+  int quad_order;     /* Gauss-Legendre nodes per element, 1..16 (paper: 10) */
+  int form;           /* bem_form */
+  int prec;           /* bem_prec */
+  int max_iter;       /* Krylov dimension limit of one GMRES run (no restart), >= 1 */
+  int max_refine;     /* outer refinement steps for MIXED / MIXED_TC, >= 1 */
+  double tol;         /* target relative residual ||b - A x||_2 / ||b||_2 (paper: 1e-8), > 0 */
+  double inner_tol;   /* relative tolerance of each inner GMRES run (MIXED / MIXED_TC), > 0 */
+} bem_opts;
+
+typedef struct bem_problem bem_problem;
+
+/* Fill *o with the defaults: quad_order 4, MOD, FP64, max_iter 500, max_refine 6, tol 1e-10,
+ * inner_tol 1e-5. */
+BEM_API void bem_default_opts(bem_opts* o);
+
+/* Create an empty problem.  *out receives a library-owned handle (free with bem_problem_destroy).
+ * EINVAL if an option is out of range. */
+BEM_API bem_status bem_problem_create(bem_problem** out, const bem_opts* opts);
+BEM_API void bem_problem_destroy(bem_problem* p);
+
+/* Change the options of an existing problem (quadrature order or form changes invalidate the matrix). */
+BEM_API bem_status bem_set_opts(bem_problem* p, const bem_opts* opts);
+
+/* Domain table (Sec. 2): k_host[d] = wavenumber k_d > 0, eps_host[d] = flux coefficient eps_d > 0 with
+ * eps_host[0] = 1 (domain 0 is the unbounded host medium).  The paper ties them as k_d = omega sqrt(eps_d);
+ * the library takes both as given.  eps_d = -1 would put the eigenvalue cluster of A^2 at the origin
+ * (Sec. 5) and is rejected with every other eps_d <= 0.  n_dom in [2, 64]. */
+BEM_API bem_status bem_set_domains(bem_problem* p, int n_dom, const double* k_host, const double* eps_host);
+
+/* Append one interface segment: a polyline of n_vert vertices xy_host[2*v], xy_host[2*v+1].  Elements
+ * join consecutive vertices; closed != 0 adds the element from the last vertex to the first.  The
+ * element normal is the tangent turned by +90 degrees; it must point out of domain dom_P and into
+ * domain dom_M (Sec. 2: on the host boundary the normal points away from the host).  EINVAL for
+ * fewer than 2 vertices (3 if closed), zero-length elements, or domain ids out of range / equal. */
+BEM_API bem_status bem_add_segment(bem_problem* p, int n_vert, const double* xy_host, int dom_P, int dom_M,
+                                   int closed);
+
+BEM_API int bem_num_elements(const bem_problem* p);   /* N */
+BEM_API int bem_num_unknowns(const bem_problem* p);   /* 2N */
+
+/* Device bytes the assembled matrix and a solve with n_rhs right-hand sides will hold (for admission). */
+BEM_API size_t bem_footprint_bytes(const bem_problem* p, int n_rhs);
+
+/* Steps a1 + a3..a5: element geometry on the device, then every entry of A (Gauss-Legendre off the
+ * diagonal, exact self terms on it) placed by the selected form.  Allocates A on first use. */
+BEM_API bem_status bem_assemble(bem_problem* p, void* stream);
+
+/* Copy the assembled matrix into A_dev (2N x 2N complex FP64, row-major, leading dimension 2N).
+ * which = 0: the matrix used by the solver (FP64 path: A; mixed: hi), which = 1: hi + lo (mixed only). */
+BEM_API bem_status bem_get_matrix(bem_problem* p, int which, bem_c64* A_dev, void* stream);
+
+/* Step a2: b for plane waves u_in = exp(i k_1 (cos t, sin t).x), t = angles_host[r], r < n_rhs.
+ * b_dev: n_rhs x 2N.  Host-domain rows get u_in (standard) or u_in + alpha du_in/dn (Burton-Miller),
+ * times the row's scale; all other rows are zero (eq. naive_bie, eq. 3dom_calderon_bie). */
+BEM_API bem_status bem_rhs_planewave(bem_problem* p, int n_rhs, const double* angles_host, bem_c64* b_dev,
+                                     void* stream);
+
+/* Steps a6 / a11 for testing: y = A x for n_rhs columns with the kernel the solver uses
+ * (FP64: FP64 GEMV/GEMM; MIXED: FP32 GEMV; MIXED_TC: tensor-core GEMM when n_rhs > 1). */
+BEM_API bem_status bem_matvec(bem_problem* p, int n_rhs, const bem_c64* x_dev, bem_c64* y_dev, void* stream);
+
+/* Steps a6..a9: solve A x = b for n_rhs right-hand sides b_dev (n_rhs x 2N) into x_dev.
+ * iters_host[r] = total GMRES iterations (matvecs) of column r, resid_host[r] = final relative residual
+ * ||b - A x|| / ||b|| computed in FP64 (FP64 path: from the GMRES estimate).  Either may be NULL. */
+BEM_API bem_status bem_solve(bem_problem* p, int n_rhs, const bem_c64* b_dev, bem_c64* x_dev, int* iters_host,
+                             double* resid_host, void* stream);
+
+/* a2 + a6..a9 for plane waves (assembles first if needed). */
+BEM_API bem_status bem_solve_planewave(bem_problem* p, int n_rhs, const double* angles_host, bem_c64* x_dev,
+                                       int* iters_host, double* resid_host, void* stream);
+
+/* Step a10: far-field pattern u_inf(theta_a), a < n_ang, of each of n_rhs solutions x_dev (n_rhs x 2N)
+ * into out_dev (n_rhs x n_ang), with u_s(x) = e^{i k_1 |x|} / sqrt|x| (u_inf + O(1/|x|)). */
+BEM_API bem_status bem_far_field(bem_problem* p, int n_rhs, const bem_c64* x_dev, int n_ang,
+                                 const double* ang_host, bem_c64* out_dev, void* stream);
+
+/* End-to-end call with host buffers: assemble (if needed), solve plane waves, far field; copies the
+ * traces (n_rhs x 2N) and far fields (n_rhs x n_ang) to the host.  x_host or ff_host may be NULL. */
+BEM_API bem_status bem_solve_planewave_host(bem_problem* p, int n_rhs, const double* angles_host,
+                                            bem_c64* x_host, int n_ang, const double* ff_ang_host,
+                                            bem_c64* ff_host, int* iters_host, double* resid_host, void* stream);
+
+/* Per-phase device timing for measurement.  When enabled, every kernel launch of the problem is bracketed
+ * by CUDA events recorded on the stream it runs on; bem_profile_read synchronises those events and returns,
+ * per phase, the summed device milliseconds and the number of kernel launches since the last enable.
+ * Arrays have BEM_PH_COUNT entries.  Enabling resets the counters; it does not change results. */
+typedef enum {
+  BEM_PH_GEOMETRY = 0,  /* a1: element geometry */
+  BEM_PH_ASSEMBLE = 1,  /* a3-a5: matrix entries */
+  BEM_PH_RHS = 2,       /* a2 */
+  BEM_PH_MATVEC = 3,    /* a6 / a11: GEMV, SIMT GEMM or tensor-core GEMM */
+  BEM_PH_ARNOLDI = 4,   /* a7: projections, updates, norms */
+  BEM_PH_GIVENS = 5,    /* a8: Hessenberg column, rotations, residual estimate, basis scaling */
+  BEM_PH_UPDATE = 6,    /* a9: least squares and x += V y */
+  BEM_PH_RESIDUAL = 7,  /* a9: refinement residual b - (hi + lo) x and norms */
+  BEM_PH_FARFIELD = 8,  /* a10 */
+  BEM_PH_OTHER = 9,     /* conversions, copies */
+  BEM_PH_COUNT = 10
+} bem_phase;
+BEM_API bem_status bem_profile_enable(bem_problem* p, int on);
+BEM_API bem_status bem_profile_read(bem_problem* p, double* ms_host, long long* launches_host);
+
+/* Thread-local message of the last failure in this thread ("" if none). */
+BEM_API const char* bem_last_error(void);
+
+/* Library version string. */
+BEM_API const char* bem_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BEM_H_ */

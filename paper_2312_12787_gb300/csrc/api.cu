@@ -1,0 +1,770 @@
+// C interface of libbem: problem object, validation, assembly and solve drivers.
+//
+// The drivers sequence the kernels of assemble.cu, matvec.cu, krylov.cu and gemm_tc.cu on the
+// caller's stream.  FP64 path: one unrestarted GMRES (paper Sec. 7) in FP64.  Mixed path: iterative
+// refinement in FP64 around inner GMRES runs on the complex FP32 matrix.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "internal.cuh"
+
+using namespace bem;
+
+namespace {
+
+thread_local std::string g_err;
+
+bem_status fail(bem_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return st;
+}
+
+#define CU(call)                                                                                  \
+  do {                                                                                            \
+    cudaError_t e_ = (call);                                                                      \
+    if (e_ != cudaSuccess) return fail(BEM_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+// Gauss-Legendre nodes and weights on [-1, 1] by Newton's method on P_Q (three-term recurrence).
+void gauss_legendre(int Q, double* t, double* w) {
+  for (int i = 0; i < Q; ++i) {
+    double x = std::cos(M_PI * (i + 0.75) / (Q + 0.5));
+    double dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = x;
+      for (int k = 2; k <= Q; ++k) {
+        const double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      if (Q == 1) { p1 = x; p0 = 1.0; }
+      dp = Q * (x * p1 - p0) / (x * x - 1.0);
+      const double dx = p1 / dp;
+      x -= dx;
+      if (std::fabs(dx) < 1e-16) break;
+    }
+    // recompute derivative at the converged node
+    double p0 = 1.0, p1 = x;
+    for (int k = 2; k <= Q; ++k) {
+      const double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+      p0 = p1;
+      p1 = p2;
+    }
+    dp = (Q == 1) ? 1.0 : Q * (x * p1 - p0) / (x * x - 1.0);
+    t[i] = x;
+    w[i] = 2.0 / ((1.0 - x * x) * dp * dp);
+  }
+}
+
+bool valid_opts(const bem_opts* o) {
+  return o && o->quad_order >= 1 && o->quad_order <= kMaxQuad && o->form >= 0 && o->form <= 3 && o->prec >= 0 &&
+         o->prec <= 2 && o->max_iter >= 1 && o->max_iter <= 1000 && o->max_refine >= 1 && o->max_refine <= 100 &&
+         o->tol > 0 && std::isfinite(o->tol) && o->inner_tol > 0 && std::isfinite(o->inner_tol);
+}
+
+}  // namespace
+
+struct bem_problem {
+  bem_opts o{};
+  DomTab dom{};
+  std::vector<double> ax, ay, bx, by;
+  std::vector<int> P, M;
+  int n = 0;
+  bool geom_dirty = true;
+  bool mat_dirty = true;
+  // device geometry: ax ay bx by mx my tx ty h (9n doubles), P M (2n ints)
+  double* d_geom = nullptr;
+  int* d_pm = nullptr;
+  size_t geom_cap = 0;
+  void* d_A = nullptr;
+  void* d_Alo = nullptr;
+  size_t A_cap = 0;       // bytes of d_A (and d_Alo when mixed)
+  int A_mixed = -1;
+  // solve workspace (grow-only)
+  char* ws = nullptr;
+  size_t ws_cap = 0;
+  double* d_small = nullptr;   // angles etc.
+  size_t small_cap = 0;
+  int* h_pin = nullptr;        // pinned host mirror of counters
+  // measurement: event pairs per phase, kernel launches per phase
+  bool prof = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[BEM_PH_COUNT];
+  long long launches[BEM_PH_COUNT] = {};
+  std::vector<cudaEvent_t> pool;
+
+  ElemDev elem() const {
+    ElemDev e;
+    e.ax = d_geom; e.ay = d_geom + n; e.bx = d_geom + 2 * n; e.by = d_geom + 3 * n;
+    e.mx = d_geom + 4 * n; e.my = d_geom + 5 * n; e.tx = d_geom + 6 * n; e.ty = d_geom + 7 * n;
+    e.h = d_geom + 8 * n;
+    e.P = d_pm; e.M = d_pm + n;
+    return e;
+  }
+  bool mixed() const { return o.prec != BEM_PREC_FP64; }
+};
+
+namespace {
+
+cudaEvent_t pool_event(bem_problem* p) {
+  if (!p->pool.empty()) {
+    cudaEvent_t e = p->pool.back();
+    p->pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+// Brackets the launches of one phase with events on stream s when profiling is on.
+struct Phase {
+  bem_problem* p;
+  int ph;
+  cudaStream_t s;
+  cudaEvent_t b = nullptr;
+  Phase(bem_problem* p_, int ph_, cudaStream_t s_, int nlaunch) : p(p_), ph(ph_), s(s_) {
+    if (!p->prof) return;
+    p->launches[ph] += nlaunch;
+    b = pool_event(p);
+    if (b) cudaEventRecord(b, s);
+  }
+  ~Phase() {
+    if (!b) return;
+    cudaEvent_t e = pool_event(p);
+    if (!e) return;
+    cudaEventRecord(e, s);
+    p->ev[ph].push_back({b, e});
+  }
+};
+
+Quad make_quad(int Q) {
+  Quad q{};
+  q.Q = Q;
+  gauss_legendre(Q, q.t, q.w);
+  return q;
+}
+
+bem_status ensure_small(bem_problem* p, size_t doubles) {
+  if (doubles <= p->small_cap) return BEM_OK;
+  if (p->d_small) cudaFree(p->d_small);
+  p->d_small = nullptr;
+  p->small_cap = 0;
+  CU(cudaMalloc(&p->d_small, doubles * sizeof(double)));
+  p->small_cap = doubles;
+  return BEM_OK;
+}
+
+bem_status upload_geometry(bem_problem* p, cudaStream_t s) {
+  if (!p->geom_dirty) return BEM_OK;
+  const int n = p->n;
+  if ((size_t)n > p->geom_cap) {
+    if (p->d_geom) cudaFree(p->d_geom);
+    if (p->d_pm) cudaFree(p->d_pm);
+    p->d_geom = nullptr;
+    p->d_pm = nullptr;
+    p->geom_cap = 0;
+    CU(cudaMalloc(&p->d_geom, (size_t)9 * n * sizeof(double)));
+    CU(cudaMalloc(&p->d_pm, (size_t)2 * n * sizeof(int)));
+    p->geom_cap = n;
+  }
+  CU(cudaMemcpyAsync(p->d_geom, p->ax.data(), n * sizeof(double), cudaMemcpyHostToDevice, s));
+  CU(cudaMemcpyAsync(p->d_geom + n, p->ay.data(), n * sizeof(double), cudaMemcpyHostToDevice, s));
+  CU(cudaMemcpyAsync(p->d_geom + 2 * n, p->bx.data(), n * sizeof(double), cudaMemcpyHostToDevice, s));
+  CU(cudaMemcpyAsync(p->d_geom + 3 * n, p->by.data(), n * sizeof(double), cudaMemcpyHostToDevice, s));
+  CU(cudaMemcpyAsync(p->d_pm, p->P.data(), n * sizeof(int), cudaMemcpyHostToDevice, s));
+  CU(cudaMemcpyAsync(p->d_pm + n, p->M.data(), n * sizeof(int), cudaMemcpyHostToDevice, s));
+  {
+    Phase ph(p, BEM_PH_GEOMETRY, s, 1);
+    CU(launch_elements(p->elem(), n, s));
+  }
+  // pageable sources: make sure the copies are done before the host vectors can change
+  CU(cudaStreamSynchronize(s));
+  p->geom_dirty = false;
+  return BEM_OK;
+}
+
+bem_status check_ready(bem_problem* p) {
+  if (!p) return fail(BEM_EINVAL, "null problem");
+  if (p->dom.n < 2) return fail(BEM_ESTATE, "domains not set");
+  if (p->n < 1) return fail(BEM_ESTATE, "no segments added");
+  for (int e = 0; e < p->n; ++e)
+    if (p->P[e] >= p->dom.n || p->M[e] >= p->dom.n)
+      return fail(BEM_EINVAL, "element %d refers to a domain beyond the %d set", e, p->dom.n);
+  // the self-element series is used for k h / 2 < 8 (elements shorter than ~2.5 wavelengths)
+  for (int e = 0; e < p->n; ++e) {
+    const double h = std::hypot(p->bx[e] - p->ax[e], p->by[e] - p->ay[e]);
+    const double kk = std::max(p->dom.k[p->P[e]], p->dom.k[p->M[e]]);
+    if (0.5 * kk * h >= 8.0)
+      return fail(BEM_EINVAL, "element %d is %.3g wavelengths long; refine the mesh", e, kk * h / (2 * M_PI));
+  }
+  return BEM_OK;
+}
+
+size_t matrix_bytes(int n, bool mixed) {
+  const size_t nn = (size_t)2 * n * 2 * n;
+  return mixed ? 2 * nn * sizeof(float2) : nn * sizeof(double2);
+}
+
+bem_status assemble_impl(bem_problem* p, cudaStream_t s) {
+  bem_status st = check_ready(p);
+  if (st != BEM_OK) return st;
+  st = upload_geometry(p, s);
+  if (st != BEM_OK) return st;
+  const bool mixed = p->mixed();
+  if (!p->mat_dirty && p->A_mixed == (int)mixed) return BEM_OK;
+  const size_t nn = (size_t)2 * p->n * 2 * p->n;
+  const size_t need = mixed ? nn * sizeof(float2) : nn * sizeof(double2);
+  if (need > p->A_cap || p->A_mixed != (int)mixed) {
+    if (p->d_A) cudaFree(p->d_A);
+    if (p->d_Alo) cudaFree(p->d_Alo);
+    p->d_A = p->d_Alo = nullptr;
+    p->A_cap = 0;
+    cudaError_t e = cudaMalloc(&p->d_A, need);
+    if (e != cudaSuccess) return fail(BEM_ENOMEM, "matrix allocation of %zu bytes failed", need);
+    if (mixed) {
+      e = cudaMalloc(&p->d_Alo, need);
+      if (e != cudaSuccess) return fail(BEM_ENOMEM, "matrix allocation of %zu bytes failed", need);
+    }
+    p->A_cap = need;
+  }
+  const Quad q = make_quad(p->o.quad_order);
+  {
+    Phase ph(p, BEM_PH_ASSEMBLE, s, 1);
+    CU(launch_assemble(p->elem(), p->n, p->dom, q, p->o.form, mixed ? 1 : 0, p->d_A, p->d_Alo, (size_t)2 * p->n, s));
+  }
+  p->A_mixed = mixed;
+  p->mat_dirty = false;
+  return BEM_OK;
+}
+
+// Workspace carve-out for a GMRES block.
+struct Carve {
+  char* base;
+  size_t off = 0;
+  template <typename T> T* take(size_t count) {
+    off = (off + 255) & ~(size_t)255;
+    T* r = reinterpret_cast<T*>(base + off);
+    off += count * sizeof(T);
+    return r;
+  }
+};
+
+size_t krylov_bytes(int n2, int nrhs, int m, bool fp32) {
+  const int nc = krylov_nchunk(n2);
+  const size_t tb = fp32 ? sizeof(float2) : sizeof(double2);
+  size_t b = 0;
+  auto add = [&](size_t x) { b = ((b + 255) & ~(size_t)255) + x; };
+  add((size_t)(m + 1) * nrhs * n2 * tb);  // V
+  add((size_t)nrhs * n2 * tb);            // W
+  add((size_t)nrhs * m * (m + 1) * 16);   // H
+  add((size_t)nrhs * m * 16);             // cs
+  add((size_t)nrhs * m * 16);             // sn
+  add((size_t)nrhs * (m + 1) * 16);       // g
+  add((size_t)nrhs * m * 16);             // y
+  add((size_t)nrhs * 8);                  // beta
+  add((size_t)nrhs * 8);                  // hnext
+  add((size_t)nrhs * nc * (m + 1) * 16);  // part
+  add((size_t)nrhs * nc * 8);             // npart
+  add((size_t)nrhs * (m + 1) * 16);       // hcol
+  add((size_t)nrhs * 4);                  // active
+  add((size_t)nrhs * 4);                  // iters
+  add((size_t)nrhs * 8);                  // resid
+  add(4);                                 // jdev
+  add(4);                                 // n_active
+  // mixed extras: residual r (FP64), rhs copy of the inner solve (FP32 not needed), tc workspace
+  add((size_t)nrhs * n2 * 16);
+  add(matvec_tc_workspace_bytes(n2, nrhs));
+  add((size_t)nrhs * n2 * 16);            // rhs / scratch block (plane waves)
+  add(4096);
+  return b + 4096;
+}
+
+bem_status ensure_ws(bem_problem* p, size_t bytes) {
+  if (bytes <= p->ws_cap) return BEM_OK;
+  if (p->ws) cudaFree(p->ws);
+  p->ws = nullptr;
+  p->ws_cap = 0;
+  cudaError_t e = cudaMalloc(&p->ws, bytes);
+  if (e != cudaSuccess) return fail(BEM_ENOMEM, "workspace allocation of %zu bytes failed", bytes);
+  p->ws_cap = bytes;
+  if (!p->h_pin) CU(cudaMallocHost(&p->h_pin, 64 * sizeof(int)));
+  return BEM_OK;
+}
+
+struct Solver {
+  KrylovState st{};
+  double2* r = nullptr;      // FP64 residual block (mixed)
+  void* tcws = nullptr;
+  size_t tcws_bytes = 0;
+  double2* rhs = nullptr;    // plane-wave rhs block
+};
+
+Solver carve_solver(bem_problem* p, int nrhs, bool fp32) {
+  const int n2 = 2 * p->n, m = p->o.max_iter;
+  const int nc = krylov_nchunk(n2);
+  const size_t tb = fp32 ? sizeof(float2) : sizeof(double2);
+  Carve c{p->ws};
+  Solver sv;
+  KrylovState& st = sv.st;
+  st.n = n2; st.nrhs = nrhs; st.m = m; st.basis_fp32 = fp32 ? 1 : 0;
+  st.V = c.take<char>((size_t)(m + 1) * nrhs * n2 * tb);
+  st.W = c.take<char>((size_t)nrhs * n2 * tb);
+  st.H = c.take<double2>((size_t)nrhs * m * (m + 1));
+  st.cs = c.take<double2>((size_t)nrhs * m);
+  st.sn = c.take<double2>((size_t)nrhs * m);
+  st.g = c.take<double2>((size_t)nrhs * (m + 1));
+  st.y = c.take<double2>((size_t)nrhs * m);
+  st.beta = c.take<double>(nrhs);
+  st.hnext = c.take<double>(nrhs);
+  st.part = c.take<double2>((size_t)nrhs * nc * (m + 1));
+  st.npart = c.take<double>((size_t)nrhs * nc);
+  st.hcol = c.take<double2>((size_t)nrhs * (m + 1));
+  st.active = c.take<int>(nrhs);
+  st.iters = c.take<int>(nrhs);
+  st.resid = c.take<double>(nrhs);
+  st.jdev = c.take<int>(1);
+  st.n_active = c.take<int>(1);
+  sv.r = c.take<double2>((size_t)nrhs * n2);
+  sv.tcws_bytes = matvec_tc_workspace_bytes(n2, nrhs);
+  sv.tcws = c.take<char>(sv.tcws_bytes);
+  sv.rhs = c.take<double2>((size_t)nrhs * n2);
+  return sv;
+}
+
+// One unrestarted GMRES run from x0 = 0 on r0 (FP64 block), adding the correction into x.
+bem_status gmres_run(bem_problem* p, Solver& sv, const double2* r0, double2* x, double tol, std::vector<int>& iters,
+                     std::vector<double>& resid, cudaStream_t s) {
+  KrylovState& st = sv.st;
+  const int n2 = st.n, nrhs = st.nrhs;
+  {
+    Phase ph(p, BEM_PH_GIVENS, s, 3);
+    CU(krylov_start(st, r0, tol, s));
+  }
+  const bool fp32 = st.basis_fp32;
+  const size_t tb = fp32 ? sizeof(float2) : sizeof(double2);
+  for (int j = 0; j < st.m; ++j) {
+    void* Vj = static_cast<char*>(st.V) + (size_t)j * nrhs * n2 * tb;
+    {
+    Phase ph(p, BEM_PH_MATVEC, s, 1);
+    if (!fp32) {
+      CU(launch_matvec_c64(static_cast<const double2*>(p->d_A), n2, n2, nrhs, static_cast<const double2*>(Vj),
+                           static_cast<double2*>(st.W), s));
+    } else if (p->o.prec == BEM_PREC_MIXED_TC && nrhs > 1 && matvec_tc_supported(n2, nrhs)) {
+      CU(launch_matvec_tc(static_cast<const float2*>(p->d_A), n2, n2, nrhs, static_cast<const float2*>(Vj),
+                          static_cast<float2*>(st.W), sv.tcws, sv.tcws_bytes, s));
+    } else {
+      CU(launch_matvec_c32(static_cast<const float2*>(p->d_A), n2, n2, nrhs, static_cast<const float2*>(Vj),
+                           static_cast<float2*>(st.W), st.active, s));
+    }
+    }
+    {
+      Phase ph(p, BEM_PH_ARNOLDI, s, 6);
+      CU(krylov_orthogonalise(st, 2, s));
+    }
+    {
+      Phase ph(p, BEM_PH_GIVENS, s, 3);
+      CU(krylov_finish_step(st, tol, s));
+    }
+    CU(cudaMemcpyAsync(p->h_pin, st.n_active, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    if (p->h_pin[0] == 0) break;
+  }
+  {
+    Phase ph(p, BEM_PH_UPDATE, s, 2);
+    CU(krylov_update_solution(st, x, s));
+  }
+  std::vector<int> it(nrhs);
+  std::vector<double> rs(nrhs);
+  CU(cudaMemcpyAsync(it.data(), st.iters, nrhs * sizeof(int), cudaMemcpyDeviceToHost, s));
+  CU(cudaMemcpyAsync(rs.data(), st.resid, nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CU(cudaStreamSynchronize(s));
+  for (int r = 0; r < nrhs; ++r) {
+    iters[r] += it[r];
+    resid[r] = rs[r];
+  }
+  return BEM_OK;
+}
+
+// column 2-norms of an FP64 block (host result)
+bem_status column_norms(bem_problem* p, Solver& sv, const double2* v, int nrhs, std::vector<double>& out,
+                        cudaStream_t s);
+
+}  // namespace
+
+namespace bem {
+cudaError_t launch_column_norms(const double2* v, int n, int nrhs, double* out, cudaStream_t s);
+}
+
+namespace {
+bem_status column_norms(bem_problem* p, Solver& sv, const double2* v, int nrhs, std::vector<double>& out,
+                        cudaStream_t s) {
+  {
+    Phase ph(p, BEM_PH_RESIDUAL, s, 1);
+    CU(launch_column_norms(v, sv.st.n, nrhs, sv.st.beta, s));
+  }
+  out.resize(nrhs);
+  CU(cudaMemcpyAsync(out.data(), sv.st.beta, nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CU(cudaStreamSynchronize(s));
+  return BEM_OK;
+}
+
+bem_status solve_impl(bem_problem* p, int nrhs, const double2* b, double2* x, int* iters_h, double* resid_h,
+                      cudaStream_t s) {
+  bem_status st = assemble_impl(p, s);
+  if (st != BEM_OK) return st;
+  const int n2 = 2 * p->n;
+  const bool mixed = p->mixed();
+  st = ensure_ws(p, krylov_bytes(n2, nrhs, p->o.max_iter, mixed));
+  if (st != BEM_OK) return st;
+  Solver sv = carve_solver(p, nrhs, mixed);
+  std::vector<int> iters(nrhs, 0);
+  std::vector<double> resid(nrhs, 0.0);
+  CU(cudaMemsetAsync(x, 0, (size_t)nrhs * n2 * sizeof(double2), s));
+  bem_status result = BEM_OK;
+  if (!mixed) {
+    st = gmres_run(p, sv, b, x, p->o.tol, iters, resid, s);
+    if (st != BEM_OK) return st;
+    for (int r = 0; r < nrhs; ++r)
+      if (resid[r] > p->o.tol) result = BEM_ENOCONV;
+  } else {
+    std::vector<double> bn, rn;
+    st = column_norms(p, sv, b, nrhs, bn, s);
+    if (st != BEM_OK) return st;
+    CU(cudaMemcpyAsync(sv.r, b, (size_t)nrhs * n2 * sizeof(double2), cudaMemcpyDeviceToDevice, s));
+    rn = bn;
+    bool done = false;
+    for (int outer = 0; outer < p->o.max_refine && !done; ++outer) {
+      // zero the residual of columns that already meet the tolerance so the inner solve skips them
+      done = true;
+      for (int r = 0; r < nrhs; ++r) {
+        resid[r] = bn[r] > 0 ? rn[r] / bn[r] : 0.0;
+        if (resid[r] <= p->o.tol) CU(cudaMemsetAsync(sv.r + (size_t)r * n2, 0, n2 * sizeof(double2), s));
+        else done = false;
+      }
+      if (done) break;
+      std::vector<double> inner_res(nrhs);
+      st = gmres_run(p, sv, sv.r, x, p->o.inner_tol, iters, inner_res, s);
+      if (st != BEM_OK) return st;
+      {
+        Phase ph(p, BEM_PH_RESIDUAL, s, 1);
+        CU(launch_residual_split(static_cast<const float2*>(p->d_A), static_cast<const float2*>(p->d_Alo), n2, n2,
+                                 nrhs, x, b, sv.r, s));
+      }
+      st = column_norms(p, sv, sv.r, nrhs, rn, s);
+      if (st != BEM_OK) return st;
+    }
+    for (int r = 0; r < nrhs; ++r) {
+      resid[r] = bn[r] > 0 ? rn[r] / bn[r] : 0.0;
+      if (resid[r] > p->o.tol) result = BEM_ENOCONV;
+    }
+  }
+  if (iters_h) std::copy(iters.begin(), iters.end(), iters_h);
+  if (resid_h) std::copy(resid.begin(), resid.end(), resid_h);
+  if (result == BEM_ENOCONV) fail(BEM_ENOCONV, "tolerance not reached within the iteration limits");
+  return result;
+}
+
+bem_status rhs_impl(bem_problem* p, int nrhs, const double* angles_h, double2* b, cudaStream_t s) {
+  bem_status st = check_ready(p);
+  if (st != BEM_OK) return st;
+  st = upload_geometry(p, s);
+  if (st != BEM_OK) return st;
+  for (int r = 0; r < nrhs; ++r)
+    if (!std::isfinite(angles_h[r])) return fail(BEM_EINVAL, "angle %d is not finite", r);
+  st = ensure_small(p, nrhs);
+  if (st != BEM_OK) return st;
+  CU(cudaMemcpyAsync(p->d_small, angles_h, nrhs * sizeof(double), cudaMemcpyHostToDevice, s));
+  {
+    Phase ph(p, BEM_PH_RHS, s, 1);
+    CU(launch_rhs_planewave(p->elem(), p->n, p->dom, p->o.form, nrhs, p->d_small, b, s));
+  }
+  CU(cudaStreamSynchronize(s));   // angles_h may be pageable
+  return BEM_OK;
+}
+
+}  // namespace
+
+// ================================== C interface ==================================================
+
+extern "C" {
+
+BEM_API void bem_default_opts(bem_opts* o) {
+  if (!o) return;
+  o->quad_order = 4;
+  o->form = BEM_FORM_MOD;
+  o->prec = BEM_PREC_FP64;
+  o->max_iter = 500;
+  o->max_refine = 6;
+  o->tol = 1e-10;
+  o->inner_tol = 1e-5;
+}
+
+BEM_API bem_status bem_problem_create(bem_problem** out, const bem_opts* opts) {
+  if (!out) return fail(BEM_EINVAL, "null output pointer");
+  *out = nullptr;
+  bem_opts o;
+  bem_default_opts(&o);
+  if (opts) o = *opts;
+  if (!valid_opts(&o)) return fail(BEM_EINVAL, "invalid options");
+  bem_problem* p = new bem_problem();
+  p->o = o;
+  *out = p;
+  return BEM_OK;
+}
+
+BEM_API void bem_problem_destroy(bem_problem* p) {
+  if (!p) return;
+  if (p->d_geom) cudaFree(p->d_geom);
+  if (p->d_pm) cudaFree(p->d_pm);
+  if (p->d_A) cudaFree(p->d_A);
+  if (p->d_Alo) cudaFree(p->d_Alo);
+  if (p->ws) cudaFree(p->ws);
+  if (p->d_small) cudaFree(p->d_small);
+  if (p->h_pin) cudaFreeHost(p->h_pin);
+  for (int k = 0; k < BEM_PH_COUNT; ++k)
+    for (auto& pr : p->ev[k]) {
+      cudaEventDestroy(pr.first);
+      cudaEventDestroy(pr.second);
+    }
+  for (auto e : p->pool) cudaEventDestroy(e);
+  delete p;
+}
+
+BEM_API bem_status bem_set_opts(bem_problem* p, const bem_opts* opts) {
+  if (!p || !valid_opts(opts)) return fail(BEM_EINVAL, "invalid options");
+  if (opts->quad_order != p->o.quad_order || opts->form != p->o.form || opts->prec != p->o.prec) p->mat_dirty = true;
+  p->o = *opts;
+  return BEM_OK;
+}
+
+BEM_API bem_status bem_set_domains(bem_problem* p, int n_dom, const double* k, const double* eps) {
+  if (!p || !k || !eps) return fail(BEM_EINVAL, "null argument");
+  if (n_dom < 2 || n_dom > kMaxDomains) return fail(BEM_EINVAL, "n_dom must be in [2, %d]", kMaxDomains);
+  for (int d = 0; d < n_dom; ++d) {
+    if (!(k[d] > 0) || !std::isfinite(k[d])) return fail(BEM_EINVAL, "k[%d] must be positive and finite", d);
+    if (!(eps[d] > 0) || !std::isfinite(eps[d])) return fail(BEM_EINVAL, "eps[%d] must be positive and finite", d);
+  }
+  if (eps[0] != 1.0) return fail(BEM_EINVAL, "eps[0] (host medium) must be 1");
+  p->dom.n = n_dom;
+  for (int d = 0; d < n_dom; ++d) {
+    p->dom.k[d] = k[d];
+    p->dom.eps[d] = eps[d];
+  }
+  p->mat_dirty = true;
+  return BEM_OK;
+}
+
+BEM_API bem_status bem_add_segment(bem_problem* p, int n_vert, const double* xy, int dom_P, int dom_M, int closed) {
+  if (!p || !xy) return fail(BEM_EINVAL, "null argument");
+  if (n_vert < (closed ? 3 : 2)) return fail(BEM_EINVAL, "too few vertices (%d)", n_vert);
+  if (dom_P < 0 || dom_M < 0 || dom_P >= kMaxDomains || dom_M >= kMaxDomains || dom_P == dom_M)
+    return fail(BEM_EINVAL, "invalid domain pair (%d, %d)", dom_P, dom_M);
+  for (int v = 0; v < 2 * n_vert; ++v)
+    if (!std::isfinite(xy[v])) return fail(BEM_EINVAL, "vertex coordinate %d is not finite", v);
+  const int ne = closed ? n_vert : n_vert - 1;
+  for (int e = 0; e < ne; ++e) {
+    const int a = e, b = (e + 1) % n_vert;
+    if (xy[2 * a] == xy[2 * b] && xy[2 * a + 1] == xy[2 * b + 1])
+      return fail(BEM_EINVAL, "zero-length element %d", e);
+  }
+  for (int e = 0; e < ne; ++e) {
+    const int a = e, b = (e + 1) % n_vert;
+    p->ax.push_back(xy[2 * a]);
+    p->ay.push_back(xy[2 * a + 1]);
+    p->bx.push_back(xy[2 * b]);
+    p->by.push_back(xy[2 * b + 1]);
+    p->P.push_back(dom_P);
+    p->M.push_back(dom_M);
+  }
+  p->n += ne;
+  p->geom_dirty = true;
+  p->mat_dirty = true;
+  return BEM_OK;
+}
+
+BEM_API int bem_num_elements(const bem_problem* p) { return p ? p->n : 0; }
+BEM_API int bem_num_unknowns(const bem_problem* p) { return p ? 2 * p->n : 0; }
+
+BEM_API size_t bem_footprint_bytes(const bem_problem* p, int n_rhs) {
+  if (!p || n_rhs < 1) return 0;
+  const bool mixed = p->o.prec != BEM_PREC_FP64;
+  return matrix_bytes(p->n, mixed) + krylov_bytes(2 * p->n, n_rhs, p->o.max_iter, mixed) + (size_t)11 * p->n * 8;
+}
+
+BEM_API bem_status bem_assemble(bem_problem* p, void* stream) {
+  return assemble_impl(p, static_cast<cudaStream_t>(stream));
+}
+
+BEM_API bem_status bem_get_matrix(bem_problem* p, int which, bem_c64* A_dev, void* stream) {
+  if (!p || !A_dev) return fail(BEM_EINVAL, "null argument");
+  if (which != 0 && which != 1) return fail(BEM_EINVAL, "which must be 0 or 1");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  bem_status st = assemble_impl(p, s);
+  if (st != BEM_OK) return st;
+  if (which == 1 && !p->mixed()) return fail(BEM_EINVAL, "which = 1 needs a mixed-precision problem");
+  const size_t nn = (size_t)2 * p->n * 2 * p->n;
+  CU(launch_matrix_to_c64(p->d_A, p->d_Alo, p->mixed() ? 1 : 0, which, nn, reinterpret_cast<double2*>(A_dev), s));
+  return BEM_OK;
+}
+
+BEM_API bem_status bem_rhs_planewave(bem_problem* p, int n_rhs, const double* angles, bem_c64* b_dev, void* stream) {
+  if (!p || !angles || !b_dev || n_rhs < 1) return fail(BEM_EINVAL, "invalid argument");
+  return rhs_impl(p, n_rhs, angles, reinterpret_cast<double2*>(b_dev), static_cast<cudaStream_t>(stream));
+}
+
+BEM_API bem_status bem_matvec(bem_problem* p, int n_rhs, const bem_c64* x_dev, bem_c64* y_dev, void* stream) {
+  if (!p || !x_dev || !y_dev || n_rhs < 1) return fail(BEM_EINVAL, "invalid argument");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  bem_status st = assemble_impl(p, s);
+  if (st != BEM_OK) return st;
+  const int n2 = 2 * p->n;
+  const double2* x = reinterpret_cast<const double2*>(x_dev);
+  double2* y = reinterpret_cast<double2*>(y_dev);
+  if (!p->mixed()) {
+    Phase ph(p, BEM_PH_MATVEC, s, 1);
+    CU(launch_matvec_c64(static_cast<const double2*>(p->d_A), n2, n2, n_rhs, x, y, s));
+    return BEM_OK;
+  }
+  // mixed: convert x to complex FP32, run the solver's kernel, widen the result
+  st = ensure_ws(p, krylov_bytes(n2, n_rhs, p->o.max_iter, true));
+  if (st != BEM_OK) return st;
+  Solver sv = carve_solver(p, n_rhs, true);
+  float2* xf = static_cast<float2*>(sv.st.V);
+  float2* yf = static_cast<float2*>(sv.st.W);
+  {
+    Phase ph(p, BEM_PH_OTHER, s, 1);
+    CU(launch_convert_c64_c32(x, xf, (size_t)n_rhs * n2, s));
+  }
+  {
+    Phase ph(p, BEM_PH_MATVEC, s, 1);
+    if (p->o.prec == BEM_PREC_MIXED_TC && n_rhs > 1 && matvec_tc_supported(n2, n_rhs)) {
+      CU(launch_matvec_tc(static_cast<const float2*>(p->d_A), n2, n2, n_rhs, xf, yf, sv.tcws, sv.tcws_bytes, s));
+    } else {
+      CU(launch_matvec_c32(static_cast<const float2*>(p->d_A), n2, n2, n_rhs, xf, yf, nullptr, s));
+    }
+  }
+  {
+    Phase ph(p, BEM_PH_OTHER, s, 1);
+    CU(launch_convert_c32_c64(yf, y, (size_t)n_rhs * n2, s));
+  }
+  return BEM_OK;
+}
+
+BEM_API bem_status bem_solve(bem_problem* p, int n_rhs, const bem_c64* b_dev, bem_c64* x_dev, int* iters,
+                             double* resid, void* stream) {
+  if (!p || !b_dev || !x_dev || n_rhs < 1) return fail(BEM_EINVAL, "invalid argument");
+  return solve_impl(p, n_rhs, reinterpret_cast<const double2*>(b_dev), reinterpret_cast<double2*>(x_dev), iters,
+                    resid, static_cast<cudaStream_t>(stream));
+}
+
+BEM_API bem_status bem_solve_planewave(bem_problem* p, int n_rhs, const double* angles, bem_c64* x_dev, int* iters,
+                                       double* resid, void* stream) {
+  if (!p || !angles || !x_dev || n_rhs < 1) return fail(BEM_EINVAL, "invalid argument");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  bem_status st = assemble_impl(p, s);
+  if (st != BEM_OK) return st;
+  const int n2 = 2 * p->n;
+  st = ensure_ws(p, krylov_bytes(n2, n_rhs, p->o.max_iter, p->mixed()));
+  if (st != BEM_OK) return st;
+  Solver sv = carve_solver(p, n_rhs, p->mixed());
+  st = rhs_impl(p, n_rhs, angles, sv.rhs, s);
+  if (st != BEM_OK) return st;
+  return solve_impl(p, n_rhs, sv.rhs, reinterpret_cast<double2*>(x_dev), iters, resid, s);
+}
+
+BEM_API bem_status bem_far_field(bem_problem* p, int n_rhs, const bem_c64* x_dev, int n_ang, const double* ang,
+                                 bem_c64* out_dev, void* stream) {
+  if (!p || !x_dev || !ang || !out_dev || n_rhs < 1 || n_ang < 1) return fail(BEM_EINVAL, "invalid argument");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  bem_status st = check_ready(p);
+  if (st != BEM_OK) return st;
+  st = upload_geometry(p, s);
+  if (st != BEM_OK) return st;
+  st = ensure_small(p, n_ang);
+  if (st != BEM_OK) return st;
+  CU(cudaMemcpyAsync(p->d_small, ang, n_ang * sizeof(double), cudaMemcpyHostToDevice, s));
+  const Quad q = make_quad(p->o.quad_order);
+  {
+    Phase ph(p, BEM_PH_FARFIELD, s, 1);
+    CU(launch_far_field(p->elem(), p->n, p->dom, q, n_rhs, reinterpret_cast<const double2*>(x_dev), n_ang,
+                        p->d_small, reinterpret_cast<double2*>(out_dev), s));
+  }
+  CU(cudaStreamSynchronize(s));
+  return BEM_OK;
+}
+
+BEM_API bem_status bem_solve_planewave_host(bem_problem* p, int n_rhs, const double* angles, bem_c64* x_host,
+                                            int n_ang, const double* ff_ang, bem_c64* ff_host, int* iters,
+                                            double* resid, void* stream) {
+  if (!p || !angles || n_rhs < 1) return fail(BEM_EINVAL, "invalid argument");
+  if (ff_host && (!ff_ang || n_ang < 1)) return fail(BEM_EINVAL, "far-field angles missing");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t n2 = (size_t)2 * (p->n);
+  double2* xd = nullptr;
+  double2* ffd = nullptr;
+  CU(cudaMallocAsync(&xd, n_rhs * n2 * sizeof(double2), s));
+  if (ff_host) CU(cudaMallocAsync(&ffd, (size_t)n_rhs * n_ang * sizeof(double2), s));
+  bem_status st = bem_solve_planewave(p, n_rhs, angles, reinterpret_cast<bem_c64*>(xd), iters, resid, stream);
+  if (st == BEM_OK || st == BEM_ENOCONV) {
+    if (ff_host) {
+      bem_status st2 = bem_far_field(p, n_rhs, reinterpret_cast<bem_c64*>(xd), n_ang, ff_ang,
+                                     reinterpret_cast<bem_c64*>(ffd), stream);
+      if (st2 != BEM_OK) st = st2;
+      else CU(cudaMemcpyAsync(ff_host, ffd, (size_t)n_rhs * n_ang * sizeof(double2), cudaMemcpyDeviceToHost, s));
+    }
+    if (x_host) CU(cudaMemcpyAsync(x_host, xd, n_rhs * n2 * sizeof(double2), cudaMemcpyDeviceToHost, s));
+  }
+  cudaFreeAsync(xd, s);
+  if (ffd) cudaFreeAsync(ffd, s);
+  CU(cudaStreamSynchronize(s));
+  return st;
+}
+
+BEM_API bem_status bem_profile_enable(bem_problem* p, int on) {
+  if (!p) return fail(BEM_EINVAL, "null problem");
+  for (int k = 0; k < BEM_PH_COUNT; ++k) {
+    for (auto& pr : p->ev[k]) {
+      cudaEventSynchronize(pr.second);
+      p->pool.push_back(pr.first);
+      p->pool.push_back(pr.second);
+    }
+    p->ev[k].clear();
+    p->launches[k] = 0;
+  }
+  p->prof = on != 0;
+  return BEM_OK;
+}
+
+BEM_API bem_status bem_profile_read(bem_problem* p, double* ms, long long* launches) {
+  if (!p) return fail(BEM_EINVAL, "null problem");
+  for (int k = 0; k < BEM_PH_COUNT; ++k) {
+    double t = 0.0;
+    for (auto& pr : p->ev[k]) {
+      CU(cudaEventSynchronize(pr.second));
+      float f = 0.f;
+      CU(cudaEventElapsedTime(&f, pr.first, pr.second));
+      t += f;
+    }
+    if (ms) ms[k] = t;
+    if (launches) launches[k] = p->launches[k];
+  }
+  return BEM_OK;
+}
+
+BEM_API const char* bem_last_error(void) { return g_err.c_str(); }
+
+BEM_API const char* bem_version(void) { return "libbem 0.1 (sm_103a)"; }
+
+}  // extern "C"

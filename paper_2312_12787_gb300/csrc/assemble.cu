@@ -1,0 +1,299 @@
+// Element geometry (step a1), collocation-matrix assembly (steps a3-a5), plane-wave right-hand side
+// (step a2) and far field (step a10).
+//
+// Assembly follows the paper: operators S, D, D*, N of Sec. 3.3 (eqs. stmp-ddtmp) with
+// G = (i/4) H0^(1)(k r) (eq. fundamental_sol); constant elements collocated at their centres and
+// Gauss-Legendre quadrature off the diagonal, exact self-element integrals on it (Sec. 7 opening
+// paragraph); rows placed by the Sec. 6 recipe (eq. calderon_bieb with beta = -alpha, eq.
+// 3dom_calderon_bie with gamma = alpha/eps) or one of the comparison forms.
+//
+// One thread owns one element pair (i, j) and writes its four entries A[i, j], A[i, N+j],
+// A[N+i, j], A[N+i, N+j]; a warp spans 32 consecutive columns, so every store is a coalesced
+// 32-entry row segment.  All kernel arithmetic is FP64 (the FP64 pipe bounds this kernel); the mixed
+// path rounds each entry to complex FP32 and keeps the FP32 rounding remainder as a second matrix.
+#include "internal.cuh"
+#include "bessel.cuh"
+
+namespace bem {
+
+namespace {
+
+__device__ __forceinline__ double2 mul_i(double2 z) { return make_double2(-z.y, z.x); }
+
+struct RowEq {
+  int dom;        // domain whose equation this row carries
+  int bm;         // 1: Burton-Miller (standard + gamma * normal derivative), 0: standard
+  double2 scale;  // row multiplier
+};
+
+// Row plan of Sec. 5-6 for element with (P, M); half 0 = upper row, 1 = lower row.
+__device__ __forceinline__ RowEq row_eq(int form, int half, int P, int M, double k1) {
+  const double2 one = make_double2(1.0, 0.0);
+  const double2 malpha = make_double2(0.0, 1.0 / k1);   // -alpha = i/k_1
+  RowEq e;
+  if (form == BEM_FORM_CONV) {
+    if (half == 0) { e.dom = P; e.bm = (P == 0); e.scale = one; }
+    else { e.dom = M; e.bm = 0; e.scale = one; }
+  } else if (half == 0) {
+    e.dom = M; e.bm = 0; e.scale = (form == BEM_FORM_BETA1) ? one : malpha;
+  } else {
+    e.dom = P;
+    if (form == BEM_FORM_ORIG && P != 0) { e.bm = 0; e.scale = malpha; }
+    else { e.bm = 1; e.scale = one; }
+  }
+  return e;
+}
+
+__global__ void k_elements(ElemDev e, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double dx = e.bx[i] - e.ax[i], dy = e.by[i] - e.ay[i];
+  const double h = sqrt(dx * dx + dy * dy);
+  e.h[i] = h;
+  e.tx[i] = dx / h;
+  e.ty[i] = dy / h;
+  e.mx[i] = 0.5 * (e.ax[i] + e.bx[i]);
+  e.my[i] = 0.5 * (e.ay[i] + e.by[i]);
+}
+
+// Coefficients of one equation row at column j: cu multiplies u_j, cw multiplies w_j.
+//   standard:        cu = 1/2 d_ij + s D,                  cw = -s eps S
+//   Burton-Miller:   cu = 1/2 d_ij + s (D + gamma N),      cw = gamma eps/2 d_ij - s eps (S + gamma D*)
+// with s = sigma_{d,j}, gamma = alpha/eps_d, alpha = -i/k_1, and
+//   S = (i/4) sS,  D = (ik/4) sD,  D* = -(ik/4) sDs,  N = (ik/4) sN.
+struct PairSums { double2 sS, sD, sDs, sN; };
+
+__device__ __forceinline__ void quad_sums(double k, double xi, double yi, double nxi, double nyi, double mxj,
+                                          double myj, double txj, double tyj, double hj, const Quad& q, int bm,
+                                          PairSums& ps) {
+  ps.sS = ps.sD = ps.sDs = ps.sN = make_double2(0.0, 0.0);
+  const double nxj = -tyj, nyj = txj;
+  const double nn = nxi * nxj + nyi * nyj;
+  const double half_h = 0.5 * hj;
+  for (int m = 0; m < q.Q; ++m) {
+    const double s = half_h * q.t[m];
+    const double W = half_h * q.w[m];
+    const double zx0 = xi - (mxj + s * txj), zy0 = yi - (myj + s * tyj);
+    const double r = sqrt(zx0 * zx0 + zy0 * zy0);
+    const double ir = 1.0 / r;
+    const double ux = zx0 * ir, uy = zy0 * ir;
+    const double ci = ux * nxi + uy * nyi;   // zh . n_i
+    const double cj = ux * nxj + uy * nyj;   // zh . n_j
+    Bessel01 b;
+    bessel01(k * r, b);
+    ps.sS.x += W * b.j0; ps.sS.y += W * b.y0;
+    ps.sD.x += W * cj * b.j1; ps.sD.y += W * cj * b.y1;
+    if (bm) {
+      ps.sDs.x += W * ci * b.j1; ps.sDs.y += W * ci * b.y1;
+      const double a1 = W * ir * (nn - 2.0 * ci * cj);
+      const double a0 = W * k * ci * cj;
+      ps.sN.x += a1 * b.j1 + a0 * b.j0;
+      ps.sN.y += a1 * b.y1 + a0 * b.y0;
+    }
+  }
+}
+
+template <int MIXED>
+__global__ void __launch_bounds__(256) k_assemble(ElemDev e, int n, DomTab dom, Quad q, int form, void* Aout,
+                                                   void* Aloout, size_t lda) {
+  const int j = blockIdx.x * 32 + threadIdx.x;
+  const int i = blockIdx.y * 8 + threadIdx.y;
+  if (i >= n || j >= n) return;
+  const double xi = e.mx[i], yi = e.my[i];
+  const double nxi = -e.ty[i], nyi = e.tx[i];
+  const int Pi = e.P[i], Mi = e.M[i];
+  const double mxj = e.mx[j], myj = e.my[j], txj = e.tx[j], tyj = e.ty[j], hj = e.h[j];
+  const int Pj = e.P[j], Mj = e.M[j];
+  const double k1 = dom.k[0];
+
+  double2 out[2][2];
+#pragma unroll
+  for (int half = 0; half < 2; ++half) {
+    const RowEq eq = row_eq(form, half, Pi, Mi, k1);
+    const int d = eq.dom;
+    const double sg = (Pj == d) ? 1.0 : ((Mj == d) ? -1.0 : 0.0);
+    const double k = dom.k[d], eps = dom.eps[d];
+    const double gim = -1.0 / (k1 * eps);          // gamma = i * gim
+    double2 cu = make_double2(0.0, 0.0), cw = make_double2(0.0, 0.0);
+    if (i == j) {
+      // exact self terms: S_ii = (i/(2k)) [int J0 + i int Y0] (0..ka), N_ii = k^2 S_ii - (ik/2) H1(ka), D = D* = 0
+      const double ka = 0.5 * k * hj;
+      double ij0, iy0;
+      int_j0_y0(ka, ij0, iy0);
+      const double2 S = make_double2(-iy0 / (2.0 * k), ij0 / (2.0 * k));
+      Bessel01 b;
+      bessel01(ka, b);
+      // -(ik/2) H1 = -(ik/2)(j1 + i y1) = (k/2) y1 - i (k/2) j1
+      const double2 N = make_double2(k * k * S.x + 0.5 * k * b.y1, k * k * S.y - 0.5 * k * b.j1);
+      cu.x = 0.5;
+      cw = make_double2(-sg * eps * S.x, -sg * eps * S.y);
+      if (eq.bm) {
+        // + s gamma N ;  + gamma eps / 2
+        const double2 gN = make_double2(-gim * N.y, gim * N.x);
+        cu.x += sg * gN.x; cu.y += sg * gN.y;
+        cw.y += 0.5 * gim * eps;
+      }
+    } else if (sg != 0.0) {
+      PairSums ps;
+      quad_sums(k, xi, yi, nxi, nyi, mxj, myj, txj, tyj, hj, q, eq.bm, ps);
+      const double2 S = cscale(mul_i(ps.sS), 0.25);
+      const double2 D = cscale(mul_i(ps.sD), 0.25 * k);
+      cu = cscale(D, sg);
+      cw = cscale(S, -sg * eps);
+      if (eq.bm) {
+        const double2 Ds = cscale(mul_i(ps.sDs), -0.25 * k);
+        const double2 N = cscale(mul_i(ps.sN), 0.25 * k);
+        const double2 gN = make_double2(-gim * N.y, gim * N.x);
+        const double2 gDs = make_double2(-gim * Ds.y, gim * Ds.x);
+        cu.x += sg * gN.x; cu.y += sg * gN.y;
+        cw.x -= sg * eps * gDs.x; cw.y -= sg * eps * gDs.y;
+      }
+    }
+    out[half][0] = cmul(eq.scale, cu);
+    out[half][1] = cmul(eq.scale, cw);
+  }
+  const size_t r0 = (size_t)i * lda, r1 = (size_t)(n + i) * lda;
+  if (MIXED) {
+    float2* A = static_cast<float2*>(Aout);
+    float2* L = static_cast<float2*>(Aloout);
+    const size_t idx[4] = {r0 + j, r0 + n + j, r1 + j, r1 + n + j};
+    const double2 v[4] = {out[0][0], out[0][1], out[1][0], out[1][1]};
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const float hx = (float)v[t].x, hy = (float)v[t].y;
+      A[idx[t]] = make_float2(hx, hy);
+      L[idx[t]] = make_float2((float)(v[t].x - (double)hx), (float)(v[t].y - (double)hy));
+    }
+  } else {
+    double2* A = static_cast<double2*>(Aout);
+    A[r0 + j] = out[0][0];
+    A[r0 + n + j] = out[0][1];
+    A[r1 + j] = out[1][0];
+    A[r1 + n + j] = out[1][1];
+  }
+}
+
+// b[r][half*N + i] for plane wave r (eq. naive_bie right-hand side, placed like the matrix rows).
+__global__ void k_rhs_planewave(ElemDev e, int n, DomTab dom, int form, int nrhs, const double* ang, double2* b) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int r = blockIdx.y;
+  if (i >= n || r >= nrhs) return;
+  const double k1 = dom.k[0];
+  double st, ct;
+  sincos(ang[r], &st, &ct);
+  const double ph = k1 * (ct * e.mx[i] + st * e.my[i]);
+  double sp, cp;
+  sincos(ph, &sp, &cp);
+  const double2 uin = make_double2(cp, sp);
+  const double dn = ct * (-e.ty[i]) + st * e.tx[i];           // d . n_i
+  // alpha q_in = (-i/k1) (i k1 dn) u_in = dn u_in
+  const double2 bm_val = make_double2(uin.x * (1.0 + dn), uin.y * (1.0 + dn));
+  double2* br = b + (size_t)r * 2 * n;
+#pragma unroll
+  for (int half = 0; half < 2; ++half) {
+    const RowEq eq = row_eq(form, half, e.P[i], e.M[i], k1);
+    double2 v = make_double2(0.0, 0.0);
+    if (eq.dom == 0) v = cmul(eq.scale, eq.bm ? bm_val : uin);
+    br[half * n + i] = v;
+  }
+}
+
+// u_inf(theta_a) = e^{i pi/4}/sqrt(8 pi k1) sum_j s_{1,j} sum_q W_q e^{-i k1 xh.y_q} [w_j + i k1 (xh.n_j) u_j]
+// One block per (angle, rhs); threads stride over elements; FP64 block reduction.
+__global__ void __launch_bounds__(256) k_far_field(ElemDev e, int n, DomTab dom, Quad q, const double2* x, int nang,
+                                                   const double* ang, double2* out) {
+  const int a = blockIdx.x, r = blockIdx.y;
+  const double k1 = dom.k[0];
+  double st, ct;
+  sincos(ang[a], &st, &ct);
+  const double2* xr = x + (size_t)r * 2 * n;
+  double2 acc = make_double2(0.0, 0.0);
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    const int Pj = e.P[j], Mj = e.M[j];
+    const double sg = (Pj == 0) ? 1.0 : ((Mj == 0) ? -1.0 : 0.0);
+    if (sg == 0.0) continue;
+    const double tx = e.tx[j], ty = e.ty[j], hh = 0.5 * e.h[j];
+    const double mx = e.mx[j], my = e.my[j];
+    double2 f = make_double2(0.0, 0.0);
+    for (int m = 0; m < q.Q; ++m) {
+      const double s = hh * q.t[m];
+      const double ph = -k1 * (ct * (mx + s * tx) + st * (my + s * ty));
+      double sp, cp;
+      sincos(ph, &sp, &cp);
+      f.x += hh * q.w[m] * cp;
+      f.y += hh * q.w[m] * sp;
+    }
+    const double xn = ct * (-ty) + st * tx;
+    const double2 u = xr[j], w = xr[n + j];
+    // w + i k1 xn u
+    const double2 brk = make_double2(w.x - k1 * xn * u.y, w.y + k1 * xn * u.x);
+    const double2 c = cmul(f, brk);
+    acc.x += sg * c.x; acc.y += sg * c.y;
+  }
+  __shared__ double2 red[256];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] = cadd(red[threadIdx.x], red[threadIdx.x + o]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double c = 1.0 / sqrt(8.0 * kPi * k1);
+    const double2 ph = make_double2(c * kInvSqrt2, c * kInvSqrt2);   // e^{i pi/4} / sqrt(8 pi k1)
+    out[(size_t)r * nang + a] = cmul(ph, red[0]);
+  }
+}
+
+__global__ void k_matrix_to_c64(const void* A, const void* Alo, int mixed, int which, size_t nn, double2* out) {
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < nn; t += (size_t)gridDim.x * blockDim.x) {
+    if (!mixed) {
+      out[t] = static_cast<const double2*>(A)[t];
+    } else {
+      const float2 h = static_cast<const float2*>(A)[t];
+      double2 v = make_double2(h.x, h.y);
+      if (which == 1) {
+        const float2 l = static_cast<const float2*>(Alo)[t];
+        v.x += (double)l.x; v.y += (double)l.y;
+      }
+      out[t] = v;
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_elements(const ElemDev& e, int n, cudaStream_t s) {
+  k_elements<<<(n + 255) / 256, 256, 0, s>>>(e, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_assemble(const ElemDev& e, int n, const DomTab& dom, const Quad& q, int form, int store_mixed,
+                            void* A, void* Alo, size_t lda, cudaStream_t s) {
+  dim3 blk(32, 8);
+  dim3 grd((n + 31) / 32, (n + 7) / 8);
+  if (store_mixed) k_assemble<1><<<grd, blk, 0, s>>>(e, n, dom, q, form, A, Alo, lda);
+  else k_assemble<0><<<grd, blk, 0, s>>>(e, n, dom, q, form, A, Alo, lda);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rhs_planewave(const ElemDev& e, int n, const DomTab& dom, int form, int nrhs,
+                                 const double* angles_dev, double2* b, cudaStream_t s) {
+  dim3 grd((n + 127) / 128, nrhs);
+  k_rhs_planewave<<<grd, 128, 0, s>>>(e, n, dom, form, nrhs, angles_dev, b);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_far_field(const ElemDev& e, int n, const DomTab& dom, const Quad& q, int nrhs, const double2* x,
+                             int nang, const double* ang_dev, double2* out, cudaStream_t s) {
+  dim3 grd(nang, nrhs);
+  k_far_field<<<grd, 256, 0, s>>>(e, n, dom, q, x, nang, ang_dev, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_matrix_to_c64(const void* A, const void* Alo, int mixed, int which, size_t nn, double2* out,
+                                 cudaStream_t s) {
+  k_matrix_to_c64<<<1024, 256, 0, s>>>(A, Alo, mixed, which, nn, out);
+  return cudaGetLastError();
+}
+
+}  // namespace bem

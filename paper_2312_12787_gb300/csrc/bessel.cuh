@@ -1,0 +1,186 @@
+// Bessel functions J0, J1, Y0, Y1 of real positive argument, giving the Hankel functions
+// H0^(1) = J0 + i Y0 and H1^(1) = J1 + i Y1 that make up the kernels of the single-, double-, adjoint
+// double- and hypersingular operators (paper Sec. 3.3, eq. fundamental_sol: G = (i/4) H0^(1)(k r)).
+//
+// Written from the published mathematics (NIST DLMF), not from any library's internals:
+//   * x < BEM_X_SERIES:   ascending power series, DLMF 10.2.2 (J_n) and 10.8.1 (Y_n, n = 0, 1).
+//   * x < BEM_X_ASYMP:    Miller's backward recurrence for J_n (DLMF 3.6(vi), 10.74(iv)), normalised by
+//                         1 = J0 + 2 sum J_2k (DLMF 10.12.4), and the Neumann expansions
+//                         Y0 = (2/pi)(ln(x/2)+gamma) J0 - (4/pi) sum_k (-1)^k J_2k / k  (a Neumann expansion, DLMF 10.23(ii))
+//                         Y1 = -Y0' = (2/pi)[(ln(x/2)+gamma) J1 - J0/x]
+//                              + (2/pi) sum_k (-1)^k (J_{2k-1} - J_{2k+1}) / k.
+//   * otherwise:          Hankel's asymptotic expansion, DLMF 10.17.5 with a_k(nu) from 10.17.1.
+// Double precision throughout; the accuracy target is ~1e-15 relative to |H|.
+#pragma once
+
+#if defined(__CUDACC__)
+#define BEM_HD __host__ __device__ __forceinline__
+#else
+#define BEM_HD inline
+#include <cmath>
+#endif
+
+namespace bem {
+
+constexpr double kPi = 3.14159265358979323846264338327950288;
+constexpr double kTwoOverPi = 0.636619772367581343075535053490057448;
+constexpr double kEulerGamma = 0.577215664901532860606512090082402431;
+constexpr double kInvSqrt2 = 0.707106781186547524400844362104849039;
+
+constexpr double BEM_X_SERIES = 2.0;   // below: ascending series
+constexpr double BEM_X_ASYMP = 18.0;   // at and above: Hankel asymptotic expansion
+constexpr int BEM_MILLER_START = 56;   // fixed (even) starting order of the backward recurrence
+constexpr int BEM_ASYMP_TERMS = 22;    // terms k = 0 .. BEM_ASYMP_TERMS-1 of DLMF 10.17.5
+
+struct Bessel01 {
+  double j0, y0, j1, y1;
+};
+
+// a_k(nu) of DLMF 10.17.1: a_0 = 1, a_k = a_{k-1} (4 nu^2 - (2k-1)^2) / (8k), for nu = 0 and nu = 1,
+// multiplied by i^k and split into the real (even k) and imaginary (odd k) parts of sum i^k a_k x^-k.
+struct AsympCoef {
+  double p0[BEM_ASYMP_TERMS], q0[BEM_ASYMP_TERMS], p1[BEM_ASYMP_TERMS], q1[BEM_ASYMP_TERMS];
+};
+constexpr AsympCoef make_asymp_coef() {
+  AsympCoef c{};
+  double a0 = 1.0, a1 = 1.0;
+  for (int k = 0; k < BEM_ASYMP_TERMS; ++k) {
+    if (k > 0) {
+      const double m = 2.0 * k - 1.0;
+      a0 = a0 * (-(m * m)) / (8.0 * k);
+      a1 = a1 * (4.0 - m * m) / (8.0 * k);
+    }
+    const int r = k & 3;   // i^k = 1, i, -1, -i
+    c.p0[k] = r == 0 ? a0 : (r == 2 ? -a0 : 0.0);
+    c.q0[k] = r == 1 ? a0 : (r == 3 ? -a0 : 0.0);
+    c.p1[k] = r == 0 ? a1 : (r == 2 ? -a1 : 0.0);
+    c.q1[k] = r == 1 ? a1 : (r == 3 ? -a1 : 0.0);
+  }
+  return c;
+}
+
+BEM_HD void bessel01_series(double x, Bessel01& b) {
+  const double t = 0.25 * x * x;
+  double e0 = 1.0;          // (-t)^m / (m!)^2
+  double e1 = 1.0;          // (-t)^m / (m! (m+1)!)
+  double sj0 = 1.0, sj1 = 1.0;
+  double hm = 0.0;          // harmonic number H_m
+  double sy0 = 0.0;         // sum_{m>=1} -(-t)^m H_m / (m!)^2
+  double sy1 = 1.0;         // sum_{m>=0} (H_m + H_{m+1}) (-t)^m / (m!(m+1)!), m = 0 term is H_1 = 1
+  for (int m = 1; m < 40; ++m) {
+    const double dm = (double)m;
+    e0 *= -t / (dm * dm);
+    e1 *= -t / (dm * (dm + 1.0));
+    const double hm1 = hm + 1.0 / dm;           // H_m
+    const double hm2 = hm1 + 1.0 / (dm + 1.0);  // H_{m+1}
+    sj0 += e0;
+    sj1 += e1;
+    sy0 -= e0 * hm1;
+    sy1 += e1 * (hm1 + hm2);
+    hm = hm1;
+    if (fabs(e0) * (hm2 + 1.0) < 1e-18 * fabs(sj0) && fabs(e1) * (hm2 + 1.0) < 1e-18 * fabs(sj1)) break;
+  }
+  const double lg = log(0.5 * x) + kEulerGamma;
+  b.j0 = sj0;
+  b.j1 = 0.5 * x * sj1;
+  b.y0 = kTwoOverPi * (lg * b.j0 + sy0);
+  b.y1 = -kTwoOverPi / x + kTwoOverPi * lg * b.j1 - (0.5 * x / kPi) * sy1;
+}
+
+// Valid for BEM_X_SERIES <= x < BEM_X_ASYMP: the fixed start order keeps f_n within range there.
+BEM_HD void bessel01_miller(double x, Bessel01& b) {
+  const double two_over_x = 2.0 / x;
+  double fp = 0.0;        // f_{n+1}
+  double f = 1e-200;      // f_n, n = BEM_MILLER_START
+  double norm = 0.0;      // sum over even n >= 2 of f_n
+  double sy0 = 0.0;       // sum_k (-1)^k f_{2k}/k
+  double sy1 = 0.0;       // sum_k (-1)^k (f_{2k-1} - f_{2k+1})/k
+  double f_odd_above = 0.0;
+#pragma unroll
+  for (int n = BEM_MILLER_START; n >= 1; --n) {
+    if ((n & 1) == 0) {
+      const int kk = n >> 1;
+      const double c = ((kk & 1) ? -1.0 : 1.0) / (double)kk;
+      norm += f;
+      sy0 += c * f;
+      f_odd_above = fp;
+    } else {
+      const int kk = (n + 1) >> 1;
+      const double c = ((kk & 1) ? -1.0 : 1.0) / (double)kk;
+      sy1 += c * (f - f_odd_above);
+    }
+    const double fm = ((double)n * two_over_x) * f - fp;   // f_{n-1}
+    fp = f;
+    f = fm;
+  }
+  const double s = 1.0 / (f + 2.0 * norm);
+  const double j0 = f * s, j1 = fp * s;
+  const double lg = log(0.5 * x) + kEulerGamma;
+  b.j0 = j0;
+  b.j1 = j1;
+  b.y0 = kTwoOverPi * (lg * j0) - 2.0 * kTwoOverPi * sy0 * s;
+  b.y1 = kTwoOverPi * (lg * j1 - j0 / x) + kTwoOverPi * sy1 * s;
+}
+
+BEM_HD void bessel01_asymp(double x, Bessel01& b) {
+  constexpr AsympCoef C = make_asymp_coef();
+  const double y = 1.0 / x;
+  double p0 = 0.0, q0 = 0.0, p1 = 0.0, q1 = 0.0;
+#pragma unroll
+  for (int k = BEM_ASYMP_TERMS - 1; k >= 0; --k) {
+    // Horner in y; the zero coefficients fold away
+    p0 = C.p0[k] + y * p0; q0 = C.q0[k] + y * q0;
+    p1 = C.p1[k] + y * p1; q1 = C.q1[k] + y * q1;
+  }
+  double sn, cs;
+#if defined(__CUDA_ARCH__)
+  sincos(x, &sn, &cs);
+#else
+  sn = sin(x); cs = cos(x);
+#endif
+  const double amp = sqrt(kTwoOverPi * y) * kInvSqrt2;
+  // e^{i(x - pi/4)} = ((cos x + sin x) + i (sin x - cos x)) / sqrt 2
+  const double er = (cs + sn) * amp, ei = (sn - cs) * amp;
+  // H0 = (p0 + i q0) e^{i(x - pi/4)};  H1 = (p1 + i q1) e^{i(x - 3pi/4)} = -i (p1 + i q1) e^{i(x - pi/4)}
+  b.j0 = p0 * er - q0 * ei;
+  b.y0 = p0 * ei + q0 * er;
+  const double hr = p1 * er - q1 * ei, hi = p1 * ei + q1 * er;
+  b.j1 = hi;
+  b.y1 = -hr;
+}
+
+BEM_HD void bessel01(double x, Bessel01& b) {
+  if (x < BEM_X_SERIES) bessel01_series(x, b);
+  else if (x < BEM_X_ASYMP) bessel01_miller(x, b);
+  else bessel01_asymp(x, b);
+}
+
+// integral_0^x J0(t) dt and integral_0^x Y0(t) dt for the weakly singular self-element integral,
+// by termwise integration of the ascending series DLMF 10.2.2 / 10.8.1 (x is small: x = k h / 2),
+// with Y0 = (2/pi)(ln(t/2)+gamma) J0(t) + (2/pi) sum_{m>=1} (-1)^{m+1} H_m (t^2/4)^m/(m!)^2 and
+//   int_0^x t^{2m} ln(t/2) dt = x^{2m+1}/(2m+1) (ln(x/2) - 1/(2m+1)).
+// Only valid for moderate x; elements are always far below a wavelength in practice (x < ~10).
+BEM_HD void int_j0_y0(double x, double& ij0, double& iy0) {
+  const double t = 0.25 * x * x;
+  double c = 1.0;             // (-t)^m/(m!)^2
+  double hm = 0.0;
+  const double lg = log(0.5 * x) + kEulerGamma;
+  double sj = 0.0, sy = 0.0;
+  for (int m = 0; m < 60; ++m) {
+    const double dm = (double)m;
+    if (m > 0) {
+      c *= -t / (dm * dm);
+      hm += 1.0 / dm;
+    }
+    const double inv = 1.0 / (2.0 * dm + 1.0);
+    const double term_j = c * inv;                       // integral of c t^0 scaled: x * c/(2m+1)
+    sj += term_j;
+    // (2/pi) [ (ln(x/2)+gamma) c/(2m+1) - c/(2m+1)^2 ] - (2/pi) c H_m/(2m+1)
+    sy += c * inv * (lg - inv - hm);
+    if (m > 3 && fabs(c) * (hm + 2.0) < 1e-19 * (fabs(sj) + 1e-300)) break;
+  }
+  ij0 = x * sj;
+  iy0 = kTwoOverPi * x * sy;
+}
+
+}  // namespace bem

@@ -1,0 +1,113 @@
+// Internal declarations shared by the translation units of libbem (not part of the C interface).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+#include <string>
+
+#include "bem.h"
+
+namespace bem {
+
+constexpr int kMaxDomains = 64;
+constexpr int kMaxQuad = 16;
+
+// Per-element geometry in structure-of-arrays form (device).  Normal = (-ty, tx).
+struct ElemDev {
+  const double* ax; const double* ay;   // start vertex
+  const double* bx; const double* by;   // end vertex
+  double* mx; double* my;               // centre (collocation point)
+  double* tx; double* ty;               // unit tangent
+  double* h;                            // length
+  const int* P; const int* M;           // domain the normal points out of / into
+};
+
+struct DomTab {
+  int n;
+  double k[kMaxDomains];
+  double eps[kMaxDomains];
+};
+
+struct Quad {
+  int Q;
+  double t[kMaxQuad];
+  double w[kMaxQuad];
+};
+
+// ---- complex helpers ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+// conj(a) * b
+__host__ __device__ __forceinline__ double2 cdotc(double2 a, double2 b) {
+  return make_double2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+
+// ---- launchers (each returns cudaGetLastError() of its launch) -----------------------------------
+cudaError_t launch_elements(const ElemDev& e, int n, cudaStream_t s);
+cudaError_t launch_assemble(const ElemDev& e, int n, const DomTab& dom, const Quad& q, int form, int store_mixed,
+                            void* A, void* Alo, size_t lda, cudaStream_t s);
+cudaError_t launch_rhs_planewave(const ElemDev& e, int n, const DomTab& dom, int form, int nrhs,
+                                 const double* angles_dev, double2* b, cudaStream_t s);
+cudaError_t launch_far_field(const ElemDev& e, int n, const DomTab& dom, const Quad& q, int nrhs, const double2* x,
+                             int nang, const double* ang_dev, double2* out, cudaStream_t s);
+// Matrix to c64 copy for inspection: which 0 -> main (c64 or hi), 1 -> hi + lo.
+cudaError_t launch_matrix_to_c64(const void* A, const void* Alo, int mixed, int which, size_t nn, double2* out,
+                                 cudaStream_t s);
+
+// y[r] = A x[r] for nrhs columns; A is n x n row-major (lda).  FP64 path.
+cudaError_t launch_matvec_c64(const double2* A, size_t lda, int n, int nrhs, const double2* x, double2* y,
+                              cudaStream_t s);
+// y[r] = A x[r] with A complex FP32 (hi only), x and y complex FP32.
+cudaError_t launch_matvec_c32(const float2* A, size_t lda, int n, int nrhs, const float2* x, float2* y,
+                              const int* active, cudaStream_t s);
+// r = b - (hi + lo) x, with FP64 x, b, r (refinement residual); also writes ||r||^2 partials per column.
+cudaError_t launch_residual_split(const float2* Ahi, const float2* Alo, size_t lda, int n, int nrhs,
+                                  const double2* x, const double2* b, double2* r, cudaStream_t s);
+// tcgen05 tensor-core GEMM Y = A X (A c32, X / Y c32, nrhs <= 64).  Returns cudaErrorNotSupported if the
+// shape is not supported by the kernel.
+cudaError_t launch_matvec_tc(const float2* A, size_t lda, int n, int nrhs, const float2* x, float2* y,
+                             void* ws, size_t ws_bytes, cudaStream_t s);
+size_t matvec_tc_workspace_bytes(int n, int nrhs);
+bool matvec_tc_supported(int n, int nrhs);
+
+// Element-wise conversions between complex FP64 and FP32 blocks; column 2-norms of an FP64 block.
+cudaError_t launch_convert_c64_c32(const double2* in, float2* out, size_t count, cudaStream_t s);
+cudaError_t launch_convert_c32_c64(const float2* in, double2* out, size_t count, cudaStream_t s);
+cudaError_t launch_column_norms(const double2* v, int n, int ncol, double* out, cudaStream_t s);
+
+// GMRES building blocks for nrhs systems sharing one matrix; see krylov.cu.
+struct KrylovState {
+  int n;            // unknowns per system
+  int nrhs;         // systems
+  int m;            // Krylov dimension limit
+  int basis_fp32;   // 1: V, W are float2; 0: double2
+  void* V;          // (m+1) x nrhs x n
+  void* W;          // nrhs x n
+  double2* H;       // nrhs x m x (m+1)   column j of system s at H + (s*m + j)*(m+1)
+  double2* cs;      // nrhs x m
+  double2* sn;      // nrhs x m
+  double2* g;       // nrhs x (m+1)
+  double2* y;       // nrhs x m (least-squares solution)
+  double* beta;     // nrhs
+  double* hnext;    // nrhs: ||w|| after orthogonalisation
+  double2* part;    // scratch: nrhs x nchunk x (m+1) partial dot products
+  double* npart;    // scratch: nrhs x nchunk partial squared norms
+  double2* hcol;    // nrhs x (m+1): projections of the current pass
+  int* active;      // nrhs: 1 while iterating
+  int* iters;       // nrhs
+  double* resid;    // nrhs: estimated relative residual
+  int* jdev;        // current iteration index (device copy)
+  int* n_active;    // device counter of active systems
+};
+int krylov_nchunk(int n);
+cudaError_t krylov_start(const KrylovState& st, const double2* r0, double tol_unused, cudaStream_t s);
+cudaError_t krylov_orthogonalise(const KrylovState& st, int passes, cudaStream_t s);
+cudaError_t krylov_finish_step(const KrylovState& st, double tol, cudaStream_t s);
+cudaError_t krylov_update_solution(const KrylovState& st, double2* x, cudaStream_t s);
+
+}  // namespace bem

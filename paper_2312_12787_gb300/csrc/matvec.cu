@@ -1,0 +1,312 @@
+// Dense complex matrix-vector and matrix-block products of the GMRES solve (steps a6, a9, a11).
+//
+// A is the 2N x 2N collocation matrix, row-major.  Right-hand-side blocks are stored column after
+// column (column s of X at X + s*n), so both A and X are contiguous along the summation index.
+//
+//  * k_gemv_f64   - y = A x, one warp per row, FP64 arithmetic (FP64 path; on GB300 the FP64 pipe,
+//                   not HBM, bounds it).  Also used with the split loader for the mixed refinement
+//                   residual r = b - (hi + lo) x.
+//  * k_gemv_c32   - y = A x with complex FP32 storage and products (mixed inner solve): each lane streams
+//                   16-byte float4 loads (two complex entries), so a warp moves 512 contiguous bytes per
+//                   step; partial sums are folded into FP64 every 16 steps.  HBM-bound.
+//  * k_gemm_f64   - Y = A X for several columns, SIMT tile 64 rows x 64 columns, FP64 arithmetic.
+//  * k_gemm_c32   - the same in complex FP32 with two-level FP32 accumulation.
+#include "internal.cuh"
+
+namespace bem {
+
+namespace {
+
+struct LoadC64 {
+  const double2* A;
+  __device__ __forceinline__ double2 operator()(size_t idx) const { return __ldg(A + idx); }
+};
+struct LoadSplit {
+  const float2* hi;
+  const float2* lo;
+  __device__ __forceinline__ double2 operator()(size_t idx) const {
+    const float2 h = __ldg(hi + idx), l = __ldg(lo + idx);
+    return make_double2((double)h.x + (double)l.x, (double)h.y + (double)l.y);
+  }
+};
+
+__device__ __forceinline__ double2 warp_sum(double2 v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+    v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+  }
+  return v;
+}
+
+// y[s][r] = (RESID ? b[s][r] - : ) sum_c A[r][c] x[s][c]; grid.y = s
+template <class ALoad, bool RESID>
+__global__ void __launch_bounds__(256) k_gemv_f64(ALoad A, size_t lda, int n, const double2* x, const double2* b,
+                                                   double2* y) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int r = blockIdx.x * 8 + warp;
+  const int s = blockIdx.y;
+  if (r >= n) return;
+  const double2* xs = x + (size_t)s * n;
+  const size_t row = (size_t)r * lda;
+  double2 acc0 = make_double2(0, 0), acc1 = make_double2(0, 0);
+  int c = lane;
+  for (; c + 32 < n; c += 64) {
+    const double2 a0 = A(row + c), a1 = A(row + c + 32);
+    const double2 x0 = __ldg(xs + c), x1 = __ldg(xs + c + 32);
+    acc0.x = fma(a0.x, x0.x, fma(-a0.y, x0.y, acc0.x));
+    acc0.y = fma(a0.x, x0.y, fma(a0.y, x0.x, acc0.y));
+    acc1.x = fma(a1.x, x1.x, fma(-a1.y, x1.y, acc1.x));
+    acc1.y = fma(a1.x, x1.y, fma(a1.y, x1.x, acc1.y));
+  }
+  for (; c < n; c += 32) {
+    const double2 a0 = A(row + c);
+    const double2 x0 = __ldg(xs + c);
+    acc0.x = fma(a0.x, x0.x, fma(-a0.y, x0.y, acc0.x));
+    acc0.y = fma(a0.x, x0.y, fma(a0.y, x0.x, acc0.y));
+  }
+  double2 acc = warp_sum(cadd(acc0, acc1));
+  if (lane == 0) {
+    if (RESID) {
+      const double2 bb = b[(size_t)s * n + r];
+      acc = csub(bb, acc);
+    }
+    y[(size_t)s * n + r] = acc;
+  }
+}
+
+// complex FP32: each lane takes two consecutive complex entries per step (one float4).
+// n must be even (it is: n = 2N).  grid.y = column; inactive columns are skipped.
+__global__ void __launch_bounds__(256) k_gemv_c32(const float2* __restrict__ A, size_t lda, int n,
+                                                   const float2* __restrict__ x, float2* __restrict__ y,
+                                                   const int* __restrict__ active) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int r = blockIdx.x * 8 + warp;
+  const int s = blockIdx.y;
+  if (r >= n) return;
+  if (active && !active[s]) return;
+  const float4* row = reinterpret_cast<const float4*>(A + (size_t)r * lda);
+  const float4* xs = reinterpret_cast<const float4*>(x + (size_t)s * n);
+  const int n2 = n >> 1;   // float4 per row
+  double accx = 0.0, accy = 0.0;
+  int c = lane;
+  while (c < n2) {
+    float px = 0.f, py = 0.f;
+    // up to 16 steps of 32 lanes in FP32, then fold into FP64
+#pragma unroll 4
+    for (int t = 0; t < 16 && c < n2; ++t, c += 32) {
+      const float4 a = __ldcs(row + c);
+      const float4 v = __ldg(xs + c);
+      px = fmaf(a.x, v.x, px); px = fmaf(-a.y, v.y, px);
+      py = fmaf(a.x, v.y, py); py = fmaf(a.y, v.x, py);
+      px = fmaf(a.z, v.z, px); px = fmaf(-a.w, v.w, px);
+      py = fmaf(a.z, v.w, py); py = fmaf(a.w, v.z, py);
+    }
+    accx += (double)px;
+    accy += (double)py;
+  }
+  double2 acc = warp_sum(make_double2(accx, accy));
+  if (lane == 0) y[(size_t)s * n + r] = make_float2((float)acc.x, (float)acc.y);
+}
+
+// SIMT tiled GEMM, FP64: Y[s][r] = sum_c A[r][c] X[s][c].  Tile 64 rows x 64 columns x 8, 256 threads,
+// each thread 4 rows x 4 columns (rows ty + 16 i, columns tx + 16 j).
+template <class ALoad, bool RESID>
+__global__ void __launch_bounds__(256) k_gemm_f64(ALoad A, size_t lda, int n, int nrhs, const double2* X,
+                                                   const double2* B, double2* Y) {
+  constexpr int BR = 64, BS = 64, BK = 8;
+  __shared__ double2 As[BK][BR + 1];
+  __shared__ double2 Xs[BK][BS + 1];
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  const int r0 = blockIdx.x * BR, s0 = blockIdx.y * BS;
+  double2 acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = make_double2(0, 0);
+  for (int k0 = 0; k0 < n; k0 += BK) {
+    // 512 A values and 512 X values per tile, two each per thread
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      const int e = tid + t * 256;
+      const int rr = e >> 3, kk = e & 7;
+      const int gr = r0 + rr, gk = k0 + kk;
+      As[kk][rr] = (gr < n && gk < n) ? A((size_t)gr * lda + gk) : make_double2(0, 0);
+      const int gs = s0 + rr;
+      Xs[kk][rr] = (gs < nrhs && gk < n) ? X[(size_t)gs * n + gk] : make_double2(0, 0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      double2 av[4], xv[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) av[a] = As[kk][ty + 16 * a];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) xv[b] = Xs[kk][tx + 16 * b];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          acc[a][b].x = fma(av[a].x, xv[b].x, fma(-av[a].y, xv[b].y, acc[a][b].x));
+          acc[a][b].y = fma(av[a].x, xv[b].y, fma(av[a].y, xv[b].x, acc[a][b].y));
+        }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int gr = r0 + ty + 16 * a, gs = s0 + tx + 16 * b;
+      if (gr < n && gs < nrhs) {
+        double2 v = acc[a][b];
+        if (RESID) v = csub(B[(size_t)gs * n + gr], v);
+        Y[(size_t)gs * n + gr] = v;
+      }
+    }
+}
+
+// SIMT tiled GEMM in complex FP32, same tiling; the inner FP32 accumulator is folded into a second FP32
+// accumulator every 64 columns to keep the summation error near FP32 rounding of short sums.
+__global__ void __launch_bounds__(256) k_gemm_c32(const float2* __restrict__ A, size_t lda, int n, int nrhs,
+                                                   const float2* __restrict__ X, float2* __restrict__ Y) {
+  constexpr int BR = 64, BS = 64, BK = 8;
+  __shared__ float2 As[BK][BR + 1];
+  __shared__ float2 Xs[BK][BS + 1];
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  const int r0 = blockIdx.x * BR, s0 = blockIdx.y * BS;
+  float2 acc[4][4], tot[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) { acc[a][b] = make_float2(0, 0); tot[a][b] = make_float2(0, 0); }
+  int tiles = 0;
+  for (int k0 = 0; k0 < n; k0 += BK) {
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      const int e = tid + t * 256;
+      const int rr = e >> 3, kk = e & 7;
+      const int gr = r0 + rr, gk = k0 + kk;
+      As[kk][rr] = (gr < n && gk < n) ? A[(size_t)gr * lda + gk] : make_float2(0, 0);
+      const int gs = s0 + rr;
+      Xs[kk][rr] = (gs < nrhs && gk < n) ? X[(size_t)gs * n + gk] : make_float2(0, 0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      float2 av[4], xv[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) av[a] = As[kk][ty + 16 * a];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) xv[b] = Xs[kk][tx + 16 * b];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          acc[a][b].x = fmaf(av[a].x, xv[b].x, fmaf(-av[a].y, xv[b].y, acc[a][b].x));
+          acc[a][b].y = fmaf(av[a].x, xv[b].y, fmaf(av[a].y, xv[b].x, acc[a][b].y));
+        }
+    }
+    __syncthreads();
+    if (++tiles == 8) {
+      tiles = 0;
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          tot[a][b].x += acc[a][b].x; tot[a][b].y += acc[a][b].y;
+          acc[a][b] = make_float2(0, 0);
+        }
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int gr = r0 + ty + 16 * a, gs = s0 + tx + 16 * b;
+      if (gr < n && gs < nrhs)
+        Y[(size_t)gs * n + gr] = make_float2(tot[a][b].x + acc[a][b].x, tot[a][b].y + acc[a][b].y);
+    }
+}
+
+__global__ void k_c64_to_c32(const double2* in, float2* out, size_t count) {
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < count; t += (size_t)gridDim.x * blockDim.x)
+    out[t] = make_float2((float)in[t].x, (float)in[t].y);
+}
+__global__ void k_c32_to_c64(const float2* in, double2* out, size_t count) {
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < count; t += (size_t)gridDim.x * blockDim.x)
+    out[t] = make_double2(in[t].x, in[t].y);
+}
+// one block per column, FP64 sum of squares
+__global__ void __launch_bounds__(256) k_column_norms(const double2* v, int n, double* out) {
+  __shared__ double red[8];
+  const double2* vs = v + (size_t)blockIdx.x * n;
+  double acc = 0.0;
+  for (int k = threadIdx.x; k < n; k += 256) acc += vs[k].x * vs[k].x + vs[k].y * vs[k].y;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += red[w];
+    out[blockIdx.x] = sqrt(t);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_convert_c64_c32(const double2* in, float2* out, size_t count, cudaStream_t s) {
+  k_c64_to_c32<<<1024, 256, 0, s>>>(in, out, count);
+  return cudaGetLastError();
+}
+cudaError_t launch_convert_c32_c64(const float2* in, double2* out, size_t count, cudaStream_t s) {
+  k_c32_to_c64<<<1024, 256, 0, s>>>(in, out, count);
+  return cudaGetLastError();
+}
+cudaError_t launch_column_norms(const double2* v, int n, int ncol, double* out, cudaStream_t s) {
+  k_column_norms<<<ncol, 256, 0, s>>>(v, n, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_matvec_c64(const double2* A, size_t lda, int n, int nrhs, const double2* x, double2* y,
+                              cudaStream_t s) {
+  LoadC64 ld{A};
+  if (nrhs == 1) {
+    dim3 grd((n + 7) / 8, 1);
+    k_gemv_f64<LoadC64, false><<<grd, 256, 0, s>>>(ld, lda, n, x, nullptr, y);
+  } else {
+    dim3 grd((n + 63) / 64, (nrhs + 63) / 64);
+    k_gemm_f64<LoadC64, false><<<grd, 256, 0, s>>>(ld, lda, n, nrhs, x, nullptr, y);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_matvec_c32(const float2* A, size_t lda, int n, int nrhs, const float2* x, float2* y,
+                              const int* active, cudaStream_t s) {
+  if (nrhs <= 2) {
+    dim3 grd((n + 7) / 8, nrhs);
+    k_gemv_c32<<<grd, 256, 0, s>>>(A, lda, n, x, y, active);
+  } else {
+    dim3 grd((n + 63) / 64, (nrhs + 63) / 64);
+    k_gemm_c32<<<grd, 256, 0, s>>>(A, lda, n, nrhs, x, y);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_residual_split(const float2* Ahi, const float2* Alo, size_t lda, int n, int nrhs,
+                                  const double2* x, const double2* b, double2* r, cudaStream_t s) {
+  LoadSplit ld{Ahi, Alo};
+  if (nrhs == 1) {
+    dim3 grd((n + 7) / 8, 1);
+    k_gemv_f64<LoadSplit, true><<<grd, 256, 0, s>>>(ld, lda, n, x, b, r);
+  } else {
+    dim3 grd((n + 63) / 64, (nrhs + 63) / 64);
+    k_gemm_f64<LoadSplit, true><<<grd, 256, 0, s>>>(ld, lda, n, nrhs, x, b, r);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace bem

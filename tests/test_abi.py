@@ -1,0 +1,89 @@
+"""The C-ABI library builds, loads without a GPU and exports every symbol include/bem.h declares;
+host-side argument validation (no device work)."""
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2312_12787_gb300 import build as B
+    B.build()
+    import paper_2312_12787_gb300 as P
+    return P
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "bem.h")).read()
+    return sorted(set(re.findall(r"BEM_API\s+[\w\s\*]+?\b(bem_\w+)\s*\(", txt)))
+
+
+def test_header_declares_entry_points():
+    names = _declared()
+    assert "bem_solve" in names and "bem_assemble" in names and len(names) >= 19
+
+
+def test_library_exports_every_declared_symbol(lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", lib.bem.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\sT\s(bem_\w+)", out))
+    missing = [n for n in _declared() if n not in exported]
+    assert not missing, missing
+    L = lib.load()
+    for n in _declared():
+        assert hasattr(L, n)
+    assert set(lib.EXPORTS) == set(_declared())
+
+
+def test_version_and_defaults(lib):
+    assert "sm_103a" in lib.bem_version()
+    o = lib.bem.bem_default_opts()
+    assert o.quad_order == 4 and o.form == lib.BEM_FORM_MOD and o.prec == lib.BEM_PREC_FP64
+    assert o.tol == 1e-10 and o.max_iter == 500
+
+
+def test_host_validation(lib):
+    P = lib.Problem
+    with pytest.raises(lib.BemError):
+        P(quad_order=0)
+    with pytest.raises(lib.BemError):
+        P(max_iter=5000)
+    p = P()
+    with pytest.raises(lib.BemError) as e:
+        p.bem_set_domains([1.0, 2.0], [2.0, 1.0])          # host eps must be 1
+    assert e.value.status == lib.BEM_EINVAL
+    with pytest.raises(lib.BemError):
+        p.bem_set_domains([1.0, -2.0], [1.0, 1.0])         # k <= 0
+    with pytest.raises(lib.BemError):
+        p.bem_set_domains([1.0, 2.0], [1.0, -1.0])         # eps = -1: cluster at the origin (Sec. 5)
+    with pytest.raises(lib.BemError):
+        p.bem_set_domains([1.0, np.nan], [1.0, 1.0])
+    p.bem_set_domains([5.0, 7.5], [1.0, 2.25])
+    with pytest.raises(lib.BemError):
+        p.bem_add_segment(np.array([[0, 0], [1, 0.0]]), 0, 1, True)      # closed needs 3 vertices
+    with pytest.raises(lib.BemError):
+        p.bem_add_segment(np.array([[0, 0], [1, 0.0], [1, 0.0]]), 0, 1, False)   # zero-length element
+    with pytest.raises(lib.BemError):
+        p.bem_add_segment(np.array([[0, 0], [1, 0.0], [0, 1.0]]), 1, 1, True)    # P == M
+    with pytest.raises(lib.BemError):
+        p.bem_add_segment(np.array([[0, 0], [1, np.inf], [0, 1.0]]), 0, 1, True)
+    p.bem_add_segment(np.array([[0, 0], [1, 0.0], [0, 1.0]]), 0, 1, True)
+    assert p.bem_num_elements() == 3 and p.bem_num_unknowns() == 6
+    assert p.bem_footprint_bytes(1) > 6 * 6 * 16
+    p.close()
+
+
+def test_workload_generators_shapes():
+    import workloads as W
+    assert W.cfg_circle_c1().n_elem == 256
+    assert W.cfg_star_c2().n_elem == 4096
+    p3 = W.cfg_junction_c3()
+    assert p3.n_elem == 8192 and len(p3.segments) == 3
+    c4 = W.cfg_random_stars_c4()
+    assert len(c4) == 256 and all(128 <= q.n_elem <= 2048 for q in c4)
+    c5 = W.cfg_serving_c5(count=50)
+    assert all(t2 > t1 for (t1, _), (t2, _) in zip(c5, c5[1:]))

@@ -1,0 +1,206 @@
+"""GPU parity: the CUDA path through the C-ABI against the CPU oracle on the same seeded inputs."""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from tests.util import ENTRY_BLOCK_TOL, ENTRY_REL_TOL, SOLUTION_TOL_FP64, SOLUTION_TOL_MIXED, block_errors, rel
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_2312_12787_gb300 import build as bld
+    bld.build()
+    import paper_2312_12787_gb300 as P
+    P.load()
+    return P
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as T
+    assert T.cuda.is_available()
+    return T
+
+
+def gpu_matrix(B, torch, wp, **kw):
+    p = B.Problem.from_workload(wp, **kw)
+    n2 = p.bem_num_unknowns()
+    A = torch.empty((n2, n2), dtype=torch.complex128, device="cuda")
+    p.bem_get_matrix(A, which=0)
+    out = {"main": A.cpu().numpy()}
+    if kw.get("prec", "fp64") != "fp64":
+        p.bem_get_matrix(A, which=1)
+        out["full"] = A.cpu().numpy()
+    p.close()
+    return out
+
+
+CASES = [
+    ("triangle", lambda: W.Problem(k=[2.0, 3.0], eps=[1.0, 2.25],
+                                   segments=[W.Segment(W.circle(3), P=0, M=1, closed=True)])),
+    ("circle17", lambda: W.circle_problem(17, 5.0, 7.5)),
+    ("circle_c1", lambda: W.cfg_circle_c1()),
+    ("star300", lambda: W.Problem(k=[20.0, 30.0], eps=[1.0, 2.25],
+                                  segments=[W.Segment(W.star(300, 0.3, 5), P=0, M=1, closed=True)])),
+    ("concentric", lambda: W.concentric(41, 83, 2.0)),
+    ("junction", lambda: W.junction_disk(150, k=(5.0, 7.5, 10.0))),
+    ("equal_density", lambda: W.circle_problem(65, 5.0, 7.5, eps_i=1.0)),
+]
+
+
+@pytest.mark.parametrize("name,mk", CASES, ids=[c[0] for c in CASES])
+@pytest.mark.parametrize("Q", [4, 10])
+def test_assembly_fp64_matches_oracle(B, torch, name, mk, Q):
+    wp = mk()
+    ref = O.assemble(wp, Q=Q)
+    got = gpu_matrix(B, torch, wp, quad_order=Q)["main"]
+    blk, rl = block_errors(got, ref)
+    assert blk <= ENTRY_BLOCK_TOL, (blk, rl)
+    assert rl <= ENTRY_REL_TOL, (blk, rl)
+
+
+@pytest.mark.parametrize("form", ["orig", "beta1", "conv"])
+def test_assembly_forms_match_oracle(B, torch, form):
+    for wp in (W.concentric(30, 61, 1.0), W.junction_disk(96, k=(3.0, 4.5, 6.0))):
+        ref = O.assemble(wp, Q=4, form=form)
+        got = gpu_matrix(B, torch, wp, form=form)["main"]
+        blk, rl = block_errors(got, ref)
+        assert blk <= ENTRY_BLOCK_TOL and rl <= ENTRY_REL_TOL, (form, blk, rl)
+
+
+def test_assembly_mixed_split_matches_oracle(B, torch):
+    wp = W.Problem(k=[20.0, 30.0], eps=[1.0, 2.25], segments=[W.Segment(W.star(300, 0.3, 5), P=0, M=1, closed=True)])
+    ref = O.assemble(wp, Q=4)
+    m = gpu_matrix(B, torch, wp, prec="mixed")
+    blk, rl = block_errors(m["full"], ref)
+    assert blk <= ENTRY_BLOCK_TOL and rl <= ENTRY_REL_TOL, (blk, rl)
+    # hi alone is the FP32 rounding of each FP64 entry
+    err = np.abs(m["main"] - ref)
+    assert np.all(err <= 2.0 ** -24 * (np.abs(ref.real) + np.abs(ref.imag)) + 1e-12 * np.max(np.abs(ref)))
+
+
+def test_rhs_matches_oracle(B, torch):
+    for wp in (W.cfg_circle_c1(), W.junction_disk(96, k=(3.0, 4.5, 6.0)), W.concentric(30, 61, 1.0)):
+        for form in ("mod", "orig", "conv"):
+            p = B.Problem.from_workload(wp, form=form)
+            ang = np.array([0.0, 0.7, 2.0])
+            b = torch.empty((3, p.bem_num_unknowns()), dtype=torch.complex128, device="cuda")
+            p.bem_rhs_planewave(ang, b)
+            got = b.cpu().numpy()
+            for r, t in enumerate(ang):
+                ref = O.rhs_planewave(wp, t, form=form)
+                assert np.max(np.abs(got[r] - ref)) <= 1e-14 * np.max(np.abs(ref)), (form, r)
+            p.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("nrhs", [1, 3, 70])
+def test_matvec_matches_reference(B, torch, prec, nrhs):
+    wp = W.circle_problem(700, 5.0, 7.5)
+    p = B.Problem.from_workload(wp, prec=prec)
+    n2 = p.bem_num_unknowns()
+    A = torch.empty((n2, n2), dtype=torch.complex128, device="cuda")
+    p.bem_get_matrix(A, which=0)
+    g = torch.Generator(device="cpu").manual_seed(7)
+    x = torch.randn((nrhs, n2), dtype=torch.complex128, generator=g).cuda()
+    y = torch.empty_like(x)
+    p.bem_matvec(x, y, n_rhs=nrhs)
+    ref = (A @ x.T).T.cpu().numpy()      # reference product of the same stored matrix
+    tol = 1e-13 if prec == "fp64" else 2e-6
+    for r in range(nrhs):
+        assert rel(y[r].cpu().numpy(), ref[r]) <= tol
+    p.close()
+
+
+def test_solve_fp64_matches_oracle_lu(B, torch):
+    wp = W.cfg_circle_c1()
+    A = O.assemble(wp, Q=4)
+    ang = np.array([0.0, 1.1])
+    p = B.Problem.from_workload(wp, tol=1e-13)
+    x = torch.empty((2, p.bem_num_unknowns()), dtype=torch.complex128, device="cuda")
+    st, it, rs = p.bem_solve_planewave(ang, x)
+    assert st == B.BEM_OK and np.all(rs <= 1e-13)
+    for r, t in enumerate(ang):
+        xl = O.solve_lu(A, O.rhs_planewave(wp, t))
+        assert rel(x[r].cpu().numpy(), xl) <= SOLUTION_TOL_FP64
+    # iteration count of the paper's stopping rule against the oracle's GMRES (MGS vs CGS2: +-2)
+    p2 = B.Problem.from_workload(wp, tol=1e-10)
+    st, it2, rs2 = p2.bem_solve_planewave(ang[:1], x[:1].contiguous())
+    _, it_ref, _ = O.gmres(A, O.rhs_planewave(wp, 0.0), tol=1e-10)
+    assert abs(int(it2[0]) - it_ref) <= 2
+    p.close()
+    p2.close()
+
+
+@pytest.mark.parametrize("name,mk", [("star700", lambda: W.Problem(
+    k=[20.0, 30.0], eps=[1.0, 2.25], segments=[W.Segment(W.star(700, 0.3, 5), P=0, M=1, closed=True)])),
+    ("junction", lambda: W.junction_disk(400, k=(5.0, 7.5, 10.0)))])
+def test_solve_mixed_matches_oracle_lu(B, torch, name, mk):
+    wp = mk()
+    A = O.assemble(wp, Q=4)
+    ang = np.array([0.0, 0.9, 2.5])
+    for prec in ("mixed",):
+        p = B.Problem.from_workload(wp, prec=prec, tol=1e-10)
+        x = torch.empty((3, p.bem_num_unknowns()), dtype=torch.complex128, device="cuda")
+        st, it, rs = p.bem_solve_planewave(ang, x)
+        assert st == B.BEM_OK and np.all(rs <= 1e-10), (st, rs)
+        for r, t in enumerate(ang):
+            xl = O.solve_lu(A, O.rhs_planewave(wp, t))
+            assert rel(x[r].cpu().numpy(), xl) <= SOLUTION_TOL_MIXED
+        p.close()
+
+
+def test_far_field_matches_oracle_and_mie(B, torch):
+    wp = W.cfg_circle_c1()
+    p = B.Problem.from_workload(wp, tol=1e-12)
+    ang = np.array([0.0])
+    x = torch.empty((1, p.bem_num_unknowns()), dtype=torch.complex128, device="cuda")
+    p.bem_solve_planewave(ang, x)
+    fa = np.linspace(0, 2 * np.pi, 37)
+    ff = torch.empty((1, len(fa)), dtype=torch.complex128, device="cuda")
+    p.bem_far_field(x, fa, ff)
+    got = ff.cpu().numpy()[0]
+    ref = O.far_field(wp, x.cpu().numpy()[0], fa, Q=4)
+    assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
+    mie = O.mie_far_field(5.0, 7.5, 2.25, fa)
+    assert rel(got, mie) < 3e-3      # discretisation error at N = 256, Q = 4
+    p.close()
+
+
+def test_host_entry_point_round_trip(B, torch):
+    wp = W.cfg_circle_c1()
+    p = B.Problem.from_workload(wp, tol=1e-12)
+    st, xh, ffh, it, rs = p.bem_solve_planewave_host([0.0, 1.0], ff_angles=np.linspace(0, 1, 5))
+    xl = O.solve_lu(O.assemble(wp, Q=4), O.rhs_planewave(wp, 1.0))
+    assert st == B.BEM_OK and rel(xh[1], xl) < 1e-10
+    assert ffh.shape == (2, 5)
+    p.close()
+
+
+def test_full_size_star_sampled_rows(B, torch):
+    """Star r = 1 + 0.3 cos 5t, 4096 elements, k = 20/30: sampled rows of the GPU matrix against the oracle's
+    rows computed one by one."""
+    wp = W.cfg_star_c2()
+    p = B.Problem.from_workload(wp, prec="mixed")
+    n2 = p.bem_num_unknowns()
+    A = torch.empty((n2, n2), dtype=torch.complex128, device="cuda")
+    p.bem_get_matrix(A, which=1)
+    rng = np.random.default_rng(11)
+    rows = np.sort(np.concatenate([[0, n2 // 2 - 1, n2 // 2, n2 - 1], rng.choice(n2, 12, replace=False)]))
+    got = A[torch.as_tensor(rows, device="cuda")].cpu().numpy()
+    ref = O.assemble_rows(wp, rows, Q=4)
+    for a, r in zip(got, ref):
+        assert np.max(np.abs(a - r)) <= ENTRY_BLOCK_TOL * 10 * np.max(np.abs(r))
+    p.close()
+
+
+def test_invalid_mesh_rejected_on_device_path(B, torch):
+    wp = W.circle_problem(8, 40.0, 80.0)     # elements several wavelengths long
+    p = B.Problem.from_workload(wp)
+    with pytest.raises(B.BemError) as e:
+        p.bem_assemble()
+    assert e.value.status == B.BEM_EINVAL
+    p.close()
