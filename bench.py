@@ -1,0 +1,345 @@
+"""Benchmark of the Burton-Miller collocation BEM hot path on one GB300 (or N independent replicas).
+
+Workload (default): star-shaped scatterer r(t) = 1 + 0.3 cos 5t, k_e = 20, k_i = 30 (eps_i = 2.25),
+4096 constant elements (8192 complex unknowns), 4-point Gauss-Legendre, 64 incident plane waves
+uniform on [0, 2 pi) solved as one multi-right-hand-side block, far field at 32 angles.
+
+One step = the whole hot path on one batch: element geometry, assembly of A, plane-wave right-hand
+sides, GMRES solves of all 64 columns to relative residual `--tol`, far fields.  The headline `value`
+is the mixed-precision path (complex FP32 storage and Krylov basis, FP64 refinement); the plain FP64
+GPU path runs the same step for comparison (`fp64` key) and gives the accuracy reference.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--fp64-steps S]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "BEM solves/s (mixed vs FP64 GPU at err<=1e-6)"
+UNIT = "solves/s"
+N_RHS = 64
+N_FF = 32
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            pk = json.load(fh)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region (SM clock, max clock, throttle reasons)."""
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if args.impl == "ours" else "gloo")
+    return ws, rank, local
+
+
+def barrier_max(ws, value):
+    if ws == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ------------------------------------------------------------------------------------------------
+# CPU oracle legs
+# ------------------------------------------------------------------------------------------------
+
+def oracle_sample(wp, rows=256, lu_ne=2048):
+    """Oracle timed on a bounded sample of the workload, scaled to one full step (64 solves):
+    assembly of `rows` of the 2N rows (scaled by 2N/rows) plus a direct solve with 64 right-hand sides of
+    the same star at N_e = lu_ne (scaled by (N_e/lu_ne)^3)."""
+    import oracle as O
+    n2 = 2 * wp.n_elem
+    sel = np.linspace(0, n2 - 1, rows).astype(int)
+    el = O.elements(wp)
+    t0 = time.perf_counter()
+    O.assemble_rows(wp, sel, Q=4, el=el)
+    t_asm = (time.perf_counter() - t0) * n2 / rows
+    small = W.Problem(k=wp.k, eps=wp.eps, segments=[W.Segment(W.star(lu_ne, 0.3, 5), P=0, M=1, closed=True)])
+    A = O.assemble(small, Q=4)
+    B = np.stack([O.rhs_planewave(small, t) for t in W.plane_wave_angles(N_RHS)], 1)
+    t0 = time.perf_counter()
+    O.solve_lu(A, B)
+    t_lu = (time.perf_counter() - t0) * (wp.n_elem / lu_ne) ** 3
+    t_step = t_asm + t_lu
+    sample = (f"oracle assemble_rows on {rows} of {n2} rows (x{n2 / rows:.0f}) + LU solve of the same star at "
+              f"N_e={lu_ne} with {N_RHS} RHS (x{(wp.n_elem / lu_ne) ** 3:.0f}); assembly single-threaded numpy, "
+              f"LU multi-threaded LAPACK")
+    return N_RHS / t_step, t_step, sample
+
+
+def run_reference(args):
+    ws, rank, _ = dist_setup(args)
+    if rank != 0:
+        return
+    wp = W.cfg_star_c2()
+    cores = os.cpu_count()
+    if args.warmup > 0:
+        oracle_sample(wp, rows=8, lu_ne=256)
+    vals = []
+    sample = ""
+    for _ in range(max(1, args.steps)):
+        v, t, sample = oracle_sample(wp, rows=128, lu_ne=2048)
+        vals.append(v)
+    value = statistics.median(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * N_RHS / value,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": wp.name, "n_elem": wp.n_elem, "n_rhs": N_RHS},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------------------------
+# GPU legs
+# ------------------------------------------------------------------------------------------------
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="mixed_tc", choices=["mixed", "mixed_tc"])
+    ap.add_argument("--tol", type=float, default=1e-10)
+    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline leg")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison leg (profiling runs)")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg (profiling runs)")
+    ap.add_argument("--n-elem", type=int, default=4096, help="elements of the star (smaller cases for ncu)")
+    ap.add_argument("--max-iter", type=int, default=400)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    ws, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    import paper_2312_12787_gb300 as P
+    from paper_2312_12787_gb300 import build as B
+    B.build()
+    P.load()
+
+    wp = W.cfg_star_c2(args.n_elem)
+    ang = W.plane_wave_angles(N_RHS)
+    ffa = np.linspace(0.0, 2 * np.pi, N_FF, endpoint=False)
+    stream = torch.cuda.current_stream()
+
+    def make(prec):
+        p = P.Problem.from_workload(wp, prec=prec, tol=args.tol, max_iter=args.max_iter)
+        n2 = p.bem_num_unknowns()
+        x = torch.empty((N_RHS, n2), dtype=torch.complex128, device="cuda")
+        ff = torch.empty((N_RHS, N_FF), dtype=torch.complex128, device="cuda")
+        return p, x, ff
+
+    def step(p, x, ff):
+        p.bem_assemble(stream)
+        st, it, rs = p.bem_solve_planewave(ang, x, stream)
+        p.bem_far_field(x, ffa, ff, n_rhs=N_RHS, stream=stream)
+        return st, it, rs
+
+    # ---- mixed path (headline) ----
+    p, x, ff = make(args.prec)
+    for _ in range(args.warmup):
+        step(p, x, ff)
+    torch.cuda.synchronize()
+    p.bem_profile_enable(True)
+    barrier(ws)
+    torch.cuda.synchronize()
+    times = []
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    iters = []
+    with ClockSampler(local) as clk:
+        t_all0 = time.perf_counter()
+        for k in range(args.steps):
+            evs[k][0].record(stream)
+            st, it, rs = step(p, x, ff)
+            evs[k][1].record(stream)
+            iters.append(it.copy())
+        torch.cuda.synchronize()
+        t_all = time.perf_counter() - t_all0
+    barrier(ws)
+    times = [a.elapsed_time(b) for a, b in evs]
+    total_ms = barrier_max(ws, sum(times))
+    prof = p.bem_profile_read()
+    p.bem_profile_enable(False)
+    x_mixed = x.clone()
+    ms_step = total_ms / args.steps
+    value = ws * N_RHS * args.steps / (total_ms / 1e3)
+    lat = sorted(times)
+    p50 = lat[len(lat) // 2]
+    p99 = lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)]
+
+    # ---- FP64 path: same step, accuracy reference ----
+    fp64 = None
+    acc = {"fp64_tol": args.tol, "iters_mixed_max": int(np.max(iters[-1]))}
+    if not args.no_fp64:
+        p64, x64, ff64 = make("fp64")
+        step(p64, x64, ff64)
+        torch.cuda.synchronize()
+        t64 = []
+        for _ in range(max(1, args.fp64_steps)):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            st64, it64, rs64 = step(p64, x64, ff64)
+            b.record(stream)
+            torch.cuda.synchronize()
+            t64.append(a.elapsed_time(b))
+        fp64_ms = statistics.median(t64)
+        err = (torch.linalg.vector_norm(x_mixed - x64, dim=1) / torch.linalg.vector_norm(x64, dim=1)).max().item()
+        acc["max_rel_err_mixed_vs_fp64"] = err
+        fp64 = {"value": N_RHS / (fp64_ms / 1e3), "unit": UNIT, "ms_per_step": fp64_ms,
+                "speedup_mixed_over_fp64": fp64_ms / ms_step, "iters_max": int(np.max(it64))}
+        p64.close()
+
+    # ---- end to end through the host-buffer entry point ----
+    nel = wp.n_elem
+    e2e = None
+    if not args.no_e2e:
+        e2e_ms = []
+        h2d = nel * (4 * 8 + 2 * 4) + N_RHS * 8 + N_FF * 8
+        d2h = N_RHS * 2 * nel * 16 + N_RHS * N_FF * 16
+        for k in range(2):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            q = P.Problem.from_workload(wp, prec=args.prec, tol=args.tol, max_iter=args.max_iter)
+            q.bem_solve_planewave_host(ang, ff_angles=ffa, want_traces=True, stream=stream)
+            q.close()
+            torch.cuda.synchronize()
+            if k:
+                e2e_ms.append(1e3 * (time.perf_counter() - t0))
+        e2e = {"value": N_RHS / (statistics.median(e2e_ms) / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h}
+
+    # ---- roofline of the dominant phase ----
+    hbm, src = _peaks()
+    ph, (ph_ms, ph_n) = max(prof.items(), key=lambda kv: kv[1][0])
+    n2 = 2 * nel
+    roof = None
+    if ph == "matvec":
+        bytes_per = n2 * n2 * 8 + 2 * N_RHS * n2 * 8          # A (complex FP32) + X + Y
+        ach = bytes_per / (ph_ms / ph_n / 1e3) / 1e9
+        roof = {"kernel": "matvec (multi-RHS complex FP32 GEMM)", "bound": "hbm", "achieved": ach, "peak": hbm,
+                "unit": "GB/s", "frac": ach / hbm, "traffic": None, "peak_source": src,
+                "launches": ph_n, "avg_launch_ms": ph_ms / ph_n}
+    else:
+        roof = {"kernel": ph, "bound": "see DESIGN.md", "achieved": None, "peak": None, "unit": None,
+                "frac": None, "traffic": None, "launches": ph_n, "avg_launch_ms": ph_ms / ph_n}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "c32 storage + f64 refinement", "data": "synthetic",
+        "config": {"workload": wp.name, "n_elem": nel, "n_unknowns": n2, "n_rhs": N_RHS, "quad": 4,
+                   "prec": args.prec, "tol": args.tol, "far_field_angles": N_FF,
+                   "l2": "inputs larger than L2 (A is 0.54 GB complex FP32 + 0.54 GB remainder)"},
+        "latency_ms": {"p50": p50, "p99": p99, "unit": "ms per 64-solve batch"},
+        "fp64": fp64,
+        "accuracy": acc,
+        "phases_ms": {k: round(v[0], 3) for k, v in prof.items() if v[1]},
+        "roofline": roof,
+        "e2e": e2e,
+        "gpu_launches": int(sum(v[1] for v in prof.values())),
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and not args.no_cpu:
+        v, t, sample = oracle_sample(wp, rows=256, lu_ne=2048)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                                "sample": sample}
+    p.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

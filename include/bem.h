@@ -119,7 +119,8 @@ BEM_API int bem_num_unknowns(const bem_problem* p);   /* 2N */
 BEM_API size_t bem_footprint_bytes(const bem_problem* p, int n_rhs);
 
 /* Steps a1 + a3..a5: element geometry on the device, then every entry of A (Gauss-Legendre off the
- * diagonal, exact self terms on it) placed by the selected form.  Allocates A on first use. */
+ * diagonal, exact self terms on it) placed by the selected form.  Always recomputes A (the solve entry
+ * points assemble only when the matrix is missing or out of date).  Allocates A on first use. */
 BEM_API bem_status bem_assemble(bem_problem* p, void* stream);
 
 /* Copy the assembled matrix into A_dev (2N x 2N complex FP64, row-major, leading dimension 2N).

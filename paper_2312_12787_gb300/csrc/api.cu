@@ -217,13 +217,13 @@ size_t matrix_bytes(int n, bool mixed) {
   return mixed ? 2 * nn * sizeof(float2) : nn * sizeof(double2);
 }
 
-bem_status assemble_impl(bem_problem* p, cudaStream_t s) {
+bem_status assemble_impl(bem_problem* p, cudaStream_t s, bool force = false) {
   bem_status st = check_ready(p);
   if (st != BEM_OK) return st;
   st = upload_geometry(p, s);
   if (st != BEM_OK) return st;
   const bool mixed = p->mixed();
-  if (!p->mat_dirty && p->A_mixed == (int)mixed) return BEM_OK;
+  if (!force && !p->mat_dirty && p->A_mixed == (int)mixed) return BEM_OK;
   const size_t nn = (size_t)2 * p->n * 2 * p->n;
   const size_t need = mixed ? nn * sizeof(float2) : nn * sizeof(double2);
   if (need > p->A_cap || p->A_mixed != (int)mixed) {
@@ -371,11 +371,11 @@ bem_status gmres_run(bem_problem* p, Solver& sv, const double2* r0, double2* x, 
     }
     {
       Phase ph(p, BEM_PH_ARNOLDI, s, 6);
-      CU(krylov_orthogonalise(st, 2, s));
+      CU(krylov_orthogonalise(st, 2, j, s));
     }
     {
       Phase ph(p, BEM_PH_GIVENS, s, 3);
-      CU(krylov_finish_step(st, tol, s));
+      CU(krylov_finish_step(st, tol, j, s));
     }
     CU(cudaMemcpyAsync(p->h_pin, st.n_active, sizeof(int), cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
@@ -604,7 +604,7 @@ BEM_API size_t bem_footprint_bytes(const bem_problem* p, int n_rhs) {
 }
 
 BEM_API bem_status bem_assemble(bem_problem* p, void* stream) {
-  return assemble_impl(p, static_cast<cudaStream_t>(stream));
+  return assemble_impl(p, static_cast<cudaStream_t>(stream), true);
 }
 
 BEM_API bem_status bem_get_matrix(bem_problem* p, int which, bem_c64* A_dev, void* stream) {

@@ -95,8 +95,8 @@ struct KrylovState {
   double2* y;       // nrhs x m (least-squares solution)
   double* beta;     // nrhs
   double* hnext;    // nrhs: ||w|| after orthogonalisation
-  double2* part;    // scratch: nrhs x nchunk x (m+1) partial dot products
-  double* npart;    // scratch: nrhs x nchunk partial squared norms
+  double2* part;    // scratch: nrhs x krylov_nchunk(n) x (m+1) partial dot products
+  double* npart;    // scratch: nrhs x krylov_nchunk(n) partial squared norms
   double2* hcol;    // nrhs x (m+1): projections of the current pass
   int* active;      // nrhs: 1 while iterating
   int* iters;       // nrhs
@@ -106,8 +106,8 @@ struct KrylovState {
 };
 int krylov_nchunk(int n);
 cudaError_t krylov_start(const KrylovState& st, const double2* r0, double tol_unused, cudaStream_t s);
-cudaError_t krylov_orthogonalise(const KrylovState& st, int passes, cudaStream_t s);
-cudaError_t krylov_finish_step(const KrylovState& st, double tol, cudaStream_t s);
+cudaError_t krylov_orthogonalise(const KrylovState& st, int passes, int j, cudaStream_t s);
+cudaError_t krylov_finish_step(const KrylovState& st, double tol, int j, cudaStream_t s);
 cudaError_t krylov_update_solution(const KrylovState& st, double2* x, cudaStream_t s);
 
 }  // namespace bem

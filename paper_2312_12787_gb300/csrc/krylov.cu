@@ -4,12 +4,15 @@
 // Arnoldi uses classical Gram-Schmidt with one re-orthogonalisation pass (CGS2) so that each pass is
 // two streaming sweeps over the basis instead of j dependent sweeps; the Hessenberg column, Givens
 // rotations and residual estimate are kept in FP64.  The basis may be complex FP64 (FP64 path) or
-// complex FP32 (mixed inner solves); in both cases partial sums of each thread are reduced across the
-// block and the grid in FP64 with warp shuffles.
+// complex FP32 (mixed inner solves); products and warp reductions run in the basis precision, the
+// per-chunk partial sums are combined in FP64.
 //
-// Work split: a vector of n unknowns is cut into chunks of kChunk entries; one CTA of 256 threads owns
-// one chunk of one system (grid = chunks x systems).  Every kernel reads the iteration index j from
-// device memory so that one iteration can be replayed from a CUDA graph.
+// Work split: a vector of n unknowns is cut into chunks of 64 entries; one CTA of 256 threads owns one
+// chunk of one system (grid = chunks x systems), so even a single system of 8192 unknowns spreads over
+// 128 CTAs.  In the projection kernel each warp owns every eighth basis vector (no block barriers); in
+// the update kernel four thread groups share the basis vectors of a chunk and meet in shared memory.
+#include <algorithm>
+
 #include "internal.cuh"
 
 namespace bem {
@@ -17,15 +20,16 @@ namespace bem {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kPer = 4;                       // entries per thread
-constexpr int kChunk = kThreads * kPer;       // entries per CTA
+constexpr int kCh = 64;                        // entries per chunk (one CTA of the projection kernels)
 
 template <typename T> struct Vec;
 template <> struct Vec<double2> {
+  using acc_t = double;
   __device__ static __forceinline__ double2 load(const double2* p) { return *p; }
   __device__ static __forceinline__ void store(double2* p, double2 v) { *p = v; }
 };
 template <> struct Vec<float2> {
+  using acc_t = float;
   __device__ static __forceinline__ double2 load(const float2* p) {
     const float2 v = *p;
     return make_double2(v.x, v.y);
@@ -33,7 +37,8 @@ template <> struct Vec<float2> {
   __device__ static __forceinline__ void store(float2* p, double2 v) { *p = make_float2((float)v.x, (float)v.y); }
 };
 
-__device__ __forceinline__ double warp_sum_d(double v) {
+template <typename F>
+__device__ __forceinline__ F warp_sum(F v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
@@ -41,7 +46,7 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 
 // Sum one double over the block; result valid in thread 0.  `red` holds 8 doubles.
 __device__ __forceinline__ double block_sum(double v, double* red) {
-  v = warp_sum_d(v);
+  v = warp_sum(v);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   __syncthreads();
   if (lane == 0) red[warp] = v;
@@ -49,35 +54,32 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   double t = 0.0;
   if (threadIdx.x < 32) {
     t = (lane < kThreads / 32) ? red[lane] : 0.0;
-    t = warp_sum_d(t);
+    t = warp_sum(t);
   }
   return t;
 }
 
+// squared norms of 256-entry blocks (grid: blocks x columns)
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_norm_part(const T* v, int n, double* npart, int nchunk) {
+__global__ void __launch_bounds__(kThreads) k_norm_part(const T* v, int n, double* npart, int nblk) {
   __shared__ double red[8];
   const int c = blockIdx.x, s = blockIdx.y;
-  const T* vs = v + (size_t)s * n;
+  const int k = c * kThreads + threadIdx.x;
   double acc = 0.0;
-#pragma unroll
-  for (int t = 0; t < kPer; ++t) {
-    const int k = c * kChunk + t * kThreads + threadIdx.x;
-    if (k < n) {
-      const double2 a = Vec<T>::load(vs + k);
-      acc += a.x * a.x + a.y * a.y;
-    }
+  if (k < n) {
+    const double2 a = Vec<T>::load(v + (size_t)s * n + k);
+    acc = a.x * a.x + a.y * a.y;
   }
   acc = block_sum(acc, red);
-  if (threadIdx.x == 0) npart[(size_t)s * nchunk + c] = acc;
+  if (threadIdx.x == 0) npart[(size_t)s * nblk + c] = acc;
 }
 
-// Start: beta = ||r0||, g = (beta, 0, ...), V_0 = r0 / beta, active = (beta > 0).
-__global__ void k_start_finish(KrylovState st, int nchunk) {
+// Start: beta = ||r0||, g = (beta, 0, ...), active = (beta > 0).
+__global__ void k_start_finish(KrylovState st, int nblk) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= st.nrhs) return;
   double t = 0.0;
-  for (int c = 0; c < nchunk; ++c) t += st.npart[(size_t)s * nchunk + c];
+  for (int c = 0; c < nblk; ++c) t += st.npart[(size_t)s * nblk + c];
   const double beta = sqrt(t);
   st.beta[s] = beta;
   st.g[(size_t)s * (st.m + 1)] = make_double2(beta, 0.0);
@@ -90,80 +92,44 @@ __global__ void k_start_finish(KrylovState st, int nchunk) {
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_start_scale(KrylovState st, const double2* r0) {
-  const int c = blockIdx.x, s = blockIdx.y;
-  if (!st.active[s]) return;
-  const double inv = 1.0 / st.beta[s];
+  const int k = blockIdx.x * kThreads + threadIdx.x, s = blockIdx.y;
+  if (!st.active[s] || k >= st.n) return;
   T* v0 = static_cast<T*>(st.V) + (size_t)s * st.n;
-#pragma unroll
-  for (int t = 0; t < kPer; ++t) {
-    const int k = c * kChunk + t * kThreads + threadIdx.x;
-    if (k < st.n) Vec<T>::store(v0 + k, cscale(r0[(size_t)s * st.n + k], inv));
-  }
+  Vec<T>::store(v0 + k, cscale(r0[(size_t)s * st.n + k], 1.0 / st.beta[s]));
 }
 
-// Partial projections <v_i, w> over one chunk, four basis vectors per block reduction.
+// Partial projections <v_i, w> over one 64-entry chunk: warp w takes basis vectors i = w, w+8, ...;
+// each lane two entries; products and the warp reduction in the basis precision, chunk partials stored
+// for an FP64 sum over chunks.
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_dots(KrylovState st, int nchunk) {
-  __shared__ double red[8 * 8];
+__global__ void __launch_bounds__(kThreads) k_dots(KrylovState st, int nchunk, int j) {
+  using F = typename Vec<T>::acc_t;
   const int c = blockIdx.x, s = blockIdx.y;
   if (!st.active[s]) return;
-  const int j = *st.jdev;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const size_t stride = (size_t)st.nrhs * st.n;
   const T* W = static_cast<const T*>(st.W) + (size_t)s * st.n;
   const T* V = static_cast<const T*>(st.V) + (size_t)s * st.n;
-  double2 w[kPer];
-  int kk[kPer];
-#pragma unroll
-  for (int t = 0; t < kPer; ++t) {
-    kk[t] = c * kChunk + t * kThreads + threadIdx.x;
-    w[t] = kk[t] < st.n ? Vec<T>::load(W + kk[t]) : make_double2(0, 0);
-  }
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int i0 = 0; i0 <= j; i0 += 4) {
-    double p[8];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      double px = 0.0, py = 0.0;
-      const int i = i0 + q;
-      if (i <= j) {
-        const T* vi = V + (size_t)i * stride;
-#pragma unroll
-        for (int t = 0; t < kPer; ++t) {
-          if (kk[t] < st.n) {
-            const double2 v = Vec<T>::load(vi + kk[t]);
-            px += v.x * w[t].x + v.y * w[t].y;     // conj(v) w
-            py += v.x * w[t].y - v.y * w[t].x;
-          }
-        }
-      }
-      p[2 * q] = warp_sum_d(px);
-      p[2 * q + 1] = warp_sum_d(py);
-    }
-    __syncthreads();
-    if (lane == 0) {
-#pragma unroll
-      for (int q = 0; q < 8; ++q) red[q * 8 + warp] = p[q];
-    }
-    __syncthreads();
-    if (threadIdx.x < 8) {
-      double t = 0.0;
-#pragma unroll
-      for (int w8 = 0; w8 < 8; ++w8) t += red[threadIdx.x * 8 + w8];
-      const int q = threadIdx.x >> 1;
-      const int i = i0 + q;
-      if (i <= j) {
-        double* dst = reinterpret_cast<double*>(st.part + ((size_t)s * nchunk + c) * (st.m + 1) + i);
-        dst[threadIdx.x & 1] = t;
-      }
-    }
+  const int k0 = c * kCh + lane, k1 = k0 + 32;
+  const bool in0 = k0 < st.n, in1 = k1 < st.n;
+  T zero;
+  zero.x = 0; zero.y = 0;
+  const T w0 = in0 ? W[k0] : zero, w1 = in1 ? W[k1] : zero;
+  for (int i = warp; i <= j; i += kThreads / 32) {
+    const T* vi = V + (size_t)i * stride;
+    const T v0 = in0 ? vi[k0] : zero, v1 = in1 ? vi[k1] : zero;
+    F px = (F)v0.x * (F)w0.x + (F)v0.y * (F)w0.y + (F)v1.x * (F)w1.x + (F)v1.y * (F)w1.y;   // conj(v) w
+    F py = (F)v0.x * (F)w0.y - (F)v0.y * (F)w0.x + (F)v1.x * (F)w1.y - (F)v1.y * (F)w1.x;
+    px = warp_sum(px);
+    py = warp_sum(py);
+    if (lane == 0) st.part[((size_t)s * nchunk + c) * (st.m + 1) + i] = make_double2((double)px, (double)py);
   }
 }
 
-// h_i = sum over chunks; accumulate into column j of H (pass 0 sets, later passes add).
-__global__ void k_dots_reduce(KrylovState st, int nchunk, int pass) {
+// h_i = sum over chunks (FP64); accumulate into column j of H (pass 0 sets, later passes add).
+__global__ void k_dots_reduce(KrylovState st, int nchunk, int pass, int j) {
   const int s = blockIdx.x;
   if (!st.active[s]) return;
-  const int j = *st.jdev;
   for (int i = threadIdx.x; i <= j; i += blockDim.x) {
     double2 h = make_double2(0, 0);
     for (int c = 0; c < nchunk; ++c) h = cadd(h, st.part[((size_t)s * nchunk + c) * (st.m + 1) + i]);
@@ -173,45 +139,54 @@ __global__ void k_dots_reduce(KrylovState st, int nchunk, int pass) {
   }
 }
 
-// w -= sum_i h_i v_i over one chunk; partial ||w||^2.
+// w -= sum_i h_i v_i over one 64-entry chunk; 256 threads = 64 entries x 4 interleaved subsets of i,
+// combined through shared memory.  Also writes the chunk's ||w||^2.
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_update(KrylovState st, int nchunk) {
+__global__ void __launch_bounds__(kThreads) k_update(KrylovState st, int nchunk, int j) {
+  using F = typename Vec<T>::acc_t;
   __shared__ double2 hs[1024];
+  __shared__ F accs[4][kCh][2];
   __shared__ double red[8];
   const int c = blockIdx.x, s = blockIdx.y;
   if (!st.active[s]) return;
-  const int j = *st.jdev;
   for (int i = threadIdx.x; i <= j; i += kThreads) hs[i] = st.hcol[(size_t)s * (st.m + 1) + i];
   __syncthreads();
+  const int e = threadIdx.x & (kCh - 1), sub = threadIdx.x >> 6;
+  const int k = c * kCh + e;
   const size_t stride = (size_t)st.nrhs * st.n;
-  T* W = static_cast<T*>(st.W) + (size_t)s * st.n;
   const T* V = static_cast<const T*>(st.V) + (size_t)s * st.n;
-  double acc = 0.0;
-#pragma unroll
-  for (int t = 0; t < kPer; ++t) {
-    const int k = c * kChunk + t * kThreads + threadIdx.x;
-    if (k >= st.n) continue;
-    double2 w = Vec<T>::load(W + k);
-    for (int i = 0; i <= j; ++i) {
-      const double2 v = Vec<T>::load(V + (size_t)i * stride + k);
-      const double2 h = hs[i];
-      w.x -= h.x * v.x - h.y * v.y;
-      w.y -= h.x * v.y + h.y * v.x;
+  F ax = 0, ay = 0;
+  if (k < st.n) {
+    for (int i = sub; i <= j; i += 4) {
+      const T v = V[(size_t)i * stride + k];
+      const F hx = (F)hs[i].x, hy = (F)hs[i].y;
+      ax += hx * (F)v.x - hy * (F)v.y;
+      ay += hx * (F)v.y + hy * (F)v.x;
     }
-    Vec<T>::store(W + k, w);
-    const double2 wr = Vec<T>::load(W + k);
-    acc += wr.x * wr.x + wr.y * wr.y;
   }
-  acc = block_sum(acc, red);
-  if (threadIdx.x == 0) st.npart[(size_t)s * nchunk + c] = acc;
+  accs[sub][e][0] = ax;
+  accs[sub][e][1] = ay;
+  __syncthreads();
+  double nrm = 0.0;
+  if (sub == 0 && k < st.n) {
+    T* W = static_cast<T*>(st.W) + (size_t)s * st.n;
+    T w = W[k];
+    const F tx = accs[0][e][0] + accs[1][e][0] + accs[2][e][0] + accs[3][e][0];
+    const F ty = accs[0][e][1] + accs[1][e][1] + accs[2][e][1] + accs[3][e][1];
+    w.x = w.x - tx;
+    w.y = w.y - ty;
+    W[k] = w;
+    nrm = (double)w.x * (double)w.x + (double)w.y * (double)w.y;
+  }
+  nrm = block_sum(nrm, red);
+  if (threadIdx.x == 0) st.npart[(size_t)s * nchunk + c] = nrm;
 }
 
 // h_{j+1,j} = ||w||; apply the previous Givens rotations to column j, form the new one, update g and
 // the residual estimate |g_{j+1}| / beta.  Rotation i acts on rows (i, i+1) as [[conj c, conj s], [-s, c]].
-__global__ void k_finish(KrylovState st, int nchunk, double tol) {
+__global__ void k_finish(KrylovState st, int nchunk, double tol, int j) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= st.nrhs || !st.active[s]) return;
-  const int j = *st.jdev;
   double t = 0.0;
   for (int c = 0; c < nchunk; ++c) t += st.npart[(size_t)s * nchunk + c];
   const double hn = sqrt(t);
@@ -222,9 +197,8 @@ __global__ void k_finish(KrylovState st, int nchunk, double tol) {
   for (int i = 0; i < j; ++i) {
     const double2 a = Hj[i], b = Hj[i + 1];
     const double2 ci = cs[i], si = sn[i];
-    // conj(c) a + conj(s) b ; -s a + c b
-    const double2 ta = cadd(cdotc(ci, a), cdotc(si, b));
-    const double2 tb = csub(cmul(ci, b), cmul(si, a));
+    const double2 ta = cadd(cdotc(ci, a), cdotc(si, b));   // conj(c) a + conj(s) b
+    const double2 tb = csub(cmul(ci, b), cmul(si, a));     // -s a + c b
     Hj[i] = ta;
     Hj[i + 1] = tb;
   }
@@ -249,22 +223,16 @@ __global__ void k_finish(KrylovState st, int nchunk, double tol) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_scale_next(KrylovState st) {
-  const int c = blockIdx.x, s = blockIdx.y;
-  if (!st.active[s]) return;
-  const int j = *st.jdev;
-  const double inv = 1.0 / st.hnext[s];
+__global__ void __launch_bounds__(kThreads) k_scale_next(KrylovState st, int j) {
+  const int k = blockIdx.x * kThreads + threadIdx.x, s = blockIdx.y;
+  if (!st.active[s] || k >= st.n) return;
   const T* W = static_cast<const T*>(st.W) + (size_t)s * st.n;
   T* Vn = static_cast<T*>(st.V) + ((size_t)(j + 1) * st.nrhs + s) * st.n;
-#pragma unroll
-  for (int t = 0; t < kPer; ++t) {
-    const int k = c * kChunk + t * kThreads + threadIdx.x;
-    if (k < st.n) Vec<T>::store(Vn + k, cscale(Vec<T>::load(W + k), inv));
-  }
+  Vec<T>::store(Vn + k, cscale(Vec<T>::load(W + k), 1.0 / st.hnext[s]));
 }
 
 __global__ void k_advance(KrylovState st) {
-  // next iteration index; count of systems still active
+  // count of systems still active; the iteration index mirror for graph replays
   if (threadIdx.x == 0) {
     *st.jdev += 1;
     int a = 0;
@@ -289,77 +257,84 @@ __global__ void k_lsq(KrylovState st) {
   }
 }
 
+// x += sum_i y_i v_i (FP64 x), same 64 x 4 decomposition as k_update.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_xupdate(KrylovState st, double2* x) {
   __shared__ double2 ys[1024];
+  __shared__ double2 accs[4][kCh];
   const int c = blockIdx.x, s = blockIdx.y;
   const int mm = st.iters[s];
   for (int i = threadIdx.x; i < mm; i += kThreads) ys[i] = st.y[(size_t)s * st.m + i];
   __syncthreads();
+  const int e = threadIdx.x & (kCh - 1), sub = threadIdx.x >> 6;
+  const int k = c * kCh + e;
   const size_t stride = (size_t)st.nrhs * st.n;
   const T* V = static_cast<const T*>(st.V) + (size_t)s * st.n;
-#pragma unroll
-  for (int t = 0; t < kPer; ++t) {
-    const int k = c * kChunk + t * kThreads + threadIdx.x;
-    if (k >= st.n) continue;
-    double2 acc = x[(size_t)s * st.n + k];
-    for (int i = 0; i < mm; ++i) acc = cadd(acc, cmul(ys[i], Vec<T>::load(V + (size_t)i * stride + k)));
-    x[(size_t)s * st.n + k] = acc;
+  double2 acc = make_double2(0, 0);
+  if (k < st.n)
+    for (int i = sub; i < mm; i += 4) acc = cadd(acc, cmul(ys[i], Vec<T>::load(V + (size_t)i * stride + k)));
+  accs[sub][e] = acc;
+  __syncthreads();
+  if (sub == 0 && k < st.n) {
+    double2 t = x[(size_t)s * st.n + k];
+    for (int q = 0; q < 4; ++q) t = cadd(t, accs[q][e]);
+    x[(size_t)s * st.n + k] = t;
   }
 }
 
+int nchunk_of(int n) { return (n + kCh - 1) / kCh; }
+int nblk_of(int n) { return (n + kThreads - 1) / kThreads; }
+
 template <typename T>
 cudaError_t start_t(const KrylovState& st, const double2* r0, cudaStream_t s) {
-  const int nc = krylov_nchunk(st.n);
-  dim3 grd(nc, st.nrhs);
-  k_norm_part<double2><<<grd, kThreads, 0, s>>>(r0, st.n, st.npart, nc);
-  k_start_finish<<<(st.nrhs + 63) / 64, 64, 0, s>>>(st, nc);
+  const int nb = nblk_of(st.n);
+  dim3 grd(nb, st.nrhs);
+  k_norm_part<double2><<<grd, kThreads, 0, s>>>(r0, st.n, st.npart, nb);
+  k_start_finish<<<(st.nrhs + 63) / 64, 64, 0, s>>>(st, nb);
   k_start_scale<T><<<grd, kThreads, 0, s>>>(st, r0);
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t orth_t(const KrylovState& st, int passes, cudaStream_t s) {
-  const int nc = krylov_nchunk(st.n);
+cudaError_t orth_t(const KrylovState& st, int passes, int j, cudaStream_t s) {
+  const int nc = nchunk_of(st.n);
   dim3 grd(nc, st.nrhs);
   for (int p = 0; p < passes; ++p) {
-    k_dots<T><<<grd, kThreads, 0, s>>>(st, nc);
-    k_dots_reduce<<<st.nrhs, 128, 0, s>>>(st, nc, p);
-    k_update<T><<<grd, kThreads, 0, s>>>(st, nc);
+    k_dots<T><<<grd, kThreads, 0, s>>>(st, nc, j);
+    k_dots_reduce<<<st.nrhs, 128, 0, s>>>(st, nc, p, j);
+    k_update<T><<<grd, kThreads, 0, s>>>(st, nc, j);
   }
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t finish_t(const KrylovState& st, double tol, cudaStream_t s) {
-  const int nc = krylov_nchunk(st.n);
-  dim3 grd(nc, st.nrhs);
-  k_finish<<<(st.nrhs + 63) / 64, 64, 0, s>>>(st, nc, tol);
-  k_scale_next<T><<<grd, kThreads, 0, s>>>(st);
+cudaError_t finish_t(const KrylovState& st, double tol, int j, cudaStream_t s) {
+  const int nc = nchunk_of(st.n);
+  k_finish<<<(st.nrhs + 63) / 64, 64, 0, s>>>(st, nc, tol, j);
+  k_scale_next<T><<<dim3(nblk_of(st.n), st.nrhs), kThreads, 0, s>>>(st, j);
   k_advance<<<1, 32, 0, s>>>(st);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t xupd_t(const KrylovState& st, double2* x, cudaStream_t s) {
-  const int nc = krylov_nchunk(st.n);
   k_lsq<<<(st.nrhs + 63) / 64, 64, 0, s>>>(st);
-  k_xupdate<T><<<dim3(nc, st.nrhs), kThreads, 0, s>>>(st, x);
+  k_xupdate<T><<<dim3(nchunk_of(st.n), st.nrhs), kThreads, 0, s>>>(st, x);
   return cudaGetLastError();
 }
 
 }  // namespace
 
-int krylov_nchunk(int n) { return (n + kChunk - 1) / kChunk; }
+int krylov_nchunk(int n) { return std::max(nchunk_of(n), nblk_of(n)); }
 
 cudaError_t krylov_start(const KrylovState& st, const double2* r0, double, cudaStream_t s) {
   return st.basis_fp32 ? start_t<float2>(st, r0, s) : start_t<double2>(st, r0, s);
 }
-cudaError_t krylov_orthogonalise(const KrylovState& st, int passes, cudaStream_t s) {
-  return st.basis_fp32 ? orth_t<float2>(st, passes, s) : orth_t<double2>(st, passes, s);
+cudaError_t krylov_orthogonalise(const KrylovState& st, int passes, int j, cudaStream_t s) {
+  return st.basis_fp32 ? orth_t<float2>(st, passes, j, s) : orth_t<double2>(st, passes, j, s);
 }
-cudaError_t krylov_finish_step(const KrylovState& st, double tol, cudaStream_t s) {
-  return st.basis_fp32 ? finish_t<float2>(st, tol, s) : finish_t<double2>(st, tol, s);
+cudaError_t krylov_finish_step(const KrylovState& st, double tol, int j, cudaStream_t s) {
+  return st.basis_fp32 ? finish_t<float2>(st, tol, j, s) : finish_t<double2>(st, tol, j, s);
 }
 cudaError_t krylov_update_solution(const KrylovState& st, double2* x, cudaStream_t s) {
   return st.basis_fp32 ? xupd_t<float2>(st, x, s) : xupd_t<double2>(st, x, s);

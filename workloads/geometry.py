@@ -151,7 +151,7 @@ def cfg_circle_c1(n: int = 256) -> Problem:
 def cfg_star_c2(n: int = 4096) -> Problem:
     """Star r(t) = 1 + 0.3 cos(5t), k_e = 20, k_i = 30, 4096 elements."""
     return Problem(k=[20.0, 30.0], eps=[1.0, 2.25],
-                   segments=[Segment(star(n, 0.3, 5), P=0, M=1, closed=True)], name="star5_k20_n4096")
+                   segments=[Segment(star(n, 0.3, 5), P=0, M=1, closed=True)], name=f"star5_k20_n{n}")
 
 
 def cfg_junction_c3(n: int = 8192) -> Problem:
