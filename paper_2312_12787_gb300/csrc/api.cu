@@ -281,6 +281,7 @@ size_t krylov_bytes(int n2, int nrhs, int m, bool fp32) {
   add((size_t)nrhs * 4);                  // active
   add((size_t)nrhs * 4);                  // iters
   add((size_t)nrhs * 8);                  // resid
+  add((size_t)nrhs * 8);                  // tolv
   add(4);                                 // jdev
   add(4);                                 // n_active
   // mixed extras: residual r (FP64), rhs copy of the inner solve (FP32 not needed), tc workspace
@@ -334,6 +335,7 @@ Solver carve_solver(bem_problem* p, int nrhs, bool fp32) {
   st.active = c.take<int>(nrhs);
   st.iters = c.take<int>(nrhs);
   st.resid = c.take<double>(nrhs);
+  st.tolv = c.take<double>(nrhs);
   st.jdev = c.take<int>(1);
   st.n_active = c.take<int>(1);
   sv.r = c.take<double2>((size_t)nrhs * n2);
@@ -344,10 +346,12 @@ Solver carve_solver(bem_problem* p, int nrhs, bool fp32) {
 }
 
 // One unrestarted GMRES run from x0 = 0 on r0 (FP64 block), adding the correction into x.
-bem_status gmres_run(bem_problem* p, Solver& sv, const double2* r0, double2* x, double tol, std::vector<int>& iters,
-                     std::vector<double>& resid, cudaStream_t s) {
+bem_status gmres_run(bem_problem* p, Solver& sv, const double2* r0, double2* x, const std::vector<double>& tols,
+                     std::vector<int>& iters, std::vector<double>& resid, cudaStream_t s) {
   KrylovState& st = sv.st;
   const int n2 = st.n, nrhs = st.nrhs;
+  const double tol = tols[0];
+  CU(cudaMemcpyAsync(const_cast<double*>(st.tolv), tols.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, s));
   {
     Phase ph(p, BEM_PH_GIVENS, s, 3);
     CU(krylov_start(st, r0, tol, s));
@@ -389,7 +393,11 @@ bem_status gmres_run(bem_problem* p, Solver& sv, const double2* r0, double2* x, 
   std::vector<double> rs(nrhs);
   CU(cudaMemcpyAsync(it.data(), st.iters, nrhs * sizeof(int), cudaMemcpyDeviceToHost, s));
   CU(cudaMemcpyAsync(rs.data(), st.resid, nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
+  int tc_err = 0;
+  if (fp32 && p->o.prec == BEM_PREC_MIXED_TC && nrhs > 1 && matvec_tc_supported(n2, nrhs))
+    CU(cudaMemcpyAsync(&tc_err, matvec_tc_error_word(sv.tcws, n2, nrhs), sizeof(int), cudaMemcpyDeviceToHost, s));
   CU(cudaStreamSynchronize(s));
+  if (tc_err) return fail(BEM_ETIMEOUT, "tensor-core GEMM wait expired (code %d)", tc_err);
   for (int r = 0; r < nrhs; ++r) {
     iters[r] += it[r];
     resid[r] = rs[r];
@@ -434,7 +442,7 @@ bem_status solve_impl(bem_problem* p, int nrhs, const double2* b, double2* x, in
   CU(cudaMemsetAsync(x, 0, (size_t)nrhs * n2 * sizeof(double2), s));
   bem_status result = BEM_OK;
   if (!mixed) {
-    st = gmres_run(p, sv, b, x, p->o.tol, iters, resid, s);
+    st = gmres_run(p, sv, b, x, std::vector<double>(nrhs, p->o.tol), iters, resid, s);
     if (st != BEM_OK) return st;
     for (int r = 0; r < nrhs; ++r)
       if (resid[r] > p->o.tol) result = BEM_ENOCONV;
@@ -454,8 +462,11 @@ bem_status solve_impl(bem_problem* p, int nrhs, const double2* b, double2* x, in
         else done = false;
       }
       if (done) break;
-      std::vector<double> inner_res(nrhs);
-      st = gmres_run(p, sv, sv.r, x, p->o.inner_tol, iters, inner_res, s);
+      // each column's inner run only needs to reach what the outer tolerance still asks of it
+      std::vector<double> inner_res(nrhs), tols(nrhs);
+      for (int r = 0; r < nrhs; ++r)
+        tols[r] = rn[r] > 0 ? std::max(p->o.inner_tol, 0.3 * p->o.tol * bn[r] / rn[r]) : 1.0;
+      st = gmres_run(p, sv, sv.r, x, tols, iters, inner_res, s);
       if (st != BEM_OK) return st;
       {
         Phase ph(p, BEM_PH_RESIDUAL, s, 1);

@@ -73,6 +73,8 @@ cudaError_t launch_residual_split(const float2* Ahi, const float2* Alo, size_t l
 cudaError_t launch_matvec_tc(const float2* A, size_t lda, int n, int nrhs, const float2* x, float2* y,
                              void* ws, size_t ws_bytes, cudaStream_t s);
 size_t matvec_tc_workspace_bytes(int n, int nrhs);
+// Device word where the tensor-core kernel records a bounded-wait expiry (0 = none) inside ws.
+int* matvec_tc_error_word(void* ws, int n, int nrhs);
 bool matvec_tc_supported(int n, int nrhs);
 
 // Element-wise conversions between complex FP64 and FP32 blocks; column 2-norms of an FP64 block.
@@ -101,6 +103,7 @@ struct KrylovState {
   int* active;      // nrhs: 1 while iterating
   int* iters;       // nrhs
   double* resid;    // nrhs: estimated relative residual
+  const double* tolv;  // nrhs per-system tolerances (overrides the scalar tol when non-null)
   int* jdev;        // current iteration index (device copy)
   int* n_active;    // device counter of active systems
 };

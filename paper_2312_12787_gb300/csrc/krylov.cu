@@ -219,7 +219,8 @@ __global__ void k_finish(KrylovState st, int nchunk, double tol, int j) {
   st.resid[s] = res;
   st.iters[s] = j + 1;
   st.hnext[s] = hn;
-  if (res <= tol || j + 1 >= st.m || hn == 0.0) st.active[s] = 0;
+  const double tl = st.tolv ? st.tolv[s] : tol;
+  if (res <= tl || j + 1 >= st.m || hn == 0.0) st.active[s] = 0;
 }
 
 template <typename T>

@@ -204,3 +204,41 @@ def test_invalid_mesh_rejected_on_device_path(B, torch):
         p.bem_assemble()
     assert e.value.status == B.BEM_EINVAL
     p.close()
+
+
+@pytest.mark.parametrize("ne,nrhs", [(700, 3), (700, 64), (4096, 64)])
+def test_matvec_tensor_core_matches_reference(B, torch, ne, nrhs):
+    """3xTF32 tcgen05 GEMM: y = A_hi x against the complex128 product of the same stored FP32 matrix.
+    4096 elements x 64 columns is the launch configuration the benchmark times."""
+    wp = W.Problem(k=[20.0, 30.0], eps=[1.0, 2.25], segments=[W.Segment(W.star(ne, 0.3, 5), P=0, M=1, closed=True)])
+    p = B.Problem.from_workload(wp, prec="mixed_tc")
+    n2 = p.bem_num_unknowns()
+    A = torch.empty((n2, n2), dtype=torch.complex128, device="cuda")
+    p.bem_get_matrix(A, which=0)
+    g = torch.Generator(device="cpu").manual_seed(nrhs)
+    x = torch.randn((nrhs, n2), dtype=torch.complex128, generator=g).cuda()
+    x = x.to(torch.complex64).to(torch.complex128)        # the kernel sees FP32 inputs
+    y = torch.empty_like(x)
+    for rep in range(2):                                   # two calls in a row: no state carried over
+        p.bem_profile_enable(True)
+        p.bem_matvec(x, y, n_rhs=nrhs)
+        prof = p.bem_profile_read()
+        assert prof["matvec"][1] == 1
+        ref = (A @ x.T).T
+        err = (torch.linalg.vector_norm(y - ref, dim=1) / torch.linalg.vector_norm(ref, dim=1)).max().item()
+        assert err <= 2e-6, err
+    p.close()
+
+
+def test_solve_mixed_tensor_core_matches_oracle_lu(B, torch):
+    wp = W.Problem(k=[20.0, 30.0], eps=[1.0, 2.25], segments=[W.Segment(W.star(700, 0.3, 5), P=0, M=1, closed=True)])
+    A = O.assemble(wp, Q=4)
+    ang = W.plane_wave_angles(8)
+    p = B.Problem.from_workload(wp, prec="mixed_tc", tol=1e-10)
+    x = torch.empty((8, p.bem_num_unknowns()), dtype=torch.complex128, device="cuda")
+    st, it, rs = p.bem_solve_planewave(ang, x)
+    assert st == B.BEM_OK and np.all(rs <= 1e-10), (st, rs)
+    for r in (0, 3, 7):
+        xl = O.solve_lu(A, O.rhs_planewave(wp, ang[r]))
+        assert rel(x[r].cpu().numpy(), xl) <= SOLUTION_TOL_MIXED
+    p.close()
