@@ -137,6 +137,12 @@ BEM_API bem_status bem_rhs_planewave(bem_problem* p, int n_rhs, const double* an
  * (FP64: FP64 GEMV/GEMM; MIXED: FP32 GEMV; MIXED_TC: tensor-core GEMM when n_rhs > 1). */
 BEM_API bem_status bem_matvec(bem_problem* p, int n_rhs, const bem_c64* x_dev, bem_c64* y_dev, void* stream);
 
+/* Step a9's residual: r = b - A x for n_rhs columns with the solver's FP64-accurate operator (FP64 path:
+ * FP64 products of A; mixed paths: (hi + lo) x in double-float arithmetic on the FP32 pipes).
+ * x_dev, b_dev, r_dev: n_rhs x 2N complex FP64 (r_dev may alias b_dev, not x_dev). */
+BEM_API bem_status bem_residual(bem_problem* p, int n_rhs, const bem_c64* x_dev, const bem_c64* b_dev, bem_c64* r_dev,
+                                void* stream);
+
 /* Steps a6..a9: solve A x = b for n_rhs right-hand sides b_dev (n_rhs x 2N) into x_dev.
  * iters_host[r] = total GMRES iterations (matvecs) of column r, resid_host[r] = final relative residual
  * ||b - A x|| / ||b|| computed in FP64 (FP64 path: from the GMRES estimate).  Either may be NULL. */

@@ -471,7 +471,7 @@ bem_status solve_impl(bem_problem* p, int nrhs, const double2* b, double2* x, in
       {
         Phase ph(p, BEM_PH_RESIDUAL, s, 1);
         CU(launch_residual_split(static_cast<const float2*>(p->d_A), static_cast<const float2*>(p->d_Alo), n2, n2,
-                                 nrhs, x, b, sv.r, s));
+                                 nrhs, x, b, sv.r, sv.st.V, s));   // the basis is free here
       }
       st = column_norms(p, sv, sv.r, nrhs, rn, s);
       if (st != BEM_OK) return st;
@@ -670,6 +670,30 @@ BEM_API bem_status bem_matvec(bem_problem* p, int n_rhs, const bem_c64* x_dev, b
     Phase ph(p, BEM_PH_OTHER, s, 1);
     CU(launch_convert_c32_c64(yf, y, (size_t)n_rhs * n2, s));
   }
+  return BEM_OK;
+}
+
+BEM_API bem_status bem_residual(bem_problem* p, int n_rhs, const bem_c64* x_dev, const bem_c64* b_dev, bem_c64* r_dev,
+                                void* stream) {
+  if (!p || !x_dev || !b_dev || !r_dev || n_rhs < 1) return fail(BEM_EINVAL, "invalid argument");
+  if ((const void*)r_dev == (const void*)x_dev) return fail(BEM_EINVAL, "r_dev must not alias x_dev");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  bem_status st = assemble_impl(p, s);
+  if (st != BEM_OK) return st;
+  const int n2 = 2 * p->n;
+  const double2* x = reinterpret_cast<const double2*>(x_dev);
+  const double2* b = reinterpret_cast<const double2*>(b_dev);
+  double2* r = reinterpret_cast<double2*>(r_dev);
+  Phase ph(p, BEM_PH_RESIDUAL, s, p->mixed() ? 2 : 1);
+  if (!p->mixed()) {
+    CU(launch_residual_c64(static_cast<const double2*>(p->d_A), n2, n2, n_rhs, x, b, r, s));
+    return BEM_OK;
+  }
+  st = ensure_ws(p, krylov_bytes(n2, n_rhs, p->o.max_iter, true));
+  if (st != BEM_OK) return st;
+  Solver sv = carve_solver(p, n_rhs, true);
+  CU(launch_residual_split(static_cast<const float2*>(p->d_A), static_cast<const float2*>(p->d_Alo), n2, n2, n_rhs, x,
+                           b, r, sv.st.V, s));
   return BEM_OK;
 }
 

@@ -65,9 +65,14 @@ cudaError_t launch_matvec_c64(const double2* A, size_t lda, int n, int nrhs, con
 // y[r] = A x[r] with A complex FP32 (hi only), x and y complex FP32.
 cudaError_t launch_matvec_c32(const float2* A, size_t lda, int n, int nrhs, const float2* x, float2* y,
                               const int* active, cudaStream_t s);
-// r = b - (hi + lo) x, with FP64 x, b, r (refinement residual); also writes ||r||^2 partials per column.
+// r = b - (hi + lo) x, with FP64 x, b, r (refinement residual) in double-float arithmetic; ws must hold
+// 2 * nrhs * n float2.  The _f64 variant computes the same in FP64 arithmetic.
 cudaError_t launch_residual_split(const float2* Ahi, const float2* Alo, size_t lda, int n, int nrhs,
-                                  const double2* x, const double2* b, double2* r, cudaStream_t s);
+                                  const double2* x, const double2* b, double2* r, void* ws, cudaStream_t s);
+cudaError_t launch_residual_c64(const double2* A, size_t lda, int n, int nrhs, const double2* x, const double2* b,
+                                double2* r, cudaStream_t s);
+cudaError_t launch_residual_split_f64(const float2* Ahi, const float2* Alo, size_t lda, int n, int nrhs,
+                                      const double2* x, const double2* b, double2* r, cudaStream_t s);
 // tcgen05 tensor-core GEMM Y = A X (A c32, X / Y c32, nrhs <= 64).  Returns cudaErrorNotSupported if the
 // shape is not supported by the kernel.
 cudaError_t launch_matvec_tc(const float2* A, size_t lda, int n, int nrhs, const float2* x, float2* y,

@@ -126,13 +126,23 @@ __global__ void __launch_bounds__(kThreads) k_dots(KrylovState st, int nchunk, i
   }
 }
 
-// h_i = sum over chunks (FP64); accumulate into column j of H (pass 0 sets, later passes add).
+// h_i = sum over chunks (FP64), one warp per (system, i); accumulate into column j of H (pass 0 sets,
+// later passes add).  grid = (ceil((j+1)/8), systems), 8 warps per block.
 __global__ void k_dots_reduce(KrylovState st, int nchunk, int pass, int j) {
-  const int s = blockIdx.x;
+  const int s = blockIdx.y;
   if (!st.active[s]) return;
-  for (int i = threadIdx.x; i <= j; i += blockDim.x) {
-    double2 h = make_double2(0, 0);
-    for (int c = 0; c < nchunk; ++c) h = cadd(h, st.part[((size_t)s * nchunk + c) * (st.m + 1) + i]);
+  const int i = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (i > j) return;
+  double hx = 0.0, hy = 0.0;
+  for (int c = lane; c < nchunk; c += 32) {
+    const double2 v = st.part[((size_t)s * nchunk + c) * (st.m + 1) + i];
+    hx += v.x;
+    hy += v.y;
+  }
+  hx = warp_sum(hx);
+  hy = warp_sum(hy);
+  if (lane == 0) {
+    const double2 h = make_double2(hx, hy);
     st.hcol[(size_t)s * (st.m + 1) + i] = h;
     double2* Hj = st.H + ((size_t)s * st.m + j) * (st.m + 1);
     Hj[i] = pass == 0 ? h : cadd(Hj[i], h);
@@ -157,6 +167,7 @@ __global__ void __launch_bounds__(kThreads) k_update(KrylovState st, int nchunk,
   const T* V = static_cast<const T*>(st.V) + (size_t)s * st.n;
   F ax = 0, ay = 0;
   if (k < st.n) {
+#pragma unroll 4
     for (int i = sub; i <= j; i += 4) {
       const T v = V[(size_t)i * stride + k];
       const F hx = (F)hs[i].x, hy = (F)hs[i].y;
@@ -184,25 +195,27 @@ __global__ void __launch_bounds__(kThreads) k_update(KrylovState st, int nchunk,
 
 // h_{j+1,j} = ||w||; apply the previous Givens rotations to column j, form the new one, update g and
 // the residual estimate |g_{j+1}| / beta.  Rotation i acts on rows (i, i+1) as [[conj c, conj s], [-s, c]].
+// One warp per system: the lanes reduce the chunk norms, lane 0 runs the (sequential) rotations.
 __global__ void k_finish(KrylovState st, int nchunk, double tol, int j) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  const int s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (s >= st.nrhs || !st.active[s]) return;
   double t = 0.0;
-  for (int c = 0; c < nchunk; ++c) t += st.npart[(size_t)s * nchunk + c];
+  for (int c = lane; c < nchunk; c += 32) t += st.npart[(size_t)s * nchunk + c];
+  t = warp_sum(t);
+  if (lane != 0) return;
   const double hn = sqrt(t);
   double2* Hj = st.H + ((size_t)s * st.m + j) * (st.m + 1);
   Hj[j + 1] = make_double2(hn, 0.0);
   double2* cs = st.cs + (size_t)s * st.m;
   double2* sn = st.sn + (size_t)s * st.m;
+  double2 a = Hj[0];
   for (int i = 0; i < j; ++i) {
-    const double2 a = Hj[i], b = Hj[i + 1];
+    const double2 b = Hj[i + 1];
     const double2 ci = cs[i], si = sn[i];
-    const double2 ta = cadd(cdotc(ci, a), cdotc(si, b));   // conj(c) a + conj(s) b
-    const double2 tb = csub(cmul(ci, b), cmul(si, a));     // -s a + c b
-    Hj[i] = ta;
-    Hj[i + 1] = tb;
+    Hj[i] = cadd(cdotc(ci, a), cdotc(si, b));   // conj(c) a + conj(s) b
+    a = csub(cmul(ci, b), cmul(si, a));         // -s a + c b  (becomes row i+1)
   }
-  const double2 a = Hj[j], b = Hj[j + 1];
+  const double2 b = Hj[j + 1];
   const double den = hypot(hypot(a.x, a.y), hypot(b.x, b.y));
   double2 c, sv;
   if (den == 0.0) { c = make_double2(1, 0); sv = make_double2(0, 0); }
@@ -302,7 +315,7 @@ cudaError_t orth_t(const KrylovState& st, int passes, int j, cudaStream_t s) {
   dim3 grd(nc, st.nrhs);
   for (int p = 0; p < passes; ++p) {
     k_dots<T><<<grd, kThreads, 0, s>>>(st, nc, j);
-    k_dots_reduce<<<st.nrhs, 128, 0, s>>>(st, nc, p, j);
+    k_dots_reduce<<<dim3((j + 8) / 8, st.nrhs), 256, 0, s>>>(st, nc, p, j);
     k_update<T><<<grd, kThreads, 0, s>>>(st, nc, j);
   }
   return cudaGetLastError();
@@ -311,7 +324,7 @@ cudaError_t orth_t(const KrylovState& st, int passes, int j, cudaStream_t s) {
 template <typename T>
 cudaError_t finish_t(const KrylovState& st, double tol, int j, cudaStream_t s) {
   const int nc = nchunk_of(st.n);
-  k_finish<<<(st.nrhs + 63) / 64, 64, 0, s>>>(st, nc, tol, j);
+  k_finish<<<(st.nrhs + 7) / 8, 256, 0, s>>>(st, nc, tol, j);
   k_scale_next<T><<<dim3(nblk_of(st.n), st.nrhs), kThreads, 0, s>>>(st, j);
   k_advance<<<1, 32, 0, s>>>(st);
   return cudaGetLastError();

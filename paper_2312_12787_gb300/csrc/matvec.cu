@@ -11,6 +11,7 @@
 //                   step; partial sums are folded into FP64 every 16 steps.  HBM-bound.
 //  * k_gemm_f64   - Y = A X for several columns, SIMT tile 64 rows x 64 columns, FP64 arithmetic.
 //  * k_gemm_c32   - the same in complex FP32 with two-level FP32 accumulation.
+//  * k_resid_df_* - refinement residual b - (hi + lo) x in double-float arithmetic (see below).
 #include "internal.cuh"
 
 namespace bem {
@@ -256,6 +257,136 @@ __global__ void __launch_bounds__(256) k_column_norms(const double2* v, int n, d
   }
 }
 
+// ---- refinement residual r = b - (hi + lo) x in double-float arithmetic on the FP32 pipes ----------
+// x (FP64) is first split into x_hi + x_lo (FP32).  The leading products hi * x_hi are formed exactly
+// (p = a b, e = fma(a, b, -p)) and summed with error-free two-sum steps into a running sum s and a
+// compensation c (the accurate dot-product scheme of Ogita, Rump and Oishi); the small terms
+// hi * x_lo + lo * x_hi join c directly.  The result s + c carries about twice FP32 precision, enough
+// for the residual of the FP64 refinement, at FP32-pipe speed instead of GB300's scarce FP64 rate.
+
+__device__ __forceinline__ void dot2_acc(float a, float b, float& s, float& c) {
+  const float p = a * b;
+  const float e = fmaf(a, b, -p);
+  const float t = s + p;
+  const float bp = t - s;
+  c += ((s - (t - bp)) + (p - bp)) + e;
+  s = t;
+}
+
+__global__ void k_split_x(const double2* __restrict__ x, float2* __restrict__ xh, float2* __restrict__ xl,
+                          size_t count) {
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < count; t += (size_t)gridDim.x * blockDim.x) {
+    const double2 v = x[t];
+    const float hx = (float)v.x, hy = (float)v.y;
+    xh[t] = make_float2(hx, hy);
+    xl[t] = make_float2((float)(v.x - (double)hx), (float)(v.y - (double)hy));
+  }
+}
+
+// one complex multiply-accumulate y += (ah + al)(xh + xl) into (sr, cr), (si, ci)
+__device__ __forceinline__ void cmac_df(float2 ah, float2 al, float2 xh, float2 xl, float& sr, float& cr, float& si,
+                                        float& ci) {
+  dot2_acc(ah.x, xh.x, sr, cr);
+  dot2_acc(-ah.y, xh.y, sr, cr);
+  dot2_acc(ah.x, xh.y, si, ci);
+  dot2_acc(ah.y, xh.x, si, ci);
+  cr = fmaf(ah.x, xl.x, cr); cr = fmaf(-ah.y, xl.y, cr); cr = fmaf(al.x, xh.x, cr); cr = fmaf(-al.y, xh.y, cr);
+  ci = fmaf(ah.x, xl.y, ci); ci = fmaf(ah.y, xl.x, ci); ci = fmaf(al.x, xh.y, ci); ci = fmaf(al.y, xh.x, ci);
+}
+
+// r[s][row] = b[s][row] - sum_c (hi + lo)[row][c] x[s][c]; one warp per row, grid.y = column.
+__global__ void __launch_bounds__(256) k_resid_df_gemv(const float2* __restrict__ Ah, const float2* __restrict__ Al,
+                                                        size_t lda, int n, const float2* __restrict__ xh,
+                                                        const float2* __restrict__ xl, const double2* __restrict__ b,
+                                                        double2* __restrict__ r) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row = blockIdx.x * 8 + warp;
+  const int s = blockIdx.y;
+  if (row >= n) return;
+  const float2* ah = Ah + (size_t)row * lda;
+  const float2* al = Al + (size_t)row * lda;
+  const float2* vh = xh + (size_t)s * n;
+  const float2* vl = xl + (size_t)s * n;
+  float sr = 0.f, cr = 0.f, si = 0.f, ci = 0.f;
+#pragma unroll 4
+  for (int c = lane; c < n; c += 32) cmac_df(__ldcs(ah + c), __ldcs(al + c), __ldg(vh + c), __ldg(vl + c), sr, cr, si, ci);
+  double re = (double)sr + (double)cr, im = (double)si + (double)ci;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    re += __shfl_xor_sync(0xffffffffu, re, o);
+    im += __shfl_xor_sync(0xffffffffu, im, o);
+  }
+  if (lane == 0) {
+    const double2 bb = b[(size_t)s * n + row];
+    r[(size_t)s * n + row] = make_double2(bb.x - re, bb.y - im);
+  }
+}
+
+// Tiled version for many columns: tile 32 rows x 64 columns x 16, 256 threads, each 2 rows x 4 columns.
+__global__ void __launch_bounds__(256) k_resid_df_gemm(const float2* __restrict__ Ah, const float2* __restrict__ Al,
+                                                        size_t lda, int n, int nrhs, const float2* __restrict__ xh,
+                                                        const float2* __restrict__ xl, const double2* __restrict__ b,
+                                                        double2* __restrict__ r) {
+  constexpr int BR = 32, BS = 64, BK = 16;
+  __shared__ float2 Ash[BK][BR + 1], Asl[BK][BR + 1];
+  __shared__ float2 Xsh[BK][BS + 1], Xsl[BK][BS + 1];
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  const int r0 = blockIdx.x * BR, s0 = blockIdx.y * BS;
+  float sr[2][4], cr[2][4], si[2][4], ci[2][4];
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) sr[a][q] = cr[a][q] = si[a][q] = ci[a][q] = 0.f;
+  const float2 z = make_float2(0.f, 0.f);
+  for (int k0 = 0; k0 < n; k0 += BK) {
+    // A: 32 x 16 = 512 entries (2 per thread); X: 64 x 16 = 1024 entries (4 per thread)
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      const int e = tid + t * 256;
+      const int rr = e >> 4, kk = e & 15;
+      const int gr = r0 + rr, gk = k0 + kk;
+      const bool in = gr < n && gk < n;
+      Ash[kk][rr] = in ? __ldcs(Ah + (size_t)gr * lda + gk) : z;
+      Asl[kk][rr] = in ? __ldcs(Al + (size_t)gr * lda + gk) : z;
+    }
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int e = tid + t * 256;
+      const int ss = e >> 4, kk = e & 15;
+      const int gs = s0 + ss, gk = k0 + kk;
+      const bool in = gs < nrhs && gk < n;
+      Xsh[kk][ss] = in ? xh[(size_t)gs * n + gk] : z;
+      Xsl[kk][ss] = in ? xl[(size_t)gs * n + gk] : z;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < BK; ++kk) {
+      float2 ah[2], al[2], vh[4], vl[4];
+#pragma unroll
+      for (int a = 0; a < 2; ++a) { ah[a] = Ash[kk][ty + 16 * a]; al[a] = Asl[kk][ty + 16 * a]; }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) { vh[q] = Xsh[kk][tx + 16 * q]; vl[q] = Xsl[kk][tx + 16 * q]; }
+#pragma unroll
+      for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) cmac_df(ah[a], al[a], vh[q], vl[q], sr[a][q], cr[a][q], si[a][q], ci[a][q]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int gr = r0 + ty + 16 * a, gs = s0 + tx + 16 * q;
+      if (gr < n && gs < nrhs) {
+        const double2 bb = b[(size_t)gs * n + gr];
+        r[(size_t)gs * n + gr] = make_double2(bb.x - ((double)sr[a][q] + (double)cr[a][q]),
+                                              bb.y - ((double)si[a][q] + (double)ci[a][q]));
+      }
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_convert_c64_c32(const double2* in, float2* out, size_t count, cudaStream_t s) {
@@ -297,7 +428,37 @@ cudaError_t launch_matvec_c32(const float2* A, size_t lda, int n, int nrhs, cons
 }
 
 cudaError_t launch_residual_split(const float2* Ahi, const float2* Alo, size_t lda, int n, int nrhs,
-                                  const double2* x, const double2* b, double2* r, cudaStream_t s) {
+                                  const double2* x, const double2* b, double2* r, void* ws, cudaStream_t s) {
+  // ws holds x split into two complex FP32 blocks (2 * nrhs * n float2)
+  float2* xh = static_cast<float2*>(ws);
+  float2* xl = xh + (size_t)nrhs * n;
+  k_split_x<<<512, 256, 0, s>>>(x, xh, xl, (size_t)nrhs * n);
+  if (nrhs < 4) {
+    dim3 grd((n + 7) / 8, nrhs);
+    k_resid_df_gemv<<<grd, 256, 0, s>>>(Ahi, Alo, lda, n, xh, xl, b, r);
+  } else {
+    dim3 grd((n + 31) / 32, (nrhs + 63) / 64);
+    k_resid_df_gemm<<<grd, 256, 0, s>>>(Ahi, Alo, lda, n, nrhs, xh, xl, b, r);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_residual_c64(const double2* A, size_t lda, int n, int nrhs, const double2* x, const double2* b,
+                                double2* r, cudaStream_t s) {
+  LoadC64 ld{A};
+  if (nrhs == 1) {
+    dim3 grd((n + 7) / 8, 1);
+    k_gemv_f64<LoadC64, true><<<grd, 256, 0, s>>>(ld, lda, n, x, b, r);
+  } else {
+    dim3 grd((n + 63) / 64, (nrhs + 63) / 64);
+    k_gemm_f64<LoadC64, true><<<grd, 256, 0, s>>>(ld, lda, n, nrhs, x, b, r);
+  }
+  return cudaGetLastError();
+}
+
+// FP64 reference implementation of the same residual (kept for tests of the double-float kernels).
+cudaError_t launch_residual_split_f64(const float2* Ahi, const float2* Alo, size_t lda, int n, int nrhs,
+                                      const double2* x, const double2* b, double2* r, cudaStream_t s) {
   LoadSplit ld{Ahi, Alo};
   if (nrhs == 1) {
     dim3 grd((n + 7) / 8, 1);

