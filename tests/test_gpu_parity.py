@@ -260,7 +260,7 @@ def test_residual_matches_oracle(B, torch, prec, nrhs):
         if kind == "random":
             x = rng.normal(size=(nrhs, n2)) + 1j * rng.normal(size=(nrhs, n2))
         else:
-            x = np.linalg.solve(A, b.T).T
+            x = np.ascontiguousarray(np.linalg.solve(A, b.T).T)
         ref = b - (A @ x.T).T
         scale = np.max(np.abs(A)) * np.max(np.abs(x)) * np.sqrt(n2)
         p = B.Problem.from_workload(wp, prec=prec)
