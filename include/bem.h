@@ -143,6 +143,20 @@ BEM_API bem_status bem_matvec(bem_problem* p, int n_rhs, const bem_c64* x_dev, b
 BEM_API bem_status bem_residual(bem_problem* p, int n_rhs, const bem_c64* x_dev, const bem_c64* b_dev, bem_c64* r_dev,
                                 void* stream);
 
+/* The same residual as bem_residual (mixed-precision problems only) without any device allocation.  The
+ * paper has no counterpart: this is a library facility.  bem_residual takes its scratch from the problem's
+ * solver workspace and may allocate it; callers that cannot allocate at that point (memory handed to their
+ * own arena or caching allocator, latency-bound loops where cudaMalloc would stall, processes near their
+ * memory limit) use this entry point instead.  Its scratch is a fixed static device array of 2 x 524288
+ * complex FP32 entries (8 MiB) that every GPU loading the library holds until exit; n_rhs * 2N must not
+ * exceed 524288 (BEM_EINVAL otherwise).  The problem must already be assembled (BEM_ESTATE otherwise;
+ * this call never assembles).  The first call on each device looks up the array's device address on the
+ * current device.  All calls share the one array: calls whose kernels overlap on the GPU (different
+ * streams, or different threads) race on it and must be serialised by the caller.  Nothing in it needs
+ * clearing between calls: each call writes every entry it reads. */
+BEM_API bem_status bem_residual_noalloc(bem_problem* p, int n_rhs, const bem_c64* x_dev, const bem_c64* b_dev,
+                                        bem_c64* r_dev, void* stream);
+
 /* Steps a6..a9: solve A x = b for n_rhs right-hand sides b_dev (n_rhs x 2N) into x_dev.
  * iters_host[r] = total GMRES iterations (matvecs) of column r, resid_host[r] = final relative residual
  * ||b - A x|| / ||b|| computed in FP64 (FP64 path: from the GMRES estimate).  Either may be NULL. */

@@ -24,7 +24,7 @@ PRECS = {"fp64": BEM_PREC_FP64, "mixed": BEM_PREC_MIXED, "mixed_tc": BEM_PREC_MI
 EXPORTS = [
     "bem_default_opts", "bem_problem_create", "bem_problem_destroy", "bem_set_opts", "bem_set_domains",
     "bem_add_segment", "bem_num_elements", "bem_num_unknowns", "bem_footprint_bytes", "bem_assemble",
-    "bem_get_matrix", "bem_rhs_planewave", "bem_matvec", "bem_residual", "bem_solve", "bem_solve_planewave", "bem_far_field",
+    "bem_get_matrix", "bem_rhs_planewave", "bem_matvec", "bem_residual", "bem_residual_noalloc", "bem_solve", "bem_solve_planewave", "bem_far_field",
     "bem_solve_planewave_host", "bem_profile_enable", "bem_profile_read", "bem_last_error", "bem_version",
 ]
 PHASES = ["geometry", "assemble", "rhs", "matvec", "arnoldi", "givens", "update", "residual", "farfield", "other"]
@@ -73,6 +73,7 @@ def load(path: str | None = None):
     L.bem_rhs_planewave.argtypes = [vp, i, vp, vp, vp]
     L.bem_matvec.argtypes = [vp, i, vp, vp, vp]
     L.bem_residual.argtypes = [vp, i, vp, vp, vp, vp]
+    L.bem_residual_noalloc.argtypes = [vp, i, vp, vp, vp, vp]
     L.bem_solve.argtypes = [vp, i, vp, vp, vp, vp, vp]
     L.bem_solve_planewave.argtypes = [vp, i, vp, vp, vp, vp, vp]
     L.bem_far_field.argtypes = [vp, i, vp, i, vp, vp, vp]
@@ -82,7 +83,7 @@ def load(path: str | None = None):
     L.bem_last_error.restype = ctypes.c_char_p
     L.bem_version.restype = ctypes.c_char_p
     for name in ("bem_problem_create", "bem_set_opts", "bem_set_domains", "bem_add_segment", "bem_assemble",
-                 "bem_get_matrix", "bem_rhs_planewave", "bem_matvec", "bem_residual", "bem_solve", "bem_solve_planewave",
+                 "bem_get_matrix", "bem_rhs_planewave", "bem_matvec", "bem_residual", "bem_residual_noalloc", "bem_solve", "bem_solve_planewave",
                  "bem_far_field", "bem_solve_planewave_host", "bem_profile_enable", "bem_profile_read"):
         getattr(L, name).restype = i
     _lib = L
@@ -203,6 +204,11 @@ class Problem:
 
     def bem_residual(self, x, b, r, n_rhs=1, stream=None):
         _check(load().bem_residual(self._h, n_rhs, _dptr(x), _dptr(b), _dptr(r), _stream_ptr(stream)))
+        return r
+
+    def bem_residual_noalloc(self, x, b, r, n_rhs=1, stream=None):
+        """bem_residual without device allocation (static scratch; see include/bem.h)."""
+        _check(load().bem_residual_noalloc(self._h, n_rhs, _dptr(x), _dptr(b), _dptr(r), _stream_ptr(stream)))
         return r
 
     def bem_solve(self, b, x, n_rhs=1, stream=None):

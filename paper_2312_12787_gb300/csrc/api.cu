@@ -507,6 +507,17 @@ bem_status rhs_impl(bem_problem* p, int nrhs, const double* angles_h, double2* b
 
 }  // namespace
 
+namespace bem {
+bool problem_mixed_matrix(bem_problem* p, const float2** hi, const float2** lo, int* n2) {
+  if (!p || !p->mixed() || p->mat_dirty || p->A_mixed != 1 || !p->d_A || !p->d_Alo) return false;
+  *hi = static_cast<const float2*>(p->d_A);
+  *lo = static_cast<const float2*>(p->d_Alo);
+  *n2 = 2 * p->n;
+  return true;
+}
+bem_status report_error(bem_status st, const char* msg) { return fail(st, "%s", msg); }
+}  // namespace bem
+
 // ================================== C interface ==================================================
 
 extern "C" {

@@ -118,4 +118,10 @@ cudaError_t krylov_orthogonalise(const KrylovState& st, int passes, int j, cudaS
 cudaError_t krylov_finish_step(const KrylovState& st, double tol, int j, cudaStream_t s);
 cudaError_t krylov_update_solution(const KrylovState& st, double2* x, cudaStream_t s);
 
+// Read-only view of a problem's assembled mixed-precision matrix (for entry points defined outside
+// api.cu).  Returns false if the problem has no current mixed-precision matrix.
+bool problem_mixed_matrix(bem_problem* p, const float2** hi, const float2** lo, int* n2);
+// Record a failure message for bem_last_error() and return st.
+bem_status report_error(bem_status st, const char* msg);
+
 }  // namespace bem
