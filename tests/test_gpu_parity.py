@@ -272,3 +272,36 @@ def test_residual_matches_oracle(B, torch, prec, nrhs):
         # the two matrices agree to ~1e-13 per entry; an FP32 residual would miss by ~1e-7
         assert np.max(np.abs(got - ref)) <= 1e-12 * scale, (kind, np.max(np.abs(got - ref)) / scale)
         p.close()
+
+
+@pytest.mark.slow
+def test_full_size_junction_disk_c3(B, torch):
+    """Junction disk, 8192 elements (16384 unknowns), host k = 15, halves k = 22.5 and 30, one plane wave.
+    Sampled rows of the mixed matrix against the oracle's rows, the mixed and FP64 GPU solutions against each
+    other, and the oracle's residual of the GPU solution on sampled rows (a property that holds at any size)."""
+    wp = W.cfg_junction_c3()
+    n2 = 2 * wp.n_elem
+    rng = np.random.default_rng(3)
+    rows = np.sort(np.concatenate([[0, 3071, 3072, 6143, 6144, 8191, 8192, n2 - 1], rng.choice(n2, 8, replace=False)]))
+    pm = B.Problem.from_workload(wp, prec="mixed", tol=1e-10)
+    Afull = torch.empty((n2, n2), dtype=torch.complex128, device="cuda")     # 4.3 GB
+    pm.bem_get_matrix(Afull, which=1)
+    got = Afull[torch.as_tensor(rows, device="cuda")].cpu().numpy()
+    del Afull
+    torch.cuda.empty_cache()
+    ref = O.assemble_rows(wp, rows, Q=4)
+    for a, r in zip(got, ref):
+        assert np.max(np.abs(a - r)) <= ENTRY_BLOCK_TOL * 10 * np.max(np.abs(r))
+    xm = torch.empty((1, n2), dtype=torch.complex128, device="cuda")
+    st, it, rs = pm.bem_solve_planewave([0.0], xm)
+    assert st == B.BEM_OK and rs[0] <= 1e-10
+    pm.close()
+    pf = B.Problem.from_workload(wp, prec="fp64", tol=1e-10)
+    xf = torch.empty_like(xm)
+    st, itf, rsf = pf.bem_solve_planewave([0.0], xf)
+    assert st == B.BEM_OK
+    pf.close()
+    assert rel(xm.cpu().numpy(), xf.cpu().numpy()) <= SOLUTION_TOL_MIXED
+    b = O.rhs_planewave(wp, 0.0)
+    r_rows = b[rows] - ref @ xf.cpu().numpy()[0]
+    assert np.max(np.abs(r_rows)) <= 1e-8 * np.max(np.abs(b))
