@@ -63,36 +63,6 @@ __global__ void k_elements(ElemDev e, int n) {
 //   S = (i/4) sS,  D = (ik/4) sD,  D* = -(ik/4) sDs,  N = (ik/4) sN.
 struct PairSums { double2 sS, sD, sDs, sN; };
 
-__device__ __forceinline__ void quad_sums(double k, double xi, double yi, double nxi, double nyi, double mxj,
-                                          double myj, double txj, double tyj, double hj, const Quad& q, int bm,
-                                          PairSums& ps) {
-  ps.sS = ps.sD = ps.sDs = ps.sN = make_double2(0.0, 0.0);
-  const double nxj = -tyj, nyj = txj;
-  const double nn = nxi * nxj + nyi * nyj;
-  const double half_h = 0.5 * hj;
-  for (int m = 0; m < q.Q; ++m) {
-    const double s = half_h * q.t[m];
-    const double W = half_h * q.w[m];
-    const double zx0 = xi - (mxj + s * txj), zy0 = yi - (myj + s * tyj);
-    const double r = sqrt(zx0 * zx0 + zy0 * zy0);
-    const double ir = 1.0 / r;
-    const double ux = zx0 * ir, uy = zy0 * ir;
-    const double ci = ux * nxi + uy * nyi;   // zh . n_i
-    const double cj = ux * nxj + uy * nyj;   // zh . n_j
-    Bessel01 b;
-    bessel01(k * r, b);
-    ps.sS.x += W * b.j0; ps.sS.y += W * b.y0;
-    ps.sD.x += W * cj * b.j1; ps.sD.y += W * cj * b.y1;
-    if (bm) {
-      ps.sDs.x += W * ci * b.j1; ps.sDs.y += W * ci * b.y1;
-      const double a1 = W * ir * (nn - 2.0 * ci * cj);
-      const double a0 = W * k * ci * cj;
-      ps.sN.x += a1 * b.j1 + a0 * b.j0;
-      ps.sN.y += a1 * b.y1 + a0 * b.y0;
-    }
-  }
-}
-
 template <int MIXED>
 __global__ void __launch_bounds__(256) k_assemble(ElemDev e, int n, DomTab dom, Quad q, int form, void* Aout,
                                                    void* Aloout, size_t lda) {
@@ -106,17 +76,24 @@ __global__ void __launch_bounds__(256) k_assemble(ElemDev e, int n, DomTab dom, 
   const int Pj = e.P[j], Mj = e.M[j];
   const double k1 = dom.k[0];
 
-  double2 out[2][2];
+  RowEq eq[2];
+  double sg[2], kk[2], eps[2], gim[2];
 #pragma unroll
   for (int half = 0; half < 2; ++half) {
-    const RowEq eq = row_eq(form, half, Pi, Mi, k1);
-    const int d = eq.dom;
-    const double sg = (Pj == d) ? 1.0 : ((Mj == d) ? -1.0 : 0.0);
-    const double k = dom.k[d], eps = dom.eps[d];
-    const double gim = -1.0 / (k1 * eps);          // gamma = i * gim
-    double2 cu = make_double2(0.0, 0.0), cw = make_double2(0.0, 0.0);
-    if (i == j) {
+    eq[half] = row_eq(form, half, Pi, Mi, k1);
+    const int d = eq[half].dom;
+    sg[half] = (Pj == d) ? 1.0 : ((Mj == d) ? -1.0 : 0.0);
+    kk[half] = dom.k[d];
+    eps[half] = dom.eps[d];
+    gim[half] = -1.0 / (k1 * eps[half]);        // gamma = alpha/eps_d = i * gim
+  }
+
+  double2 out[2][2];
+  if (i == j) {
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
       // exact self terms: S_ii = (i/(2k)) [int J0 + i int Y0] (0..ka), N_ii = k^2 S_ii - (ik/2) H1(ka), D = D* = 0
+      const double k = kk[half];
       const double ka = 0.5 * k * hj;
       double ij0, iy0;
       int_j0_y0(ka, ij0, iy0);
@@ -125,32 +102,73 @@ __global__ void __launch_bounds__(256) k_assemble(ElemDev e, int n, DomTab dom, 
       bessel01(ka, b);
       // -(ik/2) H1 = -(ik/2)(j1 + i y1) = (k/2) y1 - i (k/2) j1
       const double2 N = make_double2(k * k * S.x + 0.5 * k * b.y1, k * k * S.y - 0.5 * k * b.j1);
-      cu.x = 0.5;
-      cw = make_double2(-sg * eps * S.x, -sg * eps * S.y);
-      if (eq.bm) {
-        // + s gamma N ;  + gamma eps / 2
-        const double2 gN = make_double2(-gim * N.y, gim * N.x);
-        cu.x += sg * gN.x; cu.y += sg * gN.y;
-        cw.y += 0.5 * gim * eps;
+      double2 cu = make_double2(0.5, 0.0);
+      double2 cw = make_double2(-sg[half] * eps[half] * S.x, -sg[half] * eps[half] * S.y);
+      if (eq[half].bm) {
+        const double2 gN = make_double2(-gim[half] * N.y, gim[half] * N.x);
+        cu.x += sg[half] * gN.x; cu.y += sg[half] * gN.y;
+        cw.y += 0.5 * gim[half] * eps[half];
       }
-    } else if (sg != 0.0) {
-      PairSums ps;
-      quad_sums(k, xi, yi, nxi, nyi, mxj, myj, txj, tyj, hj, q, eq.bm, ps);
-      const double2 S = cscale(mul_i(ps.sS), 0.25);
-      const double2 D = cscale(mul_i(ps.sD), 0.25 * k);
-      cu = cscale(D, sg);
-      cw = cscale(S, -sg * eps);
-      if (eq.bm) {
-        const double2 Ds = cscale(mul_i(ps.sDs), -0.25 * k);
-        const double2 N = cscale(mul_i(ps.sN), 0.25 * k);
-        const double2 gN = make_double2(-gim * N.y, gim * N.x);
-        const double2 gDs = make_double2(-gim * Ds.y, gim * Ds.x);
-        cu.x += sg * gN.x; cu.y += sg * gN.y;
-        cw.x -= sg * eps * gDs.x; cw.y -= sg * eps * gDs.y;
+      out[half][0] = cmul(eq[half].scale, cu);
+      out[half][1] = cmul(eq[half].scale, cw);
+    }
+  } else {
+    // Gauss-Legendre sums; the geometry of each node is shared by the two row domains
+    PairSums ps[2];
+#pragma unroll
+    for (int half = 0; half < 2; ++half) ps[half].sS = ps[half].sD = ps[half].sDs = ps[half].sN = make_double2(0, 0);
+    const double nxj = -tyj, nyj = txj;
+    const double nn = nxi * nxj + nyi * nyj;
+    const double half_h = 0.5 * hj;
+    for (int m = 0; m < q.Q; ++m) {
+      const double sq = half_h * q.t[m];
+      const double W = half_h * q.w[m];
+      const double zx0 = xi - (mxj + sq * txj), zy0 = yi - (myj + sq * tyj);
+      const double r2 = zx0 * zx0 + zy0 * zy0;
+      const double ir = rsqrt(r2);
+      const double r = r2 * ir;
+      const double ux = zx0 * ir, uy = zy0 * ir;
+      const double ci = ux * nxi + uy * nyi;   // zh . n_i
+      const double cj = ux * nxj + uy * nyj;   // zh . n_j
+#pragma unroll
+      for (int half = 0; half < 2; ++half) {
+        if (sg[half] == 0.0) continue;
+        const double k = kk[half];
+        Bessel01 b;
+        bessel01(k * r, b);
+        PairSums& p = ps[half];
+        p.sS.x += W * b.j0; p.sS.y += W * b.y0;
+        p.sD.x += W * cj * b.j1; p.sD.y += W * cj * b.y1;
+        if (eq[half].bm) {
+          p.sDs.x += W * ci * b.j1; p.sDs.y += W * ci * b.y1;
+          const double a1 = W * ir * (nn - 2.0 * ci * cj);
+          const double a0 = W * k * ci * cj;
+          p.sN.x += a1 * b.j1 + a0 * b.j0;
+          p.sN.y += a1 * b.y1 + a0 * b.y0;
+        }
       }
     }
-    out[half][0] = cmul(eq.scale, cu);
-    out[half][1] = cmul(eq.scale, cw);
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+      double2 cu = make_double2(0.0, 0.0), cw = make_double2(0.0, 0.0);
+      if (sg[half] != 0.0) {
+        const double k = kk[half];
+        const double2 S = cscale(mul_i(ps[half].sS), 0.25);
+        const double2 D = cscale(mul_i(ps[half].sD), 0.25 * k);
+        cu = cscale(D, sg[half]);
+        cw = cscale(S, -sg[half] * eps[half]);
+        if (eq[half].bm) {
+          const double2 Ds = cscale(mul_i(ps[half].sDs), -0.25 * k);
+          const double2 N = cscale(mul_i(ps[half].sN), 0.25 * k);
+          const double2 gN = make_double2(-gim[half] * N.y, gim[half] * N.x);
+          const double2 gDs = make_double2(-gim[half] * Ds.y, gim[half] * Ds.x);
+          cu.x += sg[half] * gN.x; cu.y += sg[half] * gN.y;
+          cw.x -= sg[half] * eps[half] * gDs.x; cw.y -= sg[half] * eps[half] * gDs.y;
+        }
+      }
+      out[half][0] = cmul(eq[half].scale, cu);
+      out[half][1] = cmul(eq[half].scale, cw);
+    }
   }
   const size_t r0 = (size_t)i * lda, r1 = (size_t)(n + i) * lda;
   if (MIXED) {

@@ -122,6 +122,100 @@ BEM_HD void bessel01_miller(double x, Bessel01& b) {
   b.y1 = kTwoOverPi * (lg * j1 - j0 / x) + kTwoOverPi * sy1 * s;
 }
 
+// ---- double-float arithmetic (a value is hi + lo, two FP32 numbers; ~48-bit significand) ----------
+// Error-free transformations of Knuth (two-sum), Dekker (fast two-sum) and the FMA-based exact product.
+// GB300 executes FP32 at many times its FP64 rate, so recurrences that need more than FP32 accuracy run
+// faster in this form than in native FP64.
+struct F2 {
+  float h, l;
+};
+BEM_HD F2 f2_two_sum(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  return F2{s, (a - (s - bb)) + (b - bb)};
+}
+BEM_HD F2 f2_fast_two_sum(float a, float b) {   // requires |a| >= |b| or a == 0
+  const float s = a + b;
+  return F2{s, b - (s - a)};
+}
+BEM_HD F2 f2_add(F2 a, F2 b) {
+  const F2 s = f2_two_sum(a.h, b.h);
+  return f2_fast_two_sum(s.h, s.l + (a.l + b.l));
+}
+BEM_HD F2 f2_neg(F2 a) { return F2{-a.h, -a.l}; }
+BEM_HD F2 f2_mul(F2 a, F2 b) {
+  const float p = a.h * b.h;
+  float e = fmaf(a.h, b.h, -p);
+  e = fmaf(a.h, b.l, e);
+  e = fmaf(a.l, b.h, e);
+  return f2_fast_two_sum(p, e);
+}
+BEM_HD F2 f2_mulf(F2 a, float b) {
+  const float p = a.h * b;
+  const float e = fmaf(a.l, b, fmaf(a.h, b, -p));
+  return f2_fast_two_sum(p, e);
+}
+BEM_HD F2 f2_from(double d) {
+  const float h = (float)d;
+  return F2{h, (float)(d - (double)h)};
+}
+BEM_HD double f2_to(F2 a) { return (double)a.h + (double)a.l; }
+
+// +-1/k for the Neumann sums, as double-float constants folded at compile time
+struct MillerCoefF2 {
+  float h[BEM_MILLER_START / 2 + 1], l[BEM_MILLER_START / 2 + 1];
+};
+constexpr MillerCoefF2 make_miller_coef_f2() {
+  MillerCoefF2 c{};
+  for (int k = 1; k <= BEM_MILLER_START / 2; ++k) {
+    const double v = ((k & 1) ? -1.0 : 1.0) / (double)k;
+    const float h = (float)v;
+    c.h[k] = h;
+    c.l[k] = (float)(v - (double)h);
+  }
+  return c;
+}
+
+// Miller's algorithm exactly as bessel01_miller, with the recurrence and the three sums in double-float
+// arithmetic on the FP32 pipe (start value 2^-30, rescaled by 2^-40 whenever it grows past 2^40 so that it
+// stays inside the FP32 exponent range); the normalisation and the logarithmic terms are FP64.
+BEM_HD void bessel01_miller_f2(double x, Bessel01& b) {
+  constexpr MillerCoefF2 C = make_miller_coef_f2();
+  const double tox_d = 2.0 / x;
+  const F2 tox = f2_from(tox_d);
+  F2 fp{0.f, 0.f}, f{0x1p-30f, 0.f}, norm{0.f, 0.f}, sy0{0.f, 0.f}, sy1{0.f, 0.f}, fodd{0.f, 0.f};
+#pragma unroll
+  for (int n = BEM_MILLER_START; n >= 1; --n) {
+    if ((n & 1) == 0) {
+      const int kk = n >> 1;
+      norm = f2_add(norm, f);
+      sy0 = f2_add(sy0, f2_mul(f, F2{C.h[kk], C.l[kk]}));
+      fodd = fp;
+    } else {
+      const int kk = (n + 1) >> 1;
+      sy1 = f2_add(sy1, f2_mul(f2_add(f, f2_neg(fodd)), F2{C.h[kk], C.l[kk]}));
+    }
+    const F2 cn = f2_mulf(tox, (float)n);
+    const F2 fm = f2_add(f2_mul(cn, f), f2_neg(fp));
+    fp = f;
+    f = fm;
+    if ((n & 3) == 1 && fabsf(f.h) > 0x1p40f) {
+      const float sc = 0x1p-40f;
+      f = F2{f.h * sc, f.l * sc}; fp = F2{fp.h * sc, fp.l * sc};
+      norm = F2{norm.h * sc, norm.l * sc}; sy0 = F2{sy0.h * sc, sy0.l * sc};
+      sy1 = F2{sy1.h * sc, sy1.l * sc}; fodd = F2{fodd.h * sc, fodd.l * sc};
+    }
+  }
+  const double f0 = f2_to(f), f1 = f2_to(fp);
+  const double s = 1.0 / (f0 + 2.0 * f2_to(norm));
+  const double j0 = f0 * s, j1 = f1 * s;
+  const double lg = log(0.5 * x) + kEulerGamma;
+  b.j0 = j0;
+  b.j1 = j1;
+  b.y0 = kTwoOverPi * (lg * j0) - 2.0 * kTwoOverPi * f2_to(sy0) * s;
+  b.y1 = kTwoOverPi * (lg * j1 - 0.5 * tox_d * j0) + kTwoOverPi * f2_to(sy1) * s;
+}
+
 BEM_HD void bessel01_asymp(double x, Bessel01& b) {
   constexpr AsympCoef C = make_asymp_coef();
   const double y = 1.0 / x;
@@ -149,10 +243,63 @@ BEM_HD void bessel01_asymp(double x, Bessel01& b) {
   b.y1 = -hr;
 }
 
+// Same expansion, cheaper on the FP64 pipe: each of P0, Q0, P1, Q1 is a polynomial in u = 1/x^2
+// (Horner in u halves the multiply-adds), and 1/x comes from the reciprocal square root that the
+// amplitude sqrt(2/(pi x)) needs anyway (1/x = (pi/2) amp^2).
+struct AsympCoefU {
+  double p0[BEM_ASYMP_TERMS / 2], q0[BEM_ASYMP_TERMS / 2], p1[BEM_ASYMP_TERMS / 2], q1[BEM_ASYMP_TERMS / 2];
+};
+constexpr AsympCoefU make_asymp_coef_u() {
+  AsympCoef c = make_asymp_coef();
+  AsympCoefU u{};
+  for (int m = 0; m < BEM_ASYMP_TERMS / 2; ++m) {
+    u.p0[m] = c.p0[2 * m];
+    u.p1[m] = c.p1[2 * m];
+    u.q0[m] = c.q0[2 * m + 1];
+    u.q1[m] = c.q1[2 * m + 1];
+  }
+  return u;
+}
+
+BEM_HD void bessel01_asymp_u(double x, Bessel01& b) {
+  constexpr AsympCoefU C = make_asymp_coef_u();
+  constexpr int T = BEM_ASYMP_TERMS / 2;
+#if defined(__CUDA_ARCH__)
+  const double rs = rsqrt(x);
+#else
+  const double rs = 1.0 / sqrt(x);
+#endif
+  const double y = rs * rs;                    // 1/x
+  const double u = y * y;
+  double p0 = C.p0[T - 1], q0 = C.q0[T - 1], p1 = C.p1[T - 1], q1 = C.q1[T - 1];
+#pragma unroll
+  for (int m = T - 2; m >= 0; --m) {
+    p0 = fma(p0, u, C.p0[m]);
+    q0 = fma(q0, u, C.q0[m]);
+    p1 = fma(p1, u, C.p1[m]);
+    q1 = fma(q1, u, C.q1[m]);
+  }
+  q0 *= y;
+  q1 *= y;
+  double sn, cs;
+#if defined(__CUDA_ARCH__)
+  sincos(x, &sn, &cs);
+#else
+  sn = sin(x); cs = cos(x);
+#endif
+  const double amp = rs * 0.797884560802865355879892119868763737;   // sqrt(2/pi) / sqrt(x)
+  const double er = (cs + sn) * (amp * kInvSqrt2), ei = (sn - cs) * (amp * kInvSqrt2);
+  b.j0 = p0 * er - q0 * ei;
+  b.y0 = p0 * ei + q0 * er;
+  const double hr = p1 * er - q1 * ei, hi = p1 * ei + q1 * er;
+  b.j1 = hi;
+  b.y1 = -hr;
+}
+
 BEM_HD void bessel01(double x, Bessel01& b) {
   if (x < BEM_X_SERIES) bessel01_series(x, b);
-  else if (x < BEM_X_ASYMP) bessel01_miller(x, b);
-  else bessel01_asymp(x, b);
+  else if (x < BEM_X_ASYMP) bessel01_miller_f2(x, b);
+  else bessel01_asymp_u(x, b);
 }
 
 // integral_0^x J0(t) dt and integral_0^x Y0(t) dt for the weakly singular self-element integral,
