@@ -196,6 +196,7 @@ def main():
     ap.add_argument("--n-elem", type=int, default=4096, help="elements of the star (smaller cases for ncu)")
     ap.add_argument("--max-iter", type=int, default=400)
     ap.add_argument("--inner-tol", type=float, default=1e-5, help="inner GMRES tolerance of the mixed path")
+    ap.add_argument("--orth-passes", type=int, default=2, help="Gram-Schmidt passes of the mixed path (1 or 2)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -214,7 +215,8 @@ def main():
     stream = torch.cuda.current_stream()
 
     def make(prec):
-        p = P.Problem.from_workload(wp, prec=prec, tol=args.tol, max_iter=args.max_iter, inner_tol=args.inner_tol)
+        p = P.Problem.from_workload(wp, prec=prec, tol=args.tol, max_iter=args.max_iter, inner_tol=args.inner_tol,
+                                    orth_passes=args.orth_passes if prec != "fp64" else 2)
         n2 = p.bem_num_unknowns()
         x = torch.empty((N_RHS, n2), dtype=torch.complex128, device="cuda")
         ff = torch.empty((N_RHS, N_FF), dtype=torch.complex128, device="cuda")
@@ -325,7 +327,8 @@ def main():
         "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "c32 storage + f64 refinement", "data": "synthetic",
         "config": {"workload": wp.name, "n_elem": nel, "n_unknowns": n2, "n_rhs": N_RHS, "quad": 4,
-                   "prec": args.prec, "tol": args.tol, "inner_tol": args.inner_tol, "far_field_angles": N_FF,
+                   "prec": args.prec, "tol": args.tol, "inner_tol": args.inner_tol, "orth_passes": args.orth_passes,
+                   "far_field_angles": N_FF,
                    "l2": "inputs larger than L2 (A is 0.54 GB complex FP32 + 0.54 GB remainder)"},
         "latency_ms": {"p50": p50, "p99": p99, "unit": "ms per 64-solve batch"},
         "fp64": fp64,

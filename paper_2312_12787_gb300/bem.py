@@ -39,7 +39,7 @@ class BemError(RuntimeError):
 class bem_opts(ctypes.Structure):
     _fields_ = [("quad_order", ctypes.c_int), ("form", ctypes.c_int), ("prec", ctypes.c_int),
                 ("max_iter", ctypes.c_int), ("max_refine", ctypes.c_int), ("tol", ctypes.c_double),
-                ("inner_tol", ctypes.c_double)]
+                ("inner_tol", ctypes.c_double), ("orth_passes", ctypes.c_int)]
 
 
 _lib = None
@@ -120,7 +120,8 @@ def bem_default_opts() -> bem_opts:
     return o
 
 
-def make_opts(quad_order=4, form="mod", prec="fp64", max_iter=500, max_refine=6, tol=1e-10, inner_tol=1e-5):
+def make_opts(quad_order=4, form="mod", prec="fp64", max_iter=500, max_refine=6, tol=1e-10, inner_tol=1e-5,
+              orth_passes=2):
     o = bem_default_opts()
     o.quad_order = quad_order
     o.form = FORMS[form] if isinstance(form, str) else form
@@ -129,6 +130,7 @@ def make_opts(quad_order=4, form="mod", prec="fp64", max_iter=500, max_refine=6,
     o.max_refine = max_refine
     o.tol = tol
     o.inner_tol = inner_tol
+    o.orth_passes = orth_passes
     return o
 
 

@@ -71,7 +71,8 @@ void gauss_legendre(int Q, double* t, double* w) {
 bool valid_opts(const bem_opts* o) {
   return o && o->quad_order >= 1 && o->quad_order <= kMaxQuad && o->form >= 0 && o->form <= 3 && o->prec >= 0 &&
          o->prec <= 2 && o->max_iter >= 1 && o->max_iter <= 1000 && o->max_refine >= 1 && o->max_refine <= 100 &&
-         o->tol > 0 && std::isfinite(o->tol) && o->inner_tol > 0 && std::isfinite(o->inner_tol);
+         o->tol > 0 && std::isfinite(o->tol) && o->inner_tol > 0 && std::isfinite(o->inner_tol) &&
+         (o->orth_passes == 1 || o->orth_passes == 2);
 }
 
 }  // namespace
@@ -374,8 +375,8 @@ bem_status gmres_run(bem_problem* p, Solver& sv, const double2* r0, double2* x, 
     }
     }
     {
-      Phase ph(p, BEM_PH_ARNOLDI, s, 6);
-      CU(krylov_orthogonalise(st, 2, j, s));
+      Phase ph(p, BEM_PH_ARNOLDI, s, 3 * p->o.orth_passes);
+      CU(krylov_orthogonalise(st, p->o.orth_passes, j, s));
     }
     {
       Phase ph(p, BEM_PH_GIVENS, s, 3);
@@ -531,6 +532,7 @@ BEM_API void bem_default_opts(bem_opts* o) {
   o->max_refine = 6;
   o->tol = 1e-10;
   o->inner_tol = 1e-5;
+  o->orth_passes = 2;
 }
 
 BEM_API bem_status bem_problem_create(bem_problem** out, const bem_opts* opts) {

@@ -195,31 +195,39 @@ __global__ void __launch_bounds__(kThreads) k_update(KrylovState st, int nchunk,
 
 // h_{j+1,j} = ||w||; apply the previous Givens rotations to column j, form the new one, update g and
 // the residual estimate |g_{j+1}| / beta.  Rotation i acts on rows (i, i+1) as [[conj c, conj s], [-s, c]].
-// One warp per system: the lanes reduce the chunk norms, lane 0 runs the (sequential) rotations.
-__global__ void k_finish(KrylovState st, int nchunk, double tol, int j) {
-  const int s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+// One warp per system: the lanes reduce the chunk norms and stage the column and the rotations in shared
+// memory; lane 0 then runs the (sequential) rotations from shared memory.
+constexpr int kFinishMaxM = 1000;
+__global__ void __launch_bounds__(32) k_finish(KrylovState st, int nchunk, double tol, int j) {
+  __shared__ double2 sh_h[kFinishMaxM + 1], sh_c[kFinishMaxM], sh_s[kFinishMaxM];
+  const int s = blockIdx.x, lane = threadIdx.x;
   if (s >= st.nrhs || !st.active[s]) return;
   double t = 0.0;
   for (int c = lane; c < nchunk; c += 32) t += st.npart[(size_t)s * nchunk + c];
   t = warp_sum(t);
-  if (lane != 0) return;
-  const double hn = sqrt(t);
   double2* Hj = st.H + ((size_t)s * st.m + j) * (st.m + 1);
-  Hj[j + 1] = make_double2(hn, 0.0);
   double2* cs = st.cs + (size_t)s * st.m;
   double2* sn = st.sn + (size_t)s * st.m;
-  double2 a = Hj[0];
-  for (int i = 0; i < j; ++i) {
-    const double2 b = Hj[i + 1];
-    const double2 ci = cs[i], si = sn[i];
-    Hj[i] = cadd(cdotc(ci, a), cdotc(si, b));   // conj(c) a + conj(s) b
-    a = csub(cmul(ci, b), cmul(si, a));         // -s a + c b  (becomes row i+1)
+  for (int i = lane; i <= j; i += 32) {
+    sh_h[i] = Hj[i];
+    if (i < j) { sh_c[i] = cs[i]; sh_s[i] = sn[i]; }
   }
-  const double2 b = Hj[j + 1];
-  const double den = hypot(hypot(a.x, a.y), hypot(b.x, b.y));
+  __syncwarp();
+  if (lane != 0) return;
+  const double hn = sqrt(t);
+  double2 a = sh_h[0];
+  for (int i = 0; i < j; ++i) {
+    const double2 b = sh_h[i + 1];
+    const double2 ci = sh_c[i], si = sh_s[i];
+    sh_h[i] = cadd(cdotc(ci, a), cdotc(si, b));   // conj(c) a + conj(s) b
+    a = csub(cmul(ci, b), cmul(si, a));           // -s a + c b  (becomes row i+1)
+  }
+  const double2 b = make_double2(hn, 0.0);
+  const double den = hypot(hypot(a.x, a.y), hn);
   double2 c, sv;
   if (den == 0.0) { c = make_double2(1, 0); sv = make_double2(0, 0); }
   else { c = cscale(a, 1.0 / den); sv = cscale(b, 1.0 / den); }
+  for (int i = 0; i < j; ++i) Hj[i] = sh_h[i];
   cs[j] = c;
   sn[j] = sv;
   Hj[j] = make_double2(den, 0.0);
@@ -324,7 +332,7 @@ cudaError_t orth_t(const KrylovState& st, int passes, int j, cudaStream_t s) {
 template <typename T>
 cudaError_t finish_t(const KrylovState& st, double tol, int j, cudaStream_t s) {
   const int nc = nchunk_of(st.n);
-  k_finish<<<(st.nrhs + 7) / 8, 256, 0, s>>>(st, nc, tol, j);
+  k_finish<<<st.nrhs, 32, 0, s>>>(st, nc, tol, j);
   k_scale_next<T><<<dim3(nblk_of(st.n), st.nrhs), kThreads, 0, s>>>(st, j);
   k_advance<<<1, 32, 0, s>>>(st);
   return cudaGetLastError();
