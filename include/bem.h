@@ -179,6 +179,39 @@ BEM_API bem_status bem_solve_planewave_host(bem_problem* p, int n_rhs, const dou
                                             bem_c64* x_host, int n_ang, const double* ff_ang_host,
                                             bem_c64* ff_host, int* iters_host, double* resid_host, void* stream);
 
+/* ---- Batched solves of many independent problems (mixed precision only) -------------------------------
+ * A batch engine owns device pools for up to max_slots resident problems whose unknowns add up to at most
+ * pool_unknowns, each with its own matrix (allocated by the problem), Krylov basis (max_iter + 1 vectors),
+ * solution, residual and right-hand side.  Admitted problems iterate together: every kernel covers all
+ * resident problems (work lists over 64-entry chunks and 8-row blocks), the iteration body is replayed from a
+ * CUDA graph, and each problem is refined in FP64 (double-float residuals) when its inner GMRES stops.
+ * Problems can be admitted while others iterate (continuous batching); each result is the same as when the
+ * problem is solved alone.  Admitted problems must stay alive until their slot is taken.  The engine runs on
+ * its own stream, ordered after the caller's stream on entry and before it on exit. */
+typedef struct bem_batch bem_batch;
+BEM_API bem_status bem_batch_create(bem_batch** out, const bem_opts* opts, int max_slots, long long pool_unknowns);
+BEM_API void bem_batch_destroy(bem_batch* b);
+/* Admit n problems, each with one plane wave angles_host[i]: assemble all of them in one launch (tile height
+ * chosen by timing 4, 8 and 16 on the first call), form right-hand sides and start their solves.
+ * slots_host[i] = slot or -1 when no slot or contiguous pool space was free (BEM_ENOMEM, others admitted).
+ * Problems must be MIXED or MIXED_TC with the batch's quad_order and form. */
+BEM_API bem_status bem_batch_admit(bem_batch* b, int n, bem_problem* const* probs, const double* angles_host,
+                                   int* slots_host, void* stream);
+/* Run one graph replay of iterations for every iterating problem and refine the ones whose inner solve
+ * stopped; *n_running_host (may be NULL) = problems still iterating. */
+BEM_API bem_status bem_batch_step(bem_batch* b, int* n_running_host, void* stream);
+/* state: 0 free, 1 iterating, 2 finished (result waiting); iters = GMRES iterations so far; resid = last FP64
+ * relative residual. */
+BEM_API bem_status bem_batch_query(bem_batch* b, int slot, int* state_host, int* iters_host, double* resid_host);
+/* Copy a finished slot's solution (2N complex FP64, may be NULL to discard) and free the slot. */
+BEM_API bem_status bem_batch_take(bem_batch* b, int slot, bem_c64* x_dev, void* stream);
+/* Largest contiguous run of free unknowns in the pools (admission check). */
+BEM_API long long bem_batch_free_units(const bem_batch* b);
+/* Admit, iterate to completion and take n problems (they must all fit). */
+BEM_API bem_status bem_batch_solve_planewave(bem_batch* b, int n, bem_problem* const* probs, const double* angles_host,
+                                             bem_c64* const* x_dev, int* iters_host, double* resid_host,
+                                             void* stream);
+
 /* Per-phase device timing for measurement.  When enabled, every kernel launch of the problem is bracketed
  * by CUDA events recorded on the stream it runs on; bem_profile_read synchronises those events and returns,
  * per phase, the summed device milliseconds and the number of kernel launches since the last enable.

@@ -26,6 +26,8 @@ EXPORTS = [
     "bem_add_segment", "bem_num_elements", "bem_num_unknowns", "bem_footprint_bytes", "bem_assemble",
     "bem_get_matrix", "bem_rhs_planewave", "bem_matvec", "bem_residual", "bem_residual_noalloc", "bem_solve", "bem_solve_planewave", "bem_far_field",
     "bem_solve_planewave_host", "bem_profile_enable", "bem_profile_read", "bem_last_error", "bem_version",
+    "bem_batch_create", "bem_batch_destroy", "bem_batch_admit", "bem_batch_step", "bem_batch_query",
+    "bem_batch_take", "bem_batch_free_units", "bem_batch_solve_planewave",
 ]
 PHASES = ["geometry", "assemble", "rhs", "matvec", "arnoldi", "givens", "update", "residual", "farfield", "other"]
 
@@ -80,6 +82,20 @@ def load(path: str | None = None):
     L.bem_solve_planewave_host.argtypes = [vp, i, vp, vp, i, vp, vp, vp, vp, vp]
     L.bem_profile_enable.argtypes = [vp, i]
     L.bem_profile_read.argtypes = [vp, vp, vp]
+    ll = ctypes.c_longlong
+    L.bem_batch_create.argtypes = [P(vp), P(bem_opts), i, ll]
+    L.bem_batch_destroy.argtypes = [vp]
+    L.bem_batch_destroy.restype = None
+    L.bem_batch_admit.argtypes = [vp, i, vp, vp, vp, vp]
+    L.bem_batch_step.argtypes = [vp, vp, vp]
+    L.bem_batch_query.argtypes = [vp, i, vp, vp, vp]
+    L.bem_batch_take.argtypes = [vp, i, vp, vp]
+    L.bem_batch_free_units.argtypes = [vp]
+    L.bem_batch_free_units.restype = ll
+    L.bem_batch_solve_planewave.argtypes = [vp, i, vp, vp, vp, vp, vp, vp]
+    for name in ("bem_batch_create", "bem_batch_admit", "bem_batch_step", "bem_batch_query", "bem_batch_take",
+                 "bem_batch_solve_planewave"):
+        getattr(L, name).restype = i
     L.bem_last_error.restype = ctypes.c_char_p
     L.bem_version.restype = ctypes.c_char_p
     for name in ("bem_problem_create", "bem_set_opts", "bem_set_domains", "bem_add_segment", "bem_assemble",
@@ -263,6 +279,71 @@ class Problem:
             ff.ctypes.data_as(ctypes.c_void_p) if ff is not None else None, it.ctypes.data_as(ctypes.c_void_p),
             rs.ctypes.data_as(ctypes.c_void_p), _stream_ptr(stream)), allow_noconv=True)
         return st, x, ff, it, rs
+
+
+class Batch:
+    """Owns a bem_batch engine (batched mixed-precision solves of many problems; see include/bem.h)."""
+
+    def __init__(self, max_slots, pool_unknowns, opts: bem_opts | None = None, **kw):
+        L = load()
+        self._h = ctypes.c_void_p()
+        o = opts if opts is not None else make_opts(**({"prec": "mixed"} | kw))
+        _check(L.bem_batch_create(ctypes.byref(self._h), ctypes.byref(o), int(max_slots), int(pool_unknowns)))
+        self.opts = o
+
+    def close(self):
+        if self._h:
+            load().bem_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def bem_batch_admit(self, problems, angles, stream=None):
+        """Returns (status, slots); slots[i] = -1 for problems that did not fit."""
+        n = len(problems)
+        hs = (ctypes.c_void_p * n)(*[p._h.value for p in problems])
+        a, ptr = _hbuf(angles, np.float64)
+        slots = np.full(n, -1, np.int32)
+        st = load().bem_batch_admit(self._h, n, ctypes.cast(hs, ctypes.c_void_p), ptr,
+                                    slots.ctypes.data_as(ctypes.c_void_p), _stream_ptr(stream))
+        if st not in (BEM_OK, BEM_ENOMEM):
+            _check(st)
+        return st, slots
+
+    def bem_batch_step(self, stream=None):
+        r = ctypes.c_int(0)
+        _check(load().bem_batch_step(self._h, ctypes.byref(r), _stream_ptr(stream)))
+        return r.value
+
+    def bem_batch_query(self, slot):
+        st, it, rs = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_double(0)
+        _check(load().bem_batch_query(self._h, int(slot), ctypes.byref(st), ctypes.byref(it), ctypes.byref(rs)))
+        return st.value, it.value, rs.value
+
+    def bem_batch_take(self, slot, x=None, stream=None):
+        _check(load().bem_batch_take(self._h, int(slot), _dptr(x) if x is not None else None, _stream_ptr(stream)))
+        return x
+
+    def bem_batch_free_units(self):
+        return load().bem_batch_free_units(self._h)
+
+    def bem_batch_solve_planewave(self, problems, angles, xs, stream=None):
+        n = len(problems)
+        hs = (ctypes.c_void_p * n)(*[p._h.value for p in problems])
+        xp = (ctypes.c_void_p * n)(*[x.data_ptr() for x in xs])
+        a, ptr = _hbuf(angles, np.float64)
+        it = np.zeros(n, np.int32)
+        rs = np.zeros(n, np.float64)
+        st = _check(load().bem_batch_solve_planewave(self._h, n, ctypes.cast(hs, ctypes.c_void_p), ptr,
+                                                     ctypes.cast(xp, ctypes.c_void_p),
+                                                     it.ctypes.data_as(ctypes.c_void_p),
+                                                     rs.ctypes.data_as(ctypes.c_void_p), _stream_ptr(stream)),
+                    allow_noconv=True)
+        return st, it, rs
 
 
 def bem_version() -> str:

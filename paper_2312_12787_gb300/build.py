@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libbem.so")
 
-SOURCES = ["api.cu", "assemble.cu", "matvec.cu", "krylov.cu", "gemm_tc.cu", "noalloc.cu"]
+SOURCES = ["api.cu", "assemble.cu", "matvec.cu", "krylov.cu", "gemm_tc.cu", "batch.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr", "-I" + INCLUDE, "-I" + CSRC]

@@ -150,12 +150,7 @@ struct Phase {
   }
 };
 
-Quad make_quad(int Q) {
-  Quad q{};
-  q.Q = Q;
-  gauss_legendre(Q, q.t, q.w);
-  return q;
-}
+Quad make_quad(int Q) { return bem::make_quad_host(Q); }
 
 bem_status ensure_small(bem_problem* p, size_t doubles) {
   if (doubles <= p->small_cap) return BEM_OK;
@@ -509,6 +504,12 @@ bem_status rhs_impl(bem_problem* p, int nrhs, const double* angles_h, double2* b
 }  // namespace
 
 namespace bem {
+Quad make_quad_host(int Q) {
+  Quad q{};
+  q.Q = Q;
+  gauss_legendre(Q, q.t, q.w);
+  return q;
+}
 bool problem_mixed_matrix(bem_problem* p, const float2** hi, const float2** lo, int* n2) {
   if (!p || !p->mixed() || p->mat_dirty || p->A_mixed != 1 || !p->d_A || !p->d_Alo) return false;
   *hi = static_cast<const float2*>(p->d_A);
@@ -517,6 +518,39 @@ bool problem_mixed_matrix(bem_problem* p, const float2** hi, const float2** lo, 
   return true;
 }
 bem_status report_error(bem_status st, const char* msg) { return fail(st, "%s", msg); }
+ElemDev problem_elem(bem_problem* p) { return p->elem(); }
+DomTab problem_dom(bem_problem* p) { return p->dom; }
+bem_status problem_prepare_batched(bem_problem* p, cudaStream_t s, AsmJob* job, bem_opts* opts) {
+  if (!p) return fail(BEM_EINVAL, "null problem");
+  if (!p->mixed()) return fail(BEM_EINVAL, "batched solves need a mixed-precision problem");
+  bem_status st = check_ready(p);
+  if (st != BEM_OK) return st;
+  st = upload_geometry(p, s);
+  if (st != BEM_OK) return st;
+  const size_t nn = (size_t)2 * p->n * 2 * p->n;
+  const size_t need = nn * sizeof(float2);
+  if (need > p->A_cap || p->A_mixed != 1) {
+    if (p->d_A) cudaFree(p->d_A);
+    if (p->d_Alo) cudaFree(p->d_Alo);
+    p->d_A = p->d_Alo = nullptr;
+    p->A_cap = 0;
+    if (cudaMalloc(&p->d_A, need) != cudaSuccess || cudaMalloc(&p->d_Alo, need) != cudaSuccess) {
+      if (p->d_A) cudaFree(p->d_A);
+      p->d_A = nullptr;
+      return fail(BEM_ENOMEM, "matrix allocation of 2 x %zu bytes failed", need);
+    }
+    p->A_cap = need;
+  }
+  job->e = p->elem();
+  job->n = p->n;
+  job->dom = p->dom;
+  job->A = p->d_A;
+  job->Alo = p->d_Alo;
+  p->A_mixed = 1;
+  p->mat_dirty = false;
+  *opts = p->o;
+  return BEM_OK;
+}
 }  // namespace bem
 
 // ================================== C interface ==================================================

@@ -63,12 +63,10 @@ __global__ void k_elements(ElemDev e, int n) {
 //   S = (i/4) sS,  D = (ik/4) sD,  D* = -(ik/4) sDs,  N = (ik/4) sN.
 struct PairSums { double2 sS, sD, sDs, sN; };
 
-template <int MIXED>
-__global__ void __launch_bounds__(256) k_assemble(ElemDev e, int n, DomTab dom, Quad q, int form, void* Aout,
-                                                   void* Aloout, size_t lda) {
-  const int j = blockIdx.x * 32 + threadIdx.x;
-  const int i = blockIdx.y * 8 + threadIdx.y;
-  if (i >= n || j >= n) return;
+// All four entries of element pair (i, j): out[half][0] multiplies u_j, out[half][1] multiplies w_j in
+// row half*N + i.
+__device__ __forceinline__ void assemble_pair(const ElemDev& e, const DomTab& dom, const Quad& q, int form, int i,
+                                              int j, double2 (&out)[2][2]) {
   const double xi = e.mx[i], yi = e.my[i];
   const double nxi = -e.ty[i], nyi = e.tx[i];
   const int Pi = e.P[i], Mi = e.M[i];
@@ -88,7 +86,6 @@ __global__ void __launch_bounds__(256) k_assemble(ElemDev e, int n, DomTab dom, 
     gim[half] = -1.0 / (k1 * eps[half]);        // gamma = alpha/eps_d = i * gim
   }
 
-  double2 out[2][2];
   if (i == j) {
 #pragma unroll
     for (int half = 0; half < 2; ++half) {
@@ -170,6 +167,11 @@ __global__ void __launch_bounds__(256) k_assemble(ElemDev e, int n, DomTab dom, 
       out[half][1] = cmul(eq[half].scale, cw);
     }
   }
+}
+
+template <int MIXED>
+__device__ __forceinline__ void store_pair(int n, int i, int j, const double2 (&out)[2][2], void* Aout, void* Aloout,
+                                           size_t lda) {
   const size_t r0 = (size_t)i * lda, r1 = (size_t)(n + i) * lda;
   if (MIXED) {
     float2* A = static_cast<float2*>(Aout);
@@ -189,6 +191,41 @@ __global__ void __launch_bounds__(256) k_assemble(ElemDev e, int n, DomTab dom, 
     A[r1 + j] = out[1][0];
     A[r1 + n + j] = out[1][1];
   }
+}
+
+template <int MIXED>
+__global__ void __launch_bounds__(256) k_assemble(ElemDev e, int n, DomTab dom, Quad q, int form, void* Aout,
+                                                   void* Aloout, size_t lda) {
+  const int j = blockIdx.x * 32 + threadIdx.x;
+  const int i = blockIdx.y * 8 + threadIdx.y;
+  if (i >= n || j >= n) return;
+  double2 out[2][2];
+  assemble_pair(e, dom, q, form, i, j, out);
+  store_pair<MIXED>(n, i, j, out, Aout, Aloout, lda);
+}
+
+// Many problems in one launch: blockIdx.x walks a list of 32 x TY tiles of all problems (problem found by
+// binary search in the tile prefix sums); each problem keeps its own elements, domain table and matrices.
+template <int MIXED, int TY>
+__global__ void __launch_bounds__(32 * TY) k_assemble_batched(const AsmJob* __restrict__ jobs, int njobs,
+                                                              const long long* __restrict__ tile_prefix, Quad q,
+                                                              int form) {
+  const long long t = blockIdx.x;
+  int lo = 0, hi = njobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (tile_prefix[mid] <= t) lo = mid; else hi = mid - 1;
+  }
+  const AsmJob& jb = jobs[lo];
+  const long long local = t - tile_prefix[lo];
+  const int tiles_x = (jb.n + 31) / 32;
+  const int tx = (int)(local % tiles_x), ty = (int)(local / tiles_x);
+  const int j = tx * 32 + threadIdx.x;
+  const int i = ty * TY + threadIdx.y;
+  if (i >= jb.n || j >= jb.n) return;
+  double2 out[2][2];
+  assemble_pair(jb.e, jb.dom, q, form, i, j, out);
+  store_pair<MIXED>(jb.n, i, j, out, jb.A, jb.Alo, (size_t)2 * jb.n);
 }
 
 // b[r][half*N + i] for plane wave r (eq. naive_bie right-hand side, placed like the matrix rows).
@@ -291,6 +328,29 @@ cudaError_t launch_assemble(const ElemDev& e, int n, const DomTab& dom, const Qu
   dim3 grd((n + 31) / 32, (n + 7) / 8);
   if (store_mixed) k_assemble<1><<<grd, blk, 0, s>>>(e, n, dom, q, form, A, Alo, lda);
   else k_assemble<0><<<grd, blk, 0, s>>>(e, n, dom, q, form, A, Alo, lda);
+  return cudaGetLastError();
+}
+
+long long assemble_batched_tiles(int n, int ty) { return (long long)((n + 31) / 32) * ((n + ty - 1) / ty); }
+
+cudaError_t launch_assemble_batched(const AsmJob* jobs_dev, int njobs, const long long* tile_prefix_dev,
+                                   long long total_tiles, const Quad& q, int form, int store_mixed, int ty,
+                                   cudaStream_t s) {
+  if (total_tiles <= 0) return cudaSuccess;
+  if (total_tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
+  const unsigned grid = (unsigned)total_tiles;
+#define BEM_ASM_CASE(TYV)                                                                                  \
+  case TYV:                                                                                                \
+    if (store_mixed) k_assemble_batched<1, TYV><<<grid, dim3(32, TYV), 0, s>>>(jobs_dev, njobs, tile_prefix_dev, q, form); \
+    else k_assemble_batched<0, TYV><<<grid, dim3(32, TYV), 0, s>>>(jobs_dev, njobs, tile_prefix_dev, q, form); \
+    break;
+  switch (ty) {
+    BEM_ASM_CASE(4)
+    BEM_ASM_CASE(8)
+    BEM_ASM_CASE(16)
+    default: return cudaErrorInvalidValue;
+  }
+#undef BEM_ASM_CASE
   return cudaGetLastError();
 }
 

@@ -35,6 +35,15 @@ struct Quad {
   double w[kMaxQuad];
 };
 
+// One problem of a batched assembly launch.
+struct AsmJob {
+  ElemDev e;
+  int n;           // elements
+  DomTab dom;
+  void* A;         // hi (mixed) or full (FP64) matrix, 2n x 2n row-major
+  void* Alo;       // remainder (mixed) or null
+};
+
 // ---- complex helpers ---------------------------------------------------------------------------
 __host__ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
   return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
@@ -51,6 +60,11 @@ __host__ __device__ __forceinline__ double2 cdotc(double2 a, double2 b) {
 cudaError_t launch_elements(const ElemDev& e, int n, cudaStream_t s);
 cudaError_t launch_assemble(const ElemDev& e, int n, const DomTab& dom, const Quad& q, int form, int store_mixed,
                             void* A, void* Alo, size_t lda, cudaStream_t s);
+// Tiles of a problem with n elements for tile height ty (4, 8 or 16 rows of element pairs x 32 columns).
+long long assemble_batched_tiles(int n, int ty);
+cudaError_t launch_assemble_batched(const AsmJob* jobs_dev, int njobs, const long long* tile_prefix_dev,
+                                   long long total_tiles, const Quad& q, int form, int store_mixed, int ty,
+                                   cudaStream_t s);
 cudaError_t launch_rhs_planewave(const ElemDev& e, int n, const DomTab& dom, int form, int nrhs,
                                  const double* angles_dev, double2* b, cudaStream_t s);
 cudaError_t launch_far_field(const ElemDev& e, int n, const DomTab& dom, const Quad& q, int nrhs, const double2* x,
@@ -117,6 +131,16 @@ cudaError_t krylov_start(const KrylovState& st, const double2* r0, double tol_un
 cudaError_t krylov_orthogonalise(const KrylovState& st, int passes, int j, cudaStream_t s);
 cudaError_t krylov_finish_step(const KrylovState& st, double tol, int j, cudaStream_t s);
 cudaError_t krylov_update_solution(const KrylovState& st, double2* x, cudaStream_t s);
+
+// For the batch engine: validate, upload geometry and allocate the mixed-precision matrix of p (without
+// assembling it), fill its batched-assembly job and mark the matrix as current.  Also reports the
+// problem's options.
+bem_status problem_prepare_batched(bem_problem* p, cudaStream_t s, AsmJob* job, bem_opts* opts);
+// Q-point Gauss-Legendre rule on [-1, 1] (Newton's method on P_Q).
+Quad make_quad_host(int Q);
+// Element view and domain table of a problem whose geometry is on the device.
+ElemDev problem_elem(bem_problem* p);
+DomTab problem_dom(bem_problem* p);
 
 // Read-only view of a problem's assembled mixed-precision matrix (for entry points defined outside
 // api.cu).  Returns false if the problem has no current mixed-precision matrix.
