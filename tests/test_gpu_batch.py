@@ -101,6 +101,7 @@ def test_batch_admission_by_pool_footprint(B, torch):
     while bt.bem_batch_step():
         pass
     bt.bem_batch_take(int(slots[0]))
+    bt.bem_batch_take(int(slots[1]))
     assert bt.bem_batch_free_units() >= n2[2]
     st, s2 = bt.bem_batch_admit([probs[2]], [0.0])
     assert st == B.BEM_OK and s2[0] >= 0
