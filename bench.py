@@ -181,6 +181,52 @@ def run_reference(args):
 # GPU legs
 # ------------------------------------------------------------------------------------------------
 
+def run_batched_workload(args):
+    """Secondary measurements (not the headline line): the serving stream and the random-star sweep."""
+    import torch
+    import paper_2312_12787_gb300 as P
+    from paper_2312_12787_gb300 import build as Bd, serve
+    Bd.build()
+    P.load()
+    torch.cuda.set_device(0)
+    if args.workload == "sweep":
+        stars = W.cfg_random_stars_c4()
+        res = {}
+        for leg in ("warmup", "timed"):
+            probs = [P.Problem.from_workload(wp, prec="mixed", tol=args.tol, max_iter=args.max_iter) for wp in stars]
+            xs = [torch.empty(p.bem_num_unknowns(), dtype=torch.complex128, device="cuda") for p in probs]
+            bt = P.Batch(256, sum(p.bem_num_unknowns() for p in probs), tol=args.tol, max_iter=args.max_iter)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st, it, rs = bt.bem_batch_solve_planewave(probs, np.zeros(len(stars)), xs)
+            torch.cuda.synchronize()
+            res[leg] = (time.perf_counter() - t0, it, rs)
+            bt.close()
+            for p in probs:
+                p.close()
+        t, it, rs = res["timed"]
+        line = {"metric": "random-star sweep solves/s (one batch, mixed)", "value": len(stars) / t,
+                "unit": "solves/s", "wall_s": t, "n_problems": len(stars), "iters_mean": float(np.mean(it)),
+                "max_rel_resid": float(np.max(rs)), "tol": args.tol,
+                "config": {"workload": "256 random stars, N_e U[128,2048], k_e U[1,40]"}}
+        print(json.dumps(line), flush=True)
+        return
+    stream = W.cfg_serving_c5(count=args.requests)
+    requests = [(t, wp, 0.0) for t, wp in stream]
+    srv = serve.Server(max_slots=256, pool_unknowns=1 << 22, hbm_budget_bytes=96 << 30, tol=args.tol,
+                       max_iter=args.max_iter)
+    srv.run(requests[:8], time_limit_s=600)                # warm-up (kernel loading, autotuning)
+    st = srv.run(requests, time_limit_s=1200)
+    srv.close()
+    nf = min(len(requests), 40)
+    st64 = serve.serve_fp64_sequential(requests[:nf], tol=args.tol, time_limit_s=1200)
+    line = {"metric": "serving solves/s and latency (continuous batching, mixed) vs FP64 sequential",
+            "mixed": st.summary(), "fp64_sequential_first_%d" % nf: st64.summary(), "tol": args.tol,
+            "config": {"workload": f"Poisson stream, {len(requests)} requests at 200/s: circles, ellipses, "
+                                   "junction disks, N_e log-uniform [256, 16384], k_e U[1, 50]"}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -197,9 +243,15 @@ def main():
     ap.add_argument("--max-iter", type=int, default=400)
     ap.add_argument("--inner-tol", type=float, default=1e-5, help="inner GMRES tolerance of the mixed path")
     ap.add_argument("--orth-passes", type=int, default=2, help="Gram-Schmidt passes of the mixed path (1 or 2)")
+    ap.add_argument("--workload", default="star", choices=["star", "serving", "sweep"],
+                    help="star: the 64-RHS star (default line); serving: Poisson request stream; "
+                         "sweep: 256 random stars in one batch")
+    ap.add_argument("--requests", type=int, default=200, help="serving: number of requests")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload != "star":
+        return run_batched_workload(args)
 
     import torch
     ws, rank, local = dist_setup(args)
