@@ -242,7 +242,7 @@ def main():
     ap.add_argument("--n-elem", type=int, default=4096, help="elements of the star (smaller cases for ncu)")
     ap.add_argument("--max-iter", type=int, default=400)
     ap.add_argument("--inner-tol", type=float, default=1e-5, help="inner GMRES tolerance of the mixed path")
-    ap.add_argument("--orth-passes", type=int, default=2, help="Gram-Schmidt passes of the mixed path (1 or 2)")
+    ap.add_argument("--orth-passes", type=int, default=0, help="Gram-Schmidt passes of the mixed path (0 = auto)")
     ap.add_argument("--workload", default="star", choices=["star", "serving", "sweep"],
                     help="star: the 64-RHS star (default line); serving: Poisson request stream; "
                          "sweep: 256 random stars in one batch")
@@ -268,7 +268,7 @@ def main():
 
     def make(prec):
         p = P.Problem.from_workload(wp, prec=prec, tol=args.tol, max_iter=args.max_iter, inner_tol=args.inner_tol,
-                                    orth_passes=args.orth_passes if prec != "fp64" else 2)
+                                    orth_passes=args.orth_passes if prec != "fp64" else 0)
         n2 = p.bem_num_unknowns()
         x = torch.empty((N_RHS, n2), dtype=torch.complex128, device="cuda")
         ff = torch.empty((N_RHS, N_FF), dtype=torch.complex128, device="cuda")

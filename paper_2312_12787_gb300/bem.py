@@ -137,7 +137,7 @@ def bem_default_opts() -> bem_opts:
 
 
 def make_opts(quad_order=4, form="mod", prec="fp64", max_iter=500, max_refine=6, tol=1e-10, inner_tol=1e-5,
-              orth_passes=2):
+              orth_passes=0):
     o = bem_default_opts()
     o.quad_order = quad_order
     o.form = FORMS[form] if isinstance(form, str) else form

@@ -72,7 +72,7 @@ bool valid_opts(const bem_opts* o) {
   return o && o->quad_order >= 1 && o->quad_order <= kMaxQuad && o->form >= 0 && o->form <= 3 && o->prec >= 0 &&
          o->prec <= 2 && o->max_iter >= 1 && o->max_iter <= 1000 && o->max_refine >= 1 && o->max_refine <= 100 &&
          o->tol > 0 && std::isfinite(o->tol) && o->inner_tol > 0 && std::isfinite(o->inner_tol) &&
-         (o->orth_passes == 1 || o->orth_passes == 2);
+         (o->orth_passes >= 0 && o->orth_passes <= 2);
 }
 
 }  // namespace
@@ -370,8 +370,10 @@ bem_status gmres_run(bem_problem* p, Solver& sv, const double2* r0, double2* x, 
     }
     }
     {
-      Phase ph(p, BEM_PH_ARNOLDI, s, 3 * p->o.orth_passes);
-      CU(krylov_orthogonalise(st, p->o.orth_passes, j, s));
+      // automatic: re-orthogonalise the FP64 basis; the FP32 inner solves (loose tolerance) use one pass
+      const int passes = p->o.orth_passes ? p->o.orth_passes : (fp32 ? 1 : 2);
+      Phase ph(p, BEM_PH_ARNOLDI, s, 3 * passes);
+      CU(krylov_orthogonalise(st, passes, j, s));
     }
     {
       Phase ph(p, BEM_PH_GIVENS, s, 3);
@@ -566,7 +568,7 @@ BEM_API void bem_default_opts(bem_opts* o) {
   o->max_refine = 6;
   o->tol = 1e-10;
   o->inner_tol = 1e-5;
-  o->orth_passes = 2;
+  o->orth_passes = 0;
 }
 
 BEM_API bem_status bem_problem_create(bem_problem** out, const bem_opts* opts) {

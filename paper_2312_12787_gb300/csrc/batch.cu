@@ -587,7 +587,7 @@ bem_status run_iterations(bem_batch* b) {
   if (!e.gexec) {
     cudaGraph_t graph;
     BCU(cudaStreamBeginCapture(e.st, cudaStreamCaptureModeThreadLocal));
-    for (int it = 0; it < e.graph_iters; ++it) enqueue_iteration(e, d, e.o.orth_passes);
+    for (int it = 0; it < e.graph_iters; ++it) enqueue_iteration(e, d, e.o.orth_passes ? e.o.orth_passes : 1);
     BCU(cudaStreamEndCapture(e.st, &graph));
     cudaError_t ce = cudaGraphInstantiate(&e.gexec, graph, 0);
     cudaGraphDestroy(graph);

@@ -154,12 +154,16 @@ __global__ void k_dots_reduce(KrylovState st, int nchunk, int pass, int j) {
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_update(KrylovState st, int nchunk, int j) {
   using F = typename Vec<T>::acc_t;
-  __shared__ double2 hs[1024];
+  __shared__ F hs[2 * 1024];                    // projections in the basis precision, converted once
   __shared__ F accs[4][kCh][2];
   __shared__ double red[8];
   const int c = blockIdx.x, s = blockIdx.y;
   if (!st.active[s]) return;
-  for (int i = threadIdx.x; i <= j; i += kThreads) hs[i] = st.hcol[(size_t)s * (st.m + 1) + i];
+  for (int i = threadIdx.x; i <= j; i += kThreads) {
+    const double2 h = st.hcol[(size_t)s * (st.m + 1) + i];
+    hs[2 * i] = (F)h.x;
+    hs[2 * i + 1] = (F)h.y;
+  }
   __syncthreads();
   const int e = threadIdx.x & (kCh - 1), sub = threadIdx.x >> 6;
   const int k = c * kCh + e;
@@ -170,7 +174,7 @@ __global__ void __launch_bounds__(kThreads) k_update(KrylovState st, int nchunk,
 #pragma unroll 4
     for (int i = sub; i <= j; i += 4) {
       const T v = V[(size_t)i * stride + k];
-      const F hx = (F)hs[i].x, hy = (F)hs[i].y;
+      const F hx = hs[2 * i], hy = hs[2 * i + 1];
       ax += hx * (F)v.x - hy * (F)v.y;
       ay += hx * (F)v.y + hy * (F)v.x;
     }
@@ -182,10 +186,8 @@ __global__ void __launch_bounds__(kThreads) k_update(KrylovState st, int nchunk,
   if (sub == 0 && k < st.n) {
     T* W = static_cast<T*>(st.W) + (size_t)s * st.n;
     T w = W[k];
-    const F tx = accs[0][e][0] + accs[1][e][0] + accs[2][e][0] + accs[3][e][0];
-    const F ty = accs[0][e][1] + accs[1][e][1] + accs[2][e][1] + accs[3][e][1];
-    w.x = w.x - tx;
-    w.y = w.y - ty;
+    w.x = w.x - (accs[0][e][0] + accs[1][e][0] + accs[2][e][0] + accs[3][e][0]);
+    w.y = w.y - (accs[0][e][1] + accs[1][e][1] + accs[2][e][1] + accs[3][e][1]);
     W[k] = w;
     nrm = (double)w.x * (double)w.x + (double)w.y * (double)w.y;
   }
@@ -246,11 +248,16 @@ __global__ void __launch_bounds__(32) k_finish(KrylovState st, int nchunk, doubl
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_scale_next(KrylovState st, int j) {
+  using F = typename Vec<T>::acc_t;
   const int k = blockIdx.x * kThreads + threadIdx.x, s = blockIdx.y;
   if (!st.active[s] || k >= st.n) return;
   const T* W = static_cast<const T*>(st.W) + (size_t)s * st.n;
   T* Vn = static_cast<T*>(st.V) + ((size_t)(j + 1) * st.nrhs + s) * st.n;
-  Vec<T>::store(Vn + k, cscale(Vec<T>::load(W + k), 1.0 / st.hnext[s]));
+  const F inv = (F)(1.0 / st.hnext[s]);
+  T w = W[k];
+  w.x *= inv;
+  w.y *= inv;
+  Vn[k] = w;
 }
 
 __global__ void k_advance(KrylovState st) {

@@ -43,7 +43,7 @@ def test_version_and_defaults(lib):
     assert "sm_103a" in lib.bem_version()
     o = lib.bem.bem_default_opts()
     assert o.quad_order == 4 and o.form == lib.BEM_FORM_MOD and o.prec == lib.BEM_PREC_FP64
-    assert o.tol == 1e-10 and o.max_iter == 500 and o.orth_passes == 2
+    assert o.tol == 1e-10 and o.max_iter == 500 and o.orth_passes == 0
 
 
 def test_host_validation(lib):
