@@ -84,12 +84,14 @@ typedef struct {
   double inner_tol;   /* relative tolerance of each inner GMRES run (MIXED / MIXED_TC), > 0 */
   int orth_passes;    /* classical Gram-Schmidt passes per Arnoldi step: 1, 2 (re-orthogonalised), or 0 =
                          automatic (2 for the FP64 basis, 1 for the FP32 inner solves of the mixed paths) */
+  int matrix_free;    /* 1: never store A; every product recomputes the entries in FP64 (FP64 path only).
+                         For matrices that do not fit in device memory; each product costs one assembly. */
 } bem_opts;
 
 typedef struct bem_problem bem_problem;
 
 /* Fill *o with the defaults: quad_order 4, MOD, FP64, max_iter 500, max_refine 6, tol 1e-10,
- * inner_tol 1e-5, orth_passes 0 (automatic). */
+ * inner_tol 1e-5, orth_passes 0 (automatic), matrix_free 0. */
 BEM_API void bem_default_opts(bem_opts* o);
 
 /* Create an empty problem.  *out receives a library-owned handle (free with bem_problem_destroy).

@@ -72,7 +72,8 @@ bool valid_opts(const bem_opts* o) {
   return o && o->quad_order >= 1 && o->quad_order <= kMaxQuad && o->form >= 0 && o->form <= 3 && o->prec >= 0 &&
          o->prec <= 2 && o->max_iter >= 1 && o->max_iter <= 1000 && o->max_refine >= 1 && o->max_refine <= 100 &&
          o->tol > 0 && std::isfinite(o->tol) && o->inner_tol > 0 && std::isfinite(o->inner_tol) &&
-         (o->orth_passes >= 0 && o->orth_passes <= 2);
+         (o->orth_passes >= 0 && o->orth_passes <= 2) && (o->matrix_free == 0 || o->matrix_free == 1) &&
+         !(o->matrix_free && o->prec != BEM_PREC_FP64);
 }
 
 }  // namespace
@@ -219,6 +220,10 @@ bem_status assemble_impl(bem_problem* p, cudaStream_t s, bool force = false) {
   st = upload_geometry(p, s);
   if (st != BEM_OK) return st;
   const bool mixed = p->mixed();
+  if (p->o.matrix_free) {      // nothing to store: products recompute the entries
+    p->mat_dirty = false;
+    return BEM_OK;
+  }
   if (!force && !p->mat_dirty && p->A_mixed == (int)mixed) return BEM_OK;
   const size_t nn = (size_t)2 * p->n * 2 * p->n;
   const size_t need = mixed ? nn * sizeof(float2) : nn * sizeof(double2);
@@ -358,7 +363,10 @@ bem_status gmres_run(bem_problem* p, Solver& sv, const double2* r0, double2* x, 
     void* Vj = static_cast<char*>(st.V) + (size_t)j * nrhs * n2 * tb;
     {
     Phase ph(p, BEM_PH_MATVEC, s, 1);
-    if (!fp32) {
+    if (p->o.matrix_free) {
+      CU(launch_matvec_free(p->elem(), p->n, p->dom, make_quad(p->o.quad_order), p->o.form, nrhs,
+                            static_cast<const double2*>(Vj), static_cast<double2*>(st.W), s));
+    } else if (!fp32) {
       CU(launch_matvec_c64(static_cast<const double2*>(p->d_A), n2, n2, nrhs, static_cast<const double2*>(Vj),
                            static_cast<double2*>(st.W), s));
     } else if (p->o.prec == BEM_PREC_MIXED_TC && nrhs > 1 && matvec_tc_supported(n2, nrhs)) {
@@ -569,6 +577,7 @@ BEM_API void bem_default_opts(bem_opts* o) {
   o->tol = 1e-10;
   o->inner_tol = 1e-5;
   o->orth_passes = 0;
+  o->matrix_free = 0;
 }
 
 BEM_API bem_status bem_problem_create(bem_problem** out, const bem_opts* opts) {
@@ -660,7 +669,7 @@ BEM_API int bem_num_unknowns(const bem_problem* p) { return p ? 2 * p->n : 0; }
 BEM_API size_t bem_footprint_bytes(const bem_problem* p, int n_rhs) {
   if (!p || n_rhs < 1) return 0;
   const bool mixed = p->o.prec != BEM_PREC_FP64;
-  return matrix_bytes(p->n, mixed) + krylov_bytes(2 * p->n, n_rhs, p->o.max_iter, mixed) + (size_t)11 * p->n * 8;
+  return (p->o.matrix_free ? 0 : matrix_bytes(p->n, mixed)) + krylov_bytes(2 * p->n, n_rhs, p->o.max_iter, mixed) + (size_t)11 * p->n * 8;
 }
 
 BEM_API bem_status bem_assemble(bem_problem* p, void* stream) {
@@ -670,6 +679,7 @@ BEM_API bem_status bem_assemble(bem_problem* p, void* stream) {
 BEM_API bem_status bem_get_matrix(bem_problem* p, int which, bem_c64* A_dev, void* stream) {
   if (!p || !A_dev) return fail(BEM_EINVAL, "null argument");
   if (which != 0 && which != 1) return fail(BEM_EINVAL, "which must be 0 or 1");
+  if (p->o.matrix_free) return fail(BEM_ESTATE, "matrix-free problems store no matrix");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   bem_status st = assemble_impl(p, s);
   if (st != BEM_OK) return st;
@@ -692,6 +702,11 @@ BEM_API bem_status bem_matvec(bem_problem* p, int n_rhs, const bem_c64* x_dev, b
   const int n2 = 2 * p->n;
   const double2* x = reinterpret_cast<const double2*>(x_dev);
   double2* y = reinterpret_cast<double2*>(y_dev);
+  if (p->o.matrix_free) {
+    Phase ph(p, BEM_PH_MATVEC, s, n_rhs);
+    CU(launch_matvec_free(p->elem(), p->n, p->dom, make_quad(p->o.quad_order), p->o.form, n_rhs, x, y, s));
+    return BEM_OK;
+  }
   if (!p->mixed()) {
     Phase ph(p, BEM_PH_MATVEC, s, 1);
     CU(launch_matvec_c64(static_cast<const double2*>(p->d_A), n2, n2, n_rhs, x, y, s));
@@ -734,6 +749,12 @@ BEM_API bem_status bem_residual(bem_problem* p, int n_rhs, const bem_c64* x_dev,
   const double2* b = reinterpret_cast<const double2*>(b_dev);
   double2* r = reinterpret_cast<double2*>(r_dev);
   Phase ph(p, BEM_PH_RESIDUAL, s, p->mixed() ? 2 : 1);
+  if (p->o.matrix_free) {
+    // r = b - A x with recomputed entries: product into r, then r = b - r
+    CU(launch_matvec_free(p->elem(), p->n, p->dom, make_quad(p->o.quad_order), p->o.form, n_rhs, x, r, s));
+    CU(launch_axpby_neg(b, r, (size_t)n_rhs * n2, s));
+    return BEM_OK;
+  }
   if (!p->mixed()) {
     CU(launch_residual_c64(static_cast<const double2*>(p->d_A), n2, n2, n_rhs, x, b, r, s));
     return BEM_OK;

@@ -204,6 +204,35 @@ __global__ void __launch_bounds__(256) k_assemble(ElemDev e, int n, DomTab dom, 
   store_pair<MIXED>(n, i, j, out, Aout, Aloout, lda);
 }
 
+// Matrix-free product y = A x (no stored matrix): each block owns 8 element rows (16 matrix rows i and
+// N + i); the 32 lanes of a warp stride over the element columns j, evaluate the four entries of (i, j) with
+// the assembly's own code and accumulate; a warp reduction gives the two row sums.  FP64 throughout.
+__global__ void __launch_bounds__(256) k_matvec_free(ElemDev e, int n, DomTab dom, Quad q, int form,
+                                                      const double2* __restrict__ x, double2* __restrict__ y) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i = blockIdx.x * 8 + warp;
+  if (i >= n) return;
+  double2 up = make_double2(0, 0), lo = make_double2(0, 0);
+  for (int j = lane; j < n; j += 32) {
+    double2 out[2][2];
+    assemble_pair(e, dom, q, form, i, j, out);
+    const double2 xu = x[j], xw = x[n + j];
+    up = cadd(up, cadd(cmul(out[0][0], xu), cmul(out[0][1], xw)));
+    lo = cadd(lo, cadd(cmul(out[1][0], xu), cmul(out[1][1], xw)));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    up.x += __shfl_xor_sync(0xffffffffu, up.x, o);
+    up.y += __shfl_xor_sync(0xffffffffu, up.y, o);
+    lo.x += __shfl_xor_sync(0xffffffffu, lo.x, o);
+    lo.y += __shfl_xor_sync(0xffffffffu, lo.y, o);
+  }
+  if (lane == 0) {
+    y[i] = up;
+    y[n + i] = lo;
+  }
+}
+
 // Many problems in one launch: blockIdx.x walks a list of 32 x TY tiles of all problems (problem found by
 // binary search in the tile prefix sums); each problem keeps its own elements, domain table and matrices.
 template <int MIXED, int TY>
@@ -328,6 +357,13 @@ cudaError_t launch_assemble(const ElemDev& e, int n, const DomTab& dom, const Qu
   dim3 grd((n + 31) / 32, (n + 7) / 8);
   if (store_mixed) k_assemble<1><<<grd, blk, 0, s>>>(e, n, dom, q, form, A, Alo, lda);
   else k_assemble<0><<<grd, blk, 0, s>>>(e, n, dom, q, form, A, Alo, lda);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_matvec_free(const ElemDev& e, int n, const DomTab& dom, const Quad& q, int form, int nrhs,
+                               const double2* x, double2* y, cudaStream_t s) {
+  for (int r = 0; r < nrhs; ++r)
+    k_matvec_free<<<(n + 7) / 8, 256, 0, s>>>(e, n, dom, q, form, x + (size_t)r * 2 * n, y + (size_t)r * 2 * n);
   return cudaGetLastError();
 }
 

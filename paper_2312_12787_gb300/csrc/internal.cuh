@@ -60,6 +60,9 @@ __host__ __device__ __forceinline__ double2 cdotc(double2 a, double2 b) {
 cudaError_t launch_elements(const ElemDev& e, int n, cudaStream_t s);
 cudaError_t launch_assemble(const ElemDev& e, int n, const DomTab& dom, const Quad& q, int form, int store_mixed,
                             void* A, void* Alo, size_t lda, cudaStream_t s);
+// y = A x without a stored matrix (entries recomputed in FP64), n elements, nrhs columns of 2n.
+cudaError_t launch_matvec_free(const ElemDev& e, int n, const DomTab& dom, const Quad& q, int form, int nrhs,
+                               const double2* x, double2* y, cudaStream_t s);
 // Tiles of a problem with n elements for tile height ty (4, 8 or 16 rows of element pairs x 32 columns).
 long long assemble_batched_tiles(int n, int ty);
 cudaError_t launch_assemble_batched(const AsmJob* jobs_dev, int njobs, const long long* tile_prefix_dev,
@@ -99,6 +102,8 @@ bool matvec_tc_supported(int n, int nrhs);
 // Element-wise conversions between complex FP64 and FP32 blocks; column 2-norms of an FP64 block.
 cudaError_t launch_convert_c64_c32(const double2* in, float2* out, size_t count, cudaStream_t s);
 cudaError_t launch_convert_c32_c64(const float2* in, double2* out, size_t count, cudaStream_t s);
+// r = b - r (elementwise)
+cudaError_t launch_axpby_neg(const double2* b, double2* r, size_t count, cudaStream_t s);
 cudaError_t launch_column_norms(const double2* v, int n, int ncol, double* out, cudaStream_t s);
 
 // GMRES building blocks for nrhs systems sharing one matrix; see krylov.cu.

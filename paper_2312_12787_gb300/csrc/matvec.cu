@@ -387,7 +387,17 @@ __global__ void __launch_bounds__(256) k_resid_df_gemm(const float2* __restrict_
     }
 }
 
+__global__ void k_b_minus(const double2* b, double2* r, size_t count) {
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < count; t += (size_t)gridDim.x * blockDim.x)
+    r[t] = csub(b[t], r[t]);
+}
+
 }  // namespace
+
+cudaError_t launch_axpby_neg(const double2* b, double2* r, size_t count, cudaStream_t s) {
+  k_b_minus<<<1024, 256, 0, s>>>(b, r, count);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_convert_c64_c32(const double2* in, float2* out, size_t count, cudaStream_t s) {
   k_c64_to_c32<<<1024, 256, 0, s>>>(in, out, count);

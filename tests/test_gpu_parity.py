@@ -305,3 +305,35 @@ def test_full_size_junction_disk_c3(B, torch):
     b = O.rhs_planewave(wp, 0.0)
     r_rows = b[rows] - ref @ xf.cpu().numpy()[0]
     assert np.max(np.abs(r_rows)) <= 1e-8 * np.max(np.abs(b))
+
+
+def test_matrix_free_matvec_residual_and_solve(B, torch):
+    """Matrix-free products (entries recomputed, nothing stored) against the stored FP64 matrix, the
+    residual against the oracle, and the matrix-free solve against the oracle's LU solution."""
+    wp = W.Problem(k=[20.0, 30.0], eps=[1.0, 2.25], segments=[W.Segment(W.star(300, 0.3, 5), P=0, M=1, closed=True)])
+    pf = B.Problem.from_workload(wp, prec="fp64", matrix_free=1, tol=1e-12)
+    ps = B.Problem.from_workload(wp, prec="fp64")
+    n2 = pf.bem_num_unknowns()
+    assert pf.bem_footprint_bytes(1) < ps.bem_footprint_bytes(1) - n2 * n2 * 16 + 1
+    g = torch.Generator(device="cpu").manual_seed(3)
+    x = torch.randn((2, n2), dtype=torch.complex128, generator=g).cuda()
+    y1, y2 = torch.empty_like(x), torch.empty_like(x)
+    pf.bem_matvec(x, y1, n_rhs=2)
+    ps.bem_matvec(x, y2, n_rhs=2)
+    assert (torch.linalg.vector_norm(y1 - y2, dim=1) / torch.linalg.vector_norm(y2, dim=1)).max().item() <= 1e-13
+    A = O.assemble(wp, Q=4)
+    b = np.stack([O.rhs_planewave(wp, 0.0), O.rhs_planewave(wp, 1.0)])
+    r = torch.empty_like(x)
+    pf.bem_residual(x, torch.as_tensor(b, device="cuda"), r, n_rhs=2)
+    ref = b - (A @ x.cpu().numpy().T).T
+    assert np.max(np.abs(r.cpu().numpy() - ref)) <= 1e-12 * np.max(np.abs(A)) * np.max(np.abs(x.cpu().numpy())) * n2
+    xs = torch.empty((1, n2), dtype=torch.complex128, device="cuda")
+    st, it, rs = pf.bem_solve_planewave([0.0], xs)
+    assert st == B.BEM_OK
+    assert rel(xs[0].cpu().numpy(), O.solve_lu(A, b[0])) <= SOLUTION_TOL_FP64
+    with pytest.raises(B.BemError):
+        pf.bem_get_matrix(torch.empty((n2, n2), dtype=torch.complex128, device="cuda"))
+    pf.close()
+    ps.close()
+    with pytest.raises(B.BemError):                       # matrix-free is an FP64-path option
+        B.Problem(prec="mixed", matrix_free=1)
