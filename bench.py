@@ -31,6 +31,12 @@ sys.path.insert(0, ROOT)
 import workloads as W  # noqa: E402
 
 METRIC = "BEM solves/s (mixed vs FP64 GPU at err<=1e-6)"
+# Assembly roofline inputs: FP64 operations of one k_assemble launch on the star
+# r = 1 + 0.3 cos 5t with N_e = 3072 (ncu: 5.728e9 DFMA, 0.778e9 DADD, 2.468e9 DMUL), and its DRAM traffic per
+# element pair (the four complex FP32 entries of hi and of lo: 64 bytes).
+ASM_FP64_FLOPS_N3072 = 2 * 5.728e9 + 0.778e9 + 2.468e9
+ASM_TRAFFIC_BYTES_PER_PAIR = 64.0
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 UNIT = "solves/s"
 N_RHS = 64
 N_FF = 32
@@ -363,16 +369,24 @@ def main():
     hbm, src = _peaks()
     ph, (ph_ms, ph_n) = max(prof.items(), key=lambda kv: kv[1][0])
     n2 = 2 * nel
-    roof = None
-    if ph == "matvec":
+    avg_s = ph_ms / ph_n / 1e3
+    roof = {"kernel": ph, "launches": ph_n, "avg_launch_ms": ph_ms / ph_n, "traffic": None}
+    if ph == "assemble":
+        # FP64 operations per launch (2*DFMA + DADD + DMUL), counted by ncu on this kernel for the same star
+        # at N_e = 3072 and scaled by the number of element pairs; the FP64 peak is 2 DFMA per clock per SM.
+        flops = ASM_FP64_FLOPS_N3072 * (nel / 3072.0) ** 2
+        peak = FP64_PEAK_TFLOPS
+        ach = flops / avg_s / 1e12
+        roof.update({"kernel": "k_assemble (FP64 pipe)", "bound": "alu", "achieved": ach, "peak": peak,
+                     "unit": "TFLOP/s", "frac": ach / peak, "traffic": ASM_TRAFFIC_BYTES_PER_PAIR * nel * nel,
+                     "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz"})
+    elif ph == "matvec":
         bytes_per = n2 * n2 * 8 + 2 * N_RHS * n2 * 8          # A (complex FP32) + X + Y
-        ach = bytes_per / (ph_ms / ph_n / 1e3) / 1e9
-        roof = {"kernel": "matvec (multi-RHS complex FP32 GEMM)", "bound": "hbm", "achieved": ach, "peak": hbm,
-                "unit": "GB/s", "frac": ach / hbm, "traffic": None, "peak_source": src,
-                "launches": ph_n, "avg_launch_ms": ph_ms / ph_n}
+        ach = bytes_per / avg_s / 1e9
+        roof.update({"kernel": "matvec (tcgen05 3xTF32 multi-RHS GEMM)", "bound": "hbm", "achieved": ach,
+                     "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "peak_source": src})
     else:
-        roof = {"kernel": ph, "bound": "see DESIGN.md", "achieved": None, "peak": None, "unit": None,
-                "frac": None, "traffic": None, "launches": ph_n, "avg_launch_ms": ph_ms / ph_n}
+        roof.update({"bound": "see DESIGN.md", "achieved": None, "peak": None, "unit": None, "frac": None})
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
