@@ -296,10 +296,105 @@ BEM_HD void bessel01_asymp_u(double x, Bessel01& b) {
   b.y1 = -hr;
 }
 
+// ---- the expansion evaluated in double-float ------------------------------------------------------
+// Same mathematics as bessel01_asymp_u, arranged so that almost all of the arithmetic runs on the FP32
+// pipe: cos x and sin x come from a Cody-Waite reduction of x by pi/2 in FP64 (three-part split of pi/2;
+// exact for x < 2^20) followed by Taylor series of the reduced argument |r| <= pi/4 in double-float
+// (terms through r^17 and r^18); P0, Q0, P1, Q1 are Horner sums in u = 1/x^2 with double-float
+// coefficients; the final products too.  Only the reduction, the reciprocal square root and the
+// conversions stay in FP64.
+struct F2Coef {
+  float h[BEM_ASYMP_TERMS / 2], l[BEM_ASYMP_TERMS / 2];
+};
+struct AsympCoefF2 {
+  F2Coef p0, q0, p1, q1;
+  float sh[9], sl[9];    // (-1)^k / (2k+1)!, k = 0..8
+  float ch[10], cl[10];  // (-1)^k / (2k)!,   k = 0..9
+};
+constexpr void f2_split(double v, float& h, float& l) {
+  h = (float)v;
+  l = (float)(v - (double)h);
+}
+constexpr AsympCoefF2 make_asymp_coef_f2() {
+  AsympCoefU u = make_asymp_coef_u();
+  AsympCoefF2 c{};
+  for (int m = 0; m < BEM_ASYMP_TERMS / 2; ++m) {
+    f2_split(u.p0[m], c.p0.h[m], c.p0.l[m]);
+    f2_split(u.q0[m], c.q0.h[m], c.q0.l[m]);
+    f2_split(u.p1[m], c.p1.h[m], c.p1.l[m]);
+    f2_split(u.q1[m], c.q1.h[m], c.q1.l[m]);
+  }
+  double f = 1.0;   // (2k+1)! running
+  for (int k = 0; k < 9; ++k) {
+    if (k > 0) f *= (2.0 * k) * (2.0 * k + 1.0);
+    f2_split(((k & 1) ? -1.0 : 1.0) / f, c.sh[k], c.sl[k]);
+  }
+  f = 1.0;          // (2k)! running
+  for (int k = 0; k < 10; ++k) {
+    if (k > 0) f *= (2.0 * k - 1.0) * (2.0 * k);
+    f2_split(((k & 1) ? -1.0 : 1.0) / f, c.ch[k], c.cl[k]);
+  }
+  return c;
+}
+
+BEM_HD F2 f2_horner(const F2Coef& c, F2 u) {
+  constexpr int T = BEM_ASYMP_TERMS / 2;
+  F2 acc{c.h[T - 1], c.l[T - 1]};
+#pragma unroll
+  for (int m = T - 2; m >= 0; --m) acc = f2_add(f2_mul(acc, u), F2{c.h[m], c.l[m]});
+  return acc;
+}
+
+BEM_HD void bessel01_asymp_f2(double x, Bessel01& b) {
+  constexpr AsympCoefF2 C = make_asymp_coef_f2();
+  constexpr double kPio2_1 = 0x1.921fb54400000p+0;    // pi/2 = kPio2_1 + kPio2_2 + kPio2_3 + O(1e-37)
+  constexpr double kPio2_2 = 0x1.0b4611a600000p-34;
+  constexpr double kPio2_3 = 0x1.3198a2e037073p-69;
+#if defined(__CUDA_ARCH__)
+  const double rs = rsqrt(x);
+#else
+  const double rs = 1.0 / sqrt(x);
+#endif
+  const double y = rs * rs;
+  // argument reduction x = kq pi/2 + r, |r| <= pi/4
+  const double kq = rint(x * kTwoOverPi);
+  double r = fma(-kq, kPio2_1, x);
+  r = fma(-kq, kPio2_2, r);
+  r = fma(-kq, kPio2_3, r);
+  const int quad = (int)((long long)kq & 3);
+  const F2 R = f2_from(r);
+  const F2 R2 = f2_mul(R, R);
+  F2 sp{C.sh[8], C.sl[8]};
+#pragma unroll
+  for (int k = 7; k >= 0; --k) sp = f2_add(f2_mul(sp, R2), F2{C.sh[k], C.sl[k]});
+  const F2 sr = f2_mul(sp, R);
+  F2 cr{C.ch[9], C.cl[9]};
+#pragma unroll
+  for (int k = 8; k >= 0; --k) cr = f2_add(f2_mul(cr, R2), F2{C.ch[k], C.cl[k]});
+  // rotate by quad * pi/2: (sin x, cos x)
+  F2 sn, cs;
+  if (quad == 0) { sn = sr; cs = cr; }
+  else if (quad == 1) { sn = cr; cs = f2_neg(sr); }
+  else if (quad == 2) { sn = f2_neg(sr); cs = f2_neg(cr); }
+  else { sn = f2_neg(cr); cs = sr; }
+  // asymptotic sums
+  const F2 U = f2_from(y * y);
+  const F2 Y = f2_from(y);
+  const F2 p0 = f2_horner(C.p0, U), p1 = f2_horner(C.p1, U);
+  const F2 q0 = f2_mul(f2_horner(C.q0, U), Y), q1 = f2_mul(f2_horner(C.q1, U), Y);
+  // e^{i(x - pi/4)} sqrt(2/(pi x)) = (cos x + sin x, sin x - cos x) * rs / sqrt(pi)
+  const F2 A = f2_from(rs * 0.564189583547756286948079451560772586);   // 1/sqrt(pi)
+  const F2 er = f2_mul(f2_add(cs, sn), A), ei = f2_mul(f2_add(sn, f2_neg(cs)), A);
+  b.j0 = f2_to(f2_add(f2_mul(p0, er), f2_neg(f2_mul(q0, ei))));
+  b.y0 = f2_to(f2_add(f2_mul(p0, ei), f2_mul(q0, er)));
+  b.j1 = f2_to(f2_add(f2_mul(p1, ei), f2_mul(q1, er)));
+  b.y1 = -f2_to(f2_add(f2_mul(p1, er), f2_neg(f2_mul(q1, ei))));
+}
+
 BEM_HD void bessel01(double x, Bessel01& b) {
   if (x < BEM_X_SERIES) bessel01_series(x, b);
   else if (x < BEM_X_ASYMP) bessel01_miller_f2(x, b);
-  else bessel01_asymp_u(x, b);
+  else bessel01_asymp_f2(x, b);
 }
 
 // integral_0^x J0(t) dt and integral_0^x Y0(t) dt for the weakly singular self-element integral,
