@@ -176,6 +176,15 @@ BEM_API bem_status bem_solve_planewave(bem_problem* p, int n_rhs, const double* 
 BEM_API bem_status bem_far_field(bem_problem* p, int n_rhs, const bem_c64* x_dev, int n_ang,
                                  const double* ang_host, bem_c64* out_dev, void* stream);
 
+/* Field at points (the paper's accuracy study evaluates it on a 101 x 101 grid, Sec. 7.1): for each of
+ * n_rhs solutions x_dev and each point pts_host[2p], pts_host[2p+1] lying in domain dom_host[p], Green's
+ * representation u = [u_in] + sum_j sigma_{d,j} int_j (eps_d G_d w_j - dG_d/dn u_j), element integrals by the
+ * problem's Gauss-Legendre rule.  angles_host (n_rhs, or NULL) adds the incident plane wave at host points;
+ * NULL gives the scattered field there.  out_dev: n_rhs x n_pts.  Points must not lie on the boundary. */
+BEM_API bem_status bem_near_field(bem_problem* p, int n_rhs, const bem_c64* x_dev, const double* angles_host,
+                                  int n_pts, const double* pts_host, const int* dom_host, bem_c64* out_dev,
+                                  void* stream);
+
 /* End-to-end call with host buffers: assemble (if needed), solve plane waves, far field; copies the
  * traces (n_rhs x 2N) and far fields (n_rhs x n_ang) to the host.  x_host or ff_host may be NULL. */
 BEM_API bem_status bem_solve_planewave_host(bem_problem* p, int n_rhs, const double* angles_host,

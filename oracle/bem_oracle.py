@@ -42,7 +42,7 @@ from scipy import special
 __all__ = [
     "Elements", "elements", "gauss_legendre", "kernel_values", "self_terms", "operator_block",
     "sigma", "row_plan", "assemble", "assemble_rows", "rhs_planewave", "solve_lu", "gmres",
-    "far_field", "alpha_of", "FORMS",
+    "far_field", "near_field", "alpha_of", "FORMS",
 ]
 
 FORMS = ("mod", "orig", "beta1", "conv")
@@ -384,3 +384,37 @@ def far_field(problem, y, angles, Q: int = 4, el: Elements | None = None):
         elem = np.sum(Wq * ph, axis=1) * (w + 1j * k1 * (el.nrm @ xh) * u)
         out[a] = np.sum(sg * elem)
     return out * np.exp(0.25j * np.pi) / np.sqrt(8.0 * np.pi * k1)
+
+
+def near_field(problem, y, pts, dom, theta=None, Q: int = 4, el: Elements | None = None):
+    """Total field u at points `pts` (M,2) lying in domains `dom` (M,) from the traces y = [u; w].
+
+    Green's representation in the domain d that contains the point (Sec. 3.3; the same representation whose
+    boundary traces give the standard equations of Sec. 6):
+        u(x) = [u_in(x) if d is the host] + sum_j sigma_{d,j} int_j [ eps_d G_d(x-y) w_j - dG_d/dn(y) u_j ] dy
+    with element integrals by the same Q-point Gauss-Legendre rule as the matrix.  theta = incident angle of
+    the plane wave (None: scattered field only in the host).
+    """
+    if el is None:
+        el = elements(problem)
+    k = np.asarray(problem.k, dtype=np.float64)
+    eps = np.asarray(problem.eps, dtype=np.float64)
+    n = el.n
+    u, w = y[:n], y[n:]
+    t, wq = gauss_legendre(Q)
+    yq = el.mid[:, None, :] + (0.5 * el.h)[:, None, None] * t[None, :, None] * el.tau[:, None, :]   # (N,Q,2)
+    Wq = (0.5 * el.h)[:, None] * wq[None, :]
+    out = np.zeros(len(pts), dtype=np.complex128)
+    for m, (x, d) in enumerate(zip(np.asarray(pts, dtype=np.float64), np.asarray(dom))):
+        sg = sigma(el, int(d))
+        z = x[None, None, :] - yq
+        r = np.hypot(z[..., 0], z[..., 1])
+        kd = k[int(d)]
+        G = 0.25j * special.hankel1(0, kd * r)
+        dGdny = 0.25j * kd * special.hankel1(1, kd * r) * np.sum(z / r[..., None] * el.nrm[:, None, :], -1)
+        S = np.sum(Wq * G, 1)
+        D = np.sum(Wq * dGdny, 1)
+        out[m] = np.sum(sg * (eps[int(d)] * S * w - D * u))
+        if int(d) == 0 and theta is not None:
+            out[m] += np.exp(1j * k[0] * (np.cos(theta) * x[0] + np.sin(theta) * x[1]))
+    return out

@@ -25,7 +25,7 @@ EXPORTS = [
     "bem_default_opts", "bem_problem_create", "bem_problem_destroy", "bem_set_opts", "bem_set_domains",
     "bem_add_segment", "bem_num_elements", "bem_num_unknowns", "bem_footprint_bytes", "bem_assemble",
     "bem_get_matrix", "bem_rhs_planewave", "bem_matvec", "bem_residual", "bem_residual_noalloc", "bem_solve", "bem_solve_planewave", "bem_far_field",
-    "bem_solve_planewave_host", "bem_profile_enable", "bem_profile_read", "bem_last_error", "bem_version",
+    "bem_solve_planewave_host", "bem_near_field", "bem_profile_enable", "bem_profile_read", "bem_last_error", "bem_version",
     "bem_batch_create", "bem_batch_destroy", "bem_batch_admit", "bem_batch_step", "bem_batch_query",
     "bem_batch_take", "bem_batch_free_units", "bem_batch_solve_planewave",
 ]
@@ -80,6 +80,8 @@ def load(path: str | None = None):
     L.bem_solve_planewave.argtypes = [vp, i, vp, vp, vp, vp, vp]
     L.bem_far_field.argtypes = [vp, i, vp, i, vp, vp, vp]
     L.bem_solve_planewave_host.argtypes = [vp, i, vp, vp, i, vp, vp, vp, vp, vp]
+    L.bem_near_field.argtypes = [vp, i, vp, vp, i, vp, vp, vp, vp]
+    L.bem_near_field.restype = i
     L.bem_profile_enable.argtypes = [vp, i]
     L.bem_profile_read.argtypes = [vp, vp, vp]
     ll = ctypes.c_longlong
@@ -249,6 +251,16 @@ class Problem:
     def bem_far_field(self, x, angles, out, n_rhs=1, stream=None):
         a, ptr = _hbuf(angles, np.float64)
         _check(load().bem_far_field(self._h, n_rhs, _dptr(x), len(a), ptr, _dptr(out), _stream_ptr(stream)))
+        return out
+
+    def bem_near_field(self, x, pts, dom, out, angles=None, n_rhs=1, stream=None):
+        pa, pp = _hbuf(pts, np.float64)
+        da, dp = _hbuf(dom, np.int32)
+        if angles is not None:
+            aa, ap = _hbuf(angles, np.float64)
+        else:
+            ap = None
+        _check(load().bem_near_field(self._h, n_rhs, _dptr(x), ap, len(da), pp, dp, _dptr(out), _stream_ptr(stream)))
         return out
 
     def bem_profile_enable(self, on=True):

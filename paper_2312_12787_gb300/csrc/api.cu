@@ -810,6 +810,39 @@ BEM_API bem_status bem_far_field(bem_problem* p, int n_rhs, const bem_c64* x_dev
   return BEM_OK;
 }
 
+BEM_API bem_status bem_near_field(bem_problem* p, int n_rhs, const bem_c64* x_dev, const double* angles,
+                                  int n_pts, const double* pts, const int* dom, bem_c64* out_dev, void* stream) {
+  if (!p || !x_dev || !pts || !dom || !out_dev || n_rhs < 1 || n_pts < 1) return fail(BEM_EINVAL, "invalid argument");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  bem_status st = check_ready(p);
+  if (st != BEM_OK) return st;
+  for (int i = 0; i < n_pts; ++i) {
+    if (dom[i] < 0 || dom[i] >= p->dom.n) return fail(BEM_EINVAL, "point %d: domain %d out of range", i, dom[i]);
+    if (!std::isfinite(pts[2 * i]) || !std::isfinite(pts[2 * i + 1])) return fail(BEM_EINVAL, "point %d not finite", i);
+  }
+  st = upload_geometry(p, s);
+  if (st != BEM_OK) return st;
+  // points, domains and angles travel in one temporary device block
+  const size_t bytes = (size_t)2 * n_pts * sizeof(double) + (size_t)n_rhs * sizeof(double) + (size_t)n_pts * sizeof(int);
+  char* blk = nullptr;
+  CU(cudaMallocAsync(&blk, bytes, s));
+  double* dp = reinterpret_cast<double*>(blk);
+  double* da = dp + 2 * (size_t)n_pts;
+  int* dd = reinterpret_cast<int*>(da + n_rhs);
+  CU(cudaMemcpyAsync(dp, pts, 2 * (size_t)n_pts * sizeof(double), cudaMemcpyHostToDevice, s));
+  if (angles) CU(cudaMemcpyAsync(da, angles, n_rhs * sizeof(double), cudaMemcpyHostToDevice, s));
+  CU(cudaMemcpyAsync(dd, dom, n_pts * sizeof(int), cudaMemcpyHostToDevice, s));
+  {
+    Phase ph(p, BEM_PH_FARFIELD, s, 1);
+    CU(launch_near_field(p->elem(), p->n, p->dom, make_quad(p->o.quad_order), n_rhs,
+                         reinterpret_cast<const double2*>(x_dev), n_pts, dp, dd, angles ? da : nullptr,
+                         reinterpret_cast<double2*>(out_dev), s));
+  }
+  CU(cudaFreeAsync(blk, s));
+  CU(cudaStreamSynchronize(s));   // host arrays may be pageable
+  return BEM_OK;
+}
+
 BEM_API bem_status bem_solve_planewave_host(bem_problem* p, int n_rhs, const double* angles, bem_c64* x_host,
                                             int n_ang, const double* ff_ang, bem_c64* ff_host, int* iters,
                                             double* resid, void* stream) {

@@ -328,6 +328,66 @@ __global__ void __launch_bounds__(256) k_far_field(ElemDev e, int n, DomTab dom,
   }
 }
 
+// Field at points (Green's representation in the domain containing each point):
+//   u(x) = [u_in(x) for the host] + sum_j sigma_{d,j} sum_q W_q [ eps_d G_d(x - y_q) w_j - dG_d/dn(y_q) u_j ]
+// One warp per (point, right-hand side); lanes stride over elements; FP64 with the assembly's Hankel code.
+__global__ void __launch_bounds__(256) k_near_field(ElemDev e, int n, DomTab dom, Quad q, int nrhs, const double2* x,
+                                                    int npts, const double* pts, const int* pdom,
+                                                    const double* angles, double2* out) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int pt = blockIdx.x * 8 + warp;
+  const int r = blockIdx.y;
+  if (pt >= npts || r >= nrhs) return;
+  const double px = pts[2 * pt], py = pts[2 * pt + 1];
+  const int d = pdom[pt];
+  const double k = dom.k[d], eps = dom.eps[d];
+  const double2* xr = x + (size_t)r * 2 * n;
+  double2 acc = make_double2(0, 0);
+  for (int j = lane; j < n; j += 32) {
+    const int Pj = e.P[j], Mj = e.M[j];
+    const double sg = (Pj == d) ? 1.0 : ((Mj == d) ? -1.0 : 0.0);
+    if (sg == 0.0) continue;
+    const double tx = e.tx[j], ty = e.ty[j], hh = 0.5 * e.h[j], mx = e.mx[j], my = e.my[j];
+    const double nxj = -ty, nyj = tx;
+    double2 sS = make_double2(0, 0), sD = make_double2(0, 0);
+    for (int m = 0; m < q.Q; ++m) {
+      const double sq = hh * q.t[m], W = hh * q.w[m];
+      const double zx = px - (mx + sq * tx), zy = py - (my + sq * ty);
+      const double r2 = zx * zx + zy * zy;
+      const double ir = rsqrt(r2);
+      const double rr = r2 * ir;
+      const double cj = (zx * nxj + zy * nyj) * ir;
+      Bessel01 b;
+      bessel01(k * rr, b);
+      sS.x += W * b.j0; sS.y += W * b.y0;
+      sD.x += W * cj * b.j1; sD.y += W * cj * b.y1;
+    }
+    // G = (i/4) H0 -> (i/4) sS ; dG/dn(y) = (ik/4) H1 (zh . n_y) -> (ik/4) sD
+    const double2 S = make_double2(-0.25 * sS.y, 0.25 * sS.x);
+    const double2 D = make_double2(-0.25 * k * sD.y, 0.25 * k * sD.x);
+    const double2 u = xr[j], w = xr[n + j];
+    const double2 t = csub(cscale(cmul(S, w), eps), cmul(D, u));
+    acc.x += sg * t.x;
+    acc.y += sg * t.y;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+  }
+  if (lane == 0) {
+    if (d == 0 && angles) {
+      double st, ct;
+      sincos(angles[r], &st, &ct);
+      double sp, cp;
+      sincos(dom.k[0] * (ct * px + st * py), &sp, &cp);
+      acc.x += cp;
+      acc.y += sp;
+    }
+    out[(size_t)r * npts + pt] = acc;
+  }
+}
+
 __global__ void k_matrix_to_c64(const void* A, const void* Alo, int mixed, int which, size_t nn, double2* out) {
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < nn; t += (size_t)gridDim.x * blockDim.x) {
     if (!mixed) {
@@ -401,6 +461,14 @@ cudaError_t launch_far_field(const ElemDev& e, int n, const DomTab& dom, const Q
                              int nang, const double* ang_dev, double2* out, cudaStream_t s) {
   dim3 grd(nang, nrhs);
   k_far_field<<<grd, 256, 0, s>>>(e, n, dom, q, x, nang, ang_dev, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_near_field(const ElemDev& e, int n, const DomTab& dom, const Quad& q, int nrhs, const double2* x,
+                              int npts, const double* pts_dev, const int* dom_dev, const double* angles_dev,
+                              double2* out, cudaStream_t s) {
+  dim3 grd((npts + 7) / 8, nrhs);
+  k_near_field<<<grd, 256, 0, s>>>(e, n, dom, q, nrhs, x, npts, pts_dev, dom_dev, angles_dev, out);
   return cudaGetLastError();
 }
 

@@ -72,6 +72,9 @@ cudaError_t launch_rhs_planewave(const ElemDev& e, int n, const DomTab& dom, int
                                  const double* angles_dev, double2* b, cudaStream_t s);
 cudaError_t launch_far_field(const ElemDev& e, int n, const DomTab& dom, const Quad& q, int nrhs, const double2* x,
                              int nang, const double* ang_dev, double2* out, cudaStream_t s);
+cudaError_t launch_near_field(const ElemDev& e, int n, const DomTab& dom, const Quad& q, int nrhs, const double2* x,
+                              int npts, const double* pts_dev, const int* dom_dev, const double* angles_dev,
+                              double2* out, cudaStream_t s);
 // Matrix to c64 copy for inspection: which 0 -> main (c64 or hi), 1 -> hi + lo.
 cudaError_t launch_matrix_to_c64(const void* A, const void* Alo, int mixed, int which, size_t nn, double2* out,
                                  cudaStream_t s);

@@ -337,3 +337,29 @@ def test_matrix_free_matvec_residual_and_solve(B, torch):
     ps.close()
     with pytest.raises(B.BemError):                       # matrix-free is an FP64-path option
         B.Problem(prec="mixed", matrix_free=1)
+
+
+def test_near_field_matches_oracle_and_mie_grid(B, torch):
+    """Field on the paper's 101 x 101 grid over [-2.99, 2.99]^2 (Sec. 7.1): GPU against the oracle at sampled
+    points, and the paper's relative l2 error of Re u against the Mie series decreasing with N."""
+    k1, k2, e2 = 5.0, 7.5, 2.25
+    g = np.linspace(-2.99, 2.99, 101)
+    pts = np.array([(a, b) for a in g for b in g])
+    dom = (np.hypot(pts[:, 0], pts[:, 1]) < 1.0).astype(np.int32)
+    ref = O.mie_field(k1, k2, e2, pts[::97])
+    errs = []
+    for n in (256, 512):
+        wp = W.circle_problem(n, k1, k2, e2)
+        p = B.Problem.from_workload(wp, tol=1e-12, quad_order=10)
+        x = torch.empty((1, 2 * n), dtype=torch.complex128, device="cuda")
+        p.bem_solve_planewave([0.0], x)
+        u = torch.empty((1, len(pts)), dtype=torch.complex128, device="cuda")
+        p.bem_near_field(x, pts, dom, u, angles=[0.0])
+        got = u[0].cpu().numpy()
+        samp = np.arange(0, len(pts), 97)
+        oref = O.near_field(wp, x[0].cpu().numpy(), pts[samp], dom[samp], theta=0.0, Q=10)
+        assert np.max(np.abs(got[samp] - oref)) <= 1e-11 * np.max(np.abs(oref))
+        mie = O.mie_field(k1, k2, e2, pts) if n == 256 else mie
+        errs.append(np.sqrt(np.sum((got.real - mie.real) ** 2) / np.sum(mie.real ** 2)))
+        p.close()
+    assert errs[1] < errs[0] and errs[1] < 2e-2

@@ -329,3 +329,44 @@ def test_gmres_on_bem_matrix_matches_lu():
     xl = O.solve_lu(A, b)
     assert np.linalg.norm(x - xl) / np.linalg.norm(xl) < 1e-9
     assert np.linalg.norm(A @ x - b) / np.linalg.norm(b) < 1e-11
+
+
+def test_near_field_representation_reproduces_point_source():
+    """Feeding the exact traces of v = H0(k|x - z|) (z outside Omega_d) into the representation gives v back
+    inside Omega_d, up to first-order discretisation error."""
+    from scipy import special
+    errs = []
+    for n in (64, 128, 256):
+        p = W.Problem(k=[3.0, 4.0], eps=[1.0, 1.7], segments=[W.Segment(W.ellipse(n, 2.0), P=0, M=1, closed=True)])
+        el = O.elements(p)
+        # interior domain 1 (k = 4, eps = 1.7), source outside
+        z = np.array([2.5, 0.3])
+        dz = el.mid - z
+        r = np.hypot(dz[:, 0], dz[:, 1])
+        v = special.hankel1(0, 4.0 * r)
+        dvdn = -4.0 * special.hankel1(1, 4.0 * r) * np.sum(dz / r[:, None] * el.nrm, 1)
+        y = np.concatenate([v, dvdn / 1.7])                   # w = (1/eps) du/dn
+        pts = np.array([[0.1, 0.05], [-0.6, 0.2], [0.5, -0.3]])
+        got = O.near_field(p, y, pts, np.ones(3, int), Q=10)
+        ref = special.hankel1(0, 4.0 * np.hypot(*(pts - z).T))
+        errs.append(np.max(np.abs(got - ref)) / np.max(np.abs(ref)))
+    assert errs[-1] < 5e-3 and errs[0] / errs[-1] > 3.0
+
+
+def test_near_field_of_bem_solution_converges_to_mie():
+    """Sec. 7.1 accuracy metric (relative l2 error of Re u over field points) decays like 1/N."""
+    k1, k2, e2 = 5.0, 7.5, 2.25
+    g = np.linspace(-2.99, 2.99, 9)
+    pts = np.array([(a, b) for a in g for b in g])
+    rr = np.hypot(pts[:, 0], pts[:, 1])
+    keep = np.abs(rr - 1.0) > 0.15                            # away from the boundary at these sizes
+    pts = pts[keep]
+    dom = (np.hypot(pts[:, 0], pts[:, 1]) < 1.0).astype(int)
+    ref = O.mie_field(k1, k2, e2, pts)
+    errs = []
+    for n in (128, 256):
+        p = W.circle_problem(n, k1, k2, e2)
+        x = O.solve_lu(O.assemble(p, Q=10), O.rhs_planewave(p, 0.0))
+        u = O.near_field(p, x, pts, dom, theta=0.0, Q=10)
+        errs.append(np.sqrt(np.sum((u.real - ref.real) ** 2) / np.sum(ref.real ** 2)))
+    assert errs[-1] < 5e-3 and errs[0] / errs[1] > 1.7
