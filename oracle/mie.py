@@ -10,7 +10,7 @@ from __future__ import annotations
 import numpy as np
 from scipy import special
 
-__all__ = ["mie_coefficients", "mie_traces", "mie_far_field", "mie_field"]
+__all__ = ["mie_coefficients", "mie_traces", "mie_far_field", "mie_field", "mie2_coefficients", "mie2_far_field"]
 
 
 def _nmax_default(k1, k2, R):
@@ -70,3 +70,37 @@ def mie_field(k1, k2, eps2, pts, R=1.0, theta_inc=0.0, nmax=None):
         else:
             out[m] = np.sum(b * special.jv(n, k2 * r[m]) * e)
     return out
+
+
+def mie2_coefficients(k, eps, R_out=2.0, R_in=1.0, theta_inc=0.0, nmax=None):
+    """Two-layer cylinder of Sec. 7.2 (concentric circles): host k[0]; ring R_in < r < R_out with k[1], eps[1];
+    core r < R_in with k[2], eps[2].  Host: c_n J_n + a_n H_n; ring: b_n J_n + d_n H_n; core: e_n J_n.
+    Continuity of u and of (1/eps) du/dr at both radii gives a 4 x 4 system per n (eqs. jump_in_u, jump_in_w).
+    Returns (n, a, b, d, e, c)."""
+    k1, k2, k3 = k
+    e1, e2, e3 = eps
+    if nmax is None:
+        nmax = max(50, int(np.ceil(max(k) * R_out)) + 40)
+    n = np.arange(-nmax, nmax + 1)
+    c = (1j ** n) * np.exp(-1j * n * theta_inc)
+    out = np.zeros((4, len(n)), dtype=np.complex128)
+    J, H, Jp, Hp = special.jv, special.hankel1, special.jvp, special.h1vp
+    for m, nn in enumerate(n):
+        x1, x2o, x2i, x3 = k1 * R_out, k2 * R_out, k2 * R_in, k3 * R_in
+        Mat = np.array([
+            [H(nn, x1), -J(nn, x2o), -H(nn, x2o), 0.0],
+            [(k1 / e1) * Hp(nn, x1), -(k2 / e2) * Jp(nn, x2o), -(k2 / e2) * Hp(nn, x2o), 0.0],
+            [0.0, J(nn, x2i), H(nn, x2i), -J(nn, x3)],
+            [0.0, (k2 / e2) * Jp(nn, x2i), (k2 / e2) * Hp(nn, x2i), -(k3 / e3) * Jp(nn, x3)],
+        ], dtype=np.complex128)
+        rhs = np.array([-c[m] * J(nn, x1), -c[m] * (k1 / e1) * Jp(nn, x1), 0.0, 0.0], dtype=np.complex128)
+        out[:, m] = np.linalg.solve(Mat, rhs)
+    a, b, d, e = out
+    return n, a, b, d, e, c
+
+
+def mie2_far_field(k, eps, angles, R_out=2.0, R_in=1.0, theta_inc=0.0, nmax=None):
+    """Far-field pattern of the two-layer cylinder, same normalisation as mie_far_field."""
+    n, a, b, d, e, c = mie2_coefficients(k, eps, R_out, R_in, theta_inc, nmax)
+    E = np.exp(1j * np.outer(angles, n))
+    return np.sqrt(2.0 / (np.pi * k[0])) * np.exp(-0.25j * np.pi) * (E @ (a * (-1j) ** n))

@@ -363,3 +363,44 @@ def test_near_field_matches_oracle_and_mie_grid(B, torch):
         errs.append(np.sqrt(np.sum((got.real - mie.real) ** 2) / np.sum(mie.real ** 2)))
         p.close()
     assert errs[1] < errs[0] and errs[1] < 2e-2
+
+
+def test_gpu_iteration_study_matches_paper_trend(B, torch):
+    """NEXT-1 reproduction on the GPU (FP64 path, Sec. 7.1 setting): iterations of the conventional form grow
+    with N, those of the proposed form stay flat, up to N = 1600."""
+    its = {"conv": [], "mod": []}
+    for n in (200, 400, 800, 1600):
+        wp = W.circle_problem(n, 5.0, 5.0 * np.sqrt(2.0), eps_i=2.0)
+        for f in its:
+            p = B.Problem.from_workload(wp, form=f, tol=1e-8, quad_order=10, max_iter=800)
+            x = torch.empty((1, 2 * n), dtype=torch.complex128, device="cuda")
+            st, it, rs = p.bem_solve_planewave([0.0], x)
+            its[f].append(int(it[0]))
+            p.close()
+    assert max(its["mod"]) - min(its["mod"]) <= 2, its
+    assert all(b > 1.15 * a for a, b in zip(its["conv"], its["conv"][1:])), its
+
+
+def test_concentric_gpu_solution_matches_two_layer_series(B, torch):
+    """Concentric circles (Sec. 7.2): mixed-precision GPU solutions of the 'mod' system, far field against the
+    two-layer series (first order in N) and the traces against the oracle's LU solution."""
+    eps = (1.0, 2.0, 3.0)
+    om = 1.0
+    k = [om * np.sqrt(e) for e in eps]
+    ang = np.linspace(0, 2 * np.pi, 24, endpoint=False)
+    ref = O.mie2_far_field(k, eps, ang)
+    errs = []
+    for N in (300, 600):
+        wp = W.concentric(N // 3, 2 * N // 3, om, eps=eps)
+        p = B.Problem.from_workload(wp, prec="mixed", tol=1e-10, quad_order=10)
+        x = torch.empty((1, 2 * N), dtype=torch.complex128, device="cuda")
+        st, it, rs = p.bem_solve_planewave([0.0], x)
+        assert st == B.BEM_OK
+        ff = torch.empty((1, len(ang)), dtype=torch.complex128, device="cuda")
+        p.bem_far_field(x, ang, ff)
+        errs.append(rel(ff[0].cpu().numpy(), ref))
+        if N == 300:
+            xl = O.solve_lu(O.assemble(wp, Q=10), O.rhs_planewave(wp, 0.0))
+            assert rel(x[0].cpu().numpy(), xl) <= SOLUTION_TOL_MIXED
+        p.close()
+    assert errs[1] < errs[0] / 1.6 and errs[1] < 3e-3

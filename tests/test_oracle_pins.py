@@ -370,3 +370,45 @@ def test_near_field_of_bem_solution_converges_to_mie():
         u = O.near_field(p, x, pts, dom, theta=0.0, Q=10)
         errs.append(np.sqrt(np.sum((u.real - ref.real) ** 2) / np.sum(ref.real ** 2)))
     assert errs[-1] < 5e-3 and errs[0] / errs[1] > 1.7
+
+
+def test_two_layer_series_reduces_to_one_circle_and_conserves_energy():
+    """Core made of the ring material: the two-layer series equals the one-circle series of radius 2."""
+    om = 1.5
+    k = [om, om * np.sqrt(2.0), om * np.sqrt(2.0)]
+    n, a, b, d, e, c = O.mie2_coefficients(k, [1.0, 2.0, 2.0], nmax=30)
+    n1, a1, b1, c1 = O.mie_coefficients(k[0], k[1], 2.0, R=2.0, nmax=30)
+    assert np.max(np.abs(a - a1)) < 1e-12 and np.max(np.abs(d)) < 1e-12 and np.max(np.abs(e - b)) < 1e-12
+    n, a, b, d, e, c = O.mie2_coefficients([om, om * np.sqrt(2.0), om * np.sqrt(3.0)], [1.0, 2.0, 3.0], nmax=30)
+    assert np.max(np.abs(np.abs(1 + 2 * a / c) - 1)) < 1e-12
+
+
+def test_concentric_bem_converges_to_two_layer_series():
+    """Sec. 7.2: concentric circles (R = 2, eps_2 = 2; R = 1, eps_3 = 3), N/3 inner and 2N/3 outer elements;
+    the far field of the oracle's 'mod' solution approaches the two-layer series at first order."""
+    om = 1.0
+    eps = (1.0, 2.0, 3.0)
+    k = [om * np.sqrt(e) for e in eps]
+    ang = np.linspace(0, 2 * np.pi, 24, endpoint=False)
+    ref = O.mie2_far_field(k, eps, ang)
+    errs = []
+    for N in (150, 300):
+        p = W.concentric(N // 3, 2 * N // 3, om, eps=eps)
+        x = O.solve_lu(O.assemble(p, Q=10), O.rhs_planewave(p, 0.0))
+        errs.append(np.linalg.norm(O.far_field(p, x, ang, Q=10) - ref) / np.linalg.norm(ref))
+    assert errs[-1] < 5e-3 and errs[0] / errs[1] > 1.6
+
+
+def test_iterations_flat_in_n_for_proposed_forms_growing_for_conventional():
+    """Sec. 7.1 (iterations vs N, circle with omega = 5, eps_2 = 2, tolerance 1e-8, 10 Gauss nodes): the
+    conventional system's GMRES count grows with N, beta = 1 and beta = -alpha stay flat, and beta = -alpha
+    needs fewer iterations than beta = 1."""
+    its = {f: [] for f in ("conv", "beta1", "mod")}
+    for n in (100, 200):
+        p = W.circle_problem(n, 5.0, 5.0 * np.sqrt(2.0), eps_i=2.0)
+        for f in its:
+            A = O.assemble(p, Q=10, form=f)
+            its[f].append(O.gmres(A, O.rhs_planewave(p, 0.0, form=f), tol=1e-8)[1])
+    assert its["conv"][1] > 1.2 * its["conv"][0]
+    assert abs(its["mod"][1] - its["mod"][0]) <= 1 and abs(its["beta1"][1] - its["beta1"][0]) <= 1
+    assert its["mod"][1] < its["beta1"][1] < its["conv"][1]
