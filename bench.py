@@ -31,12 +31,14 @@ sys.path.insert(0, ROOT)
 import workloads as W  # noqa: E402
 
 METRIC = "BEM solves/s (mixed vs FP64 GPU at err<=1e-6)"
-# Assembly roofline inputs: FP64 operations of one k_assemble launch on the star
-# r = 1 + 0.3 cos 5t with N_e = 3072 (ncu: 5.728e9 DFMA, 0.778e9 DADD, 2.468e9 DMUL), and its DRAM traffic per
-# element pair (the four complex FP32 entries of hi and of lo: 64 bytes).
-ASM_FP64_FLOPS_N3072 = 2 * 5.728e9 + 0.778e9 + 2.468e9
-ASM_TRAFFIC_BYTES_PER_PAIR = 64.0
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# Assembly roofline inputs (profiles/assemble_star3072.md): one k_assemble launch on the star
+# r = 1 + 0.3 cos 5t with N_e = 3072 issues 7.3916e9 thread operations on the FP64 pipe (DFMA, DADD, DMUL and the
+# FP32<->FP64 conversions of its double-float parts; ncu sm__thread_inst_executed_pipe_fp64_pred_on.sum) and moves
+# 548.9 MB of DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum).  Both scale with the element pairs.
+# The FP64 pipe of a GB300 SM retires 2 thread operations per clock.
+ASM_FP64_PIPE_OPS_N3072 = 7.391610912e9
+ASM_DRAM_BYTES_N3072 = 547612416 + 1298432
+FP64_PIPE_PEAK_TOPS = 152 * 2 * 2.07e9 / 1e12
 UNIT = "solves/s"
 N_RHS = 64
 N_FF = 32
@@ -372,14 +374,14 @@ def main():
     avg_s = ph_ms / ph_n / 1e3
     roof = {"kernel": ph, "launches": ph_n, "avg_launch_ms": ph_ms / ph_n, "traffic": None}
     if ph == "assemble":
-        # FP64 operations per launch (2*DFMA + DADD + DMUL), counted by ncu on this kernel for the same star
-        # at N_e = 3072 and scaled by the number of element pairs; the FP64 peak is 2 DFMA per clock per SM.
-        flops = ASM_FP64_FLOPS_N3072 * (nel / 3072.0) ** 2
-        peak = FP64_PEAK_TFLOPS
-        ach = flops / avg_s / 1e12
+        scale = (nel / 3072.0) ** 2
+        ops = ASM_FP64_PIPE_OPS_N3072 * scale
+        peak = FP64_PIPE_PEAK_TOPS
+        ach = ops / avg_s / 1e12
         roof.update({"kernel": "k_assemble (FP64 pipe)", "bound": "alu", "achieved": ach, "peak": peak,
-                     "unit": "TFLOP/s", "frac": ach / peak, "traffic": ASM_TRAFFIC_BYTES_PER_PAIR * nel * nel,
-                     "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz"})
+                     "unit": "Top/s (FP64-pipe thread operations)", "frac": ach / peak,
+                     "traffic": ASM_DRAM_BYTES_N3072 * scale,
+                     "peak_source": "derived: 152 SMs x 2 FP64-pipe thread ops/clk x 2.07 GHz"})
     elif ph == "matvec":
         bytes_per = n2 * n2 * 8 + 2 * N_RHS * n2 * 8          # A (complex FP32) + X + Y
         ach = bytes_per / avg_s / 1e9
