@@ -255,6 +255,7 @@ def main():
                     help="star: the 64-RHS star (default line); serving: Poisson request stream; "
                          "sweep: 256 random stars in one batch")
     ap.add_argument("--requests", type=int, default=200, help="serving: number of requests")
+    ap.add_argument("--n-rhs", type=int, default=64, help="star: incident angles per step (64 = the workload)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -269,6 +270,8 @@ def main():
     B.build()
     P.load()
 
+    global N_RHS
+    N_RHS = args.n_rhs
     wp = W.cfg_star_c2(args.n_elem)
     ang = W.plane_wave_angles(N_RHS)
     ffa = np.linspace(0.0, 2 * np.pi, N_FF, endpoint=False)
