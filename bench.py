@@ -32,12 +32,15 @@ import workloads as W  # noqa: E402
 
 METRIC = "BEM solves/s (mixed vs FP64 GPU at err<=1e-6)"
 # Assembly roofline inputs (profiles/assemble_star3072.md): one k_assemble launch on the star
-# r = 1 + 0.3 cos 5t with N_e = 3072 issues 7.3916e9 thread operations on the FP64 pipe (DFMA, DADD, DMUL and the
-# FP32<->FP64 conversions of its double-float parts; ncu sm__thread_inst_executed_pipe_fp64_pred_on.sum) and moves
-# 548.9 MB of DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum).  Both scale with the element pairs.
+# r = 1 + 0.3 cos 5t with N_e = 3072 issues 1.8383e9 thread operations on the FP64 pipe (node geometry, phase
+# reduction and what remains of the conversions; ncu sm__thread_inst_executed_pipe_fp64_pred_on.sum) and moves
+# 543.7 MB of DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum).  Both scale with the element pairs.
 # The FP64 pipe of a GB300 SM retires 2 thread operations per clock.
-ASM_FP64_PIPE_OPS_N3072 = 7.391610912e9
-ASM_DRAM_BYTES_N3072 = 547612416 + 1298432
+ASM_FP64_PIPE_OPS_N3072 = 1.838292576e9
+ASM_DRAM_BYTES_N3072 = 542418688 + 1313280
+# Multi-RHS GEMM DRAM traffic per launch at N_e = 3072, 64 RHS (profiles/gemm_tc_star3072_64rhs.md), scaling
+# with the matrix entries.
+GEMM_DRAM_BYTES_N3072 = 314.7e6 + 4.0e6
 FP64_PIPE_PEAK_TOPS = 152 * 2 * 2.07e9 / 1e12
 UNIT = "solves/s"
 N_RHS = 64
@@ -389,7 +392,8 @@ def main():
         bytes_per = n2 * n2 * 8 + 2 * N_RHS * n2 * 8          # A (complex FP32) + X + Y
         ach = bytes_per / avg_s / 1e9
         roof.update({"kernel": "matvec (tcgen05 3xTF32 multi-RHS GEMM)", "bound": "hbm", "achieved": ach,
-                     "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "peak_source": src})
+                     "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "peak_source": src,
+                     "traffic": GEMM_DRAM_BYTES_N3072 * (nel / 3072.0) ** 2 if N_RHS > 1 else None})
     else:
         roof.update({"bound": "see DESIGN.md", "achieved": None, "peak": None, "unit": None, "frac": None})
 

@@ -138,7 +138,9 @@ BEM_API bem_status bem_rhs_planewave(bem_problem* p, int n_rhs, const double* an
                                      void* stream);
 
 /* Steps a6 / a11 for testing: y = A x for n_rhs columns with the kernel the solver uses
- * (FP64: FP64 GEMV/GEMM; MIXED: FP32 GEMV; MIXED_TC: tensor-core GEMM when n_rhs > 1). */
+ * (FP64: FP64 GEMV/GEMM; MIXED: FP32 GEMV; MIXED_TC: tensor-core GEMM when n_rhs > 1).  Asynchronous on
+ * `stream`, except the tensor-core path, which waits for the stream to read the kernel's error word and
+ * returns BEM_ETIMEOUT if one of its bounded waits expired. */
 BEM_API bem_status bem_matvec(bem_problem* p, int n_rhs, const bem_c64* x_dev, bem_c64* y_dev, void* stream);
 
 /* Step a9's residual: r = b - A x for n_rhs columns with the solver's FP64-accurate operator (FP64 path:

@@ -86,7 +86,7 @@ struct bem_problem {
   int n = 0;
   bool geom_dirty = true;
   bool mat_dirty = true;
-  // device geometry: ax ay bx by mx my tx ty h (9n doubles), P M (2n ints)
+  // device geometry: ax ay bx by mx my tx ty h (9n doubles), their double-float copies (6n floats), P M
   double* d_geom = nullptr;
   int* d_pm = nullptr;
   size_t geom_cap = 0;
@@ -111,6 +111,8 @@ struct bem_problem {
     e.ax = d_geom; e.ay = d_geom + n; e.bx = d_geom + 2 * n; e.by = d_geom + 3 * n;
     e.mx = d_geom + 4 * n; e.my = d_geom + 5 * n; e.tx = d_geom + 6 * n; e.ty = d_geom + 7 * n;
     e.h = d_geom + 8 * n;
+    float* f = reinterpret_cast<float*>(d_geom + 9 * n);
+    e.txh = f; e.txl = f + n; e.tyh = f + 2 * n; e.tyl = f + 3 * n; e.hhh = f + 4 * n; e.hhl = f + 5 * n;
     e.P = d_pm; e.M = d_pm + n;
     return e;
   }
@@ -172,7 +174,7 @@ bem_status upload_geometry(bem_problem* p, cudaStream_t s) {
     p->d_geom = nullptr;
     p->d_pm = nullptr;
     p->geom_cap = 0;
-    CU(cudaMalloc(&p->d_geom, (size_t)9 * n * sizeof(double)));
+    CU(cudaMalloc(&p->d_geom, (size_t)12 * n * sizeof(double)));   // 9n doubles + 6n floats
     CU(cudaMalloc(&p->d_pm, (size_t)2 * n * sizeof(int)));
     p->geom_cap = n;
   }
@@ -359,22 +361,29 @@ bem_status gmres_run(bem_problem* p, Solver& sv, const double2* r0, double2* x, 
   }
   const bool fp32 = st.basis_fp32;
   const size_t tb = fp32 ? sizeof(float2) : sizeof(double2);
+  const bool use_tc = fp32 && p->o.prec == BEM_PREC_MIXED_TC && nrhs > 1 && matvec_tc_supported(n2, nrhs);
+  if (use_tc) CU(matvec_tc_clear_error(sv.tcws, n2, nrhs, s));
+  // Iterations are queued kSyncEvery at a time before the host reads the active count: the GPU never
+  // waits for the host between iterations.  Once every system has converged, the queued iterations find
+  // their gates closed (n_active = 0, active flags cleared) and return at once.
+  constexpr int kSyncEvery = 4;
+  const int* gate = st.n_active;
   for (int j = 0; j < st.m; ++j) {
     void* Vj = static_cast<char*>(st.V) + (size_t)j * nrhs * n2 * tb;
     {
     Phase ph(p, BEM_PH_MATVEC, s, 1);
     if (p->o.matrix_free) {
       CU(launch_matvec_free(p->elem(), p->n, p->dom, make_quad(p->o.quad_order), p->o.form, nrhs,
-                            static_cast<const double2*>(Vj), static_cast<double2*>(st.W), s));
+                            static_cast<const double2*>(Vj), static_cast<double2*>(st.W), s, gate));
     } else if (!fp32) {
       CU(launch_matvec_c64(static_cast<const double2*>(p->d_A), n2, n2, nrhs, static_cast<const double2*>(Vj),
-                           static_cast<double2*>(st.W), s));
-    } else if (p->o.prec == BEM_PREC_MIXED_TC && nrhs > 1 && matvec_tc_supported(n2, nrhs)) {
+                           static_cast<double2*>(st.W), s, gate));
+    } else if (use_tc) {
       CU(launch_matvec_tc(static_cast<const float2*>(p->d_A), n2, n2, nrhs, static_cast<const float2*>(Vj),
-                          static_cast<float2*>(st.W), sv.tcws, sv.tcws_bytes, s));
+                          static_cast<float2*>(st.W), sv.tcws, sv.tcws_bytes, s, gate));
     } else {
       CU(launch_matvec_c32(static_cast<const float2*>(p->d_A), n2, n2, nrhs, static_cast<const float2*>(Vj),
-                           static_cast<float2*>(st.W), st.active, s));
+                           static_cast<float2*>(st.W), st.active, s, gate));
     }
     }
     {
@@ -387,9 +396,11 @@ bem_status gmres_run(bem_problem* p, Solver& sv, const double2* r0, double2* x, 
       Phase ph(p, BEM_PH_GIVENS, s, 3);
       CU(krylov_finish_step(st, tol, j, s));
     }
-    CU(cudaMemcpyAsync(p->h_pin, st.n_active, sizeof(int), cudaMemcpyDeviceToHost, s));
-    CU(cudaStreamSynchronize(s));
-    if (p->h_pin[0] == 0) break;
+    if ((j + 1) % kSyncEvery == 0) {
+      CU(cudaMemcpyAsync(p->h_pin, st.n_active, sizeof(int), cudaMemcpyDeviceToHost, s));
+      CU(cudaStreamSynchronize(s));
+      if (p->h_pin[0] == 0) break;
+    }
   }
   {
     Phase ph(p, BEM_PH_UPDATE, s, 2);
@@ -400,7 +411,7 @@ bem_status gmres_run(bem_problem* p, Solver& sv, const double2* r0, double2* x, 
   CU(cudaMemcpyAsync(it.data(), st.iters, nrhs * sizeof(int), cudaMemcpyDeviceToHost, s));
   CU(cudaMemcpyAsync(rs.data(), st.resid, nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
   int tc_err = 0;
-  if (fp32 && p->o.prec == BEM_PREC_MIXED_TC && nrhs > 1 && matvec_tc_supported(n2, nrhs))
+  if (use_tc)
     CU(cudaMemcpyAsync(&tc_err, matvec_tc_error_word(sv.tcws, n2, nrhs), sizeof(int), cudaMemcpyDeviceToHost, s));
   CU(cudaStreamSynchronize(s));
   if (tc_err) return fail(BEM_ETIMEOUT, "tensor-core GEMM wait expired (code %d)", tc_err);
@@ -518,7 +529,24 @@ Quad make_quad_host(int Q) {
   Quad q{};
   q.Q = Q;
   gauss_legendre(Q, q.t, q.w);
+  for (int m = 0; m < Q; ++m) {
+    q.wh[m] = (float)q.w[m];
+    q.wl[m] = (float)(q.w[m] - (double)q.wh[m]);
+  }
   return q;
+}
+
+void domtab_finish(DomTab& d) {
+  auto split = [](double v, float& h, float& l) {
+    h = (float)v;
+    l = (float)(v - (double)h);
+  };
+  for (int i = 0; i < d.n; ++i) {
+    split(d.k[i], d.kh[i], d.kl[i]);
+    split(d.eps[i], d.eh[i], d.el[i]);
+    split(-1.0 / (d.k[0] * d.eps[i]), d.gh[i], d.gl[i]);
+  }
+  split(1.0 / d.k[0], d.ik1h, d.ik1l);
 }
 bool problem_mixed_matrix(bem_problem* p, const float2** hi, const float2** lo, int* n2) {
   if (!p || !p->mixed() || p->mat_dirty || p->A_mixed != 1 || !p->d_A || !p->d_Alo) return false;
@@ -631,6 +659,7 @@ BEM_API bem_status bem_set_domains(bem_problem* p, int n_dom, const double* k, c
     p->dom.k[d] = k[d];
     p->dom.eps[d] = eps[d];
   }
+  domtab_finish(p->dom);
   p->mat_dirty = true;
   return BEM_OK;
 }
@@ -725,7 +754,12 @@ BEM_API bem_status bem_matvec(bem_problem* p, int n_rhs, const bem_c64* x_dev, b
   {
     Phase ph(p, BEM_PH_MATVEC, s, 1);
     if (p->o.prec == BEM_PREC_MIXED_TC && n_rhs > 1 && matvec_tc_supported(n2, n_rhs)) {
+      CU(matvec_tc_clear_error(sv.tcws, n2, n_rhs, s));
       CU(launch_matvec_tc(static_cast<const float2*>(p->d_A), n2, n2, n_rhs, xf, yf, sv.tcws, sv.tcws_bytes, s));
+      int tc_err = 0;
+      CU(cudaMemcpyAsync(&tc_err, matvec_tc_error_word(sv.tcws, n2, n_rhs), sizeof(int), cudaMemcpyDeviceToHost, s));
+      CU(cudaStreamSynchronize(s));
+      if (tc_err) return fail(BEM_ETIMEOUT, "tensor-core GEMM wait expired (code %d)", tc_err);
     } else {
       CU(launch_matvec_c32(static_cast<const float2*>(p->d_A), n2, n2, n_rhs, xf, yf, nullptr, s));
     }

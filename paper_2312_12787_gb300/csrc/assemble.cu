@@ -8,41 +8,16 @@
 // 3dom_calderon_bie with gamma = alpha/eps) or one of the comparison forms.
 //
 // One thread owns one element pair (i, j) and writes its four entries A[i, j], A[i, N+j],
-// A[N+i, j], A[N+i, N+j]; a warp spans 32 consecutive columns, so every store is a coalesced
-// 32-entry row segment.  All kernel arithmetic is FP64 (the FP64 pipe bounds this kernel); the mixed
-// path rounds each entry to complex FP32 and keeps the FP32 rounding remainder as a second matrix.
+// A[N+i, j], A[N+i, N+j] (pair.cuh); a warp spans 32 consecutive columns, so every store is a coalesced
+// 32-entry row segment.  The node geometry and the phase k r are FP64, the rest double-float on the FP32
+// pipe; the mixed path stores the double-float entry as complex FP32 (hi) plus its FP32 remainder (lo).
 #include "internal.cuh"
 #include "bessel.cuh"
+#include "pair.cuh"
 
 namespace bem {
 
 namespace {
-
-__device__ __forceinline__ double2 mul_i(double2 z) { return make_double2(-z.y, z.x); }
-
-struct RowEq {
-  int dom;        // domain whose equation this row carries
-  int bm;         // 1: Burton-Miller (standard + gamma * normal derivative), 0: standard
-  double2 scale;  // row multiplier
-};
-
-// Row plan of Sec. 5-6 for element with (P, M); half 0 = upper row, 1 = lower row.
-__device__ __forceinline__ RowEq row_eq(int form, int half, int P, int M, double k1) {
-  const double2 one = make_double2(1.0, 0.0);
-  const double2 malpha = make_double2(0.0, 1.0 / k1);   // -alpha = i/k_1
-  RowEq e;
-  if (form == BEM_FORM_CONV) {
-    if (half == 0) { e.dom = P; e.bm = (P == 0); e.scale = one; }
-    else { e.dom = M; e.bm = 0; e.scale = one; }
-  } else if (half == 0) {
-    e.dom = M; e.bm = 0; e.scale = (form == BEM_FORM_BETA1) ? one : malpha;
-  } else {
-    e.dom = P;
-    if (form == BEM_FORM_ORIG && P != 0) { e.bm = 0; e.scale = malpha; }
-    else { e.bm = 1; e.scale = one; }
-  }
-  return e;
-}
 
 __global__ void k_elements(ElemDev e, int n) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -54,142 +29,32 @@ __global__ void k_elements(ElemDev e, int n) {
   e.ty[i] = dy / h;
   e.mx[i] = 0.5 * (e.ax[i] + e.bx[i]);
   e.my[i] = 0.5 * (e.ay[i] + e.by[i]);
+  const F2 tx = f2_from(dx / h), ty = f2_from(dy / h), hh = f2_from(0.5 * h);
+  e.txh[i] = tx.h; e.txl[i] = tx.l;
+  e.tyh[i] = ty.h; e.tyl[i] = ty.l;
+  e.hhh[i] = hh.h; e.hhl[i] = hh.l;
 }
 
-// Coefficients of one equation row at column j: cu multiplies u_j, cw multiplies w_j.
-//   standard:        cu = 1/2 d_ij + s D,                  cw = -s eps S
-//   Burton-Miller:   cu = 1/2 d_ij + s (D + gamma N),      cw = gamma eps/2 d_ij - s eps (S + gamma D*)
-// with s = sigma_{d,j}, gamma = alpha/eps_d, alpha = -i/k_1, and
-//   S = (i/4) sS,  D = (ik/4) sD,  D* = -(ik/4) sDs,  N = (ik/4) sN.
-struct PairSums { double2 sS, sD, sDs, sN; };
-
-// All four entries of element pair (i, j): out[half][0] multiplies u_j, out[half][1] multiplies w_j in
-// row half*N + i.
-__device__ __forceinline__ void assemble_pair(const ElemDev& e, const DomTab& dom, const Quad& q, int form, int i,
-                                              int j, double2 (&out)[2][2]) {
-  const double xi = e.mx[i], yi = e.my[i];
-  const double nxi = -e.ty[i], nyi = e.tx[i];
-  const int Pi = e.P[i], Mi = e.M[i];
-  const double mxj = e.mx[j], myj = e.my[j], txj = e.tx[j], tyj = e.ty[j], hj = e.h[j];
-  const int Pj = e.P[j], Mj = e.M[j];
-  const double k1 = dom.k[0];
-
-  RowEq eq[2];
-  double sg[2], kk[2], eps[2], gim[2];
-#pragma unroll
-  for (int half = 0; half < 2; ++half) {
-    eq[half] = row_eq(form, half, Pi, Mi, k1);
-    const int d = eq[half].dom;
-    sg[half] = (Pj == d) ? 1.0 : ((Mj == d) ? -1.0 : 0.0);
-    kk[half] = dom.k[d];
-    eps[half] = dom.eps[d];
-    gim[half] = -1.0 / (k1 * eps[half]);        // gamma = alpha/eps_d = i * gim
-  }
-
-  if (i == j) {
-#pragma unroll
-    for (int half = 0; half < 2; ++half) {
-      // exact self terms: S_ii = (i/(2k)) [int J0 + i int Y0] (0..ka), N_ii = k^2 S_ii - (ik/2) H1(ka), D = D* = 0
-      const double k = kk[half];
-      const double ka = 0.5 * k * hj;
-      double ij0, iy0;
-      int_j0_y0(ka, ij0, iy0);
-      const double2 S = make_double2(-iy0 / (2.0 * k), ij0 / (2.0 * k));
-      Bessel01 b;
-      bessel01(ka, b);
-      // -(ik/2) H1 = -(ik/2)(j1 + i y1) = (k/2) y1 - i (k/2) j1
-      const double2 N = make_double2(k * k * S.x + 0.5 * k * b.y1, k * k * S.y - 0.5 * k * b.j1);
-      double2 cu = make_double2(0.5, 0.0);
-      double2 cw = make_double2(-sg[half] * eps[half] * S.x, -sg[half] * eps[half] * S.y);
-      if (eq[half].bm) {
-        const double2 gN = make_double2(-gim[half] * N.y, gim[half] * N.x);
-        cu.x += sg[half] * gN.x; cu.y += sg[half] * gN.y;
-        cw.y += 0.5 * gim[half] * eps[half];
-      }
-      out[half][0] = cmul(eq[half].scale, cu);
-      out[half][1] = cmul(eq[half].scale, cw);
-    }
-  } else {
-    // Gauss-Legendre sums; the geometry of each node is shared by the two row domains
-    PairSums ps[2];
-#pragma unroll
-    for (int half = 0; half < 2; ++half) ps[half].sS = ps[half].sD = ps[half].sDs = ps[half].sN = make_double2(0, 0);
-    const double nxj = -tyj, nyj = txj;
-    const double nn = nxi * nxj + nyi * nyj;
-    const double half_h = 0.5 * hj;
-    for (int m = 0; m < q.Q; ++m) {
-      const double sq = half_h * q.t[m];
-      const double W = half_h * q.w[m];
-      const double zx0 = xi - (mxj + sq * txj), zy0 = yi - (myj + sq * tyj);
-      const double r2 = zx0 * zx0 + zy0 * zy0;
-      const double ir = rsqrt(r2);
-      const double r = r2 * ir;
-      const double ux = zx0 * ir, uy = zy0 * ir;
-      const double ci = ux * nxi + uy * nyi;   // zh . n_i
-      const double cj = ux * nxj + uy * nyj;   // zh . n_j
-#pragma unroll
-      for (int half = 0; half < 2; ++half) {
-        if (sg[half] == 0.0) continue;
-        const double k = kk[half];
-        Bessel01 b;
-        bessel01(k * r, b);
-        PairSums& p = ps[half];
-        p.sS.x += W * b.j0; p.sS.y += W * b.y0;
-        p.sD.x += W * cj * b.j1; p.sD.y += W * cj * b.y1;
-        if (eq[half].bm) {
-          p.sDs.x += W * ci * b.j1; p.sDs.y += W * ci * b.y1;
-          const double a1 = W * ir * (nn - 2.0 * ci * cj);
-          const double a0 = W * k * ci * cj;
-          p.sN.x += a1 * b.j1 + a0 * b.j0;
-          p.sN.y += a1 * b.y1 + a0 * b.y0;
-        }
-      }
-    }
-#pragma unroll
-    for (int half = 0; half < 2; ++half) {
-      double2 cu = make_double2(0.0, 0.0), cw = make_double2(0.0, 0.0);
-      if (sg[half] != 0.0) {
-        const double k = kk[half];
-        const double2 S = cscale(mul_i(ps[half].sS), 0.25);
-        const double2 D = cscale(mul_i(ps[half].sD), 0.25 * k);
-        cu = cscale(D, sg[half]);
-        cw = cscale(S, -sg[half] * eps[half]);
-        if (eq[half].bm) {
-          const double2 Ds = cscale(mul_i(ps[half].sDs), -0.25 * k);
-          const double2 N = cscale(mul_i(ps[half].sN), 0.25 * k);
-          const double2 gN = make_double2(-gim[half] * N.y, gim[half] * N.x);
-          const double2 gDs = make_double2(-gim[half] * Ds.y, gim[half] * Ds.x);
-          cu.x += sg[half] * gN.x; cu.y += sg[half] * gN.y;
-          cw.x -= sg[half] * eps[half] * gDs.x; cw.y -= sg[half] * eps[half] * gDs.y;
-        }
-      }
-      out[half][0] = cmul(eq[half].scale, cu);
-      out[half][1] = cmul(eq[half].scale, cw);
-    }
-  }
-}
-
+// Mixed store: the double-float entry (hi, lo) is already the complex FP32 rounding of the entry and the
+// FP32 rounding of its remainder; the FP64 store adds the two parts.
 template <int MIXED>
-__device__ __forceinline__ void store_pair(int n, int i, int j, const double2 (&out)[2][2], void* Aout, void* Aloout,
+__device__ __forceinline__ void store_pair(int n, int i, int j, const C2 (&out)[2][2], void* Aout, void* Aloout,
                                            size_t lda) {
   const size_t r0 = (size_t)i * lda, r1 = (size_t)(n + i) * lda;
+  const size_t idx[4] = {r0 + j, r0 + n + j, r1 + j, r1 + n + j};
+  const C2 v[4] = {out[0][0], out[0][1], out[1][0], out[1][1]};
   if (MIXED) {
     float2* A = static_cast<float2*>(Aout);
     float2* L = static_cast<float2*>(Aloout);
-    const size_t idx[4] = {r0 + j, r0 + n + j, r1 + j, r1 + n + j};
-    const double2 v[4] = {out[0][0], out[0][1], out[1][0], out[1][1]};
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
-      const float hx = (float)v[t].x, hy = (float)v[t].y;
-      A[idx[t]] = make_float2(hx, hy);
-      L[idx[t]] = make_float2((float)(v[t].x - (double)hx), (float)(v[t].y - (double)hy));
+      A[idx[t]] = make_float2(v[t].x.h, v[t].y.h);
+      L[idx[t]] = make_float2(v[t].x.l, v[t].y.l);
     }
   } else {
     double2* A = static_cast<double2*>(Aout);
-    A[r0 + j] = out[0][0];
-    A[r0 + n + j] = out[0][1];
-    A[r1 + j] = out[1][0];
-    A[r1 + n + j] = out[1][1];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) A[idx[t]] = c2_to(v[t]);
   }
 }
 
@@ -199,26 +64,28 @@ __global__ void __launch_bounds__(256) k_assemble(ElemDev e, int n, DomTab dom, 
   const int j = blockIdx.x * 32 + threadIdx.x;
   const int i = blockIdx.y * 8 + threadIdx.y;
   if (i >= n || j >= n) return;
-  double2 out[2][2];
-  assemble_pair(e, dom, q, form, i, j, out);
+  C2 out[2][2];
+  assemble_pair_f2(e, dom, q, form, i, j, out);
   store_pair<MIXED>(n, i, j, out, Aout, Aloout, lda);
 }
 
 // Matrix-free product y = A x (no stored matrix): each block owns 8 element rows (16 matrix rows i and
 // N + i); the 32 lanes of a warp stride over the element columns j, evaluate the four entries of (i, j) with
-// the assembly's own code and accumulate; a warp reduction gives the two row sums.  FP64 throughout.
+// the assembly's own code and accumulate; a warp reduction gives the two row sums (FP64 products and sums).
 __global__ void __launch_bounds__(256) k_matvec_free(ElemDev e, int n, DomTab dom, Quad q, int form,
-                                                      const double2* __restrict__ x, double2* __restrict__ y) {
+                                                      const double2* __restrict__ x, double2* __restrict__ y,
+                                                      const int* gate) {
+  if (gate && *gate == 0) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int i = blockIdx.x * 8 + warp;
   if (i >= n) return;
   double2 up = make_double2(0, 0), lo = make_double2(0, 0);
   for (int j = lane; j < n; j += 32) {
-    double2 out[2][2];
-    assemble_pair(e, dom, q, form, i, j, out);
+    C2 o2[2][2];
+    assemble_pair_f2(e, dom, q, form, i, j, o2);
     const double2 xu = x[j], xw = x[n + j];
-    up = cadd(up, cadd(cmul(out[0][0], xu), cmul(out[0][1], xw)));
-    lo = cadd(lo, cadd(cmul(out[1][0], xu), cmul(out[1][1], xw)));
+    up = cadd(up, cadd(cmul(c2_to(o2[0][0]), xu), cmul(c2_to(o2[0][1]), xw)));
+    lo = cadd(lo, cadd(cmul(c2_to(o2[1][0]), xu), cmul(c2_to(o2[1][1]), xw)));
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -252,8 +119,8 @@ __global__ void __launch_bounds__(32 * TY) k_assemble_batched(const AsmJob* __re
   const int j = tx * 32 + threadIdx.x;
   const int i = ty * TY + threadIdx.y;
   if (i >= jb.n || j >= jb.n) return;
-  double2 out[2][2];
-  assemble_pair(jb.e, jb.dom, q, form, i, j, out);
+  C2 out[2][2];
+  assemble_pair_f2(jb.e, jb.dom, q, form, i, j, out);
   store_pair<MIXED>(jb.n, i, j, out, jb.A, jb.Alo, (size_t)2 * jb.n);
 }
 
@@ -421,9 +288,10 @@ cudaError_t launch_assemble(const ElemDev& e, int n, const DomTab& dom, const Qu
 }
 
 cudaError_t launch_matvec_free(const ElemDev& e, int n, const DomTab& dom, const Quad& q, int form, int nrhs,
-                               const double2* x, double2* y, cudaStream_t s) {
+                               const double2* x, double2* y, cudaStream_t s, const int* gate) {
   for (int r = 0; r < nrhs; ++r)
-    k_matvec_free<<<(n + 7) / 8, 256, 0, s>>>(e, n, dom, q, form, x + (size_t)r * 2 * n, y + (size_t)r * 2 * n);
+    k_matvec_free<<<(n + 7) / 8, 256, 0, s>>>(e, n, dom, q, form, x + (size_t)r * 2 * n, y + (size_t)r * 2 * n,
+                                              gate);
   return cudaGetLastError();
 }
 

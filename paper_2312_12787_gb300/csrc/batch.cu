@@ -16,6 +16,7 @@
 #include <cstring>
 #include <vector>
 
+#include "givens.cuh"
 #include "internal.cuh"
 
 namespace bem {
@@ -219,19 +220,14 @@ __global__ void __launch_bounds__(32) kv_finish(VDev d) {
     if (i < j) { sh_c[i] = cs[i]; sh_s[i] = sn[i]; }
   }
   __syncwarp();
+  const double2 a = warp_rotate_column(sh_h, sh_c, sh_s, j);
+  for (int i = lane; i < j; i += 32) Hj[i] = sh_h[i];
   if (lane != 0) return;
   const double hn = sqrt(t);
-  double2 a = sh_h[0];
-  for (int i = 0; i < j; ++i) {
-    const double2 b = sh_h[i + 1];
-    sh_h[i] = cadd(cdotc(sh_c[i], a), cdotc(sh_s[i], b));
-    a = csub(cmul(sh_c[i], b), cmul(sh_s[i], a));
-  }
   const double den = hypot(hypot(a.x, a.y), hn);
   double2 c, sv;
   if (den == 0.0) { c = make_double2(1, 0); sv = make_double2(0, 0); }
   else { c = cscale(a, 1.0 / den); sv = make_double2(hn / den, 0.0); }
-  for (int i = 0; i < j; ++i) Hj[i] = sh_h[i];
   cs[j] = c;
   sn[j] = sv;
   Hj[j] = make_double2(den, 0.0);
@@ -310,20 +306,13 @@ __global__ void __launch_bounds__(kCh) kv_start_scale(VDev d) {
   vbase(d, s)[k] = make_float2((float)(r.x * inv), (float)(r.y * inv));
 }
 
-// y = H^-1 g (back substitution), one thread per flagged slot
-__global__ void kv_lsq(VDev d) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+// y = H^-1 g (back substitution), one CTA per flagged slot
+__global__ void __launch_bounds__(kBsThreads) kv_lsq(VDev d) {
+  __shared__ double2 sg[kMaxM], sinv[kMaxM], sy;
+  const int s = blockIdx.x;
   if (s >= d.cap || !d.flag[s]) return;
-  const int mm = d.iters[s];
-  const double2* g = d.g + (size_t)s * (d.m + 1);
-  double2* y = d.y + (size_t)s * d.m;
-  for (int i = mm - 1; i >= 0; --i) {
-    double2 acc = g[i];
-    for (int l = i + 1; l < mm; ++l) acc = csub(acc, cmul(d.H[((size_t)s * d.m + l) * (d.m + 1) + i], y[l]));
-    const double2 dd = d.H[((size_t)s * d.m + i) * (d.m + 1) + i];
-    const double q = dd.x * dd.x + dd.y * dd.y;
-    y[i] = make_double2((acc.x * dd.x + acc.y * dd.y) / q, (acc.y * dd.x - acc.x * dd.y) / q);
-  }
+  block_back_substitute(d.H + (size_t)s * d.m * (d.m + 1), d.m + 1, d.g + (size_t)s * (d.m + 1),
+                        d.y + (size_t)s * d.m, d.iters[s], sg, sinv, &sy);
 }
 
 // x += V y (FP64 x); 64 entries x 4 subsets of i per block
@@ -627,7 +616,7 @@ bem_status refine_finished(bem_batch* b) {
   for (int s : fin) e.h_flag[s] = 1;
   BCU(cudaMemcpyAsync(e.flag, e.h_flag, e.cap * sizeof(int), cudaMemcpyHostToDevice, e.st));
   const VDev d = view(e);
-  kv_lsq<<<(e.cap + 63) / 64, 64, 0, e.st>>>(d);
+  kv_lsq<<<e.cap, kBsThreads, 0, e.st>>>(d);
   kv_xupdate<<<e.nchunks, 256, 0, e.st>>>(d);
   kv_split<<<e.nchunks, kCh, 0, e.st>>>(d);
   kv_resid<<<e.nrb, 256, 0, e.st>>>(d);

@@ -13,6 +13,8 @@
 // Double precision throughout; the accuracy target is ~1e-15 relative to |H|.
 #pragma once
 
+#include <cstring>
+
 #if defined(__CUDACC__)
 #define BEM_HD __host__ __device__ __forceinline__
 #else
@@ -160,6 +162,34 @@ BEM_HD F2 f2_from(double d) {
   return F2{h, (float)(d - (double)h)};
 }
 BEM_HD double f2_to(F2 a) { return (double)a.h + (double)a.l; }
+
+// The split of f2_from done with integer operations only: hi = d truncated to a float's 24 significant bits,
+// lo = the remaining 29 mantissa bits rounded to a float (|d - hi - lo| <= 2^-47 |d|).  On GB300 the
+// conversions of f2_from run on the FP64 pipe; this form keeps them off it.  For |d| < 2^-126 the result is
+// (0, 0) and for |d| < 2^-74 lo is 0 (an absolute error below 2^-97); |d| must be below 2^128.
+BEM_HD F2 f2_from_bits(double d) {
+#if defined(__CUDA_ARCH__)
+  const unsigned hi32 = (unsigned)__double2hiint(d), lo32 = (unsigned)__double2loint(d);
+#else
+  unsigned long long b;
+  memcpy(&b, &d, sizeof b);
+  const unsigned hi32 = (unsigned)(b >> 32), lo32 = (unsigned)b;
+#endif
+  const int e = (int)((hi32 >> 20) & 0x7ffu);
+  if (e < 897) return F2{0.f, 0.f};
+  const unsigned sign = hi32 & 0x80000000u;
+  const unsigned hb = sign | ((unsigned)(e - 896) << 23) | ((hi32 & 0xfffffu) << 3) | (lo32 >> 29);
+  const unsigned sb = e >= 949 ? (sign | ((unsigned)(e - 948) << 23)) : sign;   // +-2^(e-1075), or +-0
+  const float rem = (float)(lo32 & 0x1fffffffu);
+#if defined(__CUDA_ARCH__)
+  return F2{__uint_as_float(hb), rem * __uint_as_float(sb)};
+#else
+  float hf, sf;
+  memcpy(&hf, &hb, sizeof hf);
+  memcpy(&sf, &sb, sizeof sf);
+  return F2{hf, rem * sf};
+#endif
+}
 
 // +-1/k for the Neumann sums, as double-float constants folded at compile time
 struct MillerCoefF2 {
@@ -337,8 +367,9 @@ constexpr AsympCoefF2 make_asymp_coef_f2() {
   return c;
 }
 
+// Horner sum of the first T coefficients (T <= BEM_ASYMP_TERMS / 2)
+template <int T = BEM_ASYMP_TERMS / 2>
 BEM_HD F2 f2_horner(const F2Coef& c, F2 u) {
-  constexpr int T = BEM_ASYMP_TERMS / 2;
   F2 acc{c.h[T - 1], c.l[T - 1]};
 #pragma unroll
   for (int m = T - 2; m >= 0; --m) acc = f2_add(f2_mul(acc, u), F2{c.h[m], c.l[m]});
@@ -395,6 +426,215 @@ BEM_HD void bessel01(double x, Bessel01& b) {
   if (x < BEM_X_SERIES) bessel01_series(x, b);
   else if (x < BEM_X_ASYMP) bessel01_miller_f2(x, b);
   else bessel01_asymp_f2(x, b);
+}
+
+// ---- results in double-float ----------------------------------------------------------------------
+// The assembly accumulates its Gauss sums in double-float, so the three branches below hand their results
+// over in that form and skip the conversions back to FP64.  x (FP64) selects the branch and, in the
+// expansion, fixes the phase (the reduction of x by pi/2 needs all of FP64's bits when k r reaches ~100);
+// X = x in double-float carries everything that only needs relative accuracy (amplitudes, 1/x).
+struct Bessel01F2 {
+  F2 j0, y0, j1, y1;
+};
+
+BEM_HD F2 f2_sub(F2 a, F2 b) { return f2_add(a, f2_neg(b)); }
+BEM_HD F2 f2_pow2(F2 a, float s) { return F2{a.h * s, a.l * s}; }   // s a power of two: exact
+
+BEM_HD float f32_rsqrt_seed(float v) {
+#if defined(__CUDA_ARCH__)
+  return rsqrtf(v);
+#else
+  return 1.0f / sqrtf(v);
+#endif
+}
+BEM_HD float f32_rcp_seed(float v) {
+#if defined(__CUDA_ARCH__)
+  return __frcp_rn(v);
+#else
+  return 1.0f / v;
+#endif
+}
+
+// 1/sqrt(a), a > 0: an FP32 estimate refined by two Newton steps y <- y + y (1 - a y^2) / 2 in double-float
+// (each step squares the relative error: ~1e-7 -> ~1e-14 -> double-float rounding).
+BEM_HD F2 f2_rsqrt(F2 a) {
+  F2 y{f32_rsqrt_seed(a.h), 0.f};
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const F2 e = f2_sub(F2{1.f, 0.f}, f2_mul(a, f2_mul(y, y)));
+    y = f2_add(y, f2_mul(y, f2_pow2(e, 0.5f)));
+  }
+  return y;
+}
+// 1/a, a != 0: Newton steps y <- y + y (1 - a y).
+BEM_HD F2 f2_rcp(F2 a) {
+  F2 y{f32_rcp_seed(a.h), 0.f};
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const F2 e = f2_sub(F2{1.f, 0.f}, f2_mul(a, y));
+    y = f2_add(y, f2_mul(y, e));
+  }
+  return y;
+}
+
+// Coefficient tables of the ascending series (DLMF 10.2.2, 10.8.1): 1/m^2, 1/(m(m+1)) and the harmonic
+// numbers H_m, so that the loop multiplies instead of dividing.
+constexpr int kSeriesTerms = 14;   // x < 2: t = x^2/4 < 1, so the last term t^13/(13!)^2 < 3e-20
+struct SeriesCoef {
+  double inv_mm[kSeriesTerms], inv_mm1[kSeriesTerms], hm[kSeriesTerms + 1];
+};
+constexpr SeriesCoef make_series_coef() {
+  SeriesCoef c{};
+  c.hm[0] = 0.0;
+  for (int m = 1; m < kSeriesTerms; ++m) {
+    c.inv_mm[m] = 1.0 / ((double)m * (double)m);
+    c.inv_mm1[m] = 1.0 / ((double)m * (double)(m + 1));
+  }
+  for (int m = 1; m <= kSeriesTerms; ++m) c.hm[m] = c.hm[m - 1] + 1.0 / (double)m;
+  return c;
+}
+
+// The ascending series of bessel01_series with tabulated coefficients, in FP64 (x < 2, a few per cent of
+// the evaluations), converted to double-float.
+BEM_HD void bessel01_series_f2(double x, Bessel01F2& b) {
+  constexpr SeriesCoef C = make_series_coef();
+  const double t = 0.25 * x * x;
+  double e0 = 1.0, e1 = 1.0, sj0 = 1.0, sj1 = 1.0, sy0 = 0.0, sy1 = 1.0;
+#pragma unroll   // a fixed count: constant indices make the coefficients immediates (no table in memory)
+  for (int m = 1; m < kSeriesTerms; ++m) {
+    e0 *= -t * C.inv_mm[m];
+    e1 *= -t * C.inv_mm1[m];
+    sj0 += e0;
+    sj1 += e1;
+    sy0 -= e0 * C.hm[m];
+    sy1 += e1 * (C.hm[m] + C.hm[m + 1]);
+  }
+  const double lg = log(0.5 * x) + kEulerGamma;
+  const double j1 = 0.5 * x * sj1;
+  b.j0 = f2_from(sj0);
+  b.j1 = f2_from(j1);
+  b.y0 = f2_from(kTwoOverPi * (lg * sj0 + sy0));
+  b.y1 = f2_from(-kTwoOverPi / x + kTwoOverPi * lg * j1 - (0.5 * x / kPi) * sy1);
+}
+
+constexpr F2 f2_const(double v) { return F2{(float)v, (float)(v - (double)(float)v)}; }
+
+// Miller's algorithm as bessel01_miller_f2 with the normalisation, 2/x and the Neumann sums also in
+// double-float; only ln(x/2) is FP64.
+BEM_HD void bessel01_miller_f2x(double x, F2 X, Bessel01F2& b, int start = BEM_MILLER_START) {
+  constexpr MillerCoefF2 C = make_miller_coef_f2();
+  const F2 tox = f2_pow2(f2_rcp(X), 2.f);
+  F2 fp{0.f, 0.f}, f{0x1p-30f, 0.f}, norm{0.f, 0.f}, sy0{0.f, 0.f}, sy1{0.f, 0.f}, fodd{0.f, 0.f};
+#pragma unroll
+  for (int n = BEM_MILLER_START; n >= 1; --n) {
+    if (n > start) continue;   // start: even, <= BEM_MILLER_START
+    if ((n & 1) == 0) {
+      const int kk = n >> 1;
+      norm = f2_add(norm, f);
+      sy0 = f2_add(sy0, f2_mul(f, F2{C.h[kk], C.l[kk]}));
+      fodd = fp;
+    } else {
+      const int kk = (n + 1) >> 1;
+      sy1 = f2_add(sy1, f2_mul(f2_sub(f, fodd), F2{C.h[kk], C.l[kk]}));
+    }
+    const F2 cn = f2_mulf(tox, (float)n);
+    const F2 fm = f2_sub(f2_mul(cn, f), fp);
+    fp = f;
+    f = fm;
+    if ((n & 3) == 1 && fabsf(f.h) > 0x1p40f) {
+      const float sc = 0x1p-40f;
+      f = f2_pow2(f, sc); fp = f2_pow2(fp, sc);
+      norm = f2_pow2(norm, sc); sy0 = f2_pow2(sy0, sc);
+      sy1 = f2_pow2(sy1, sc); fodd = f2_pow2(fodd, sc);
+    }
+  }
+  constexpr F2 kTwoPi = f2_const(kTwoOverPi);
+  const F2 s = f2_rcp(f2_add(f, f2_pow2(norm, 2.f)));
+  const F2 j0 = f2_mul(f, s), j1 = f2_mul(fp, s);
+  const F2 lg = f2_from_bits(log(0.5 * x) + kEulerGamma);
+  b.j0 = j0;
+  b.j1 = j1;
+  // Y0 = (2/pi) [lg J0 - 2 sy0 s];  Y1 = (2/pi) [lg J1 - J0 / x + sy1 s]
+  b.y0 = f2_mul(kTwoPi, f2_sub(f2_mul(lg, j0), f2_pow2(f2_mul(sy0, s), 2.f)));
+  b.y1 = f2_mul(kTwoPi, f2_add(f2_sub(f2_mul(lg, j1), f2_mul(j0, f2_pow2(tox, 0.5f))), f2_mul(sy1, s)));
+}
+
+// Hankel's expansion as bessel01_asymp_f2, with 1/sqrt(x) and 1/x from X in double-float.
+BEM_HD void bessel01_asymp_f2x(double x, F2 X, Bessel01F2& b) {
+  constexpr AsympCoefF2 C = make_asymp_coef_f2();
+  constexpr double kPio2_1 = 0x1.921fb54400000p+0;    // pi/2 = kPio2_1 + kPio2_2 + kPio2_3 + O(1e-37)
+  constexpr double kPio2_2 = 0x1.0b4611a600000p-34;
+  constexpr double kPio2_3 = 0x1.3198a2e037073p-69;
+  const F2 rs = f2_rsqrt(X);
+  const F2 Y = f2_mul(rs, rs);
+  const F2 U = f2_mul(Y, Y);
+  // kq = x 2/pi rounded to an integer: adding 1.5 * 2^52 leaves it in the low bits of t (0 < x < 2^50)
+  const double t = fma(x, kTwoOverPi, 0x1.8p52);
+  const double kq = t - 0x1.8p52;
+  double r = fma(-kq, kPio2_1, x);
+  r = fma(-kq, kPio2_2, r);
+  r = fma(-kq, kPio2_3, r);
+#if defined(__CUDA_ARCH__)
+  const int quad = __double2loint(t) & 3;
+#else
+  unsigned long long tb;
+  memcpy(&tb, &t, sizeof tb);
+  const int quad = (int)(tb & 3u);
+#endif
+  const F2 R = f2_from_bits(r);
+  const F2 R2 = f2_mul(R, R);
+  F2 sp{C.sh[8], C.sl[8]};
+#pragma unroll
+  for (int k = 7; k >= 0; --k) sp = f2_add(f2_mul(sp, R2), F2{C.sh[k], C.sl[k]});
+  const F2 sr = f2_mul(sp, R);
+  F2 cr{C.ch[9], C.cl[9]};
+#pragma unroll
+  for (int k = 8; k >= 0; --k) cr = f2_add(f2_mul(cr, R2), F2{C.ch[k], C.cl[k]});
+  F2 sn, cs;
+  if (quad == 0) { sn = sr; cs = cr; }
+  else if (quad == 1) { sn = cr; cs = f2_neg(sr); }
+  else if (quad == 2) { sn = f2_neg(sr); cs = f2_neg(cr); }
+  else { sn = f2_neg(cr); cs = sr; }
+  // terms of the expansion: 22 below x = 25, 16 up to 35, 12 beyond (each keeps the truncation below
+  // 1e-15 of |H|); the tier is the one the smallest x of the warp's active lanes needs
+  float xmin = X.h;
+#if defined(__CUDA_ARCH__)
+  xmin = __int_as_float(__reduce_min_sync(__activemask(), __float_as_int(xmin)));   // x > 0: int order = float order
+#endif
+  F2 p0, p1, q0, q1;
+  if (xmin >= 35.f) {
+    p0 = f2_horner<6>(C.p0, U); p1 = f2_horner<6>(C.p1, U); q0 = f2_horner<6>(C.q0, U); q1 = f2_horner<6>(C.q1, U);
+  } else if (xmin >= 25.f) {
+    p0 = f2_horner<8>(C.p0, U); p1 = f2_horner<8>(C.p1, U); q0 = f2_horner<8>(C.q0, U); q1 = f2_horner<8>(C.q1, U);
+  } else {
+    p0 = f2_horner(C.p0, U); p1 = f2_horner(C.p1, U); q0 = f2_horner(C.q0, U); q1 = f2_horner(C.q1, U);
+  }
+  q0 = f2_mul(q0, Y);
+  q1 = f2_mul(q1, Y);
+  constexpr F2 kInvSqrtPi = f2_const(0.564189583547756286948079451560772586);
+  const F2 A = f2_mul(rs, kInvSqrtPi);
+  const F2 er = f2_mul(f2_add(cs, sn), A), ei = f2_mul(f2_sub(sn, cs), A);
+  b.j0 = f2_sub(f2_mul(p0, er), f2_mul(q0, ei));
+  b.y0 = f2_add(f2_mul(p0, ei), f2_mul(q0, er));
+  b.j1 = f2_add(f2_mul(p1, ei), f2_mul(q1, er));
+  b.y1 = f2_neg(f2_sub(f2_mul(p1, er), f2_mul(q1, ei)));
+}
+
+BEM_HD void bessel01_f2(double x, F2 X, Bessel01F2& b) {
+  if (X.h < (float)BEM_X_SERIES) {
+    bessel01_series_f2(x, b);
+  } else if (X.h < (float)BEM_X_ASYMP) {
+    // even start order 1.6 x + 23 (rounded up): at least four orders beyond the smallest one that keeps
+    // the truncation of J0, J1, Y0, Y1 below 2e-16 of |H0| on [2, 18); the largest of the warp's active lanes
+    int start = 2 * (int)ceilf(0.8f * X.h + 11.5f);
+    start = start < BEM_MILLER_START ? start : BEM_MILLER_START;
+#if defined(__CUDA_ARCH__)
+    start = __reduce_max_sync(__activemask(), start);
+#endif
+    bessel01_miller_f2x(x, X, b, start);
+  } else {
+    bessel01_asymp_f2x(x, X, b);
+  }
 }
 
 // integral_0^x J0(t) dt and integral_0^x Y0(t) dt for the weakly singular self-element integral,

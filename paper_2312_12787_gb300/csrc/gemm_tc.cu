@@ -147,7 +147,8 @@ __device__ __forceinline__ float tf32_hi(float v) { return __uint_as_float(__flo
 __global__ void __launch_bounds__(kThreads, 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapBhi,
               const __grid_constant__ CUtensorMap mapBlo, int n, int ksteps_total, int nsplit, float* partial,
-              int* err) {
+              int* err, const int* gate) {
+  if (gate && *gate == 0) return;   // every system of the block has converged (uniform for the grid)
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   Bars* bars = reinterpret_cast<Bars*>(smem + kStages * kStage);
@@ -311,7 +312,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 // Bt rows (K-major, 2n FP32 each): row s < 64: (Re x_s[c], -Im x_s[c]); row 64+s: (Im x_s[c], Re x_s[c]);
 // rows of absent columns are zero.  Written as TF32-exact hi and lo = v - hi.
 __global__ void k_tc_prep_b(const float2* __restrict__ x, int n, int nrhs, float* __restrict__ bhi,
-                            float* __restrict__ blo) {
+                            float* __restrict__ blo, const int* gate) {
+  if (gate && *gate == 0) return;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;   // complex column index along K
   const int row = blockIdx.y;                             // 0..127
   if (c >= n) return;
@@ -329,7 +331,9 @@ __global__ void k_tc_prep_b(const float2* __restrict__ x, int n, int nrhs, float
 }
 
 // Y[s][r] = (sum_k P[k][r][s], sum_k P[k][r][64+s]) in FP32.
-__global__ void k_tc_reduce(const float* __restrict__ partial, int n, int nrhs, int nsplit, float2* __restrict__ y) {
+__global__ void k_tc_reduce(const float* __restrict__ partial, int n, int nrhs, int nsplit, float2* __restrict__ y,
+                            const int* gate) {
+  if (gate && *gate == 0) return;
   const int s = threadIdx.x & 63;
   const int r = blockIdx.x * (blockDim.x >> 6) + (threadIdx.x >> 6);
   if (r >= n || s >= nrhs) return;
@@ -412,8 +416,14 @@ int* matvec_tc_error_word(void* ws, int n, int nrhs) {
   return reinterpret_cast<int*>(w + 2 * (size_t)kN * 2 * n * 4 + (size_t)choose_split(n) * n * kN * 4);
 }
 
+cudaError_t matvec_tc_clear_error(void* ws, int n, int nrhs, cudaStream_t s) {
+  int* err = matvec_tc_error_word(ws, n, nrhs);
+  if (!err) return cudaErrorInvalidValue;
+  return cudaMemsetAsync(err, 0, sizeof(int), s);
+}
+
 cudaError_t launch_matvec_tc(const float2* A, size_t lda, int n, int nrhs, const float2* x, float2* y, void* ws,
-                             size_t ws_bytes, cudaStream_t s) {
+                             size_t ws_bytes, cudaStream_t s, const int* gate) {
   if (!matvec_tc_supported(n, nrhs) || lda != (size_t)n) return cudaErrorNotSupported;
   if (ws_bytes < matvec_tc_workspace_bytes(n, nrhs)) return cudaErrorInvalidValue;
   const int n2 = 2 * n;
@@ -432,13 +442,11 @@ cudaError_t launch_matvec_tc(const float2* A, size_t lda, int n, int nrhs, const
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int), s);
-  if (e != cudaSuccess) return e;
-  k_tc_prep_b<<<dim3((n + 255) / 256, kN), 256, 0, s>>>(x, n, nrhs, bhi, blo);
+  k_tc_prep_b<<<dim3((n + 255) / 256, kN), 256, 0, s>>>(x, n, nrhs, bhi, blo, gate);
   const int tiles = (n + kM - 1) / kM;
   const int ksteps = (n2 + kKs - 1) / kKs;
-  k_gemm_tc<<<dim3(tiles, nsplit), kThreads, kSmemBytes, s>>>(mA, mBh, mBl, n, ksteps, nsplit, part, err);
-  k_tc_reduce<<<(n + 3) / 4, 256, 0, s>>>(part, n, nrhs, nsplit, y);
+  k_gemm_tc<<<dim3(tiles, nsplit), kThreads, kSmemBytes, s>>>(mA, mBh, mBl, n, ksteps, nsplit, part, err, gate);
+  k_tc_reduce<<<(n + 3) / 4, 256, 0, s>>>(part, n, nrhs, nsplit, y, gate);
   return cudaGetLastError();
 }
 

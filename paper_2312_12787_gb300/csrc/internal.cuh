@@ -21,18 +21,28 @@ struct ElemDev {
   double* tx; double* ty;               // unit tangent
   double* h;                            // length
   const int* P; const int* M;           // domain the normal points out of / into
+  // double-float copies (hi, lo FP32 pairs) of the tangent and of half the length, for the assembly
+  float* txh; float* txl; float* tyh; float* tyl; float* hhh; float* hhl;
 };
 
 struct DomTab {
   int n;
   double k[kMaxDomains];
   double eps[kMaxDomains];
+  // double-float copies (hi, lo) of k_d, eps_d, gim_d = -1/(k_1 eps_d) and 1/k_1 (domtab_finish)
+  float kh[kMaxDomains], kl[kMaxDomains];
+  float eh[kMaxDomains], el[kMaxDomains];
+  float gh[kMaxDomains], gl[kMaxDomains];
+  float ik1h, ik1l;
 };
+// Fill the double-float copies of a DomTab from k and eps (host).
+void domtab_finish(DomTab& d);
 
 struct Quad {
   int Q;
   double t[kMaxQuad];
   double w[kMaxQuad];
+  float wh[kMaxQuad], wl[kMaxQuad];   // weights in double-float
 };
 
 // One problem of a batched assembly launch.
@@ -61,8 +71,10 @@ cudaError_t launch_elements(const ElemDev& e, int n, cudaStream_t s);
 cudaError_t launch_assemble(const ElemDev& e, int n, const DomTab& dom, const Quad& q, int form, int store_mixed,
                             void* A, void* Alo, size_t lda, cudaStream_t s);
 // y = A x without a stored matrix (entries recomputed in FP64), n elements, nrhs columns of 2n.
+// `gate` (optional, device int): when it reads 0 the product is skipped (every system of the block has
+// converged; the solver queues several iterations ahead of its convergence check).
 cudaError_t launch_matvec_free(const ElemDev& e, int n, const DomTab& dom, const Quad& q, int form, int nrhs,
-                               const double2* x, double2* y, cudaStream_t s);
+                               const double2* x, double2* y, cudaStream_t s, const int* gate = nullptr);
 // Tiles of a problem with n elements for tile height ty (4, 8 or 16 rows of element pairs x 32 columns).
 long long assemble_batched_tiles(int n, int ty);
 cudaError_t launch_assemble_batched(const AsmJob* jobs_dev, int njobs, const long long* tile_prefix_dev,
@@ -81,10 +93,10 @@ cudaError_t launch_matrix_to_c64(const void* A, const void* Alo, int mixed, int 
 
 // y[r] = A x[r] for nrhs columns; A is n x n row-major (lda).  FP64 path.
 cudaError_t launch_matvec_c64(const double2* A, size_t lda, int n, int nrhs, const double2* x, double2* y,
-                              cudaStream_t s);
+                              cudaStream_t s, const int* gate = nullptr);
 // y[r] = A x[r] with A complex FP32 (hi only), x and y complex FP32.
 cudaError_t launch_matvec_c32(const float2* A, size_t lda, int n, int nrhs, const float2* x, float2* y,
-                              const int* active, cudaStream_t s);
+                              const int* active, cudaStream_t s, const int* gate = nullptr);
 // r = b - (hi + lo) x, with FP64 x, b, r (refinement residual) in double-float arithmetic; ws must hold
 // 2 * nrhs * n float2.  The _f64 variant computes the same in FP64 arithmetic.
 cudaError_t launch_residual_split(const float2* Ahi, const float2* Alo, size_t lda, int n, int nrhs,
@@ -95,8 +107,11 @@ cudaError_t launch_residual_split_f64(const float2* Ahi, const float2* Alo, size
                                       const double2* x, const double2* b, double2* r, cudaStream_t s);
 // tcgen05 tensor-core GEMM Y = A X (A c32, X / Y c32, nrhs <= 64).  Returns cudaErrorNotSupported if the
 // shape is not supported by the kernel.
+// The kernel records a bounded-wait expiry in an error word inside ws and never clears it: callers clear it
+// (matvec_tc_clear_error) before a run of products and read it (matvec_tc_error_word) afterwards.
 cudaError_t launch_matvec_tc(const float2* A, size_t lda, int n, int nrhs, const float2* x, float2* y,
-                             void* ws, size_t ws_bytes, cudaStream_t s);
+                             void* ws, size_t ws_bytes, cudaStream_t s, const int* gate = nullptr);
+cudaError_t matvec_tc_clear_error(void* ws, int n, int nrhs, cudaStream_t s);
 size_t matvec_tc_workspace_bytes(int n, int nrhs);
 // Device word where the tensor-core kernel records a bounded-wait expiry (0 = none) inside ws.
 int* matvec_tc_error_word(void* ws, int n, int nrhs);

@@ -13,6 +13,7 @@
 // the update kernel four thread groups share the basis vectors of a chunk and meet in shared memory.
 #include <algorithm>
 
+#include "givens.cuh"
 #include "internal.cuh"
 
 namespace bem {
@@ -87,7 +88,10 @@ __global__ void k_start_finish(KrylovState st, int nblk) {
   st.iters[s] = 0;
   st.resid[s] = beta > 0.0 ? 1.0 : 0.0;
   st.hnext[s] = beta;
-  if (s == 0) *st.jdev = 0;
+  if (s == 0) {
+    *st.jdev = 0;
+    *st.n_active = st.nrhs;   // upper bound until the first k_advance
+  }
 }
 
 template <typename T>
@@ -196,9 +200,9 @@ __global__ void __launch_bounds__(kThreads) k_update(KrylovState st, int nchunk,
 }
 
 // h_{j+1,j} = ||w||; apply the previous Givens rotations to column j, form the new one, update g and
-// the residual estimate |g_{j+1}| / beta.  Rotation i acts on rows (i, i+1) as [[conj c, conj s], [-s, c]].
-// One warp per system: the lanes reduce the chunk norms and stage the column and the rotations in shared
-// memory; lane 0 then runs the (sequential) rotations from shared memory.
+// the residual estimate |g_{j+1}| / beta.  One warp per system: the lanes reduce the chunk norms, stage the
+// column and the rotations in shared memory and apply the rotations as a scan (warp_rotate_column); lane 0
+// then forms the new rotation.
 constexpr int kFinishMaxM = 1000;
 __global__ void __launch_bounds__(32) k_finish(KrylovState st, int nchunk, double tol, int j) {
   __shared__ double2 sh_h[kFinishMaxM + 1], sh_c[kFinishMaxM], sh_s[kFinishMaxM];
@@ -215,21 +219,14 @@ __global__ void __launch_bounds__(32) k_finish(KrylovState st, int nchunk, doubl
     if (i < j) { sh_c[i] = cs[i]; sh_s[i] = sn[i]; }
   }
   __syncwarp();
+  const double2 a = warp_rotate_column(sh_h, sh_c, sh_s, j);
+  for (int i = lane; i < j; i += 32) Hj[i] = sh_h[i];
   if (lane != 0) return;
   const double hn = sqrt(t);
-  double2 a = sh_h[0];
-  for (int i = 0; i < j; ++i) {
-    const double2 b = sh_h[i + 1];
-    const double2 ci = sh_c[i], si = sh_s[i];
-    sh_h[i] = cadd(cdotc(ci, a), cdotc(si, b));   // conj(c) a + conj(s) b
-    a = csub(cmul(ci, b), cmul(si, a));           // -s a + c b  (becomes row i+1)
-  }
-  const double2 b = make_double2(hn, 0.0);
   const double den = hypot(hypot(a.x, a.y), hn);
   double2 c, sv;
   if (den == 0.0) { c = make_double2(1, 0); sv = make_double2(0, 0); }
-  else { c = cscale(a, 1.0 / den); sv = cscale(b, 1.0 / den); }
-  for (int i = 0; i < j; ++i) Hj[i] = sh_h[i];
+  else { c = cscale(a, 1.0 / den); sv = make_double2(hn / den, 0.0); }
   cs[j] = c;
   sn[j] = sv;
   Hj[j] = make_double2(den, 0.0);
@@ -270,20 +267,13 @@ __global__ void k_advance(KrylovState st) {
   }
 }
 
-// Least squares: back-substitution of the triangularised Hessenberg system, one thread per system.
-__global__ void k_lsq(KrylovState st) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+// Least squares: back substitution of the triangularised Hessenberg system, one CTA per system.
+__global__ void __launch_bounds__(kBsThreads) k_lsq(KrylovState st) {
+  __shared__ double2 sg[kFinishMaxM], sinv[kFinishMaxM], sy;
+  const int s = blockIdx.x;
   if (s >= st.nrhs) return;
-  const int mm = st.iters[s];
-  const double2* g = st.g + (size_t)s * (st.m + 1);
-  double2* y = st.y + (size_t)s * st.m;
-  for (int i = mm - 1; i >= 0; --i) {
-    double2 acc = g[i];
-    for (int l = i + 1; l < mm; ++l) acc = csub(acc, cmul(st.H[((size_t)s * st.m + l) * (st.m + 1) + i], y[l]));
-    const double2 d = st.H[((size_t)s * st.m + i) * (st.m + 1) + i];
-    const double dd = d.x * d.x + d.y * d.y;
-    y[i] = make_double2((acc.x * d.x + acc.y * d.y) / dd, (acc.y * d.x - acc.x * d.y) / dd);
-  }
+  block_back_substitute(st.H + (size_t)s * st.m * (st.m + 1), st.m + 1, st.g + (size_t)s * (st.m + 1),
+                        st.y + (size_t)s * st.m, st.iters[s], sg, sinv, &sy);
 }
 
 // x += sum_i y_i v_i (FP64 x), same 64 x 4 decomposition as k_update.
@@ -347,7 +337,7 @@ cudaError_t finish_t(const KrylovState& st, double tol, int j, cudaStream_t s) {
 
 template <typename T>
 cudaError_t xupd_t(const KrylovState& st, double2* x, cudaStream_t s) {
-  k_lsq<<<(st.nrhs + 63) / 64, 64, 0, s>>>(st);
+  k_lsq<<<st.nrhs, kBsThreads, 0, s>>>(st);
   k_xupdate<T><<<dim3(nchunk_of(st.n), st.nrhs), kThreads, 0, s>>>(st, x);
   return cudaGetLastError();
 }

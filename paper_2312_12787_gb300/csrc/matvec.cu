@@ -12,6 +12,9 @@
 //  * k_gemm_f64   - Y = A X for several columns, SIMT tile 64 rows x 64 columns, FP64 arithmetic.
 //  * k_gemm_c32   - the same in complex FP32 with two-level FP32 accumulation.
 //  * k_resid_df_* - refinement residual b - (hi + lo) x in double-float arithmetic (see below).
+#include <algorithm>
+#include <atomic>
+
 #include "internal.cuh"
 
 namespace bem {
@@ -43,7 +46,8 @@ __device__ __forceinline__ double2 warp_sum(double2 v) {
 // y[s][r] = (RESID ? b[s][r] - : ) sum_c A[r][c] x[s][c]; grid.y = s
 template <class ALoad, bool RESID>
 __global__ void __launch_bounds__(256) k_gemv_f64(ALoad A, size_t lda, int n, const double2* x, const double2* b,
-                                                   double2* y) {
+                                                   double2* y, const int* gate) {
+  if (gate && *gate == 0) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int r = blockIdx.x * 8 + warp;
   const int s = blockIdx.y;
@@ -76,45 +80,87 @@ __global__ void __launch_bounds__(256) k_gemv_f64(ALoad A, size_t lda, int n, co
   }
 }
 
-// complex FP32: each lane takes two consecutive complex entries per step (one float4).
-// n must be even (it is: n = 2N).  grid.y = column; inactive columns are skipped.
+// complex FP32, up to NR right-hand sides per read of A.  One CTA per row at a time: its 256 threads split
+// the row into 16-byte pieces (two complex entries, columns 2c and 2c+1 for c = tid, tid + 256, ...), so a
+// row is 4 KB per step and a CTA finishes a row quickly.  CTAs stride over the rows (the grid fills every SM
+// exactly once), which leaves no partial second wave: with one warp per row, the 8192 rows of a 0.5 GB
+// matrix needed 1.12 waves and the tail cost a third of the bandwidth.  Products are FP32, folded into
+// FP64 every 16 steps; the warp sums go to shared memory and are combined in a fixed order (deterministic)
+// once per group of kGvGroup rows.  n must be even (it is: n = 2N); inactive columns are skipped.
+constexpr int kGvGroup = 16;
+template <int NR>
 __global__ void __launch_bounds__(256) k_gemv_c32(const float2* __restrict__ A, size_t lda, int n,
                                                    const float2* __restrict__ x, float2* __restrict__ y,
                                                    const int* __restrict__ active) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int r = blockIdx.x * 8 + warp;
-  const int s = blockIdx.y;
-  if (r >= n) return;
-  if (active && !active[s]) return;
-  const float4* row = reinterpret_cast<const float4*>(A + (size_t)r * lda);
-  const float4* xs = reinterpret_cast<const float4*>(x + (size_t)s * n);
-  const int n2 = n >> 1;   // float4 per row
-  double accx = 0.0, accy = 0.0;
-  int c = lane;
-  while (c < n2) {
-    float px = 0.f, py = 0.f;
-    // up to 16 steps of 32 lanes in FP32, then fold into FP64
-#pragma unroll 4
-    for (int t = 0; t < 16 && c < n2; ++t, c += 32) {
-      const float4 a = __ldcs(row + c);
-      const float4 v = __ldg(xs + c);
-      px = fmaf(a.x, v.x, px); px = fmaf(-a.y, v.y, px);
-      py = fmaf(a.x, v.y, py); py = fmaf(a.y, v.x, py);
-      px = fmaf(a.z, v.z, px); px = fmaf(-a.w, v.w, px);
-      py = fmaf(a.z, v.w, py); py = fmaf(a.w, v.z, py);
-    }
-    accx += (double)px;
-    accy += (double)py;
+  __shared__ double2 part[kGvGroup][8][NR];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  bool act[NR];
+  bool any = false;
+#pragma unroll
+  for (int s = 0; s < NR; ++s) {
+    act[s] = !active || active[s];
+    any = any || act[s];
   }
-  double2 acc = warp_sum(make_double2(accx, accy));
-  if (lane == 0) y[(size_t)s * n + r] = make_float2((float)acc.x, (float)acc.y);
+  if (!any) return;
+  const int n2 = n >> 1;   // float4 per row
+  const int G = gridDim.x;
+  for (int base = blockIdx.x; base < n; base += kGvGroup * G) {
+    int k = 0;
+    for (; k < kGvGroup && base + k * G < n; ++k) {
+      const int r = base + k * G;
+      const float4* row = reinterpret_cast<const float4*>(A + (size_t)r * lda);
+      double ax[NR], ay[NR];
+#pragma unroll
+      for (int s = 0; s < NR; ++s) ax[s] = ay[s] = 0.0;
+      int c = tid;
+      while (c < n2) {
+        float px[NR], py[NR];
+#pragma unroll
+        for (int s = 0; s < NR; ++s) px[s] = py[s] = 0.f;
+#pragma unroll 4
+        for (int t = 0; t < 16 && c < n2; ++t, c += 256) {
+          const float4 a = __ldcs(row + c);
+#pragma unroll
+          for (int s = 0; s < NR; ++s) {
+            const float4 v = __ldg(reinterpret_cast<const float4*>(x + (size_t)s * n) + c);
+            px[s] = fmaf(a.x, v.x, px[s]); px[s] = fmaf(-a.y, v.y, px[s]);
+            py[s] = fmaf(a.x, v.y, py[s]); py[s] = fmaf(a.y, v.x, py[s]);
+            px[s] = fmaf(a.z, v.z, px[s]); px[s] = fmaf(-a.w, v.w, px[s]);
+            py[s] = fmaf(a.z, v.w, py[s]); py[s] = fmaf(a.w, v.z, py[s]);
+          }
+        }
+#pragma unroll
+        for (int s = 0; s < NR; ++s) {
+          ax[s] += (double)px[s];
+          ay[s] += (double)py[s];
+        }
+      }
+#pragma unroll
+      for (int s = 0; s < NR; ++s) {
+        const double2 w = warp_sum(make_double2(ax[s], ay[s]));
+        if (lane == 0) part[k][warp][s] = w;
+      }
+    }
+    __syncthreads();
+    if (tid < k * NR) {
+      const int kk = tid / NR, s = tid % NR;
+      if (act[s]) {
+        double2 acc = part[kk][0][s];
+#pragma unroll
+        for (int w = 1; w < 8; ++w) acc = cadd(acc, part[kk][w][s]);
+        y[(size_t)s * n + base + kk * G] = make_float2((float)acc.x, (float)acc.y);
+      }
+    }
+    __syncthreads();
+  }
 }
 
 // SIMT tiled GEMM, FP64: Y[s][r] = sum_c A[r][c] X[s][c].  Tile 64 rows x 64 columns x 8, 256 threads,
 // each thread 4 rows x 4 columns (rows ty + 16 i, columns tx + 16 j).
 template <class ALoad, bool RESID>
 __global__ void __launch_bounds__(256) k_gemm_f64(ALoad A, size_t lda, int n, int nrhs, const double2* X,
-                                                   const double2* B, double2* Y) {
+                                                   const double2* B, double2* Y, const int* gate) {
+  if (gate && *gate == 0) return;
   constexpr int BR = 64, BS = 64, BK = 8;
   __shared__ double2 As[BK][BR + 1];
   __shared__ double2 Xs[BK][BS + 1];
@@ -171,7 +217,9 @@ __global__ void __launch_bounds__(256) k_gemm_f64(ALoad A, size_t lda, int n, in
 // SIMT tiled GEMM in complex FP32, same tiling; the inner FP32 accumulator is folded into a second FP32
 // accumulator every 64 columns to keep the summation error near FP32 rounding of short sums.
 __global__ void __launch_bounds__(256) k_gemm_c32(const float2* __restrict__ A, size_t lda, int n, int nrhs,
-                                                   const float2* __restrict__ X, float2* __restrict__ Y) {
+                                                   const float2* __restrict__ X, float2* __restrict__ Y,
+                                                   const int* gate) {
+  if (gate && *gate == 0) return;
   constexpr int BR = 64, BS = 64, BK = 8;
   __shared__ float2 As[BK][BR + 1];
   __shared__ float2 Xs[BK][BS + 1];
@@ -394,6 +442,25 @@ __global__ void k_b_minus(const double2* b, double2* r, size_t count) {
 
 }  // namespace
 
+// CTAs that fill every SM of the current device once (cached per device and width).
+static int gemv_c32_grid(int nrhs) {
+  constexpr int kGvMaxDevices = 64;
+  static std::atomic<int> cache[kGvMaxDevices][2];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kGvMaxDevices) return 0;
+  const int w = nrhs == 1 ? 0 : 1;
+  int g = cache[dev][w].load(std::memory_order_relaxed);
+  if (g > 0) return g;
+  int sms = 0, per = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  const cudaError_t e = w == 0 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_gemv_c32<1>, 256, 0)
+                               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_gemv_c32<2>, 256, 0);
+  if (e != cudaSuccess || per <= 0) return 0;
+  g = sms * per;
+  cache[dev][w].store(g, std::memory_order_relaxed);
+  return g;
+}
+
 cudaError_t launch_axpby_neg(const double2* b, double2* r, size_t count, cudaStream_t s) {
   k_b_minus<<<1024, 256, 0, s>>>(b, r, count);
   return cudaGetLastError();
@@ -413,26 +480,30 @@ cudaError_t launch_column_norms(const double2* v, int n, int ncol, double* out, 
 }
 
 cudaError_t launch_matvec_c64(const double2* A, size_t lda, int n, int nrhs, const double2* x, double2* y,
-                              cudaStream_t s) {
+                              cudaStream_t s, const int* gate) {
   LoadC64 ld{A};
   if (nrhs == 1) {
     dim3 grd((n + 7) / 8, 1);
-    k_gemv_f64<LoadC64, false><<<grd, 256, 0, s>>>(ld, lda, n, x, nullptr, y);
+    k_gemv_f64<LoadC64, false><<<grd, 256, 0, s>>>(ld, lda, n, x, nullptr, y, gate);
   } else {
     dim3 grd((n + 63) / 64, (nrhs + 63) / 64);
-    k_gemm_f64<LoadC64, false><<<grd, 256, 0, s>>>(ld, lda, n, nrhs, x, nullptr, y);
+    k_gemm_f64<LoadC64, false><<<grd, 256, 0, s>>>(ld, lda, n, nrhs, x, nullptr, y, gate);
   }
   return cudaGetLastError();
 }
 
 cudaError_t launch_matvec_c32(const float2* A, size_t lda, int n, int nrhs, const float2* x, float2* y,
-                              const int* active, cudaStream_t s) {
+                              const int* active, cudaStream_t s, const int* gate) {
   if (nrhs <= 2) {
-    dim3 grd((n + 7) / 8, nrhs);
-    k_gemv_c32<<<grd, 256, 0, s>>>(A, lda, n, x, y, active);
+    const int grd = std::min(n, gemv_c32_grid(nrhs));
+    if (grd <= 0) return cudaErrorInvalidValue;
+    if (nrhs == 1)
+      k_gemv_c32<1><<<grd, 256, 0, s>>>(A, lda, n, x, y, active);
+    else
+      k_gemv_c32<2><<<grd, 256, 0, s>>>(A, lda, n, x, y, active);
   } else {
     dim3 grd((n + 63) / 64, (nrhs + 63) / 64);
-    k_gemm_c32<<<grd, 256, 0, s>>>(A, lda, n, nrhs, x, y);
+    k_gemm_c32<<<grd, 256, 0, s>>>(A, lda, n, nrhs, x, y, gate);
   }
   return cudaGetLastError();
 }
@@ -458,10 +529,10 @@ cudaError_t launch_residual_c64(const double2* A, size_t lda, int n, int nrhs, c
   LoadC64 ld{A};
   if (nrhs == 1) {
     dim3 grd((n + 7) / 8, 1);
-    k_gemv_f64<LoadC64, true><<<grd, 256, 0, s>>>(ld, lda, n, x, b, r);
+    k_gemv_f64<LoadC64, true><<<grd, 256, 0, s>>>(ld, lda, n, x, b, r, nullptr);
   } else {
     dim3 grd((n + 63) / 64, (nrhs + 63) / 64);
-    k_gemm_f64<LoadC64, true><<<grd, 256, 0, s>>>(ld, lda, n, nrhs, x, b, r);
+    k_gemm_f64<LoadC64, true><<<grd, 256, 0, s>>>(ld, lda, n, nrhs, x, b, r, nullptr);
   }
   return cudaGetLastError();
 }
@@ -472,10 +543,10 @@ cudaError_t launch_residual_split_f64(const float2* Ahi, const float2* Alo, size
   LoadSplit ld{Ahi, Alo};
   if (nrhs == 1) {
     dim3 grd((n + 7) / 8, 1);
-    k_gemv_f64<LoadSplit, true><<<grd, 256, 0, s>>>(ld, lda, n, x, b, r);
+    k_gemv_f64<LoadSplit, true><<<grd, 256, 0, s>>>(ld, lda, n, x, b, r, nullptr);
   } else {
     dim3 grd((n + 63) / 64, (nrhs + 63) / 64);
-    k_gemm_f64<LoadSplit, true><<<grd, 256, 0, s>>>(ld, lda, n, nrhs, x, b, r);
+    k_gemm_f64<LoadSplit, true><<<grd, 256, 0, s>>>(ld, lda, n, nrhs, x, b, r, nullptr);
   }
   return cudaGetLastError();
 }
