@@ -31,17 +31,22 @@ sys.path.insert(0, ROOT)
 import workloads as W  # noqa: E402
 
 METRIC = "BEM solves/s (mixed vs FP64 GPU at err<=1e-6)"
-# Assembly roofline inputs (profiles/assemble_star3072.md): one k_assemble launch on the star
-# r = 1 + 0.3 cos 5t with N_e = 3072 issues 1.8383e9 thread operations on the FP64 pipe (node geometry, phase
-# reduction and what remains of the conversions; ncu sm__thread_inst_executed_pipe_fp64_pred_on.sum) and moves
-# 543.7 MB of DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum).  Both scale with the element pairs.
-# The FP64 pipe of a GB300 SM retires 2 thread operations per clock.
-ASM_FP64_PIPE_OPS_N3072 = 1.838292576e9
-ASM_DRAM_BYTES_N3072 = 542418688 + 1313280
-# Multi-RHS GEMM DRAM traffic per launch at N_e = 3072, 64 RHS (profiles/gemm_tc_star3072_64rhs.md), scaling
-# with the matrix entries.
-GEMM_DRAM_BYTES_N3072 = 314.7e6 + 4.0e6
-FP64_PIPE_PEAK_TOPS = 152 * 2 * 2.07e9 / 1e12
+# Roofline inputs, from ncu counts of one launch on the star r = 1 + 0.3 cos 5t with N_e = 3072 (64 RHS),
+# scaled to other sizes by the number of matrix entries (profiles/assemble_star3072.md,
+# profiles/gemm_tc_star3072_64rhs.md):
+#  * k_assemble issues 4.976e9 warp instructions (sm__inst_executed.sum) over both the FP64 pipe (node
+#    geometry, phase reduction) and the FP32 pipe (double-float Bessel arithmetic); neither pipe alone binds,
+#    so its roofline is the issue rate: 4 warp instructions per clock per SM.  DRAM traffic 549.1 MB.
+#  * the multi-RHS GEMM streams A once: 2 x 2 bytes per real entry; measured DRAM traffic 316.3 MB.
+#  * the refinement residual runs 44 FP32 operations per complex multiply-add (double-float dot product):
+#    FP32 pipe, 128 operations per clock per SM.
+ASM_WARP_INST_N3072 = 4.976357746e9
+ASM_DRAM_BYTES_N3072 = 547283456 + 1771008
+GEMM_DRAM_BYTES_N3072 = 311.3e6 + 5.0e6
+RESID_FP32_OPS_PER_CMAC = 44
+SM_COUNT, SM_CLOCK_HZ = 152, 2.07e9
+ISSUE_PEAK_G = SM_COUNT * 4 * SM_CLOCK_HZ / 1e9          # G warp instructions / s
+FP32_PEAK_T = SM_COUNT * 128 * SM_CLOCK_HZ / 1e12        # T FP32 thread operations / s
 UNIT = "solves/s"
 N_RHS = 64
 N_FF = 32
@@ -373,29 +378,37 @@ def main():
         e2e = {"value": N_RHS / (statistics.median(e2e_ms) / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h}
 
-    # ---- roofline of the dominant phase ----
+    # ---- roofline of the dominant kernel (the phase with the most device time among those with a model) ----
     hbm, src = _peaks()
-    ph, (ph_ms, ph_n) = max(prof.items(), key=lambda kv: kv[1][0])
+    models = ("assemble", "matvec", "residual")
+    ph, (ph_ms, ph_n) = max(((k, v) for k, v in prof.items() if k in models), key=lambda kv: kv[1][0])
     n2 = 2 * nel
-    avg_s = ph_ms / ph_n / 1e3
+    scale = (nel / 3072.0) ** 2
     roof = {"kernel": ph, "launches": ph_n, "avg_launch_ms": ph_ms / ph_n, "traffic": None}
     if ph == "assemble":
-        scale = (nel / 3072.0) ** 2
-        ops = ASM_FP64_PIPE_OPS_N3072 * scale
-        peak = FP64_PIPE_PEAK_TOPS
-        ach = ops / avg_s / 1e12
-        roof.update({"kernel": "k_assemble (FP64 pipe)", "bound": "alu", "achieved": ach, "peak": peak,
-                     "unit": "Top/s (FP64-pipe thread operations)", "frac": ach / peak,
+        avg_s = ph_ms / ph_n / 1e3
+        ach = ASM_WARP_INST_N3072 * scale / avg_s / 1e9
+        roof.update({"kernel": "k_assemble (issue-bound: FP64 geometry + double-float Bessel on FP32)", "bound": "alu",
+                     "achieved": ach, "peak": ISSUE_PEAK_G, "unit": "G warp instructions/s", "frac": ach / ISSUE_PEAK_G,
                      "traffic": ASM_DRAM_BYTES_N3072 * scale,
-                     "peak_source": "derived: 152 SMs x 2 FP64-pipe thread ops/clk x 2.07 GHz"})
+                     "peak_source": "derived: 152 SMs x 4 issue slots/clk x 2.07 GHz"})
     elif ph == "matvec":
-        bytes_per = n2 * n2 * 8 + 2 * N_RHS * n2 * 8          # A (complex FP32) + X + Y
+        avg_s = ph_ms / ph_n / 1e3
+        bytes_per = n2 * n2 * 8 + 2 * N_RHS * n2 * 8          # A (2 x FP16 per real entry) + X + Y
         ach = bytes_per / avg_s / 1e9
-        roof.update({"kernel": "matvec (tcgen05 3xTF32 multi-RHS GEMM)", "bound": "hbm", "achieved": ach,
-                     "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "peak_source": src,
-                     "traffic": GEMM_DRAM_BYTES_N3072 * (nel / 3072.0) ** 2 if N_RHS > 1 else None})
+        roof.update({"kernel": "matvec (tcgen05 FP16x3 multi-RHS GEMM, with its operand prep)", "bound": "hbm",
+                     "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "peak_source": src,
+                     "traffic": GEMM_DRAM_BYTES_N3072 * scale if N_RHS > 1 else None})
     else:
-        roof.update({"bound": "see DESIGN.md", "achieved": None, "peak": None, "unit": None, "frac": None})
+        # the residual phase holds two launches per refinement step: the split of x and the df product
+        n_gemm = max(1, ph_n // 2)
+        avg_s = ph_ms / n_gemm / 1e3
+        ops = RESID_FP32_OPS_PER_CMAC * n2 * n2 * N_RHS
+        ach = ops / avg_s / 1e12
+        roof.update({"kernel": "k_resid_df_gemm (double-float residual on the FP32 pipe)", "bound": "alu",
+                     "launches": n_gemm, "avg_launch_ms": ph_ms / n_gemm, "achieved": ach, "peak": FP32_PEAK_T,
+                     "unit": "T FP32 operations/s", "frac": ach / FP32_PEAK_T,
+                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz"})
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,

@@ -238,9 +238,9 @@ typedef enum {
   BEM_PH_ARNOLDI = 4,   /* a7: projections, updates, norms */
   BEM_PH_GIVENS = 5,    /* a8: Hessenberg column, rotations, residual estimate, basis scaling */
   BEM_PH_UPDATE = 6,    /* a9: least squares and x += V y */
-  BEM_PH_RESIDUAL = 7,  /* a9: refinement residual b - (hi + lo) x and norms */
+  BEM_PH_RESIDUAL = 7,  /* a9: refinement residual b - (hi + lo) x (its norms count as OTHER) */
   BEM_PH_FARFIELD = 8,  /* a10 */
-  BEM_PH_OTHER = 9,     /* conversions, copies */
+  BEM_PH_OTHER = 9,     /* conversions, copies, column norms, the FP16 split copy of A */
   BEM_PH_COUNT = 10
 } bem_phase;
 BEM_API bem_status bem_profile_enable(bem_problem* p, int on);

@@ -93,6 +93,9 @@ struct bem_problem {
   void* d_A = nullptr;
   void* d_Alo = nullptr;
   size_t A_cap = 0;       // bytes of d_A (and d_Alo when mixed)
+  void* d_A16 = nullptr;  // FP16 split copy of the complex FP32 matrix for the tensor-core product
+  size_t A16_cap = 0;
+  bool a16_dirty = true;
   int A_mixed = -1;
   // solve workspace (grow-only)
   char* ws = nullptr;
@@ -249,6 +252,27 @@ bem_status assemble_impl(bem_problem* p, cudaStream_t s, bool force = false) {
   }
   p->A_mixed = mixed;
   p->mat_dirty = false;
+  p->a16_dirty = true;
+  return BEM_OK;
+}
+
+// The FP16 split copy of the (mixed) matrix that the tensor-core product reads; made once per assembly.
+bem_status ensure_a16(bem_problem* p, cudaStream_t s) {
+  if (!p->a16_dirty && p->d_A16) return BEM_OK;
+  const int n2 = 2 * p->n;
+  const size_t need = matvec_tc_a16_bytes(n2);
+  if (need > p->A16_cap) {
+    if (p->d_A16) cudaFree(p->d_A16);
+    p->d_A16 = nullptr;
+    p->A16_cap = 0;
+    if (cudaMalloc(&p->d_A16, need) != cudaSuccess) return fail(BEM_ENOMEM, "matrix allocation of %zu bytes failed", need);
+    p->A16_cap = need;
+  }
+  {
+    Phase ph(p, BEM_PH_OTHER, s, 1);
+    CU(launch_tc_prepare_a(static_cast<const float2*>(p->d_A), n2, p->d_A16, s));
+  }
+  p->a16_dirty = false;
   return BEM_OK;
 }
 
@@ -362,7 +386,11 @@ bem_status gmres_run(bem_problem* p, Solver& sv, const double2* r0, double2* x, 
   const bool fp32 = st.basis_fp32;
   const size_t tb = fp32 ? sizeof(float2) : sizeof(double2);
   const bool use_tc = fp32 && p->o.prec == BEM_PREC_MIXED_TC && nrhs > 1 && matvec_tc_supported(n2, nrhs);
-  if (use_tc) CU(matvec_tc_clear_error(sv.tcws, n2, nrhs, s));
+  if (use_tc) {
+    const bem_status a = ensure_a16(p, s);
+    if (a != BEM_OK) return a;
+    CU(matvec_tc_clear_error(sv.tcws, n2, nrhs, s));
+  }
   // Iterations are queued kSyncEvery at a time before the host reads the active count: the GPU never
   // waits for the host between iterations.  Once every system has converged, the queued iterations find
   // their gates closed (n_active = 0, active flags cleared) and return at once.
@@ -379,8 +407,8 @@ bem_status gmres_run(bem_problem* p, Solver& sv, const double2* r0, double2* x, 
       CU(launch_matvec_c64(static_cast<const double2*>(p->d_A), n2, n2, nrhs, static_cast<const double2*>(Vj),
                            static_cast<double2*>(st.W), s, gate));
     } else if (use_tc) {
-      CU(launch_matvec_tc(static_cast<const float2*>(p->d_A), n2, n2, nrhs, static_cast<const float2*>(Vj),
-                          static_cast<float2*>(st.W), sv.tcws, sv.tcws_bytes, s, gate));
+      CU(launch_matvec_tc(p->d_A16, n2, nrhs, static_cast<const float2*>(Vj), static_cast<float2*>(st.W), sv.tcws,
+                          sv.tcws_bytes, s, gate));
     } else {
       CU(launch_matvec_c32(static_cast<const float2*>(p->d_A), n2, n2, nrhs, static_cast<const float2*>(Vj),
                            static_cast<float2*>(st.W), st.active, s, gate));
@@ -436,7 +464,7 @@ namespace {
 bem_status column_norms(bem_problem* p, Solver& sv, const double2* v, int nrhs, std::vector<double>& out,
                         cudaStream_t s) {
   {
-    Phase ph(p, BEM_PH_RESIDUAL, s, 1);
+    Phase ph(p, BEM_PH_OTHER, s, 1);
     CU(launch_column_norms(v, sv.st.n, nrhs, sv.st.beta, s));
   }
   out.resize(nrhs);
@@ -486,7 +514,7 @@ bem_status solve_impl(bem_problem* p, int nrhs, const double2* b, double2* x, in
       st = gmres_run(p, sv, sv.r, x, tols, iters, inner_res, s);
       if (st != BEM_OK) return st;
       {
-        Phase ph(p, BEM_PH_RESIDUAL, s, 1);
+        Phase ph(p, BEM_PH_RESIDUAL, s, 2);   // split of x, double-float product
         CU(launch_residual_split(static_cast<const float2*>(p->d_A), static_cast<const float2*>(p->d_Alo), n2, n2,
                                  nrhs, x, b, sv.r, sv.st.V, s));   // the basis is free here
       }
@@ -586,6 +614,7 @@ bem_status problem_prepare_batched(bem_problem* p, cudaStream_t s, AsmJob* job, 
   job->Alo = p->d_Alo;
   p->A_mixed = 1;
   p->mat_dirty = false;
+  p->a16_dirty = true;
   *opts = p->o;
   return BEM_OK;
 }
@@ -627,6 +656,7 @@ BEM_API void bem_problem_destroy(bem_problem* p) {
   if (p->d_pm) cudaFree(p->d_pm);
   if (p->d_A) cudaFree(p->d_A);
   if (p->d_Alo) cudaFree(p->d_Alo);
+  if (p->d_A16) cudaFree(p->d_A16);
   if (p->ws) cudaFree(p->ws);
   if (p->d_small) cudaFree(p->d_small);
   if (p->h_pin) cudaFreeHost(p->h_pin);
@@ -698,7 +728,9 @@ BEM_API int bem_num_unknowns(const bem_problem* p) { return p ? 2 * p->n : 0; }
 BEM_API size_t bem_footprint_bytes(const bem_problem* p, int n_rhs) {
   if (!p || n_rhs < 1) return 0;
   const bool mixed = p->o.prec != BEM_PREC_FP64;
-  return (p->o.matrix_free ? 0 : matrix_bytes(p->n, mixed)) + krylov_bytes(2 * p->n, n_rhs, p->o.max_iter, mixed) + (size_t)11 * p->n * 8;
+  const size_t a16 = (!p->o.matrix_free && p->o.prec == BEM_PREC_MIXED_TC && n_rhs > 1) ? matvec_tc_a16_bytes(2 * p->n) : 0;
+  return (p->o.matrix_free ? 0 : matrix_bytes(p->n, mixed)) + a16 + krylov_bytes(2 * p->n, n_rhs, p->o.max_iter, mixed) +
+         (size_t)12 * p->n * 8;
 }
 
 BEM_API bem_status bem_assemble(bem_problem* p, void* stream) {
@@ -754,8 +786,10 @@ BEM_API bem_status bem_matvec(bem_problem* p, int n_rhs, const bem_c64* x_dev, b
   {
     Phase ph(p, BEM_PH_MATVEC, s, 1);
     if (p->o.prec == BEM_PREC_MIXED_TC && n_rhs > 1 && matvec_tc_supported(n2, n_rhs)) {
+      st = ensure_a16(p, s);
+      if (st != BEM_OK) return st;
       CU(matvec_tc_clear_error(sv.tcws, n2, n_rhs, s));
-      CU(launch_matvec_tc(static_cast<const float2*>(p->d_A), n2, n2, n_rhs, xf, yf, sv.tcws, sv.tcws_bytes, s));
+      CU(launch_matvec_tc(p->d_A16, n2, n_rhs, xf, yf, sv.tcws, sv.tcws_bytes, s));
       int tc_err = 0;
       CU(cudaMemcpyAsync(&tc_err, matvec_tc_error_word(sv.tcws, n2, n_rhs), sizeof(int), cudaMemcpyDeviceToHost, s));
       CU(cudaStreamSynchronize(s));

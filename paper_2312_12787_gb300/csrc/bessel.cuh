@@ -206,6 +206,20 @@ constexpr MillerCoefF2 make_miller_coef_f2() {
   return c;
 }
 
+// Coefficient tables read with a loop index: constant memory on the device (the index is uniform over a
+// warp, so reads are broadcasts), a constexpr table on the host.
+#if defined(__CUDACC__)
+static __constant__ MillerCoefF2 kMillerCoefDev = make_miller_coef_f2();
+#endif
+static constexpr MillerCoefF2 kMillerCoefHost = make_miller_coef_f2();
+BEM_HD F2 bem_miller_coef(int k) {
+#if defined(__CUDA_ARCH__)
+  return F2{kMillerCoefDev.h[k], kMillerCoefDev.l[k]};
+#else
+  return F2{kMillerCoefHost.h[k], kMillerCoefHost.l[k]};
+#endif
+}
+
 // Miller's algorithm exactly as bessel01_miller, with the recurrence and the three sums in double-float
 // arithmetic on the FP32 pipe (start value 2^-30, rescaled by 2^-40 whenever it grows past 2^40 so that it
 // stays inside the FP32 exponent range); the normalisation and the logarithmic terms are FP64.
@@ -522,26 +536,24 @@ constexpr F2 f2_const(double v) { return F2{(float)v, (float)(v - (double)(float
 // Miller's algorithm as bessel01_miller_f2 with the normalisation, 2/x and the Neumann sums also in
 // double-float; only ln(x/2) is FP64.
 BEM_HD void bessel01_miller_f2x(double x, F2 X, Bessel01F2& b, int start = BEM_MILLER_START) {
-  constexpr MillerCoefF2 C = make_miller_coef_f2();
   const F2 tox = f2_pow2(f2_rcp(X), 2.f);
   F2 fp{0.f, 0.f}, f{0x1p-30f, 0.f}, norm{0.f, 0.f}, sy0{0.f, 0.f}, sy1{0.f, 0.f}, fodd{0.f, 0.f};
-#pragma unroll
-  for (int n = BEM_MILLER_START; n >= 1; --n) {
-    if (n > start) continue;   // start: even, <= BEM_MILLER_START
-    if ((n & 1) == 0) {
-      const int kk = n >> 1;
-      norm = f2_add(norm, f);
-      sy0 = f2_add(sy0, f2_mul(f, F2{C.h[kk], C.l[kk]}));
-      fodd = fp;
-    } else {
-      const int kk = (n + 1) >> 1;
-      sy1 = f2_add(sy1, f2_mul(f2_sub(f, fodd), F2{C.h[kk], C.l[kk]}));
-    }
-    const F2 cn = f2_mulf(tox, (float)n);
-    const F2 fm = f2_sub(f2_mul(cn, f), fp);
+  // two orders per pass (even n, then n - 1); both use the coefficient (-1)^k / k with k = n / 2.  A
+  // rolled loop keeps the code small enough for the instruction cache (start is uniform over the warp).
+#pragma unroll 1
+  for (int n = start; n >= 2; n -= 2) {
+    const F2 ck = bem_miller_coef(n >> 1);
+    norm = f2_add(norm, f);
+    sy0 = f2_add(sy0, f2_mul(f, ck));
+    fodd = fp;
+    F2 fm = f2_sub(f2_mul(f2_mulf(tox, (float)n), f), fp);
     fp = f;
     f = fm;
-    if ((n & 3) == 1 && fabsf(f.h) > 0x1p40f) {
+    sy1 = f2_add(sy1, f2_mul(f2_sub(f, fodd), ck));
+    fm = f2_sub(f2_mul(f2_mulf(tox, (float)(n - 1)), f), fp);
+    fp = f;
+    f = fm;
+    if ((n & 3) == 2 && fabsf(f.h) > 0x1p40f) {
       const float sc = 0x1p-40f;
       f = f2_pow2(f, sc); fp = f2_pow2(fp, sc);
       norm = f2_pow2(norm, sc); sy0 = f2_pow2(sy0, sc);
@@ -558,6 +570,27 @@ BEM_HD void bessel01_miller_f2x(double x, F2 X, Bessel01F2& b, int start = BEM_M
   b.y0 = f2_mul(kTwoPi, f2_sub(f2_mul(lg, j0), f2_pow2(f2_mul(sy0, s), 2.f)));
   b.y1 = f2_mul(kTwoPi, f2_add(f2_sub(f2_mul(lg, j1), f2_mul(j0, f2_pow2(tox, 0.5f))), f2_mul(sy1, s)));
 }
+
+// The expansion's coefficients for a rolled Horner loop: which = 0..3 selects P0, Q0, P1, Q1 (constant memory
+// on the device, as for the Miller coefficients).
+#if defined(__CUDACC__)
+static __constant__ AsympCoefF2 kAsympCoefDev = make_asymp_coef_f2();
+#endif
+static constexpr AsympCoefF2 kAsympCoefHost = make_asymp_coef_f2();
+#if defined(__CUDA_ARCH__)
+#define BEM_ASYMP_TAB kAsympCoefDev
+#else
+#define BEM_ASYMP_TAB kAsympCoefHost
+#endif
+BEM_HD F2 bem_asymp_coef(int which, int m) {
+  switch (which) {
+    case 0: return F2{BEM_ASYMP_TAB.p0.h[m], BEM_ASYMP_TAB.p0.l[m]};
+    case 1: return F2{BEM_ASYMP_TAB.q0.h[m], BEM_ASYMP_TAB.q0.l[m]};
+    case 2: return F2{BEM_ASYMP_TAB.p1.h[m], BEM_ASYMP_TAB.p1.l[m]};
+    default: return F2{BEM_ASYMP_TAB.q1.h[m], BEM_ASYMP_TAB.q1.l[m]};
+  }
+}
+#undef BEM_ASYMP_TAB
 
 // Hankel's expansion as bessel01_asymp_f2, with 1/sqrt(x) and 1/x from X in double-float.
 BEM_HD void bessel01_asymp_f2x(double x, F2 X, Bessel01F2& b) {
@@ -601,13 +634,15 @@ BEM_HD void bessel01_asymp_f2x(double x, F2 X, Bessel01F2& b) {
 #if defined(__CUDA_ARCH__)
   xmin = __int_as_float(__reduce_min_sync(__activemask(), __float_as_int(xmin)));   // x > 0: int order = float order
 #endif
-  F2 p0, p1, q0, q1;
-  if (xmin >= 35.f) {
-    p0 = f2_horner<6>(C.p0, U); p1 = f2_horner<6>(C.p1, U); q0 = f2_horner<6>(C.q0, U); q1 = f2_horner<6>(C.q1, U);
-  } else if (xmin >= 25.f) {
-    p0 = f2_horner<8>(C.p0, U); p1 = f2_horner<8>(C.p1, U); q0 = f2_horner<8>(C.q0, U); q1 = f2_horner<8>(C.q1, U);
-  } else {
-    p0 = f2_horner(C.p0, U); p1 = f2_horner(C.p1, U); q0 = f2_horner(C.q0, U); q1 = f2_horner(C.q1, U);
+  const int T = xmin >= 35.f ? 6 : (xmin >= 25.f ? 8 : BEM_ASYMP_TERMS / 2);
+  F2 p0 = bem_asymp_coef(0, T - 1), q0 = bem_asymp_coef(1, T - 1);
+  F2 p1 = bem_asymp_coef(2, T - 1), q1 = bem_asymp_coef(3, T - 1);
+#pragma unroll 1
+  for (int m = T - 2; m >= 0; --m) {   // four independent Horner sums in u = 1/x^2
+    p0 = f2_add(f2_mul(p0, U), bem_asymp_coef(0, m));
+    q0 = f2_add(f2_mul(q0, U), bem_asymp_coef(1, m));
+    p1 = f2_add(f2_mul(p1, U), bem_asymp_coef(2, m));
+    q1 = f2_add(f2_mul(q1, U), bem_asymp_coef(3, m));
   }
   q0 = f2_mul(q0, Y);
   q1 = f2_mul(q1, Y);

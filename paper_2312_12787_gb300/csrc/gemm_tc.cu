@@ -1,27 +1,38 @@
 // Multi-right-hand-side complex matrix product Y = A X on the tcgen05 tensor cores (step a11).
 //
-// The complex FP32 matrix A (n x n, row-major, re/im interleaved) is read as a real n x 2n matrix that
-// is contiguous along K, and the block X (nrhs <= 64 columns) becomes a real K-major operand Bt of 128
-// rows:  Bt[s] = (Re x_s, -Im x_s) pairs and Bt[64+s] = (Im x_s, Re x_s) pairs, so that one real GEMM
+// The complex matrix A (n x n, re/im interleaved) is read as a real n x 2n matrix that is contiguous along
+// K, and the block X (nrhs <= 64 columns) becomes a real K-major operand Bt of 128 rows:
+// Bt[s] = (Re x_s, -Im x_s) pairs and Bt[64+s] = (Im x_s, Re x_s) pairs, so that one real GEMM
 // D = A_real Bt^T gives D[r][s] = Re y_s[r] and D[r][64+s] = Im y_s[r].
 //
-// Precision: 3xTF32 split.  Each FP32 value v is written as hi + lo with hi = v with its 13 low mantissa
-// bits cleared (exactly representable in TF32) and lo = v - hi; D accumulates A_hi B_hi + A_hi B_lo +
-// A_lo B_hi in FP32, which keeps the products at about FP32 accuracy.  B is split once by a prep kernel;
-// A is split inside the GEMM: TMA brings an FP32 tile into shared memory and two converter warps rewrite
-// it in place as hi and write lo beside it (same swizzled positions, so the same descriptors apply).
+// Precision: FP16 x 3 with power-of-two scaling.  Row r of A is scaled by 2^-e_r so that its largest
+// magnitude lies in [1/2, 1); each scaled value v is written as hi = fp16(v) and lo = fp16(2^11 (v - hi)),
+// 22 significant bits in all.  Bt is split the same way with one scale per right-hand side.  The tensor
+// cores accumulate D1 = A_hi B_hi and D2 = A_lo B_hi + A_hi B_lo in FP32 (two TMEM accumulators; the
+// lo x lo term is below the FP32 rounding of the result) and the epilogue forms
+// (D1 + 2^-11 D2) / (2^-e_r t_s).  Values far below a row's largest entry fall into FP16's subnormal range,
+// where hi and lo still hold them to an absolute error of ~1e-11 of that largest entry.  A's split is made
+// once per assembled matrix (tc_prepare_a) and costs no more memory traffic per product than complex FP32:
+// 2 x 2 bytes per real entry.  FP16 operands move half the bytes of TF32 ones through shared memory and run
+// at twice the rate, so the product is bound by streaming A from HBM.
 //
-// Tiling: one CTA per (128-row tile, K split); 3 pipeline stages of 64 KB (A, A_lo, B_hi, B_lo tiles of
-// 128 x 32 FP32, 128-byte swizzle).  Warp roles: 0 = TMA producer, 1 = TMEM owner and MMA issuer,
-// 2-3 = split converters, 4-7 = accumulator readers.  The accumulator lives in TMEM as two 128 x 128 FP32
-// buffers; every kSeg K-steps the MMA warp switches buffers and the reader warps add the finished buffer
-// into FP32 registers, which bounds the length of each tensor-core accumulation chain.  Partial results
-// of the K splits are summed by a small reduction kernel that also writes Y in complex layout.
+// Work split (stream-K): the (row tile, K-step) pairs of the whole product are cut into G equal contiguous
+// ranges, G a multiple of the SM count with G >= row tiles, so every CTA does the same amount of work and
+// touches at most two row tiles.  Each CTA writes one partial 128 x 128 tile per row tile it touches; a
+// reduction kernel adds the partials of each tile in CTA order (deterministic) and applies the scales.
+//
+// CTA roles (256 threads): warp 0 = TMA producer, warp 1 = TMEM owner and MMA issuer, warps 4-7 =
+// accumulator readers (TMEM lanes 0-127).  3 pipeline stages of 64 KB (A_hi, A_lo, B_hi, B_lo tiles of
+// 128 x 64 FP16, 128-byte swizzle).  TMEM holds two buffers of (D1, D2), 512 columns; every kSeg K-steps (and
+// at a row-tile boundary) the MMA warp switches buffers and the readers fold the finished one into FP32
+// registers, which bounds the length of each tensor-core accumulation chain.
 //
 // Every mbarrier wait is bounded by the global timer; on expiry the kernel records an error code, stops
 // issuing work, waits (bounded) for its own in-flight copies and MMAs, frees its TMEM and returns.
 #include <cuda.h>
+#include <cuda_fp16.h>
 
+#include <atomic>
 #include <cstdio>
 
 #include "internal.cuh"
@@ -30,21 +41,22 @@ namespace bem {
 
 namespace {
 
-constexpr int kM = 128;              // rows per CTA (UMMA M)
+constexpr int kM = 128;              // rows per tile (UMMA M)
 constexpr int kN = 128;              // Bt rows: 64 real parts + 64 imaginary parts
-constexpr int kKs = 32;              // FP32 elements per K-step = 128 bytes = one swizzle row
+constexpr int kKs = 64;              // FP16 elements per K-step = 128 bytes = one swizzle row
 constexpr int kStages = 3;
-constexpr int kSeg = 8;              // K-steps per accumulation segment
-constexpr int kTile = kM * kKs * 4;  // 16 KB
-constexpr int kStage = 4 * kTile;    // A, A_lo, B_hi, B_lo
+constexpr int kSeg = 4;              // K-steps per accumulation segment (256 K values)
+constexpr int kTile = kM * kKs * 2;  // 16 KB
+constexpr int kStage = 4 * kTile;    // A_hi, A_lo, B_hi, B_lo
 constexpr int kThreads = 256;
-constexpr uint32_t kTmemCols = 256;  // two 128-column FP32 accumulators
+constexpr uint32_t kTmemCols = 512;  // two buffers x (D1, D2) x 128 FP32 columns
 constexpr int kMaxRhs = 64;
+constexpr float kLoScale = 2048.f;   // lo parts are stored times 2^11
 constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s
+constexpr int kMaxDev = 64;
 
 struct Bars {
   unsigned long long full[kStages];
-  unsigned long long conv[kStages];
   unsigned long long empty[kStages];
   unsigned long long accf[2];
   unsigned long long acce[2];
@@ -109,14 +121,14 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
   return d;
 }
 
-// Instruction descriptor, kind::tf32: D FP32, A and B TF32, both K-major, N = 128, M = 128.
-constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kN >> 3) << 17) |
+// Instruction descriptor, kind::f16: D FP32, A and B FP16, both K-major, N = 128, M = 128.
+constexpr uint32_t kIdesc = (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(kN >> 3) << 17) |
                             ((uint32_t)(kM >> 4) << 24);
 
-__device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t accum) {
+__device__ __forceinline__ void mma_f16(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t accum) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
       ::"r"(dtmem), "l"(a), "l"(b), "r"(kIdesc), "r"(accum)
       : "memory");
 }
@@ -142,27 +154,48 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__device__ __forceinline__ float tf32_hi(float v) { return __uint_as_float(__float_as_uint(v) & 0xFFFFE000u); }
+// Row stride (FP16 elements) of the split copies of A and of Bt: 2n rounded up to 8 (16-byte TMA strides).
+inline size_t ld16(int n) { return ((size_t)2 * n + 7) & ~(size_t)7; }
 
+// The accumulation schedule of one CTA's range [kb, kb + nk) of global K-steps (kpt K-steps per row tile):
+// a segment ends after kSeg K-steps, at the end of a row tile and at the end of the range.  MMA issuer and
+// readers walk it identically.
+struct SegWalk {
+  int kb, nk, kpt;
+  int it = 0;                  // next K-step (relative to kb)
+  __device__ bool next(int& beg, int& end, bool& tile_end) {
+    if (it >= nk) return false;
+    beg = it;
+    const int g = kb + it;
+    const int to_tile_end = kpt - g % kpt;
+    int len = kSeg < to_tile_end ? kSeg : to_tile_end;
+    if (len > nk - it) len = nk - it;
+    end = it + len;
+    tile_end = (len == to_tile_end) || (end == nk);
+    it = end;
+    return true;
+  }
+};
+
+// One CTA per stream-K range.  partial: G x 2 x kM x kN FP32 (slot 0 = first row tile of the range, 1 = the
+// next one).
 __global__ void __launch_bounds__(kThreads, 1)
-    k_gemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapBhi,
-              const __grid_constant__ CUtensorMap mapBlo, int n, int ksteps_total, int nsplit, float* partial,
-              int* err, const int* gate) {
+    k_gemm_tc(const __grid_constant__ CUtensorMap mapAh, const __grid_constant__ CUtensorMap mapAl,
+              const __grid_constant__ CUtensorMap mapBh, const __grid_constant__ CUtensorMap mapBl, int n,
+              int kpt, long long total, float* partial, int* err, const int* gate) {
   if (gate && *gate == 0) return;   // every system of the block has converged (uniform for the grid)
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   Bars* bars = reinterpret_cast<Bars*>(smem + kStages * kStage);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int tile = blockIdx.x, split = blockIdx.y;
-  const int kb = (int)(((long long)ksteps_total * split) / nsplit);
-  const int ke = (int)(((long long)ksteps_total * (split + 1)) / nsplit);
-  const int nk = ke - kb;
-  const int nseg = (nk + kSeg - 1) / kSeg;
+  const int G = gridDim.x, c = blockIdx.x;
+  const long long gb = total * c / G, ge = total * (c + 1) / G;
+  const int kb = (int)gb, nk = (int)(ge - gb);
+  const int tile0 = kb / kpt;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
       mbar_init(su32(&bars->full[s]), 1);
-      mbar_init(su32(&bars->conv[s]), 64);
       mbar_init(su32(&bars->empty[s]), 1);
     }
     for (int b = 0; b < 2; ++b) {
@@ -194,11 +227,13 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (*(volatile int*)err) break;
         unsigned char* base = smem + st * kStage;
         const uint32_t fb = su32(&bars->full[st]);
-        mbar_expect_tx(fb, 3 * kTile);
-        const int x = (kb + it) * kKs;
-        tma_load_2d(su32(base), &mapA, x, tile * kM, fb);
-        tma_load_2d(su32(base + 2 * kTile), &mapBhi, x, 0, fb);
-        tma_load_2d(su32(base + 3 * kTile), &mapBlo, x, 0, fb);
+        mbar_expect_tx(fb, 4 * kTile);
+        const int g = kb + it;
+        const int x = (g % kpt) * kKs, y = (g / kpt) * kM;
+        tma_load_2d(su32(base), &mapAh, x, y, fb);
+        tma_load_2d(su32(base + kTile), &mapAl, x, y, fb);
+        tma_load_2d(su32(base + 2 * kTile), &mapBh, x, 0, fb);
+        tma_load_2d(su32(base + 3 * kTile), &mapBl, x, 0, fb);
         issued = it + 1;
       }
     }
@@ -206,89 +241,79 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
       bool ok = true;
-      for (int it = 0; it < nk && ok; ++it) {
-        const int st = it % kStages;
-        const uint32_t ph = (uint32_t)((it / kStages) & 1);
-        const int seg = it / kSeg;
+      SegWalk w{kb, nk, kpt};
+      int beg, end, seg = 0;
+      bool tile_end;
+      while (ok && w.next(beg, end, tile_end)) {
         const int b = seg & 1;
-        const bool seg_first = (it % kSeg) == 0;
-        const bool seg_last = ((it % kSeg) == kSeg - 1) || (it == nk - 1);
-        if (seg_first) {
-          // the accumulator buffer must have been drained by the readers (segments seg-2, seg-4, ...)
-          if (!mbar_wait(su32(&bars->acce[b]), (uint32_t)(((seg >> 1) & 1) ^ 1), err, 2)) { ok = false; break; }
-          tc_fence_after();
-        }
-        if (!mbar_wait(su32(&bars->conv[st]), ph, err, 3)) { ok = false; break; }
+        // the buffer must have been drained by the readers (segments seg-2, seg-4, ...)
+        if (!mbar_wait(su32(&bars->acce[b]), (uint32_t)(((seg >> 1) & 1) ^ 1), err, 2)) { ok = false; break; }
         tc_fence_after();
-        unsigned char* base = smem + st * kStage;
-        const uint64_t da = sdesc(su32(base)), dal = sdesc(su32(base + kTile));
-        const uint64_t dbh = sdesc(su32(base + 2 * kTile)), dbl = sdesc(su32(base + 3 * kTile));
-        const uint32_t dt = tmem + (uint32_t)(b * kN);
+        const uint32_t d1 = tmem + (uint32_t)(b * 2 * kN), d2 = d1 + (uint32_t)kN;
+        for (int it = beg; it < end; ++it) {
+          const int st = it % kStages;
+          const uint32_t ph = (uint32_t)((it / kStages) & 1);
+          if (!mbar_wait(su32(&bars->full[st]), ph, err, 3)) { ok = false; break; }
+          tc_fence_after();
+          unsigned char* base = smem + st * kStage;
+          const uint64_t dah = sdesc(su32(base)), dal = sdesc(su32(base + kTile));
+          const uint64_t dbh = sdesc(su32(base + 2 * kTile)), dbl = sdesc(su32(base + 3 * kTile));
 #pragma unroll
-        for (int k = 0; k < kKs / 8; ++k) {
-          const uint64_t off = (uint64_t)((k * 32) >> 4);   // 8 TF32 = 32 bytes along the swizzled row
-          const uint32_t acc0 = (seg_first && k == 0) ? 0u : 1u;
-          mma_tf32(dt, da + off, dbh + off, acc0);
-          mma_tf32(dt, da + off, dbl + off, 1u);
-          mma_tf32(dt, dal + off, dbh + off, 1u);
+          for (int k = 0; k < kKs / 16; ++k) {
+            const uint64_t off = (uint64_t)((k * 32) >> 4);   // 16 FP16 = 32 bytes along the swizzled row
+            const uint32_t acc0 = (it == beg && k == 0) ? 0u : 1u;
+            mma_f16(d1, dah + off, dbh + off, acc0);
+            mma_f16(d2, dal + off, dbh + off, acc0);
+            mma_f16(d2, dah + off, dbl + off, 1u);
+          }
+          mma_commit(su32(&bars->empty[st]));
         }
-        mma_commit(su32(&bars->empty[st]));
-        if (seg_last) mma_commit(su32(&bars->accf[b]));
+        if (!ok) break;
+        mma_commit(su32(&bars->accf[b]));
+        ++seg;
       }
       // all MMAs issued by this thread complete before `fin` arrives
       mma_commit(su32(&bars->fin));
     }
-  } else if (warp < 4) {
-    // ---------------- split converters (64 threads) ----------------
-    const int t = threadIdx.x - 64;
-    for (int it = 0; it < nk; ++it) {
-      const int st = it % kStages;
-      const uint32_t ph = (uint32_t)((it / kStages) & 1);
-      if (!mbar_wait(su32(&bars->full[st]), ph, err, 4)) break;
-      float4* a = reinterpret_cast<float4*>(smem + st * kStage);
-      float4* al = reinterpret_cast<float4*>(smem + st * kStage + kTile);
-#pragma unroll 4
-      for (int i = 0; i < kTile / 16 / 64; ++i) {
-        const int idx = i * 64 + t;
-        const float4 v = a[idx];
-        float4 h, l;
-        h.x = tf32_hi(v.x); h.y = tf32_hi(v.y); h.z = tf32_hi(v.z); h.w = tf32_hi(v.w);
-        l.x = v.x - h.x; l.y = v.y - h.y; l.z = v.z - h.z; l.w = v.w - h.w;
-        a[idx] = h;
-        al[idx] = l;
-      }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      mbar_arrive(su32(&bars->conv[st]));
-    }
-  } else {
+  } else if (warp >= 4) {
     // ---------------- accumulator readers (128 threads, TMEM lanes 0..127) ----------------
     const int q = warp - 4;
     float acc[kN];
 #pragma unroll
-    for (int c = 0; c < kN; ++c) acc[c] = 0.f;
+    for (int j = 0; j < kN; ++j) acc[j] = 0.f;
     bool ok = true;
-    for (int seg = 0; seg < nseg && ok; ++seg) {
+    SegWalk w{kb, nk, kpt};
+    int beg, end, seg = 0, slot = 0;
+    bool tile_end;
+    while (ok && w.next(beg, end, tile_end)) {
       const int b = seg & 1;
       // the TMEM loads below are warp-collective: the whole warp proceeds or stops together
       ok = __all_sync(0xffffffffu, mbar_wait(su32(&bars->accf[b]), (uint32_t)((seg >> 1) & 1), err, 5));
       if (!ok) break;
       tc_fence_after();
-      const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * kN);
+      const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * 2 * kN);
 #pragma unroll
-      for (int c = 0; c < kN / 32; ++c) {
+      for (int cc = 0; cc < kN / 32; ++cc) {
         float v[32];
-        tmem_ld32(ta + (uint32_t)(c * 32), v);
+        tmem_ld32(ta + (uint32_t)(cc * 32), v);                  // D1
 #pragma unroll
-        for (int i = 0; i < 32; ++i) acc[c * 32 + i] += v[i];
+        for (int i = 0; i < 32; ++i) acc[cc * 32 + i] += v[i];
+        tmem_ld32(ta + (uint32_t)(kN + cc * 32), v);             // D2, lo terms times 2^11
+#pragma unroll
+        for (int i = 0; i < 32; ++i) acc[cc * 32 + i] = fmaf(v[i], 1.f / kLoScale, acc[cc * 32 + i]);
       }
       tc_fence_before();
       mbar_arrive(su32(&bars->acce[b]));
-    }
-    const int row = tile * kM + q * 32 + lane;
-    if (ok && row < n) {
-      float4* dst = reinterpret_cast<float4*>(partial + ((size_t)split * n + row) * kN);
+      ++seg;
+      if (tile_end) {
+        float4* dst = reinterpret_cast<float4*>(partial + (((size_t)c * 2 + slot) * kM + q * 32 + lane) * kN);
 #pragma unroll
-      for (int c = 0; c < kN / 4; ++c) dst[c] = make_float4(acc[4 * c], acc[4 * c + 1], acc[4 * c + 2], acc[4 * c + 3]);
+        for (int j = 0; j < kN / 4; ++j) {
+          dst[j] = make_float4(acc[4 * j], acc[4 * j + 1], acc[4 * j + 2], acc[4 * j + 3]);
+          acc[4 * j] = acc[4 * j + 1] = acc[4 * j + 2] = acc[4 * j + 3] = 0.f;
+        }
+        ++slot;
+      }
     }
   }
 
@@ -297,7 +322,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp == 1 && lane == 0) mbar_wait(su32(&bars->fin), 0u, err, 6);
   if (warp == 0 && lane == 0 && *(volatile int*)err) {
     // drain TMA loads that were issued but possibly not consumed (the last kStages issues); a phase that
-    // the converters already consumed reads as complete because nothing newer was issued on it
+    // the MMA warp already consumed reads as complete because nothing newer was issued on it
     for (int it = (issued > kStages ? issued - kStages : 0); it < issued; ++it)
       mbar_wait(su32(&bars->full[it % kStages]), (uint32_t)((it / kStages) & 1), err, 7);
   }
@@ -307,43 +332,120 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp == 1) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
   }
+  (void)tile0;
 }
 
-// Bt rows (K-major, 2n FP32 each): row s < 64: (Re x_s[c], -Im x_s[c]); row 64+s: (Im x_s[c], Re x_s[c]);
-// rows of absent columns are zero.  Written as TF32-exact hi and lo = v - hi.
-__global__ void k_tc_prep_b(const float2* __restrict__ x, int n, int nrhs, float* __restrict__ bhi,
-                            float* __restrict__ blo, const int* gate) {
+// Largest |value| of each column block of X (one per right-hand side), as float bits for atomicMax
+// (non-negative floats order like their bit patterns).
+__global__ void k_tc_colmax(const float2* __restrict__ x, int n, int nrhs, unsigned* __restrict__ cmax,
+                            const int* gate) {
+  if (gate && *gate == 0) return;
+  const int s = blockIdx.y;
+  float m = 0.f;
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+    const float2 v = x[(size_t)s * n + c];
+    m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0 && m > 0.f) atomicMax(cmax + s, __float_as_uint(m));
+}
+
+// 2^-e with m 2^e = v, m in [1/2, 1) (1 for v = 0): the power-of-two scale that maps v into [1/2, 1).
+__device__ __forceinline__ float pow2_scale(float v) {
+  if (!(v > 0.f)) return 1.f;
+  int e;
+  frexpf(v, &e);
+  return ldexpf(1.f, -e);
+}
+
+__device__ __forceinline__ void split16(float v, __half& h, __half& l) {
+  h = __float2half_rn(v);
+  l = __float2half_rn((v - __half2float(h)) * kLoScale);
+}
+
+// Bt rows (K-major, ld16(n) FP16 each): row s < 64: (Re x_s[c], -Im x_s[c]); row 64+s: (Im x_s[c], Re x_s[c]),
+// scaled by t_s = pow2_scale(max |x_s|) and split into hi and lo; rows of absent columns are zero.
+__global__ void k_tc_prep_b(const float2* __restrict__ x, int n, int nrhs, const unsigned* __restrict__ cmax,
+                            __half* __restrict__ bhi, __half* __restrict__ blo, size_t ldb, float* __restrict__ tsc,
+                            const int* gate) {
   if (gate && *gate == 0) return;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;   // complex column index along K
   const int row = blockIdx.y;                             // 0..127
   if (c >= n) return;
   const int s = row & 63;
-  float v0 = 0.f, v1 = 0.f;
+  float v0 = 0.f, v1 = 0.f, t = 1.f;
   if (s < nrhs) {
+    t = pow2_scale(__uint_as_float(cmax[s]));
     const float2 xv = x[(size_t)s * n + c];
     if (row < 64) { v0 = xv.x; v1 = -xv.y; }
     else { v0 = xv.y; v1 = xv.x; }
+    v0 *= t;
+    v1 *= t;
   }
-  const size_t o = (size_t)row * 2 * n + 2 * c;
-  const float h0 = tf32_hi(v0), h1 = tf32_hi(v1);
+  if (c == 0 && row < 64) tsc[row] = t;
+  const size_t o = (size_t)row * ldb + 2 * c;
+  __half h0, l0, h1, l1;
+  split16(v0, h0, l0);
+  split16(v1, h1, l1);
   bhi[o] = h0; bhi[o + 1] = h1;
-  blo[o] = v0 - h0; blo[o + 1] = v1 - h1;
+  blo[o] = l0; blo[o + 1] = l1;
 }
 
-// Y[s][r] = (sum_k P[k][r][s], sum_k P[k][r][64+s]) in FP32.
-__global__ void k_tc_reduce(const float* __restrict__ partial, int n, int nrhs, int nsplit, float2* __restrict__ y,
+// Split copy of A: one CTA per row; row scale 2^-e_r from the row's largest |real entry|.
+__global__ void __launch_bounds__(256) k_tc_prep_a(const float2* __restrict__ A, int n, __half* __restrict__ ahi,
+                                                   __half* __restrict__ alo, size_t lda16, float* __restrict__ rsc) {
+  __shared__ float red[8];
+  const int r = blockIdx.x;
+  const float2* row = A + (size_t)r * n;
+  float m = 0.f;
+  for (int c = threadIdx.x; c < n; c += 256) m = fmaxf(m, fmaxf(fabsf(row[c].x), fabsf(row[c].y)));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  m = red[0];
+#pragma unroll
+  for (int w = 1; w < 8; ++w) m = fmaxf(m, red[w]);
+  const float sc = pow2_scale(m);
+  if (threadIdx.x == 0) rsc[r] = sc;
+  __half* hr = ahi + (size_t)r * lda16;
+  __half* lr = alo + (size_t)r * lda16;
+  for (int c = threadIdx.x; c < n; c += 256) {
+    const float2 v = row[c];
+    __half h0, l0, h1, l1;
+    split16(v.x * sc, h0, l0);
+    split16(v.y * sc, h1, l1);
+    hr[2 * c] = h0; hr[2 * c + 1] = h1;
+    lr[2 * c] = l0; lr[2 * c + 1] = l1;
+  }
+}
+
+// Y[s][r] = (sum of the partials of r's row tile) / (rsc[r] tsc[s]), real part in column s, imaginary part
+// in column 64 + s; one thread per (r, s).
+__global__ void k_tc_reduce(const float* __restrict__ partial, int n, int nrhs, int kpt, long long total, int G,
+                            const float* __restrict__ rsc, const float* __restrict__ tsc, float2* __restrict__ y,
                             const int* gate) {
   if (gate && *gate == 0) return;
   const int s = threadIdx.x & 63;
   const int r = blockIdx.x * (blockDim.x >> 6) + (threadIdx.x >> 6);
   if (r >= n || s >= nrhs) return;
+  const int t = r / kM, rl = r % kM;
+  // CTAs whose range [total c / G, total (c+1) / G) meets [t kpt, (t+1) kpt)
+  const long long lo = (long long)t * kpt, hi = lo + kpt;
+  int c0 = (int)((lo * G) / total);
+  while (c0 > 0 && total * c0 / G > lo) --c0;
+  while (total * (c0 + 1) / G <= lo) ++c0;
   float re = 0.f, im = 0.f;
-  for (int k = 0; k < nsplit; ++k) {
-    const float* p = partial + ((size_t)k * n + r) * kN;
+  for (int c = c0; c < G && total * c / G < hi; ++c) {
+    const int first_tile = (int)((total * c / G) / kpt);
+    const int slot = (first_tile == t) ? 0 : 1;
+    const float* p = partial + (((size_t)c * 2 + slot) * kM + rl) * kN;
     re += p[s];
     im += p[64 + s];
   }
-  y[(size_t)s * n + r] = make_float2(re, im);
+  const float inv = 1.f / (rsc[r] * tsc[s]);   // a power of two: exact
+  y[(size_t)s * n + r] = make_float2(re * inv, im * inv);
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -364,38 +466,59 @@ EncodeTiledFn encode_fn() {
   return fn;
 }
 
-// rows x (2n) FP32, box 32 x 128, 128-byte swizzle, zero fill out of bounds
-bool make_map(CUtensorMap* m, const void* base, int n2real, int rows) {
+// rows x cols FP16 (row stride ld16 elements), box 64 x 128, 128-byte swizzle, zero fill out of bounds
+bool make_map16(CUtensorMap* m, const void* base, int cols, size_t ld, int rows) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return false;
-  cuuint64_t dims[2] = {(cuuint64_t)n2real, (cuuint64_t)rows};
-  cuuint64_t strides[1] = {(cuuint64_t)n2real * 4};
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
   cuuint32_t box[2] = {(cuuint32_t)kKs, (cuuint32_t)kM};
   cuuint32_t es[2] = {1, 1};
-  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims, strides, box, es,
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 int num_sms() {
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms <= 0) sms = 1;
-  }
-  return sms;
-}
-
-int choose_split(int n) {
-  const int tiles = (n + kM - 1) / kM;
-  int s = num_sms() / tiles;
-  const int ksteps = (2 * n + kKs - 1) / kKs;
-  if (s < 1) s = 1;
-  if (s > ksteps / kSeg) s = ksteps / kSeg > 0 ? ksteps / kSeg : 1;
+  static std::atomic<int> cache[kMaxDev];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) return 1;
+  int s = cache[dev].load(std::memory_order_relaxed);
+  if (s > 0) return s;
+  if (cudaDeviceGetAttribute(&s, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || s <= 0) s = 1;
+  cache[dev].store(s, std::memory_order_relaxed);
   return s;
 }
+
+// Stream-K grid: a multiple of the SM count, at least the number of row tiles (so a range spans at most two
+// tiles), and at most one CTA per K-step.
+int grid_of(int n) {
+  const int tiles = (n + kM - 1) / kM;
+  const long long total = (long long)tiles * (((long long)2 * n + kKs - 1) / kKs);
+  const int sms = num_sms();
+  long long g = (long long)sms * ((tiles + sms - 1) / sms);
+  if (g > total) g = total;
+  return (int)g;
+}
+
+size_t b_bytes(int n) { return (size_t)kN * ld16(n) * 2; }
+
+bool smem_attr_set() {
+  static std::atomic<int> done[kMaxDev];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) return false;
+  if (done[dev].load(std::memory_order_relaxed)) return true;
+  if (cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes) != cudaSuccess)
+    return false;
+  done[dev].store(1, std::memory_order_relaxed);
+  return true;
+}
+
+// workspace layout: B_hi | B_lo | partials | column max (64 u32) | column scales (64 f32) | error word
+size_t off_part(int n) { return (2 * b_bytes(n) + 255) & ~(size_t)255; }
+size_t off_cmax(int n) { return off_part(n) + (size_t)grid_of(n) * 2 * kM * kN * 4; }
+size_t off_tsc(int n) { return off_cmax(n) + 256; }
+size_t off_err(int n) { return off_tsc(n) + 256; }
 
 }  // namespace
 
@@ -405,15 +528,12 @@ bool matvec_tc_supported(int n, int nrhs) {
 
 size_t matvec_tc_workspace_bytes(int n, int nrhs) {
   if (nrhs < 2 || nrhs > kMaxRhs || n < kM) return 0;
-  const size_t b = (size_t)kN * 2 * n * 4;                              // one of B_hi / B_lo
-  const size_t part = (size_t)choose_split(n) * n * kN * 4;            // split partials
-  return 2 * b + part + 256 + 64;                                      // + error word
+  return off_err(n) + 64;
 }
 
 int* matvec_tc_error_word(void* ws, int n, int nrhs) {
   if (nrhs < 2 || nrhs > kMaxRhs || n < kM) return nullptr;
-  char* w = static_cast<char*>(ws);
-  return reinterpret_cast<int*>(w + 2 * (size_t)kN * 2 * n * 4 + (size_t)choose_split(n) * n * kN * 4);
+  return reinterpret_cast<int*>(static_cast<char*>(ws) + off_err(n));
 }
 
 cudaError_t matvec_tc_clear_error(void* ws, int n, int nrhs, cudaStream_t s) {
@@ -422,33 +542,51 @@ cudaError_t matvec_tc_clear_error(void* ws, int n, int nrhs, cudaStream_t s) {
   return cudaMemsetAsync(err, 0, sizeof(int), s);
 }
 
-cudaError_t launch_matvec_tc(const float2* A, size_t lda, int n, int nrhs, const float2* x, float2* y, void* ws,
-                             size_t ws_bytes, cudaStream_t s, const int* gate) {
-  if (!matvec_tc_supported(n, nrhs) || lda != (size_t)n) return cudaErrorNotSupported;
-  if (ws_bytes < matvec_tc_workspace_bytes(n, nrhs)) return cudaErrorInvalidValue;
-  const int n2 = 2 * n;
-  char* w = static_cast<char*>(ws);
-  float* bhi = reinterpret_cast<float*>(w);
-  float* blo = reinterpret_cast<float*>(w + (size_t)kN * n2 * 4);
-  float* part = reinterpret_cast<float*>(w + 2 * (size_t)kN * n2 * 4);
-  const int nsplit = choose_split(n);
-  int* err = matvec_tc_error_word(ws, n, nrhs);
-  CUtensorMap mA, mBh, mBl;
-  if (!make_map(&mA, A, n2, n) || !make_map(&mBh, bhi, n2, kN) || !make_map(&mBl, blo, n2, kN))
-    return cudaErrorInvalidValue;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
-  k_tc_prep_b<<<dim3((n + 255) / 256, kN), 256, 0, s>>>(x, n, nrhs, bhi, blo, gate);
-  const int tiles = (n + kM - 1) / kM;
-  const int ksteps = (n2 + kKs - 1) / kKs;
-  k_gemm_tc<<<dim3(tiles, nsplit), kThreads, kSmemBytes, s>>>(mA, mBh, mBl, n, ksteps, nsplit, part, err, gate);
-  k_tc_reduce<<<(n + 3) / 4, 256, 0, s>>>(part, n, nrhs, nsplit, y, gate);
+size_t matvec_tc_a16_bytes(int n) { return ((2 * (size_t)n * ld16(n) * 2 + 255) & ~(size_t)255) + (size_t)n * 4; }
+
+cudaError_t launch_tc_prepare_a(const float2* A, int n, void* a16, cudaStream_t s) {
+  if (n < kM || (n % 2) != 0) return cudaErrorInvalidValue;
+  const size_t ld = ld16(n);
+  __half* ahi = static_cast<__half*>(a16);
+  __half* alo = ahi + (size_t)n * ld;
+  float* rsc = reinterpret_cast<float*>(static_cast<char*>(a16) + ((2 * (size_t)n * ld * 2 + 255) & ~(size_t)255));
+  k_tc_prep_a<<<n, 256, 0, s>>>(A, n, ahi, alo, ld, rsc);
   return cudaGetLastError();
 }
 
+cudaError_t launch_matvec_tc(const void* a16, int n, int nrhs, const float2* x, float2* y, void* ws,
+                             size_t ws_bytes, cudaStream_t s, const int* gate) {
+  if (!matvec_tc_supported(n, nrhs)) return cudaErrorNotSupported;
+  if (ws_bytes < matvec_tc_workspace_bytes(n, nrhs)) return cudaErrorInvalidValue;
+  const size_t ld = ld16(n);
+  const __half* ahi = static_cast<const __half*>(a16);
+  const __half* alo = ahi + (size_t)n * ld;
+  const float* rsc =
+      reinterpret_cast<const float*>(static_cast<const char*>(a16) + ((2 * (size_t)n * ld * 2 + 255) & ~(size_t)255));
+  char* w = static_cast<char*>(ws);
+  __half* bhi = reinterpret_cast<__half*>(w);
+  __half* blo = reinterpret_cast<__half*>(w + b_bytes(n));
+  float* part = reinterpret_cast<float*>(w + off_part(n));
+  unsigned* cmax = reinterpret_cast<unsigned*>(w + off_cmax(n));
+  float* tsc = reinterpret_cast<float*>(w + off_tsc(n));
+  int* err = reinterpret_cast<int*>(w + off_err(n));
+  const int cols = 2 * n;
+  CUtensorMap mAh, mAl, mBh, mBl;
+  if (!make_map16(&mAh, ahi, cols, ld, n) || !make_map16(&mAl, alo, cols, ld, n) ||
+      !make_map16(&mBh, bhi, cols, ld, kN) || !make_map16(&mBl, blo, cols, ld, kN))
+    return cudaErrorInvalidValue;
+  if (!smem_attr_set()) return cudaErrorInvalidValue;
+  const int tiles = (n + kM - 1) / kM;
+  const int kpt = (cols + kKs - 1) / kKs;
+  const long long total = (long long)tiles * kpt;
+  const int G = grid_of(n);
+  cudaError_t e = cudaMemsetAsync(cmax, 0, 64 * sizeof(unsigned), s);
+  if (e != cudaSuccess) return e;
+  k_tc_colmax<<<dim3(8, nrhs), 256, 0, s>>>(x, n, nrhs, cmax, gate);
+  k_tc_prep_b<<<dim3((n + 255) / 256, kN), 256, 0, s>>>(x, n, nrhs, cmax, bhi, blo, ld, tsc, gate);
+  k_gemm_tc<<<G, kThreads, kSmemBytes, s>>>(mAh, mAl, mBh, mBl, n, kpt, total, part, err, gate);
+  k_tc_reduce<<<(n + 3) / 4, 256, 0, s>>>(part, n, nrhs, kpt, total, G, rsc, tsc, y, gate);
+  return cudaGetLastError();
+}
 
 }  // namespace bem

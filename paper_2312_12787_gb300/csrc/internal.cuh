@@ -107,11 +107,16 @@ cudaError_t launch_residual_split_f64(const float2* Ahi, const float2* Alo, size
                                       const double2* x, const double2* b, double2* r, cudaStream_t s);
 // tcgen05 tensor-core GEMM Y = A X (A c32, X / Y c32, nrhs <= 64).  Returns cudaErrorNotSupported if the
 // shape is not supported by the kernel.
-// The kernel records a bounded-wait expiry in an error word inside ws and never clears it: callers clear it
-// (matvec_tc_clear_error) before a run of products and read it (matvec_tc_error_word) afterwards.
-cudaError_t launch_matvec_tc(const float2* A, size_t lda, int n, int nrhs, const float2* x, float2* y,
-                             void* ws, size_t ws_bytes, cudaStream_t s, const int* gate = nullptr);
+// tcgen05 tensor-core GEMM Y = A X (X / Y complex FP32, 2 <= nrhs <= 64) on the FP16 split copy of A that
+// launch_tc_prepare_a makes (matvec_tc_a16_bytes(n) bytes, from the complex FP32 matrix A, n x n).  Returns
+// cudaErrorNotSupported if the shape is not supported.  The kernel records a bounded-wait expiry in an
+// error word inside ws and never clears it: callers clear it (matvec_tc_clear_error) before a run of
+// products and read it (matvec_tc_error_word) afterwards.
+cudaError_t launch_matvec_tc(const void* a16, int n, int nrhs, const float2* x, float2* y, void* ws,
+                             size_t ws_bytes, cudaStream_t s, const int* gate = nullptr);
 cudaError_t matvec_tc_clear_error(void* ws, int n, int nrhs, cudaStream_t s);
+size_t matvec_tc_a16_bytes(int n);
+cudaError_t launch_tc_prepare_a(const float2* A, int n, void* a16, cudaStream_t s);
 size_t matvec_tc_workspace_bytes(int n, int nrhs);
 // Device word where the tensor-core kernel records a bounded-wait expiry (0 = none) inside ws.
 int* matvec_tc_error_word(void* ws, int n, int nrhs);

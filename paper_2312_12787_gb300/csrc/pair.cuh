@@ -167,11 +167,27 @@ BEM_HD void assemble_pair_f2(const ElemDev& e, const DomTab& dom, const Quad& q,
       A1 = f2_mul(f2_mul(WD, IR), f2_sub(NN, f2_pow2(CC, 2.f)));
       A0 = f2_mul(WD, CC);
     }
+    // The Hankel values of both row domains.  One call site in a rolled loop: the Bessel code is long,
+    // and two inlined copies overflow the instruction cache.
+    Bessel01F2 bh[2];
+    {
+      const double x0 = kk[0] * r, x1 = kk[1] * r;
+      const F2 X0 = f2_mul(K[0], R), X1 = f2_mul(K[1], R);
+      Bessel01F2 b0{}, b1{};
+#pragma unroll 1
+      for (int h = 0; h < 2; ++h) {
+        if ((h ? sg[1] : sg[0]) == 0.f) continue;
+        Bessel01F2 b;
+        bessel01_f2(h ? x1 : x0, h ? X1 : X0, b);
+        if (h) b1 = b; else b0 = b;
+      }
+      bh[0] = b0;
+      bh[1] = b1;
+    }
 #pragma unroll
     for (int half = 0; half < 2; ++half) {
       if (sg[half] == 0.f) continue;
-      Bessel01F2 b;
-      bessel01_f2(kk[half] * r, f2_mul(K[half], R), b);
+      const Bessel01F2& b = bh[half];
       c2_acc(sS[half], WD, b.j0, b.y0);
       c2_acc(sD[half], WCJ, b.j1, b.y1);
       if (eq[half].bm) {

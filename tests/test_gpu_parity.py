@@ -206,18 +206,22 @@ def test_invalid_mesh_rejected_on_device_path(B, torch):
     p.close()
 
 
-@pytest.mark.parametrize("ne,nrhs", [(700, 3), (700, 64), (4096, 64)])
+@pytest.mark.parametrize("ne,nrhs", [(700, 3), (701, 64), (4096, 64)])
 def test_matvec_tensor_core_matches_reference(B, torch, ne, nrhs):
-    """3xTF32 tcgen05 GEMM: y = A_hi x against the complex128 product of the same stored FP32 matrix.
-    4096 elements x 64 columns is the launch configuration the benchmark times."""
+    """FP16 x 3 tcgen05 GEMM: y = A_hi x against the complex128 product of the same stored FP32 matrix.
+    4096 elements x 64 columns is the launch configuration the benchmark times; 701 elements give a row
+    length that needs the padded FP16 stride.  Column 1 is scaled by 1e-4 and column 2 has entries spread
+    over six decades, which exercises the per-column scaling and FP16's subnormal range."""
     wp = W.Problem(k=[20.0, 30.0], eps=[1.0, 2.25], segments=[W.Segment(W.star(ne, 0.3, 5), P=0, M=1, closed=True)])
     p = B.Problem.from_workload(wp, prec="mixed_tc")
     n2 = p.bem_num_unknowns()
     A = torch.empty((n2, n2), dtype=torch.complex128, device="cuda")
     p.bem_get_matrix(A, which=0)
     g = torch.Generator(device="cpu").manual_seed(nrhs)
-    x = torch.randn((nrhs, n2), dtype=torch.complex128, generator=g).cuda()
-    x = x.to(torch.complex64).to(torch.complex128)        # the kernel sees FP32 inputs
+    x = torch.randn((nrhs, n2), dtype=torch.complex128, generator=g)
+    x[1] *= 1e-4
+    x[2] *= 10.0 ** (-6.0 * torch.rand(n2, generator=g, dtype=torch.float64))
+    x = x.cuda().to(torch.complex64).to(torch.complex128)  # the kernel sees FP32 inputs
     y = torch.empty_like(x)
     for rep in range(2):                                   # two calls in a row: no state carried over
         p.bem_profile_enable(True)
@@ -226,8 +230,9 @@ def test_matvec_tensor_core_matches_reference(B, torch, ne, nrhs):
         assert prof["matvec"][1] == 1
         ref = (A @ x.T).T
         err = (torch.linalg.vector_norm(y - ref, dim=1) / torch.linalg.vector_norm(ref, dim=1)).max().item()
-        # 3xTF32 products with FP32 tensor-core accumulation over 8-step segments: measured 2.1e-6 at
-        # 8192 x 64; the FP32 SIMT kernels reach ~1e-6.  The inner solves run at 1e-5.
+        # 22-bit split operands with FP32 tensor-core accumulation over 256-value segments (the previous
+        # 3xTF32 kernel measured 2.1e-6 at 8192 x 64); the FP32 SIMT kernels reach ~1e-6.  The inner
+        # solves run at 1e-5.
         assert err <= 5e-6, err
     p.close()
 
