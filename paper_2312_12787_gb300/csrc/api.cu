@@ -372,6 +372,11 @@ Solver carve_solver(bem_problem* p, int nrhs, bool fp32) {
   return sv;
 }
 
+// Bytes of the Krylov basis of a solver (free scratch outside a GMRES run).
+size_t basis_bytes(const Solver& sv) {
+  return (size_t)(sv.st.m + 1) * sv.st.nrhs * sv.st.n * (sv.st.basis_fp32 ? sizeof(float2) : sizeof(double2));
+}
+
 // One unrestarted GMRES run from x0 = 0 on r0 (FP64 block), adding the correction into x.
 bem_status gmres_run(bem_problem* p, Solver& sv, const double2* r0, double2* x, const std::vector<double>& tols,
                      std::vector<int>& iters, std::vector<double>& resid, cudaStream_t s) {
@@ -516,7 +521,7 @@ bem_status solve_impl(bem_problem* p, int nrhs, const double2* b, double2* x, in
       {
         Phase ph(p, BEM_PH_RESIDUAL, s, 2);   // split of x, double-float product
         CU(launch_residual_split(static_cast<const float2*>(p->d_A), static_cast<const float2*>(p->d_Alo), n2, n2,
-                                 nrhs, x, b, sv.r, sv.st.V, s));   // the basis is free here
+                                 nrhs, x, b, sv.r, sv.st.V, s, basis_bytes(sv)));   // the basis is free here
       }
       st = column_norms(p, sv, sv.r, nrhs, rn, s);
       if (st != BEM_OK) return st;
@@ -831,7 +836,7 @@ BEM_API bem_status bem_residual(bem_problem* p, int n_rhs, const bem_c64* x_dev,
   if (st != BEM_OK) return st;
   Solver sv = carve_solver(p, n_rhs, true);
   CU(launch_residual_split(static_cast<const float2*>(p->d_A), static_cast<const float2*>(p->d_Alo), n2, n2, n_rhs, x,
-                           b, r, sv.st.V, s));
+                           b, r, sv.st.V, s, basis_bytes(sv)));
   return BEM_OK;
 }
 

@@ -98,9 +98,11 @@ cudaError_t launch_matvec_c64(const double2* A, size_t lda, int n, int nrhs, con
 cudaError_t launch_matvec_c32(const float2* A, size_t lda, int n, int nrhs, const float2* x, float2* y,
                               const int* active, cudaStream_t s, const int* gate = nullptr);
 // r = b - (hi + lo) x, with FP64 x, b, r (refinement residual) in double-float arithmetic; ws must hold
-// 2 * nrhs * n float2.  The _f64 variant computes the same in FP64 arithmetic.
+// 2 * nrhs * n float2 (ws_bytes: its size, 0 = exactly that).  The _f64 variant computes the same in FP64 arithmetic.
+// With ws_bytes beyond the x split, the tiled product may split K over CTAs and keep FP64 partials there.
 cudaError_t launch_residual_split(const float2* Ahi, const float2* Alo, size_t lda, int n, int nrhs,
-                                  const double2* x, const double2* b, double2* r, void* ws, cudaStream_t s);
+                                  const double2* x, const double2* b, double2* r, void* ws, cudaStream_t s,
+                                  size_t ws_bytes = 0);
 cudaError_t launch_residual_c64(const double2* A, size_t lda, int n, int nrhs, const double2* x, const double2* b,
                                 double2* r, cudaStream_t s);
 cudaError_t launch_residual_split_f64(const float2* Ahi, const float2* Alo, size_t lda, int n, int nrhs,

@@ -12,6 +12,7 @@
 // 128 CTAs.  In the projection kernel each warp owns every eighth basis vector (no block barriers); in
 // the update kernel four thread groups share the basis vectors of a chunk and meet in shared memory.
 #include <algorithm>
+#include <atomic>
 
 #include "givens.cuh"
 #include "internal.cuh"
@@ -102,31 +103,63 @@ __global__ void __launch_bounds__(kThreads) k_start_scale(KrylovState st, const 
   Vec<T>::store(v0 + k, cscale(r0[(size_t)s * st.n + k], 1.0 / st.beta[s]));
 }
 
-// Partial projections <v_i, w> over one 64-entry chunk: warp w takes basis vectors i = w, w+8, ...;
-// each lane two entries; products and the warp reduction in the basis precision, chunk partials stored
-// for an FP64 sum over chunks.
-template <typename T>
+// Two consecutive entries in the basis precision, moved as one 16-byte (float2) or two 16-byte (double2)
+// accesses; entry indices are even and n is even, so a pair never straddles the end of a vector.
+template <typename T> struct Pair;
+template <> struct Pair<float2> {
+  __device__ static __forceinline__ void load(const float2* p, float2& a, float2& b) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    a = make_float2(v.x, v.y);
+    b = make_float2(v.z, v.w);
+  }
+  __device__ static __forceinline__ void store(float2* p, float2 a, float2 b) {
+    *reinterpret_cast<float4*>(p) = make_float4(a.x, a.y, b.x, b.y);
+  }
+};
+template <> struct Pair<double2> {
+  __device__ static __forceinline__ void load(const double2* p, double2& a, double2& b) { a = p[0]; b = p[1]; }
+  __device__ static __forceinline__ void store(double2* p, double2 a, double2 b) { p[0] = a; p[1] = b; }
+};
+
+// Partial projections <v_i, w> over one chunk of CH entries: warp w takes basis vectors i = w, w+8, ...;
+// lane l holds the pairs k = chunk start + 2 (32 p + l), p < CH/64, so each load instruction of the warp
+// moves 512 (FP32) or 1024 (FP64) contiguous bytes.  Products in the basis precision, the lane sums and the
+// warp reduction in FP64; chunk partials are stored for an FP64 sum over chunks.
+template <typename T, int CH>
 __global__ void __launch_bounds__(kThreads) k_dots(KrylovState st, int nchunk, int j) {
   using F = typename Vec<T>::acc_t;
+  constexpr int P = CH / 64;
   const int c = blockIdx.x, s = blockIdx.y;
   if (!st.active[s]) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const size_t stride = (size_t)st.nrhs * st.n;
   const T* W = static_cast<const T*>(st.W) + (size_t)s * st.n;
   const T* V = static_cast<const T*>(st.V) + (size_t)s * st.n;
-  const int k0 = c * kCh + lane, k1 = k0 + 32;
-  const bool in0 = k0 < st.n, in1 = k1 < st.n;
-  T zero;
-  zero.x = 0; zero.y = 0;
-  const T w0 = in0 ? W[k0] : zero, w1 = in1 ? W[k1] : zero;
+  T w[2 * P];
+#pragma unroll
+  for (int p = 0; p < P; ++p) {
+    const int k = c * CH + 2 * (32 * p + lane);
+    if (k < st.n) {
+      Pair<T>::load(W + k, w[2 * p], w[2 * p + 1]);
+    } else {
+      w[2 * p].x = w[2 * p].y = w[2 * p + 1].x = w[2 * p + 1].y = 0;
+    }
+  }
   for (int i = warp; i <= j; i += kThreads / 32) {
     const T* vi = V + (size_t)i * stride;
-    const T v0 = in0 ? vi[k0] : zero, v1 = in1 ? vi[k1] : zero;
-    F px = (F)v0.x * (F)w0.x + (F)v0.y * (F)w0.y + (F)v1.x * (F)w1.x + (F)v1.y * (F)w1.y;   // conj(v) w
-    F py = (F)v0.x * (F)w0.y - (F)v0.y * (F)w0.x + (F)v1.x * (F)w1.y - (F)v1.y * (F)w1.x;
-    px = warp_sum(px);
-    py = warp_sum(py);
-    if (lane == 0) st.part[((size_t)s * nchunk + c) * (st.m + 1) + i] = make_double2((double)px, (double)py);
+    F px = 0, py = 0;
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+      const int k = c * CH + 2 * (32 * p + lane);
+      if (k < st.n) {
+        T a, b;
+        Pair<T>::load(vi + k, a, b);
+        px += (F)a.x * (F)w[2 * p].x + (F)a.y * (F)w[2 * p].y + (F)b.x * (F)w[2 * p + 1].x + (F)b.y * (F)w[2 * p + 1].y;
+        py += (F)a.x * (F)w[2 * p].y - (F)a.y * (F)w[2 * p].x + (F)b.x * (F)w[2 * p + 1].y - (F)b.y * (F)w[2 * p + 1].x;
+      }
+    }
+    const double hx = warp_sum((double)px), hy = warp_sum((double)py);
+    if (lane == 0) st.part[((size_t)s * nchunk + c) * (st.m + 1) + i] = make_double2(hx, hy);
   }
 }
 
@@ -153,50 +186,56 @@ __global__ void k_dots_reduce(KrylovState st, int nchunk, int pass, int j) {
   }
 }
 
-// w -= sum_i h_i v_i over one 64-entry chunk; 256 threads = 64 entries x 4 interleaved subsets of i,
-// combined through shared memory.  Also writes the chunk's ||w||^2.
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_update(KrylovState st, int nchunk, int j) {
+// w -= sum_i h_i v_i over one chunk of CH entries: CH/2 threads, each owning one pair of entries and
+// running over all i (h staged in shared memory in the basis precision), so no partial sums are combined
+// across threads; also writes the chunk's ||w||^2.
+constexpr int kHsMax = 1001;
+template <typename T, int CH>
+__global__ void __launch_bounds__(CH / 2) k_update(KrylovState st, int nchunk, int j) {
   using F = typename Vec<T>::acc_t;
-  __shared__ F hs[2 * 1024];                    // projections in the basis precision, converted once
-  __shared__ F accs[4][kCh][2];
-  __shared__ double red[8];
+  __shared__ F hs[2 * kHsMax];
+  __shared__ double red[CH / 64];
   const int c = blockIdx.x, s = blockIdx.y;
   if (!st.active[s]) return;
-  for (int i = threadIdx.x; i <= j; i += kThreads) {
+  for (int i = threadIdx.x; i <= j; i += CH / 2) {
     const double2 h = st.hcol[(size_t)s * (st.m + 1) + i];
     hs[2 * i] = (F)h.x;
     hs[2 * i + 1] = (F)h.y;
   }
   __syncthreads();
-  const int e = threadIdx.x & (kCh - 1), sub = threadIdx.x >> 6;
-  const int k = c * kCh + e;
+  const int k = c * CH + 2 * threadIdx.x;
   const size_t stride = (size_t)st.nrhs * st.n;
-  const T* V = static_cast<const T*>(st.V) + (size_t)s * st.n;
-  F ax = 0, ay = 0;
-  if (k < st.n) {
-#pragma unroll 4
-    for (int i = sub; i <= j; i += 4) {
-      const T v = V[(size_t)i * stride + k];
-      const F hx = hs[2 * i], hy = hs[2 * i + 1];
-      ax += hx * (F)v.x - hy * (F)v.y;
-      ay += hx * (F)v.y + hy * (F)v.x;
-    }
-  }
-  accs[sub][e][0] = ax;
-  accs[sub][e][1] = ay;
-  __syncthreads();
   double nrm = 0.0;
-  if (sub == 0 && k < st.n) {
-    T* W = static_cast<T*>(st.W) + (size_t)s * st.n;
-    T w = W[k];
-    w.x = w.x - (accs[0][e][0] + accs[1][e][0] + accs[2][e][0] + accs[3][e][0]);
-    w.y = w.y - (accs[0][e][1] + accs[1][e][1] + accs[2][e][1] + accs[3][e][1]);
-    W[k] = w;
-    nrm = (double)w.x * (double)w.x + (double)w.y * (double)w.y;
+  if (k < st.n) {
+    const T* V = static_cast<const T*>(st.V) + (size_t)s * st.n + k;
+    F ax = 0, ay = 0, bx = 0, by = 0;
+#pragma unroll 8
+    for (int i = 0; i <= j; ++i) {
+      T a, b;
+      Pair<T>::load(V + (size_t)i * stride, a, b);
+      const F hx = hs[2 * i], hy = hs[2 * i + 1];
+      ax += hx * (F)a.x - hy * (F)a.y;
+      ay += hx * (F)a.y + hy * (F)a.x;
+      bx += hx * (F)b.x - hy * (F)b.y;
+      by += hx * (F)b.y + hy * (F)b.x;
+    }
+    T* W = static_cast<T*>(st.W) + (size_t)s * st.n + k;
+    T w0, w1;
+    Pair<T>::load(W, w0, w1);
+    w0.x -= ax; w0.y -= ay;
+    w1.x -= bx; w1.y -= by;
+    Pair<T>::store(W, w0, w1);
+    nrm = (double)w0.x * (double)w0.x + (double)w0.y * (double)w0.y + (double)w1.x * (double)w1.x +
+          (double)w1.y * (double)w1.y;
   }
-  nrm = block_sum(nrm, red);
-  if (threadIdx.x == 0) st.npart[(size_t)s * nchunk + c] = nrm;
+  nrm = warp_sum(nrm);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = nrm;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < CH / 64; ++q) t += red[q];
+    st.npart[(size_t)s * nchunk + c] = t;
+  }
 }
 
 // h_{j+1,j} = ||w||; apply the previous Givens rotations to column j, form the new one, update g and
@@ -304,6 +343,35 @@ __global__ void __launch_bounds__(kThreads) k_xupdate(KrylovState st, double2* x
 int nchunk_of(int n) { return (n + kCh - 1) / kCh; }
 int nblk_of(int n) { return (n + kThreads - 1) / kThreads; }
 
+int sm_count() {
+  static std::atomic<int> cache[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+  int v = cache[dev].load(std::memory_order_relaxed);
+  if (v > 0) return v;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 1;
+  cache[dev].store(v, std::memory_order_relaxed);
+  return v;
+}
+
+// Chunk length of the projection and update kernels: the largest of 512, 256, 128 entries that still gives
+// at least two CTAs per SM over all systems, else 64 (a single system of a few thousand unknowns).  Longer
+// chunks move more bytes per warp reduction and per instruction.
+int chunk_of(int n, int nrhs) {
+  for (int ch : {512, 256, 128})
+    if ((long long)((n + ch - 1) / ch) * nrhs >= 2LL * sm_count()) return ch;
+  return kCh;
+}
+
+template <typename T, int CH>
+void orth_pass(const KrylovState& st, int pass, int j, cudaStream_t s) {
+  const int nc = (st.n + CH - 1) / CH;
+  dim3 grd(nc, st.nrhs);
+  k_dots<T, CH><<<grd, kThreads, 0, s>>>(st, nc, j);
+  k_dots_reduce<<<dim3((j + 8) / 8, st.nrhs), 256, 0, s>>>(st, nc, pass, j);
+  k_update<T, CH><<<grd, CH / 2, 0, s>>>(st, nc, j);
+}
+
 template <typename T>
 cudaError_t start_t(const KrylovState& st, const double2* r0, cudaStream_t s) {
   const int nb = nblk_of(st.n);
@@ -316,19 +384,22 @@ cudaError_t start_t(const KrylovState& st, const double2* r0, cudaStream_t s) {
 
 template <typename T>
 cudaError_t orth_t(const KrylovState& st, int passes, int j, cudaStream_t s) {
-  const int nc = nchunk_of(st.n);
-  dim3 grd(nc, st.nrhs);
+  const int ch = chunk_of(st.n, st.nrhs);
   for (int p = 0; p < passes; ++p) {
-    k_dots<T><<<grd, kThreads, 0, s>>>(st, nc, j);
-    k_dots_reduce<<<dim3((j + 8) / 8, st.nrhs), 256, 0, s>>>(st, nc, p, j);
-    k_update<T><<<grd, kThreads, 0, s>>>(st, nc, j);
+    switch (ch) {
+      case 512: orth_pass<T, 512>(st, p, j, s); break;
+      case 256: orth_pass<T, 256>(st, p, j, s); break;
+      case 128: orth_pass<T, 128>(st, p, j, s); break;
+      default: orth_pass<T, 64>(st, p, j, s); break;
+    }
   }
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t finish_t(const KrylovState& st, double tol, int j, cudaStream_t s) {
-  const int nc = nchunk_of(st.n);
+  const int ch = chunk_of(st.n, st.nrhs);
+  const int nc = (st.n + ch - 1) / ch;   // the update kernel's chunks (its squared norms)
   k_finish<<<st.nrhs, 32, 0, s>>>(st, nc, tol, j);
   k_scale_next<T><<<dim3(nblk_of(st.n), st.nrhs), kThreads, 0, s>>>(st, j);
   k_advance<<<1, 32, 0, s>>>(st);

@@ -371,11 +371,17 @@ __global__ void __launch_bounds__(256) k_resid_df_gemv(const float2* __restrict_
 }
 
 // Tiled version for many columns: tile 32 rows x 64 columns x 16, 256 threads, each 2 rows x 4 columns.
+// K may be split over blockIdx.z in ranges of kchunk columns: then each CTA writes its partial product
+// (rounded to FP64) to part[z][s][row] and k_resid_combine forms r; with part == nullptr the CTA covers all
+// of K and writes r directly.
+constexpr int kResBR = 32, kResBS = 64, kResBK = 16;
 __global__ void __launch_bounds__(256) k_resid_df_gemm(const float2* __restrict__ Ah, const float2* __restrict__ Al,
                                                         size_t lda, int n, int nrhs, const float2* __restrict__ xh,
                                                         const float2* __restrict__ xl, const double2* __restrict__ b,
-                                                        double2* __restrict__ r) {
-  constexpr int BR = 32, BS = 64, BK = 16;
+                                                        double2* __restrict__ r, int kchunk,
+                                                        double2* __restrict__ part) {
+  constexpr int BR = kResBR, BS = kResBS, BK = kResBK;
+  const int kbeg = blockIdx.z * kchunk, kend = min(n, kbeg + kchunk);
   __shared__ float2 Ash[BK][BR + 1], Asl[BK][BR + 1];
   __shared__ float2 Xsh[BK][BS + 1], Xsl[BK][BS + 1];
   const int tid = threadIdx.x;
@@ -387,14 +393,14 @@ __global__ void __launch_bounds__(256) k_resid_df_gemm(const float2* __restrict_
 #pragma unroll
     for (int q = 0; q < 4; ++q) sr[a][q] = cr[a][q] = si[a][q] = ci[a][q] = 0.f;
   const float2 z = make_float2(0.f, 0.f);
-  for (int k0 = 0; k0 < n; k0 += BK) {
+  for (int k0 = kbeg; k0 < kend; k0 += BK) {
     // A: 32 x 16 = 512 entries (2 per thread); X: 64 x 16 = 1024 entries (4 per thread)
 #pragma unroll
     for (int t = 0; t < 2; ++t) {
       const int e = tid + t * 256;
       const int rr = e >> 4, kk = e & 15;
       const int gr = r0 + rr, gk = k0 + kk;
-      const bool in = gr < n && gk < n;
+      const bool in = gr < n && gk < kend;
       Ash[kk][rr] = in ? __ldcs(Ah + (size_t)gr * lda + gk) : z;
       Asl[kk][rr] = in ? __ldcs(Al + (size_t)gr * lda + gk) : z;
     }
@@ -403,7 +409,7 @@ __global__ void __launch_bounds__(256) k_resid_df_gemm(const float2* __restrict_
       const int e = tid + t * 256;
       const int ss = e >> 4, kk = e & 15;
       const int gs = s0 + ss, gk = k0 + kk;
-      const bool in = gs < nrhs && gk < n;
+      const bool in = gs < nrhs && gk < kend;
       Xsh[kk][ss] = in ? xh[(size_t)gs * n + gk] : z;
       Xsl[kk][ss] = in ? xl[(size_t)gs * n + gk] : z;
     }
@@ -428,11 +434,30 @@ __global__ void __launch_bounds__(256) k_resid_df_gemm(const float2* __restrict_
     for (int q = 0; q < 4; ++q) {
       const int gr = r0 + ty + 16 * a, gs = s0 + tx + 16 * q;
       if (gr < n && gs < nrhs) {
-        const double2 bb = b[(size_t)gs * n + gr];
-        r[(size_t)gs * n + gr] = make_double2(bb.x - ((double)sr[a][q] + (double)cr[a][q]),
-                                              bb.y - ((double)si[a][q] + (double)ci[a][q]));
+        const double2 ax = make_double2((double)sr[a][q] + (double)cr[a][q], (double)si[a][q] + (double)ci[a][q]);
+        if (part) {
+          part[((size_t)blockIdx.z * nrhs + gs) * n + gr] = ax;
+        } else {
+          const double2 bb = b[(size_t)gs * n + gr];
+          r[(size_t)gs * n + gr] = make_double2(bb.x - ax.x, bb.y - ax.y);
+        }
       }
     }
+}
+
+// r = b - sum over the K splits of the partial products (FP64, in split order).
+__global__ void k_resid_combine(const double2* __restrict__ part, int nsplit, size_t count,
+                                const double2* __restrict__ b, double2* __restrict__ r) {
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < count; t += (size_t)gridDim.x * blockDim.x) {
+    double ax = 0.0, ay = 0.0;
+    for (int z = 0; z < nsplit; ++z) {
+      const double2 v = part[(size_t)z * count + t];
+      ax += v.x;
+      ay += v.y;
+    }
+    const double2 bb = b[t];
+    r[t] = make_double2(bb.x - ax, bb.y - ay);
+  }
 }
 
 __global__ void k_b_minus(const double2* b, double2* r, size_t count) {
@@ -508,9 +533,40 @@ cudaError_t launch_matvec_c32(const float2* A, size_t lda, int n, int nrhs, cons
   return cudaGetLastError();
 }
 
+// Number of K splits for the tiled residual: the CTA count tiles x S should fill whole waves of the SMs
+// (tiles alone, e.g. 256 for 8192 unknowns x 64 columns, leave a partial second wave), with at least 512
+// columns of K per split and the partials within the workspace.
+static int resid_splits(int n, int nrhs, size_t part_room) {
+  static std::atomic<int> slots_cache{0};
+  int slots = slots_cache.load(std::memory_order_relaxed);
+  if (slots <= 0) {
+    int dev = 0, sms = 0, per = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_resid_df_gemm, 256, 0) != cudaSuccess || per <= 0)
+      return 1;
+    slots = sms * per;
+    slots_cache.store(slots, std::memory_order_relaxed);
+  }
+  const long long tiles = (long long)((n + kResBR - 1) / kResBR) * ((nrhs + kResBS - 1) / kResBS);
+  int best = 1;
+  double best_eff = 0.0;
+  for (int S = 1; S <= 32; ++S) {
+    if (S > 1 && (n / S < 512 || (size_t)S * nrhs * n * sizeof(double2) > part_room)) break;
+    const long long ctas = tiles * S;
+    const double eff = (double)ctas / ((double)slots * (double)((ctas + slots - 1) / slots));
+    if (eff > best_eff + 1e-3) {
+      best_eff = eff;
+      best = S;
+    }
+  }
+  return best;
+}
+
 cudaError_t launch_residual_split(const float2* Ahi, const float2* Alo, size_t lda, int n, int nrhs,
-                                  const double2* x, const double2* b, double2* r, void* ws, cudaStream_t s) {
-  // ws holds x split into two complex FP32 blocks (2 * nrhs * n float2)
+                                  const double2* x, const double2* b, double2* r, void* ws, cudaStream_t s,
+                                  size_t ws_bytes) {
+  // ws holds x split into two complex FP32 blocks (2 * nrhs * n float2), then the K-split partials
   float2* xh = static_cast<float2*>(ws);
   float2* xl = xh + (size_t)nrhs * n;
   k_split_x<<<512, 256, 0, s>>>(x, xh, xl, (size_t)nrhs * n);
@@ -518,8 +574,13 @@ cudaError_t launch_residual_split(const float2* Ahi, const float2* Alo, size_t l
     dim3 grd((n + 7) / 8, nrhs);
     k_resid_df_gemv<<<grd, 256, 0, s>>>(Ahi, Alo, lda, n, xh, xl, b, r);
   } else {
-    dim3 grd((n + 31) / 32, (nrhs + 63) / 64);
-    k_resid_df_gemm<<<grd, 256, 0, s>>>(Ahi, Alo, lda, n, nrhs, xh, xl, b, r);
+    const size_t xbytes = ((2 * (size_t)nrhs * n * sizeof(float2)) + 255) & ~(size_t)255;
+    const int S = ws_bytes > xbytes ? resid_splits(n, nrhs, ws_bytes - xbytes) : 1;
+    const int kchunk = ((n + S - 1) / S + kResBK - 1) / kResBK * kResBK;
+    double2* part = S > 1 ? reinterpret_cast<double2*>(static_cast<char*>(ws) + xbytes) : nullptr;
+    dim3 grd((n + kResBR - 1) / kResBR, (nrhs + kResBS - 1) / kResBS, S);
+    k_resid_df_gemm<<<grd, 256, 0, s>>>(Ahi, Alo, lda, n, nrhs, xh, xl, b, r, S > 1 ? kchunk : n, part);
+    if (S > 1) k_resid_combine<<<1024, 256, 0, s>>>(part, S, (size_t)nrhs * n, b, r);
   }
   return cudaGetLastError();
 }
