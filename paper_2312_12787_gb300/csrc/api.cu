@@ -384,17 +384,25 @@ bem_status gmres_run(bem_problem* p, Solver& sv, const double2* r0, double2* x, 
   const int n2 = st.n, nrhs = st.nrhs;
   const double tol = tols[0];
   CU(cudaMemcpyAsync(const_cast<double*>(st.tolv), tols.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, s));
-  {
-    Phase ph(p, BEM_PH_GIVENS, s, 3);
-    CU(krylov_start(st, r0, tol, s));
-  }
   const bool fp32 = st.basis_fp32;
   const size_t tb = fp32 ? sizeof(float2) : sizeof(double2);
   const bool use_tc = fp32 && p->o.prec == BEM_PREC_MIXED_TC && nrhs > 1 && matvec_tc_supported(n2, nrhs);
+  struct ClearB {   // the operand pointers belong to this run only
+    KrylovState& st;
+    ~ClearB() { st.b16hi = st.b16lo = nullptr; }
+  } clear_b{st};
   if (use_tc) {
     const bem_status a = ensure_a16(p, s);
     if (a != BEM_OK) return a;
     CU(matvec_tc_clear_error(sv.tcws, n2, nrhs, s));
+    // the Krylov kernels write each unit-norm basis vector as the product's FP16 operand (scale 1); rows
+    // of absent systems stay zero
+    matvec_tc_b_operand(sv.tcws, n2, &st.b16hi, &st.b16lo, &st.ldb16);
+    CU(cudaMemsetAsync(sv.tcws, 0, matvec_tc_b_bytes(n2), s));
+  }
+  {
+    Phase ph(p, BEM_PH_GIVENS, s, 3);
+    CU(krylov_start(st, r0, tol, s));
   }
   // Iterations are queued kSyncEvery at a time before the host reads the active count: the GPU never
   // waits for the host between iterations.  Once every system has converged, the queued iterations find
@@ -412,8 +420,8 @@ bem_status gmres_run(bem_problem* p, Solver& sv, const double2* r0, double2* x, 
       CU(launch_matvec_c64(static_cast<const double2*>(p->d_A), n2, n2, nrhs, static_cast<const double2*>(Vj),
                            static_cast<double2*>(st.W), s, gate));
     } else if (use_tc) {
-      CU(launch_matvec_tc(p->d_A16, n2, nrhs, static_cast<const float2*>(Vj), static_cast<float2*>(st.W), sv.tcws,
-                          sv.tcws_bytes, s, gate));
+      CU(launch_matvec_tc(p->d_A16, n2, nrhs, nullptr, static_cast<float2*>(st.W), sv.tcws, sv.tcws_bytes, s,
+                          gate));   // B = V_j, written by the Krylov kernels
     } else {
       CU(launch_matvec_c32(static_cast<const float2*>(p->d_A), n2, n2, nrhs, static_cast<const float2*>(Vj),
                            static_cast<float2*>(st.W), st.active, s, gate));

@@ -36,6 +36,7 @@
 #include <cstdio>
 
 #include "internal.cuh"
+#include "tc_operand.cuh"
 
 namespace bem {
 
@@ -51,7 +52,6 @@ constexpr int kStage = 4 * kTile;    // A_hi, A_lo, B_hi, B_lo
 constexpr int kThreads = 256;
 constexpr uint32_t kTmemCols = 512;  // two buffers x (D1, D2) x 128 FP32 columns
 constexpr int kMaxRhs = 64;
-constexpr float kLoScale = 2048.f;   // lo parts are stored times 2^11
 constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s
 constexpr int kMaxDev = 64;
 
@@ -300,7 +300,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int i = 0; i < 32; ++i) acc[cc * 32 + i] += v[i];
         tmem_ld32(ta + (uint32_t)(kN + cc * 32), v);             // D2, lo terms times 2^11
 #pragma unroll
-        for (int i = 0; i < 32; ++i) acc[cc * 32 + i] = fmaf(v[i], 1.f / kLoScale, acc[cc * 32 + i]);
+        for (int i = 0; i < 32; ++i) acc[cc * 32 + i] = fmaf(v[i], 1.f / kTcLoScale, acc[cc * 32 + i]);
       }
       tc_fence_before();
       mbar_arrive(su32(&bars->acce[b]));
@@ -359,11 +359,6 @@ __device__ __forceinline__ float pow2_scale(float v) {
   return ldexpf(1.f, -e);
 }
 
-__device__ __forceinline__ void split16(float v, __half& h, __half& l) {
-  h = __float2half_rn(v);
-  l = __float2half_rn((v - __half2float(h)) * kLoScale);
-}
-
 // Bt rows (K-major, ld16(n) FP16 each): row s < 64: (Re x_s[c], -Im x_s[c]); row 64+s: (Im x_s[c], Re x_s[c]),
 // scaled by t_s = pow2_scale(max |x_s|) and split into hi and lo; rows of absent columns are zero.
 __global__ void k_tc_prep_b(const float2* __restrict__ x, int n, int nrhs, const unsigned* __restrict__ cmax,
@@ -371,25 +366,17 @@ __global__ void k_tc_prep_b(const float2* __restrict__ x, int n, int nrhs, const
                             const int* gate) {
   if (gate && *gate == 0) return;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;   // complex column index along K
-  const int row = blockIdx.y;                             // 0..127
+  const int s = blockIdx.y;                               // 0..63
   if (c >= n) return;
-  const int s = row & 63;
-  float v0 = 0.f, v1 = 0.f, t = 1.f;
+  float re = 0.f, im = 0.f, t = 1.f;
   if (s < nrhs) {
     t = pow2_scale(__uint_as_float(cmax[s]));
     const float2 xv = x[(size_t)s * n + c];
-    if (row < 64) { v0 = xv.x; v1 = -xv.y; }
-    else { v0 = xv.y; v1 = xv.x; }
-    v0 *= t;
-    v1 *= t;
+    re = xv.x * t;
+    im = xv.y * t;
   }
-  if (c == 0 && row < 64) tsc[row] = t;
-  const size_t o = (size_t)row * ldb + 2 * c;
-  __half h0, l0, h1, l1;
-  split16(v0, h0, l0);
-  split16(v1, h1, l1);
-  bhi[o] = h0; bhi[o + 1] = h1;
-  blo[o] = l0; blo[o + 1] = l1;
+  if (c == 0) tsc[s] = t;
+  tc_write_b(bhi, blo, ldb, s, c, re, im);
 }
 
 // Split copy of A: one CTA per row; row scale 2^-e_r from the row's largest |real entry|.
@@ -414,8 +401,8 @@ __global__ void __launch_bounds__(256) k_tc_prep_a(const float2* __restrict__ A,
   for (int c = threadIdx.x; c < n; c += 256) {
     const float2 v = row[c];
     __half h0, l0, h1, l1;
-    split16(v.x * sc, h0, l0);
-    split16(v.y * sc, h1, l1);
+    tc_split16(v.x * sc, h0, l0);
+    tc_split16(v.y * sc, h1, l1);
     hr[2 * c] = h0; hr[2 * c + 1] = h1;
     lr[2 * c] = l0; lr[2 * c + 1] = l1;
   }
@@ -444,7 +431,7 @@ __global__ void k_tc_reduce(const float* __restrict__ partial, int n, int nrhs, 
     re += p[s];
     im += p[64 + s];
   }
-  const float inv = 1.f / (rsc[r] * tsc[s]);   // a power of two: exact
+  const float inv = 1.f / (rsc[r] * (tsc ? tsc[s] : 1.f));   // a power of two: exact
   y[(size_t)s * n + r] = make_float2(re * inv, im * inv);
 }
 
@@ -580,13 +567,25 @@ cudaError_t launch_matvec_tc(const void* a16, int n, int nrhs, const float2* x, 
   const int kpt = (cols + kKs - 1) / kKs;
   const long long total = (long long)tiles * kpt;
   const int G = grid_of(n);
-  cudaError_t e = cudaMemsetAsync(cmax, 0, 64 * sizeof(unsigned), s);
-  if (e != cudaSuccess) return e;
-  k_tc_colmax<<<dim3(8, nrhs), 256, 0, s>>>(x, n, nrhs, cmax, gate);
-  k_tc_prep_b<<<dim3((n + 255) / 256, kN), 256, 0, s>>>(x, n, nrhs, cmax, bhi, blo, ld, tsc, gate);
+  if (x) {
+    cudaError_t e = cudaMemsetAsync(cmax, 0, 64 * sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+  }
+  if (x) {
+    k_tc_colmax<<<dim3(8, nrhs), 256, 0, s>>>(x, n, nrhs, cmax, gate);
+    k_tc_prep_b<<<dim3((n + 255) / 256, kMaxRhs), 256, 0, s>>>(x, n, nrhs, cmax, bhi, blo, ld, tsc, gate);
+  }
   k_gemm_tc<<<G, kThreads, kSmemBytes, s>>>(mAh, mAl, mBh, mBl, n, kpt, total, part, err, gate);
-  k_tc_reduce<<<(n + 3) / 4, 256, 0, s>>>(part, n, nrhs, kpt, total, G, rsc, tsc, y, gate);
+  k_tc_reduce<<<(n + 3) / 4, 256, 0, s>>>(part, n, nrhs, kpt, total, G, rsc, x ? tsc : nullptr, y, gate);
   return cudaGetLastError();
 }
+
+void matvec_tc_b_operand(void* ws, int n, void** bhi, void** blo, size_t* ldb) {
+  *bhi = ws;
+  *blo = static_cast<char*>(ws) + b_bytes(n);
+  *ldb = ld16(n);
+}
+
+size_t matvec_tc_b_bytes(int n) { return 2 * b_bytes(n); }
 
 }  // namespace bem

@@ -114,8 +114,12 @@ cudaError_t launch_residual_split_f64(const float2* Ahi, const float2* Alo, size
 // cudaErrorNotSupported if the shape is not supported.  The kernel records a bounded-wait expiry in an
 // error word inside ws and never clears it: callers clear it (matvec_tc_clear_error) before a run of
 // products and read it (matvec_tc_error_word) afterwards.
+// x == nullptr: the block's B operand is already in ws in the FP16 x 3 format with scale 1 (the Krylov kernels
+// write it for unit-norm basis vectors; matvec_tc_b_operand gives its place).
 cudaError_t launch_matvec_tc(const void* a16, int n, int nrhs, const float2* x, float2* y, void* ws,
                              size_t ws_bytes, cudaStream_t s, const int* gate = nullptr);
+void matvec_tc_b_operand(void* ws, int n, void** bhi, void** blo, size_t* ldb);
+size_t matvec_tc_b_bytes(int n);
 cudaError_t matvec_tc_clear_error(void* ws, int n, int nrhs, cudaStream_t s);
 size_t matvec_tc_a16_bytes(int n);
 cudaError_t launch_tc_prepare_a(const float2* A, int n, void* a16, cudaStream_t s);
@@ -155,6 +159,11 @@ struct KrylovState {
   const double* tolv;  // nrhs per-system tolerances (overrides the scalar tol when non-null)
   int* jdev;        // current iteration index (device copy)
   int* n_active;    // device counter of active systems
+  // when non-null (FP32 basis feeding the tensor-core product): every new basis vector is also written as
+  // the FP16 x 3 operand of the next product (tc_operand.cuh), rows of stride ldb16
+  void* b16hi;
+  void* b16lo;
+  size_t ldb16;
 };
 int krylov_nchunk(int n);
 cudaError_t krylov_start(const KrylovState& st, const double2* r0, double tol_unused, cudaStream_t s);

@@ -16,6 +16,7 @@
 
 #include "givens.cuh"
 #include "internal.cuh"
+#include "tc_operand.cuh"
 
 namespace bem {
 
@@ -100,7 +101,10 @@ __global__ void __launch_bounds__(kThreads) k_start_scale(KrylovState st, const 
   const int k = blockIdx.x * kThreads + threadIdx.x, s = blockIdx.y;
   if (!st.active[s] || k >= st.n) return;
   T* v0 = static_cast<T*>(st.V) + (size_t)s * st.n;
-  Vec<T>::store(v0 + k, cscale(r0[(size_t)s * st.n + k], 1.0 / st.beta[s]));
+  const double2 v = cscale(r0[(size_t)s * st.n + k], 1.0 / st.beta[s]);
+  Vec<T>::store(v0 + k, v);
+  if (st.b16hi)
+    tc_write_b(static_cast<__half*>(st.b16hi), static_cast<__half*>(st.b16lo), st.ldb16, s, k, (float)v.x, (float)v.y);
 }
 
 // Two consecutive entries in the basis precision, moved as one 16-byte (float2) or two 16-byte (double2)
@@ -294,6 +298,8 @@ __global__ void __launch_bounds__(kThreads) k_scale_next(KrylovState st, int j) 
   w.x *= inv;
   w.y *= inv;
   Vn[k] = w;
+  if (st.b16hi)
+    tc_write_b(static_cast<__half*>(st.b16hi), static_cast<__half*>(st.b16lo), st.ldb16, s, k, (float)w.x, (float)w.y);
 }
 
 __global__ void k_advance(KrylovState st) {
