@@ -309,7 +309,6 @@ size_t krylov_bytes(int n2, int nrhs, int m, bool fp32) {
   add((size_t)nrhs * 4);                  // iters
   add((size_t)nrhs * 8);                  // resid
   add((size_t)nrhs * 8);                  // tolv
-  add(4);                                 // jdev
   add(4);                                 // n_active
   // mixed extras: residual r (FP64), rhs copy of the inner solve (FP32 not needed), tc workspace
   add((size_t)nrhs * n2 * 16);
@@ -363,7 +362,6 @@ Solver carve_solver(bem_problem* p, int nrhs, bool fp32) {
   st.iters = c.take<int>(nrhs);
   st.resid = c.take<double>(nrhs);
   st.tolv = c.take<double>(nrhs);
-  st.jdev = c.take<int>(1);
   st.n_active = c.take<int>(1);
   sv.r = c.take<double2>((size_t)nrhs * n2);
   sv.tcws_bytes = matvec_tc_workspace_bytes(n2, nrhs);
@@ -878,14 +876,17 @@ BEM_API bem_status bem_far_field(bem_problem* p, int n_rhs, const bem_c64* x_dev
   if (st != BEM_OK) return st;
   st = upload_geometry(p, s);
   if (st != BEM_OK) return st;
-  st = ensure_small(p, n_ang);
+  // d_small: the angles, then the per-angle element sums (2 x n_ang x N complex)
+  const size_t ang_slots = ((size_t)n_ang + 1) & ~(size_t)1;   // keep the complex part 16-byte aligned
+  st = ensure_small(p, ang_slots + (size_t)4 * n_ang * p->n);
   if (st != BEM_OK) return st;
   CU(cudaMemcpyAsync(p->d_small, ang, n_ang * sizeof(double), cudaMemcpyHostToDevice, s));
   const Quad q = make_quad(p->o.quad_order);
   {
-    Phase ph(p, BEM_PH_FARFIELD, s, 1);
+    Phase ph(p, BEM_PH_FARFIELD, s, 2);
     CU(launch_far_field(p->elem(), p->n, p->dom, q, n_rhs, reinterpret_cast<const double2*>(x_dev), n_ang,
-                        p->d_small, reinterpret_cast<double2*>(out_dev), s));
+                        p->d_small, reinterpret_cast<double2*>(out_dev),
+                        reinterpret_cast<double2*>(p->d_small + ang_slots), s));
   }
   CU(cudaStreamSynchronize(s));
   return BEM_OK;

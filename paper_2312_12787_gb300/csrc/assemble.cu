@@ -11,6 +11,8 @@
 // A[N+i, j], A[N+i, N+j] (pair.cuh); a warp spans 32 consecutive columns, so every store is a coalesced
 // 32-entry row segment.  The node geometry and the phase k r are FP64, the rest double-float on the FP32
 // pipe; the mixed path stores the double-float entry as complex FP32 (hi) plus its FP32 remainder (lo).
+#include <algorithm>
+
 #include "internal.cuh"
 #include "bessel.cuh"
 #include "pair.cuh"
@@ -151,36 +153,53 @@ __global__ void k_rhs_planewave(ElemDev e, int n, DomTab dom, int form, int nrhs
 
 // u_inf(theta_a) = e^{i pi/4}/sqrt(8 pi k1) sum_j s_{1,j} sum_q W_q e^{-i k1 xh.y_q} [w_j + i k1 (xh.n_j) u_j]
 // One block per (angle, rhs); threads stride over elements; FP64 block reduction.
-__global__ void __launch_bounds__(256) k_far_field(ElemDev e, int n, DomTab dom, Quad q, const double2* x, int nang,
-                                                   const double* ang, double2* out) {
-  const int a = blockIdx.x, r = blockIdx.y;
+// Far field in two steps.  The element sums depend on the angle and the element only, so they are formed
+// once for all right-hand sides:
+//   F[a][j] = s_j (h_j / 2) sum_m w_m exp(-i k1 xh_a . y_m),   G[a][j] = i k1 (xh_a . n_j) F[a][j],
+// with s_j = +1 / -1 / 0 as the host is on the element's P side / M side / neither; then
+//   u_inf(a) = e^{i pi/4} / sqrt(8 pi k1) sum_j (F[a][j] w_j + G[a][j] u_j)
+// for every solution, one CTA per (angle, solution) with a fixed-order reduction.
+__global__ void __launch_bounds__(256) k_ff_table(ElemDev e, int n, DomTab dom, Quad q, int nang,
+                                                  const double* ang, double2* F, double2* G) {
   const double k1 = dom.k[0];
-  double st, ct;
-  sincos(ang[a], &st, &ct);
-  const double2* xr = x + (size_t)r * 2 * n;
-  double2 acc = make_double2(0.0, 0.0);
-  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < (size_t)nang * n;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const int a = (int)(t / n), j = (int)(t % n);
     const int Pj = e.P[j], Mj = e.M[j];
     const double sg = (Pj == 0) ? 1.0 : ((Mj == 0) ? -1.0 : 0.0);
-    if (sg == 0.0) continue;
-    const double tx = e.tx[j], ty = e.ty[j], hh = 0.5 * e.h[j];
-    const double mx = e.mx[j], my = e.my[j];
-    double2 f = make_double2(0.0, 0.0);
-    for (int m = 0; m < q.Q; ++m) {
-      const double s = hh * q.t[m];
-      const double ph = -k1 * (ct * (mx + s * tx) + st * (my + s * ty));
-      double sp, cp;
-      sincos(ph, &sp, &cp);
-      f.x += hh * q.w[m] * cp;
-      f.y += hh * q.w[m] * sp;
+    double2 f = make_double2(0.0, 0.0), g = make_double2(0.0, 0.0);
+    if (sg != 0.0) {
+      double st, ct;
+      sincos(ang[a], &st, &ct);
+      const double tx = e.tx[j], ty = e.ty[j], hh = 0.5 * e.h[j];
+      const double mx = e.mx[j], my = e.my[j];
+      for (int m = 0; m < q.Q; ++m) {
+        const double sq = hh * q.t[m];
+        const double ph = -k1 * (ct * (mx + sq * tx) + st * (my + sq * ty));
+        double sp, cp;
+        sincos(ph, &sp, &cp);
+        f.x += hh * q.w[m] * cp;
+        f.y += hh * q.w[m] * sp;
+      }
+      f = cscale(f, sg);
+      const double xn = ct * (-ty) + st * tx;   // xh . n_j
+      g = make_double2(-k1 * xn * f.y, k1 * xn * f.x);
     }
-    const double xn = ct * (-ty) + st * tx;
-    const double2 u = xr[j], w = xr[n + j];
-    // w + i k1 xn u
-    const double2 brk = make_double2(w.x - k1 * xn * u.y, w.y + k1 * xn * u.x);
-    const double2 c = cmul(f, brk);
-    acc.x += sg * c.x; acc.y += sg * c.y;
+    F[t] = f;
+    G[t] = g;
   }
+}
+
+__global__ void __launch_bounds__(256) k_ff_apply(int n, int nang, const double2* __restrict__ F,
+                                                  const double2* __restrict__ G, const double2* __restrict__ x,
+                                                  double k1, double2* __restrict__ out) {
+  const int a = blockIdx.x, r = blockIdx.y;
+  const double2* xr = x + (size_t)r * 2 * n;
+  const double2* Fa = F + (size_t)a * n;
+  const double2* Ga = G + (size_t)a * n;
+  double2 acc = make_double2(0.0, 0.0);
+  for (int j = threadIdx.x; j < n; j += blockDim.x)
+    acc = cadd(acc, cadd(cmul(Fa[j], xr[n + j]), cmul(Ga[j], xr[j])));
   __shared__ double2 red[256];
   red[threadIdx.x] = acc;
   __syncthreads();
@@ -326,9 +345,13 @@ cudaError_t launch_rhs_planewave(const ElemDev& e, int n, const DomTab& dom, int
 }
 
 cudaError_t launch_far_field(const ElemDev& e, int n, const DomTab& dom, const Quad& q, int nrhs, const double2* x,
-                             int nang, const double* ang_dev, double2* out, cudaStream_t s) {
-  dim3 grd(nang, nrhs);
-  k_far_field<<<grd, 256, 0, s>>>(e, n, dom, q, x, nang, ang_dev, out);
+                             int nang, const double* ang_dev, double2* out, double2* scratch, cudaStream_t s) {
+  double2* F = scratch;
+  double2* G = scratch + (size_t)nang * n;
+  const size_t cnt = (size_t)nang * n;
+  const int blocks = (int)std::min<size_t>((cnt + 255) / 256, 4096);
+  k_ff_table<<<blocks, 256, 0, s>>>(e, n, dom, q, nang, ang_dev, F, G);
+  k_ff_apply<<<dim3(nang, nrhs), 256, 0, s>>>(n, nang, F, G, x, dom.k[0], out);
   return cudaGetLastError();
 }
 

@@ -250,7 +250,7 @@ __global__ void __launch_bounds__(kCh) kv_scale(VDev d) {
   const int n = d.n[s];
   const int k = d.ch_loc[c] * kCh + threadIdx.x;
   if (k >= n) return;
-  const float inv = (float)(1.0 / d.hnext[s]);
+  const float inv = 1.f / (float)d.hnext[s];   // FP32: an FP64 division per entry is costly
   const float2 w = d.W[d.u[s] + k];
   vbase(d, s)[(size_t)(d.j[s] + 1) * n + k] = make_float2(w.x * inv, w.y * inv);
 }

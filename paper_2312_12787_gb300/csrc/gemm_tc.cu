@@ -408,31 +408,59 @@ __global__ void __launch_bounds__(256) k_tc_prep_a(const float2* __restrict__ A,
   }
 }
 
-// Y[s][r] = (sum of the partials of r's row tile) / (rsc[r] tsc[s]), real part in column s, imaginary part
-// in column 64 + s; one thread per (r, s).
-__global__ void k_tc_reduce(const float* __restrict__ partial, int n, int nrhs, int kpt, long long total, int G,
-                            const float* __restrict__ rsc, const float* __restrict__ tsc, float2* __restrict__ y,
-                            const int* gate) {
+// Y[s][r] = (sum of the partials of r's row tile) / (rsc[r] tsc[s]), the real part from column s of D and
+// the imaginary part from column 64 + s.  One CTA per kRedRows rows: the partial rows are read along D's columns
+// (coalesced), summed in CTA order (deterministic), transposed in shared memory and written along r.
+// 8 rows per CTA keep enough CTAs in flight for the loads.
+constexpr int kRedRows = 8;
+__global__ void __launch_bounds__(256) k_tc_reduce(const float* __restrict__ partial, int n, int nrhs, int kpt,
+                                                   long long total, int G, const float* __restrict__ rsc,
+                                                   const float* __restrict__ tsc, float2* __restrict__ y,
+                                                   const int* gate) {
   if (gate && *gate == 0) return;
-  const int s = threadIdx.x & 63;
-  const int r = blockIdx.x * (blockDim.x >> 6) + (threadIdx.x >> 6);
-  if (r >= n || s >= nrhs) return;
-  const int t = r / kM, rl = r % kM;
-  // CTAs whose range [total c / G, total (c+1) / G) meets [t kpt, (t+1) kpt)
-  const long long lo = (long long)t * kpt, hi = lo + kpt;
-  int c0 = (int)((lo * G) / total);
-  while (c0 > 0 && total * c0 / G > lo) --c0;
-  while (total * (c0 + 1) / G <= lo) ++c0;
-  float re = 0.f, im = 0.f;
-  for (int c = c0; c < G && total * c / G < hi; ++c) {
-    const int first_tile = (int)((total * c / G) / kpt);
-    const int slot = (first_tile == t) ? 0 : 1;
-    const float* p = partial + (((size_t)c * 2 + slot) * kM + rl) * kN;
-    re += p[s];
-    im += p[64 + s];
+  constexpr int kMaxCover = 64;
+  __shared__ float2 tile[kMaxRhs][kRedRows + 1];
+  __shared__ const float* src[kMaxCover];   // partial tiles covering this row tile, in CTA order
+  __shared__ int nsrc;
+  const int r0 = blockIdx.x * kRedRows;
+  const int t = r0 / kM;
+  if (threadIdx.x == 0) {
+    // CTAs whose range [total c / G, total (c+1) / G) meets row tile t's K-steps [t kpt, (t+1) kpt)
+    const long long lo = (long long)t * kpt, hi = lo + kpt;
+    int c0 = (int)((lo * G) / total);
+    while (c0 > 0 && total * c0 / G > lo) --c0;
+    while (total * (c0 + 1) / G <= lo) ++c0;
+    int m = 0;
+    for (int c = c0; c < G && total * c / G < hi && m < kMaxCover; ++c) {
+      const int slot = ((total * c / G) / kpt == t) ? 0 : 1;
+      src[m++] = partial + ((size_t)c * 2 + slot) * kM * kN;
+    }
+    nsrc = m;
   }
-  const float inv = 1.f / (rsc[r] * (tsc ? tsc[s] : 1.f));   // a power of two: exact
-  y[(size_t)s * n + r] = make_float2(re * inv, im * inv);
+  __syncthreads();
+  const int ns = nsrc;
+#pragma unroll
+  for (int e = threadIdx.x; e < kRedRows * kN; e += 256) {
+    const int rr = e / kN, col = e % kN;
+    const int r = r0 + rr;
+    float v = 0.f;
+    if (r < n) {
+      const size_t off = (size_t)(r % kM) * kN + col;
+      for (int q = 0; q < ns; ++q) v += src[q][off];
+    }
+    if (col < 64) tile[col][rr].x = v;
+    else tile[col - 64][rr].y = v;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < kMaxRhs * kRedRows; e += 256) {
+    const int sidx = e / kRedRows, rr = e % kRedRows;
+    const int r = r0 + rr;
+    if (sidx < nrhs && r < n) {
+      const float inv = 1.f / (rsc[r] * (tsc ? tsc[sidx] : 1.f));   // a power of two: exact
+      const float2 v = tile[sidx][rr];
+      y[(size_t)sidx * n + r] = make_float2(v.x * inv, v.y * inv);
+    }
+  }
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -576,7 +604,8 @@ cudaError_t launch_matvec_tc(const void* a16, int n, int nrhs, const float2* x, 
     k_tc_prep_b<<<dim3((n + 255) / 256, kMaxRhs), 256, 0, s>>>(x, n, nrhs, cmax, bhi, blo, ld, tsc, gate);
   }
   k_gemm_tc<<<G, kThreads, kSmemBytes, s>>>(mAh, mAl, mBh, mBl, n, kpt, total, part, err, gate);
-  k_tc_reduce<<<(n + 3) / 4, 256, 0, s>>>(part, n, nrhs, kpt, total, G, rsc, x ? tsc : nullptr, y, gate);
+  k_tc_reduce<<<(n + kRedRows - 1) / kRedRows, 256, 0, s>>>(part, n, nrhs, kpt, total, G, rsc, x ? tsc : nullptr, y,
+                                                             gate);
   return cudaGetLastError();
 }
 

@@ -82,8 +82,9 @@ cudaError_t launch_assemble_batched(const AsmJob* jobs_dev, int njobs, const lon
                                    cudaStream_t s);
 cudaError_t launch_rhs_planewave(const ElemDev& e, int n, const DomTab& dom, int form, int nrhs,
                                  const double* angles_dev, double2* b, cudaStream_t s);
+// scratch: 2 * nang * n complex entries (the per-angle element sums).
 cudaError_t launch_far_field(const ElemDev& e, int n, const DomTab& dom, const Quad& q, int nrhs, const double2* x,
-                             int nang, const double* ang_dev, double2* out, cudaStream_t s);
+                             int nang, const double* ang_dev, double2* out, double2* scratch, cudaStream_t s);
 cudaError_t launch_near_field(const ElemDev& e, int n, const DomTab& dom, const Quad& q, int nrhs, const double2* x,
                               int npts, const double* pts_dev, const int* dom_dev, const double* angles_dev,
                               double2* out, cudaStream_t s);
@@ -157,8 +158,7 @@ struct KrylovState {
   int* iters;       // nrhs
   double* resid;    // nrhs: estimated relative residual
   const double* tolv;  // nrhs per-system tolerances (overrides the scalar tol when non-null)
-  int* jdev;        // current iteration index (device copy)
-  int* n_active;    // device counter of active systems
+  int* n_active;    // device count of active systems (the gate of queued iterations)
   // when non-null (FP32 basis feeding the tensor-core product): every new basis vector is also written as
   // the FP16 x 3 operand of the next product (tc_operand.cuh), rows of stride ldb16
   void* b16hi;

@@ -90,10 +90,7 @@ __global__ void k_start_finish(KrylovState st, int nblk) {
   st.iters[s] = 0;
   st.resid[s] = beta > 0.0 ? 1.0 : 0.0;
   st.hnext[s] = beta;
-  if (s == 0) {
-    *st.jdev = 0;
-    *st.n_active = st.nrhs;   // upper bound until the first k_advance
-  }
+  if (beta > 0.0) atomicAdd(st.n_active, 1);   // zeroed by the launcher
 }
 
 template <typename T>
@@ -194,15 +191,28 @@ __global__ void k_dots_reduce(KrylovState st, int nchunk, int pass, int j) {
 // running over all i (h staged in shared memory in the basis precision), so no partial sums are combined
 // across threads; also writes the chunk's ||w||^2.
 constexpr int kHsMax = 1001;
+// With fused != 0 every CTA also sums the chunk partials of the projections itself (FP64, chunk order) and
+// CTA 0 records them in column j of H (pass 0 sets, later passes add); otherwise k_dots_reduce did that.
 template <typename T, int CH>
-__global__ void __launch_bounds__(CH / 2) k_update(KrylovState st, int nchunk, int j) {
+__global__ void __launch_bounds__(CH / 2) k_update(KrylovState st, int nchunk, int pass, int j, int fused) {
   using F = typename Vec<T>::acc_t;
   __shared__ F hs[2 * kHsMax];
   __shared__ double red[CH / 64];
   const int c = blockIdx.x, s = blockIdx.y;
   if (!st.active[s]) return;
   for (int i = threadIdx.x; i <= j; i += CH / 2) {
-    const double2 h = st.hcol[(size_t)s * (st.m + 1) + i];
+    double2 h;
+    if (fused) {
+      h = make_double2(0.0, 0.0);
+      for (int cc = 0; cc < nchunk; ++cc) h = cadd(h, st.part[((size_t)s * nchunk + cc) * (st.m + 1) + i]);
+      if (c == 0) {
+        st.hcol[(size_t)s * (st.m + 1) + i] = h;
+        double2* Hj = st.H + ((size_t)s * st.m + j) * (st.m + 1);
+        Hj[i] = pass == 0 ? h : cadd(Hj[i], h);
+      }
+    } else {
+      h = st.hcol[(size_t)s * (st.m + 1) + i];
+    }
     hs[2 * i] = (F)h.x;
     hs[2 * i + 1] = (F)h.y;
   }
@@ -283,7 +293,10 @@ __global__ void __launch_bounds__(32) k_finish(KrylovState st, int nchunk, doubl
   st.iters[s] = j + 1;
   st.hnext[s] = hn;
   const double tl = st.tolv ? st.tolv[s] : tol;
-  if (res <= tl || j + 1 >= st.m || hn == 0.0) st.active[s] = 0;
+  if (res <= tl || j + 1 >= st.m || hn == 0.0) {
+    st.active[s] = 0;
+    atomicSub(st.n_active, 1);   // the gate of the queued iterations closes with the last system
+  }
 }
 
 template <typename T>
@@ -293,23 +306,13 @@ __global__ void __launch_bounds__(kThreads) k_scale_next(KrylovState st, int j) 
   if (!st.active[s] || k >= st.n) return;
   const T* W = static_cast<const T*>(st.W) + (size_t)s * st.n;
   T* Vn = static_cast<T*>(st.V) + ((size_t)(j + 1) * st.nrhs + s) * st.n;
-  const F inv = (F)(1.0 / st.hnext[s]);
+  const F inv = (F)1 / (F)st.hnext[s];   // in the basis precision (an FP64 division per entry is costly)
   T w = W[k];
   w.x *= inv;
   w.y *= inv;
   Vn[k] = w;
   if (st.b16hi)
     tc_write_b(static_cast<__half*>(st.b16hi), static_cast<__half*>(st.b16lo), st.ldb16, s, k, (float)w.x, (float)w.y);
-}
-
-__global__ void k_advance(KrylovState st) {
-  // count of systems still active; the iteration index mirror for graph replays
-  if (threadIdx.x == 0) {
-    *st.jdev += 1;
-    int a = 0;
-    for (int s = 0; s < st.nrhs; ++s) a += st.active[s];
-    *st.n_active = a;
-  }
 }
 
 // Least squares: back substitution of the triangularised Hessenberg system, one CTA per system.
@@ -321,29 +324,39 @@ __global__ void __launch_bounds__(kBsThreads) k_lsq(KrylovState st) {
                         st.y + (size_t)s * st.m, st.iters[s], sg, sinv, &sy);
 }
 
-// x += sum_i y_i v_i (FP64 x), same 64 x 4 decomposition as k_update.
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_xupdate(KrylovState st, double2* x) {
-  __shared__ double2 ys[1024];
-  __shared__ double2 accs[4][kCh];
+// x += sum_i y_i v_i: CH/2 threads per chunk, each owning one pair of entries and running over all i;
+// products and sums in the basis precision (the correction only needs the inner solve's accuracy), added
+// to the FP64 x.
+template <typename T, int CH>
+__global__ void __launch_bounds__(CH / 2) k_xupdate(KrylovState st, double2* x) {
+  using F = typename Vec<T>::acc_t;
+  __shared__ F ys[2 * kHsMax];
   const int c = blockIdx.x, s = blockIdx.y;
   const int mm = st.iters[s];
-  for (int i = threadIdx.x; i < mm; i += kThreads) ys[i] = st.y[(size_t)s * st.m + i];
-  __syncthreads();
-  const int e = threadIdx.x & (kCh - 1), sub = threadIdx.x >> 6;
-  const int k = c * kCh + e;
-  const size_t stride = (size_t)st.nrhs * st.n;
-  const T* V = static_cast<const T*>(st.V) + (size_t)s * st.n;
-  double2 acc = make_double2(0, 0);
-  if (k < st.n)
-    for (int i = sub; i < mm; i += 4) acc = cadd(acc, cmul(ys[i], Vec<T>::load(V + (size_t)i * stride + k)));
-  accs[sub][e] = acc;
-  __syncthreads();
-  if (sub == 0 && k < st.n) {
-    double2 t = x[(size_t)s * st.n + k];
-    for (int q = 0; q < 4; ++q) t = cadd(t, accs[q][e]);
-    x[(size_t)s * st.n + k] = t;
+  for (int i = threadIdx.x; i < mm; i += CH / 2) {
+    const double2 y = st.y[(size_t)s * st.m + i];
+    ys[2 * i] = (F)y.x;
+    ys[2 * i + 1] = (F)y.y;
   }
+  __syncthreads();
+  const int k = c * CH + 2 * threadIdx.x;
+  if (k >= st.n || mm == 0) return;
+  const size_t stride = (size_t)st.nrhs * st.n;
+  const T* V = static_cast<const T*>(st.V) + (size_t)s * st.n + k;
+  F ax = 0, ay = 0, bx = 0, by = 0;
+#pragma unroll 8
+  for (int i = 0; i < mm; ++i) {
+    T a, b;
+    Pair<T>::load(V + (size_t)i * stride, a, b);
+    const F yx = ys[2 * i], yy = ys[2 * i + 1];
+    ax += yx * (F)a.x - yy * (F)a.y;
+    ay += yx * (F)a.y + yy * (F)a.x;
+    bx += yx * (F)b.x - yy * (F)b.y;
+    by += yx * (F)b.y + yy * (F)b.x;
+  }
+  double2* xs = x + (size_t)s * st.n + k;
+  xs[0] = make_double2(xs[0].x + (double)ax, xs[0].y + (double)ay);
+  xs[1] = make_double2(xs[1].x + (double)bx, xs[1].y + (double)by);
 }
 
 int nchunk_of(int n) { return (n + kCh - 1) / kCh; }
@@ -373,9 +386,10 @@ template <typename T, int CH>
 void orth_pass(const KrylovState& st, int pass, int j, cudaStream_t s) {
   const int nc = (st.n + CH - 1) / CH;
   dim3 grd(nc, st.nrhs);
+  const int fused = nc <= 32;   // few chunks: each update CTA sums the partials itself (one launch less)
   k_dots<T, CH><<<grd, kThreads, 0, s>>>(st, nc, j);
-  k_dots_reduce<<<dim3((j + 8) / 8, st.nrhs), 256, 0, s>>>(st, nc, pass, j);
-  k_update<T, CH><<<grd, CH / 2, 0, s>>>(st, nc, j);
+  if (!fused) k_dots_reduce<<<dim3((j + 8) / 8, st.nrhs), 256, 0, s>>>(st, nc, pass, j);
+  k_update<T, CH><<<grd, CH / 2, 0, s>>>(st, nc, pass, j, fused);
 }
 
 template <typename T>
@@ -383,6 +397,8 @@ cudaError_t start_t(const KrylovState& st, const double2* r0, cudaStream_t s) {
   const int nb = nblk_of(st.n);
   dim3 grd(nb, st.nrhs);
   k_norm_part<double2><<<grd, kThreads, 0, s>>>(r0, st.n, st.npart, nb);
+  cudaError_t e = cudaMemsetAsync(st.n_active, 0, sizeof(int), s);
+  if (e != cudaSuccess) return e;
   k_start_finish<<<(st.nrhs + 63) / 64, 64, 0, s>>>(st, nb);
   k_start_scale<T><<<grd, kThreads, 0, s>>>(st, r0);
   return cudaGetLastError();
@@ -408,14 +424,20 @@ cudaError_t finish_t(const KrylovState& st, double tol, int j, cudaStream_t s) {
   const int nc = (st.n + ch - 1) / ch;   // the update kernel's chunks (its squared norms)
   k_finish<<<st.nrhs, 32, 0, s>>>(st, nc, tol, j);
   k_scale_next<T><<<dim3(nblk_of(st.n), st.nrhs), kThreads, 0, s>>>(st, j);
-  k_advance<<<1, 32, 0, s>>>(st);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t xupd_t(const KrylovState& st, double2* x, cudaStream_t s) {
   k_lsq<<<st.nrhs, kBsThreads, 0, s>>>(st);
-  k_xupdate<T><<<dim3(nchunk_of(st.n), st.nrhs), kThreads, 0, s>>>(st, x);
+  const int ch = chunk_of(st.n, st.nrhs);
+  const dim3 grd((st.n + ch - 1) / ch, st.nrhs);
+  switch (ch) {
+    case 512: k_xupdate<T, 512><<<grd, 256, 0, s>>>(st, x); break;
+    case 256: k_xupdate<T, 256><<<grd, 128, 0, s>>>(st, x); break;
+    case 128: k_xupdate<T, 128><<<grd, 64, 0, s>>>(st, x); break;
+    default: k_xupdate<T, 64><<<grd, 32, 0, s>>>(st, x); break;
+  }
   return cudaGetLastError();
 }
 
