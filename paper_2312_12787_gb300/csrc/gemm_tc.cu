@@ -400,11 +400,10 @@ __global__ void __launch_bounds__(256) k_tc_prep_a(const float2* __restrict__ A,
   __half* lr = alo + (size_t)r * lda16;
   for (int c = threadIdx.x; c < n; c += 256) {
     const float2 v = row[c];
-    __half h0, l0, h1, l1;
-    tc_split16(v.x * sc, h0, l0);
-    tc_split16(v.y * sc, h1, l1);
-    hr[2 * c] = h0; hr[2 * c + 1] = h1;
-    lr[2 * c] = l0; lr[2 * c + 1] = l1;
+    __half2 h, l;
+    tc_split16x2(v.x * sc, v.y * sc, h, l);
+    *reinterpret_cast<__half2*>(hr + 2 * c) = h;
+    *reinterpret_cast<__half2*>(lr + 2 * c) = l;
   }
 }
 

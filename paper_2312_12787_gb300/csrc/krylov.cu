@@ -124,8 +124,8 @@ template <> struct Pair<double2> {
 
 // Partial projections <v_i, w> over one chunk of CH entries: warp w takes basis vectors i = w, w+8, ...;
 // lane l holds the pairs k = chunk start + 2 (32 p + l), p < CH/64, so each load instruction of the warp
-// moves 512 (FP32) or 1024 (FP64) contiguous bytes.  Products in the basis precision, the lane sums and the
-// warp reduction in FP64; chunk partials are stored for an FP64 sum over chunks.
+// moves 512 (FP32) or 1024 (FP64) contiguous bytes.  Products, lane sums and the warp reduction in the basis
+// precision; chunk partials are stored for an FP64 sum over chunks.
 template <typename T, int CH>
 __global__ void __launch_bounds__(kThreads) k_dots(KrylovState st, int nchunk, int j) {
   using F = typename Vec<T>::acc_t;
@@ -159,8 +159,9 @@ __global__ void __launch_bounds__(kThreads) k_dots(KrylovState st, int nchunk, i
         py += (F)a.x * (F)w[2 * p].y - (F)a.y * (F)w[2 * p].x + (F)b.x * (F)w[2 * p + 1].y - (F)b.y * (F)w[2 * p + 1].x;
       }
     }
-    const double hx = warp_sum((double)px), hy = warp_sum((double)py);
-    if (lane == 0) st.part[((size_t)s * nchunk + c) * (st.m + 1) + i] = make_double2(hx, hy);
+    // the warp reduction in the basis precision too: FP64 adds run at 1/64 of the FP32 rate on GB300
+    const F hx = warp_sum(px), hy = warp_sum(py);
+    if (lane == 0) st.part[((size_t)s * nchunk + c) * (st.m + 1) + i] = make_double2((double)hx, (double)hy);
   }
 }
 
@@ -219,7 +220,7 @@ __global__ void __launch_bounds__(CH / 2) k_update(KrylovState st, int nchunk, i
   __syncthreads();
   const int k = c * CH + 2 * threadIdx.x;
   const size_t stride = (size_t)st.nrhs * st.n;
-  double nrm = 0.0;
+  F nrm_f = 0;
   if (k < st.n) {
     const T* V = static_cast<const T*>(st.V) + (size_t)s * st.n + k;
     F ax = 0, ay = 0, bx = 0, by = 0;
@@ -239,11 +240,10 @@ __global__ void __launch_bounds__(CH / 2) k_update(KrylovState st, int nchunk, i
     w0.x -= ax; w0.y -= ay;
     w1.x -= bx; w1.y -= by;
     Pair<T>::store(W, w0, w1);
-    nrm = (double)w0.x * (double)w0.x + (double)w0.y * (double)w0.y + (double)w1.x * (double)w1.x +
-          (double)w1.y * (double)w1.y;
+    nrm_f = w0.x * w0.x + w0.y * w0.y + w1.x * w1.x + w1.y * w1.y;
   }
-  nrm = warp_sum(nrm);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = nrm;
+  nrm_f = warp_sum(nrm_f);   // basis precision within the warp, FP64 across warps and chunks
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = (double)nrm_f;
   __syncthreads();
   if (threadIdx.x == 0) {
     double t = 0.0;
