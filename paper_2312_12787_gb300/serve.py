@@ -7,9 +7,16 @@ pools (Krylov bases, solutions, residuals, right-hand sides) and room in the HBM
 then iterate together with the ones already on the device; finished solves are taken out at once, which frees
 their slot, pool space and matrix.  Latency is measured from arrival to the moment the solution is back in a
 device buffer.  All compute runs in libbem; this module only schedules.
+
+Requests whose complex-FP32 matrix would exceed `matrix_free_bytes` (8e9 by default: N_e above ~15.8k) store no
+matrix at all: a worker thread solves them one at a time with the matrix-free FP64 path (every product
+recomputes the entries) on a CUDA stream of its own, while the batch engine keeps iterating the others.  Their
+HBM footprint (the FP64 Krylov basis) is charged to the budget while they run.
 """
 from __future__ import annotations
 
+import queue
+import threading
 import time
 from dataclasses import dataclass, field
 
@@ -27,6 +34,8 @@ class ServeStats:
     max_resident: int = 0
     admissions: int = 0
     deferred: int = 0          # admission attempts that had to wait for space
+    matrix_free: int = 0       # requests solved by the matrix-free path
+    overlapped: int = 0        # matrix-free solves that finished while batch slots were resident
 
     def summary(self):
         lat = np.array(self.latencies_s) if self.latencies_s else np.zeros(1)
@@ -34,7 +43,8 @@ class ServeStats:
                 "solves_per_s": self.n_done / self.wall_s if self.wall_s > 0 else 0.0,
                 "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
                 "mean_iters": float(np.mean(self.iters)) if self.iters else 0.0,
-                "max_resident": self.max_resident, "deferred_admissions": self.deferred}
+                "max_resident": self.max_resident, "deferred_admissions": self.deferred,
+                "matrix_free": self.matrix_free, "matrix_free_overlapped": self.overlapped}
 
 
 def matrix_bytes(wp) -> int:
@@ -42,23 +52,64 @@ def matrix_bytes(wp) -> int:
     return 16 * n2 * n2
 
 
+def c32_matrix_bytes(wp) -> int:
+    n2 = wp.n_unknowns
+    return 8 * n2 * n2
+
+
+def mf_footprint_bytes(wp, max_iter) -> int:
+    """Device bytes of a matrix-free FP64 solve: the Krylov basis and the Hessenberg data dominate."""
+    n2 = wp.n_unknowns
+    return 16 * (max_iter + 1) * n2 + 16 * max_iter * (max_iter + 1) + 64 * n2
+
+
 class Server:
     """Continuous-batching solver: slots of a bem_batch engine plus an HBM budget for matrices."""
 
     def __init__(self, max_slots=128, pool_unknowns=1 << 21, hbm_budget_bytes=64 << 30, tol=1e-8, max_iter=300,
-                 prec="mixed", quad_order=4):
+                 prec="mixed", quad_order=4, matrix_free_bytes=8e9, mf_max_iter=600):
         self.opts = dict(prec=prec, tol=tol, max_iter=max_iter, quad_order=quad_order)
         self.batch = _bem.Batch(max_slots, pool_unknowns, **self.opts)
         self.batch_max_slots = max_slots
         self.budget = hbm_budget_bytes
         self.resident = {}          # slot -> (request id, problem, matrix bytes)
         self.used_bytes = 0
+        self.mf_limit = matrix_free_bytes
+        self.mf_opts = dict(prec="fp64", matrix_free=1, tol=tol, max_iter=mf_max_iter, quad_order=quad_order)
+        self._mf_in = queue.Queue()
+        self._mf_out = queue.Queue()
+        self._mf_thread = None
 
     def close(self):
         for (_, p, _) in self.resident.values():
             p.close()
         self.resident.clear()
+        if self._mf_thread is not None:
+            self._mf_in.put(None)
+            self._mf_thread.join()
+            self._mf_thread = None
         self.batch.close()
+
+    def _mf_worker(self, device):
+        """Matrix-free solves, one at a time, on a stream of their own (ctypes releases the GIL in the calls)."""
+        import torch
+        torch.cuda.set_device(device)
+        stream = torch.cuda.Stream()
+        while True:
+            item = self._mf_in.get()
+            if item is None:
+                return
+            rid, wp, ang = item
+            try:
+                p = _bem.Problem.from_workload(wp, **self.mf_opts)
+                with torch.cuda.stream(stream):
+                    x = torch.empty((1, p.bem_num_unknowns()), dtype=torch.complex128, device="cuda")
+                st, it, rs = p.bem_solve_planewave([ang], x, stream=stream)
+                stream.synchronize()
+                p.close()
+                self._mf_out.put((rid, x[0], int(it[0]), time.perf_counter(), None))
+            except Exception as e:   # reported to the loop, which re-raises
+                self._mf_out.put((rid, None, 0, time.perf_counter(), e))
 
     def run(self, requests, out=None, stream=None, time_limit_s=600.0):
         """requests: list of (arrival_s, workloads.Problem, angle).  Arrival times are relative to the start
@@ -67,29 +118,62 @@ class Server:
         import torch
         st = ServeStats()
         order = sorted(range(len(requests)), key=lambda i: requests[i][0])
-        queue = []                  # arrived, not admitted
+        waiting = []                # arrived, not admitted
         nxt = 0
         t0 = time.perf_counter()
         pending = len(requests)
+        mf_running = {}             # request id -> footprint bytes (queued at or running in the worker)
         while pending:
             now = time.perf_counter() - t0
             if now > time_limit_s:
                 raise TimeoutError("serving run exceeded its time limit")
             while nxt < len(order) and requests[order[nxt]][0] <= now:
-                queue.append(order[nxt])
+                waiting.append(order[nxt])
                 nxt += 1
+            # finished matrix-free solves
+            while True:
+                try:
+                    rid, x, it, t_done, err = self._mf_out.get_nowait()
+                except queue.Empty:
+                    break
+                if err is not None:
+                    raise err
+                self.used_bytes -= mf_running.pop(rid)
+                st.latencies_s.append(t_done - t0 - requests[rid][0])
+                st.iters.append(it)
+                st.n_done += 1
+                st.matrix_free += 1
+                if self.resident:
+                    st.overlapped += 1
+                pending -= 1
+                if out is not None:
+                    out[rid] = x
             # admit in arrival order while the head of the queue fits
             batch_ids, batch_probs, batch_angles = [], [], []
-            while queue:
-                rid = queue[0]
+            while waiting:
+                rid = waiting[0]
                 wp = requests[rid][1]
+                if c32_matrix_bytes(wp) > self.mf_limit:
+                    need = mf_footprint_bytes(wp, self.mf_opts["max_iter"])
+                    if self.used_bytes + need > self.budget:
+                        st.deferred += 1
+                        break
+                    waiting.pop(0)
+                    if self._mf_thread is None:
+                        self._mf_thread = threading.Thread(target=self._mf_worker, args=(torch.cuda.current_device(),),
+                                                           daemon=True)
+                        self._mf_thread.start()
+                    mf_running[rid] = need
+                    self.used_bytes += need
+                    self._mf_in.put((rid, wp, requests[rid][2]))
+                    continue
                 need = matrix_bytes(wp)
                 units = sum(p.bem_num_unknowns() for p in batch_probs) + wp.n_unknowns
                 if (self.used_bytes + need > self.budget or self.batch.bem_batch_free_units() < units or
                         len(self.resident) + len(batch_probs) >= self.batch_max_slots):
                     st.deferred += 1
                     break
-                queue.pop(0)
+                waiting.pop(0)
                 p = _bem.Problem.from_workload(wp, **self.opts)
                 batch_ids.append(rid)
                 batch_probs.append(p)
@@ -101,15 +185,17 @@ class Server:
                     if s < 0:           # did not fit after all (fragmented pool): back to the queue head
                         self.used_bytes -= matrix_bytes(requests[rid][1])
                         p.close()
-                        queue.insert(0, rid)
+                        waiting.insert(0, rid)
                     else:
                         self.resident[int(s)] = (rid, p, matrix_bytes(requests[rid][1]))
                         st.admissions += 1
                 st.max_resident = max(st.max_resident, len(self.resident))
             if not self.resident:
-                # idle until the next arrival
+                # idle until the next arrival or the next matrix-free result
                 if nxt < len(order):
                     time.sleep(max(0.0, min(0.002, requests[order[nxt]][0] - (time.perf_counter() - t0))))
+                elif mf_running:
+                    time.sleep(0.002)
                 continue
             self.batch.bem_batch_step(stream)
             for s in list(self.resident):
