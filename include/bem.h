@@ -83,7 +83,9 @@ typedef struct {
   double tol;         /* target relative residual ||b - A x||_2 / ||b||_2 (paper: 1e-8), > 0 */
   double inner_tol;   /* relative tolerance of each inner GMRES run (MIXED / MIXED_TC), > 0 */
   int orth_passes;    /* classical Gram-Schmidt passes per Arnoldi step: 1, 2 (re-orthogonalised), or 0 =
-                         automatic (2 for the FP64 basis, 1 for the FP32 inner solves of the mixed paths) */
+                         automatic: 2 for the FP64 basis; for the FP32 inner solves of the mixed paths one
+                         pass, plus a second one in the iterations where the first shrank the new vector below
+                         a tenth of its length (selective reorthogonalisation) */
   int matrix_free;    /* 1: never store A; every product recomputes the entries in FP64 (FP64 path only).
                          For matrices that do not fit in device memory; each product costs one assembly. */
 } bem_opts;

@@ -304,6 +304,8 @@ size_t krylov_bytes(int n2, int nrhs, int m, bool fp32) {
   add((size_t)nrhs * 8);                  // hnext
   add((size_t)nrhs * nc * (m + 1) * 16);  // part
   add((size_t)nrhs * nc * 8);             // npart
+  add((size_t)nrhs * nc * 8);             // wpart
+  add((size_t)nrhs * 4);                  // reo
   add((size_t)nrhs * (m + 1) * 16);       // hcol
   add((size_t)nrhs * 4);                  // active
   add((size_t)nrhs * 4);                  // iters
@@ -357,6 +359,8 @@ Solver carve_solver(bem_problem* p, int nrhs, bool fp32) {
   st.hnext = c.take<double>(nrhs);
   st.part = c.take<double2>((size_t)nrhs * nc * (m + 1));
   st.npart = c.take<double>((size_t)nrhs * nc);
+  st.wpart = c.take<double>((size_t)nrhs * nc);
+  st.reo = c.take<int>(nrhs);
   st.hcol = c.take<double2>((size_t)nrhs * (m + 1));
   st.active = c.take<int>(nrhs);
   st.iters = c.take<int>(nrhs);
@@ -426,9 +430,10 @@ bem_status gmres_run(bem_problem* p, Solver& sv, const double2* r0, double2* x, 
     }
     }
     {
-      // automatic: re-orthogonalise the FP64 basis; the FP32 inner solves (loose tolerance) use one pass
-      const int passes = p->o.orth_passes ? p->o.orth_passes : (fp32 ? 1 : 2);
-      Phase ph(p, BEM_PH_ARNOLDI, s, 3 * passes);
+      // automatic: two passes for the FP64 basis; for the FP32 basis one pass, and a second one only for the
+      // systems whose vector the first pass shrank below a tenth of its length (selective reorthogonalisation)
+      const int passes = p->o.orth_passes ? p->o.orth_passes : (fp32 ? 0 : 2);
+      Phase ph(p, BEM_PH_ARNOLDI, s, 3 * (passes == 1 ? 1 : 2));
       CU(krylov_orthogonalise(st, passes, j, s));
     }
     {

@@ -63,6 +63,8 @@ struct VDev {
   int nrb;
   double2* part;
   double* npart;
+  double* wpart;    // per chunk: ||w||^2 before projection (selective reorthogonalisation)
+  int* reo;         // per slot: 1 if the conditional second Gram-Schmidt pass runs this iteration
   int* n_active;
 };
 
@@ -109,10 +111,29 @@ __global__ void __launch_bounds__(256) kv_gemv(VDev d) {
 }
 
 // partial projections <v_i, w> of one chunk; warp w takes i = w, w+8, ...
-__global__ void __launch_bounds__(256) kv_dots(VDev d) {
+// mode 0: first pass (warp 0 also records the chunk's ||w||^2 before projection); mode 1: conditional second
+// pass, run only for slots whose first pass shrank w below a tenth of its length (the decision, taken
+// alike by every CTA of the slot from the chunk sums, goes to d.reo for the reduction and update kernels);
+// mode 2: unconditional second pass.
+__global__ void __launch_bounds__(256) kv_dots(VDev d, int mode) {
   const int c = blockIdx.x;
   const int s = d.ch_slot[c];
   if (!d.active[s]) return;
+  if (mode == 1) {
+    __shared__ int need;
+    if (threadIdx.x == 0) {
+      double before = 0.0, after = 0.0;
+      const int c0 = d.cbeg[s], cn = d.ccnt[s];
+      for (int cc = 0; cc < cn; ++cc) {
+        before += d.wpart[c0 + cc];
+        after += d.npart[c0 + cc];
+      }
+      need = after < 0.01 * before;   // ||w_after|| < ||w_before|| / 10
+      if (c == c0) d.reo[s] = need;
+    }
+    __syncthreads();
+    if (!need) return;
+  }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n = d.n[s], j = d.j[s];
   const float2* W = d.W + d.u[s];
@@ -121,6 +142,10 @@ __global__ void __launch_bounds__(256) kv_dots(VDev d) {
   const bool in0 = k0 < n, in1 = k1 < n;
   const float2 z = make_float2(0.f, 0.f);
   const float2 w0 = in0 ? W[k0] : z, w1 = in1 ? W[k1] : z;
+  if (mode == 0 && warp == 0) {
+    const float nw = wsum(w0.x * w0.x + w0.y * w0.y + w1.x * w1.x + w1.y * w1.y);
+    if (lane == 0) d.wpart[c] = (double)nw;
+  }
   for (int i = warp; i <= j; i += 8) {
     const float2* vi = V + (size_t)i * n;
     const float2 v0 = in0 ? vi[k0] : z, v1 = in1 ? vi[k1] : z;
@@ -132,9 +157,9 @@ __global__ void __launch_bounds__(256) kv_dots(VDev d) {
   }
 }
 
-__global__ void kv_dots_reduce(VDev d, int pass) {
+__global__ void kv_dots_reduce(VDev d, int pass, int cond) {
   const int s = blockIdx.y;
-  if (s >= d.cap || !d.active[s]) return;
+  if (s >= d.cap || !d.active[s] || (cond && !d.reo[s])) return;
   const int i = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   const int j = d.j[s];
   if (i > j) return;
@@ -155,13 +180,13 @@ __global__ void kv_dots_reduce(VDev d, int pass) {
   }
 }
 
-__global__ void __launch_bounds__(256) kv_update(VDev d) {
+__global__ void __launch_bounds__(256) kv_update(VDev d, int cond) {
   __shared__ float2 hs[kMaxM + 1];
   __shared__ float accs[4][kCh][2];
   __shared__ double red[8];
   const int c = blockIdx.x;
   const int s = d.ch_slot[c];
-  if (!d.active[s]) return;
+  if (!d.active[s] || (cond && !d.reo[s])) return;   // cond: a conditional pass the slot did not need
   const int n = d.n[s], j = d.j[s];
   for (int i = threadIdx.x; i <= j; i += 256) {
     const double2 h = d.hcol[(size_t)s * (d.m + 1) + i];
@@ -422,6 +447,8 @@ struct BatchEngine {
   int *cbeg = nullptr, *ccnt = nullptr, *ch_slot = nullptr, *ch_loc = nullptr, *rb_slot = nullptr, *rb_row = nullptr;
   double2* part = nullptr;
   double* npart = nullptr;
+  double* wpart = nullptr;
+  int* reo = nullptr;
   double* angles = nullptr;
   int max_chunks = 0, max_rb = 0;
   int nchunks = 0, nrb = 0;
@@ -486,7 +513,7 @@ VDev view(const BatchEngine& e) {
   d.active = e.active; d.iters = e.iters; d.j = e.jj; d.flag = e.flag;
   d.cbeg = e.cbeg; d.ccnt = e.ccnt; d.ch_slot = e.ch_slot; d.ch_loc = e.ch_loc; d.nchunks = e.nchunks;
   d.rb_slot = e.rb_slot; d.rb_row = e.rb_row; d.nrb = e.nrb;
-  d.part = e.part; d.npart = e.npart; d.n_active = e.n_active;
+  d.part = e.part; d.npart = e.npart; d.wpart = e.wpart; d.reo = e.reo; d.n_active = e.n_active;
   return d;
 }
 
@@ -552,13 +579,16 @@ bem_status rebuild_tables(bem_batch* b) {
   return BEM_OK;
 }
 
+// passes: 1, 2, or 0 = one pass plus the conditional second one (selective reorthogonalisation)
 void enqueue_iteration(const BatchEngine& e, const VDev& d, int passes) {
   if (e.nchunks == 0) return;
   kv_gemv<<<e.nrb, 256, 0, e.st>>>(d);
-  for (int p = 0; p < passes; ++p) {
-    kv_dots<<<e.nchunks, 256, 0, e.st>>>(d);
-    kv_dots_reduce<<<dim3((e.m + 8) / 8, e.cap), 256, 0, e.st>>>(d, p);
-    kv_update<<<e.nchunks, 256, 0, e.st>>>(d);
+  const int np = passes == 1 ? 1 : 2;
+  for (int p = 0; p < np; ++p) {
+    const int mode = p == 0 ? 0 : (passes == 0 ? 1 : 2);
+    kv_dots<<<e.nchunks, 256, 0, e.st>>>(d, mode);
+    kv_dots_reduce<<<dim3((e.m + 8) / 8, e.cap), 256, 0, e.st>>>(d, p, mode == 1);
+    kv_update<<<e.nchunks, 256, 0, e.st>>>(d, mode == 1);
   }
   kv_finish<<<e.cap, 32, 0, e.st>>>(d);
   kv_scale<<<e.nchunks, kCh, 0, e.st>>>(d);
@@ -576,7 +606,7 @@ bem_status run_iterations(bem_batch* b) {
   if (!e.gexec) {
     cudaGraph_t graph;
     BCU(cudaStreamBeginCapture(e.st, cudaStreamCaptureModeThreadLocal));
-    for (int it = 0; it < e.graph_iters; ++it) enqueue_iteration(e, d, e.o.orth_passes ? e.o.orth_passes : 1);
+    for (int it = 0; it < e.graph_iters; ++it) enqueue_iteration(e, d, e.o.orth_passes);
     BCU(cudaStreamEndCapture(e.st, &graph));
     cudaError_t ce = cudaGraphInstantiate(&e.gexec, graph, 0);
     cudaGraphDestroy(graph);
@@ -691,7 +721,8 @@ BEM_API bem_status bem_batch_create(bem_batch** out, const bem_opts* opts, int m
        dalloc(&e.flag, cap) && dalloc(&e.n_active, 1) && dalloc(&e.cbeg, cap) && dalloc(&e.ccnt, cap) &&
        dalloc(&e.ch_slot, e.max_chunks) && dalloc(&e.ch_loc, e.max_chunks) && dalloc(&e.rb_slot, e.max_rb) &&
        dalloc(&e.rb_row, e.max_rb) && dalloc(&e.part, (size_t)e.max_chunks * (m + 1)) &&
-       dalloc(&e.npart, e.max_chunks) && dalloc(&e.angles, cap);
+       dalloc(&e.npart, e.max_chunks) && dalloc(&e.wpart, e.max_chunks) && dalloc(&e.reo, cap) &&
+       dalloc(&e.angles, cap);
   ok = ok && cudaMallocHost(&e.h_active, cap * sizeof(int)) == cudaSuccess &&
        cudaMallocHost(&e.h_iters, cap * sizeof(int)) == cudaSuccess &&
        cudaMallocHost(&e.h_rnorm, cap * sizeof(double)) == cudaSuccess &&
@@ -719,7 +750,7 @@ BEM_API void bem_batch_destroy(bem_batch* b) {
   if (e.gexec) cudaGraphExecDestroy(e.gexec);
   void* ptrs[] = {e.dA, e.dAlo, e.dn, e.du, e.V, e.W, e.X, e.R, e.Bv, e.H, e.cs, e.sn, e.g, e.y, e.hcol, e.beta,
                   e.hnext, e.resid, e.tol, e.rnorm, e.active, e.iters, e.jj, e.flag, e.n_active, e.cbeg, e.ccnt,
-                  e.ch_slot, e.ch_loc, e.rb_slot, e.rb_row, e.part, e.npart, e.angles};
+                  e.ch_slot, e.ch_loc, e.rb_slot, e.rb_row, e.part, e.npart, e.wpart, e.reo, e.angles};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (e.h_active) cudaFreeHost(e.h_active);

@@ -153,6 +153,8 @@ struct KrylovState {
   double* hnext;    // nrhs: ||w|| after orthogonalisation
   double2* part;    // scratch: nrhs x krylov_nchunk(n) x (m+1) partial dot products
   double* npart;    // scratch: nrhs x krylov_nchunk(n) partial squared norms
+  double* wpart;    // scratch: nrhs x krylov_nchunk(n) partial squared norms of w before projection
+  int* reo;         // nrhs: 1 if the conditional second Gram-Schmidt pass runs this iteration
   double2* hcol;    // nrhs x (m+1): projections of the current pass
   int* active;      // nrhs: 1 while iterating
   int* iters;       // nrhs
@@ -167,6 +169,8 @@ struct KrylovState {
 };
 int krylov_nchunk(int n);
 cudaError_t krylov_start(const KrylovState& st, const double2* r0, double tol_unused, cudaStream_t s);
+// passes: 1, 2, or 0 = one pass plus a second one for the systems whose w the first pass shrank below a tenth
+// of its length (selective reorthogonalisation).
 cudaError_t krylov_orthogonalise(const KrylovState& st, int passes, int j, cudaStream_t s);
 cudaError_t krylov_finish_step(const KrylovState& st, double tol, int j, cudaStream_t s);
 cudaError_t krylov_update_solution(const KrylovState& st, double2* x, cudaStream_t s);

@@ -126,12 +126,36 @@ template <> struct Pair<double2> {
 // lane l holds the pairs k = chunk start + 2 (32 p + l), p < CH/64, so each load instruction of the warp
 // moves 512 (FP32) or 1024 (FP64) contiguous bytes.  Products, lane sums and the warp reduction in the basis
 // precision; chunk partials are stored for an FP64 sum over chunks.
+//
+// mode 0: first pass; warp 0 also records the chunk's ||w||^2 (before projection) in st.wpart.
+// mode 1: conditional second pass (selective reorthogonalisation, after the norm-drop test of Daniel, Gragg,
+//         Kaufman and Stewart).  A system is projected again only if the first pass shrank w below a tenth
+//         of its length, ||w_after||^2 < ||w_before||^2 / 100: the cancellation then costs one classical
+//         Gram-Schmidt pass in FP32 about a factor 10 of orthogonality, which the inner solves' 1e-5 tolerance
+//         no longer absorbs (the textbook 1/sqrt(2) threshold re-projects most steps of smooth problems, for
+//         the same iteration counts).  Every CTA takes the same decision from the chunk sums; CTA 0 records it
+//         in st.reo for the update kernel.
+// mode 2: unconditional second pass.
 template <typename T, int CH>
-__global__ void __launch_bounds__(kThreads) k_dots(KrylovState st, int nchunk, int j) {
+__global__ void __launch_bounds__(kThreads) k_dots(KrylovState st, int nchunk, int j, int mode) {
   using F = typename Vec<T>::acc_t;
   constexpr int P = CH / 64;
   const int c = blockIdx.x, s = blockIdx.y;
   if (!st.active[s]) return;
+  if (mode == 1) {
+    __shared__ int need;
+    if (threadIdx.x == 0) {
+      double before = 0.0, after = 0.0;
+      for (int cc = 0; cc < nchunk; ++cc) {
+        before += st.wpart[(size_t)s * nchunk + cc];
+        after += st.npart[(size_t)s * nchunk + cc];
+      }
+      need = after < 0.01 * before;   // ||w_after|| < ||w_before|| / 10
+      if (c == 0) st.reo[s] = need;
+    }
+    __syncthreads();
+    if (!need) return;
+  }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const size_t stride = (size_t)st.nrhs * st.n;
   const T* W = static_cast<const T*>(st.W) + (size_t)s * st.n;
@@ -145,6 +169,13 @@ __global__ void __launch_bounds__(kThreads) k_dots(KrylovState st, int nchunk, i
     } else {
       w[2 * p].x = w[2 * p].y = w[2 * p + 1].x = w[2 * p + 1].y = 0;
     }
+  }
+  if (mode == 0 && warp == 0) {
+    F nw = 0;
+#pragma unroll
+    for (int p = 0; p < 2 * P; ++p) nw += (F)w[p].x * (F)w[p].x + (F)w[p].y * (F)w[p].y;
+    nw = warp_sum(nw);
+    if (lane == 0) st.wpart[(size_t)s * nchunk + c] = (double)nw;
   }
   for (int i = warp; i <= j; i += kThreads / 32) {
     const T* vi = V + (size_t)i * stride;
@@ -167,9 +198,9 @@ __global__ void __launch_bounds__(kThreads) k_dots(KrylovState st, int nchunk, i
 
 // h_i = sum over chunks (FP64), one warp per (system, i); accumulate into column j of H (pass 0 sets,
 // later passes add).  grid = (ceil((j+1)/8), systems), 8 warps per block.
-__global__ void k_dots_reduce(KrylovState st, int nchunk, int pass, int j) {
+__global__ void k_dots_reduce(KrylovState st, int nchunk, int pass, int j, int cond) {
   const int s = blockIdx.y;
-  if (!st.active[s]) return;
+  if (!st.active[s] || (cond && !st.reo[s])) return;
   const int i = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (i > j) return;
   double hx = 0.0, hy = 0.0;
@@ -195,12 +226,13 @@ constexpr int kHsMax = 1001;
 // With fused != 0 every CTA also sums the chunk partials of the projections itself (FP64, chunk order) and
 // CTA 0 records them in column j of H (pass 0 sets, later passes add); otherwise k_dots_reduce did that.
 template <typename T, int CH>
-__global__ void __launch_bounds__(CH / 2) k_update(KrylovState st, int nchunk, int pass, int j, int fused) {
+__global__ void __launch_bounds__(CH / 2) k_update(KrylovState st, int nchunk, int pass, int j, int fused,
+                                                   int cond) {
   using F = typename Vec<T>::acc_t;
   __shared__ F hs[2 * kHsMax];
   __shared__ double red[CH / 64];
   const int c = blockIdx.x, s = blockIdx.y;
-  if (!st.active[s]) return;
+  if (!st.active[s] || (cond && !st.reo[s])) return;   // cond: a conditional pass the system did not need
   for (int i = threadIdx.x; i <= j; i += CH / 2) {
     double2 h;
     if (fused) {
@@ -382,14 +414,16 @@ int chunk_of(int n, int nrhs) {
   return kCh;
 }
 
+// mode as for k_dots (0: first pass, 1: conditional second pass, 2: second pass)
 template <typename T, int CH>
-void orth_pass(const KrylovState& st, int pass, int j, cudaStream_t s) {
+void orth_pass(const KrylovState& st, int pass, int mode, int j, cudaStream_t s) {
   const int nc = (st.n + CH - 1) / CH;
   dim3 grd(nc, st.nrhs);
   const int fused = nc <= 32;   // few chunks: each update CTA sums the partials itself (one launch less)
-  k_dots<T, CH><<<grd, kThreads, 0, s>>>(st, nc, j);
-  if (!fused) k_dots_reduce<<<dim3((j + 8) / 8, st.nrhs), 256, 0, s>>>(st, nc, pass, j);
-  k_update<T, CH><<<grd, CH / 2, 0, s>>>(st, nc, pass, j, fused);
+  const int cond = mode == 1;
+  k_dots<T, CH><<<grd, kThreads, 0, s>>>(st, nc, j, mode);
+  if (!fused) k_dots_reduce<<<dim3((j + 8) / 8, st.nrhs), 256, 0, s>>>(st, nc, pass, j, cond);
+  k_update<T, CH><<<grd, CH / 2, 0, s>>>(st, nc, pass, j, fused, cond);
 }
 
 template <typename T>
@@ -404,15 +438,19 @@ cudaError_t start_t(const KrylovState& st, const double2* r0, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// passes: 1 (classical Gram-Schmidt), 2 (twice, CGS2) or 0 (once, then again only for the systems that the
+// norm-drop test flags).
 template <typename T>
 cudaError_t orth_t(const KrylovState& st, int passes, int j, cudaStream_t s) {
   const int ch = chunk_of(st.n, st.nrhs);
-  for (int p = 0; p < passes; ++p) {
+  const int np = passes == 1 ? 1 : 2;
+  for (int p = 0; p < np; ++p) {
+    const int mode = p == 0 ? 0 : (passes == 0 ? 1 : 2);
     switch (ch) {
-      case 512: orth_pass<T, 512>(st, p, j, s); break;
-      case 256: orth_pass<T, 256>(st, p, j, s); break;
-      case 128: orth_pass<T, 128>(st, p, j, s); break;
-      default: orth_pass<T, 64>(st, p, j, s); break;
+      case 512: orth_pass<T, 512>(st, p, mode, j, s); break;
+      case 256: orth_pass<T, 256>(st, p, mode, j, s); break;
+      case 128: orth_pass<T, 128>(st, p, mode, j, s); break;
+      default: orth_pass<T, 64>(st, p, mode, j, s); break;
     }
   }
   return cudaGetLastError();

@@ -409,3 +409,25 @@ def test_concentric_gpu_solution_matches_two_layer_series(B, torch):
             assert rel(x[0].cpu().numpy(), xl) <= SOLUTION_TOL_MIXED
         p.close()
     assert errs[1] < errs[0] / 1.6 and errs[1] < 3e-3
+
+
+@pytest.mark.parametrize("name", ["circle_11", "junction_16"])
+def test_mixed_inner_solves_keep_orthogonality(B, torch, name):
+    """A high-frequency circle and a low-frequency junction disk of the serving stream: one classical
+    Gram-Schmidt pass in FP32 loses orthogonality there (measured: 1275 and 309 iterations against 106 and 43
+    for FP64); the selective second pass brings the mixed path back within a small factor of FP64."""
+    wp = next(w for _, w in W.cfg_serving_c5(count=20) if w.name == name)
+    q = B.Problem.from_workload(wp, prec="mixed", tol=1e-8, max_iter=400)
+    x = torch.empty((1, wp.n_unknowns), dtype=torch.complex128, device="cuda")
+    st, it, rs = q.bem_solve_planewave([0.0], x)
+    q.close()
+    q = B.Problem.from_workload(wp, prec="fp64", tol=1e-12, max_iter=800)
+    x64 = torch.empty((1, wp.n_unknowns), dtype=torch.complex128, device="cuda")
+    st64, it64, rs64 = q.bem_solve_planewave([0.0], x64)
+    q.close()
+    q = B.Problem.from_workload(wp, prec="fp64", tol=1e-8, max_iter=800)
+    st8, it8, rs8 = q.bem_solve_planewave([0.0], torch.empty_like(x64))
+    q.close()
+    assert st == B.BEM_OK and rs[0] <= 1e-8
+    assert it[0] <= 3 * it8[0], (int(it[0]), int(it8[0]))
+    assert rel(x[0].cpu().numpy(), x64[0].cpu().numpy()) <= SOLUTION_TOL_MIXED
