@@ -103,6 +103,13 @@ struct bem_problem {
   double* d_small = nullptr;   // angles etc.
   size_t small_cap = 0;
   int* h_pin = nullptr;        // pinned host mirror of counters
+  // tensor-core GMRES iterations recorded as a CUDA graph (replayed on an internal stream)
+  cudaGraphExec_t ig_exec = nullptr;
+  const void* ig_ws = nullptr;
+  const void* ig_a16 = nullptr;
+  int ig_n2 = 0, ig_nrhs = 0, ig_m = 0, ig_passes = -1;
+  cudaStream_t ig_stream = nullptr;
+  cudaEvent_t ig_ev[3] = {nullptr, nullptr, nullptr};
   // measurement: event pairs per phase, kernel launches per phase
   bool prof = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[BEM_PH_COUNT];
@@ -312,6 +319,7 @@ size_t krylov_bytes(int n2, int nrhs, int m, bool fp32) {
   add((size_t)nrhs * 8);                  // resid
   add((size_t)nrhs * 8);                  // tolv
   add(4);                                 // n_active
+  add(4);                                 // jdev
   // mixed extras: residual r (FP64), rhs copy of the inner solve (FP32 not needed), tc workspace
   add((size_t)nrhs * n2 * 16);
   add(matvec_tc_workspace_bytes(n2, nrhs));
@@ -367,6 +375,7 @@ Solver carve_solver(bem_problem* p, int nrhs, bool fp32) {
   st.resid = c.take<double>(nrhs);
   st.tolv = c.take<double>(nrhs);
   st.n_active = c.take<int>(1);
+  st.jdev = c.take<int>(1);
   sv.r = c.take<double2>((size_t)nrhs * n2);
   sv.tcws_bytes = matvec_tc_workspace_bytes(n2, nrhs);
   sv.tcws = c.take<char>(sv.tcws_bytes);
@@ -406,44 +415,100 @@ bem_status gmres_run(bem_problem* p, Solver& sv, const double2* r0, double2* x, 
     Phase ph(p, BEM_PH_GIVENS, s, 3);
     CU(krylov_start(st, r0, tol, s));
   }
-  // Iterations are queued kSyncEvery at a time before the host reads the active count: the GPU never
-  // waits for the host between iterations.  Once every system has converged, the queued iterations find
-  // their gates closed (n_active = 0, active flags cleared) and return at once.
-  constexpr int kSyncEvery = 4;
+  // automatic: two passes for the FP64 basis; for the FP32 basis one pass, and a second one only for the
+  // systems whose vector the first pass shrank below a tenth of its length (selective reorthogonalisation)
+  const int passes = p->o.orth_passes ? p->o.orth_passes : (fp32 ? 0 : 2);
   const int* gate = st.n_active;
-  for (int j = 0; j < st.m; ++j) {
+  // one iteration: product, orthogonalisation, rotations and scaling of the next basis vector (the kernels read
+  // the iteration index from the device; only the non-tensor-core products take the basis vector's address)
+  auto iteration = [&](int j) -> cudaError_t {
     void* Vj = static_cast<char*>(st.V) + (size_t)j * nrhs * n2 * tb;
+    cudaError_t e;
     {
-    Phase ph(p, BEM_PH_MATVEC, s, 1);
-    if (p->o.matrix_free) {
-      CU(launch_matvec_free(p->elem(), p->n, p->dom, make_quad(p->o.quad_order), p->o.form, nrhs,
-                            static_cast<const double2*>(Vj), static_cast<double2*>(st.W), s, gate));
-    } else if (!fp32) {
-      CU(launch_matvec_c64(static_cast<const double2*>(p->d_A), n2, n2, nrhs, static_cast<const double2*>(Vj),
-                           static_cast<double2*>(st.W), s, gate));
-    } else if (use_tc) {
-      CU(launch_matvec_tc(p->d_A16, n2, nrhs, nullptr, static_cast<float2*>(st.W), sv.tcws, sv.tcws_bytes, s,
-                          gate));   // B = V_j, written by the Krylov kernels
-    } else {
-      CU(launch_matvec_c32(static_cast<const float2*>(p->d_A), n2, n2, nrhs, static_cast<const float2*>(Vj),
-                           static_cast<float2*>(st.W), st.active, s, gate));
+      Phase ph(p, BEM_PH_MATVEC, s, 1);
+      if (p->o.matrix_free) {
+        e = launch_matvec_free(p->elem(), p->n, p->dom, make_quad(p->o.quad_order), p->o.form, nrhs,
+                               static_cast<const double2*>(Vj), static_cast<double2*>(st.W), s, gate);
+      } else if (!fp32) {
+        e = launch_matvec_c64(static_cast<const double2*>(p->d_A), n2, n2, nrhs, static_cast<const double2*>(Vj),
+                              static_cast<double2*>(st.W), s, gate);
+      } else if (use_tc) {
+        e = launch_matvec_tc(p->d_A16, n2, nrhs, nullptr, static_cast<float2*>(st.W), sv.tcws, sv.tcws_bytes, s,
+                             gate);   // B = V_j, written by the Krylov kernels
+      } else {
+        e = launch_matvec_c32(static_cast<const float2*>(p->d_A), n2, n2, nrhs, static_cast<const float2*>(Vj),
+                              static_cast<float2*>(st.W), st.active, s, gate);
+      }
     }
-    }
+    if (e != cudaSuccess) return e;
     {
-      // automatic: two passes for the FP64 basis; for the FP32 basis one pass, and a second one only for the
-      // systems whose vector the first pass shrank below a tenth of its length (selective reorthogonalisation)
-      const int passes = p->o.orth_passes ? p->o.orth_passes : (fp32 ? 0 : 2);
       Phase ph(p, BEM_PH_ARNOLDI, s, 3 * (passes == 1 ? 1 : 2));
-      CU(krylov_orthogonalise(st, passes, j, s));
+      e = krylov_orthogonalise(st, passes, s);
     }
-    {
-      Phase ph(p, BEM_PH_GIVENS, s, 3);
-      CU(krylov_finish_step(st, tol, j, s));
+    if (e != cudaSuccess) return e;
+    Phase ph(p, BEM_PH_GIVENS, s, 3);
+    return krylov_finish_step(st, tol, s);
+  };
+  if (use_tc && !p->prof) {
+    // The tensor-core path's launches do not depend on the iteration index, so kGraphIters iterations are
+    // recorded once per workspace layout as a CUDA graph and replayed on an internal stream ordered after s.
+    // The host reads the active count of one replay while the next one runs.
+    constexpr int kGraphIters = 8;
+    if (!p->ig_stream) {
+      CU(cudaStreamCreateWithFlags(&p->ig_stream, cudaStreamNonBlocking));
+      for (cudaEvent_t& e : p->ig_ev) CU(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     }
-    if ((j + 1) % kSyncEvery == 0) {
-      CU(cudaMemcpyAsync(p->h_pin, st.n_active, sizeof(int), cudaMemcpyDeviceToHost, s));
-      CU(cudaStreamSynchronize(s));
-      if (p->h_pin[0] == 0) break;
+    if (p->ig_exec && (p->ig_ws != p->ws || p->ig_a16 != p->d_A16 || p->ig_n2 != n2 || p->ig_nrhs != nrhs ||
+                       p->ig_m != st.m || p->ig_passes != passes)) {
+      cudaGraphExecDestroy(p->ig_exec);
+      p->ig_exec = nullptr;
+    }
+    cudaStream_t gs = p->ig_stream;
+    if (!p->ig_exec) {
+      CU(matvec_tc_setup());
+      const cudaStream_t user = s;
+      s = gs;   // the iteration body launches on the capturing stream
+      CU(cudaStreamBeginCapture(gs, cudaStreamCaptureModeThreadLocal));
+      cudaError_t ce = cudaSuccess;
+      for (int k = 0; k < kGraphIters && ce == cudaSuccess; ++k) ce = iteration(0);
+      cudaGraph_t graph = nullptr;
+      const cudaError_t ee = cudaStreamEndCapture(gs, &graph);
+      s = user;
+      if (ce == cudaSuccess) ce = ee;
+      if (ce == cudaSuccess) ce = cudaGraphInstantiate(&p->ig_exec, graph, 0);
+      if (graph) cudaGraphDestroy(graph);
+      if (ce != cudaSuccess) {
+        p->ig_exec = nullptr;
+        return fail(BEM_ECUDA, "recording the GMRES iteration graph failed: %s", cudaGetErrorString(ce));
+      }
+      p->ig_ws = p->ws; p->ig_a16 = p->d_A16; p->ig_n2 = n2; p->ig_nrhs = nrhs; p->ig_m = st.m;
+      p->ig_passes = passes;
+    }
+    CU(cudaEventRecord(p->ig_ev[2], s));
+    CU(cudaStreamWaitEvent(gs, p->ig_ev[2], 0));
+    for (int j = 0, r = 0; j < st.m; j += kGraphIters, ++r) {
+      CU(cudaGraphLaunch(p->ig_exec, gs));
+      CU(cudaMemcpyAsync(p->h_pin + (r & 1), st.n_active, sizeof(int), cudaMemcpyDeviceToHost, gs));
+      CU(cudaEventRecord(p->ig_ev[r & 1], gs));
+      if (r > 0) {
+        CU(cudaEventSynchronize(p->ig_ev[(r - 1) & 1]));
+        if (p->h_pin[(r - 1) & 1] == 0) break;
+      }
+    }
+    CU(cudaEventRecord(p->ig_ev[2], gs));
+    CU(cudaStreamWaitEvent(s, p->ig_ev[2], 0));
+  } else {
+    // Iterations are queued kSyncEvery at a time before the host reads the active count: the GPU never
+    // waits for the host between iterations.  Once every system has converged, the queued iterations find
+    // their gates closed (n_active = 0, active flags cleared) and return at once.
+    constexpr int kSyncEvery = 4;
+    for (int j = 0; j < st.m; ++j) {
+      CU(iteration(j));
+      if ((j + 1) % kSyncEvery == 0) {
+        CU(cudaMemcpyAsync(p->h_pin, st.n_active, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+        if (p->h_pin[0] == 0) break;
+      }
     }
   }
   {
@@ -676,6 +741,10 @@ BEM_API void bem_problem_destroy(bem_problem* p) {
   if (p->ws) cudaFree(p->ws);
   if (p->d_small) cudaFree(p->d_small);
   if (p->h_pin) cudaFreeHost(p->h_pin);
+  if (p->ig_exec) cudaGraphExecDestroy(p->ig_exec);
+  for (cudaEvent_t e : p->ig_ev)
+    if (e) cudaEventDestroy(e);
+  if (p->ig_stream) cudaStreamDestroy(p->ig_stream);
   for (int k = 0; k < BEM_PH_COUNT; ++k)
     for (auto& pr : p->ev[k]) {
       cudaEventDestroy(pr.first);

@@ -616,4 +616,6 @@ void matvec_tc_b_operand(void* ws, int n, void** bhi, void** blo, size_t* ldb) {
 
 size_t matvec_tc_b_bytes(int n) { return 2 * b_bytes(n); }
 
+cudaError_t matvec_tc_setup() { return smem_attr_set() && encode_fn() ? cudaSuccess : cudaErrorNotSupported; }
+
 }  // namespace bem

@@ -121,6 +121,8 @@ cudaError_t launch_matvec_tc(const void* a16, int n, int nrhs, const float2* x, 
                              size_t ws_bytes, cudaStream_t s, const int* gate = nullptr);
 void matvec_tc_b_operand(void* ws, int n, void** bhi, void** blo, size_t* ldb);
 size_t matvec_tc_b_bytes(int n);
+// One-time settings of the tensor-core kernel (shared-memory limit); call before recording it in a graph.
+cudaError_t matvec_tc_setup();
 cudaError_t matvec_tc_clear_error(void* ws, int n, int nrhs, cudaStream_t s);
 size_t matvec_tc_a16_bytes(int n);
 cudaError_t launch_tc_prepare_a(const float2* A, int n, void* a16, cudaStream_t s);
@@ -161,6 +163,7 @@ struct KrylovState {
   double* resid;    // nrhs: estimated relative residual
   const double* tolv;  // nrhs per-system tolerances (overrides the scalar tol when non-null)
   int* n_active;    // device count of active systems (the gate of queued iterations)
+  int* jdev;        // current iteration index (set by the start kernel, advanced after each iteration)
   // when non-null (FP32 basis feeding the tensor-core product): every new basis vector is also written as
   // the FP16 x 3 operand of the next product (tc_operand.cuh), rows of stride ldb16
   void* b16hi;
@@ -171,8 +174,8 @@ int krylov_nchunk(int n);
 cudaError_t krylov_start(const KrylovState& st, const double2* r0, double tol_unused, cudaStream_t s);
 // passes: 1, 2, or 0 = one pass plus a second one for the systems whose w the first pass shrank below a tenth
 // of its length (selective reorthogonalisation).
-cudaError_t krylov_orthogonalise(const KrylovState& st, int passes, int j, cudaStream_t s);
-cudaError_t krylov_finish_step(const KrylovState& st, double tol, int j, cudaStream_t s);
+cudaError_t krylov_orthogonalise(const KrylovState& st, int passes, cudaStream_t s);
+cudaError_t krylov_finish_step(const KrylovState& st, double tol, cudaStream_t s);
 cudaError_t krylov_update_solution(const KrylovState& st, double2* x, cudaStream_t s);
 
 // For the batch engine: validate, upload geometry and allocate the mixed-precision matrix of p (without

@@ -91,6 +91,7 @@ __global__ void k_start_finish(KrylovState st, int nblk) {
   st.resid[s] = beta > 0.0 ? 1.0 : 0.0;
   st.hnext[s] = beta;
   if (beta > 0.0) atomicAdd(st.n_active, 1);   // zeroed by the launcher
+  if (s == 0) *st.jdev = 0;
 }
 
 template <typename T>
@@ -137,11 +138,12 @@ template <> struct Pair<double2> {
 //         in st.reo for the update kernel.
 // mode 2: unconditional second pass.
 template <typename T, int CH>
-__global__ void __launch_bounds__(kThreads) k_dots(KrylovState st, int nchunk, int j, int mode) {
+__global__ void __launch_bounds__(kThreads) k_dots(KrylovState st, int nchunk, int mode) {
   using F = typename Vec<T>::acc_t;
   constexpr int P = CH / 64;
   const int c = blockIdx.x, s = blockIdx.y;
   if (!st.active[s]) return;
+  const int j = *st.jdev;
   if (mode == 1) {
     __shared__ int need;
     if (threadIdx.x == 0) {
@@ -197,10 +199,11 @@ __global__ void __launch_bounds__(kThreads) k_dots(KrylovState st, int nchunk, i
 }
 
 // h_i = sum over chunks (FP64), one warp per (system, i); accumulate into column j of H (pass 0 sets,
-// later passes add).  grid = (ceil((j+1)/8), systems), 8 warps per block.
-__global__ void k_dots_reduce(KrylovState st, int nchunk, int pass, int j, int cond) {
+// later passes add).  grid = (ceil((m+1)/8), systems), 8 warps per block.
+__global__ void k_dots_reduce(KrylovState st, int nchunk, int pass, int cond) {
   const int s = blockIdx.y;
   if (!st.active[s] || (cond && !st.reo[s])) return;
+  const int j = *st.jdev;
   const int i = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (i > j) return;
   double hx = 0.0, hy = 0.0;
@@ -226,13 +229,13 @@ constexpr int kHsMax = 1001;
 // With fused != 0 every CTA also sums the chunk partials of the projections itself (FP64, chunk order) and
 // CTA 0 records them in column j of H (pass 0 sets, later passes add); otherwise k_dots_reduce did that.
 template <typename T, int CH>
-__global__ void __launch_bounds__(CH / 2) k_update(KrylovState st, int nchunk, int pass, int j, int fused,
-                                                   int cond) {
+__global__ void __launch_bounds__(CH / 2) k_update(KrylovState st, int nchunk, int pass, int fused, int cond) {
   using F = typename Vec<T>::acc_t;
   __shared__ F hs[2 * kHsMax];
   __shared__ double red[CH / 64];
   const int c = blockIdx.x, s = blockIdx.y;
   if (!st.active[s] || (cond && !st.reo[s])) return;   // cond: a conditional pass the system did not need
+  const int j = *st.jdev;
   for (int i = threadIdx.x; i <= j; i += CH / 2) {
     double2 h;
     if (fused) {
@@ -289,10 +292,11 @@ __global__ void __launch_bounds__(CH / 2) k_update(KrylovState st, int nchunk, i
 // column and the rotations in shared memory and apply the rotations as a scan (warp_rotate_column); lane 0
 // then forms the new rotation.
 constexpr int kFinishMaxM = 1000;
-__global__ void __launch_bounds__(32) k_finish(KrylovState st, int nchunk, double tol, int j) {
+__global__ void __launch_bounds__(32) k_finish(KrylovState st, int nchunk, double tol) {
   __shared__ double2 sh_h[kFinishMaxM + 1], sh_c[kFinishMaxM], sh_s[kFinishMaxM];
   const int s = blockIdx.x, lane = threadIdx.x;
   if (s >= st.nrhs || !st.active[s]) return;
+  const int j = *st.jdev;
   double t = 0.0;
   for (int c = lane; c < nchunk; c += 32) t += st.npart[(size_t)s * nchunk + c];
   t = warp_sum(t);
@@ -332,10 +336,11 @@ __global__ void __launch_bounds__(32) k_finish(KrylovState st, int nchunk, doubl
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_scale_next(KrylovState st, int j) {
+__global__ void __launch_bounds__(kThreads) k_scale_next(KrylovState st) {
   using F = typename Vec<T>::acc_t;
   const int k = blockIdx.x * kThreads + threadIdx.x, s = blockIdx.y;
   if (!st.active[s] || k >= st.n) return;
+  const int j = *st.jdev;
   const T* W = static_cast<const T*>(st.W) + (size_t)s * st.n;
   T* Vn = static_cast<T*>(st.V) + ((size_t)(j + 1) * st.nrhs + s) * st.n;
   const F inv = (F)1 / (F)st.hnext[s];   // in the basis precision (an FP64 division per entry is costly)
@@ -345,6 +350,12 @@ __global__ void __launch_bounds__(kThreads) k_scale_next(KrylovState st, int j) 
   Vn[k] = w;
   if (st.b16hi)
     tc_write_b(static_cast<__half*>(st.b16hi), static_cast<__half*>(st.b16lo), st.ldb16, s, k, (float)w.x, (float)w.y);
+}
+
+// The iteration index lives on the device, so one recorded sequence of launches serves every iteration (the
+// tensor-core path replays it as a CUDA graph).
+__global__ void k_advance(KrylovState st) {
+  if (threadIdx.x == 0) *st.jdev += 1;
 }
 
 // Least squares: back substitution of the triangularised Hessenberg system, one CTA per system.
@@ -416,14 +427,14 @@ int chunk_of(int n, int nrhs) {
 
 // mode as for k_dots (0: first pass, 1: conditional second pass, 2: second pass)
 template <typename T, int CH>
-void orth_pass(const KrylovState& st, int pass, int mode, int j, cudaStream_t s) {
+void orth_pass(const KrylovState& st, int pass, int mode, cudaStream_t s) {
   const int nc = (st.n + CH - 1) / CH;
   dim3 grd(nc, st.nrhs);
   const int fused = nc <= 32;   // few chunks: each update CTA sums the partials itself (one launch less)
   const int cond = mode == 1;
-  k_dots<T, CH><<<grd, kThreads, 0, s>>>(st, nc, j, mode);
-  if (!fused) k_dots_reduce<<<dim3((j + 8) / 8, st.nrhs), 256, 0, s>>>(st, nc, pass, j, cond);
-  k_update<T, CH><<<grd, CH / 2, 0, s>>>(st, nc, pass, j, fused, cond);
+  k_dots<T, CH><<<grd, kThreads, 0, s>>>(st, nc, mode);
+  if (!fused) k_dots_reduce<<<dim3((st.m + 8) / 8, st.nrhs), 256, 0, s>>>(st, nc, pass, cond);
+  k_update<T, CH><<<grd, CH / 2, 0, s>>>(st, nc, pass, fused, cond);
 }
 
 template <typename T>
@@ -441,27 +452,28 @@ cudaError_t start_t(const KrylovState& st, const double2* r0, cudaStream_t s) {
 // passes: 1 (classical Gram-Schmidt), 2 (twice, CGS2) or 0 (once, then again only for the systems that the
 // norm-drop test flags).
 template <typename T>
-cudaError_t orth_t(const KrylovState& st, int passes, int j, cudaStream_t s) {
+cudaError_t orth_t(const KrylovState& st, int passes, cudaStream_t s) {
   const int ch = chunk_of(st.n, st.nrhs);
   const int np = passes == 1 ? 1 : 2;
   for (int p = 0; p < np; ++p) {
     const int mode = p == 0 ? 0 : (passes == 0 ? 1 : 2);
     switch (ch) {
-      case 512: orth_pass<T, 512>(st, p, mode, j, s); break;
-      case 256: orth_pass<T, 256>(st, p, mode, j, s); break;
-      case 128: orth_pass<T, 128>(st, p, mode, j, s); break;
-      default: orth_pass<T, 64>(st, p, mode, j, s); break;
+      case 512: orth_pass<T, 512>(st, p, mode, s); break;
+      case 256: orth_pass<T, 256>(st, p, mode, s); break;
+      case 128: orth_pass<T, 128>(st, p, mode, s); break;
+      default: orth_pass<T, 64>(st, p, mode, s); break;
     }
   }
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t finish_t(const KrylovState& st, double tol, int j, cudaStream_t s) {
+cudaError_t finish_t(const KrylovState& st, double tol, cudaStream_t s) {
   const int ch = chunk_of(st.n, st.nrhs);
   const int nc = (st.n + ch - 1) / ch;   // the update kernel's chunks (its squared norms)
-  k_finish<<<st.nrhs, 32, 0, s>>>(st, nc, tol, j);
-  k_scale_next<T><<<dim3(nblk_of(st.n), st.nrhs), kThreads, 0, s>>>(st, j);
+  k_finish<<<st.nrhs, 32, 0, s>>>(st, nc, tol);
+  k_scale_next<T><<<dim3(nblk_of(st.n), st.nrhs), kThreads, 0, s>>>(st);
+  k_advance<<<1, 32, 0, s>>>(st);
   return cudaGetLastError();
 }
 
@@ -486,11 +498,11 @@ int krylov_nchunk(int n) { return std::max(nchunk_of(n), nblk_of(n)); }
 cudaError_t krylov_start(const KrylovState& st, const double2* r0, double, cudaStream_t s) {
   return st.basis_fp32 ? start_t<float2>(st, r0, s) : start_t<double2>(st, r0, s);
 }
-cudaError_t krylov_orthogonalise(const KrylovState& st, int passes, int j, cudaStream_t s) {
-  return st.basis_fp32 ? orth_t<float2>(st, passes, j, s) : orth_t<double2>(st, passes, j, s);
+cudaError_t krylov_orthogonalise(const KrylovState& st, int passes, cudaStream_t s) {
+  return st.basis_fp32 ? orth_t<float2>(st, passes, s) : orth_t<double2>(st, passes, s);
 }
-cudaError_t krylov_finish_step(const KrylovState& st, double tol, int j, cudaStream_t s) {
-  return st.basis_fp32 ? finish_t<float2>(st, tol, j, s) : finish_t<double2>(st, tol, j, s);
+cudaError_t krylov_finish_step(const KrylovState& st, double tol, cudaStream_t s) {
+  return st.basis_fp32 ? finish_t<float2>(st, tol, s) : finish_t<double2>(st, tol, s);
 }
 cudaError_t krylov_update_solution(const KrylovState& st, double2* x, cudaStream_t s) {
   return st.basis_fp32 ? xupd_t<float2>(st, x, s) : xupd_t<double2>(st, x, s);
