@@ -370,7 +370,7 @@ def main():
         e2e_ms = []
         h2d = nel * (4 * 8 + 2 * 4) + N_RHS * 8 + N_FF * 8
         d2h = N_RHS * 2 * nel * 16 + N_RHS * N_FF * 16
-        for k in range(2):
+        for k in range(4):   # one warm-up call, the median of three timed ones
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             q = P.Problem.from_workload(wp, prec=args.prec, tol=args.tol, max_iter=args.max_iter)
