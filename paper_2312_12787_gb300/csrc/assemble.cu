@@ -12,12 +12,29 @@
 // 32-entry row segment.  The node geometry and the phase k r are FP64, the rest double-float on the FP32
 // pipe; the mixed path stores the double-float entry as complex FP32 (hi) plus its FP32 remainder (lo).
 #include <algorithm>
+#include <mutex>
 
 #include "internal.cuh"
 #include "bessel.cuh"
 #include "pair.cuh"
 
 namespace bem {
+
+// The Bessel table of the Taylor branch (bessel.cuh) lives in this translation unit's device memory; it is
+// copied in once per device, before the first launch of a kernel that evaluates Hankel functions.
+static cudaError_t ensure_bessel_table() {
+  static std::mutex mu;
+  static bool done[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(mu);
+  if (done[dev]) return cudaSuccess;
+  e = cudaMemcpyToSymbol(g_bessel_tab, bessel_tab_host(), sizeof(BesselTabEntry) * kTabN);
+  if (e == cudaSuccess) done[dev] = true;
+  return e;
+}
 
 namespace {
 
@@ -299,6 +316,7 @@ cudaError_t launch_elements(const ElemDev& e, int n, cudaStream_t s) {
 
 cudaError_t launch_assemble(const ElemDev& e, int n, const DomTab& dom, const Quad& q, int form, int store_mixed,
                             void* A, void* Alo, size_t lda, cudaStream_t s) {
+  if (const cudaError_t te = ensure_bessel_table(); te != cudaSuccess) return te;
   dim3 blk(32, 8);
   dim3 grd((n + 31) / 32, (n + 7) / 8);
   if (store_mixed) k_assemble<1><<<grd, blk, 0, s>>>(e, n, dom, q, form, A, Alo, lda);
@@ -308,6 +326,7 @@ cudaError_t launch_assemble(const ElemDev& e, int n, const DomTab& dom, const Qu
 
 cudaError_t launch_matvec_free(const ElemDev& e, int n, const DomTab& dom, const Quad& q, int form, int nrhs,
                                const double2* x, double2* y, cudaStream_t s, const int* gate) {
+  if (const cudaError_t te = ensure_bessel_table(); te != cudaSuccess) return te;
   for (int r = 0; r < nrhs; ++r)
     k_matvec_free<<<(n + 7) / 8, 256, 0, s>>>(e, n, dom, q, form, x + (size_t)r * 2 * n, y + (size_t)r * 2 * n,
                                               gate);
@@ -321,6 +340,7 @@ cudaError_t launch_assemble_batched(const AsmJob* jobs_dev, int njobs, const lon
                                    cudaStream_t s) {
   if (total_tiles <= 0) return cudaSuccess;
   if (total_tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
+  if (const cudaError_t te = ensure_bessel_table(); te != cudaSuccess) return te;
   const unsigned grid = (unsigned)total_tiles;
 #define BEM_ASM_CASE(TYV)                                                                                  \
   case TYV:                                                                                                \

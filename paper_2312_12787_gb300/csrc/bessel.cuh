@@ -14,6 +14,7 @@
 #pragma once
 
 #include <cstring>
+#include <vector>
 
 #if defined(__CUDACC__)
 #define BEM_HD __host__ __device__ __forceinline__
@@ -655,9 +656,121 @@ BEM_HD void bessel01_asymp_f2x(double x, F2 X, Bessel01F2& b) {
   b.y1 = f2_neg(f2_sub(f2_mul(p1, er), f2_mul(q1, ei)));
 }
 
+// ---- tabulated values and Taylor steps on 2 <= x < 35 --------------------------------------------------
+// J0, Y0, J1, Y1 at x_k = 2 + k/32 (computed once on the host with the FP64 routines above, error ~1e-15 of
+// |H|), stored in double-float with 1/x_k.  Between grid points both pairs obey the same first-order system
+// Z0' = -Z1, Z1' = Z0 - Z1/x (DLMF 10.6.2), so with Z0(x_k + h) = sum a_n h^n and Z1(x_k + h) = sum b_n h^n the
+// Taylor coefficients follow from
+//   a_{n+1} = -b_n / (n+1),   b_{n+1} = (a_n - c_n) / (n+1),   c_n = (b_n - c_{n-1}) / x_k,
+// where c_n are the coefficients of Z1/(x_k + h).  With |h| <= 1/64, eight orders leave a remainder below
+// 1e-16; orders 0-3 run in double-float, orders 4-7 (below 3e-9 of the value) in FP32.  This replaces the
+// recurrence of Miller's algorithm (56 steps) and the long expansion near x = 18 by about a fifth of the
+// arithmetic.
+constexpr double kTabStep = 1.0 / 32.0;
+constexpr int kTabN = 1057;          // x_k = 2 + k / 32, k = 0 .. 1056: [2, 35]
+constexpr float kTabXMax = 35.0f;    // the table serves 2 <= x < 35
+struct alignas(16) BesselTabEntry {
+  float j0h, j0l, y0h, y0l, j1h, j1l, y1h, y1l, ixh, ixl, pad0, pad1;   // 48 bytes: three 16-byte loads
+};
+
+#if defined(__CUDACC__)
+static __device__ BesselTabEntry g_bessel_tab[kTabN];
+#endif
+
+// Host copy of the table (built on first use, thread-safe).
+inline const BesselTabEntry* bessel_tab_host() {
+  static const std::vector<BesselTabEntry> tab = [] {
+    std::vector<BesselTabEntry> t(kTabN);
+    for (int k = 0; k < kTabN; ++k) {
+      const double x = 2.0 + k * kTabStep;
+      Bessel01 b;
+      if (x < BEM_X_ASYMP) bessel01_miller(x, b);
+      else bessel01_asymp(x, b);
+      auto put = [](double v, float& h, float& l) {
+        h = (float)v;
+        l = (float)(v - (double)h);
+      };
+      BesselTabEntry& e = t[k];
+      put(b.j0, e.j0h, e.j0l);
+      put(b.y0, e.y0h, e.y0l);
+      put(b.j1, e.j1h, e.j1l);
+      put(b.y1, e.y1h, e.y1l);
+      put(1.0 / x, e.ixh, e.ixl);
+      e.pad0 = e.pad1 = 0.f;
+    }
+    return t;
+  }();
+  return tab.data();
+}
+
+// Taylor coefficients and sums for one pair (Z0, Z1) from (z0, z1) at x_k; inv = 1/x_k; H = h.
+BEM_HD void taylor_pair(F2 z0, F2 z1, F2 inv, F2 H, F2& out0, F2& out1) {
+  constexpr F2 kInv2 = F2{0.5f, 0.f};
+  constexpr F2 kInv3 = f2_const(1.0 / 3.0);
+  // orders 0..3 in double-float
+  const F2 a0 = z0, b0 = z1;
+  const F2 c0 = f2_mul(b0, inv);
+  const F2 a1 = f2_neg(b0);
+  const F2 b1 = f2_sub(a0, c0);
+  const F2 c1 = f2_mul(f2_sub(b1, c0), inv);
+  const F2 a2 = f2_pow2(f2_neg(b1), 0.5f);
+  const F2 b2 = f2_mul(f2_sub(a1, c1), kInv2);
+  const F2 c2 = f2_mul(f2_sub(b2, c1), inv);
+  const F2 a3 = f2_mul(f2_neg(b2), kInv3);
+  const F2 b3 = f2_mul(f2_sub(a2, c2), kInv3);
+  const F2 c3 = f2_mul(f2_sub(b3, c2), inv);
+  // orders 4..7 in FP32
+  const float iv = inv.h, hf = H.h;
+  float an = -b3.h * 0.25f, bn = (a3.h - c3.h) * 0.25f, cn = (bn - c3.h) * iv;
+  float a[4], bq[4];
+  a[0] = an; bq[0] = bn;
+#pragma unroll
+  for (int n = 4; n < 7; ++n) {
+    const float r = 1.f / (float)(n + 1);
+    const float an1 = -bn * r, bn1 = (an - cn) * r;
+    an = an1; bn = bn1;
+    cn = (bn - cn) * iv;
+    a[n - 3] = an; bq[n - 3] = bn;
+  }
+  float pa = a[3], pb = bq[3];
+#pragma unroll
+  for (int n = 2; n >= 0; --n) {
+    pa = fmaf(pa, hf, a[n]);
+    pb = fmaf(pb, hf, bq[n]);
+  }
+  // double-float Horner over orders 3..0 with the FP32 tail
+  F2 s0 = f2_add(a3, f2_mulf(H, pa));
+  F2 s1 = f2_add(b3, f2_mulf(H, pb));
+  s0 = f2_add(a2, f2_mul(s0, H));
+  s1 = f2_add(b2, f2_mul(s1, H));
+  s0 = f2_add(a1, f2_mul(s0, H));
+  s1 = f2_add(b1, f2_mul(s1, H));
+  out0 = f2_add(a0, f2_mul(s0, H));
+  out1 = f2_add(b0, f2_mul(s1, H));
+}
+
+BEM_HD void bessel01_taylor_f2(double x, F2 X, Bessel01F2& b) {
+#if defined(__CUDA_ARCH__)
+  const int k = __float2int_rn((X.h - 2.f) * 32.f);
+  const float4* ep = reinterpret_cast<const float4*>(&g_bessel_tab[k]);
+  const float4 e0 = __ldg(ep), e1 = __ldg(ep + 1), e2 = __ldg(ep + 2);
+  const F2 j0{e0.x, e0.y}, y0{e0.z, e0.w}, j1{e1.x, e1.y}, y1{e1.z, e1.w}, inv{e2.x, e2.y};
+#else
+  const int k = (int)lrintf((X.h - 2.f) * 32.f);
+  const BesselTabEntry& e = bessel_tab_host()[k];
+  const F2 j0{e.j0h, e.j0l}, y0{e.y0h, e.y0l}, j1{e.j1h, e.j1l}, y1{e.y1h, e.y1l}, inv{e.ixh, e.ixl};
+#endif
+  const double h = x - (2.0 + k * kTabStep);   // exact: x and the grid point agree to within 1/64
+  const F2 H = f2_from_bits(h);
+  taylor_pair(j0, j1, inv, H, b.j0, b.j1);
+  taylor_pair(y0, y1, inv, H, b.y0, b.y1);
+}
+
 BEM_HD void bessel01_f2(double x, F2 X, Bessel01F2& b) {
   if (X.h < (float)BEM_X_SERIES) {
     bessel01_series_f2(x, b);
+  } else if (X.h < kTabXMax) {
+    bessel01_taylor_f2(x, X, b);
   } else if (X.h < (float)BEM_X_ASYMP) {
     // even start order 1.6 x + 23 (rounded up): at least four orders beyond the smallest one that keeps
     // the truncation of J0, J1, Y0, Y1 below 2e-16 of |H0| on [2, 18); the largest of the warp's active lanes
