@@ -34,14 +34,14 @@ METRIC = "BEM solves/s (mixed vs FP64 GPU at err<=1e-6)"
 # Roofline inputs, from ncu counts of one launch on the star r = 1 + 0.3 cos 5t with N_e = 3072 (64 RHS),
 # scaled to other sizes by the number of matrix entries (profiles/assemble_star3072.md,
 # profiles/gemm_tc_star3072_64rhs.md):
-#  * k_assemble issues 4.976e9 warp instructions (sm__inst_executed.sum) over both the FP64 pipe (node
+#  * k_assemble issues 2.912e9 warp instructions (sm__inst_executed.sum) over both the FP64 pipe (node
 #    geometry, phase reduction) and the FP32 pipe (double-float Bessel arithmetic); neither pipe alone binds,
-#    so its roofline is the issue rate: 4 warp instructions per clock per SM.  DRAM traffic 549.1 MB.
+#    so its roofline is the issue rate: 4 warp instructions per clock per SM.  DRAM traffic 551.8 MB.
 #  * the multi-RHS GEMM streams A once: 2 x 2 bytes per real entry; measured DRAM traffic 316.3 MB.
 #  * the refinement residual runs 44 FP32 operations per complex multiply-add (double-float dot product):
 #    FP32 pipe, 128 operations per clock per SM.
-ASM_WARP_INST_N3072 = 4.976357746e9
-ASM_DRAM_BYTES_N3072 = 547283456 + 1771008
+ASM_WARP_INST_N3072 = 2.91162048e9
+ASM_DRAM_BYTES_N3072 = 550810112 + 970496
 GEMM_DRAM_BYTES_N3072 = 311.3e6 + 5.0e6
 RESID_FP32_OPS_PER_CMAC = 44
 SM_COUNT, SM_CLOCK_HZ = 152, 2.07e9
