@@ -313,6 +313,7 @@ size_t krylov_bytes(int n2, int nrhs, int m, bool fp32) {
   add((size_t)nrhs * nc * 8);             // npart
   add((size_t)nrhs * nc * 8);             // wpart
   add((size_t)nrhs * 4);                  // reo
+  add((size_t)nrhs * 4);                  // arrive
   add((size_t)nrhs * (m + 1) * 16);       // hcol
   add((size_t)nrhs * 4);                  // active
   add((size_t)nrhs * 4);                  // iters
@@ -369,6 +370,7 @@ Solver carve_solver(bem_problem* p, int nrhs, bool fp32) {
   st.npart = c.take<double>((size_t)nrhs * nc);
   st.wpart = c.take<double>((size_t)nrhs * nc);
   st.reo = c.take<int>(nrhs);
+  st.arrive = c.take<int>(nrhs);
   st.hcol = c.take<double2>((size_t)nrhs * (m + 1));
   st.active = c.take<int>(nrhs);
   st.iters = c.take<int>(nrhs);

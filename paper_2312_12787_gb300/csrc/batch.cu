@@ -65,6 +65,7 @@ struct VDev {
   double* npart;
   double* wpart;    // per chunk: ||w||^2 before projection (selective reorthogonalisation)
   int* reo;         // per slot: 1 if the conditional second Gram-Schmidt pass runs this iteration
+  int* arrive;      // per slot: first-pass update CTAs done (the last one takes the decision)
   int* n_active;
 };
 
@@ -112,28 +113,13 @@ __global__ void __launch_bounds__(256) kv_gemv(VDev d) {
 
 // partial projections <v_i, w> of one chunk; warp w takes i = w, w+8, ...
 // mode 0: first pass (warp 0 also records the chunk's ||w||^2 before projection); mode 1: conditional second
-// pass, run only for slots whose first pass shrank w below a tenth of its length (the decision, taken
-// alike by every CTA of the slot from the chunk sums, goes to d.reo for the reduction and update kernels);
-// mode 2: unconditional second pass.
+// pass, run only for slots whose first pass shrank w below a tenth of its length (the first pass's update
+// kernel records the decision in d.reo); mode 2: unconditional second pass.
 __global__ void __launch_bounds__(256) kv_dots(VDev d, int mode) {
   const int c = blockIdx.x;
   const int s = d.ch_slot[c];
   if (!d.active[s]) return;
-  if (mode == 1) {
-    __shared__ int need;
-    if (threadIdx.x == 0) {
-      double before = 0.0, after = 0.0;
-      const int c0 = d.cbeg[s], cn = d.ccnt[s];
-      for (int cc = 0; cc < cn; ++cc) {
-        before += d.wpart[c0 + cc];
-        after += d.npart[c0 + cc];
-      }
-      need = after < 0.01 * before;   // ||w_after|| < ||w_before|| / 10
-      if (c == c0) d.reo[s] = need;
-    }
-    __syncthreads();
-    if (!need) return;
-  }
+  if (mode == 1 && !d.reo[s]) return;   // decided by the first pass's update kernel
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n = d.n[s], j = d.j[s];
   const float2* W = d.W + d.u[s];
@@ -180,7 +166,7 @@ __global__ void kv_dots_reduce(VDev d, int pass, int cond) {
   }
 }
 
-__global__ void __launch_bounds__(256) kv_update(VDev d, int cond) {
+__global__ void __launch_bounds__(256) kv_update(VDev d, int pass, int cond) {
   __shared__ float2 hs[kMaxM + 1];
   __shared__ float accs[4][kCh][2];
   __shared__ double red[8];
@@ -224,6 +210,21 @@ __global__ void __launch_bounds__(256) kv_update(VDev d, int cond) {
     double t = 0.0;
     for (int w8 = 0; w8 < 8; ++w8) t += red[w8];
     d.npart[c] = t;
+    if (pass == 0) {
+      // the slot's last CTA to finish takes the decision for the conditional second pass (see kv_dots)
+      __threadfence();
+      if (atomicAdd(d.arrive + s, 1) == d.ccnt[s] - 1) {
+        __threadfence();
+        double before = 0.0, after = 0.0;
+        const int c0 = d.cbeg[s], cn = d.ccnt[s];
+        for (int cc = 0; cc < cn; ++cc) {
+          before += ((volatile double*)d.wpart)[c0 + cc];
+          after += ((volatile double*)d.npart)[c0 + cc];
+        }
+        d.reo[s] = after < 0.01 * before;   // ||w_after|| < ||w_before|| / 10
+        d.arrive[s] = 0;
+      }
+    }
   }
 }
 
@@ -317,6 +318,8 @@ __global__ void kv_start_fin(VDev d) {
   d.iters[s] = 0;
   d.j[s] = 0;
   d.resid[s] = beta > 0.0 ? 1.0 : 0.0;
+  d.arrive[s] = 0;
+  d.reo[s] = 0;
 }
 
 __global__ void __launch_bounds__(kCh) kv_start_scale(VDev d) {
@@ -449,6 +452,7 @@ struct BatchEngine {
   double* npart = nullptr;
   double* wpart = nullptr;
   int* reo = nullptr;
+  int* arrive = nullptr;
   double* angles = nullptr;
   int max_chunks = 0, max_rb = 0;
   int nchunks = 0, nrb = 0;
@@ -513,7 +517,7 @@ VDev view(const BatchEngine& e) {
   d.active = e.active; d.iters = e.iters; d.j = e.jj; d.flag = e.flag;
   d.cbeg = e.cbeg; d.ccnt = e.ccnt; d.ch_slot = e.ch_slot; d.ch_loc = e.ch_loc; d.nchunks = e.nchunks;
   d.rb_slot = e.rb_slot; d.rb_row = e.rb_row; d.nrb = e.nrb;
-  d.part = e.part; d.npart = e.npart; d.wpart = e.wpart; d.reo = e.reo; d.n_active = e.n_active;
+  d.part = e.part; d.npart = e.npart; d.wpart = e.wpart; d.reo = e.reo; d.arrive = e.arrive; d.n_active = e.n_active;
   return d;
 }
 
@@ -588,7 +592,7 @@ void enqueue_iteration(const BatchEngine& e, const VDev& d, int passes) {
     const int mode = p == 0 ? 0 : (passes == 0 ? 1 : 2);
     kv_dots<<<e.nchunks, 256, 0, e.st>>>(d, mode);
     kv_dots_reduce<<<dim3((e.m + 8) / 8, e.cap), 256, 0, e.st>>>(d, p, mode == 1);
-    kv_update<<<e.nchunks, 256, 0, e.st>>>(d, mode == 1);
+    kv_update<<<e.nchunks, 256, 0, e.st>>>(d, p, mode == 1);
   }
   kv_finish<<<e.cap, 32, 0, e.st>>>(d);
   kv_scale<<<e.nchunks, kCh, 0, e.st>>>(d);
@@ -721,7 +725,7 @@ BEM_API bem_status bem_batch_create(bem_batch** out, const bem_opts* opts, int m
        dalloc(&e.flag, cap) && dalloc(&e.n_active, 1) && dalloc(&e.cbeg, cap) && dalloc(&e.ccnt, cap) &&
        dalloc(&e.ch_slot, e.max_chunks) && dalloc(&e.ch_loc, e.max_chunks) && dalloc(&e.rb_slot, e.max_rb) &&
        dalloc(&e.rb_row, e.max_rb) && dalloc(&e.part, (size_t)e.max_chunks * (m + 1)) &&
-       dalloc(&e.npart, e.max_chunks) && dalloc(&e.wpart, e.max_chunks) && dalloc(&e.reo, cap) &&
+       dalloc(&e.npart, e.max_chunks) && dalloc(&e.wpart, e.max_chunks) && dalloc(&e.reo, cap) && dalloc(&e.arrive, cap) &&
        dalloc(&e.angles, cap);
   ok = ok && cudaMallocHost(&e.h_active, cap * sizeof(int)) == cudaSuccess &&
        cudaMallocHost(&e.h_iters, cap * sizeof(int)) == cudaSuccess &&
@@ -750,7 +754,7 @@ BEM_API void bem_batch_destroy(bem_batch* b) {
   if (e.gexec) cudaGraphExecDestroy(e.gexec);
   void* ptrs[] = {e.dA, e.dAlo, e.dn, e.du, e.V, e.W, e.X, e.R, e.Bv, e.H, e.cs, e.sn, e.g, e.y, e.hcol, e.beta,
                   e.hnext, e.resid, e.tol, e.rnorm, e.active, e.iters, e.jj, e.flag, e.n_active, e.cbeg, e.ccnt,
-                  e.ch_slot, e.ch_loc, e.rb_slot, e.rb_row, e.part, e.npart, e.wpart, e.reo, e.angles};
+                  e.ch_slot, e.ch_loc, e.rb_slot, e.rb_row, e.part, e.npart, e.wpart, e.reo, e.arrive, e.angles};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (e.h_active) cudaFreeHost(e.h_active);

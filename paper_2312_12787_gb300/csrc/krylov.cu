@@ -91,6 +91,8 @@ __global__ void k_start_finish(KrylovState st, int nblk) {
   st.resid[s] = beta > 0.0 ? 1.0 : 0.0;
   st.hnext[s] = beta;
   if (beta > 0.0) atomicAdd(st.n_active, 1);   // zeroed by the launcher
+  st.arrive[s] = 0;
+  st.reo[s] = 0;
   if (s == 0) *st.jdev = 0;
 }
 
@@ -134,8 +136,7 @@ template <> struct Pair<double2> {
 //         of its length, ||w_after||^2 < ||w_before||^2 / 100: the cancellation then costs one classical
 //         Gram-Schmidt pass in FP32 about a factor 10 of orthogonality, which the inner solves' 1e-5 tolerance
 //         no longer absorbs (the textbook 1/sqrt(2) threshold re-projects most steps of smooth problems, for
-//         the same iteration counts).  Every CTA takes the same decision from the chunk sums; CTA 0 records it
-//         in st.reo for the update kernel.
+//         the same iteration counts).  The first pass's update kernel records the decision in st.reo.
 // mode 2: unconditional second pass.
 template <typename T, int CH>
 __global__ void __launch_bounds__(kThreads) k_dots(KrylovState st, int nchunk, int mode) {
@@ -144,20 +145,7 @@ __global__ void __launch_bounds__(kThreads) k_dots(KrylovState st, int nchunk, i
   const int c = blockIdx.x, s = blockIdx.y;
   if (!st.active[s]) return;
   const int j = *st.jdev;
-  if (mode == 1) {
-    __shared__ int need;
-    if (threadIdx.x == 0) {
-      double before = 0.0, after = 0.0;
-      for (int cc = 0; cc < nchunk; ++cc) {
-        before += st.wpart[(size_t)s * nchunk + cc];
-        after += st.npart[(size_t)s * nchunk + cc];
-      }
-      need = after < 0.01 * before;   // ||w_after|| < ||w_before|| / 10
-      if (c == 0) st.reo[s] = need;
-    }
-    __syncthreads();
-    if (!need) return;
-  }
+  if (mode == 1 && !st.reo[s]) return;   // decided by the first pass's update kernel
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const size_t stride = (size_t)st.nrhs * st.n;
   const T* W = static_cast<const T*>(st.W) + (size_t)s * st.n;
@@ -284,6 +272,21 @@ __global__ void __launch_bounds__(CH / 2) k_update(KrylovState st, int nchunk, i
     double t = 0.0;
     for (int q = 0; q < CH / 64; ++q) t += red[q];
     st.npart[(size_t)s * nchunk + c] = t;
+    if (pass == 0) {
+      // the last CTA of the system to finish takes the reorthogonalisation decision for the conditional pass
+      // (norm-drop test, see k_dots) from all chunk sums, so that the conditional kernels only read a flag
+      __threadfence();
+      if (atomicAdd(st.arrive + s, 1) == nchunk - 1) {
+        __threadfence();
+        double before = 0.0, after = 0.0;
+        for (int cc = 0; cc < nchunk; ++cc) {
+          before += ((volatile double*)st.wpart)[(size_t)s * nchunk + cc];
+          after += ((volatile double*)st.npart)[(size_t)s * nchunk + cc];
+        }
+        st.reo[s] = after < 0.01 * before;   // ||w_after|| < ||w_before|| / 10
+        st.arrive[s] = 0;
+      }
+    }
   }
 }
 
