@@ -38,12 +38,13 @@ METRIC = "BEM solves/s (mixed vs FP64 GPU at err<=1e-6)"
 #    geometry, phase reduction) and the FP32 pipe (double-float Bessel arithmetic); neither pipe alone binds,
 #    so its roofline is the issue rate: 4 warp instructions per clock per SM.  DRAM traffic 551.8 MB.
 #  * the multi-RHS GEMM streams A once: 2 x 2 bytes per real entry; measured DRAM traffic 316.3 MB.
-#  * the refinement residual runs 44 FP32 operations per complex multiply-add (double-float dot product):
-#    FP32 pipe, 128 operations per clock per SM.
+#  * the refinement residual runs 24 FP32 operations per complex multiply-add (four exact products summed
+#    with an offset accumulator, four operations each, and eight FMAs for the small terms; the per-run
+#    offsets and the double-float fold are not counted): FP32 pipe, 128 operations per clock per SM.
 ASM_WARP_INST_N3072 = 2.91162048e9
 ASM_DRAM_BYTES_N3072 = 550810112 + 970496
 GEMM_DRAM_BYTES_N3072 = 311.3e6 + 5.0e6
-RESID_FP32_OPS_PER_CMAC = 44
+RESID_FP32_OPS_PER_CMAC = 24
 SM_COUNT, SM_CLOCK_HZ = 152, 2.07e9
 ISSUE_PEAK_G = SM_COUNT * 4 * SM_CLOCK_HZ / 1e9          # G warp instructions / s
 FP32_PEAK_T = SM_COUNT * 128 * SM_CLOCK_HZ / 1e12        # T FP32 thread operations / s

@@ -308,9 +308,18 @@ __global__ void __launch_bounds__(256) k_column_norms(const double2* v, int n, d
 // ---- refinement residual r = b - (hi + lo) x in double-float arithmetic on the FP32 pipes ----------
 // x (FP64) is first split into x_hi + x_lo (FP32).  The leading products hi * x_hi are formed exactly
 // (p = a b, e = fma(a, b, -p)) and summed with error-free two-sum steps into a running sum s and a
-// compensation c (the accurate dot-product scheme of Ogita, Rump and Oishi); the small terms
-// hi * x_lo + lo * x_hi join c directly.  The result s + c carries about twice FP32 precision, enough
-// for the residual of the FP64 refinement, at FP32-pipe speed instead of GB300's scarce FP64 rate.
+// compensation c (the accurate dot-product scheme of Ogita, Rump and Oishi; the one-column kernel) or with
+// an offset accumulator (the tiled kernel, below); the small terms hi * x_lo + lo * x_hi join c directly.
+// The result s + c carries about twice FP32 precision, enough for the residual of the FP64 refinement, at
+// FP32-pipe speed instead of GB300's scarce FP64 rate.
+
+// s + e = a + b exactly (Knuth's two-sum)
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  const float t = a + b;
+  const float bp = t - a;
+  e = (a - (t - bp)) + (b - bp);
+  s = t;
+}
 
 __device__ __forceinline__ void dot2_acc(float a, float b, float& s, float& c) {
   const float p = a * b;
@@ -374,35 +383,77 @@ __global__ void __launch_bounds__(256) k_resid_df_gemv(const float2* __restrict_
 // K may be split over blockIdx.z in ranges of kchunk columns: then each CTA writes its partial product
 // (rounded to FP64) to part[z][s][row] and k_resid_combine forms r; with part == nullptr the CTA covers all
 // of K and writes r directly.
-constexpr int kResBR = 32, kResBS = 64, kResBK = 16;
+//
+// The leading products hi * x_hi are summed with an offset accumulator instead of two-sum steps.  For a run
+// of kResSub columns, let M bound every |hi_re/im| * |x_hi re/im| of the run (from the run's maxima) and
+// let sigma be a power of two with sigma >= 64 M.  The accumulator starts at sigma; each product enters as
+//     t = fma(a, b, acc),  d = t - acc,  c += fma(a, b, -d),  acc = t.
+// acc stays within sigma +- 17 M, so t and acc lie within a factor two of each other and d is exact
+// (Sterbenz); d + (a b - d) is the exact product, and fma(a, b, -d) rounds a quantity below ulp(sigma).  At
+// the end of the run acc - sigma (again exact) joins a double-float total (S, L) by one two-sum step, and
+// c joins L.  Four FP32 operations per product instead of ten; the price is that the rounding of c is
+// relative to sigma instead of the running sum, a few times the error of the two-sum scheme and far below
+// what the refinement needs.
+constexpr int kResBR = 32, kResBS = 64, kResBK = 16, kResSub = 8, kResMargin = 6;
+static_assert(kResBK % kResSub == 0 && kResSub == 8, "the maxima of a run are reduced over 8 lanes");
+static_assert((1 << kResMargin) >= 2 * (2 * kResSub + 1) + 2, "offset too small for exact differences");
+
+// max(|v.x|, |v.y|) over the 8 lanes that hold one run of one row (or column) of the staged tile
+__device__ __forceinline__ float run_max8(float2 v) {
+  float m = fmaxf(fabsf(v.x), fabsf(v.y));
+  m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 1));
+  m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 2));
+  m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 4));
+  return m;
+}
+
+// power of two sigma >= 2^kResMargin * M (M < 2^e  ->  sigma = 2^(e + kResMargin)), capped at 2^127
+__device__ __forceinline__ float offset_of(float m) {
+  const unsigned e = __float_as_uint(m) & 0x7f800000u;
+  return __uint_as_float(min(e + ((unsigned)(kResMargin + 1) << 23), 0x7f000000u));
+}
+
+__device__ __forceinline__ void offset_acc(float a, float b, float& acc, float& c) {
+  const float t = fmaf(a, b, acc);
+  const float d = t - acc;
+  c += fmaf(a, b, -d);
+  acc = t;
+}
+
 __global__ void __launch_bounds__(256) k_resid_df_gemm(const float2* __restrict__ Ah, const float2* __restrict__ Al,
                                                         size_t lda, int n, int nrhs, const float2* __restrict__ xh,
                                                         const float2* __restrict__ xl, const double2* __restrict__ b,
                                                         double2* __restrict__ r, int kchunk,
                                                         double2* __restrict__ part) {
-  constexpr int BR = kResBR, BS = kResBS, BK = kResBK;
+  constexpr int BR = kResBR, BS = kResBS, BK = kResBK, NSUB = kResBK / kResSub;
   const int kbeg = blockIdx.z * kchunk, kend = min(n, kbeg + kchunk);
   __shared__ float2 Ash[BK][BR + 1], Asl[BK][BR + 1];
   __shared__ float2 Xsh[BK][BS + 1], Xsl[BK][BS + 1];
+  __shared__ float Amax[NSUB][BR], Xmax[NSUB][BS];
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
   const int r0 = blockIdx.x * BR, s0 = blockIdx.y * BS;
-  float sr[2][4], cr[2][4], si[2][4], ci[2][4];
+  // double-float totals (S, L) of the real and imaginary parts
+  float Sr[2][4], Lr[2][4], Si[2][4], Li[2][4];
 #pragma unroll
   for (int a = 0; a < 2; ++a)
 #pragma unroll
-    for (int q = 0; q < 4; ++q) sr[a][q] = cr[a][q] = si[a][q] = ci[a][q] = 0.f;
+    for (int q = 0; q < 4; ++q) Sr[a][q] = Lr[a][q] = Si[a][q] = Li[a][q] = 0.f;
   const float2 z = make_float2(0.f, 0.f);
   for (int k0 = kbeg; k0 < kend; k0 += BK) {
-    // A: 32 x 16 = 512 entries (2 per thread); X: 64 x 16 = 1024 entries (4 per thread)
+    // A: 32 x 16 = 512 entries (2 per thread); X: 64 x 16 = 1024 entries (4 per thread).  The 16 lanes
+    // of a half-warp hold one row (column) of the tile; each run of 8 lanes is one offset run.
 #pragma unroll
     for (int t = 0; t < 2; ++t) {
       const int e = tid + t * 256;
       const int rr = e >> 4, kk = e & 15;
       const int gr = r0 + rr, gk = k0 + kk;
       const bool in = gr < n && gk < kend;
-      Ash[kk][rr] = in ? __ldcs(Ah + (size_t)gr * lda + gk) : z;
+      const float2 vh = in ? __ldcs(Ah + (size_t)gr * lda + gk) : z;
+      Ash[kk][rr] = vh;
       Asl[kk][rr] = in ? __ldcs(Al + (size_t)gr * lda + gk) : z;
+      const float m = run_max8(vh);
+      if ((kk & (kResSub - 1)) == 0) Amax[kk / kResSub][rr] = m;
     }
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
@@ -410,21 +461,57 @@ __global__ void __launch_bounds__(256) k_resid_df_gemm(const float2* __restrict_
       const int ss = e >> 4, kk = e & 15;
       const int gs = s0 + ss, gk = k0 + kk;
       const bool in = gs < nrhs && gk < kend;
-      Xsh[kk][ss] = in ? xh[(size_t)gs * n + gk] : z;
+      const float2 vh = in ? xh[(size_t)gs * n + gk] : z;
+      Xsh[kk][ss] = vh;
       Xsl[kk][ss] = in ? xl[(size_t)gs * n + gk] : z;
+      const float m = run_max8(vh);
+      if ((kk & (kResSub - 1)) == 0) Xmax[kk / kResSub][ss] = m;
     }
     __syncthreads();
-#pragma unroll 4
-    for (int kk = 0; kk < BK; ++kk) {
-      float2 ah[2], al[2], vh[4], vl[4];
 #pragma unroll
-      for (int a = 0; a < 2; ++a) { ah[a] = Ash[kk][ty + 16 * a]; al[a] = Asl[kk][ty + 16 * a]; }
-#pragma unroll
-      for (int q = 0; q < 4; ++q) { vh[q] = Xsh[kk][tx + 16 * q]; vl[q] = Xsl[kk][tx + 16 * q]; }
+    for (int sub = 0; sub < NSUB; ++sub) {
+      float sg[2][4], ar[2][4], ai[2][4], cr[2][4], ci[2][4];
 #pragma unroll
       for (int a = 0; a < 2; ++a)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) cmac_df(ah[a], al[a], vh[q], vl[q], sr[a][q], cr[a][q], si[a][q], ci[a][q]);
+        for (int q = 0; q < 4; ++q) {
+          sg[a][q] = offset_of(Amax[sub][ty + 16 * a] * Xmax[sub][tx + 16 * q]);
+          ar[a][q] = ai[a][q] = sg[a][q];
+          cr[a][q] = ci[a][q] = 0.f;
+        }
+#pragma unroll 2
+      for (int kk = sub * kResSub; kk < (sub + 1) * kResSub; ++kk) {
+        float2 ah[2], al[2], vh[4], vl[4];
+#pragma unroll
+        for (int a = 0; a < 2; ++a) { ah[a] = Ash[kk][ty + 16 * a]; al[a] = Asl[kk][ty + 16 * a]; }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) { vh[q] = Xsh[kk][tx + 16 * q]; vl[q] = Xsl[kk][tx + 16 * q]; }
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            offset_acc(ah[a].x, vh[q].x, ar[a][q], cr[a][q]);
+            offset_acc(-ah[a].y, vh[q].y, ar[a][q], cr[a][q]);
+            offset_acc(ah[a].x, vh[q].y, ai[a][q], ci[a][q]);
+            offset_acc(ah[a].y, vh[q].x, ai[a][q], ci[a][q]);
+            float& c1 = cr[a][q];
+            float& c2 = ci[a][q];
+            c1 = fmaf(ah[a].x, vl[q].x, c1); c1 = fmaf(-ah[a].y, vl[q].y, c1);
+            c1 = fmaf(al[a].x, vh[q].x, c1); c1 = fmaf(-al[a].y, vh[q].y, c1);
+            c2 = fmaf(ah[a].x, vl[q].y, c2); c2 = fmaf(ah[a].y, vl[q].x, c2);
+            c2 = fmaf(al[a].x, vh[q].y, c2); c2 = fmaf(al[a].y, vh[q].x, c2);
+          }
+      }
+#pragma unroll
+      for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          float e;
+          two_sum(Sr[a][q], ar[a][q] - sg[a][q], Sr[a][q], e);
+          Lr[a][q] += e + cr[a][q];
+          two_sum(Si[a][q], ai[a][q] - sg[a][q], Si[a][q], e);
+          Li[a][q] += e + ci[a][q];
+        }
     }
     __syncthreads();
   }
@@ -434,7 +521,7 @@ __global__ void __launch_bounds__(256) k_resid_df_gemm(const float2* __restrict_
     for (int q = 0; q < 4; ++q) {
       const int gr = r0 + ty + 16 * a, gs = s0 + tx + 16 * q;
       if (gr < n && gs < nrhs) {
-        const double2 ax = make_double2((double)sr[a][q] + (double)cr[a][q], (double)si[a][q] + (double)ci[a][q]);
+        const double2 ax = make_double2((double)Sr[a][q] + (double)Lr[a][q], (double)Si[a][q] + (double)Li[a][q]);
         if (part) {
           part[((size_t)blockIdx.z * nrhs + gs) * n + gr] = ax;
         } else {

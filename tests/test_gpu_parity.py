@@ -254,26 +254,39 @@ def test_solve_mixed_tensor_core_matches_oracle_lu(B, torch):
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 @pytest.mark.parametrize("nrhs", [1, 5])
 def test_residual_matches_oracle(B, torch, prec, nrhs):
-    """r = b - A x through the C-ABI against the oracle's FP64 matrix: for random x (no cancellation) and
-    for the LU solution (residual dominated by cancellation, where the double-float sum matters)."""
+    """r = b - A x through the C-ABI against the oracle's FP64 matrix: for random x (no cancellation), for
+    the LU solution (residual dominated by cancellation, where the double-float sum matters), for that
+    solution scaled by 2^70, for x spread over 30 decades, and for x = 0 (r must be b exactly)."""
     wp = W.Problem(k=[20.0, 30.0], eps=[1.0, 2.25], segments=[W.Segment(W.star(300, 0.3, 5), P=0, M=1, closed=True)])
     A = O.assemble(wp, Q=4)
     n2 = A.shape[0]
     rng = np.random.default_rng(5)
     b = np.stack([O.rhs_planewave(wp, t) for t in np.linspace(0, 3, nrhs)])
-    for kind in ("random", "solution"):
+    for kind in ("random", "solution", "scaled", "spread", "zero"):
+        bk = b
         if kind == "random":
             x = rng.normal(size=(nrhs, n2)) + 1j * rng.normal(size=(nrhs, n2))
-        else:
+        elif kind == "solution":
             x = np.ascontiguousarray(np.linalg.solve(A, b.T).T)
-        ref = b - (A @ x.T).T
+        elif kind == "scaled":          # far from unit magnitude: the offsets follow the data's exponents
+            x = np.ascontiguousarray(np.linalg.solve(A, b.T).T) * 2.0 ** 70
+            bk = b * 2.0 ** 70
+        elif kind == "spread":          # entries spread over 30 decades
+            x = (rng.normal(size=(nrhs, n2)) + 1j * rng.normal(size=(nrhs, n2))) * 10.0 ** rng.uniform(-20, 10, (nrhs, n2))
+        else:
+            x = np.zeros((nrhs, n2), complex)
+        ref = bk - (A @ x.T).T
         scale = np.max(np.abs(A)) * np.max(np.abs(x)) * np.sqrt(n2)
         p = B.Problem.from_workload(wp, prec=prec)
         xd = torch.as_tensor(x, device="cuda")
-        bd = torch.as_tensor(b, device="cuda")
+        bd = torch.as_tensor(bk, device="cuda")
         rd = torch.empty_like(bd)
         p.bem_residual(xd, bd, rd, n_rhs=nrhs)
         got = rd.cpu().numpy()
+        if kind == "zero":
+            assert np.array_equal(got, bk)
+            p.close()
+            continue
         # the two matrices agree to ~1e-13 per entry; an FP32 residual would miss by ~1e-7
         assert np.max(np.abs(got - ref)) <= 1e-12 * scale, (kind, np.max(np.abs(got - ref)) / scale)
         p.close()
