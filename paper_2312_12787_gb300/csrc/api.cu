@@ -321,6 +321,7 @@ size_t krylov_bytes(int n2, int nrhs, int m, bool fp32) {
   add((size_t)nrhs * 8);                  // tolv
   add(4);                                 // n_active
   add(4);                                 // jdev
+  add(4);                                 // arrive_all
   // mixed extras: residual r (FP64), rhs copy of the inner solve (FP32 not needed), tc workspace
   add((size_t)nrhs * n2 * 16);
   add(matvec_tc_workspace_bytes(n2, nrhs));
@@ -378,6 +379,7 @@ Solver carve_solver(bem_problem* p, int nrhs, bool fp32) {
   st.tolv = c.take<double>(nrhs);
   st.n_active = c.take<int>(1);
   st.jdev = c.take<int>(1);
+  st.arrive_all = c.take<int>(1);
   sv.r = c.take<double2>((size_t)nrhs * n2);
   sv.tcws_bytes = matvec_tc_workspace_bytes(n2, nrhs);
   sv.tcws = c.take<char>(sv.tcws_bytes);

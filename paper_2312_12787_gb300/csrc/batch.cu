@@ -250,10 +250,11 @@ __global__ void __launch_bounds__(32) kv_finish(VDev d) {
   for (int i = lane; i < j; i += 32) Hj[i] = sh_h[i];
   if (lane != 0) return;
   const double hn = sqrt(t);
-  const double den = hypot(hypot(a.x, a.y), hn);
+  double den, inv;
+  givens_norm(a, hn, den, inv);
   double2 c, sv;
   if (den == 0.0) { c = make_double2(1, 0); sv = make_double2(0, 0); }
-  else { c = cscale(a, 1.0 / den); sv = make_double2(hn / den, 0.0); }
+  else { c = cscale(a, inv); sv = make_double2(hn * inv, 0.0); }
   cs[j] = c;
   sn[j] = sv;
   Hj[j] = make_double2(den, 0.0);
@@ -262,7 +263,7 @@ __global__ void __launch_bounds__(32) kv_finish(VDev d) {
   const double2 gj = g[j];
   g[j + 1] = make_double2(-(sv.x * gj.x - sv.y * gj.y), -(sv.x * gj.y + sv.y * gj.x));
   g[j] = cdotc(c, gj);
-  const double res = hypot(g[j + 1].x, g[j + 1].y) / d.beta[s];
+  const double res = d.resid[s] * sv.x;   // |g_{j+1}| = |s_j| |g_j| (resid starts at 1)
   d.resid[s] = res;
   d.iters[s] = j + 1;
   d.hnext[s] = hn;

@@ -183,6 +183,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap mapAh, const __grid_constant__ CUtensorMap mapAl,
               const __grid_constant__ CUtensorMap mapBh, const __grid_constant__ CUtensorMap mapBl, int n,
               int kpt, long long total, float* partial, int* err, const int* gate) {
+  pdl_enter();
   if (gate && *gate == 0) return;   // every system of the block has converged (uniform for the grid)
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -416,6 +417,7 @@ __global__ void __launch_bounds__(256) k_tc_reduce(const float* __restrict__ par
                                                    long long total, int G, const float* __restrict__ rsc,
                                                    const float* __restrict__ tsc, float2* __restrict__ y,
                                                    const int* gate) {
+  pdl_enter();
   if (gate && *gate == 0) return;
   constexpr int kMaxCover = 64;
   __shared__ float2 tile[kMaxRhs][kRedRows + 1];
@@ -602,10 +604,11 @@ cudaError_t launch_matvec_tc(const void* a16, int n, int nrhs, const float2* x, 
     k_tc_colmax<<<dim3(8, nrhs), 256, 0, s>>>(x, n, nrhs, cmax, gate);
     k_tc_prep_b<<<dim3((n + 255) / 256, kMaxRhs), 256, 0, s>>>(x, n, nrhs, cmax, bhi, blo, ld, tsc, gate);
   }
-  k_gemm_tc<<<G, kThreads, kSmemBytes, s>>>(mAh, mAl, mBh, mBl, n, kpt, total, part, err, gate);
-  k_tc_reduce<<<(n + kRedRows - 1) / kRedRows, 256, 0, s>>>(part, n, nrhs, kpt, total, G, rsc, x ? tsc : nullptr, y,
-                                                             gate);
-  return cudaGetLastError();
+  cudaError_t e = launch_pdl(k_gemm_tc, dim3(G), dim3(kThreads), kSmemBytes, s, mAh, mAl, mBh, mBl, n, kpt, total,
+                             part, err, gate);
+  if (e != cudaSuccess) return e;
+  return launch_pdl(k_tc_reduce, dim3((n + kRedRows - 1) / kRedRows), dim3(256), 0, s, part, n, nrhs, kpt, total, G,
+                    rsc, x ? tsc : static_cast<const float*>(nullptr), y, gate);
 }
 
 void matvec_tc_b_operand(void* ws, int n, void** bhi, void** blo, size_t* ldb) {

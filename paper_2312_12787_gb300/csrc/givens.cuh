@@ -61,6 +61,21 @@ __device__ __forceinline__ double2 warp_rotate_column(double2* h, const double2*
   return shfl2(a, (j - 1) / seg);
 }
 
+// den = sqrt(|a|^2 + hn^2) and inv = 1 / den for a new Givens rotation, by one reciprocal square root
+// (FP64 division and hypot are long instruction sequences on GB300's narrow FP64 pipe, and this runs once
+// per system and iteration on the critical path); hypot only where the sum of squares would leave the
+// normal range.  inv = 0 when den = 0.
+__device__ __forceinline__ void givens_norm(double2 a, double hn, double& den, double& inv) {
+  const double q = fma(a.x, a.x, fma(a.y, a.y, hn * hn));
+  if (q > 1e-280 && q < 1e280) {
+    inv = rsqrt(q);
+    den = q * inv;
+  } else {
+    den = hypot(hypot(a.x, a.y), hn);
+    inv = den > 0.0 ? 1.0 / den : 0.0;
+  }
+}
+
 // Back substitution R y = g for the mm x mm upper-triangular R (column i at R + i*ld, rows 0..i), by a whole
 // CTA of kBsThreads threads: column-oriented, y_i = g_i / R_ii and then g_k -= R_ki y_i for every k < i in
 // parallel, with the next column prefetched into registers while the current one is applied.

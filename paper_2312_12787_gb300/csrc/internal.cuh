@@ -10,6 +10,32 @@
 
 namespace bem {
 
+// Programmatic dependent launch for the kernels of one GMRES iteration: launch_pdl lets the next kernel of
+// the stream be scheduled while its predecessor drains, and the kernel's first statement, pdl_enter(),
+// waits until the predecessor has completed and its writes are visible, then lets its own successor be
+// scheduled.  So at most two grids are resident at a time, each reads its inputs only after they are
+// complete, and the launch latency of each kernel overlaps the tail of the one before (in stream order
+// and in the recorded CUDA graph alike).  Without the launch attribute the two instructions do nothing.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 constexpr int kMaxDomains = 64;
 constexpr int kMaxQuad = 16;
 
@@ -165,6 +191,7 @@ struct KrylovState {
   const double* tolv;  // nrhs per-system tolerances (overrides the scalar tol when non-null)
   int* n_active;    // device count of active systems (the gate of queued iterations)
   int* jdev;        // current iteration index (set by the start kernel, advanced after each iteration)
+  int* arrive_all;  // systems whose end-of-iteration CTAs are all done (the last one advances jdev)
   // when non-null (FP32 basis feeding the tensor-core product): every new basis vector is also written as
   // the FP16 x 3 operand of the next product (tc_operand.cuh), rows of stride ldb16
   void* b16hi;

@@ -93,7 +93,10 @@ __global__ void k_start_finish(KrylovState st, int nblk) {
   if (beta > 0.0) atomicAdd(st.n_active, 1);   // zeroed by the launcher
   st.arrive[s] = 0;
   st.reo[s] = 0;
-  if (s == 0) *st.jdev = 0;
+  if (s == 0) {
+    *st.jdev = 0;
+    *st.arrive_all = 0;
+  }
 }
 
 template <typename T>
@@ -140,6 +143,7 @@ template <> struct Pair<double2> {
 // mode 2: unconditional second pass.
 template <typename T, int CH>
 __global__ void __launch_bounds__(kThreads) k_dots(KrylovState st, int nchunk, int mode) {
+  pdl_enter();
   using F = typename Vec<T>::acc_t;
   constexpr int P = CH / 64;
   const int c = blockIdx.x, s = blockIdx.y;
@@ -189,6 +193,7 @@ __global__ void __launch_bounds__(kThreads) k_dots(KrylovState st, int nchunk, i
 // h_i = sum over chunks (FP64), one warp per (system, i); accumulate into column j of H (pass 0 sets,
 // later passes add).  grid = (ceil((m+1)/8), systems), 8 warps per block.
 __global__ void k_dots_reduce(KrylovState st, int nchunk, int pass, int cond) {
+  pdl_enter();
   const int s = blockIdx.y;
   if (!st.active[s] || (cond && !st.reo[s])) return;
   const int j = *st.jdev;
@@ -217,7 +222,8 @@ constexpr int kHsMax = 1001;
 // With fused != 0 every CTA also sums the chunk partials of the projections itself (FP64, chunk order) and
 // CTA 0 records them in column j of H (pass 0 sets, later passes add); otherwise k_dots_reduce did that.
 template <typename T, int CH>
-__global__ void __launch_bounds__(CH / 2) k_update(KrylovState st, int nchunk, int pass, int fused, int cond) {
+__global__ void __launch_bounds__(CH / 2, sizeof(T) == sizeof(float2) ? 8 : 1) k_update(KrylovState st, int nchunk, int pass, int fused, int cond) {
+  pdl_enter();
   using F = typename Vec<T>::acc_t;
   __shared__ F hs[2 * kHsMax];
   __shared__ double red[CH / 64];
@@ -290,19 +296,20 @@ __global__ void __launch_bounds__(CH / 2) k_update(KrylovState st, int nchunk, i
   }
 }
 
-// h_{j+1,j} = ||w||; apply the previous Givens rotations to column j, form the new one, update g and
-// the residual estimate |g_{j+1}| / beta.  One warp per system: the lanes reduce the chunk norms, stage the
-// column and the rotations in shared memory and apply the rotations as a scan (warp_rotate_column); lane 0
-// then forms the new rotation.
+// End of iteration j, one kernel (grid = blocks of kThreads entries x systems):
+//  * every CTA forms ||w|| = h_{j+1,j} from the update kernel's chunk sums and scales its entries of w into
+//    V_{j+1} (and into the FP16 x 3 operand of the next tensor-core product);
+//  * the first warp of CTA 0 of each system applies the previous Givens rotations to column j of H, forms
+//    the new rotation and updates g and the residual estimate |g_{j+1}| / beta (finish_column);
+//  * the last CTA to finish advances the iteration index (all CTAs have read it by then).
+// A system that converges at this step still gets V_{j+1}; nothing reads it.
 constexpr int kFinishMaxM = 1000;
-__global__ void __launch_bounds__(32) k_finish(KrylovState st, int nchunk, double tol) {
-  __shared__ double2 sh_h[kFinishMaxM + 1], sh_c[kFinishMaxM], sh_s[kFinishMaxM];
-  const int s = blockIdx.x, lane = threadIdx.x;
-  if (s >= st.nrhs || !st.active[s]) return;
-  const int j = *st.jdev;
-  double t = 0.0;
-  for (int c = lane; c < nchunk; c += 32) t += st.npart[(size_t)s * nchunk + c];
-  t = warp_sum(t);
+
+// One warp: h_{j+1,j} = hn.  The lanes stage column j and the rotations in shared memory and apply the
+// rotations as a scan (warp_rotate_column); lane 0 then forms the new rotation.
+__device__ __forceinline__ void finish_column(const KrylovState& st, int s, int j, double hn, double tol,
+                                              double2* sh_h, double2* sh_c, double2* sh_s) {
+  const int lane = threadIdx.x & 31;
   double2* Hj = st.H + ((size_t)s * st.m + j) * (st.m + 1);
   double2* cs = st.cs + (size_t)s * st.m;
   double2* sn = st.sn + (size_t)s * st.m;
@@ -314,11 +321,11 @@ __global__ void __launch_bounds__(32) k_finish(KrylovState st, int nchunk, doubl
   const double2 a = warp_rotate_column(sh_h, sh_c, sh_s, j);
   for (int i = lane; i < j; i += 32) Hj[i] = sh_h[i];
   if (lane != 0) return;
-  const double hn = sqrt(t);
-  const double den = hypot(hypot(a.x, a.y), hn);
+  double den, inv;
+  givens_norm(a, hn, den, inv);
   double2 c, sv;
   if (den == 0.0) { c = make_double2(1, 0); sv = make_double2(0, 0); }
-  else { c = cscale(a, 1.0 / den); sv = make_double2(hn / den, 0.0); }
+  else { c = cscale(a, inv); sv = make_double2(hn * inv, 0.0); }
   cs[j] = c;
   sn[j] = sv;
   Hj[j] = make_double2(den, 0.0);
@@ -327,7 +334,8 @@ __global__ void __launch_bounds__(32) k_finish(KrylovState st, int nchunk, doubl
   const double2 gj = g[j];
   g[j + 1] = make_double2(-(sv.x * gj.x - sv.y * gj.y), -(sv.x * gj.y + sv.y * gj.x));
   g[j] = cdotc(c, gj);
-  const double res = hypot(g[j + 1].x, g[j + 1].y) / st.beta[s];
+  // |g_{j+1}| = |s_j| |g_j|: the estimate shrinks by the rotation's sine (resid starts at 1)
+  const double res = st.resid[s] * sv.x;
   st.resid[s] = res;
   st.iters[s] = j + 1;
   st.hnext[s] = hn;
@@ -338,27 +346,56 @@ __global__ void __launch_bounds__(32) k_finish(KrylovState st, int nchunk, doubl
   }
 }
 
+// dynamic shared memory: 3 (m + 1) double2 (column and rotations for finish_column)
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_scale_next(KrylovState st) {
+__global__ void __launch_bounds__(kThreads) k_step_end(KrylovState st, int nchunk, double tol) {
+  pdl_enter();
   using F = typename Vec<T>::acc_t;
-  const int k = blockIdx.x * kThreads + threadIdx.x, s = blockIdx.y;
-  if (!st.active[s] || k >= st.n) return;
+  extern __shared__ double2 fin_sh[];
+  __shared__ double s_hn;
+  __shared__ F s_inv;
+  const int c = blockIdx.x, s = blockIdx.y;
   const int j = *st.jdev;
-  const T* W = static_cast<const T*>(st.W) + (size_t)s * st.n;
-  T* Vn = static_cast<T*>(st.V) + ((size_t)(j + 1) * st.nrhs + s) * st.n;
-  const F inv = (F)1 / (F)st.hnext[s];   // in the basis precision (an FP64 division per entry is costly)
-  T w = W[k];
-  w.x *= inv;
-  w.y *= inv;
-  Vn[k] = w;
-  if (st.b16hi)
-    tc_write_b(static_cast<__half*>(st.b16hi), static_cast<__half*>(st.b16lo), st.ldb16, s, k, (float)w.x, (float)w.y);
-}
-
-// The iteration index lives on the device, so one recorded sequence of launches serves every iteration (the
-// tensor-core path replays it as a CUDA graph).
-__global__ void k_advance(KrylovState st) {
-  if (threadIdx.x == 0) *st.jdev += 1;
+  if (st.active[s]) {
+    if (threadIdx.x < 32) {
+      double t = 0.0;
+      for (int cc = threadIdx.x; cc < nchunk; cc += 32) t += st.npart[(size_t)s * nchunk + cc];
+      t = warp_sum(t);
+      if (threadIdx.x == 0) {
+        s_hn = sqrt(t);
+        s_inv = (F)1 / (F)s_hn;   // in the basis precision (one division per CTA)
+      }
+    }
+    __syncthreads();
+    const double hn = s_hn;
+    // the rotations are the long dependent chain of this kernel: start them before the scaling
+    if (c == 0 && threadIdx.x < 32)
+      finish_column(st, s, j, hn, tol, fin_sh, fin_sh + (st.m + 1), fin_sh + 2 * (st.m + 1));
+    const int k = c * kThreads + threadIdx.x;
+    if (k < st.n && hn > 0.0 && j + 1 < st.m) {
+      const T* W = static_cast<const T*>(st.W) + (size_t)s * st.n;
+      T* Vn = static_cast<T*>(st.V) + ((size_t)(j + 1) * st.nrhs + s) * st.n;
+      const F inv = s_inv;
+      T w = W[k];
+      w.x *= inv;
+      w.y *= inv;
+      Vn[k] = w;
+      if (st.b16hi)
+        tc_write_b(static_cast<__half*>(st.b16hi), static_cast<__half*>(st.b16lo), st.ldb16, s, k, (float)w.x,
+                   (float)w.y);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();   // this CTA's reads of the iteration index precede the advance
+    if (atomicAdd(st.arrive + s, 1) == (int)gridDim.x - 1) {
+      st.arrive[s] = 0;
+      if (atomicAdd(st.arrive_all, 1) == (int)gridDim.y - 1) {
+        *st.arrive_all = 0;
+        *st.jdev = j + 1;
+      }
+    }
+  }
 }
 
 // Least squares: back substitution of the triangularised Hessenberg system, one CTA per system.
@@ -435,9 +472,9 @@ void orth_pass(const KrylovState& st, int pass, int mode, cudaStream_t s) {
   dim3 grd(nc, st.nrhs);
   const int fused = nc <= 32;   // few chunks: each update CTA sums the partials itself (one launch less)
   const int cond = mode == 1;
-  k_dots<T, CH><<<grd, kThreads, 0, s>>>(st, nc, mode);
-  if (!fused) k_dots_reduce<<<dim3((st.m + 8) / 8, st.nrhs), 256, 0, s>>>(st, nc, pass, cond);
-  k_update<T, CH><<<grd, CH / 2, 0, s>>>(st, nc, pass, fused, cond);
+  launch_pdl(k_dots<T, CH>, grd, dim3(kThreads), 0, s, st, nc, mode);
+  if (!fused) launch_pdl(k_dots_reduce, dim3((st.m + 8) / 8, st.nrhs), dim3(256), 0, s, st, nc, pass, cond);
+  launch_pdl(k_update<T, CH>, grd, dim3(CH / 2), 0, s, st, nc, pass, fused, cond);
 }
 
 template <typename T>
@@ -474,10 +511,8 @@ template <typename T>
 cudaError_t finish_t(const KrylovState& st, double tol, cudaStream_t s) {
   const int ch = chunk_of(st.n, st.nrhs);
   const int nc = (st.n + ch - 1) / ch;   // the update kernel's chunks (its squared norms)
-  k_finish<<<st.nrhs, 32, 0, s>>>(st, nc, tol);
-  k_scale_next<T><<<dim3(nblk_of(st.n), st.nrhs), kThreads, 0, s>>>(st);
-  k_advance<<<1, 32, 0, s>>>(st);
-  return cudaGetLastError();
+  return launch_pdl(k_step_end<T>, dim3(nblk_of(st.n), st.nrhs), dim3(kThreads), 3 * (st.m + 1) * sizeof(double2), s,
+                    st, nc, tol);
 }
 
 template <typename T>
