@@ -206,6 +206,7 @@ __global__ void __launch_bounds__(256) kv_update(VDev d, int pass, int cond) {
   nrm = wsum(nrm);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = nrm;
   __syncthreads();
+  __shared__ int s_last;
   if (threadIdx.x == 0) {
     double t = 0.0;
     for (int w8 = 0; w8 < 8; ++w8) t += red[w8];
@@ -213,18 +214,25 @@ __global__ void __launch_bounds__(256) kv_update(VDev d, int pass, int cond) {
     if (pass == 0) {
       // the slot's last CTA to finish takes the decision for the conditional second pass (see kv_dots)
       __threadfence();
-      if (atomicAdd(d.arrive + s, 1) == d.ccnt[s] - 1) {
-        __threadfence();
-        double before = 0.0, after = 0.0;
-        const int c0 = d.cbeg[s], cn = d.ccnt[s];
-        for (int cc = 0; cc < cn; ++cc) {
-          before += ((volatile double*)d.wpart)[c0 + cc];
-          after += ((volatile double*)d.npart)[c0 + cc];
-        }
-        d.reo[s] = after < 0.01 * before;   // ||w_after|| < ||w_before|| / 10
-        d.arrive[s] = 0;
-      }
+      s_last = atomicAdd(d.arrive + s, 1) == d.ccnt[s] - 1;
     }
+  }
+  if (pass != 0) return;
+  __syncthreads();
+  if (!s_last || threadIdx.x >= 32) return;
+  __threadfence();
+  // one warp loads the chunk sums in parallel (L2, bypassing L1) and reduces them
+  double before = 0.0, after = 0.0;
+  const int c0 = d.cbeg[s], cn = d.ccnt[s];
+  for (int cc = threadIdx.x; cc < cn; cc += 32) {
+    before += __ldcg(d.wpart + c0 + cc);
+    after += __ldcg(d.npart + c0 + cc);
+  }
+  before = wsum(before);
+  after = wsum(after);
+  if (threadIdx.x == 0) {
+    d.reo[s] = after < 0.01 * before;   // ||w_after|| < ||w_before|| / 10
+    d.arrive[s] = 0;
   }
 }
 

@@ -426,15 +426,29 @@ __global__ void __launch_bounds__(256) k_tc_reduce(const float* __restrict__ par
   const int r0 = blockIdx.x * kRedRows;
   const int t = r0 / kM;
   if (threadIdx.x == 0) {
-    // CTAs whose range [total c / G, total (c+1) / G) meets row tile t's K-steps [t kpt, (t+1) kpt)
-    const long long lo = (long long)t * kpt, hi = lo + kpt;
-    int c0 = (int)((lo * G) / total);
-    while (c0 > 0 && total * c0 / G > lo) --c0;
-    while (total * (c0 + 1) / G <= lo) ++c0;
+    // CTAs whose range [total c / G, total (c+1) / G) meets row tile t's K-steps [t kpt, (t+1) kpt).  32-bit
+    // unsigned divisions where total G fits (every practical size): 64-bit divisions are long sequences.
     int m = 0;
-    for (int c = c0; c < G && total * c / G < hi && m < kMaxCover; ++c) {
-      const int slot = ((total * c / G) / kpt == t) ? 0 : 1;
-      src[m++] = partial + ((size_t)c * 2 + slot) * kM * kN;
+    if ((unsigned long long)total * (unsigned long long)G < (1ull << 32)) {
+      const unsigned tot = (unsigned)total, g = (unsigned)G, lo = (unsigned)t * (unsigned)kpt, hi = lo + (unsigned)kpt;
+      unsigned c0 = (lo * g) / tot;
+      while (c0 > 0 && tot * c0 / g > lo) --c0;
+      while (tot * (c0 + 1) / g <= lo) ++c0;
+      for (unsigned c = c0; c < g && m < kMaxCover; ++c) {
+        const unsigned beg = tot * c / g;
+        if (beg >= hi) break;
+        const int slot = (beg / (unsigned)kpt == (unsigned)t) ? 0 : 1;
+        src[m++] = partial + ((size_t)c * 2 + slot) * kM * kN;
+      }
+    } else {
+      const long long lo = (long long)t * kpt, hi = lo + kpt;
+      int c0 = (int)((lo * G) / total);
+      while (c0 > 0 && total * c0 / G > lo) --c0;
+      while (total * (c0 + 1) / G <= lo) ++c0;
+      for (int c = c0; c < G && total * c / G < hi && m < kMaxCover; ++c) {
+        const int slot = ((total * c / G) / kpt == t) ? 0 : 1;
+        src[m++] = partial + ((size_t)c * 2 + slot) * kM * kN;
+      }
     }
     nsrc = m;
   }

@@ -1,6 +1,8 @@
 // Small dense steps of GMRES (Sec. 3.2, no restart): the Givens rotations that triangularise each new
 // Hessenberg column, and the back substitution for the least-squares coefficients.  Shared by the
-// single-problem solver (krylov.cu) and the batched engine (batch.cu).  All arithmetic is FP64.
+// single-problem solver (krylov.cu) and the batched engine (batch.cu).  The rotations run in FP64, or in
+// FP32 for the inner solves on an FP32 basis (complex type C = double2 or float2); the back substitution
+// is FP64.
 #pragma once
 
 #include "internal.cuh"
@@ -13,6 +15,15 @@ __device__ __forceinline__ double2 shfl_up2(double2 v, int off) {
 __device__ __forceinline__ double2 shfl2(double2 v, int lane) {
   return make_double2(__shfl_sync(0xffffffffu, v.x, lane), __shfl_sync(0xffffffffu, v.y, lane));
 }
+__device__ __forceinline__ float2 shfl_up2(float2 v, int off) {
+  return make_float2(__shfl_up_sync(0xffffffffu, v.x, off), __shfl_up_sync(0xffffffffu, v.y, off));
+}
+__device__ __forceinline__ float2 shfl2(float2 v, int lane) {
+  return make_float2(__shfl_sync(0xffffffffu, v.x, lane), __shfl_sync(0xffffffffu, v.y, lane));
+}
+template <typename C> __device__ __forceinline__ C cx(double x, double y);
+template <> __device__ __forceinline__ double2 cx<double2>(double x, double y) { return make_double2(x, y); }
+template <> __device__ __forceinline__ float2 cx<float2>(double x, double y) { return make_float2((float)x, (float)y); }
 
 // Apply rotations 0..j-1 to the Hessenberg column h[0..j] (shared memory; rotation i acts on rows (i, i+1)
 // as [[conj c_i, conj s_i], [-s_i, c_i]]).  Called by all 32 lanes of one warp.
@@ -24,36 +35,37 @@ __device__ __forceinline__ double2 shfl2(double2 v, int lane) {
 // runs, and each lane then walks its own run from its entry value.  That is ceil(j/32) + 5 + ceil(j/32)
 // dependent steps instead of j (|s_i| <= 1, so the composed maps stay bounded).
 // On return h[0..j-1] hold the rotated entries and every lane has the rotated row j (the new pivot).
-__device__ __forceinline__ double2 warp_rotate_column(double2* h, const double2* c, const double2* s, int j) {
+template <typename C>
+__device__ __forceinline__ C warp_rotate_column(C* h, const C* c, const C* s, int j) {
   const int lane = threadIdx.x & 31;
-  const double2 h0 = h[0];
+  const C h0 = h[0];
   if (j == 0) return h0;
   const int seg = (j + 31) >> 5;
   const int lo = min(lane * seg, j), hi = min(lo + seg, j);
-  const double2 hb = h[hi];     // first entry of the next run: the next lane overwrites it during its walk
-  double2 P = make_double2(1.0, 0.0), Q = make_double2(0.0, 0.0);
+  const C hb = h[hi];     // first entry of the next run: the next lane overwrites it during its walk
+  C P = cx<C>(1.0, 0.0), Q = cx<C>(0.0, 0.0);
   for (int i = lo; i < hi; ++i) {
-    const double2 p = make_double2(-s[i].x, -s[i].y);
+    const C p = cx<C>(-s[i].x, -s[i].y);
     Q = cadd(cmul(p, Q), cmul(c[i], h[i + 1]));
     P = cmul(p, P);
   }
 #pragma unroll
   for (int off = 1; off < 32; off <<= 1) {
-    const double2 Pp = shfl_up2(P, off), Qp = shfl_up2(Q, off);
+    const C Pp = shfl_up2(P, off), Qp = shfl_up2(Q, off);
     if (lane >= off) {
       Q = cadd(cmul(P, Qp), Q);
       P = cmul(P, Pp);
     }
   }
-  double2 Pe = shfl_up2(P, 1), Qe = shfl_up2(Q, 1);
+  C Pe = shfl_up2(P, 1), Qe = shfl_up2(Q, 1);
   if (lane == 0) {
-    Pe = make_double2(1.0, 0.0);
-    Qe = make_double2(0.0, 0.0);
+    Pe = cx<C>(1.0, 0.0);
+    Qe = cx<C>(0.0, 0.0);
   }
-  double2 a = cadd(cmul(Pe, h0), Qe);
+  C a = cadd(cmul(Pe, h0), Qe);
   __syncwarp();
   for (int i = lo; i < hi; ++i) {
-    const double2 b = (i + 1 < hi) ? h[i + 1] : hb;
+    const C b = (i + 1 < hi) ? h[i + 1] : hb;
     h[i] = cadd(cdotc(c[i], a), cdotc(s[i], b));
     a = csub(cmul(c[i], b), cmul(s[i], a));
   }
@@ -73,6 +85,16 @@ __device__ __forceinline__ void givens_norm(double2 a, double hn, double& den, d
   } else {
     den = hypot(hypot(a.x, a.y), hn);
     inv = den > 0.0 ? 1.0 / den : 0.0;
+  }
+}
+__device__ __forceinline__ void givens_norm(float2 a, float hn, float& den, float& inv) {
+  const float q = fmaf(a.x, a.x, fmaf(a.y, a.y, hn * hn));
+  if (q > 1e-30f && q < 1e30f) {
+    inv = rsqrtf(q);
+    den = q * inv;
+  } else {
+    den = hypotf(hypotf(a.x, a.y), hn);
+    inv = den > 0.f ? 1.f / den : 0.f;
   }
 }
 

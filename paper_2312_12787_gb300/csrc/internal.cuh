@@ -91,6 +91,15 @@ __host__ __device__ __forceinline__ double2 cscale(double2 a, double s) { return
 __host__ __device__ __forceinline__ double2 cdotc(double2 a, double2 b) {
   return make_double2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
 }
+// the same for complex FP32
+__host__ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ float2 cdotc(float2 a, float2 b) {
+  return make_float2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
 
 // ---- launchers (each returns cudaGetLastError() of its launch) -----------------------------------
 cudaError_t launch_elements(const ElemDev& e, int n, cudaStream_t s);

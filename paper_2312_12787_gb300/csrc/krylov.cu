@@ -142,10 +142,12 @@ template <> struct Pair<double2> {
 //         the same iteration counts).  The first pass's update kernel records the decision in st.reo.
 // mode 2: unconditional second pass.
 template <typename T, int CH>
-__global__ void __launch_bounds__(kThreads) k_dots(KrylovState st, int nchunk, int mode) {
+__global__ void __launch_bounds__(kThreads, sizeof(T) == sizeof(float2) ? 8 : 1)
+    k_dots(KrylovState st, int nchunk, int mode) {
   pdl_enter();
   using F = typename Vec<T>::acc_t;
   constexpr int P = CH / 64;
+  __shared__ __align__(16) T ws[CH];   // the chunk of w, read by every warp
   const int c = blockIdx.x, s = blockIdx.y;
   if (!st.active[s]) return;
   const int j = *st.jdev;
@@ -154,34 +156,42 @@ __global__ void __launch_bounds__(kThreads) k_dots(KrylovState st, int nchunk, i
   const size_t stride = (size_t)st.nrhs * st.n;
   const T* W = static_cast<const T*>(st.W) + (size_t)s * st.n;
   const T* V = static_cast<const T*>(st.V) + (size_t)s * st.n;
-  T w[2 * P];
-#pragma unroll
-  for (int p = 0; p < P; ++p) {
-    const int k = c * CH + 2 * (32 * p + lane);
+  for (int q = threadIdx.x; q < CH / 2; q += kThreads) {
+    const int k = c * CH + 2 * q;
+    T a, b;
     if (k < st.n) {
-      Pair<T>::load(W + k, w[2 * p], w[2 * p + 1]);
+      Pair<T>::load(W + k, a, b);
     } else {
-      w[2 * p].x = w[2 * p].y = w[2 * p + 1].x = w[2 * p + 1].y = 0;
+      a.x = a.y = b.x = b.y = 0;
     }
+    Pair<T>::store(ws + 2 * q, a, b);
   }
+  __syncthreads();
   if (mode == 0 && warp == 0) {
     F nw = 0;
 #pragma unroll
-    for (int p = 0; p < 2 * P; ++p) nw += (F)w[p].x * (F)w[p].x + (F)w[p].y * (F)w[p].y;
+    for (int p = 0; p < P; ++p) {
+      T a, b;
+      Pair<T>::load(ws + 2 * (32 * p + lane), a, b);
+      nw += (F)a.x * (F)a.x + (F)a.y * (F)a.y + (F)b.x * (F)b.x + (F)b.y * (F)b.y;
+    }
     nw = warp_sum(nw);
     if (lane == 0) st.wpart[(size_t)s * nchunk + c] = (double)nw;
   }
   for (int i = warp; i <= j; i += kThreads / 32) {
     const T* vi = V + (size_t)i * stride;
     F px = 0, py = 0;
-#pragma unroll
+    constexpr int kU = P >= 8 ? 4 : 2;   // loads in flight per lane within the register budget
+#pragma unroll kU
     for (int p = 0; p < P; ++p) {
-      const int k = c * CH + 2 * (32 * p + lane);
+      const int q = 32 * p + lane;
+      const int k = c * CH + 2 * q;
       if (k < st.n) {
-        T a, b;
+        T a, b, w0, w1;
         Pair<T>::load(vi + k, a, b);
-        px += (F)a.x * (F)w[2 * p].x + (F)a.y * (F)w[2 * p].y + (F)b.x * (F)w[2 * p + 1].x + (F)b.y * (F)w[2 * p + 1].y;
-        py += (F)a.x * (F)w[2 * p].y - (F)a.y * (F)w[2 * p].x + (F)b.x * (F)w[2 * p + 1].y - (F)b.y * (F)w[2 * p + 1].x;
+        Pair<T>::load(ws + 2 * q, w0, w1);
+        px += (F)a.x * (F)w0.x + (F)a.y * (F)w0.y + (F)b.x * (F)w1.x + (F)b.y * (F)w1.y;
+        py += (F)a.x * (F)w0.y - (F)a.y * (F)w0.x + (F)b.x * (F)w1.y - (F)b.y * (F)w1.x;
       }
     }
     // the warp reduction in the basis precision too: FP64 adds run at 1/64 of the FP32 rate on GB300
@@ -234,6 +244,7 @@ __global__ void __launch_bounds__(CH / 2, sizeof(T) == sizeof(float2) ? 8 : 1) k
     double2 h;
     if (fused) {
       h = make_double2(0.0, 0.0);
+#pragma unroll 4
       for (int cc = 0; cc < nchunk; ++cc) h = cadd(h, st.part[((size_t)s * nchunk + cc) * (st.m + 1) + i]);
       if (c == 0) {
         st.hcol[(size_t)s * (st.m + 1) + i] = h;
@@ -274,6 +285,7 @@ __global__ void __launch_bounds__(CH / 2, sizeof(T) == sizeof(float2) ? 8 : 1) k
   nrm_f = warp_sum(nrm_f);   // basis precision within the warp, FP64 across warps and chunks
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = (double)nrm_f;
   __syncthreads();
+  __shared__ int s_last;
   if (threadIdx.x == 0) {
     double t = 0.0;
     for (int q = 0; q < CH / 64; ++q) t += red[q];
@@ -282,17 +294,24 @@ __global__ void __launch_bounds__(CH / 2, sizeof(T) == sizeof(float2) ? 8 : 1) k
       // the last CTA of the system to finish takes the reorthogonalisation decision for the conditional pass
       // (norm-drop test, see k_dots) from all chunk sums, so that the conditional kernels only read a flag
       __threadfence();
-      if (atomicAdd(st.arrive + s, 1) == nchunk - 1) {
-        __threadfence();
-        double before = 0.0, after = 0.0;
-        for (int cc = 0; cc < nchunk; ++cc) {
-          before += ((volatile double*)st.wpart)[(size_t)s * nchunk + cc];
-          after += ((volatile double*)st.npart)[(size_t)s * nchunk + cc];
-        }
-        st.reo[s] = after < 0.01 * before;   // ||w_after|| < ||w_before|| / 10
-        st.arrive[s] = 0;
-      }
+      s_last = atomicAdd(st.arrive + s, 1) == nchunk - 1;
     }
+  }
+  if (pass != 0) return;
+  __syncthreads();
+  if (!s_last || threadIdx.x >= 32) return;
+  __threadfence();
+  // one warp loads the chunk sums in parallel (L2, bypassing L1) and reduces them
+  double before = 0.0, after = 0.0;
+  for (int cc = threadIdx.x; cc < nchunk; cc += 32) {
+    before += __ldcg(st.wpart + (size_t)s * nchunk + cc);
+    after += __ldcg(st.npart + (size_t)s * nchunk + cc);
+  }
+  before = warp_sum(before);
+  after = warp_sum(after);
+  if (threadIdx.x == 0) {
+    st.reo[s] = after < 0.01 * before;   // ||w_after|| < ||w_before|| / 10
+    st.arrive[s] = 0;
   }
 }
 
@@ -305,27 +324,35 @@ __global__ void __launch_bounds__(CH / 2, sizeof(T) == sizeof(float2) ? 8 : 1) k
 // A system that converges at this step still gets V_{j+1}; nothing reads it.
 constexpr int kFinishMaxM = 1000;
 
-// One warp: h_{j+1,j} = hn.  The lanes stage column j and the rotations in shared memory and apply the
-// rotations as a scan (warp_rotate_column); lane 0 then forms the new rotation.
-__device__ __forceinline__ void finish_column(const KrylovState& st, int s, int j, double hn, double tol,
-                                              double2* sh_h, double2* sh_c, double2* sh_s) {
+// One warp: h_{j+1,j} = hn.  The lanes stage column j and the rotations in shared memory (complex type C:
+// FP64, or FP32 for an FP32 basis) and apply the rotations as a scan (warp_rotate_column); lane 0 then forms
+// the new rotation.  g and the residual estimate stay FP64.
+template <typename C>
+__device__ __forceinline__ void finish_column(const KrylovState& st, int s, int j, double hn, double tol, C* sh_h,
+                                              C* sh_c, C* sh_s) {
+  using R = decltype(C{}.x);
   const int lane = threadIdx.x & 31;
   double2* Hj = st.H + ((size_t)s * st.m + j) * (st.m + 1);
   double2* cs = st.cs + (size_t)s * st.m;
   double2* sn = st.sn + (size_t)s * st.m;
   for (int i = lane; i <= j; i += 32) {
-    sh_h[i] = Hj[i];
-    if (i < j) { sh_c[i] = cs[i]; sh_s[i] = sn[i]; }
+    const double2 h = Hj[i];
+    sh_h[i] = cx<C>(h.x, h.y);
+    if (i < j) {
+      const double2 ci = cs[i], si = sn[i];
+      sh_c[i] = cx<C>(ci.x, ci.y);
+      sh_s[i] = cx<C>(si.x, si.y);
+    }
   }
   __syncwarp();
-  const double2 a = warp_rotate_column(sh_h, sh_c, sh_s, j);
-  for (int i = lane; i < j; i += 32) Hj[i] = sh_h[i];
+  const C a = warp_rotate_column(sh_h, sh_c, sh_s, j);
+  for (int i = lane; i < j; i += 32) Hj[i] = make_double2(sh_h[i].x, sh_h[i].y);
   if (lane != 0) return;
-  double den, inv;
-  givens_norm(a, hn, den, inv);
+  R den, inv;
+  givens_norm(a, (R)hn, den, inv);
   double2 c, sv;
-  if (den == 0.0) { c = make_double2(1, 0); sv = make_double2(0, 0); }
-  else { c = cscale(a, inv); sv = make_double2(hn * inv, 0.0); }
+  if (den == (R)0) { c = make_double2(1, 0); sv = make_double2(0, 0); }
+  else { c = make_double2(a.x * inv, a.y * inv); sv = make_double2((R)hn * inv, 0.0); }
   cs[j] = c;
   sn[j] = sv;
   Hj[j] = make_double2(den, 0.0);
@@ -346,48 +373,56 @@ __device__ __forceinline__ void finish_column(const KrylovState& st, int s, int 
   }
 }
 
-// dynamic shared memory: 3 (m + 1) double2 (column and rotations for finish_column)
+// dynamic shared memory: 3 (m + 1) entries of T (column and rotations for finish_column).  Each thread scales
+// kStepPer entries, so that the grid of one iteration fits on the GPU in one wave.
+constexpr int kStepPer = 4;
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_step_end(KrylovState st, int nchunk, double tol) {
   pdl_enter();
   using F = typename Vec<T>::acc_t;
-  extern __shared__ double2 fin_sh[];
-  __shared__ double s_hn;
-  __shared__ F s_inv;
+  extern __shared__ __align__(16) unsigned char fin_raw[];
+  T* fin_sh = reinterpret_cast<T*>(fin_raw);
+  __shared__ F s_hn;
   const int c = blockIdx.x, s = blockIdx.y;
-  const int j = *st.jdev;
+  // read once, before the arrival below: the last CTA to arrive advances the index
+  const int j = *(volatile const int*)st.jdev;
   if (st.active[s]) {
     if (threadIdx.x < 32) {
-      double t = 0.0;
-      for (int cc = threadIdx.x; cc < nchunk; cc += 32) t += st.npart[(size_t)s * nchunk + cc];
+      F t = 0;   // in the basis precision
+      for (int cc = threadIdx.x; cc < nchunk; cc += 32) t += (F)st.npart[(size_t)s * nchunk + cc];
       t = warp_sum(t);
-      if (threadIdx.x == 0) {
-        s_hn = sqrt(t);
-        s_inv = (F)1 / (F)s_hn;   // in the basis precision (one division per CTA)
-      }
+      if (threadIdx.x == 0) s_hn = sqrt(t);
     }
     __syncthreads();
-    const double hn = s_hn;
+    const F hn = s_hn;
     // the rotations are the long dependent chain of this kernel: start them before the scaling
     if (c == 0 && threadIdx.x < 32)
-      finish_column(st, s, j, hn, tol, fin_sh, fin_sh + (st.m + 1), fin_sh + 2 * (st.m + 1));
-    const int k = c * kThreads + threadIdx.x;
-    if (k < st.n && hn > 0.0 && j + 1 < st.m) {
+      finish_column(st, s, j, (double)hn, tol, fin_sh, fin_sh + (st.m + 1), fin_sh + 2 * (st.m + 1));
+    if (hn > (F)0 && j + 1 < st.m) {
       const T* W = static_cast<const T*>(st.W) + (size_t)s * st.n;
       T* Vn = static_cast<T*>(st.V) + ((size_t)(j + 1) * st.nrhs + s) * st.n;
-      const F inv = s_inv;
-      T w = W[k];
-      w.x *= inv;
-      w.y *= inv;
-      Vn[k] = w;
-      if (st.b16hi)
-        tc_write_b(static_cast<__half*>(st.b16hi), static_cast<__half*>(st.b16lo), st.ldb16, s, k, (float)w.x,
-                   (float)w.y);
+      const F inv = (F)1 / hn;
+      const int k0 = c * (kThreads * kStepPer) + threadIdx.x;
+      T w[kStepPer];
+#pragma unroll
+      for (int q = 0; q < kStepPer; ++q)
+        if (k0 + q * kThreads < st.n) w[q] = W[k0 + q * kThreads];
+#pragma unroll
+      for (int q = 0; q < kStepPer; ++q) {
+        const int k = k0 + q * kThreads;
+        if (k < st.n) {
+          w[q].x *= inv;
+          w[q].y *= inv;
+          Vn[k] = w[q];
+          if (st.b16hi)
+            tc_write_b(static_cast<__half*>(st.b16hi), static_cast<__half*>(st.b16lo), st.ldb16, s, k, (float)w[q].x,
+                       (float)w[q].y);
+        }
+      }
     }
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    __threadfence();   // this CTA's reads of the iteration index precede the advance
     if (atomicAdd(st.arrive + s, 1) == (int)gridDim.x - 1) {
       st.arrive[s] = 0;
       if (atomicAdd(st.arrive_all, 1) == (int)gridDim.y - 1) {
@@ -511,8 +546,8 @@ template <typename T>
 cudaError_t finish_t(const KrylovState& st, double tol, cudaStream_t s) {
   const int ch = chunk_of(st.n, st.nrhs);
   const int nc = (st.n + ch - 1) / ch;   // the update kernel's chunks (its squared norms)
-  return launch_pdl(k_step_end<T>, dim3(nblk_of(st.n), st.nrhs), dim3(kThreads), 3 * (st.m + 1) * sizeof(double2), s,
-                    st, nc, tol);
+  const int nb = (st.n + kThreads * kStepPer - 1) / (kThreads * kStepPer);
+  return launch_pdl(k_step_end<T>, dim3(nb, st.nrhs), dim3(kThreads), 3 * (st.m + 1) * sizeof(T), s, st, nc, tol);
 }
 
 template <typename T>
