@@ -38,13 +38,15 @@ METRIC = "BEM solves/s (mixed vs FP64 GPU at err<=1e-6)"
 #    geometry, phase reduction) and the FP32 pipe (double-float Bessel arithmetic); neither pipe alone binds,
 #    so its roofline is the issue rate: 4 warp instructions per clock per SM.  DRAM traffic 551.8 MB.
 #  * the multi-RHS GEMM streams A once: 2 x 2 bytes per real entry; measured DRAM traffic 316.3 MB.
-#  * the refinement residual runs 24 FP32 operations per complex multiply-add (four exact products summed
-#    with an offset accumulator, four operations each, and eight FMAs for the small terms; the per-run
-#    offsets and the double-float fold are not counted): FP32 pipe, 128 operations per clock per SM.
+#  * the refinement residual runs 16 FP32 operations per complex multiply-add on the FP32 pipe (four exact
+#    products summed with an offset accumulator, four operations each; the per-run offsets and the
+#    double-float fold are not counted), 128 operations per clock per SM; with the tensor-core product the
+#    small terms hi x_lo + lo x_hi are two FP16x3 GEMMs (11 kernels per residual, 12 with a K split).
 ASM_WARP_INST_N3072 = 2.91162048e9
 ASM_DRAM_BYTES_N3072 = 550810112 + 970496
 GEMM_DRAM_BYTES_N3072 = 311.3e6 + 5.0e6
-RESID_FP32_OPS_PER_CMAC = 24
+RESID_FP32_OPS_PER_CMAC = 16
+RESID_LAUNCHES_TC = 11
 SM_COUNT, SM_CLOCK_HZ = 152, 2.07e9
 ISSUE_PEAK_G = SM_COUNT * 4 * SM_CLOCK_HZ / 1e9          # G warp instructions / s
 FP32_PEAK_T = SM_COUNT * 128 * SM_CLOCK_HZ / 1e12        # T FP32 thread operations / s
@@ -405,12 +407,12 @@ def main():
                      "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "peak_source": src,
                      "traffic": GEMM_DRAM_BYTES_N3072 * scale if N_RHS > 1 else None})
     else:
-        # the residual phase holds two launches per refinement step: the split of x and the df product
-        n_gemm = max(1, ph_n // 2)
+        # launches per refinement residual: 11 (12 with a K split) with the tensor-core small terms
+        n_gemm = max(1, ph_n // RESID_LAUNCHES_TC)
         avg_s = ph_ms / n_gemm / 1e3
         ops = RESID_FP32_OPS_PER_CMAC * n2 * n2 * N_RHS
         ach = ops / avg_s / 1e12
-        roof.update({"kernel": "k_resid_df_gemm (double-float residual on the FP32 pipe)", "bound": "alu",
+        roof.update({"kernel": "k_resid_df_gemm (double-float residual: exact products on the FP32 pipe)", "bound": "alu",
                      "launches": n_gemm, "avg_launch_ms": ph_ms / n_gemm, "achieved": ach, "peak": FP32_PEAK_T,
                      "unit": "T FP32 operations/s", "frac": ach / FP32_PEAK_T,
                      "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz"})

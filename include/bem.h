@@ -146,8 +146,10 @@ BEM_API bem_status bem_rhs_planewave(bem_problem* p, int n_rhs, const double* an
 BEM_API bem_status bem_matvec(bem_problem* p, int n_rhs, const bem_c64* x_dev, bem_c64* y_dev, void* stream);
 
 /* Step a9's residual: r = b - A x for n_rhs columns with the solver's FP64-accurate operator (FP64 path:
- * FP64 products of A; mixed paths: (hi + lo) x in double-float arithmetic on the FP32 pipes).
- * x_dev, b_dev, r_dev: n_rhs x 2N complex FP64 (r_dev may alias b_dev, not x_dev). */
+ * FP64 products of A; mixed paths: (hi + lo) x in double-float arithmetic, the exact products hi x_hi on the
+ * FP32 pipes; MIXED_TC with n_rhs >= 2 forms the small terms hi x_lo + lo x_hi as tensor-core products, and
+ * then waits for the stream to read the product's error word, returning BEM_ETIMEOUT if one of its bounded
+ * waits expired).  x_dev, b_dev, r_dev: n_rhs x 2N complex FP64 (r_dev may alias b_dev, not x_dev). */
 BEM_API bem_status bem_residual(bem_problem* p, int n_rhs, const bem_c64* x_dev, const bem_c64* b_dev, bem_c64* r_dev,
                                 void* stream);
 

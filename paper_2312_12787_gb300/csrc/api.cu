@@ -95,6 +95,8 @@ struct bem_problem {
   size_t A_cap = 0;       // bytes of d_A (and d_Alo when mixed)
   void* d_A16 = nullptr;  // FP16 split copy of the complex FP32 matrix for the tensor-core product
   size_t A16_cap = 0;
+  void* d_Alo16 = nullptr;  // the same of the remainder lo (the residual's small terms)
+  size_t Alo16_cap = 0;
   bool a16_dirty = true;
   int A_mixed = -1;
   // solve workspace (grow-only)
@@ -153,6 +155,9 @@ struct Phase {
     p->launches[ph] += nlaunch;
     b = pool_event(p);
     if (b) cudaEventRecord(b, s);
+  }
+  void add_launches(int n) {
+    if (p->prof) p->launches[ph] += n;
   }
   ~Phase() {
     if (!b) return;
@@ -275,9 +280,18 @@ bem_status ensure_a16(bem_problem* p, cudaStream_t s) {
     if (cudaMalloc(&p->d_A16, need) != cudaSuccess) return fail(BEM_ENOMEM, "matrix allocation of %zu bytes failed", need);
     p->A16_cap = need;
   }
+  if (need > p->Alo16_cap) {
+    if (p->d_Alo16) cudaFree(p->d_Alo16);
+    p->d_Alo16 = nullptr;
+    p->Alo16_cap = 0;
+    if (cudaMalloc(&p->d_Alo16, need) != cudaSuccess)
+      return fail(BEM_ENOMEM, "matrix allocation of %zu bytes failed", need);
+    p->Alo16_cap = need;
+  }
   {
-    Phase ph(p, BEM_PH_OTHER, s, 1);
+    Phase ph(p, BEM_PH_OTHER, s, 2);
     CU(launch_tc_prepare_a(static_cast<const float2*>(p->d_A), n2, p->d_A16, s));
+    CU(launch_tc_prepare_a(static_cast<const float2*>(p->d_Alo), n2, p->d_Alo16, s));
   }
   p->a16_dirty = false;
   return BEM_OK;
@@ -535,6 +549,13 @@ bem_status gmres_run(bem_problem* p, Solver& sv, const double2* r0, double2* x, 
   return BEM_OK;
 }
 
+// The refinement residual r = b - (hi + lo) x of a mixed problem.  Problems that use the tensor-core product
+// form the small terms hi x_lo + lo x_hi on the tensor cores (the FP32 pipes then only sum the exact products
+// hi x_hi); that path waits for the stream to read the product's error word.  ws = the solver's basis
+// (free outside a GMRES run).
+bem_status residual_mixed(bem_problem* p, Solver& sv, int nrhs, const double2* x, const double2* b, double2* r,
+                          cudaStream_t s);
+
 // column 2-norms of an FP64 block (host result)
 bem_status column_norms(bem_problem* p, Solver& sv, const double2* v, int nrhs, std::vector<double>& out,
                         cudaStream_t s);
@@ -555,6 +576,33 @@ bem_status column_norms(bem_problem* p, Solver& sv, const double2* v, int nrhs, 
   out.resize(nrhs);
   CU(cudaMemcpyAsync(out.data(), sv.st.beta, nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
   CU(cudaStreamSynchronize(s));
+  return BEM_OK;
+}
+
+bem_status residual_mixed(bem_problem* p, Solver& sv, int nrhs, const double2* x, const double2* b, double2* r,
+                          cudaStream_t s) {
+  const int n2 = 2 * p->n;
+  const float2* A = static_cast<const float2*>(p->d_A);
+  const float2* Alo = static_cast<const float2*>(p->d_Alo);
+  if (p->o.prec == BEM_PREC_MIXED_TC && nrhs > 1 && matvec_tc_supported(n2, nrhs) &&
+      basis_bytes(sv) >= residual_tc_ws_bytes(n2, nrhs)) {
+    const bem_status a = ensure_a16(p, s);
+    if (a != BEM_OK) return a;
+    CU(matvec_tc_clear_error(sv.tcws, n2, nrhs, s));
+    int nl = 0, tc_err = 0;
+    {
+      Phase ph(p, BEM_PH_RESIDUAL, s, 0);
+      CU(launch_residual_split_tc(A, Alo, n2, p->d_A16, p->d_Alo16, n2, nrhs, x, b, r, sv.st.V, basis_bytes(sv),
+                                  sv.tcws, sv.tcws_bytes, s, &nl));
+      ph.add_launches(nl);
+    }
+    CU(cudaMemcpyAsync(&tc_err, matvec_tc_error_word(sv.tcws, n2, nrhs), sizeof(int), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    if (tc_err) return fail(BEM_ETIMEOUT, "tensor-core GEMM wait expired (code %d)", tc_err);
+    return BEM_OK;
+  }
+  Phase ph(p, BEM_PH_RESIDUAL, s, 2);   // split of x, double-float product
+  CU(launch_residual_split(A, Alo, n2, n2, nrhs, x, b, r, sv.st.V, s, basis_bytes(sv)));
   return BEM_OK;
 }
 
@@ -598,11 +646,8 @@ bem_status solve_impl(bem_problem* p, int nrhs, const double2* b, double2* x, in
         tols[r] = rn[r] > 0 ? std::max(p->o.inner_tol, 0.3 * p->o.tol * bn[r] / rn[r]) : 1.0;
       st = gmres_run(p, sv, sv.r, x, tols, iters, inner_res, s);
       if (st != BEM_OK) return st;
-      {
-        Phase ph(p, BEM_PH_RESIDUAL, s, 2);   // split of x, double-float product
-        CU(launch_residual_split(static_cast<const float2*>(p->d_A), static_cast<const float2*>(p->d_Alo), n2, n2,
-                                 nrhs, x, b, sv.r, sv.st.V, s, basis_bytes(sv)));   // the basis is free here
-      }
+      st = residual_mixed(p, sv, nrhs, x, b, sv.r, s);
+      if (st != BEM_OK) return st;
       st = column_norms(p, sv, sv.r, nrhs, rn, s);
       if (st != BEM_OK) return st;
     }
@@ -742,6 +787,7 @@ BEM_API void bem_problem_destroy(bem_problem* p) {
   if (p->d_A) cudaFree(p->d_A);
   if (p->d_Alo) cudaFree(p->d_Alo);
   if (p->d_A16) cudaFree(p->d_A16);
+  if (p->d_Alo16) cudaFree(p->d_Alo16);
   if (p->ws) cudaFree(p->ws);
   if (p->d_small) cudaFree(p->d_small);
   if (p->h_pin) cudaFreeHost(p->h_pin);
@@ -817,7 +863,8 @@ BEM_API int bem_num_unknowns(const bem_problem* p) { return p ? 2 * p->n : 0; }
 BEM_API size_t bem_footprint_bytes(const bem_problem* p, int n_rhs) {
   if (!p || n_rhs < 1) return 0;
   const bool mixed = p->o.prec != BEM_PREC_FP64;
-  const size_t a16 = (!p->o.matrix_free && p->o.prec == BEM_PREC_MIXED_TC && n_rhs > 1) ? matvec_tc_a16_bytes(2 * p->n) : 0;
+  const size_t a16 =
+      (!p->o.matrix_free && p->o.prec == BEM_PREC_MIXED_TC && n_rhs > 1) ? 2 * matvec_tc_a16_bytes(2 * p->n) : 0;
   return (p->o.matrix_free ? 0 : matrix_bytes(p->n, mixed)) + a16 + krylov_bytes(2 * p->n, n_rhs, p->o.max_iter, mixed) +
          (size_t)12 * p->n * 8;
 }
@@ -905,23 +952,22 @@ BEM_API bem_status bem_residual(bem_problem* p, int n_rhs, const bem_c64* x_dev,
   const double2* x = reinterpret_cast<const double2*>(x_dev);
   const double2* b = reinterpret_cast<const double2*>(b_dev);
   double2* r = reinterpret_cast<double2*>(r_dev);
-  Phase ph(p, BEM_PH_RESIDUAL, s, p->mixed() ? 2 : 1);
   if (p->o.matrix_free) {
+    Phase ph(p, BEM_PH_RESIDUAL, s, 2);
     // r = b - A x with recomputed entries: product into r, then r = b - r
     CU(launch_matvec_free(p->elem(), p->n, p->dom, make_quad(p->o.quad_order), p->o.form, n_rhs, x, r, s));
     CU(launch_axpby_neg(b, r, (size_t)n_rhs * n2, s));
     return BEM_OK;
   }
   if (!p->mixed()) {
+    Phase ph(p, BEM_PH_RESIDUAL, s, 1);
     CU(launch_residual_c64(static_cast<const double2*>(p->d_A), n2, n2, n_rhs, x, b, r, s));
     return BEM_OK;
   }
   st = ensure_ws(p, krylov_bytes(n2, n_rhs, p->o.max_iter, true));
   if (st != BEM_OK) return st;
   Solver sv = carve_solver(p, n_rhs, true);
-  CU(launch_residual_split(static_cast<const float2*>(p->d_A), static_cast<const float2*>(p->d_Alo), n2, n2, n_rhs, x,
-                           b, r, sv.st.V, s, basis_bytes(sv)));
-  return BEM_OK;
+  return residual_mixed(p, sv, n_rhs, x, b, r, s);
 }
 
 BEM_API bem_status bem_solve(bem_problem* p, int n_rhs, const bem_c64* b_dev, bem_c64* x_dev, int* iters,

@@ -139,6 +139,15 @@ cudaError_t launch_matvec_c32(const float2* A, size_t lda, int n, int nrhs, cons
 cudaError_t launch_residual_split(const float2* Ahi, const float2* Alo, size_t lda, int n, int nrhs,
                                   const double2* x, const double2* b, double2* r, void* ws, cudaStream_t s,
                                   size_t ws_bytes = 0);
+// The same residual for problems with the tensor-core product: the small terms hi * x_lo + lo * x_hi are two
+// tensor-core products (a16 = FP16 split copy of hi, alo16 = the same of lo; tcws = a tensor-core workspace),
+// so the FP32-pipe kernel only sums the exact products hi * x_hi.  ws holds residual_tc_ws_bytes(n, nrhs)
+// bytes and more for K-split partials.  Needs 2 <= nrhs <= 64.
+size_t residual_tc_ws_bytes(int n, int nrhs);
+cudaError_t launch_residual_split_tc(const float2* Ahi, const float2* Alo, size_t lda, const void* a16,
+                                     const void* alo16, int n, int nrhs, const double2* x, const double2* b,
+                                     double2* r, void* ws, size_t ws_bytes, void* tcws, size_t tcws_bytes,
+                                     cudaStream_t s, int* nlaunch = nullptr);
 cudaError_t launch_residual_c64(const double2* A, size_t lda, int n, int nrhs, const double2* x, const double2* b,
                                 double2* r, cudaStream_t s);
 cudaError_t launch_residual_split_f64(const float2* Ahi, const float2* Alo, size_t lda, int n, int nrhs,

@@ -420,11 +420,16 @@ __device__ __forceinline__ void offset_acc(float a, float b, float& acc, float& 
   acc = t;
 }
 
+//
+// kCross = false: the small terms hi * x_lo + lo * x_hi are not formed here; they arrive as the FP32 block
+// cross (nrhs x n, a tensor-core product: they carry 2^-24 of the sum, so its FP32 accumulation is ample)
+// and join the sum in FP64 (in k_resid_combine when K is split).
+template <bool kCross>
 __global__ void __launch_bounds__(256) k_resid_df_gemm(const float2* __restrict__ Ah, const float2* __restrict__ Al,
                                                         size_t lda, int n, int nrhs, const float2* __restrict__ xh,
                                                         const float2* __restrict__ xl, const double2* __restrict__ b,
                                                         double2* __restrict__ r, int kchunk,
-                                                        double2* __restrict__ part) {
+                                                        double2* __restrict__ part, const float2* __restrict__ cross) {
   constexpr int BR = kResBR, BS = kResBS, BK = kResBK, NSUB = kResBK / kResSub;
   const int kbeg = blockIdx.z * kchunk, kend = min(n, kbeg + kchunk);
   __shared__ float2 Ash[BK][BR + 1], Asl[BK][BR + 1];
@@ -451,7 +456,7 @@ __global__ void __launch_bounds__(256) k_resid_df_gemm(const float2* __restrict_
       const bool in = gr < n && gk < kend;
       const float2 vh = in ? __ldcs(Ah + (size_t)gr * lda + gk) : z;
       Ash[kk][rr] = vh;
-      Asl[kk][rr] = in ? __ldcs(Al + (size_t)gr * lda + gk) : z;
+      if (kCross) Asl[kk][rr] = in ? __ldcs(Al + (size_t)gr * lda + gk) : z;
       const float m = run_max8(vh);
       if ((kk & (kResSub - 1)) == 0) Amax[kk / kResSub][rr] = m;
     }
@@ -463,7 +468,7 @@ __global__ void __launch_bounds__(256) k_resid_df_gemm(const float2* __restrict_
       const bool in = gs < nrhs && gk < kend;
       const float2 vh = in ? xh[(size_t)gs * n + gk] : z;
       Xsh[kk][ss] = vh;
-      Xsl[kk][ss] = in ? xl[(size_t)gs * n + gk] : z;
+      if (kCross) Xsl[kk][ss] = in ? xl[(size_t)gs * n + gk] : z;
       const float m = run_max8(vh);
       if ((kk & (kResSub - 1)) == 0) Xmax[kk / kResSub][ss] = m;
     }
@@ -483,9 +488,15 @@ __global__ void __launch_bounds__(256) k_resid_df_gemm(const float2* __restrict_
       for (int kk = sub * kResSub; kk < (sub + 1) * kResSub; ++kk) {
         float2 ah[2], al[2], vh[4], vl[4];
 #pragma unroll
-        for (int a = 0; a < 2; ++a) { ah[a] = Ash[kk][ty + 16 * a]; al[a] = Asl[kk][ty + 16 * a]; }
+        for (int a = 0; a < 2; ++a) {
+          ah[a] = Ash[kk][ty + 16 * a];
+          if (kCross) al[a] = Asl[kk][ty + 16 * a];
+        }
 #pragma unroll
-        for (int q = 0; q < 4; ++q) { vh[q] = Xsh[kk][tx + 16 * q]; vl[q] = Xsl[kk][tx + 16 * q]; }
+        for (int q = 0; q < 4; ++q) {
+          vh[q] = Xsh[kk][tx + 16 * q];
+          if (kCross) vl[q] = Xsl[kk][tx + 16 * q];
+        }
 #pragma unroll
         for (int a = 0; a < 2; ++a)
 #pragma unroll
@@ -494,12 +505,14 @@ __global__ void __launch_bounds__(256) k_resid_df_gemm(const float2* __restrict_
             offset_acc(-ah[a].y, vh[q].y, ar[a][q], cr[a][q]);
             offset_acc(ah[a].x, vh[q].y, ai[a][q], ci[a][q]);
             offset_acc(ah[a].y, vh[q].x, ai[a][q], ci[a][q]);
-            float& c1 = cr[a][q];
-            float& c2 = ci[a][q];
-            c1 = fmaf(ah[a].x, vl[q].x, c1); c1 = fmaf(-ah[a].y, vl[q].y, c1);
-            c1 = fmaf(al[a].x, vh[q].x, c1); c1 = fmaf(-al[a].y, vh[q].y, c1);
-            c2 = fmaf(ah[a].x, vl[q].y, c2); c2 = fmaf(ah[a].y, vl[q].x, c2);
-            c2 = fmaf(al[a].x, vh[q].y, c2); c2 = fmaf(al[a].y, vh[q].x, c2);
+            if (kCross) {
+              float& c1 = cr[a][q];
+              float& c2 = ci[a][q];
+              c1 = fmaf(ah[a].x, vl[q].x, c1); c1 = fmaf(-ah[a].y, vl[q].y, c1);
+              c1 = fmaf(al[a].x, vh[q].x, c1); c1 = fmaf(-al[a].y, vh[q].y, c1);
+              c2 = fmaf(ah[a].x, vl[q].y, c2); c2 = fmaf(ah[a].y, vl[q].x, c2);
+              c2 = fmaf(al[a].x, vh[q].y, c2); c2 = fmaf(al[a].y, vh[q].x, c2);
+            }
           }
       }
 #pragma unroll
@@ -521,10 +534,15 @@ __global__ void __launch_bounds__(256) k_resid_df_gemm(const float2* __restrict_
     for (int q = 0; q < 4; ++q) {
       const int gr = r0 + ty + 16 * a, gs = s0 + tx + 16 * q;
       if (gr < n && gs < nrhs) {
-        const double2 ax = make_double2((double)Sr[a][q] + (double)Lr[a][q], (double)Si[a][q] + (double)Li[a][q]);
+        double2 ax = make_double2((double)Sr[a][q] + (double)Lr[a][q], (double)Si[a][q] + (double)Li[a][q]);
         if (part) {
           part[((size_t)blockIdx.z * nrhs + gs) * n + gr] = ax;
         } else {
+          if (!kCross) {
+            const float2 cv = cross[(size_t)gs * n + gr];
+            ax.x += (double)cv.x;
+            ax.y += (double)cv.y;
+          }
           const double2 bb = b[(size_t)gs * n + gr];
           r[(size_t)gs * n + gr] = make_double2(bb.x - ax.x, bb.y - ax.y);
         }
@@ -532,9 +550,10 @@ __global__ void __launch_bounds__(256) k_resid_df_gemm(const float2* __restrict_
     }
 }
 
-// r = b - sum over the K splits of the partial products (FP64, in split order).
+// r = b - sum over the K splits of the partial products (FP64, in split order) - cross (if given).
 __global__ void k_resid_combine(const double2* __restrict__ part, int nsplit, size_t count,
-                                const double2* __restrict__ b, double2* __restrict__ r) {
+                                const double2* __restrict__ b, double2* __restrict__ r,
+                                const float2* __restrict__ cross) {
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < count; t += (size_t)gridDim.x * blockDim.x) {
     double ax = 0.0, ay = 0.0;
     for (int z = 0; z < nsplit; ++z) {
@@ -542,8 +561,19 @@ __global__ void k_resid_combine(const double2* __restrict__ part, int nsplit, si
       ax += v.x;
       ay += v.y;
     }
+    if (cross) {
+      ax += (double)cross[t].x;
+      ay += (double)cross[t].y;
+    }
     const double2 bb = b[t];
     r[t] = make_double2(bb.x - ax, bb.y - ay);
+  }
+}
+
+__global__ void k_add_c32(float2* __restrict__ a, const float2* __restrict__ b, size_t count) {
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < count; t += (size_t)gridDim.x * blockDim.x) {
+    const float2 u = a[t], v = b[t];
+    a[t] = make_float2(u.x + v.x, u.y + v.y);
   }
 }
 
@@ -623,17 +653,20 @@ cudaError_t launch_matvec_c32(const float2* A, size_t lda, int n, int nrhs, cons
 // Number of K splits for the tiled residual: the CTA count tiles x S should fill whole waves of the SMs
 // (tiles alone, e.g. 256 for 8192 unknowns x 64 columns, leave a partial second wave), with at least 512
 // columns of K per split and the partials within the workspace.
-static int resid_splits(int n, int nrhs, size_t part_room) {
-  static std::atomic<int> slots_cache{0};
-  int slots = slots_cache.load(std::memory_order_relaxed);
+static int resid_splits(int n, int nrhs, size_t part_room, bool cross_terms) {
+  static std::atomic<int> slots_cache[2];
+  int slots = slots_cache[cross_terms].load(std::memory_order_relaxed);
   if (slots <= 0) {
     int dev = 0, sms = 0, per = 0;
+    const cudaError_t e =
+        cross_terms ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_resid_df_gemm<true>, 256, 0)
+                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_resid_df_gemm<false>, 256, 0);
     if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_resid_df_gemm, 256, 0) != cudaSuccess || per <= 0)
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || e != cudaSuccess ||
+        per <= 0)
       return 1;
     slots = sms * per;
-    slots_cache.store(slots, std::memory_order_relaxed);
+    slots_cache[cross_terms].store(slots, std::memory_order_relaxed);
   }
   const long long tiles = (long long)((n + kResBR - 1) / kResBR) * ((nrhs + kResBS - 1) / kResBS);
   int best = 1;
@@ -662,13 +695,45 @@ cudaError_t launch_residual_split(const float2* Ahi, const float2* Alo, size_t l
     k_resid_df_gemv<<<grd, 256, 0, s>>>(Ahi, Alo, lda, n, xh, xl, b, r);
   } else {
     const size_t xbytes = ((2 * (size_t)nrhs * n * sizeof(float2)) + 255) & ~(size_t)255;
-    const int S = ws_bytes > xbytes ? resid_splits(n, nrhs, ws_bytes - xbytes) : 1;
+    const int S = ws_bytes > xbytes ? resid_splits(n, nrhs, ws_bytes - xbytes, true) : 1;
     const int kchunk = ((n + S - 1) / S + kResBK - 1) / kResBK * kResBK;
     double2* part = S > 1 ? reinterpret_cast<double2*>(static_cast<char*>(ws) + xbytes) : nullptr;
     dim3 grd((n + kResBR - 1) / kResBR, (nrhs + kResBS - 1) / kResBS, S);
-    k_resid_df_gemm<<<grd, 256, 0, s>>>(Ahi, Alo, lda, n, nrhs, xh, xl, b, r, S > 1 ? kchunk : n, part);
-    if (S > 1) k_resid_combine<<<1024, 256, 0, s>>>(part, S, (size_t)nrhs * n, b, r);
+    k_resid_df_gemm<true><<<grd, 256, 0, s>>>(Ahi, Alo, lda, n, nrhs, xh, xl, b, r, S > 1 ? kchunk : n, part, nullptr);
+    if (S > 1) k_resid_combine<<<1024, 256, 0, s>>>(part, S, (size_t)nrhs * n, b, r, nullptr);
   }
+  return cudaGetLastError();
+}
+
+size_t residual_tc_ws_bytes(int n, int nrhs) {
+  return ((4 * (size_t)nrhs * n * sizeof(float2)) + 255) & ~(size_t)255;
+}
+
+cudaError_t launch_residual_split_tc(const float2* Ahi, const float2* Alo, size_t lda, const void* a16,
+                                     const void* alo16, int n, int nrhs, const double2* x, const double2* b,
+                                     double2* r, void* ws, size_t ws_bytes, void* tcws, size_t tcws_bytes,
+                                     cudaStream_t s, int* nlaunch) {
+  const size_t xbytes = residual_tc_ws_bytes(n, nrhs);
+  if (ws_bytes < xbytes || nrhs < 2) return cudaErrorInvalidValue;
+  // ws: x_hi | x_lo | hi x_lo | lo x_hi (each nrhs x n complex FP32), then the K-split partials
+  float2* xh = static_cast<float2*>(ws);
+  float2* xl = xh + (size_t)nrhs * n;
+  float2* c1 = xl + (size_t)nrhs * n;
+  float2* c2 = c1 + (size_t)nrhs * n;
+  k_split_x<<<512, 256, 0, s>>>(x, xh, xl, (size_t)nrhs * n);
+  cudaError_t e = launch_matvec_tc(a16, n, nrhs, xl, c1, tcws, tcws_bytes, s);
+  if (e != cudaSuccess) return e;
+  e = launch_matvec_tc(alo16, n, nrhs, xh, c2, tcws, tcws_bytes, s);
+  if (e != cudaSuccess) return e;
+  k_add_c32<<<512, 256, 0, s>>>(c1, c2, (size_t)nrhs * n);
+  const int S = resid_splits(n, nrhs, ws_bytes - xbytes, false);
+  const int kchunk = ((n + S - 1) / S + kResBK - 1) / kResBK * kResBK;
+  double2* part = S > 1 ? reinterpret_cast<double2*>(static_cast<char*>(ws) + xbytes) : nullptr;
+  dim3 grd((n + kResBR - 1) / kResBR, (nrhs + kResBS - 1) / kResBS, S);
+  k_resid_df_gemm<false><<<grd, 256, 0, s>>>(Ahi, Alo, lda, n, nrhs, xh, xl, b, r, S > 1 ? kchunk : n, part, c1);
+  if (S > 1) k_resid_combine<<<1024, 256, 0, s>>>(part, S, (size_t)nrhs * n, b, r, c1);
+  // kernels: split, 2 x (column maxima, operand, product, reduction), sum, residual [, combine]
+  if (nlaunch) *nlaunch = 11 + (S > 1 ? 1 : 0);
   return cudaGetLastError();
 }
 

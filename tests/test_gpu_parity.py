@@ -251,12 +251,13 @@ def test_solve_mixed_tensor_core_matches_oracle_lu(B, torch):
     p.close()
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "mixed_tc"])
 @pytest.mark.parametrize("nrhs", [1, 5])
 def test_residual_matches_oracle(B, torch, prec, nrhs):
     """r = b - A x through the C-ABI against the oracle's FP64 matrix: for random x (no cancellation), for
     the LU solution (residual dominated by cancellation, where the double-float sum matters), for that
-    solution scaled by 2^70, for x spread over 30 decades, and for x = 0 (r must be b exactly)."""
+    solution scaled by 2^70, for x spread over 30 decades, and for x = 0 (r must be b exactly).  mixed_tc with
+    several columns forms the small terms hi x_lo + lo x_hi on the tensor cores."""
     wp = W.Problem(k=[20.0, 30.0], eps=[1.0, 2.25], segments=[W.Segment(W.star(300, 0.3, 5), P=0, M=1, closed=True)])
     A = O.assemble(wp, Q=4)
     n2 = A.shape[0]
