@@ -17,7 +17,10 @@
  *   - Complex numbers are bem_c64 {re, im} (16 bytes, layout-compatible with double _Complex).
  *   - Pointers named *_dev are CUDA device pointers on the current device; pointers named *_host are
  *     host pointers.  The caller owns every buffer it passes; the library owns the assembled matrix,
- *     the Krylov workspace and any scratch it allocates (freed by bem_problem_destroy).
+ *     the Krylov workspace and any scratch it allocates (freed by bem_problem_destroy).  These come from
+ *     a per-device memory pool of the library that keeps up to 32 GiB of freed blocks for the next
+ *     problem (so creating problems one after another maps no new pages); allocation and release are
+ *     synchronous, and a release waits for the device to be idle, as cudaFree does.
  *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).  Device work is
  *     stream-ordered on it.  Entry points that return host values (iteration counts, residuals,
  *     host outputs) synchronise the stream before returning.

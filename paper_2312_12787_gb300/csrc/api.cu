@@ -7,6 +7,8 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
+#include <mutex>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -168,14 +170,80 @@ struct Phase {
   }
 };
 
+// ---- device memory of problems ---------------------------------------------------------------------
+// Problem buffers (matrix copies, Krylov workspace, geometry) come from a per-device memory pool of this
+// library that keeps up to kPoolKeepBytes of freed blocks, so a problem created after another one was
+// destroyed (a serving loop, the host-buffer entry point) reuses the memory instead of mapping new pages.
+// dev_malloc and dev_free are synchronous like cudaMalloc and cudaFree: the allocation is made on an
+// internal stream and waited for (usable on every stream on return); a free first waits for the device to
+// be idle, as cudaFree does.  Without pool support they are cudaMalloc and cudaFree.
+constexpr uint64_t kPoolKeepBytes = 32ull << 30;
+constexpr int kPoolDevs = 64;
+struct DevPool {
+  std::once_flag once;
+  cudaMemPool_t pool = nullptr;
+  cudaStream_t s = nullptr;
+  bool ok = false;
+};
+DevPool g_pools[kPoolDevs];
+
+DevPool* dev_pool() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kPoolDevs) return nullptr;
+  DevPool& d = g_pools[dev];
+  std::call_once(d.once, [&d, dev] {
+    int supported = 0;
+    if (cudaDeviceGetAttribute(&supported, cudaDevAttrMemoryPoolsSupported, dev) != cudaSuccess || !supported) return;
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    if (cudaMemPoolCreate(&d.pool, &props) != cudaSuccess) return;
+    uint64_t keep = kPoolKeepBytes;
+    if (cudaMemPoolSetAttribute(d.pool, cudaMemPoolAttrReleaseThreshold, &keep) != cudaSuccess) return;
+    if (cudaStreamCreateWithFlags(&d.s, cudaStreamNonBlocking) != cudaSuccess) return;
+    d.ok = true;
+  });
+  return d.ok ? &d : nullptr;
+}
+
+cudaError_t dev_malloc(void** ptr, size_t bytes) {
+  DevPool* d = dev_pool();
+  if (!d) return cudaMalloc(ptr, bytes);
+  cudaError_t e = cudaMallocFromPoolAsync(ptr, bytes, d->pool, d->s);
+  if (e != cudaSuccess) return e;
+  return cudaStreamSynchronize(d->s);
+}
+template <typename T> cudaError_t dev_malloc(T** ptr, size_t bytes) {
+  return dev_malloc(reinterpret_cast<void**>(ptr), bytes);
+}
+
+// Stream-ordered scratch of one call (freed with cudaFreeAsync on the same stream), from the same pool.
+template <typename T> cudaError_t dev_malloc_async(T** ptr, size_t bytes, cudaStream_t s) {
+  DevPool* d = dev_pool();
+  if (!d) return cudaMallocAsync(reinterpret_cast<void**>(ptr), bytes, s);
+  return cudaMallocFromPoolAsync(reinterpret_cast<void**>(ptr), bytes, d->pool, s);
+}
+
+void dev_free(void* ptr) {
+  if (!ptr) return;
+  DevPool* d = dev_pool();
+  if (!d) {
+    cudaFree(ptr);
+    return;
+  }
+  cudaDeviceSynchronize();
+  if (cudaFreeAsync(ptr, d->s) == cudaSuccess) cudaStreamSynchronize(d->s);
+}
+
 Quad make_quad(int Q) { return bem::make_quad_host(Q); }
 
 bem_status ensure_small(bem_problem* p, size_t doubles) {
   if (doubles <= p->small_cap) return BEM_OK;
-  if (p->d_small) cudaFree(p->d_small);
+  if (p->d_small) dev_free(p->d_small);
   p->d_small = nullptr;
   p->small_cap = 0;
-  CU(cudaMalloc(&p->d_small, doubles * sizeof(double)));
+  CU(dev_malloc(&p->d_small, doubles * sizeof(double)));
   p->small_cap = doubles;
   return BEM_OK;
 }
@@ -184,13 +252,13 @@ bem_status upload_geometry(bem_problem* p, cudaStream_t s) {
   if (!p->geom_dirty) return BEM_OK;
   const int n = p->n;
   if ((size_t)n > p->geom_cap) {
-    if (p->d_geom) cudaFree(p->d_geom);
-    if (p->d_pm) cudaFree(p->d_pm);
+    if (p->d_geom) dev_free(p->d_geom);
+    if (p->d_pm) dev_free(p->d_pm);
     p->d_geom = nullptr;
     p->d_pm = nullptr;
     p->geom_cap = 0;
-    CU(cudaMalloc(&p->d_geom, (size_t)12 * n * sizeof(double)));   // 9n doubles + 6n floats
-    CU(cudaMalloc(&p->d_pm, (size_t)2 * n * sizeof(int)));
+    CU(dev_malloc(&p->d_geom, (size_t)12 * n * sizeof(double)));   // 9n doubles + 6n floats
+    CU(dev_malloc(&p->d_pm, (size_t)2 * n * sizeof(int)));
     p->geom_cap = n;
   }
   CU(cudaMemcpyAsync(p->d_geom, p->ax.data(), n * sizeof(double), cudaMemcpyHostToDevice, s));
@@ -245,14 +313,14 @@ bem_status assemble_impl(bem_problem* p, cudaStream_t s, bool force = false) {
   const size_t nn = (size_t)2 * p->n * 2 * p->n;
   const size_t need = mixed ? nn * sizeof(float2) : nn * sizeof(double2);
   if (need > p->A_cap || p->A_mixed != (int)mixed) {
-    if (p->d_A) cudaFree(p->d_A);
-    if (p->d_Alo) cudaFree(p->d_Alo);
+    if (p->d_A) dev_free(p->d_A);
+    if (p->d_Alo) dev_free(p->d_Alo);
     p->d_A = p->d_Alo = nullptr;
     p->A_cap = 0;
-    cudaError_t e = cudaMalloc(&p->d_A, need);
+    cudaError_t e = dev_malloc(&p->d_A, need);
     if (e != cudaSuccess) return fail(BEM_ENOMEM, "matrix allocation of %zu bytes failed", need);
     if (mixed) {
-      e = cudaMalloc(&p->d_Alo, need);
+      e = dev_malloc(&p->d_Alo, need);
       if (e != cudaSuccess) return fail(BEM_ENOMEM, "matrix allocation of %zu bytes failed", need);
     }
     p->A_cap = need;
@@ -274,17 +342,17 @@ bem_status ensure_a16(bem_problem* p, cudaStream_t s) {
   const int n2 = 2 * p->n;
   const size_t need = matvec_tc_a16_bytes(n2);
   if (need > p->A16_cap) {
-    if (p->d_A16) cudaFree(p->d_A16);
+    if (p->d_A16) dev_free(p->d_A16);
     p->d_A16 = nullptr;
     p->A16_cap = 0;
-    if (cudaMalloc(&p->d_A16, need) != cudaSuccess) return fail(BEM_ENOMEM, "matrix allocation of %zu bytes failed", need);
+    if (dev_malloc(&p->d_A16, need) != cudaSuccess) return fail(BEM_ENOMEM, "matrix allocation of %zu bytes failed", need);
     p->A16_cap = need;
   }
   if (need > p->Alo16_cap) {
-    if (p->d_Alo16) cudaFree(p->d_Alo16);
+    if (p->d_Alo16) dev_free(p->d_Alo16);
     p->d_Alo16 = nullptr;
     p->Alo16_cap = 0;
-    if (cudaMalloc(&p->d_Alo16, need) != cudaSuccess)
+    if (dev_malloc(&p->d_Alo16, need) != cudaSuccess)
       return fail(BEM_ENOMEM, "matrix allocation of %zu bytes failed", need);
     p->Alo16_cap = need;
   }
@@ -346,10 +414,10 @@ size_t krylov_bytes(int n2, int nrhs, int m, bool fp32) {
 
 bem_status ensure_ws(bem_problem* p, size_t bytes) {
   if (bytes <= p->ws_cap) return BEM_OK;
-  if (p->ws) cudaFree(p->ws);
+  if (p->ws) dev_free(p->ws);
   p->ws = nullptr;
   p->ws_cap = 0;
-  cudaError_t e = cudaMalloc(&p->ws, bytes);
+  cudaError_t e = dev_malloc(&p->ws, bytes);
   if (e != cudaSuccess) return fail(BEM_ENOMEM, "workspace allocation of %zu bytes failed", bytes);
   p->ws_cap = bytes;
   if (!p->h_pin) CU(cudaMallocHost(&p->h_pin, 64 * sizeof(int)));
@@ -726,12 +794,12 @@ bem_status problem_prepare_batched(bem_problem* p, cudaStream_t s, AsmJob* job, 
   const size_t nn = (size_t)2 * p->n * 2 * p->n;
   const size_t need = nn * sizeof(float2);
   if (need > p->A_cap || p->A_mixed != 1) {
-    if (p->d_A) cudaFree(p->d_A);
-    if (p->d_Alo) cudaFree(p->d_Alo);
+    if (p->d_A) dev_free(p->d_A);
+    if (p->d_Alo) dev_free(p->d_Alo);
     p->d_A = p->d_Alo = nullptr;
     p->A_cap = 0;
-    if (cudaMalloc(&p->d_A, need) != cudaSuccess || cudaMalloc(&p->d_Alo, need) != cudaSuccess) {
-      if (p->d_A) cudaFree(p->d_A);
+    if (dev_malloc(&p->d_A, need) != cudaSuccess || dev_malloc(&p->d_Alo, need) != cudaSuccess) {
+      if (p->d_A) dev_free(p->d_A);
       p->d_A = nullptr;
       return fail(BEM_ENOMEM, "matrix allocation of 2 x %zu bytes failed", need);
     }
@@ -782,14 +850,14 @@ BEM_API bem_status bem_problem_create(bem_problem** out, const bem_opts* opts) {
 
 BEM_API void bem_problem_destroy(bem_problem* p) {
   if (!p) return;
-  if (p->d_geom) cudaFree(p->d_geom);
-  if (p->d_pm) cudaFree(p->d_pm);
-  if (p->d_A) cudaFree(p->d_A);
-  if (p->d_Alo) cudaFree(p->d_Alo);
-  if (p->d_A16) cudaFree(p->d_A16);
-  if (p->d_Alo16) cudaFree(p->d_Alo16);
-  if (p->ws) cudaFree(p->ws);
-  if (p->d_small) cudaFree(p->d_small);
+  if (p->d_geom) dev_free(p->d_geom);
+  if (p->d_pm) dev_free(p->d_pm);
+  if (p->d_A) dev_free(p->d_A);
+  if (p->d_Alo) dev_free(p->d_Alo);
+  if (p->d_A16) dev_free(p->d_A16);
+  if (p->d_Alo16) dev_free(p->d_Alo16);
+  if (p->ws) dev_free(p->ws);
+  if (p->d_small) dev_free(p->d_small);
   if (p->h_pin) cudaFreeHost(p->h_pin);
   if (p->ig_exec) cudaGraphExecDestroy(p->ig_exec);
   for (cudaEvent_t e : p->ig_ev)
@@ -1031,7 +1099,7 @@ BEM_API bem_status bem_near_field(bem_problem* p, int n_rhs, const bem_c64* x_de
   // points, domains and angles travel in one temporary device block
   const size_t bytes = (size_t)2 * n_pts * sizeof(double) + (size_t)n_rhs * sizeof(double) + (size_t)n_pts * sizeof(int);
   char* blk = nullptr;
-  CU(cudaMallocAsync(&blk, bytes, s));
+  CU(dev_malloc_async(&blk, bytes, s));
   double* dp = reinterpret_cast<double*>(blk);
   double* da = dp + 2 * (size_t)n_pts;
   int* dd = reinterpret_cast<int*>(da + n_rhs);
@@ -1058,8 +1126,8 @@ BEM_API bem_status bem_solve_planewave_host(bem_problem* p, int n_rhs, const dou
   const size_t n2 = (size_t)2 * (p->n);
   double2* xd = nullptr;
   double2* ffd = nullptr;
-  CU(cudaMallocAsync(&xd, n_rhs * n2 * sizeof(double2), s));
-  if (ff_host) CU(cudaMallocAsync(&ffd, (size_t)n_rhs * n_ang * sizeof(double2), s));
+  CU(dev_malloc_async(&xd, n_rhs * n2 * sizeof(double2), s));
+  if (ff_host) CU(dev_malloc_async(&ffd, (size_t)n_rhs * n_ang * sizeof(double2), s));
   bem_status st = bem_solve_planewave(p, n_rhs, angles, reinterpret_cast<bem_c64*>(xd), iters, resid, stream);
   if (st == BEM_OK || st == BEM_ENOCONV) {
     if (ff_host) {
