@@ -669,13 +669,45 @@ BEM_HD void bessel01_asymp_f2x(double x, F2 X, Bessel01F2& b) {
 constexpr double kTabStep = 1.0 / 32.0;
 constexpr int kTabN = 1057;          // x_k = 2 + k / 32, k = 0 .. 1056: [2, 35]
 constexpr float kTabXMax = 35.0f;    // the table serves 2 <= x < 35
+// One grid point x_k: for each pair (J0, J1) and (Y0, Y1) the Taylor coefficients of orders 0..3 of Z0 (a_n)
+// and Z1 (b_n) as double-float (a_1 = -b_0 is not stored), c_3 (FP32, the start of the FP32 orders) and
+// 1/x_k (FP32).  The coefficients depend on x_k only, so they are made once on the host in FP64.
+struct alignas(16) BesselTabPair {
+  float a0h, a0l, b0h, b0l;
+  float b1h, b1l, a2h, a2l;
+  float b2h, b2l, a3h, a3l;
+  float b3h, b3l, c3, inv;   // inv = 1/x_k (both pairs)
+};
 struct alignas(16) BesselTabEntry {
-  float j0h, j0l, y0h, y0l, j1h, j1l, y1h, y1l, ixh, ixl, pad0, pad1;   // 48 bytes: three 16-byte loads
+  BesselTabPair j, y;   // 128 bytes: eight 16-byte loads
 };
 
 #if defined(__CUDACC__)
 static __device__ BesselTabEntry g_bessel_tab[kTabN];
 #endif
+
+// Taylor coefficients at x of a solution pair of Z0' = -Z1, Z1' = Z0 - Z1/x (DLMF 10.6.2) with values z0, z1:
+// with Z0 = sum a_n h^n, Z1 = sum b_n h^n and Z1/x = sum c_n h^n (x c_n + c_{n-1} = b_n),
+// a_{n+1} = -b_n/(n+1), b_{n+1} = (a_n - c_n)/(n+1).
+inline void taylor_coefs_host(double x, double z0, double z1, BesselTabPair& t) {
+  auto put = [](double v, float& h, float& l) {
+    h = (float)v;
+    l = (float)(v - (double)h);
+  };
+  const double a0 = z0, b0 = z1, c0 = b0 / x;
+  const double a1 = -b0, b1 = a0 - c0, c1 = (b1 - c0) / x;
+  const double a2 = -b1 / 2, b2 = (a1 - c1) / 2, c2 = (b2 - c1) / x;
+  const double a3 = -b2 / 3, b3 = (a2 - c2) / 3, c3 = (b3 - c2) / x;
+  put(a0, t.a0h, t.a0l);
+  put(b0, t.b0h, t.b0l);
+  put(b1, t.b1h, t.b1l);
+  put(a2, t.a2h, t.a2l);
+  put(b2, t.b2h, t.b2l);
+  put(a3, t.a3h, t.a3l);
+  put(b3, t.b3h, t.b3l);
+  t.c3 = (float)c3;
+  t.inv = (float)(1.0 / x);
+}
 
 // Host copy of the table (built on first use, thread-safe).
 inline const BesselTabEntry* bessel_tab_host() {
@@ -686,42 +718,22 @@ inline const BesselTabEntry* bessel_tab_host() {
       Bessel01 b;
       if (x < BEM_X_ASYMP) bessel01_miller(x, b);
       else bessel01_asymp(x, b);
-      auto put = [](double v, float& h, float& l) {
-        h = (float)v;
-        l = (float)(v - (double)h);
-      };
-      BesselTabEntry& e = t[k];
-      put(b.j0, e.j0h, e.j0l);
-      put(b.y0, e.y0h, e.y0l);
-      put(b.j1, e.j1h, e.j1l);
-      put(b.y1, e.y1h, e.y1l);
-      put(1.0 / x, e.ixh, e.ixl);
-      e.pad0 = e.pad1 = 0.f;
+      taylor_coefs_host(x, b.j0, b.j1, t[k].j);
+      taylor_coefs_host(x, b.y0, b.y1, t[k].y);
     }
     return t;
   }();
   return tab.data();
 }
 
-// Taylor coefficients and sums for one pair (Z0, Z1) from (z0, z1) at x_k; inv = 1/x_k; H = h.
-BEM_HD void taylor_pair(F2 z0, F2 z1, F2 inv, F2 H, F2& out0, F2& out1) {
-  constexpr F2 kInv2 = F2{0.5f, 0.f};
-  constexpr F2 kInv3 = f2_const(1.0 / 3.0);
-  // orders 0..3 in double-float
-  const F2 a0 = z0, b0 = z1;
-  const F2 c0 = f2_mul(b0, inv);
+// Taylor sums for one pair from the stored coefficients: orders 0..3 in double-float, orders 4..7 by the
+// same recurrence in FP32 (their terms are below 2^-24 of the sum for |h| <= 1/64); H = h.
+BEM_HD void taylor_pair(float4 q0, float4 q1, float4 q2, float4 q3, F2 H, F2& out0, F2& out1) {
+  const F2 a0{q0.x, q0.y}, b0{q0.z, q0.w}, b1{q1.x, q1.y}, a2{q1.z, q1.w};
+  const F2 b2{q2.x, q2.y}, a3{q2.z, q2.w}, b3{q3.x, q3.y};
   const F2 a1 = f2_neg(b0);
-  const F2 b1 = f2_sub(a0, c0);
-  const F2 c1 = f2_mul(f2_sub(b1, c0), inv);
-  const F2 a2 = f2_pow2(f2_neg(b1), 0.5f);
-  const F2 b2 = f2_mul(f2_sub(a1, c1), kInv2);
-  const F2 c2 = f2_mul(f2_sub(b2, c1), inv);
-  const F2 a3 = f2_mul(f2_neg(b2), kInv3);
-  const F2 b3 = f2_mul(f2_sub(a2, c2), kInv3);
-  const F2 c3 = f2_mul(f2_sub(b3, c2), inv);
-  // orders 4..7 in FP32
-  const float iv = inv.h, hf = H.h;
-  float an = -b3.h * 0.25f, bn = (a3.h - c3.h) * 0.25f, cn = (bn - c3.h) * iv;
+  const float c3 = q3.z, iv = q3.w, hf = H.h;
+  float an = -b3.h * 0.25f, bn = (a3.h - c3) * 0.25f, cn = (bn - c3) * iv;
   float a[4], bq[4];
   a[0] = an; bq[0] = bn;
 #pragma unroll
@@ -753,17 +765,17 @@ BEM_HD void bessel01_taylor_f2(double x, F2 X, Bessel01F2& b) {
 #if defined(__CUDA_ARCH__)
   const int k = __float2int_rn((X.h - 2.f) * 32.f);
   const float4* ep = reinterpret_cast<const float4*>(&g_bessel_tab[k]);
-  const float4 e0 = __ldg(ep), e1 = __ldg(ep + 1), e2 = __ldg(ep + 2);
-  const F2 j0{e0.x, e0.y}, y0{e0.z, e0.w}, j1{e1.x, e1.y}, y1{e1.z, e1.w}, inv{e2.x, e2.y};
+  const float4 e0 = __ldg(ep), e1 = __ldg(ep + 1), e2 = __ldg(ep + 2), e3 = __ldg(ep + 3);
+  const float4 e4 = __ldg(ep + 4), e5 = __ldg(ep + 5), e6 = __ldg(ep + 6), e7 = __ldg(ep + 7);
 #else
   const int k = (int)lrintf((X.h - 2.f) * 32.f);
-  const BesselTabEntry& e = bessel_tab_host()[k];
-  const F2 j0{e.j0h, e.j0l}, y0{e.y0h, e.y0l}, j1{e.j1h, e.j1l}, y1{e.y1h, e.y1l}, inv{e.ixh, e.ixl};
+  const float4* ep = reinterpret_cast<const float4*>(&bessel_tab_host()[k]);
+  const float4 e0 = ep[0], e1 = ep[1], e2 = ep[2], e3 = ep[3], e4 = ep[4], e5 = ep[5], e6 = ep[6], e7 = ep[7];
 #endif
   const double h = x - (2.0 + k * kTabStep);   // exact: x and the grid point agree to within 1/64
   const F2 H = f2_from_bits(h);
-  taylor_pair(j0, j1, inv, H, b.j0, b.j1);
-  taylor_pair(y0, y1, inv, H, b.y0, b.y1);
+  taylor_pair(e0, e1, e2, e3, H, b.j0, b.j1);
+  taylor_pair(e4, e5, e6, e7, H, b.y0, b.y1);
 }
 
 BEM_HD void bessel01_f2(double x, F2 X, Bessel01F2& b) {
