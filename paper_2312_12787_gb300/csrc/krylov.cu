@@ -324,17 +324,21 @@ __global__ void __launch_bounds__(CH / 2, sizeof(T) == sizeof(float2) ? 8 : 1) k
 // A system that converges at this step still gets V_{j+1}; nothing reads it.
 constexpr int kFinishMaxM = 1000;
 
-// One warp: h_{j+1,j} = hn.  The lanes stage column j and the rotations in shared memory (complex type C:
-// FP64, or FP32 for an FP32 basis) and apply the rotations as a scan (warp_rotate_column); lane 0 then forms
-// the new rotation.  g and the residual estimate stay FP64.
+// The inputs of the rotations of column j, staged by one warp (another warp than the one that computes
+// h_{j+1,j}, so the two sets of loads overlap): column j of H and the previous rotations in shared memory (complex
+// type C: FP64, or FP32 for an FP32 basis), and g_j, the previous residual estimate and the tolerance.
+struct FinishIn {
+  double2 gj;
+  double res;
+  double tl;
+};
 template <typename C>
-__device__ __forceinline__ void finish_column(const KrylovState& st, int s, int j, double hn, double tol, C* sh_h,
-                                              C* sh_c, C* sh_s) {
-  using R = decltype(C{}.x);
+__device__ __forceinline__ void finish_stage(const KrylovState& st, int s, int j, double tol, C* sh_h, C* sh_c,
+                                             C* sh_s, FinishIn* in) {
   const int lane = threadIdx.x & 31;
-  double2* Hj = st.H + ((size_t)s * st.m + j) * (st.m + 1);
-  double2* cs = st.cs + (size_t)s * st.m;
-  double2* sn = st.sn + (size_t)s * st.m;
+  const double2* Hj = st.H + ((size_t)s * st.m + j) * (st.m + 1);
+  const double2* cs = st.cs + (size_t)s * st.m;
+  const double2* sn = st.sn + (size_t)s * st.m;
   for (int i = lane; i <= j; i += 32) {
     const double2 h = Hj[i];
     sh_h[i] = cx<C>(h.x, h.y);
@@ -344,7 +348,22 @@ __device__ __forceinline__ void finish_column(const KrylovState& st, int s, int 
       sh_s[i] = cx<C>(si.x, si.y);
     }
   }
-  __syncwarp();
+  if (lane == 0) {
+    in->gj = st.g[(size_t)s * (st.m + 1) + j];
+    in->res = st.resid[s];
+    in->tl = st.tolv ? st.tolv[s] : tol;
+  }
+}
+
+// One warp, after finish_stage and a barrier: h_{j+1,j} = hn.  The lanes apply the previous rotations to the
+// staged column as a scan (warp_rotate_column); lane 0 then forms the new rotation.  g and the residual
+// estimate stay FP64.
+template <typename C>
+__device__ __forceinline__ void finish_column(const KrylovState& st, int s, int j, double hn, C* sh_h, C* sh_c,
+                                              C* sh_s, const FinishIn* in) {
+  using R = decltype(C{}.x);
+  const int lane = threadIdx.x & 31;
+  double2* Hj = st.H + ((size_t)s * st.m + j) * (st.m + 1);
   const C a = warp_rotate_column(sh_h, sh_c, sh_s, j);
   for (int i = lane; i < j; i += 32) Hj[i] = make_double2(sh_h[i].x, sh_h[i].y);
   if (lane != 0) return;
@@ -353,21 +372,20 @@ __device__ __forceinline__ void finish_column(const KrylovState& st, int s, int 
   double2 c, sv;
   if (den == (R)0) { c = make_double2(1, 0); sv = make_double2(0, 0); }
   else { c = make_double2(a.x * inv, a.y * inv); sv = make_double2((R)hn * inv, 0.0); }
-  cs[j] = c;
-  sn[j] = sv;
+  st.cs[(size_t)s * st.m + j] = c;
+  st.sn[(size_t)s * st.m + j] = sv;
   Hj[j] = make_double2(den, 0.0);
   Hj[j + 1] = make_double2(0.0, 0.0);
   double2* g = st.g + (size_t)s * (st.m + 1);
-  const double2 gj = g[j];
+  const double2 gj = in->gj;
   g[j + 1] = make_double2(-(sv.x * gj.x - sv.y * gj.y), -(sv.x * gj.y + sv.y * gj.x));
   g[j] = cdotc(c, gj);
   // |g_{j+1}| = |s_j| |g_j|: the estimate shrinks by the rotation's sine (resid starts at 1)
-  const double res = st.resid[s] * sv.x;
+  const double res = in->res * sv.x;
   st.resid[s] = res;
   st.iters[s] = j + 1;
   st.hnext[s] = hn;
-  const double tl = st.tolv ? st.tolv[s] : tol;
-  if (res <= tl || j + 1 >= st.m || hn == 0.0) {
+  if (res <= in->tl || j + 1 >= st.m || hn == 0.0) {
     st.active[s] = 0;
     atomicSub(st.n_active, 1);   // the gate of the queued iterations closes with the last system
   }
@@ -383,6 +401,7 @@ __global__ void __launch_bounds__(kThreads) k_step_end(KrylovState st, int nchun
   extern __shared__ __align__(16) unsigned char fin_raw[];
   T* fin_sh = reinterpret_cast<T*>(fin_raw);
   __shared__ F s_hn;
+  __shared__ FinishIn s_in;
   const int c = blockIdx.x, s = blockIdx.y;
   // read once, before the arrival below: the last CTA to arrive advances the index
   const int j = *(volatile const int*)st.jdev;
@@ -392,12 +411,14 @@ __global__ void __launch_bounds__(kThreads) k_step_end(KrylovState st, int nchun
       for (int cc = threadIdx.x; cc < nchunk; cc += 32) t += (F)st.npart[(size_t)s * nchunk + cc];
       t = warp_sum(t);
       if (threadIdx.x == 0) s_hn = sqrt(t);
+    } else if (c == 0 && threadIdx.x < 64) {
+      finish_stage(st, s, j, tol, fin_sh, fin_sh + (st.m + 1), fin_sh + 2 * (st.m + 1), &s_in);
     }
     __syncthreads();
     const F hn = s_hn;
     // the rotations are the long dependent chain of this kernel: start them before the scaling
     if (c == 0 && threadIdx.x < 32)
-      finish_column(st, s, j, (double)hn, tol, fin_sh, fin_sh + (st.m + 1), fin_sh + 2 * (st.m + 1));
+      finish_column(st, s, j, (double)hn, fin_sh, fin_sh + (st.m + 1), fin_sh + 2 * (st.m + 1), &s_in);
     if (hn > (F)0 && j + 1 < st.m) {
       const T* W = static_cast<const T*>(st.W) + (size_t)s * st.n;
       T* Vn = static_cast<T*>(st.V) + ((size_t)(j + 1) * st.nrhs + s) * st.n;
