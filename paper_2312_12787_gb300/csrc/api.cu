@@ -511,7 +511,7 @@ bem_status gmres_run(bem_problem* p, Solver& sv, const double2* r0, double2* x, 
     void* Vj = static_cast<char*>(st.V) + (size_t)j * nrhs * n2 * tb;
     cudaError_t e;
     {
-      Phase ph(p, BEM_PH_MATVEC, s, 1);
+      Phase ph(p, BEM_PH_MATVEC, s, use_tc ? 2 : 1);   // tensor cores: product and stream-K reduction
       if (p->o.matrix_free) {
         e = launch_matvec_free(p->elem(), p->n, p->dom, make_quad(p->o.quad_order), p->o.form, nrhs,
                                static_cast<const double2*>(Vj), static_cast<double2*>(st.W), s, gate);
@@ -528,11 +528,11 @@ bem_status gmres_run(bem_problem* p, Solver& sv, const double2* r0, double2* x, 
     }
     if (e != cudaSuccess) return e;
     {
-      Phase ph(p, BEM_PH_ARNOLDI, s, 3 * (passes == 1 ? 1 : 2));
+      Phase ph(p, BEM_PH_ARNOLDI, s, krylov_orth_launches(st, passes));
       e = krylov_orthogonalise(st, passes, s);
     }
     if (e != cudaSuccess) return e;
-    Phase ph(p, BEM_PH_GIVENS, s, 3);
+    Phase ph(p, BEM_PH_GIVENS, s, 1);
     return krylov_finish_step(st, tol, s);
   };
   if (use_tc && !p->prof) {
@@ -669,8 +669,10 @@ bem_status residual_mixed(bem_problem* p, Solver& sv, int nrhs, const double2* x
     if (tc_err) return fail(BEM_ETIMEOUT, "tensor-core GEMM wait expired (code %d)", tc_err);
     return BEM_OK;
   }
-  Phase ph(p, BEM_PH_RESIDUAL, s, 2);   // split of x, double-float product
-  CU(launch_residual_split(A, Alo, n2, n2, nrhs, x, b, r, sv.st.V, s, basis_bytes(sv)));
+  Phase ph(p, BEM_PH_RESIDUAL, s, 0);
+  int nl = 0;
+  CU(launch_residual_split(A, Alo, n2, n2, nrhs, x, b, r, sv.st.V, s, basis_bytes(sv), &nl));
+  ph.add_launches(nl);   // split of x, double-float product [, combination of the K splits]
   return BEM_OK;
 }
 

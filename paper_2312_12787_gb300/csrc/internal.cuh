@@ -138,7 +138,7 @@ cudaError_t launch_matvec_c32(const float2* A, size_t lda, int n, int nrhs, cons
 // With ws_bytes beyond the x split, the tiled product may split K over CTAs and keep FP64 partials there.
 cudaError_t launch_residual_split(const float2* Ahi, const float2* Alo, size_t lda, int n, int nrhs,
                                   const double2* x, const double2* b, double2* r, void* ws, cudaStream_t s,
-                                  size_t ws_bytes = 0);
+                                  size_t ws_bytes = 0, int* nlaunch = nullptr);
 // The same residual for problems with the tensor-core product: the small terms hi * x_lo + lo * x_hi are two
 // tensor-core products (a16 = FP16 split copy of hi, alo16 = the same of lo; tcws = a tensor-core workspace),
 // so the FP32-pipe kernel only sums the exact products hi * x_hi.  ws holds residual_tc_ws_bytes(n, nrhs)
@@ -221,7 +221,8 @@ cudaError_t krylov_start(const KrylovState& st, const double2* r0, double tol_un
 // passes: 1, 2, or 0 = one pass plus a second one for the systems whose w the first pass shrank below a tenth
 // of its length (selective reorthogonalisation).
 cudaError_t krylov_orthogonalise(const KrylovState& st, int passes, cudaStream_t s);
-cudaError_t krylov_finish_step(const KrylovState& st, double tol, cudaStream_t s);
+cudaError_t krylov_finish_step(const KrylovState& st, double tol, cudaStream_t s);   // one kernel
+int krylov_orth_launches(const KrylovState& st, int passes);   // kernels of krylov_orthogonalise
 cudaError_t krylov_update_solution(const KrylovState& st, double2* x, cudaStream_t s);
 
 // For the batch engine: validate, upload geometry and allocate the mixed-precision matrix of p (without

@@ -595,6 +595,11 @@ cudaError_t krylov_start(const KrylovState& st, const double2* r0, double, cudaS
 cudaError_t krylov_orthogonalise(const KrylovState& st, int passes, cudaStream_t s) {
   return st.basis_fp32 ? orth_t<float2>(st, passes, s) : orth_t<double2>(st, passes, s);
 }
+int krylov_orth_launches(const KrylovState& st, int passes) {
+  const int ch = chunk_of(st.n, st.nrhs);
+  const int nc = (st.n + ch - 1) / ch;
+  return (passes == 1 ? 1 : 2) * (nc <= 32 ? 2 : 3);   // projections, [reduction,] update per pass
+}
 cudaError_t krylov_finish_step(const KrylovState& st, double tol, cudaStream_t s) {
   return st.basis_fp32 ? finish_t<float2>(st, tol, s) : finish_t<double2>(st, tol, s);
 }

@@ -685,7 +685,7 @@ static int resid_splits(int n, int nrhs, size_t part_room, bool cross_terms) {
 
 cudaError_t launch_residual_split(const float2* Ahi, const float2* Alo, size_t lda, int n, int nrhs,
                                   const double2* x, const double2* b, double2* r, void* ws, cudaStream_t s,
-                                  size_t ws_bytes) {
+                                  size_t ws_bytes, int* nlaunch) {
   // ws holds x split into two complex FP32 blocks (2 * nrhs * n float2), then the K-split partials
   float2* xh = static_cast<float2*>(ws);
   float2* xl = xh + (size_t)nrhs * n;
@@ -701,6 +701,9 @@ cudaError_t launch_residual_split(const float2* Ahi, const float2* Alo, size_t l
     dim3 grd((n + kResBR - 1) / kResBR, (nrhs + kResBS - 1) / kResBS, S);
     k_resid_df_gemm<true><<<grd, 256, 0, s>>>(Ahi, Alo, lda, n, nrhs, xh, xl, b, r, S > 1 ? kchunk : n, part, nullptr);
     if (S > 1) k_resid_combine<<<1024, 256, 0, s>>>(part, S, (size_t)nrhs * n, b, r, nullptr);
+    if (nlaunch) *nlaunch = S > 1 ? 3 : 2;
+  } else if (nlaunch) {
+    *nlaunch = 2;
   }
   return cudaGetLastError();
 }
