@@ -693,6 +693,7 @@ cudaError_t launch_residual_split(const float2* Ahi, const float2* Alo, size_t l
   if (nrhs < 4) {
     dim3 grd((n + 7) / 8, nrhs);
     k_resid_df_gemv<<<grd, 256, 0, s>>>(Ahi, Alo, lda, n, xh, xl, b, r);
+    if (nlaunch) *nlaunch = 2;
   } else {
     const size_t xbytes = ((2 * (size_t)nrhs * n * sizeof(float2)) + 255) & ~(size_t)255;
     const int S = ws_bytes > xbytes ? resid_splits(n, nrhs, ws_bytes - xbytes, true) : 1;
@@ -702,8 +703,6 @@ cudaError_t launch_residual_split(const float2* Ahi, const float2* Alo, size_t l
     k_resid_df_gemm<true><<<grd, 256, 0, s>>>(Ahi, Alo, lda, n, nrhs, xh, xl, b, r, S > 1 ? kchunk : n, part, nullptr);
     if (S > 1) k_resid_combine<<<1024, 256, 0, s>>>(part, S, (size_t)nrhs * n, b, r, nullptr);
     if (nlaunch) *nlaunch = S > 1 ? 3 : 2;
-  } else if (nlaunch) {
-    *nlaunch = 2;
   }
   return cudaGetLastError();
 }
