@@ -1,16 +1,19 @@
 // GMRES without restart from x0 = 0 for a block of systems that share one matrix (paper Sec. 3.2,
 // eqs. preconditioned_krylov_space / unpreconditioned_krylov_space; Sec. 7: no restart).
 //
-// Arnoldi uses classical Gram-Schmidt with one re-orthogonalisation pass (CGS2) so that each pass is
-// two streaming sweeps over the basis instead of j dependent sweeps; the Hessenberg column, Givens
-// rotations and residual estimate are kept in FP64.  The basis may be complex FP64 (FP64 path) or
-// complex FP32 (mixed inner solves); products and warp reductions run in the basis precision, the
-// per-chunk partial sums are combined in FP64.
+// Arnoldi uses classical Gram-Schmidt, so that each pass is two streaming sweeps over the basis (projections,
+// update) instead of j dependent sweeps: twice (CGS2) for an FP64 basis, and for an FP32 basis once plus a
+// second pass only for the systems whose vector the first pass shrank below a tenth of its length.  The
+// basis may be complex FP64 (FP64 path) or complex FP32 (mixed inner solves); products and warp reductions
+// run in the basis precision, the per-chunk partial sums are combined in FP64.  The Hessenberg column, g and
+// the residual estimate are FP64; the rotations run in the basis precision.
 //
-// Work split: a vector of n unknowns is cut into chunks of 64 entries; one CTA of 256 threads owns one
-// chunk of one system (grid = chunks x systems), so even a single system of 8192 unknowns spreads over
-// 128 CTAs.  In the projection kernel each warp owns every eighth basis vector (no block barriers); in
-// the update kernel four thread groups share the basis vectors of a chunk and meet in shared memory.
+// Work split: a vector of n unknowns is cut into chunks (512, 256, 128 or 64 entries, the largest that
+// still gives two CTAs per SM over all systems); one CTA owns one chunk of one system (grid = chunks x
+// systems).  In the projection kernel the chunk of w is staged in shared memory and each warp owns every
+// eighth basis vector; in the update kernel each thread owns a pair of entries over all basis vectors.  One
+// kernel ends each iteration (norm, next basis vector, rotations, iteration index).  The kernels of an
+// iteration read the iteration index from the device and use programmatic dependent launch.
 #include <algorithm>
 #include <atomic>
 
