@@ -109,6 +109,8 @@ struct bem_problem {
   int* h_pin = nullptr;        // pinned host mirror of counters
   // tensor-core GMRES iterations recorded as a CUDA graph (replayed on an internal stream)
   cudaGraphExec_t ig_exec = nullptr;
+  bool ig_loop = false;      // ig_exec is one device-side loop over iterations (conditional WHILE node)
+  bool ig_noloop = false;    // building the loop failed once on this device: use replays of 8 iterations
   const void* ig_ws = nullptr;
   const void* ig_a16 = nullptr;
   int ig_n2 = 0, ig_nrhs = 0, ig_m = 0, ig_passes = -1;
@@ -540,6 +542,7 @@ bem_status gmres_run(bem_problem* p, Solver& sv, const double2* r0, double2* x, 
     // recorded once per workspace layout as a CUDA graph and replayed on an internal stream ordered after s.
     // The host reads the active count of one replay while the next one runs.
     constexpr int kGraphIters = 8;
+    constexpr int kLoopIters = 4;
     if (!p->ig_stream) {
       CU(cudaStreamCreateWithFlags(&p->ig_stream, cudaStreamNonBlocking));
       for (cudaEvent_t& e : p->ig_ev) CU(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
@@ -554,15 +557,56 @@ bem_status gmres_run(bem_problem* p, Solver& sv, const double2* r0, double2* x, 
       CU(matvec_tc_setup());
       const cudaStream_t user = s;
       s = gs;   // the iteration body launches on the capturing stream
-      CU(cudaStreamBeginCapture(gs, cudaStreamCaptureModeThreadLocal));
-      cudaError_t ce = cudaSuccess;
-      for (int k = 0; k < kGraphIters && ce == cudaSuccess; ++k) ce = iteration(0);
-      cudaGraph_t graph = nullptr;
-      const cudaError_t ee = cudaStreamEndCapture(gs, &graph);
+      cudaError_t ce = cudaErrorNotSupported;
+      if (!p->ig_noloop) {
+        // One graph for the whole inner solve: a WHILE node whose body is kLoopIters iterations; the
+        // end-of-iteration kernel sets the loop condition to (some system still iterating), so the host does
+        // not poll and at most kLoopIters - 1 gated iterations run past convergence (one iteration per body
+        // made each pass through the loop cost more than the iterations it saved).
+        cudaGraph_t graph = nullptr;
+        cudaGraphConditionalHandle h = 0;
+        ce = cudaGraphCreate(&graph, 0);
+        if (ce == cudaSuccess) ce = cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault);
+        cudaGraphNodeParams cp = {};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        cudaGraphNode_t node = nullptr;
+        if (ce == cudaSuccess) ce = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp);
+        if (ce == cudaSuccess) {
+          cudaGraph_t body = cp.conditional.phGraph_out[0];
+          ce = cudaStreamBeginCaptureToGraph(gs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+          if (ce == cudaSuccess) {
+            st.cond_handle = (unsigned long long)h;
+            cudaError_t ie = cudaSuccess;
+            for (int k = 0; k < kLoopIters && ie == cudaSuccess; ++k) ie = iteration(0);
+            st.cond_handle = 0;
+            cudaGraph_t out = nullptr;
+            const cudaError_t ee = cudaStreamEndCapture(gs, &out);
+            ce = ie != cudaSuccess ? ie : ee;
+          }
+        }
+        if (ce == cudaSuccess) ce = cudaGraphInstantiate(&p->ig_exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (ce != cudaSuccess) {
+          p->ig_exec = nullptr;
+          p->ig_noloop = true;
+          (void)cudaGetLastError();   // clear the failure; the replay form below is recorded instead
+        }
+        p->ig_loop = ce == cudaSuccess;
+      }
+      if (!p->ig_loop) {
+        CU(cudaStreamBeginCapture(gs, cudaStreamCaptureModeThreadLocal));
+        ce = cudaSuccess;
+        for (int k = 0; k < kGraphIters && ce == cudaSuccess; ++k) ce = iteration(0);
+        cudaGraph_t graph = nullptr;
+        const cudaError_t ee = cudaStreamEndCapture(gs, &graph);
+        if (ce == cudaSuccess) ce = ee;
+        if (ce == cudaSuccess) ce = cudaGraphInstantiate(&p->ig_exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+      }
       s = user;
-      if (ce == cudaSuccess) ce = ee;
-      if (ce == cudaSuccess) ce = cudaGraphInstantiate(&p->ig_exec, graph, 0);
-      if (graph) cudaGraphDestroy(graph);
       if (ce != cudaSuccess) {
         p->ig_exec = nullptr;
         return fail(BEM_ECUDA, "recording the GMRES iteration graph failed: %s", cudaGetErrorString(ce));
@@ -572,13 +616,17 @@ bem_status gmres_run(bem_problem* p, Solver& sv, const double2* r0, double2* x, 
     }
     CU(cudaEventRecord(p->ig_ev[2], s));
     CU(cudaStreamWaitEvent(gs, p->ig_ev[2], 0));
-    for (int j = 0, r = 0; j < st.m; j += kGraphIters, ++r) {
+    if (p->ig_loop) {
       CU(cudaGraphLaunch(p->ig_exec, gs));
-      CU(cudaMemcpyAsync(p->h_pin + (r & 1), st.n_active, sizeof(int), cudaMemcpyDeviceToHost, gs));
-      CU(cudaEventRecord(p->ig_ev[r & 1], gs));
-      if (r > 0) {
-        CU(cudaEventSynchronize(p->ig_ev[(r - 1) & 1]));
-        if (p->h_pin[(r - 1) & 1] == 0) break;
+    } else {
+      for (int j = 0, r = 0; j < st.m; j += kGraphIters, ++r) {
+        CU(cudaGraphLaunch(p->ig_exec, gs));
+        CU(cudaMemcpyAsync(p->h_pin + (r & 1), st.n_active, sizeof(int), cudaMemcpyDeviceToHost, gs));
+        CU(cudaEventRecord(p->ig_ev[r & 1], gs));
+        if (r > 0) {
+          CU(cudaEventSynchronize(p->ig_ev[(r - 1) & 1]));
+          if (p->h_pin[(r - 1) & 1] == 0) break;
+        }
       }
     }
     CU(cudaEventRecord(p->ig_ev[2], gs));

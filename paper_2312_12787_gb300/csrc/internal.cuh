@@ -210,6 +210,9 @@ struct KrylovState {
   int* n_active;    // device count of active systems (the gate of queued iterations)
   int* jdev;        // current iteration index (set by the start kernel, advanced after each iteration)
   int* arrive_all;  // systems whose end-of-iteration CTAs are all done (the last one advances jdev)
+  // when non-zero: the cudaGraphConditionalHandle of the graph's loop over iterations; the end-of-iteration
+  // kernel sets it to (some system still iterating)
+  unsigned long long cond_handle;
   // when non-null (FP32 basis feeding the tensor-core product): every new basis vector is also written as
   // the FP16 x 3 operand of the next product (tc_operand.cuh), rows of stride ldb16
   void* b16hi;

@@ -447,11 +447,17 @@ __global__ void __launch_bounds__(kThreads) k_step_end(KrylovState st, int nchun
   }
   __syncthreads();
   if (threadIdx.x == 0) {
+    // with a graph loop, the last CTA reads the active count: the rotations' decrements must be visible
+    if (st.cond_handle) __threadfence();
     if (atomicAdd(st.arrive + s, 1) == (int)gridDim.x - 1) {
       st.arrive[s] = 0;
       if (atomicAdd(st.arrive_all, 1) == (int)gridDim.y - 1) {
         *st.arrive_all = 0;
         *st.jdev = j + 1;
+        if (st.cond_handle) {
+          __threadfence();
+          cudaGraphSetConditional((cudaGraphConditionalHandle)st.cond_handle, atomicAdd(st.n_active, 0) > 0 ? 1u : 0u);
+        }
       }
     }
   }

@@ -197,6 +197,39 @@ def test_full_size_star_sampled_rows(B, torch):
     p.close()
 
 
+def test_full_size_star_solve_in_bench_configuration(B, torch):
+    """The measured configuration itself: star, 4096 elements, 64 plane waves, mixed path with the tensor-core
+    product and CUDA-graph iterations, tol 1e-8.  Properties that hold at any size, checked on sampled rows with
+    the oracle's rows computed one by one: the oracle's residual b - A x of the GPU solution is within the
+    tolerance on every sampled row and column, and the GPU far field equals the oracle's far-field formula
+    applied to the GPU traces."""
+    wp = W.cfg_star_c2()
+    ang = W.plane_wave_angles(64)
+    p = B.Problem.from_workload(wp, prec="mixed_tc", tol=1e-8)
+    n2 = p.bem_num_unknowns()
+    x = torch.empty((64, n2), dtype=torch.complex128, device="cuda")
+    st, it, rs = p.bem_solve_planewave(ang, x)
+    assert st == B.BEM_OK and np.all(rs <= 1e-8) and np.all(it > 0)
+    ffa = np.linspace(0.0, 2 * np.pi, 32, endpoint=False)
+    ff = torch.empty((64, 32), dtype=torch.complex128, device="cuda")
+    p.bem_far_field(x, ffa, ff, n_rhs=64)
+    xs = x.cpu().numpy()
+    ffs = ff.cpu().numpy()
+    p.close()
+    rng = np.random.default_rng(21)
+    rows = np.sort(np.concatenate([[0, n2 // 2 - 1, n2 // 2, n2 - 1], rng.choice(n2, 12, replace=False)]))
+    Ar = O.assemble_rows(wp, rows, Q=4)
+    el = O.elements(wp)
+    for c in rng.choice(64, 6, replace=False):
+        b = O.rhs_planewave(wp, ang[c], el=el)
+        r_rows = b[rows] - Ar @ xs[c]
+        # |r_i| <= ||r||_2 <= tol ||b||_2 for the solver's residual; the oracle's matrix differs from the
+        # GPU's by ~1e-13 of an entry, far below that
+        assert np.max(np.abs(r_rows)) <= 2e-8 * np.linalg.norm(b), (c, np.max(np.abs(r_rows)) / np.linalg.norm(b))
+        ref_ff = O.far_field(wp, xs[c], ffa, Q=4, el=el)
+        assert np.max(np.abs(ffs[c] - ref_ff)) <= 1e-10 * np.max(np.abs(ref_ff))
+
+
 def test_invalid_mesh_rejected_on_device_path(B, torch):
     wp = W.circle_problem(8, 40.0, 80.0)     # elements several wavelengths long
     p = B.Problem.from_workload(wp)
