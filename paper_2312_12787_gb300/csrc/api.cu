@@ -177,8 +177,8 @@ struct Phase {
 // library that keeps up to kPoolKeepBytes of freed blocks, so a problem created after another one was
 // destroyed (a serving loop, the host-buffer entry point) reuses the memory instead of mapping new pages.
 // dev_malloc and dev_free are synchronous like cudaMalloc and cudaFree: the allocation is made on an
-// internal stream and waited for (usable on every stream on return); a free first waits for the device to
-// be idle, as cudaFree does.  Without pool support they are cudaMalloc and cudaFree.
+// internal stream and waited for (usable on every stream on return); the release is cudaFree.  Without pool
+// support they are cudaMalloc and cudaFree.
 constexpr uint64_t kPoolKeepBytes = 32ull << 30;
 constexpr int kPoolDevs = 64;
 struct DevPool {
@@ -227,15 +227,10 @@ template <typename T> cudaError_t dev_malloc_async(T** ptr, size_t bytes, cudaSt
   return cudaMallocFromPoolAsync(reinterpret_cast<void**>(ptr), bytes, d->pool, s);
 }
 
+// cudaFree also takes stream-ordered allocations back into their pool (after its implicit synchronisation);
+// unlike an explicit device synchronisation it leaves stream captures of other threads intact.
 void dev_free(void* ptr) {
-  if (!ptr) return;
-  DevPool* d = dev_pool();
-  if (!d) {
-    cudaFree(ptr);
-    return;
-  }
-  cudaDeviceSynchronize();
-  if (cudaFreeAsync(ptr, d->s) == cudaSuccess) cudaStreamSynchronize(d->s);
+  if (ptr) cudaFree(ptr);
 }
 
 Quad make_quad(int Q) { return bem::make_quad_host(Q); }
