@@ -183,15 +183,21 @@ __global__ void __launch_bounds__(kThreads, 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap mapAh, const __grid_constant__ CUtensorMap mapAl,
               const __grid_constant__ CUtensorMap mapBh, const __grid_constant__ CUtensorMap mapBl, int n,
               int kpt, long long total, float* partial, int* err, const int* gate) {
-  pdl_enter();
-  if (gate && *gate == 0) return;   // every system of the block has converged (uniform for the grid)
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   Bars* bars = reinterpret_cast<Bars*>(smem + kStages * kStage);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int G = gridDim.x, c = blockIdx.x;
-  const long long gb = total * c / G, ge = total * (c + 1) / G;
-  const int kb = (int)gb, nk = (int)(ge - gb);
+  int kb, nk;
+  if ((unsigned long long)total * (unsigned long long)G < (1ull << 32)) {   // 32-bit divisions where they fit
+    const unsigned t = (unsigned)total, g = (unsigned)G;
+    kb = (int)(t * (unsigned)c / g);
+    nk = (int)(t * (unsigned)(c + 1) / g) - kb;
+  } else {
+    const long long gb = total * c / G, ge = total * (c + 1) / G;
+    kb = (int)gb;
+    nk = (int)(ge - gb);
+  }
   const int tile0 = kb / kpt;
 
   if (threadIdx.x == 0) {
@@ -216,6 +222,14 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = bars->tmem;
+  // The set-up above overlaps the previous kernel's tail; its outputs (the B operand, the gate) are read only
+  // from here on.
+  pdl_enter();
+  if (gate && *gate == 0) {   // every system of the block has converged (uniform for the grid)
+    if (warp == 1)
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+    return;
+  }
   int issued = 0;   // TMA stages issued by the producer thread
 
   if (warp == 0) {
