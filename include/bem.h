@@ -248,7 +248,8 @@ typedef enum {
   BEM_PH_RESIDUAL = 7,  /* a9: refinement residual b - (hi + lo) x (its norms count as OTHER) */
   BEM_PH_FARFIELD = 8,  /* a10 */
   BEM_PH_OTHER = 9,     /* conversions, copies, column norms, the FP16 split copy of A */
-  BEM_PH_COUNT = 10
+  BEM_PH_REDUCE = 10,   /* a11: stream-K reduction of the tensor-core GEMM inside GMRES (the GEMM is MATVEC) */
+  BEM_PH_COUNT = 11
 } bem_phase;
 BEM_API bem_status bem_profile_enable(bem_problem* p, int on);
 BEM_API bem_status bem_profile_read(bem_problem* p, double* ms_host, long long* launches_host);

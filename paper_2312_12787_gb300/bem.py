@@ -29,7 +29,8 @@ EXPORTS = [
     "bem_batch_create", "bem_batch_destroy", "bem_batch_admit", "bem_batch_step", "bem_batch_query",
     "bem_batch_take", "bem_batch_free_units", "bem_batch_solve_planewave",
 ]
-PHASES = ["geometry", "assemble", "rhs", "matvec", "arnoldi", "givens", "update", "residual", "farfield", "other"]
+PHASES = ["geometry", "assemble", "rhs", "matvec", "arnoldi", "givens", "update", "residual", "farfield", "other",
+          "reduce"]
 
 
 class BemError(RuntimeError):

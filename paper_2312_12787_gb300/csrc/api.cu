@@ -507,17 +507,24 @@ bem_status gmres_run(bem_problem* p, Solver& sv, const double2* r0, double2* x, 
   auto iteration = [&](int j) -> cudaError_t {
     void* Vj = static_cast<char*>(st.V) + (size_t)j * nrhs * n2 * tb;
     cudaError_t e;
-    {
-      Phase ph(p, BEM_PH_MATVEC, s, use_tc ? 2 : 1);   // tensor cores: product and stream-K reduction
+    if (use_tc) {   // the GEMM (B = V_j, written by the Krylov kernels), then its stream-K reduction
+      {
+        Phase ph(p, BEM_PH_MATVEC, s, 1);
+        e = launch_matvec_tc(p->d_A16, n2, nrhs, nullptr, static_cast<float2*>(st.W), sv.tcws, sv.tcws_bytes, s,
+                             gate, 1);
+      }
+      if (e != cudaSuccess) return e;
+      Phase ph(p, BEM_PH_REDUCE, s, 1);
+      e = launch_matvec_tc(p->d_A16, n2, nrhs, nullptr, static_cast<float2*>(st.W), sv.tcws, sv.tcws_bytes, s,
+                           gate, 2);
+    } else {
+      Phase ph(p, BEM_PH_MATVEC, s, 1);
       if (p->o.matrix_free) {
         e = launch_matvec_free(p->elem(), p->n, p->dom, make_quad(p->o.quad_order), p->o.form, nrhs,
                                static_cast<const double2*>(Vj), static_cast<double2*>(st.W), s, gate);
       } else if (!fp32) {
         e = launch_matvec_c64(static_cast<const double2*>(p->d_A), n2, n2, nrhs, static_cast<const double2*>(Vj),
                               static_cast<double2*>(st.W), s, gate);
-      } else if (use_tc) {
-        e = launch_matvec_tc(p->d_A16, n2, nrhs, nullptr, static_cast<float2*>(st.W), sv.tcws, sv.tcws_bytes, s,
-                             gate);   // B = V_j, written by the Krylov kernels
       } else {
         e = launch_matvec_c32(static_cast<const float2*>(p->d_A), n2, n2, nrhs, static_cast<const float2*>(Vj),
                               static_cast<float2*>(st.W), st.active, s, gate);
@@ -1033,8 +1040,9 @@ BEM_API bem_status bem_matvec(bem_problem* p, int n_rhs, const bem_c64* x_dev, b
     CU(launch_convert_c64_c32(x, xf, (size_t)n_rhs * n2, s));
   }
   {
-    Phase ph(p, BEM_PH_MATVEC, s, 1);
-    if (p->o.prec == BEM_PREC_MIXED_TC && n_rhs > 1 && matvec_tc_supported(n2, n_rhs)) {
+    const bool tc = p->o.prec == BEM_PREC_MIXED_TC && n_rhs > 1 && matvec_tc_supported(n2, n_rhs);
+    Phase ph(p, BEM_PH_MATVEC, s, tc ? 4 : 1);   // tensor cores: column maxima, operand, GEMM, reduction
+    if (tc) {
       st = ensure_a16(p, s);
       if (st != BEM_OK) return st;
       CU(matvec_tc_clear_error(sv.tcws, n2, n_rhs, s));

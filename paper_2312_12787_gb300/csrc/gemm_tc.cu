@@ -599,7 +599,7 @@ cudaError_t launch_tc_prepare_a(const float2* A, int n, void* a16, cudaStream_t 
 }
 
 cudaError_t launch_matvec_tc(const void* a16, int n, int nrhs, const float2* x, float2* y, void* ws,
-                             size_t ws_bytes, cudaStream_t s, const int* gate) {
+                             size_t ws_bytes, cudaStream_t s, const int* gate, int stage) {
   if (!matvec_tc_supported(n, nrhs)) return cudaErrorNotSupported;
   if (ws_bytes < matvec_tc_workspace_bytes(n, nrhs)) return cudaErrorInvalidValue;
   const size_t ld = ld16(n);
@@ -615,15 +615,18 @@ cudaError_t launch_matvec_tc(const void* a16, int n, int nrhs, const float2* x, 
   float* tsc = reinterpret_cast<float*>(w + off_tsc(n));
   int* err = reinterpret_cast<int*>(w + off_err(n));
   const int cols = 2 * n;
+  const int tiles = (n + kM - 1) / kM;
+  const int kpt = (cols + kKs - 1) / kKs;
+  const long long total = (long long)tiles * kpt;
+  const int G = grid_of(n);
+  if (stage == 2)   // the reduction alone (its partials come from a stage-1 call with the same arguments)
+    return launch_pdl(k_tc_reduce, dim3((n + kRedRows - 1) / kRedRows), dim3(256), 0, s, part, n, nrhs, kpt, total,
+                      G, rsc, x ? tsc : static_cast<const float*>(nullptr), y, gate);
   CUtensorMap mAh, mAl, mBh, mBl;
   if (!make_map16(&mAh, ahi, cols, ld, n) || !make_map16(&mAl, alo, cols, ld, n) ||
       !make_map16(&mBh, bhi, cols, ld, kN) || !make_map16(&mBl, blo, cols, ld, kN))
     return cudaErrorInvalidValue;
   if (!smem_attr_set()) return cudaErrorInvalidValue;
-  const int tiles = (n + kM - 1) / kM;
-  const int kpt = (cols + kKs - 1) / kKs;
-  const long long total = (long long)tiles * kpt;
-  const int G = grid_of(n);
   if (x) {
     cudaError_t e = cudaMemsetAsync(cmax, 0, 64 * sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
@@ -634,7 +637,7 @@ cudaError_t launch_matvec_tc(const void* a16, int n, int nrhs, const float2* x, 
   }
   cudaError_t e = launch_pdl(k_gemm_tc, dim3(G), dim3(kThreads), kSmemBytes, s, mAh, mAl, mBh, mBl, n, kpt, total,
                              part, err, gate);
-  if (e != cudaSuccess) return e;
+  if (e != cudaSuccess || stage == 1) return e;
   return launch_pdl(k_tc_reduce, dim3((n + kRedRows - 1) / kRedRows), dim3(256), 0, s, part, n, nrhs, kpt, total, G,
                     rsc, x ? tsc : static_cast<const float*>(nullptr), y, gate);
 }

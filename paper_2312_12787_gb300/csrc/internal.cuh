@@ -160,9 +160,10 @@ cudaError_t launch_residual_split_f64(const float2* Ahi, const float2* Alo, size
 // error word inside ws and never clears it: callers clear it (matvec_tc_clear_error) before a run of
 // products and read it (matvec_tc_error_word) afterwards.
 // x == nullptr: the block's B operand is already in ws in the FP16 x 3 format with scale 1 (the Krylov kernels
-// write it for unit-norm basis vectors; matvec_tc_b_operand gives its place).
+// write it for unit-norm basis vectors; matvec_tc_b_operand gives its place).  stage 0: the whole product;
+// 1: operand preparation and the GEMM; 2: the stream-K reduction of a stage-1 call with the same arguments.
 cudaError_t launch_matvec_tc(const void* a16, int n, int nrhs, const float2* x, float2* y, void* ws,
-                             size_t ws_bytes, cudaStream_t s, const int* gate = nullptr);
+                             size_t ws_bytes, cudaStream_t s, const int* gate = nullptr, int stage = 0);
 void matvec_tc_b_operand(void* ws, int n, void** bhi, void** blo, size_t* ldb);
 size_t matvec_tc_b_bytes(int n);
 // One-time settings of the tensor-core kernel (shared-memory limit); call before recording it in a graph.

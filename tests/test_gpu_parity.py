@@ -260,7 +260,7 @@ def test_matvec_tensor_core_matches_reference(B, torch, ne, nrhs):
         p.bem_profile_enable(True)
         p.bem_matvec(x, y, n_rhs=nrhs)
         prof = p.bem_profile_read()
-        assert prof["matvec"][1] == 1
+        assert prof["matvec"][1] == 4   # column maxima, B operand, GEMM, stream-K reduction
         ref = (A @ x.T).T
         err = (torch.linalg.vector_norm(y - ref, dim=1) / torch.linalg.vector_norm(ref, dim=1)).max().item()
         # 22-bit split operands with FP32 tensor-core accumulation over 256-value segments (the previous
