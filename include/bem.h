@@ -156,7 +156,9 @@ BEM_API bem_status bem_matvec(bem_problem* p, int n_rhs, const bem_c64* x_dev, b
 BEM_API bem_status bem_residual(bem_problem* p, int n_rhs, const bem_c64* x_dev, const bem_c64* b_dev, bem_c64* r_dev,
                                 void* stream);
 
-/* The same residual as bem_residual (mixed-precision problems only) without any device allocation.  The
+/* The same residual as bem_residual (mixed-precision problems only; for MIXED_TC with n_rhs >= 2, where
+ * bem_residual forms the small terms hi x_lo + lo x_hi on the tensor cores, this one forms them on the FP32
+ * pipes, and the two agree to the residual's accuracy) without any device allocation.  The
  * paper has no counterpart: this is a library facility.  bem_residual takes its scratch from the problem's
  * solver workspace and may allocate it; callers that cannot allocate at that point (memory handed to their
  * own arena or caching allocator, latency-bound loops where cudaMalloc would stall, processes near their
