@@ -34,16 +34,16 @@ METRIC = "BEM solves/s (mixed vs FP64 GPU at err<=1e-6)"
 # Roofline inputs, from ncu counts of one launch on the star r = 1 + 0.3 cos 5t with N_e = 3072 (64 RHS),
 # scaled to other sizes by the number of matrix entries (profiles/assemble_star3072.md,
 # profiles/gemm_tc_star3072_64rhs.md):
-#  * k_assemble issues 2.912e9 warp instructions (sm__inst_executed.sum) over both the FP64 pipe (node
+#  * k_assemble issues 2.547e9 warp instructions (sm__inst_executed.sum) over both the FP64 pipe (node
 #    geometry, phase reduction) and the FP32 pipe (double-float Bessel arithmetic); neither pipe alone binds,
-#    so its roofline is the issue rate: 4 warp instructions per clock per SM.  DRAM traffic 551.8 MB.
+#    so its roofline is the issue rate: 4 warp instructions per clock per SM.  DRAM traffic 550.4 MB.
 #  * the multi-RHS GEMM streams A once: 2 x 2 bytes per real entry; measured DRAM traffic 316.3 MB.
 #  * the refinement residual runs 16 FP32 operations per complex multiply-add on the FP32 pipe (four exact
 #    products summed with an offset accumulator, four operations each; the per-run offsets and the
 #    double-float fold are not counted), 128 operations per clock per SM; with the tensor-core product the
 #    small terms hi x_lo + lo x_hi are two FP16x3 GEMMs (11 kernels per residual, 12 with a K split).
-ASM_WARP_INST_N3072 = 2.91162048e9
-ASM_DRAM_BYTES_N3072 = 550810112 + 970496
+ASM_WARP_INST_N3072 = 2.546915828e9
+ASM_DRAM_BYTES_N3072 = 549714432 + 713728
 GEMM_DRAM_BYTES_N3072 = 311.3e6 + 5.0e6
 RESID_FP32_OPS_PER_CMAC = 16
 RESID_LAUNCHES_TC = 11
