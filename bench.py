@@ -208,6 +208,39 @@ def run_batched_workload(args):
     Bd.build()
     P.load()
     torch.cuda.set_device(0)
+    if args.workload == "omega_eps":
+        # Sec. 7.1's iteration study (GMRES iterations vs omega and vs eps_2 on the unit circle) for the proposed
+        # ("mod") and the conventional ("conv") arrangement, each as one batch of all its problems
+        cases = W.cfg_omega_eps_sweep()
+        out = {}
+        for form in ("mod", "conv"):
+            res = {}
+            for leg in ("warmup", "timed"):
+                probs = [P.Problem.from_workload(wp, prec="mixed", form=form, tol=args.tol, max_iter=1000)
+                         for _, _, wp in cases]
+                xs = [torch.empty(p.bem_num_unknowns(), dtype=torch.complex128, device="cuda") for p in probs]
+                bt = P.Batch(len(probs), sum(p.bem_num_unknowns() for p in probs), form=form, tol=args.tol,
+                             max_iter=1000)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                st, it, rs = bt.bem_batch_solve_planewave(probs, np.zeros(len(probs)), xs)
+                torch.cuda.synchronize()
+                res[leg] = (time.perf_counter() - t0, it, rs)
+                bt.close()
+                for p in probs:
+                    p.close()
+            t, it, rs = res["timed"]
+            kinds = np.array([c[0] for c in cases])
+            out[form] = {"solves_per_s": len(cases) / t, "wall_s": t, "max_rel_resid": float(np.max(rs)),
+                         "iters_vs_omega": [int(v) for v in it[kinds == "omega"]],
+                         "iters_vs_eps": [int(v) for v in it[kinds == "eps"]]}
+        line = {"metric": "omega / eps_2 sweeps of the unit circle (one batch per arrangement, mixed)",
+                "value": out["mod"]["solves_per_s"], "unit": "solves/s", "tol": args.tol, "results": out,
+                "omega": [c[1] for c in cases if c[0] == "omega"], "eps_2": [c[1] for c in cases if c[0] == "eps"],
+                "config": {"workload": "unit circle, 600 elements, Q = 4: 64 omega in [0.5, 20] (eps_2 = 2) and "
+                                       "64 eps_2 in [1.1, 10] (omega = 5)"}}
+        print(json.dumps(line), flush=True)
+        return
     if args.workload == "sweep":
         stars = W.cfg_random_stars_c4()
         res = {}
@@ -262,9 +295,10 @@ def main():
     ap.add_argument("--max-iter", type=int, default=400)
     ap.add_argument("--inner-tol", type=float, default=1e-5, help="inner GMRES tolerance of the mixed path")
     ap.add_argument("--orth-passes", type=int, default=0, help="Gram-Schmidt passes of the mixed path (0 = auto)")
-    ap.add_argument("--workload", default="star", choices=["star", "serving", "sweep"],
+    ap.add_argument("--workload", default="star", choices=["star", "serving", "sweep", "omega_eps"],
                     help="star: the 64-RHS star (default line); serving: Poisson request stream; "
-                         "sweep: 256 random stars in one batch")
+                         "sweep: 256 random stars in one batch; omega_eps: Sec. 7.1's omega and eps_2 sweeps "
+                         "of the unit circle, one batch per arrangement")
     ap.add_argument("--requests", type=int, default=200, help="serving: number of requests")
     ap.add_argument("--n-rhs", type=int, default=64, help="star: incident angles per step (64 = the workload)")
     args = ap.parse_args()

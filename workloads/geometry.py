@@ -177,6 +177,19 @@ def cfg_random_stars_c4(count: int = 256, seed: int = 2312, n_min: int = 128, n_
     return out
 
 
+def cfg_omega_eps_sweep(n: int = 600, count: int = 64):
+    """The single-material iteration study of Sec. 7.1 as one workload: the unit circle of n elements,
+    (a) `count` angular frequencies omega in [0.5, 20] with eps_2 = 2, and (b) `count` contrasts eps_2 in
+    [1.1, 10] with omega = 5.  The paper plots both (ranges read off its setting; the text gives none), for the
+    proposed and the conventional arrangement.  Returns [(label, value, Problem)]."""
+    out = []
+    for w in np.linspace(0.5, 20.0, count):
+        out.append(("omega", float(w), circle_problem(n, w, w * math.sqrt(2.0), eps_i=2.0, name=f"circle_w{w:.3f}")))
+    for e in np.linspace(1.1, 10.0, count):
+        out.append(("eps", float(e), circle_problem(n, 5.0, 5.0 * math.sqrt(e), eps_i=float(e), name=f"circle_e{e:.3f}")))
+    return out
+
+
 def cfg_serving_c5(count: int = 2000, seed: int = 2313, rate: float = 200.0,
                    n_min: int = 256, n_max: int = 16384):
     """Poisson request stream mixing circles, ellipses (aspect U[1,4]) and two-material junction disks.
