@@ -209,11 +209,11 @@ def run_batched_workload(args):
     P.load()
     torch.cuda.set_device(0)
     if args.workload == "omega_eps":
-        # Sec. 7.1's iteration study (GMRES iterations vs omega and vs eps_2 on the unit circle) for the proposed
-        # ("mod") and the conventional ("conv") arrangement, each as one batch of all its problems
-        cases = W.cfg_omega_eps_sweep()
-        out = {}
-        for form in ("mod", "conv"):
+        # The iteration studies of Sec. 7.1 (unit circle: GMRES iterations vs omega and vs eps_2) and Sec. 7.2
+        # (concentric circles: vs omega and vs eps_2 = 1/eps_3) for the proposed ("mod") arrangement and the
+        # others the paper compares ("orig": beta = -alpha on the standard rows only; "conv": conventional),
+        # each as one batch of all its problems
+        def run_batch(cases, form):
             res = {}
             for leg in ("warmup", "timed"):
                 probs = [P.Problem.from_workload(wp, prec="mixed", form=form, tol=args.tol, max_iter=1000)
@@ -231,14 +231,24 @@ def run_batched_workload(args):
                     p.close()
             t, it, rs = res["timed"]
             kinds = np.array([c[0] for c in cases])
-            out[form] = {"solves_per_s": len(cases) / t, "wall_s": t, "max_rel_resid": float(np.max(rs)),
-                         "iters_vs_omega": [int(v) for v in it[kinds == "omega"]],
-                         "iters_vs_eps": [int(v) for v in it[kinds == "eps"]]}
-        line = {"metric": "omega / eps_2 sweeps of the unit circle (one batch per arrangement, mixed)",
-                "value": out["mod"]["solves_per_s"], "unit": "solves/s", "tol": args.tol, "results": out,
-                "omega": [c[1] for c in cases if c[0] == "omega"], "eps_2": [c[1] for c in cases if c[0] == "eps"],
-                "config": {"workload": "unit circle, 600 elements, Q = 4: 64 omega in [0.5, 20] (eps_2 = 2) and "
-                                       "64 eps_2 in [1.1, 10] (omega = 5)"}}
+            return {"solves_per_s": len(cases) / t, "wall_s": t, "max_rel_resid": float(np.max(rs)),
+                    "iters_vs_omega": [int(v) for v in it[kinds == "omega"]],
+                    "iters_vs_eps": [int(v) for v in it[kinds == "eps"]]}
+        circ = W.cfg_omega_eps_sweep()
+        conc = W.cfg_concentric_sweep()
+        out = {"circle": {f: run_batch(circ, f) for f in ("mod", "conv")},
+               "concentric": {f: run_batch(conc, f) for f in ("mod", "orig", "conv")}}
+        line = {"metric": "omega / eps sweeps of Sec. 7 (one batch per geometry and arrangement, mixed)",
+                "value": out["circle"]["mod"]["solves_per_s"], "unit": "solves/s", "tol": args.tol,
+                "results": out,
+                "circle_omega": [c[1] for c in circ if c[0] == "omega"],
+                "circle_eps_2": [c[1] for c in circ if c[0] == "eps"],
+                "concentric_omega": [c[1] for c in conc if c[0] == "omega"],
+                "concentric_eps_3": [c[1] for c in conc if c[0] == "eps"],
+                "config": {"workload": "unit circle, 600 elements: 64 omega in [0.5, 20] (eps_2 = 2), 64 eps_2 in "
+                                       "[1.1, 10] (omega = 5); concentric circles, 600 + 1200 elements: 32 omega "
+                                       "in [0.5, 10] (eps_i = i), 32 eps_3 in [0.1, 10] with eps_2 = 1/eps_3 "
+                                       "(omega = 5); Q = 4"}}
         print(json.dumps(line), flush=True)
         return
     if args.workload == "sweep":

@@ -392,6 +392,7 @@ size_t krylov_bytes(int n2, int nrhs, int m, bool fp32) {
   add((size_t)nrhs * nc * 8);             // npart
   add((size_t)nrhs * nc * 8);             // wpart
   add((size_t)nrhs * 4);                  // reo
+  add((size_t)nrhs * 4);                  // strict
   add((size_t)nrhs * 4);                  // arrive
   add((size_t)nrhs * (m + 1) * 16);       // hcol
   add((size_t)nrhs * 4);                  // active
@@ -450,6 +451,7 @@ Solver carve_solver(bem_problem* p, int nrhs, bool fp32) {
   st.npart = c.take<double>((size_t)nrhs * nc);
   st.wpart = c.take<double>((size_t)nrhs * nc);
   st.reo = c.take<int>(nrhs);
+  st.strict = c.take<int>(nrhs);
   st.arrive = c.take<int>(nrhs);
   st.hcol = c.take<double2>((size_t)nrhs * (m + 1));
   st.active = c.take<int>(nrhs);
@@ -738,6 +740,7 @@ bem_status solve_impl(bem_problem* p, int nrhs, const double2* b, double2* x, in
   std::vector<int> iters(nrhs, 0);
   std::vector<double> resid(nrhs, 0.0);
   CU(cudaMemsetAsync(x, 0, (size_t)nrhs * n2 * sizeof(double2), s));
+  CU(cudaMemsetAsync(sv.st.strict, 0, nrhs * sizeof(int), s));
   bem_status result = BEM_OK;
   if (!mixed) {
     st = gmres_run(p, sv, b, x, std::vector<double>(nrhs, p->o.tol), iters, resid, s);
@@ -750,6 +753,7 @@ bem_status solve_impl(bem_problem* p, int nrhs, const double2* b, double2* x, in
     if (st != BEM_OK) return st;
     CU(cudaMemcpyAsync(sv.r, b, (size_t)nrhs * n2 * sizeof(double2), cudaMemcpyDeviceToDevice, s));
     rn = bn;
+    std::vector<int> strict(nrhs, 0);
     bool done = false;
     for (int outer = 0; outer < p->o.max_refine && !done; ++outer) {
       // zero the residual of columns that already meet the tolerance so the inner solve skips them
@@ -764,12 +768,25 @@ bem_status solve_impl(bem_problem* p, int nrhs, const double2* b, double2* x, in
       std::vector<double> inner_res(nrhs), tols(nrhs);
       for (int r = 0; r < nrhs; ++r)
         tols[r] = rn[r] > 0 ? std::max(p->o.inner_tol, 0.3 * p->o.tol * bn[r] / rn[r]) : 1.0;
+      const std::vector<int> it_before = iters;
+      const std::vector<double> rn_before = rn;
       st = gmres_run(p, sv, sv.r, x, tols, iters, inner_res, s);
       if (st != BEM_OK) return st;
       st = residual_mixed(p, sv, nrhs, x, b, sv.r, s);
       if (st != BEM_OK) return st;
       st = column_norms(p, sv, sv.r, nrhs, rn, s);
       if (st != BEM_OK) return st;
+      // A column whose step used every iteration or cut its residual by less than 4x lost orthogonality in
+      // its FP32 basis under the selective second pass: from now on it runs Gram-Schmidt twice.
+      bool changed = false;
+      for (int r = 0; r < nrhs; ++r) {
+        if (strict[r] || resid[r] <= p->o.tol) continue;
+        if (iters[r] - it_before[r] >= p->o.max_iter || rn[r] > 0.25 * rn_before[r]) {
+          strict[r] = 1;
+          changed = true;
+        }
+      }
+      if (changed) CU(cudaMemcpyAsync(sv.st.strict, strict.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, s));
     }
     for (int r = 0; r < nrhs; ++r) {
       resid[r] = bn[r] > 0 ? rn[r] / bn[r] : 0.0;

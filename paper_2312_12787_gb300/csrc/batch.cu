@@ -65,6 +65,7 @@ struct VDev {
   double* npart;
   double* wpart;    // per chunk: ||w||^2 before projection (selective reorthogonalisation)
   int* reo;         // per slot: 1 if the conditional second Gram-Schmidt pass runs this iteration
+  int* strict;      // per slot: 1 once a refinement step stagnated (the second pass then always runs)
   int* arrive;      // per slot: first-pass update CTAs done (the last one takes the decision)
   int* n_active;
 };
@@ -231,7 +232,7 @@ __global__ void __launch_bounds__(256) kv_update(VDev d, int pass, int cond) {
   before = wsum(before);
   after = wsum(after);
   if (threadIdx.x == 0) {
-    d.reo[s] = after < 0.01 * before;   // ||w_after|| < ||w_before|| / 10
+    d.reo[s] = d.strict[s] || after < 0.01 * before;   // ||w_after|| < ||w_before|| / 10
     d.arrive[s] = 0;
   }
 }
@@ -461,6 +462,8 @@ struct BatchEngine {
   double* npart = nullptr;
   double* wpart = nullptr;
   int* reo = nullptr;
+  int* strict = nullptr;
+  int* h_strict = nullptr;   // pinned host copy
   int* arrive = nullptr;
   double* angles = nullptr;
   int max_chunks = 0, max_rb = 0;
@@ -492,6 +495,7 @@ struct BatchSlot {
   int iters = 0;
   double resid = 0.0;
   int outer = 0;
+  bool strict = false;      // a refinement step stagnated: Gram-Schmidt twice from then on
 };
 
 struct bem_batch {
@@ -502,6 +506,7 @@ struct bem_batch {
   std::vector<int> hn;
   std::vector<long long> hu;
   std::vector<double> htol;
+  std::vector<int> hstrict;
 };
 
 namespace {
@@ -526,7 +531,7 @@ VDev view(const BatchEngine& e) {
   d.active = e.active; d.iters = e.iters; d.j = e.jj; d.flag = e.flag;
   d.cbeg = e.cbeg; d.ccnt = e.ccnt; d.ch_slot = e.ch_slot; d.ch_loc = e.ch_loc; d.nchunks = e.nchunks;
   d.rb_slot = e.rb_slot; d.rb_row = e.rb_row; d.nrb = e.nrb;
-  d.part = e.part; d.npart = e.npart; d.wpart = e.wpart; d.reo = e.reo; d.arrive = e.arrive; d.n_active = e.n_active;
+  d.part = e.part; d.npart = e.npart; d.wpart = e.wpart; d.reo = e.reo; d.strict = e.strict; d.arrive = e.arrive; d.n_active = e.n_active;
   return d;
 }
 
@@ -637,11 +642,14 @@ bem_status start_flagged(bem_batch* b, const std::vector<int>& list) {
   for (int s : list) e.h_flag[s] = 1;
   BCU(cudaMemcpyAsync(e.flag, e.h_flag, e.cap * sizeof(int), cudaMemcpyHostToDevice, e.st));
   BCU(cudaMemcpyAsync(e.tol, b->htol.data(), e.cap * sizeof(double), cudaMemcpyHostToDevice, e.st));
+  b->hstrict.resize(e.cap);
+  for (int s = 0; s < e.cap; ++s) b->hstrict[s] = b->slot[s].strict ? 1 : 0;
+  BCU(cudaMemcpyAsync(e.strict, b->hstrict.data(), e.cap * sizeof(int), cudaMemcpyHostToDevice, e.st));
   const VDev d = view(e);
   kv_start_fin<<<(e.cap + 127) / 128, 128, 0, e.st>>>(d);
   if (e.nchunks) kv_start_scale<<<e.nchunks, kCh, 0, e.st>>>(d);
   BCU(cudaGetLastError());
-  BCU(cudaStreamSynchronize(e.st));   // htol is pageable
+  BCU(cudaStreamSynchronize(e.st));   // htol and hstrict are pageable
   return BEM_OK;
 }
 
@@ -670,9 +678,13 @@ bem_status refine_finished(bem_batch* b) {
   std::vector<int> restart;
   for (int s : fin) {
     BatchSlot& sl = b->slot[s];
+    const double prev = sl.outer > 0 ? sl.resid : 1.0;   // relative residual before this step
     sl.iters += e.h_iters[s];
     sl.outer += 1;
     const double rel = sl.bnorm > 0 ? e.h_rnorm[s] / sl.bnorm : 0.0;
+    // A step that used every iteration or cut the residual by less than 4x: the FP32 basis lost
+    // orthogonality under the selective second pass, so from now on the slot runs Gram-Schmidt twice.
+    if (e.h_iters[s] >= e.o.max_iter || rel > 0.25 * prev) sl.strict = true;
     sl.resid = rel;
     if (rel <= e.o.tol || sl.outer >= e.o.max_refine) {
       sl.state = 2;
@@ -734,7 +746,7 @@ BEM_API bem_status bem_batch_create(bem_batch** out, const bem_opts* opts, int m
        dalloc(&e.flag, cap) && dalloc(&e.n_active, 1) && dalloc(&e.cbeg, cap) && dalloc(&e.ccnt, cap) &&
        dalloc(&e.ch_slot, e.max_chunks) && dalloc(&e.ch_loc, e.max_chunks) && dalloc(&e.rb_slot, e.max_rb) &&
        dalloc(&e.rb_row, e.max_rb) && dalloc(&e.part, (size_t)e.max_chunks * (m + 1)) &&
-       dalloc(&e.npart, e.max_chunks) && dalloc(&e.wpart, e.max_chunks) && dalloc(&e.reo, cap) && dalloc(&e.arrive, cap) &&
+       dalloc(&e.npart, e.max_chunks) && dalloc(&e.wpart, e.max_chunks) && dalloc(&e.reo, cap) && dalloc(&e.strict, cap) && dalloc(&e.arrive, cap) &&
        dalloc(&e.angles, cap);
   ok = ok && cudaMallocHost(&e.h_active, cap * sizeof(int)) == cudaSuccess &&
        cudaMallocHost(&e.h_iters, cap * sizeof(int)) == cudaSuccess &&
@@ -763,7 +775,7 @@ BEM_API void bem_batch_destroy(bem_batch* b) {
   if (e.gexec) cudaGraphExecDestroy(e.gexec);
   void* ptrs[] = {e.dA, e.dAlo, e.dn, e.du, e.V, e.W, e.X, e.R, e.Bv, e.H, e.cs, e.sn, e.g, e.y, e.hcol, e.beta,
                   e.hnext, e.resid, e.tol, e.rnorm, e.active, e.iters, e.jj, e.flag, e.n_active, e.cbeg, e.ccnt,
-                  e.ch_slot, e.ch_loc, e.rb_slot, e.rb_row, e.part, e.npart, e.wpart, e.reo, e.arrive, e.angles};
+                  e.ch_slot, e.ch_loc, e.rb_slot, e.rb_row, e.part, e.npart, e.wpart, e.reo, e.strict, e.arrive, e.angles};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (e.h_active) cudaFreeHost(e.h_active);

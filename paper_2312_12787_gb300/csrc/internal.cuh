@@ -202,6 +202,7 @@ struct KrylovState {
   double* npart;    // scratch: nrhs x krylov_nchunk(n) partial squared norms
   double* wpart;    // scratch: nrhs x krylov_nchunk(n) partial squared norms of w before projection
   int* reo;         // nrhs: 1 if the conditional second Gram-Schmidt pass runs this iteration
+  int* strict;      // nrhs: 1 once a refinement step stagnated (the conditional second pass then always runs)
   int* arrive;      // nrhs: CTAs of the first-pass update kernel done (the last one takes the decision)
   double2* hcol;    // nrhs x (m+1): projections of the current pass
   int* active;      // nrhs: 1 while iterating

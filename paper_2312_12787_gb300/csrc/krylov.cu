@@ -313,7 +313,7 @@ __global__ void __launch_bounds__(CH / 2, sizeof(T) == sizeof(float2) ? 8 : 1) k
   before = warp_sum(before);
   after = warp_sum(after);
   if (threadIdx.x == 0) {
-    st.reo[s] = after < 0.01 * before;   // ||w_after|| < ||w_before|| / 10
+    st.reo[s] = st.strict[s] || after < 0.01 * before;   // ||w_after|| < ||w_before|| / 10
     st.arrive[s] = 0;
   }
 }

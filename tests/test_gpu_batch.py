@@ -137,3 +137,33 @@ def test_random_star_sweep_full_c4(B, torch):
     bt.close()
     for p in probs:
         p.close()
+
+
+def test_high_contrast_concentric_converges_on_every_mixed_path(B, torch):
+    """The concentric case of Sec. 7.2 at the high-contrast end of its sweep (eps_2 = 1/eps_3 = 10, omega = 5,
+    600 + 1200 elements), where the FP32 inner solves lose orthogonality under the selective second
+    Gram-Schmidt pass: the stagnation test must switch the system to two passes, so that the single-problem
+    path, the tensor-core path and the batched engine all reach the tolerance and agree with the FP64 solve."""
+    wp = W.concentric(600, 1200, 5.0, eps=(1.0, 10.0, 0.1))
+    n2 = 2 * wp.n_elem
+    p = B.Problem.from_workload(wp, prec="fp64", tol=1e-10, max_iter=1000)
+    x64 = torch.empty((1, n2), dtype=torch.complex128, device="cuda")
+    st, it, rs = p.bem_solve_planewave([0.0], x64)
+    p.close()
+    assert st == B.BEM_OK
+    ref = x64[0].cpu().numpy()
+    for prec, nr in (("mixed", 1), ("mixed_tc", 2)):
+        p = B.Problem.from_workload(wp, prec=prec, tol=1e-8, max_iter=1000)
+        x = torch.empty((nr, n2), dtype=torch.complex128, device="cuda")
+        st, it, rs = p.bem_solve_planewave([0.0] * nr, x)
+        p.close()
+        assert st == B.BEM_OK and np.all(rs <= 1e-8), (prec, st, it, rs)
+        assert rel(x[0].cpu().numpy(), ref) <= SOLUTION_TOL_MIXED, prec
+    q = B.Problem.from_workload(wp, prec="mixed")
+    xb = [torch.empty(n2, dtype=torch.complex128, device="cuda")]
+    bt = B.Batch(2, n2, tol=1e-8, max_iter=1000)
+    st, it, rs = bt.bem_batch_solve_planewave([q], np.zeros(1), xb)
+    bt.close()
+    q.close()
+    assert st == B.BEM_OK and rs[0] <= 1e-8, (st, it, rs)
+    assert rel(xb[0].cpu().numpy(), ref) <= SOLUTION_TOL_MIXED

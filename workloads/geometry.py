@@ -190,6 +190,19 @@ def cfg_omega_eps_sweep(n: int = 600, count: int = 64):
     return out
 
 
+def cfg_concentric_sweep(n_inner: int = 600, n_outer: int = 1200, count: int = 32):
+    """The concentric iteration study of Sec. 7.2: (a) `count` angular frequencies omega in [0.5, 10] with
+    eps_i = i, and (b) `count` contrasts eps_2 = 1/eps_3 for eps_3 in [0.1, 10] with omega = 5, on the inner
+    and outer circles of n_inner and n_outer elements (ranges read off the setting; the text gives none).
+    Returns [(label, value, Problem)]."""
+    out = []
+    for w in np.linspace(0.5, 10.0, count):
+        out.append(("omega", float(w), concentric(n_inner, n_outer, float(w), eps=(1.0, 2.0, 3.0))))
+    for e3 in np.linspace(0.1, 10.0, count):
+        out.append(("eps", float(e3), concentric(n_inner, n_outer, 5.0, eps=(1.0, 1.0 / float(e3), float(e3)))))
+    return out
+
+
 def cfg_serving_c5(count: int = 2000, seed: int = 2313, rate: float = 200.0,
                    n_min: int = 256, n_max: int = 16384):
     """Poisson request stream mixing circles, ellipses (aspect U[1,4]) and two-material junction disks.
