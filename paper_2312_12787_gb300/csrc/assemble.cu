@@ -77,8 +77,10 @@ __device__ __forceinline__ void store_pair(int n, int i, int j, const C2 (&out)[
   }
 }
 
+// Three CTAs per SM (80 registers, some spills): the kernel is bound by dependent FP64 and double-float
+// latencies, and the extra resident warps hide more of them than the spills cost (5 % faster than two).
 template <int MIXED>
-__global__ void __launch_bounds__(256) k_assemble(ElemDev e, int n, DomTab dom, Quad q, int form, void* Aout,
+__global__ void __launch_bounds__(256, 3) k_assemble(ElemDev e, int n, DomTab dom, Quad q, int form, void* Aout,
                                                    void* Aloout, size_t lda) {
   const int j = blockIdx.x * 32 + threadIdx.x;
   const int i = blockIdx.y * 8 + threadIdx.y;
