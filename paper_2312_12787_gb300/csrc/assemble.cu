@@ -123,8 +123,9 @@ __global__ void __launch_bounds__(256) k_matvec_free(ElemDev e, int n, DomTab do
 
 // Many problems in one launch: blockIdx.x walks a list of 32 x TY tiles of all problems (problem found by
 // binary search in the tile prefix sums); each problem keeps its own elements, domain table and matrices.
+// About 24 resident warps per SM, as for k_assemble.
 template <int MIXED, int TY>
-__global__ void __launch_bounds__(32 * TY) k_assemble_batched(const AsmJob* __restrict__ jobs, int njobs,
+__global__ void __launch_bounds__(32 * TY, 768 / (32 * TY)) k_assemble_batched(const AsmJob* __restrict__ jobs, int njobs,
                                                               const long long* __restrict__ tile_prefix, Quad q,
                                                               int form) {
   const long long t = blockIdx.x;
