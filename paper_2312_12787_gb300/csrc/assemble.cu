@@ -93,7 +93,8 @@ __global__ void __launch_bounds__(256, 3) k_assemble(ElemDev e, int n, DomTab do
 // Matrix-free product y = A x (no stored matrix): each block owns 8 element rows (16 matrix rows i and
 // N + i); the 32 lanes of a warp stride over the element columns j, evaluate the four entries of (i, j) with
 // the assembly's own code and accumulate; a warp reduction gives the two row sums (FP64 products and sums).
-__global__ void __launch_bounds__(256) k_matvec_free(ElemDev e, int n, DomTab dom, Quad q, int form,
+// Three CTAs per SM, as for k_assemble.
+__global__ void __launch_bounds__(256, 3) k_matvec_free(ElemDev e, int n, DomTab dom, Quad q, int form,
                                                       const double2* __restrict__ x, double2* __restrict__ y,
                                                       const int* gate) {
   if (gate && *gate == 0) return;
