@@ -207,20 +207,6 @@ constexpr MillerCoefF2 make_miller_coef_f2() {
   return c;
 }
 
-// Coefficient tables read with a loop index: constant memory on the device (the index is uniform over a
-// warp, so reads are broadcasts), a constexpr table on the host.
-#if defined(__CUDACC__)
-static __constant__ MillerCoefF2 kMillerCoefDev = make_miller_coef_f2();
-#endif
-static constexpr MillerCoefF2 kMillerCoefHost = make_miller_coef_f2();
-BEM_HD F2 bem_miller_coef(int k) {
-#if defined(__CUDA_ARCH__)
-  return F2{kMillerCoefDev.h[k], kMillerCoefDev.l[k]};
-#else
-  return F2{kMillerCoefHost.h[k], kMillerCoefHost.l[k]};
-#endif
-}
-
 // Miller's algorithm exactly as bessel01_miller, with the recurrence and the three sums in double-float
 // arithmetic on the FP32 pipe (start value 2^-30, rescaled by 2^-40 whenever it grows past 2^40 so that it
 // stays inside the FP32 exponent range); the normalisation and the logarithmic terms are FP64.
@@ -534,46 +520,8 @@ BEM_HD void bessel01_series_f2(double x, Bessel01F2& b) {
 
 constexpr F2 f2_const(double v) { return F2{(float)v, (float)(v - (double)(float)v)}; }
 
-// Miller's algorithm as bessel01_miller_f2 with the normalisation, 2/x and the Neumann sums also in
-// double-float; only ln(x/2) is FP64.
-BEM_HD void bessel01_miller_f2x(double x, F2 X, Bessel01F2& b, int start = BEM_MILLER_START) {
-  const F2 tox = f2_pow2(f2_rcp(X), 2.f);
-  F2 fp{0.f, 0.f}, f{0x1p-30f, 0.f}, norm{0.f, 0.f}, sy0{0.f, 0.f}, sy1{0.f, 0.f}, fodd{0.f, 0.f};
-  // two orders per pass (even n, then n - 1); both use the coefficient (-1)^k / k with k = n / 2.  A
-  // rolled loop keeps the code small enough for the instruction cache (start is uniform over the warp).
-#pragma unroll 1
-  for (int n = start; n >= 2; n -= 2) {
-    const F2 ck = bem_miller_coef(n >> 1);
-    norm = f2_add(norm, f);
-    sy0 = f2_add(sy0, f2_mul(f, ck));
-    fodd = fp;
-    F2 fm = f2_sub(f2_mul(f2_mulf(tox, (float)n), f), fp);
-    fp = f;
-    f = fm;
-    sy1 = f2_add(sy1, f2_mul(f2_sub(f, fodd), ck));
-    fm = f2_sub(f2_mul(f2_mulf(tox, (float)(n - 1)), f), fp);
-    fp = f;
-    f = fm;
-    if ((n & 3) == 2 && fabsf(f.h) > 0x1p40f) {
-      const float sc = 0x1p-40f;
-      f = f2_pow2(f, sc); fp = f2_pow2(fp, sc);
-      norm = f2_pow2(norm, sc); sy0 = f2_pow2(sy0, sc);
-      sy1 = f2_pow2(sy1, sc); fodd = f2_pow2(fodd, sc);
-    }
-  }
-  constexpr F2 kTwoPi = f2_const(kTwoOverPi);
-  const F2 s = f2_rcp(f2_add(f, f2_pow2(norm, 2.f)));
-  const F2 j0 = f2_mul(f, s), j1 = f2_mul(fp, s);
-  const F2 lg = f2_from_bits(log(0.5 * x) + kEulerGamma);
-  b.j0 = j0;
-  b.j1 = j1;
-  // Y0 = (2/pi) [lg J0 - 2 sy0 s];  Y1 = (2/pi) [lg J1 - J0 / x + sy1 s]
-  b.y0 = f2_mul(kTwoPi, f2_sub(f2_mul(lg, j0), f2_pow2(f2_mul(sy0, s), 2.f)));
-  b.y1 = f2_mul(kTwoPi, f2_add(f2_sub(f2_mul(lg, j1), f2_mul(j0, f2_pow2(tox, 0.5f))), f2_mul(sy1, s)));
-}
-
 // The expansion's coefficients for a rolled Horner loop: which = 0..3 selects P0, Q0, P1, Q1 (constant memory
-// on the device, as for the Miller coefficients).
+// on the device: the index is uniform over a warp, so reads are broadcasts; a constexpr table on the host).
 #if defined(__CUDACC__)
 static __constant__ AsympCoefF2 kAsympCoefDev = make_asymp_coef_f2();
 #endif
@@ -783,15 +731,6 @@ BEM_HD void bessel01_f2(double x, F2 X, Bessel01F2& b) {
     bessel01_series_f2(x, b);
   } else if (X.h < kTabXMax) {
     bessel01_taylor_f2(x, X, b);
-  } else if (X.h < (float)BEM_X_ASYMP) {
-    // even start order 1.6 x + 23 (rounded up): at least four orders beyond the smallest one that keeps
-    // the truncation of J0, J1, Y0, Y1 below 2e-16 of |H0| on [2, 18); the largest of the warp's active lanes
-    int start = 2 * (int)ceilf(0.8f * X.h + 11.5f);
-    start = start < BEM_MILLER_START ? start : BEM_MILLER_START;
-#if defined(__CUDA_ARCH__)
-    start = __reduce_max_sync(__activemask(), start);
-#endif
-    bessel01_miller_f2x(x, X, b, start);
   } else {
     bessel01_asymp_f2x(x, X, b);
   }
