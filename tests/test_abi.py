@@ -87,3 +87,46 @@ def test_workload_generators_shapes():
     assert len(c4) == 256 and all(128 <= q.n_elem <= 2048 for q in c4)
     c5 = W.cfg_serving_c5(count=50)
     assert all(t2 > t1 for (t1, _), (t2, _) in zip(c5, c5[1:]))
+
+
+def test_empty_and_null_arguments_rejected_before_device_work(lib):
+    """Empty inputs (n_rhs = 0, n_ang = 0, n_pts = 0) and NULL buffers are argument errors, reported before any
+    device call: on a machine without a GPU a call that reached the device would answer BEM_ECUDA instead."""
+    import ctypes
+    L = lib.load()
+    p = lib.Problem(prec="mixed")
+    p.bem_set_domains([5.0, 7.5], [1.0, 2.25])
+    p.bem_add_segment(np.array([[1.0, 0.0], [0.0, 1.0], [-1.0, 0.0], [0.0, -1.0]]), 0, 1, True)
+    h = p._h
+    ang = np.zeros(2)
+    ap = ang.ctypes.data_as(ctypes.c_void_p)
+    buf = ctypes.c_void_p(1 << 20)          # never dereferenced: every call below fails validation first
+    it = np.zeros(2, np.int32)
+    rs = np.zeros(2)
+    itp, rsp = it.ctypes.data_as(ctypes.c_void_p), rs.ctypes.data_as(ctypes.c_void_p)
+    calls = {
+        "rhs n_rhs=0": lambda: L.bem_rhs_planewave(h, 0, ap, buf, None),
+        "rhs NULL angles": lambda: L.bem_rhs_planewave(h, 1, None, buf, None),
+        "matvec n_rhs=0": lambda: L.bem_matvec(h, 0, buf, buf, None),
+        "matvec NULL y": lambda: L.bem_matvec(h, 1, buf, None, None),
+        "residual n_rhs=0": lambda: L.bem_residual(h, 0, buf, buf, buf, None),
+        "residual NULL r": lambda: L.bem_residual(h, 1, buf, buf, None, None),
+        "noalloc n_rhs=0": lambda: L.bem_residual_noalloc(h, 0, buf, buf, buf, None),
+        "noalloc r aliases x": lambda: L.bem_residual_noalloc(h, 1, buf, ctypes.c_void_p(1 << 21), buf, None),
+        "solve n_rhs=0": lambda: L.bem_solve(h, 0, buf, buf, itp, rsp, None),
+        "solve NULL b": lambda: L.bem_solve(h, 1, None, buf, itp, rsp, None),
+        "solve_planewave n_rhs=0": lambda: L.bem_solve_planewave(h, 0, ap, buf, itp, rsp, None),
+        "solve_planewave NULL x": lambda: L.bem_solve_planewave(h, 1, ap, None, itp, rsp, None),
+        "far_field n_ang=0": lambda: L.bem_far_field(h, 1, buf, 0, ap, buf, None),
+        "far_field n_rhs=0": lambda: L.bem_far_field(h, 0, buf, 2, ap, buf, None),
+        "near_field n_pts=0": lambda: L.bem_near_field(h, 1, buf, None, 0, ap, ap, buf, None),
+        "host solve n_rhs=0": lambda: L.bem_solve_planewave_host(h, 0, ap, None, 0, None, None, itp, rsp, None),
+        "NULL problem": lambda: L.bem_matvec(None, 1, buf, buf, None),
+    }
+    for what, call in calls.items():
+        assert call() == lib.BEM_EINVAL, what
+        assert L.bem_last_error().decode(), what
+    # the no-allocation residual never assembles: an unassembled problem is a state error, again host-side
+    assert L.bem_residual_noalloc(h, 1, buf, ctypes.c_void_p(1 << 21), ctypes.c_void_p(1 << 22), None) == lib.BEM_ESTATE
+    assert L.bem_num_unknowns(None) == 0 and L.bem_footprint_bytes(h, 0) == 0
+    p.close()
