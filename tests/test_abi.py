@@ -87,6 +87,21 @@ def test_workload_generators_shapes():
     assert len(c4) == 256 and all(128 <= q.n_elem <= 2048 for q in c4)
     c5 = W.cfg_serving_c5(count=50)
     assert all(t2 > t1 for (t1, _), (t2, _) in zip(c5, c5[1:]))
+    # the sweeps of Sec. 7.1 / 7.2: k_d = omega sqrt(eps_d) in every domain (Sec. 2)
+    sw = W.cfg_omega_eps_sweep()
+    assert len(sw) == 128 and {lab for lab, _, _ in sw} == {"omega", "eps"}
+    for lab, v, q in sw:
+        assert q.n_elem == 600 and q.eps[0] == 1.0
+        om = q.k[0]
+        assert np.allclose(q.k, [om * np.sqrt(e) for e in q.eps], rtol=1e-14)
+        assert (om == v) if lab == "omega" else (q.eps[1] == v and om == 5.0)
+    cs = W.cfg_concentric_sweep()
+    assert len(cs) == 64
+    for lab, v, q in cs:
+        assert q.n_elem == 1800 and len(q.k) == 3
+        assert np.allclose(q.k, [q.k[0] * np.sqrt(e) for e in q.eps], rtol=1e-14)
+        if lab == "eps":
+            assert q.eps[2] == v and abs(q.eps[1] * q.eps[2] - 1.0) < 1e-14
 
 
 def test_empty_and_null_arguments_rejected_before_device_work(lib):
