@@ -68,13 +68,16 @@ typedef enum {
  *          equations of the outward domain first, standard equations of the inward domain second. */
 typedef enum { BEM_FORM_MOD = 0, BEM_FORM_ORIG = 1, BEM_FORM_BETA1 = 2, BEM_FORM_CONV = 3 } bem_form;
 
-/* Arithmetic of the solve.  Assembly is always evaluated in FP64.
+/* Arithmetic of the solve.  Assembly is the same for every precision: FP64 node geometry and phase k r,
+ * then the Hankel values, Gauss sums and entry formulas in double-float arithmetic (pairs of FP32), within
+ * about 1e-14 of the largest entry of a block of the FP64 definition.
  *  FP64     - A stored as complex FP64; FP64 matvec, FP64 Arnoldi; one unrestarted GMRES to `tol`.
  *  MIXED    - A stored as complex FP32 (hi) plus its FP32 rounding remainder (lo).  Inner GMRES runs on
  *             hi with FP32 products and an FP32 Krylov basis to `inner_tol`; the outer loop refines
  *             x in FP64 with residuals b - (hi + lo) x accumulated in double-float arithmetic.
  *  MIXED_TC - as MIXED, but the inner matvec of a multi-right-hand-side block runs as one dense complex
- *             GEMM on the tcgen05 tensor cores (3xTF32 split products, FP32 accumulation). */
+ *             GEMM on the tcgen05 tensor cores (hi split into two FP16 parts, hi16 + 2^-11 lo16; three FP16
+ *             products per term, FP32 accumulation in tensor memory). */
 typedef enum { BEM_PREC_FP64 = 0, BEM_PREC_MIXED = 1, BEM_PREC_MIXED_TC = 2 } bem_prec;
 
 typedef struct {
