@@ -150,8 +150,6 @@ cudaError_t launch_residual_split_tc(const float2* Ahi, const float2* Alo, size_
                                      cudaStream_t s, int* nlaunch = nullptr);
 cudaError_t launch_residual_c64(const double2* A, size_t lda, int n, int nrhs, const double2* x, const double2* b,
                                 double2* r, cudaStream_t s);
-cudaError_t launch_residual_split_f64(const float2* Ahi, const float2* Alo, size_t lda, int n, int nrhs,
-                                      const double2* x, const double2* b, double2* r, cudaStream_t s);
 // tcgen05 tensor-core GEMM Y = A X (A c32, X / Y c32, nrhs <= 64).  Returns cudaErrorNotSupported if the
 // shape is not supported by the kernel.
 // tcgen05 tensor-core GEMM Y = A X (X / Y complex FP32, 2 <= nrhs <= 64) on the FP16 split copy of A that

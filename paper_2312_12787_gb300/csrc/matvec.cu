@@ -4,8 +4,7 @@
 // column (column s of X at X + s*n), so both A and X are contiguous along the summation index.
 //
 //  * k_gemv_f64   - y = A x, one warp per row, FP64 arithmetic (FP64 path; on GB300 the FP64 pipe,
-//                   not HBM, bounds it).  Also used with the split loader for the mixed refinement
-//                   residual r = b - (hi + lo) x.
+//                   not HBM, bounds it); with RESID it forms the FP64 path's residual b - A x.
 //  * k_gemv_c32   - y = A x with complex FP32 storage and products (mixed inner solve): each lane streams
 //                   16-byte float4 loads (two complex entries), so a warp moves 512 contiguous bytes per
 //                   step; partial sums are folded into FP64 every 16 steps.  HBM-bound.
@@ -24,14 +23,6 @@ namespace {
 struct LoadC64 {
   const double2* A;
   __device__ __forceinline__ double2 operator()(size_t idx) const { return __ldg(A + idx); }
-};
-struct LoadSplit {
-  const float2* hi;
-  const float2* lo;
-  __device__ __forceinline__ double2 operator()(size_t idx) const {
-    const float2 h = __ldg(hi + idx), l = __ldg(lo + idx);
-    return make_double2((double)h.x + (double)l.x, (double)h.y + (double)l.y);
-  }
 };
 
 __device__ __forceinline__ double2 warp_sum(double2 v) {
@@ -748,20 +739,6 @@ cudaError_t launch_residual_c64(const double2* A, size_t lda, int n, int nrhs, c
   } else {
     dim3 grd((n + 63) / 64, (nrhs + 63) / 64);
     k_gemm_f64<LoadC64, true><<<grd, 256, 0, s>>>(ld, lda, n, nrhs, x, b, r, nullptr);
-  }
-  return cudaGetLastError();
-}
-
-// FP64 reference implementation of the same residual (kept for tests of the double-float kernels).
-cudaError_t launch_residual_split_f64(const float2* Ahi, const float2* Alo, size_t lda, int n, int nrhs,
-                                      const double2* x, const double2* b, double2* r, cudaStream_t s) {
-  LoadSplit ld{Ahi, Alo};
-  if (nrhs == 1) {
-    dim3 grd((n + 7) / 8, 1);
-    k_gemv_f64<LoadSplit, true><<<grd, 256, 0, s>>>(ld, lda, n, x, b, r, nullptr);
-  } else {
-    dim3 grd((n + 63) / 64, (nrhs + 63) / 64);
-    k_gemm_f64<LoadSplit, true><<<grd, 256, 0, s>>>(ld, lda, n, nrhs, x, b, r, nullptr);
   }
   return cudaGetLastError();
 }
