@@ -10,6 +10,10 @@ is the mixed-precision path (complex FP32 storage and Krylov basis, FP64 refinem
 GPU path runs the same step for comparison (`fp64` key) and gives the accuracy reference.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--fp64-steps S]
+                       [--workload star|sweep|serving|omega_eps]
+Other workloads: `sweep` = 256 random stars in one batch, `serving` = a Poisson request stream through the
+continuous-batching loop (p50/p99 latency), `omega_eps` = the frequency and contrast sweeps of Sec. 7.1
+and 7.2 as batched launches.
 """
 from __future__ import annotations
 
