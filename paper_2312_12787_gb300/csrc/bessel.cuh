@@ -274,9 +274,7 @@ BEM_HD void bessel01_asymp(double x, Bessel01& b) {
   b.y1 = -hr;
 }
 
-// Same expansion, cheaper on the FP64 pipe: each of P0, Q0, P1, Q1 is a polynomial in u = 1/x^2
-// (Horner in u halves the multiply-adds), and 1/x comes from the reciprocal square root that the
-// amplitude sqrt(2/(pi x)) needs anyway (1/x = (pi/2) amp^2).
+// The expansion's P0, Q0, P1, Q1 as polynomials in u = 1/x^2 (Horner in u halves the multiply-adds).
 struct AsympCoefU {
   double p0[BEM_ASYMP_TERMS / 2], q0[BEM_ASYMP_TERMS / 2], p1[BEM_ASYMP_TERMS / 2], q1[BEM_ASYMP_TERMS / 2];
 };
@@ -292,47 +290,12 @@ constexpr AsympCoefU make_asymp_coef_u() {
   return u;
 }
 
-BEM_HD void bessel01_asymp_u(double x, Bessel01& b) {
-  constexpr AsympCoefU C = make_asymp_coef_u();
-  constexpr int T = BEM_ASYMP_TERMS / 2;
-#if defined(__CUDA_ARCH__)
-  const double rs = rsqrt(x);
-#else
-  const double rs = 1.0 / sqrt(x);
-#endif
-  const double y = rs * rs;                    // 1/x
-  const double u = y * y;
-  double p0 = C.p0[T - 1], q0 = C.q0[T - 1], p1 = C.p1[T - 1], q1 = C.q1[T - 1];
-#pragma unroll
-  for (int m = T - 2; m >= 0; --m) {
-    p0 = fma(p0, u, C.p0[m]);
-    q0 = fma(q0, u, C.q0[m]);
-    p1 = fma(p1, u, C.p1[m]);
-    q1 = fma(q1, u, C.q1[m]);
-  }
-  q0 *= y;
-  q1 *= y;
-  double sn, cs;
-#if defined(__CUDA_ARCH__)
-  sincos(x, &sn, &cs);
-#else
-  sn = sin(x); cs = cos(x);
-#endif
-  const double amp = rs * 0.797884560802865355879892119868763737;   // sqrt(2/pi) / sqrt(x)
-  const double er = (cs + sn) * (amp * kInvSqrt2), ei = (sn - cs) * (amp * kInvSqrt2);
-  b.j0 = p0 * er - q0 * ei;
-  b.y0 = p0 * ei + q0 * er;
-  const double hr = p1 * er - q1 * ei, hi = p1 * ei + q1 * er;
-  b.j1 = hi;
-  b.y1 = -hr;
-}
-
 // ---- the expansion evaluated in double-float ------------------------------------------------------
-// Same mathematics as bessel01_asymp_u, arranged so that almost all of the arithmetic runs on the FP32
-// pipe: cos x and sin x come from a Cody-Waite reduction of x by pi/2 in FP64 (three-part split of pi/2;
-// exact for x < 2^20) followed by Taylor series of the reduced argument |r| <= pi/4 in double-float
-// (terms through r^17 and r^18); P0, Q0, P1, Q1 are Horner sums in u = 1/x^2 with double-float
-// coefficients; the final products too.  Only the reduction, the reciprocal square root and the
+// Hankel's expansion (DLMF 10.17.5) with each of P0, Q0, P1, Q1 written as a polynomial in u = 1/x^2,
+// arranged so that almost all of the arithmetic runs on the FP32 pipe: cos x and sin x come from a
+// Cody-Waite reduction of x by pi/2 in FP64 (three-part split of pi/2; exact for x < 2^20) followed by
+// Taylor series of the reduced argument |r| <= pi/4 in double-float (terms through r^17 and r^18); P0, Q0,
+// P1, Q1 are Horner sums in u = 1/x^2 with double-float coefficients; the final products too.  Only the reduction, the reciprocal square root and the
 // conversions stay in FP64.
 struct F2Coef {
   float h[BEM_ASYMP_TERMS / 2], l[BEM_ASYMP_TERMS / 2];
@@ -448,14 +411,6 @@ BEM_HD float f32_rsqrt_seed(float v) {
   return 1.0f / sqrtf(v);
 #endif
 }
-BEM_HD float f32_rcp_seed(float v) {
-#if defined(__CUDA_ARCH__)
-  return __frcp_rn(v);
-#else
-  return 1.0f / v;
-#endif
-}
-
 // 1/sqrt(a), a > 0: an FP32 estimate refined by two Newton steps y <- y + y (1 - a y^2) / 2 in double-float
 // (each step squares the relative error: ~1e-7 -> ~1e-14 -> double-float rounding).
 BEM_HD F2 f2_rsqrt(F2 a) {
@@ -464,16 +419,6 @@ BEM_HD F2 f2_rsqrt(F2 a) {
   for (int it = 0; it < 2; ++it) {
     const F2 e = f2_sub(F2{1.f, 0.f}, f2_mul(a, f2_mul(y, y)));
     y = f2_add(y, f2_mul(y, f2_pow2(e, 0.5f)));
-  }
-  return y;
-}
-// 1/a, a != 0: Newton steps y <- y + y (1 - a y).
-BEM_HD F2 f2_rcp(F2 a) {
-  F2 y{f32_rcp_seed(a.h), 0.f};
-#pragma unroll
-  for (int it = 0; it < 2; ++it) {
-    const F2 e = f2_sub(F2{1.f, 0.f}, f2_mul(a, y));
-    y = f2_add(y, f2_mul(y, e));
   }
   return y;
 }
