@@ -1,0 +1,20 @@
+// Host build of the library's Bessel routines (bessel.cuh is host-and-device code) for the CPU test
+// tests/test_bessel_host.py.  Reads x values (one per line) from stdin and prints, per x, the double-float
+// path the assembly kernels use (J0, Y0, J1, Y1 as hi + lo) and the FP64 path (self terms, near field),
+// in hexadecimal floating point so that no digits are lost.  No CUDA call is made.
+#include <cstdio>
+
+#include "bessel.cuh"
+
+int main() {
+  double x;
+  while (std::scanf("%lf", &x) == 1) {
+    bem::Bessel01F2 f;
+    bem::bessel01_f2(x, bem::f2_from(x), f);
+    bem::Bessel01 d;
+    bem::bessel01(x, d);
+    std::printf("%a %a %a %a %a %a %a %a %a\n", x, bem::f2_to(f.j0), bem::f2_to(f.y0), bem::f2_to(f.j1),
+                bem::f2_to(f.y1), d.j0, d.y0, d.j1, d.y1);
+  }
+  return 0;
+}

@@ -1,0 +1,79 @@
+"""The library's Bessel routines (bessel.cuh, host-and-device code) built for the host and checked against
+mpmath on every branch: the ascending series (x < 2), the Taylor steps from the tabulated coefficients
+(2 <= x < 35), Hankel's expansion (x >= 35), and the branch boundaries.  Errors are measured relative to
+|H0| for J0, Y0 and to |H1| for J1, Y1 (the Hankel functions the kernels are made of, Sec. 3.3).
+
+Two entry points are checked: bessel01_f2, the double-float path of the assembly and matrix-free kernels, and
+bessel01, the FP64 path of the self terms and the near field.  The host build runs the same source as the
+device build except for the table loads, the warp-uniform choices and the FP32 reciprocal-square-root seed
+(refined by Newton steps on both)."""
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CSRC = os.path.join(ROOT, "paper_2312_12787_gb300", "csrc")
+
+
+def _nvcc():
+    for cand in (shutil.which("nvcc"), "/usr/local/cuda/bin/nvcc"):
+        if cand and os.path.exists(cand):
+            return cand
+    return None
+
+
+@pytest.fixture(scope="module")
+def values(tmp_path_factory):
+    mpmath = pytest.importorskip("mpmath")
+    nvcc = _nvcc()
+    if nvcc is None:
+        pytest.skip("nvcc not found")
+    exe = str(tmp_path_factory.mktemp("bessel") / "bessel_host_check")
+    # -ffp-contract=off: the double-float error-free transformations must not be fused on any host
+    subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O2", "-std=c++17",
+                    "--expt-relaxed-constexpr", "-Xcompiler", "-ffp-contract=off", "-I" + CSRC,
+                    "-I" + os.path.join(ROOT, "include"), os.path.join(ROOT, "tests", "bessel_host_check.cu"),
+                    "-o", exe], check=True, capture_output=True)
+    rng = np.random.default_rng(7)
+    xs = np.concatenate([
+        np.geomspace(1e-3, 1.999, 40),
+        [2.0 - 2.0 ** -40, 2.0, 2.0 + 2.0 ** -40],
+        2.0 + np.arange(1, 1056, 3) / 32.0 + rng.uniform(-1 / 64, 1 / 64, 352),   # around the grid points
+        2.0 + (np.arange(0, 1056, 5) + 0.5) / 32.0,                              # half-way between them
+        [18.0, 25.0, 35.0 - 2.0 ** -40, 35.0, 35.0 + 2.0 ** -40],
+        np.geomspace(35.0, 2000.0, 160),
+    ])
+    out = subprocess.run([exe], input="\n".join(repr(float(v)) for v in xs), capture_output=True, text=True,
+                         check=True).stdout
+    got = np.array([[float.fromhex(t) for t in line.split()] for line in out.strip().splitlines()])
+    assert got.shape == (len(xs), 9) and np.array_equal(got[:, 0], xs)
+    mpmath.mp.dps = 30
+    ref = np.array([[float(mpmath.besselj(0, x)), float(mpmath.bessely(0, x)), float(mpmath.besselj(1, x)),
+                     float(mpmath.bessely(1, x))] for x in xs])
+    return xs, got, ref
+
+
+def _rel_err(got4, ref):
+    h0 = np.hypot(ref[:, 0], ref[:, 1])
+    h1 = np.hypot(ref[:, 2], ref[:, 3])
+    scale = np.stack([h0, h0, h1, h1], 1)
+    return np.max(np.abs(got4 - ref) / scale, axis=1)
+
+
+@pytest.mark.parametrize("lo,hi,bound", [(0.0, 2.0, 3e-15), (2.0, 35.0, 1e-14), (35.0, np.inf, 2.5e-14)])
+def test_double_float_path_matches_mpmath(values, lo, hi, bound):
+    xs, got, ref = values
+    sel = (xs >= lo) & (xs < hi)
+    err = _rel_err(got[sel, 1:5], ref[sel])
+    assert sel.sum() > 30 and err.max() <= bound, (err.max(), xs[sel][np.argmax(err)])
+
+
+@pytest.mark.parametrize("lo,hi,bound", [(0.0, 2.0, 1e-15), (2.0, 35.0, 1e-13), (35.0, np.inf, 2.5e-14)])
+def test_fp64_path_matches_mpmath(values, lo, hi, bound):
+    xs, got, ref = values
+    sel = (xs >= lo) & (xs < hi)
+    err = _rel_err(got[sel, 5:9], ref[sel])
+    assert sel.sum() > 30 and err.max() <= bound, (err.max(), xs[sel][np.argmax(err)])
