@@ -64,3 +64,24 @@ def test_single_rank_needs_no_process_group():
         for k, v in saved.items():
             if v is not None:
                 os.environ[k] = v
+
+
+def test_clock_summary_parses_samples_and_throttle_reasons():
+    """The clock record of the timed region: median SM clock, the maximum clock and every throttle reason
+    seen active (the ones that reject a run, and sw_power_cap, which is kept and noted)."""
+    import bench
+    cs = bench.ClockSampler()
+    na = "Not Active"
+    cs.lines = [
+        f"0, 2070, 2070, 812.4, 0x0, {na}, {na}, {na}, {na}",
+        f"0, 1980, 2070, 1390.2, 0x4, {na}, {na}, {na}, Active",
+        f"0, 2055, 2070, 1201.0, 0x0, {na}, {na}, {na}, {na}",
+        "0, [N/A], 2070, 0, 0x0",              # malformed and short lines are skipped
+        "",
+    ]
+    s = cs.summary()
+    assert s["sm_mhz"] == 2055 and s["sm_max_mhz"] == 2070 and s["samples"] == 3
+    assert s["reasons"] == ["sw_power_cap"]
+    cs.lines.append(f"0, 1500, 2070, 1400.0, 0x40, {na}, Active, {na}, {na}")
+    assert cs.summary()["reasons"] == ["hw_thermal_slowdown", "sw_power_cap"]
+    assert bench.ClockSampler().summary() == {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
