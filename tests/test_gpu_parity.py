@@ -433,6 +433,22 @@ def test_gpu_iteration_study_matches_paper_trend(B, torch):
     assert all(b > 1.15 * a for a, b in zip(its["conv"], its["conv"][1:])), its
 
 
+def test_concentric_largest_eigenvalue_from_gpu_matrix(B, torch):
+    """Sec. 7.2's printed largest-magnitude eigenvalue of A^2 (concentric circles: 100 inner and 200 outer
+    elements, omega = 1, eps = 1, 2, 3; Q = 10), taken from the matrix the GPU assembles: 'mod' to the printed
+    four digits, 'orig' within 1 % (its printed imaginary part is 0.7 % off the oracle's)."""
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")) as fh:
+        g = json.load(fh)["concentric_largest_eig"]
+    wp = W.concentric(g["n_inner"], g["n_outer"], g["omega"], eps=tuple(g["eps"]))
+    for form, tol in (("mod", 1e-3), ("orig", 0.01 * abs(complex(*g["orig"])))):
+        A = gpu_matrix(B, torch, wp, quad_order=10, form=form)["main"]
+        ev = np.linalg.eigvals(A @ A)
+        lam = ev[np.argmax(np.abs(ev))]
+        assert abs(lam - complex(*g[form])) < tol, (form, lam)
+
+
 def test_concentric_gpu_solution_matches_two_layer_series(B, torch):
     """Concentric circles (Sec. 7.2): mixed-precision GPU solutions of the 'mod' system, far field against the
     two-layer series (first order in N) and the traces against the oracle's LU solution."""
