@@ -3,10 +3,11 @@ mpmath on every branch: the ascending series (x < 2), the Taylor steps from the 
 (2 <= x < 35), Hankel's expansion (x >= 35), and the branch boundaries.  Errors are measured relative to
 |H0| for J0, Y0 and to |H1| for J1, Y1 (the Hankel functions the kernels are made of, Sec. 3.3).
 
-Two entry points are checked: bessel01_f2, the double-float path of the assembly and matrix-free kernels, and
-bessel01, the FP64 path of the self terms and the near field.  The host build runs the same source as the
-device build except for the table loads, the warp-uniform choices and the FP32 reciprocal-square-root seed
-(refined by Newton steps on both)."""
+Three paths are checked: bessel01_f2, the double-float path of the assembly and matrix-free kernels;
+bessel01, the FP64 path of the self terms and the near field; and the FP64 routines (Miller's recurrence below
+18, the 22-term expansion beyond) from which the host builds the Taylor table.  The host build runs the same
+source as the device build except for the table loads, the warp-uniform choices and the FP32
+reciprocal-square-root seed (refined by Newton steps on both)."""
 import os
 import shutil
 import subprocess
@@ -49,7 +50,7 @@ def values(tmp_path_factory):
     out = subprocess.run([exe], input="\n".join(repr(float(v)) for v in xs), capture_output=True, text=True,
                          check=True).stdout
     got = np.array([[float.fromhex(t) for t in line.split()] for line in out.strip().splitlines()])
-    assert got.shape == (len(xs), 9) and np.array_equal(got[:, 0], xs)
+    assert got.shape == (len(xs), 13) and np.array_equal(got[:, 0], xs)
     mpmath.mp.dps = 30
     ref = np.array([[float(mpmath.besselj(0, x)), float(mpmath.bessely(0, x)), float(mpmath.besselj(1, x)),
                      float(mpmath.bessely(1, x))] for x in xs])
@@ -76,4 +77,12 @@ def test_fp64_path_matches_mpmath(values, lo, hi, bound):
     xs, got, ref = values
     sel = (xs >= lo) & (xs < hi)
     err = _rel_err(got[sel, 5:9], ref[sel])
+    assert sel.sum() > 30 and err.max() <= bound, (err.max(), xs[sel][np.argmax(err)])
+
+
+@pytest.mark.parametrize("lo,hi,bound", [(0.0, 2.0, 1e-15), (2.0, 18.0, 2e-15), (18.0, np.inf, 2e-15)])
+def test_table_builders_match_mpmath(values, lo, hi, bound):
+    xs, got, ref = values
+    sel = (xs >= lo) & (xs < hi)
+    err = _rel_err(got[sel, 9:13], ref[sel])
     assert sel.sum() > 30 and err.max() <= bound, (err.max(), xs[sel][np.argmax(err)])
