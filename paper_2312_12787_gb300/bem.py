@@ -99,7 +99,9 @@ def load(path: str | None = None):
     for name in ("bem_batch_create", "bem_batch_admit", "bem_batch_step", "bem_batch_query", "bem_batch_take",
                  "bem_batch_solve_planewave"):
         getattr(L, name).restype = i
+    L.bem_last_error.argtypes = []
     L.bem_last_error.restype = ctypes.c_char_p
+    L.bem_version.argtypes = []
     L.bem_version.restype = ctypes.c_char_p
     for name in ("bem_problem_create", "bem_set_opts", "bem_set_domains", "bem_add_segment", "bem_assemble",
                  "bem_get_matrix", "bem_rhs_planewave", "bem_matvec", "bem_residual", "bem_residual_noalloc", "bem_solve", "bem_solve_planewave",

@@ -145,3 +145,40 @@ def test_empty_and_null_arguments_rejected_before_device_work(lib):
     assert L.bem_residual_noalloc(h, 1, buf, ctypes.c_void_p(1 << 21), ctypes.c_void_p(1 << 22), None) == lib.BEM_ESTATE
     assert L.bem_num_unknowns(None) == 0 and L.bem_footprint_bytes(h, 0) == 0
     p.close()
+
+
+def test_binding_signatures_match_the_header(lib):
+    """Every entry point of include/bem.h has ctypes argument types in the binding, one per declared parameter
+    and of the declared kind (pointers as pointers, so that no 64-bit address is passed as a C int)."""
+    import ctypes
+    L = lib.load()
+    txt = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "bem.h")).read(), flags=re.S)
+    decls = re.findall(r"BEM_API\s+([\w\s\*]+?)\b(bem_\w+)\s*\(([^)]*)\)", txt)
+    assert len(decls) == len(_declared())
+    ptr_types = (ctypes.c_void_p, ctypes.c_char_p)
+    for ret, name, params in decls:
+        params = [q.strip() for q in params.split(",") if q.strip() and q.strip() != "void"]
+        f = getattr(L, name)
+        assert f.argtypes is not None and len(f.argtypes) == len(params), name
+        for q, t in zip(params, f.argtypes):
+            if "*" in q:
+                assert t in ptr_types or issubclass(t, ctypes._Pointer), (name, q, t)
+            elif "long long" in q:
+                assert t is ctypes.c_longlong, (name, q, t)
+            elif "size_t" in q:
+                assert t is ctypes.c_size_t, (name, q, t)
+            elif "double" in q:
+                assert t is ctypes.c_double, (name, q, t)
+            else:
+                assert t is ctypes.c_int, (name, q, t)
+        ret = ret.strip()
+        if "*" in ret:
+            assert f.restype in ptr_types, (name, ret)
+        elif ret == "void":
+            assert f.restype is None, name
+        elif ret == "long long":
+            assert f.restype is ctypes.c_longlong, name
+        elif ret == "size_t":
+            assert f.restype is ctypes.c_size_t, name
+        else:
+            assert f.restype is ctypes.c_int, (name, ret, f.restype)
