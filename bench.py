@@ -445,7 +445,8 @@ def main():
         ach = ASM_WARP_INST_N3072 * scale / avg_s / 1e9
         roof.update({"kernel": "k_assemble (issue-bound: FP64 geometry + double-float Bessel on FP32)", "bound": "alu",
                      "achieved": ach, "peak": ISSUE_PEAK_G, "unit": "G warp instructions/s", "frac": ach / ISSUE_PEAK_G,
-                     "traffic": ASM_DRAM_BYTES_N3072 * scale,
+                     # the kernel changed after the capture (occupancy, Bessel clean-up): no current counters
+                     "traffic": None, "traffic_before_last_change": ASM_DRAM_BYTES_N3072 * scale,
                      "peak_source": "derived: 152 SMs x 4 issue slots/clk x 2.07 GHz"})
     elif ph == "matvec":
         # one kernel per product: the GEMM (its stream-K reduction is timed as the "reduce" phase)
@@ -454,7 +455,9 @@ def main():
         ach = bytes_per / avg_s / 1e9
         roof.update({"kernel": "k_gemm_tc (tcgen05 FP16x3 multi-RHS GEMM; its stream-K reduction is the reduce phase)", "bound": "hbm",
                      "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "peak_source": src,
-                     "traffic": GEMM_DRAM_BYTES_N3072 * scale if N_RHS > 1 else None})
+                     # the kernel changed after the capture (set-up order, 32-bit range split): no current counters
+                     "traffic": None,
+                     "traffic_before_last_change": GEMM_DRAM_BYTES_N3072 * scale if N_RHS > 1 else None})
     else:
         # launches per refinement residual: 11 (12 with a K split) with the tensor-core small terms
         n_gemm = max(1, ph_n // RESID_LAUNCHES_TC)
