@@ -182,3 +182,17 @@ def test_binding_signatures_match_the_header(lib):
             assert f.restype is ctypes.c_size_t, name
         else:
             assert f.restype is ctypes.c_int, (name, ret, f.restype)
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    """There is no CPU fallback: without libbem.so the binding raises instead of computing anything."""
+    import subprocess
+    import sys
+    code = ("import paper_2312_12787_gb300.bem as b\n"
+            "b.LIB_PATH = %r\n"
+            "try:\n"
+            "    b.Problem()\n"
+            "except RuntimeError as e:\n"
+            "    print('raised:', e)\n" % str(tmp_path / "libbem.so"))
+    out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=300)
+    assert out.returncode == 0 and "raised:" in out.stdout and "missing" in out.stdout, out.stdout + out.stderr
