@@ -412,3 +412,94 @@ def test_iterations_flat_in_n_for_proposed_forms_growing_for_conventional():
     assert its["conv"][1] > 1.2 * its["conv"][0]
     assert abs(its["mod"][1] - its["mod"][0]) <= 1 and abs(its["beta1"][1] - its["beta1"][0]) <= 1
     assert its["mod"][1] < its["beta1"][1] < its["conv"][1]
+
+
+# ------------------------------------------------------------------------------------------------
+# the arrangements compared in Sec. 5-7 at the level of the discrete solution
+# ------------------------------------------------------------------------------------------------
+
+def _lu_solutions(p, theta=0.3, Q=4, forms=O.FORMS):
+    return {f: O.solve_lu(O.assemble(p, Q=Q, form=f), O.rhs_planewave(p, theta, form=f)) for f in forms}
+
+
+def test_single_material_arrangements_are_one_discrete_system():
+    """One material: eq. naive_bie (conventional), eq. calderon_bie1 (beta = 1) and eq. calderon_bieb
+    (beta = -alpha) hold the same two equations per element (the host's Burton-Miller equation and the
+    scatterer's standard equation), only reordered (conventional) or with the standard rows scaled (beta):
+    their collocation systems have one solution.  'orig' differs from 'mod' only on interior lower rows,
+    which one material does not have, so its matrix is 'mod's."""
+    p = W.circle_problem(128, 5.0, 7.5, 2.25)
+    assert np.array_equal(O.assemble(p, Q=4, form="orig"), O.assemble(p, Q=4, form="mod"))
+    xs = _lu_solutions(p)
+    ref = xs["mod"]
+    for f in ("beta1", "conv"):
+        assert np.linalg.norm(xs[f] - ref) / np.linalg.norm(ref) < 1e-12, f
+
+
+@pytest.mark.parametrize("geo", ["concentric", "junction"])
+def test_multi_material_arrangements_pair_up(geo):
+    """Several materials (Sec. 6): the conventional system (eq. 3dom_conv_bie: the host's Burton-Miller
+    equation, every interior domain's standard equation) and 'orig' (eq. 3dom_calderon_bie0: the same
+    equations, the standard ones scaled by -alpha, rows per element swapped) have one solution; 'beta1'
+    only rescales 'mod's standard rows, so it shares 'mod's solution.  'mod' replaces interior standard
+    equations by Burton-Miller ones (gamma = alpha/eps), a different discretisation of the same problem:
+    its solution differs at discretisation level, which shows the comparison can tell the two apart."""
+    if geo == "concentric":
+        p = W.concentric(40, 80, 1.0, eps=(1.0, 2.0, 3.0))
+    else:
+        p = W.junction_disk(160, k=(5.0, 7.5, 9.0))
+    xs = _lu_solutions(p)
+    rel = lambda a, b: np.linalg.norm(a - b) / np.linalg.norm(b)  # noqa: E731
+    assert rel(xs["conv"], xs["orig"]) < 1e-12
+    assert rel(xs["beta1"], xs["mod"]) < 1e-12
+    assert rel(xs["mod"], xs["orig"]) > 1e-4
+
+
+def test_arrangement_pin_catches_a_dropped_burton_miller_row(monkeypatch):
+    """Plant a plausible mistake in the oracle's conventional plan (the host's lower-order equation taken as
+    the standard one, i.e. alpha dropped from the Burton-Miller row): the solution then no longer equals the
+    proposed arrangement's, so the equality above pins the conventional plan."""
+    p = W.circle_problem(96, 5.0, 7.5, 2.25)
+    good = _lu_solutions(p, forms=("mod",))["mod"]
+    orig_plan = O.bem_oracle.row_plan
+
+    def broken(el, k, form="mod"):
+        up, lo = orig_plan(el, k, form)
+        if form == "conv":
+            up = (up[0], np.where(up[1] == "bm", "std", up[1]).astype(object), up[2])
+        return up, lo
+    monkeypatch.setattr(O.bem_oracle, "row_plan", broken)
+    bad = _lu_solutions(p, forms=("conv",))["conv"]
+    assert np.linalg.norm(bad - good) / np.linalg.norm(good) > 1e-6
+
+
+def test_orig_and_conv_converge_to_two_layer_series():
+    """Sec. 7.2: the 'orig' and conventional arrangements discretise the same concentric problem; their far
+    fields approach the two-layer series at first order as 'mod's do."""
+    om = 1.0
+    eps = (1.0, 2.0, 3.0)
+    k = [om * np.sqrt(e) for e in eps]
+    ang = np.linspace(0, 2 * np.pi, 24, endpoint=False)
+    ref = O.mie2_far_field(k, eps, ang)
+    for f in ("orig", "conv"):
+        errs = []
+        for N in (150, 300):
+            p = W.concentric(N // 3, 2 * N // 3, om, eps=eps)
+            x = O.solve_lu(O.assemble(p, Q=10, form=f), O.rhs_planewave(p, 0.0, form=f))
+            errs.append(np.linalg.norm(O.far_field(p, x, ang, Q=10) - ref) / np.linalg.norm(ref))
+        assert errs[-1] < 5e-3 and errs[0] / errs[1] > 1.6, (f, errs)
+
+
+def test_orig_and_conv_equal_halves_junction_match_mie():
+    """Equal halves make the diameter a fictitious interface: 'orig' and the conventional arrangement of the
+    junction disk converge to the circle's series, as 'mod' does."""
+    k1, k2, e2 = 5.0, 7.5, 2.25
+    ang = np.linspace(0, 2 * np.pi, 32, endpoint=False)
+    ffm = O.mie_far_field(k1, k2, e2, ang)
+    for f in ("orig", "conv"):
+        errs = []
+        for n in (128, 256):
+            p = W.junction_disk(n, k=(k1, k2, k2), eps=(1.0, e2, e2))
+            x = O.solve_lu(O.assemble(p, Q=10, form=f), O.rhs_planewave(p, 0.0, form=f))
+            errs.append(np.linalg.norm(O.far_field(p, x, ang, Q=10) - ffm) / np.linalg.norm(ffm))
+        assert errs[-1] < 6e-3 and errs[0] / errs[1] > 1.5, (f, errs)
