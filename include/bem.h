@@ -168,8 +168,11 @@ BEM_API bem_status bem_residual(bem_problem* p, int n_rhs, const bem_c64* x_dev,
  * memory limit) use this entry point instead.  Its scratch is a fixed static device array of 2 x 524288
  * complex FP32 entries (8 MiB) that every GPU loading the library holds until exit; n_rhs * 2N must not
  * exceed 524288 (BEM_EINVAL otherwise).  The problem must already be assembled (BEM_ESTATE otherwise;
- * this call never assembles).  The first call on each device looks up the array's device address on the
- * current device.  All calls share the one array: calls whose kernels overlap on the GPU (different
+ * this call never assembles).  Set-up: the assembly of a mixed-precision problem on a device (bem_assemble,
+ * the solve entry points, bem_batch_admit), which allocates anyway, also looks up the array's device address
+ * on that device and loads the residual kernels there (under lazy module loading both would otherwise take
+ * device memory at their first use); so no call of this entry point allocates, the first one included.  All
+ * calls share the one array and each overwrites it: calls whose kernels overlap on the GPU (different
  * streams, or different threads) race on it and must be serialised by the caller.  Nothing in it needs
  * clearing between calls: each call writes every entry it reads. */
 BEM_API bem_status bem_residual_noalloc(bem_problem* p, int n_rhs, const bem_c64* x_dev, const bem_c64* b_dev,
@@ -258,6 +261,14 @@ typedef enum {
 } bem_phase;
 BEM_API bem_status bem_profile_enable(bem_problem* p, int on);
 BEM_API bem_status bem_profile_read(bem_problem* p, double* ms_host, long long* launches_host);
+
+/* Failure-path testing: the limit, in seconds, of the waits in the main loop of the tensor-core product
+ * kernels launched from now on (process-wide; 0 restores the default of 2 s; CUDA graphs that the solver
+ * recorded earlier keep the limit they were recorded with).  A wait that runs out records an error word that
+ * the host reads after the product (BEM_ETIMEOUT); the kernel then stops issuing work, waits with the default
+ * limit for its own copies and MMAs in flight, frees its tensor memory and returns, so the context stays
+ * usable.  EINVAL outside [0, 10]. */
+BEM_API bem_status bem_test_set_wait_limit(double seconds);
 
 /* Thread-local message of the last failure in this thread ("" if none). */
 BEM_API const char* bem_last_error(void);

@@ -27,7 +27,7 @@ EXPORTS = [
     "bem_get_matrix", "bem_rhs_planewave", "bem_matvec", "bem_residual", "bem_residual_noalloc", "bem_solve", "bem_solve_planewave", "bem_far_field",
     "bem_solve_planewave_host", "bem_near_field", "bem_profile_enable", "bem_profile_read", "bem_last_error", "bem_version",
     "bem_batch_create", "bem_batch_destroy", "bem_batch_admit", "bem_batch_step", "bem_batch_query",
-    "bem_batch_take", "bem_batch_free_units", "bem_batch_solve_planewave",
+    "bem_batch_take", "bem_batch_free_units", "bem_batch_solve_planewave", "bem_test_set_wait_limit",
 ]
 PHASES = ["geometry", "assemble", "rhs", "matvec", "arnoldi", "givens", "update", "residual", "farfield", "other",
           "reduce"]
@@ -99,6 +99,8 @@ def load(path: str | None = None):
     for name in ("bem_batch_create", "bem_batch_admit", "bem_batch_step", "bem_batch_query", "bem_batch_take",
                  "bem_batch_solve_planewave"):
         getattr(L, name).restype = i
+    L.bem_test_set_wait_limit.argtypes = [d]
+    L.bem_test_set_wait_limit.restype = i
     L.bem_last_error.argtypes = []
     L.bem_last_error.restype = ctypes.c_char_p
     L.bem_version.argtypes = []
@@ -360,6 +362,11 @@ class Batch:
                                                      rs.ctypes.data_as(ctypes.c_void_p), _stream_ptr(stream)),
                     allow_noconv=True)
         return st, it, rs
+
+
+def bem_test_set_wait_limit(seconds: float) -> None:
+    """Main-loop wait limit of the tensor-core kernels launched from now on (0 = default); for failure tests."""
+    _check(load().bem_test_set_wait_limit(float(seconds)))
 
 
 def bem_version() -> str:

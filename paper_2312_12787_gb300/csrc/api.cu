@@ -330,6 +330,9 @@ bem_status assemble_impl(bem_problem* p, cudaStream_t s, bool force = false) {
   p->A_mixed = mixed;
   p->mat_dirty = false;
   p->a16_dirty = true;
+  // the no-allocation residual needs an assembled mixed matrix: its one-time set-up on this device (which
+  // takes device memory under lazy module loading) belongs here, where the library allocates anyway
+  if (mixed) return noalloc_setup();
   return BEM_OK;
 }
 
@@ -883,7 +886,7 @@ bem_status problem_prepare_batched(bem_problem* p, cudaStream_t s, AsmJob* job, 
   p->mat_dirty = false;
   p->a16_dirty = true;
   *opts = p->o;
-  return BEM_OK;
+  return noalloc_setup();   // as in assemble_impl
 }
 }  // namespace bem
 
@@ -1242,6 +1245,12 @@ BEM_API bem_status bem_profile_read(bem_problem* p, double* ms, long long* launc
     if (ms) ms[k] = t;
     if (launches) launches[k] = p->launches[k];
   }
+  return BEM_OK;
+}
+
+BEM_API bem_status bem_test_set_wait_limit(double seconds) {
+  if (!(seconds >= 0.0) || seconds > 10.0) return fail(BEM_EINVAL, "wait limit must be in [0, 10] s");
+  matvec_tc_set_wait_ns((unsigned long long)(seconds * 1e9));
   return BEM_OK;
 }
 

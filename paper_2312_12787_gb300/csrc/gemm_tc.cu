@@ -91,13 +91,14 @@ __device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait: false (and the error code recorded) if the phase does not complete within kWaitNs.
-__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, int* err, int code) {
+// Bounded wait: false (and the error code recorded) if the phase does not complete within limit_ns.
+__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, int* err, int code,
+                                          unsigned long long limit_ns = kWaitNs) {
   if (mbar_try(a, parity)) return true;
   const unsigned long long t0 = gtime();
   while (true) {
     if (mbar_try(a, parity)) return true;
-    if (gtime() - t0 > kWaitNs) {
+    if (gtime() - t0 > limit_ns) {
       atomicCAS(err, 0, code);
       return false;
     }
@@ -178,11 +179,12 @@ struct SegWalk {
 };
 
 // One CTA per stream-K range.  partial: G x 2 x kM x kN FP32 (slot 0 = first row tile of the range, 1 = the
-// next one).
+// next one).  wait_ns bounds the waits of the main loop (normally kWaitNs); the waits that drain this CTA's
+// own copies and MMAs before it releases TMEM always keep kWaitNs.
 __global__ void __launch_bounds__(kThreads, 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap mapAh, const __grid_constant__ CUtensorMap mapAl,
               const __grid_constant__ CUtensorMap mapBh, const __grid_constant__ CUtensorMap mapBl, int n,
-              int kpt, long long total, float* partial, int* err, const int* gate) {
+              int kpt, long long total, float* partial, int* err, const int* gate, unsigned long long wait_ns) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   Bars* bars = reinterpret_cast<Bars*>(smem + kStages * kStage);
@@ -238,7 +240,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int it = 0; it < nk; ++it) {
         const int st = it % kStages;
         const uint32_t ph = (uint32_t)((it / kStages) & 1);
-        if (!mbar_wait(su32(&bars->empty[st]), ph ^ 1u, err, 1)) break;
+        if (!mbar_wait(su32(&bars->empty[st]), ph ^ 1u, err, 1, wait_ns)) break;
         if (*(volatile int*)err) break;
         unsigned char* base = smem + st * kStage;
         const uint32_t fb = su32(&bars->full[st]);
@@ -262,13 +264,16 @@ __global__ void __launch_bounds__(kThreads, 1)
       while (ok && w.next(beg, end, tile_end)) {
         const int b = seg & 1;
         // the buffer must have been drained by the readers (segments seg-2, seg-4, ...)
-        if (!mbar_wait(su32(&bars->acce[b]), (uint32_t)(((seg >> 1) & 1) ^ 1), err, 2)) { ok = false; break; }
+        if (!mbar_wait(su32(&bars->acce[b]), (uint32_t)(((seg >> 1) & 1) ^ 1), err, 2, wait_ns)) {
+          ok = false;
+          break;
+        }
         tc_fence_after();
         const uint32_t d1 = tmem + (uint32_t)(b * 2 * kN), d2 = d1 + (uint32_t)kN;
         for (int it = beg; it < end; ++it) {
           const int st = it % kStages;
           const uint32_t ph = (uint32_t)((it / kStages) & 1);
-          if (!mbar_wait(su32(&bars->full[st]), ph, err, 3)) { ok = false; break; }
+          if (!mbar_wait(su32(&bars->full[st]), ph, err, 3, wait_ns)) { ok = false; break; }
           tc_fence_after();
           unsigned char* base = smem + st * kStage;
           const uint64_t dah = sdesc(su32(base)), dal = sdesc(su32(base + kTile));
@@ -303,7 +308,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     while (ok && w.next(beg, end, tile_end)) {
       const int b = seg & 1;
       // the TMEM loads below are warp-collective: the whole warp proceeds or stops together
-      ok = __all_sync(0xffffffffu, mbar_wait(su32(&bars->accf[b]), (uint32_t)((seg >> 1) & 1), err, 5));
+      ok = __all_sync(0xffffffffu, mbar_wait(su32(&bars->accf[b]), (uint32_t)((seg >> 1) & 1), err, 5, wait_ns));
       if (!ok) break;
       tc_fence_after();
       const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * 2 * kN);
@@ -547,6 +552,9 @@ int grid_of(int n) {
 
 size_t b_bytes(int n) { return (size_t)kN * ld16(n) * 2; }
 
+// Main-loop wait limit of the kernels launched from now on (graphs keep the value they were recorded with).
+std::atomic<unsigned long long> g_wait_ns{kWaitNs};
+
 bool smem_attr_set() {
   static std::atomic<int> done[kMaxDev];
   int dev = 0;
@@ -636,7 +644,7 @@ cudaError_t launch_matvec_tc(const void* a16, int n, int nrhs, const float2* x, 
     k_tc_prep_b<<<dim3((n + 255) / 256, kMaxRhs), 256, 0, s>>>(x, n, nrhs, cmax, bhi, blo, ld, tsc, gate);
   }
   cudaError_t e = launch_pdl(k_gemm_tc, dim3(G), dim3(kThreads), kSmemBytes, s, mAh, mAl, mBh, mBl, n, kpt, total,
-                             part, err, gate);
+                             part, err, gate, g_wait_ns.load(std::memory_order_relaxed));
   if (e != cudaSuccess || stage == 1) return e;
   return launch_pdl(k_tc_reduce, dim3((n + kRedRows - 1) / kRedRows), dim3(256), 0, s, part, n, nrhs, kpt, total, G,
                     rsc, x ? tsc : static_cast<const float*>(nullptr), y, gate);
@@ -651,5 +659,7 @@ void matvec_tc_b_operand(void* ws, int n, void** bhi, void** blo, size_t* ldb) {
 size_t matvec_tc_b_bytes(int n) { return 2 * b_bytes(n); }
 
 cudaError_t matvec_tc_setup() { return smem_attr_set() && encode_fn() ? cudaSuccess : cudaErrorNotSupported; }
+
+void matvec_tc_set_wait_ns(unsigned long long ns) { g_wait_ns.store(ns ? ns : kWaitNs, std::memory_order_relaxed); }
 
 }  // namespace bem

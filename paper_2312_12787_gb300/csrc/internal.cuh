@@ -150,6 +150,12 @@ cudaError_t launch_residual_split_tc(const float2* Ahi, const float2* Alo, size_
                                      cudaStream_t s, int* nlaunch = nullptr);
 cudaError_t launch_residual_c64(const double2* A, size_t lda, int n, int nrhs, const double2* x, const double2* b,
                                 double2* r, cudaStream_t s);
+// Load the kernels of launch_residual_split (without a tensor-core workspace) on the current device, so that
+// a later call does not load them lazily (which takes device memory).
+cudaError_t residual_split_preload();
+// Set-up of the no-allocation residual on the current device (noalloc.cu): looks up its static scratch
+// array and loads its kernels.  Called where the library allocates anyway (assembly of mixed problems).
+bem_status noalloc_setup();
 // tcgen05 tensor-core GEMM Y = A X (A c32, X / Y c32, nrhs <= 64).  Returns cudaErrorNotSupported if the
 // shape is not supported by the kernel.
 // tcgen05 tensor-core GEMM Y = A X (X / Y complex FP32, 2 <= nrhs <= 64) on the FP16 split copy of A that
@@ -166,6 +172,8 @@ void matvec_tc_b_operand(void* ws, int n, void** bhi, void** blo, size_t* ldb);
 size_t matvec_tc_b_bytes(int n);
 // One-time settings of the tensor-core kernel (shared-memory limit); call before recording it in a graph.
 cudaError_t matvec_tc_setup();
+// Main-loop wait limit (ns) of the tensor-core kernels launched from now on; 0 restores the default (2 s).
+void matvec_tc_set_wait_ns(unsigned long long ns);
 cudaError_t matvec_tc_clear_error(void* ws, int n, int nrhs, cudaStream_t s);
 size_t matvec_tc_a16_bytes(int n);
 cudaError_t launch_tc_prepare_a(const float2* A, int n, void* a16, cudaStream_t s);

@@ -698,6 +698,14 @@ cudaError_t launch_residual_split(const float2* Ahi, const float2* Alo, size_t l
   return cudaGetLastError();
 }
 
+cudaError_t residual_split_preload() {
+  cudaFuncAttributes a;
+  cudaError_t e = cudaFuncGetAttributes(&a, k_split_x);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_resid_df_gemv);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_resid_df_gemm<true>);
+  return e;
+}
+
 size_t residual_tc_ws_bytes(int n, int nrhs) {
   return ((4 * (size_t)nrhs * n * sizeof(float2)) + 255) & ~(size_t)255;
 }

@@ -6,8 +6,16 @@
 // latency-bound loop in which a cudaMalloc would stall or synchronise the device, or a process running
 // close to its memory limit where a new allocation could fail halfway through a computation.  For them,
 // bem_residual_noalloc runs the same double-float residual kernels with their scratch in a fixed static
-// device array of this file (kNoAllocMaxEntries complex entries for x_hi plus as many for x_lo, 8 MiB in
-// all), which every GPU that loads the library holds until the process exits.
+// device array of this file (2 x kNoAllocMaxEntries complex FP32 entries, 8 MiB), which every GPU that
+// loads the library holds until the process exits.
+//
+// Set-up.  Under CUDA's lazy module loading the array (and the residual kernels, which live in another
+// translation unit) only become resident on a device when first touched, and that costs device memory.  So
+// the set-up, which looks up the array's device address with cudaGetSymbolAddress and loads the residual
+// kernels, runs from calls that allocate anyway: the assembly of a mixed-precision problem (bem_assemble and
+// the solve entry points) and the batched admission.  bem_residual_noalloc then only reads the cached
+// address.  Should a device reach it without that set-up (not possible through the public interface, since
+// it needs an assembled mixed-precision problem), the call performs the set-up itself.
 #include <mutex>
 
 #include "internal.cuh"
@@ -16,19 +24,20 @@ namespace {
 
 constexpr size_t kNoAllocMaxEntries = (size_t)1 << 19;   // n_rhs * 2N complex entries per call, at most
 
-// x_hi in the first kNoAllocMaxEntries entries, x_lo in the rest.  Device code could name the array
-// directly; host code only ever passes the device address obtained below.
+// x_hi and x_lo are packed back to back at the start of the array (n_rhs * 2N entries each).  Device code
+// could name the array directly; host code only ever passes the device address obtained below.
 static __device__ __align__(256) float2 g_noalloc_scratch[2 * kNoAllocMaxEntries];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_addr_mutex;
 void* g_addr[kMaxDevices] = {};
 
-// Device address of the scratch array on the current device, looked up once per device.
+// Device address of the scratch array on the current device, looked up once per device (and, at the same
+// time, the residual kernels loaded on it).
 bem_status scratch_address(void** out) {
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return bem::report_error(BEM_ECUDA, "cudaGetDevice failed in bem_residual_noalloc");
+  if (e != cudaSuccess) return bem::report_error(BEM_ECUDA, "cudaGetDevice failed in the no-allocation residual set-up");
   if (dev < 0 || dev >= kMaxDevices) return bem::report_error(BEM_EINVAL, "device index out of range");
   std::lock_guard<std::mutex> lock(g_addr_mutex);
   if (!g_addr[dev]) {
@@ -36,6 +45,8 @@ bem_status scratch_address(void** out) {
     e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
     if (e != cudaSuccess || !ptr)
       return bem::report_error(BEM_ECUDA, "cudaGetSymbolAddress of the static residual scratch failed");
+    e = bem::residual_split_preload();
+    if (e != cudaSuccess) return bem::report_error(BEM_ECUDA, "loading the residual kernels failed");
     g_addr[dev] = ptr;
   }
   *out = g_addr[dev];
@@ -43,6 +54,13 @@ bem_status scratch_address(void** out) {
 }
 
 }  // namespace
+
+namespace bem {
+bem_status noalloc_setup() {
+  void* ptr = nullptr;
+  return scratch_address(&ptr);
+}
+}  // namespace bem
 
 extern "C" BEM_API bem_status bem_residual_noalloc(bem_problem* p, int n_rhs, const bem_c64* x_dev,
                                                    const bem_c64* b_dev, bem_c64* r_dev, void* stream) {

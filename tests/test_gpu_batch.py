@@ -167,3 +167,26 @@ def test_high_contrast_concentric_converges_on_every_mixed_path(B, torch):
     q.close()
     assert st == B.BEM_OK and rs[0] <= 1e-8, (st, it, rs)
     assert rel(xb[0].cpu().numpy(), ref) <= SOLUTION_TOL_MIXED
+
+
+@pytest.mark.parametrize("form", ["orig", "conv", "beta1"])
+def test_batch_engine_forms_match_oracle_lu(B, torch, form):
+    """The comparison arrangements of Sec. 5-7 through the batched engine (which the omega / eps sweeps and
+    the junction study use): a few concentric and junction problems in one batch, each against the oracle's
+    LU solution of the same arrangement, element by element."""
+    cases = [W.concentric(30, 60, 1.0, eps=(1.0, 2.0, 3.0)),
+             W.concentric(40, 80, 2.0, eps=(1.0, 0.5, 2.0)),
+             W.junction_disk(120, k=(4.0, 6.0, 7.2)),
+             W.junction_disk(160, k=(3.0, 4.5, 6.0))]
+    angles = np.array([0.0, 0.7, 1.9, 3.3])
+    probs = [B.Problem.from_workload(wp, prec="mixed", form=form, tol=1e-10, max_iter=1000) for wp in cases]
+    xs = [torch.empty(p.bem_num_unknowns(), dtype=torch.complex128, device="cuda") for p in probs]
+    bt = B.Batch(len(cases), sum(p.bem_num_unknowns() for p in probs), form=form, tol=1e-10, max_iter=1000)
+    st, it, rs = bt.bem_batch_solve_planewave(probs, angles, xs)
+    assert st == B.BEM_OK and np.all(rs <= 1e-10), (form, st, it, rs)
+    for k, wp in enumerate(cases):
+        xl = O.solve_lu(O.assemble(wp, Q=4, form=form), O.rhs_planewave(wp, angles[k], form=form))
+        assert rel(xs[k].cpu().numpy(), xl) <= SOLUTION_TOL_MIXED, (form, k)
+    bt.close()
+    for p in probs:
+        p.close()

@@ -503,3 +503,12 @@ def test_orig_and_conv_equal_halves_junction_match_mie():
             x = O.solve_lu(O.assemble(p, Q=10, form=f), O.rhs_planewave(p, 0.0, form=f))
             errs.append(np.linalg.norm(O.far_field(p, x, ang, Q=10) - ffm) / np.linalg.norm(ffm))
         assert errs[-1] < 6e-3 and errs[0] / errs[1] > 1.5, (f, errs)
+
+
+def test_row_parallel_assembly_is_the_serial_assembly():
+    """The row-parallel driver only splits rows over spawned processes: its matrix is the serial one, bit for
+    bit, on a multi-material case whose upper and lower rows use different domains."""
+    p = W.junction_disk(120, k=(5.0, 7.5, 9.0))
+    for form in ("mod", "conv"):
+        assert np.array_equal(O.assemble_parallel(p, Q=4, form=form, workers=3, block=16),
+                              O.assemble(p, Q=4, form=form))

@@ -22,27 +22,28 @@ def B():
     return P
 
 
-def test_residual_noalloc_matches_residual(B):
+@pytest.mark.parametrize("prec,nrhs", [("mixed", 3), ("mixed", 5), ("mixed_tc", 5)])
+def test_residual_noalloc_matches_residual(B, prec, nrhs):
+    """n_rhs = 3 takes the per-row residual kernel, n_rhs = 5 the tiled one; on a tensor-core problem
+    bem_residual forms the small terms on the tensor cores and the no-allocation call on the FP32 pipes.
+    Free device memory is unchanged across every no-allocation call, the first one after assembly included
+    (assembly does the one-time set-up)."""
     import torch
     wp = W.Problem(k=[20.0, 30.0], eps=[1.0, 2.25],
                    segments=[W.Segment(W.star(300, 0.3, 5), P=0, M=1, closed=True)])
-    p = B.Problem.from_workload(wp, prec="mixed")
+    p = B.Problem.from_workload(wp, prec=prec)
     p.bem_assemble()                         # all allocation happens here, before the no-alloc calls
     n2 = p.bem_num_unknowns()
-    nrhs = 3
-    g = torch.Generator(device="cpu").manual_seed(42)
-    free_before = None
+    g = torch.Generator(device="cpu").manual_seed(42 + nrhs)
     for call in range(2):                    # two calls in a row, different inputs each time
         x = torch.randn((nrhs, n2), dtype=torch.complex128, generator=g).cuda()
         b = torch.randn((nrhs, n2), dtype=torch.complex128, generator=g).cuda()
         r_na = torch.full_like(b, complex(np.nan, np.nan))
         torch.cuda.synchronize()
-        if call == 1:
-            free_before = torch.cuda.mem_get_info()[0]
+        free_before = torch.cuda.mem_get_info()[0]
         p.bem_residual_noalloc(x, b, r_na, n_rhs=nrhs)
         torch.cuda.synchronize()
-        if call == 1:
-            assert torch.cuda.mem_get_info()[0] == free_before      # nothing allocated by the call
+        assert torch.cuda.mem_get_info()[0] == free_before, call     # nothing allocated by the call
         r_ref = torch.empty_like(b)
         p.bem_residual(x, b, r_ref, n_rhs=nrhs)                     # existing entry point
         A = torch.empty((n2, n2), dtype=torch.complex128, device="cuda")
