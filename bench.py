@@ -7,13 +7,17 @@ uniform on [0, 2 pi) solved as one multi-right-hand-side block, far field at 32 
 One step = the whole hot path on one batch: element geometry, assembly of A, plane-wave right-hand
 sides, GMRES solves of all 64 columns to relative residual `--tol`, far fields.  The headline `value`
 is the mixed-precision path (complex FP32 storage and Krylov basis, FP64 refinement); the plain FP64
-GPU path runs the same step for comparison (`fp64` key) and gives the accuracy reference.
+GPU path runs the same step for comparison (`fp64` key).  The CPU oracle solves the whole workload on
+the host cores (`cpu_baseline`), and its LU solution is the reference of the `accuracy` key.
+
+The same line carries two secondary keys, each with its own clock record and an FP64 comparator on
+identical problems: `sweep` (256 random stars solved as one batch) and `serving` (a Poisson stream of
+2000 requests through the continuous-batching loop, p50/p99 latency).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--fp64-steps S]
-                       [--workload star|sweep|serving|omega_eps]
-Other workloads: `sweep` = 256 random stars in one batch, `serving` = a Poisson request stream through the
-continuous-batching loop (p50/p99 latency), `omega_eps` = the frequency and contrast sweeps of Sec. 7.1
-and 7.2 as batched launches.
+                       [--workload star|sweep|serving|omega_eps] [--no-secondary] [--requests R]
+Other workloads print one leg alone: `sweep`, `serving`, and `omega_eps` (the frequency and contrast
+sweeps of Sec. 7.1 and 7.2 as batched launches).
 """
 from __future__ import annotations
 
@@ -35,20 +39,21 @@ sys.path.insert(0, ROOT)
 import workloads as W  # noqa: E402
 
 METRIC = "BEM solves/s (mixed vs FP64 GPU at err<=1e-6)"
-# Roofline inputs, from ncu counts of one launch on the star r = 1 + 0.3 cos 5t with N_e = 3072 (64 RHS),
-# scaled to other sizes by the number of matrix entries (profiles/assemble_star3072.md,
-# profiles/gemm_tc_star3072_64rhs.md):
-#  * k_assemble issues 2.547e9 warp instructions (sm__inst_executed.sum) over both the FP64 pipe (node
-#    geometry, phase reduction) and the FP32 pipe (double-float Bessel arithmetic); neither pipe alone binds,
-#    so its roofline is the issue rate: 4 warp instructions per clock per SM.  DRAM traffic 550.4 MB.
-#  * the multi-RHS GEMM streams A once: 2 x 2 bytes per real entry; measured DRAM traffic 316.3 MB.
+# Roofline inputs from ncu counts of single launches (profiles/assemble_star3072.md, profiles/gemm_tc_star4096_64rhs.md):
+#  * k_assemble issues 2.547e9 warp instructions (sm__inst_executed.sum) on the star r = 1 + 0.3 cos 5t with
+#    N_e = 3072, over both the FP64 pipe (node geometry, phase reduction) and the FP32 pipe (double-float Bessel
+#    arithmetic); neither pipe alone binds, so its roofline is the issue rate: 4 warp instructions per clock per
+#    SM.  Scaled to other sizes by the number of element pairs.  Its DRAM traffic is set once the current kernel
+#    is captured (None: no capture of the current kernel).
+#  * the multi-RHS GEMM streams the FP16 split copy of A once per launch: 2 x 2 bytes per real entry; its DRAM
+#    traffic per launch at N_e = 4096 (None until captured), scaled by the matrix size.
 #  * the refinement residual runs 16 FP32 operations per complex multiply-add on the FP32 pipe (four exact
 #    products summed with an offset accumulator, four operations each; the per-run offsets and the
 #    double-float fold are not counted), 128 operations per clock per SM; with the tensor-core product the
 #    small terms hi x_lo + lo x_hi are two FP16x3 GEMMs (11 kernels per residual, 12 with a K split).
 ASM_WARP_INST_N3072 = 2.546915828e9
-ASM_DRAM_BYTES_N3072 = 549714432 + 713728
-GEMM_DRAM_BYTES_N3072 = 311.3e6 + 5.0e6
+ASM_DRAM_BYTES_N3072 = None
+GEMM_DRAM_BYTES_N4096 = None
 RESID_FP32_OPS_PER_CMAC = 16
 RESID_LAUNCHES_TC = 11
 SM_COUNT, SM_CLOCK_HZ = 152, 2.07e9
@@ -153,49 +158,65 @@ def barrier(ws):
 # CPU oracle legs
 # ------------------------------------------------------------------------------------------------
 
-def oracle_sample(wp, rows=256, lu_ne=2048):
-    """Oracle timed on a bounded sample of the workload, scaled to one full step (64 solves):
-    assembly of `rows` of the 2N rows (scaled by 2N/rows) plus a direct solve with 64 right-hand sides of
-    the same star at N_e = lu_ne (scaled by (N_e/lu_ne)^3)."""
+def oracle_full(wp, ang, tol, gmres_cols=1, single_rows=128):
+    """The oracle on the whole workload, on every host core: the full matrix (rows split over spawned
+    processes, the oracle's arithmetic unchanged), the right-hand sides and a direct solve of all columns
+    (LAPACK LU, multi-threaded).  Also, for context: the single-process assembly time, extrapolated from
+    `single_rows` rows (labelled as such), and the paper's solver (the oracle's unrestarted MGS-GMRES) on
+    `gmres_cols` columns.  Returns (timings dict, LU solutions n_rhs x 2N)."""
     import oracle as O
+    workers = O.default_workers()
     n2 = 2 * wp.n_elem
-    sel = np.linspace(0, n2 - 1, rows).astype(int)
+    t0 = time.perf_counter()
+    A = O.assemble_parallel(wp, Q=4, workers=workers)
+    t_asm = time.perf_counter() - t0
+    t0 = time.perf_counter()
     el = O.elements(wp)
-    t0 = time.perf_counter()
-    O.assemble_rows(wp, sel, Q=4, el=el)
-    t_asm = (time.perf_counter() - t0) * n2 / rows
-    small = W.Problem(k=wp.k, eps=wp.eps, segments=[W.Segment(W.star(lu_ne, 0.3, 5), P=0, M=1, closed=True)])
-    A = O.assemble(small, Q=4)
-    B = np.stack([O.rhs_planewave(small, t) for t in W.plane_wave_angles(N_RHS)], 1)
-    t0 = time.perf_counter()
-    O.solve_lu(A, B)
-    t_lu = (time.perf_counter() - t0) * (wp.n_elem / lu_ne) ** 3
-    t_step = t_asm + t_lu
-    sample = (f"oracle assemble_rows on {rows} of {n2} rows (x{n2 / rows:.0f}) + LU solve of the same star at "
-              f"N_e={lu_ne} with {N_RHS} RHS (x{(wp.n_elem / lu_ne) ** 3:.0f}); assembly single-threaded numpy, "
-              f"LU multi-threaded LAPACK")
-    return N_RHS / t_step, t_step, sample
+    Bm = np.stack([O.rhs_planewave(wp, t, el=el) for t in ang], 1)
+    X = O.solve_lu(A, Bm).T.copy()
+    t_lu = time.perf_counter() - t0
+    out = {"cores": workers, "assembly_s": t_asm, "rhs_and_lu_s": t_lu, "n_rhs": len(ang)}
+    if single_rows:
+        rows = np.linspace(0, n2 - 1, single_rows).astype(int)
+        t0 = time.perf_counter()
+        O.assemble_rows(wp, rows, Q=4, el=el)
+        out["single_process_assembly_s"] = (time.perf_counter() - t0) * n2 / single_rows
+        out["single_process_assembly_extrapolated_from_rows"] = single_rows
+    if gmres_cols:
+        t0 = time.perf_counter()
+        its = [O.gmres(A, Bm[:, c], tol=tol)[1] for c in range(gmres_cols)]
+        out["gmres_s_per_column"] = (time.perf_counter() - t0) / gmres_cols
+        out["gmres_iters"] = its
+    return out, X
 
 
 def run_reference(args):
+    """The oracle as the reference arm: every timed step is the whole workload (full assembly on all host
+    cores + LU solve of the 64 plane waves); warm-up steps run a small star."""
     ws, rank, _ = dist_setup(args)
     if rank != 0:
         return
     wp = W.cfg_star_c2()
-    cores = os.cpu_count()
-    if args.warmup > 0:
-        oracle_sample(wp, rows=8, lu_ne=256)
-    vals = []
-    sample = ""
+    ang = W.plane_wave_angles(N_RHS)
+    small = W.cfg_star_c2(256)
+    for _ in range(args.warmup):
+        oracle_full(small, ang, args.tol, gmres_cols=0, single_rows=0)
+    t = []
+    info = {}
     for _ in range(max(1, args.steps)):
-        v, t, sample = oracle_sample(wp, rows=128, lu_ne=2048)
-        vals.append(v)
-    value = statistics.median(vals)
+        t0 = time.perf_counter()
+        info, _ = oracle_full(wp, ang, args.tol, gmres_cols=0, single_rows=0)
+        t.append(time.perf_counter() - t0)
+    ms = 1e3 * float(np.mean(t))
+    value = N_RHS / (ms / 1e3)
+    sample = (f"the whole workload each step: assembly of all {2 * wp.n_elem} rows on {info['cores']} host "
+              f"processes + LU solve of {N_RHS} right-hand sides (not extrapolated)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * N_RHS / value,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": wp.name, "n_elem": wp.n_elem, "n_rhs": N_RHS},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": info["cores"], "kind": "oracle",
+                             "sample": sample, "extrapolated": False},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -204,93 +225,155 @@ def run_reference(args):
 # GPU legs
 # ------------------------------------------------------------------------------------------------
 
-def run_batched_workload(args):
-    """Secondary measurements (not the headline line): the serving stream and the random-star sweep."""
+def _load_lib():
     import torch
     import paper_2312_12787_gb300 as P
-    from paper_2312_12787_gb300 import build as Bd, serve
+    from paper_2312_12787_gb300 import build as Bd
     Bd.build()
     P.load()
-    torch.cuda.set_device(0)
-    if args.workload == "omega_eps":
-        # The iteration studies of Sec. 7.1 (unit circle: GMRES iterations vs omega and vs eps_2) and Sec. 7.2
-        # (concentric circles: vs omega and vs eps_2 = 1/eps_3) for the proposed ("mod") arrangement and the
-        # others the paper compares ("orig": beta = -alpha on the standard rows only; "conv": conventional),
-        # each as one batch of all its problems
-        def run_batch(cases, form):
-            res = {}
-            for leg in ("warmup", "timed"):
-                probs = [P.Problem.from_workload(wp, prec="mixed", form=form, tol=args.tol, max_iter=1000)
-                         for _, _, wp in cases]
-                xs = [torch.empty(p.bem_num_unknowns(), dtype=torch.complex128, device="cuda") for p in probs]
-                bt = P.Batch(len(probs), sum(p.bem_num_unknowns() for p in probs), form=form, tol=args.tol,
-                             max_iter=1000)
-                torch.cuda.synchronize()
-                t0 = time.perf_counter()
-                st, it, rs = bt.bem_batch_solve_planewave(probs, np.zeros(len(probs)), xs)
-                torch.cuda.synchronize()
-                res[leg] = (time.perf_counter() - t0, it, rs)
-                bt.close()
-                for p in probs:
-                    p.close()
-            t, it, rs = res["timed"]
-            kinds = np.array([c[0] for c in cases])
-            return {"solves_per_s": len(cases) / t, "wall_s": t, "max_rel_resid": float(np.max(rs)),
-                    "iters_vs_omega": [int(v) for v in it[kinds == "omega"]],
-                    "iters_vs_eps": [int(v) for v in it[kinds == "eps"]]}
-        circ = W.cfg_omega_eps_sweep()
-        conc = W.cfg_concentric_sweep()
-        out = {"circle": {f: run_batch(circ, f) for f in ("mod", "conv")},
-               "concentric": {f: run_batch(conc, f) for f in ("mod", "orig", "conv")}}
-        line = {"metric": "omega / eps sweeps of Sec. 7 (one batch per geometry and arrangement, mixed)",
-                "value": out["circle"]["mod"]["solves_per_s"], "unit": "solves/s", "tol": args.tol,
-                "results": out,
-                "circle_omega": [c[1] for c in circ if c[0] == "omega"],
-                "circle_eps_2": [c[1] for c in circ if c[0] == "eps"],
-                "concentric_omega": [c[1] for c in conc if c[0] == "omega"],
-                "concentric_eps_3": [c[1] for c in conc if c[0] == "eps"],
-                "config": {"workload": "unit circle, 600 elements: 64 omega in [0.5, 20] (eps_2 = 2), 64 eps_2 in "
-                                       "[1.1, 10] (omega = 5); concentric circles, 600 + 1200 elements: 32 omega "
-                                       "in [0.5, 10] (eps_i = i), 32 eps_3 in [0.1, 10] with eps_2 = 1/eps_3 "
-                                       "(omega = 5); Q = 4"}}
-        print(json.dumps(line), flush=True)
-        return
-    if args.workload == "sweep":
-        stars = W.cfg_random_stars_c4()
-        res = {}
-        for leg in ("warmup", "timed"):
-            probs = [P.Problem.from_workload(wp, prec="mixed", tol=args.tol, max_iter=args.max_iter) for wp in stars]
-            xs = [torch.empty(p.bem_num_unknowns(), dtype=torch.complex128, device="cuda") for p in probs]
-            bt = P.Batch(256, sum(p.bem_num_unknowns() for p in probs), tol=args.tol, max_iter=args.max_iter)
-            torch.cuda.synchronize()
+    return torch, P
+
+
+def sweep_leg(args, clock_index=0):
+    """The random-star sweep (256 stars, N_e U[128, 2048], k_e U[1, 40]) solved as one batch by the mixed
+    engine, and the same 256 problems through the plain FP64 single-problem path one after another."""
+    torch, P = _load_lib()
+    stars = W.cfg_random_stars_c4()
+    res = {}
+    for leg in ("warmup", "timed"):
+        kw = dict(tol=args.tol, max_iter=args.max_iter, inner_tol=args.inner_tol, orth_passes=args.orth_passes)
+        probs = [P.Problem.from_workload(wp, prec="mixed", **kw) for wp in stars]
+        xs = [torch.empty(p.bem_num_unknowns(), dtype=torch.complex128, device="cuda") for p in probs]
+        bt = P.Batch(len(stars), sum(p.bem_num_unknowns() for p in probs), **kw)
+        torch.cuda.synchronize()
+        with ClockSampler(clock_index) as clk:
             t0 = time.perf_counter()
             st, it, rs = bt.bem_batch_solve_planewave(probs, np.zeros(len(stars)), xs)
+            torch.cuda.synchronize()
+            t = time.perf_counter() - t0
+        res[leg] = (t, it, rs, xs, clk.summary())
+        bt.close()
+        for p in probs:
+            p.close()
+    t, it, rs, xs, clocks = res["timed"]
+    # the FP64 comparator on the identical problems (one warm-up solve first)
+    it64, rs64, err = [], [], []
+    q = P.Problem.from_workload(stars[0], prec="fp64", tol=args.tol, max_iter=600)
+    q.bem_solve_planewave([0.0], torch.empty((1, q.bem_num_unknowns()), dtype=torch.complex128, device="cuda"))
+    q.close()
+    torch.cuda.synchronize()
+    with ClockSampler(clock_index) as clk64:
+        t0 = time.perf_counter()
+        x64s = []
+        for wp in stars:
+            q = P.Problem.from_workload(wp, prec="fp64", tol=args.tol, max_iter=600)
+            x64 = torch.empty((1, q.bem_num_unknowns()), dtype=torch.complex128, device="cuda")
+            _, i64, r64 = q.bem_solve_planewave([0.0], x64)
+            q.close()
+            it64.append(int(i64[0]))
+            rs64.append(float(r64[0]))
+            x64s.append(x64[0])
+        torch.cuda.synchronize()
+        t64 = time.perf_counter() - t0
+    for xm, x64 in zip(xs, x64s):
+        err.append((torch.linalg.vector_norm(xm - x64) / torch.linalg.vector_norm(x64)).item())
+    return {"metric": "random-star sweep solves/s (one mixed batch) vs FP64 one problem at a time",
+            "value": len(stars) / t, "unit": "solves/s", "wall_s": t, "n_problems": len(stars),
+            "iters_mean": float(np.mean(it)), "max_rel_resid": float(np.max(rs)), "tol": args.tol,
+            "clocks": clocks,
+            "fp64": {"value": len(stars) / t64, "unit": "solves/s", "wall_s": t64, "iters_mean": float(np.mean(it64)),
+                     "max_rel_resid": float(np.max(rs64)), "clocks": clk64.summary()},
+            "speedup_mixed_over_fp64": t64 / t,
+            "max_rel_diff_mixed_vs_fp64": float(np.max(err)),
+            "config": {"workload": "256 random stars (seed 2312): lobes 3-7, amplitude U[0.1, 0.4], "
+                                   "N_e U[128, 2048], k_e U[1, 40], contrast U[1.2, 2.0]; one plane wave each",
+                       "l2": "sum of the matrices 12 GB (> L2)"}}
+
+
+def serving_leg(args, clock_index=0):
+    """The Poisson request stream through the continuous-batching loop (mixed), and the identical requests
+    through the plain FP64 single-problem path one at a time in arrival order."""
+    torch, P = _load_lib()
+    from paper_2312_12787_gb300 import serve
+    stream = W.cfg_serving_c5(count=args.requests)
+    requests = [(t, wp, 0.0) for t, wp in stream]
+    srv = serve.Server(max_slots=256, pool_unknowns=1 << 22, hbm_budget_bytes=96 << 30, tol=args.tol,
+                       max_iter=args.max_iter, inner_tol=args.inner_tol, orth_passes=args.orth_passes)
+    warm = W.cfg_serving_c5(count=8, seed=7)
+    srv.run([(0.0, wp, 0.0) for _, wp in warm], time_limit_s=600)      # warm-up (kernel loading, autotuning)
+    with ClockSampler(clock_index) as clk:
+        stm = srv.run(requests, time_limit_s=3600)
+    srv.close()
+    with ClockSampler(clock_index) as clk64:
+        st64 = serve.serve_fp64_sequential(requests, tol=args.tol, time_limit_s=3600)
+    big = sum(serve.c32_matrix_bytes(wp) > 8e9 for _, wp, _ in requests)
+    return {"metric": "serving solves/s and p50/p99 latency: continuous batching (mixed) vs FP64 one at a time",
+            "mixed": stm.summary() | {"clocks": clk.summary()},
+            "fp64_sequential": st64.summary() | {"clocks": clk64.summary()},
+            "speedup_mixed_over_fp64": st64.wall_s / stm.wall_s if stm.wall_s > 0 else None,
+            "tol": args.tol, "requests": len(requests), "matrix_free_requests": int(big),
+            "config": {"workload": f"Poisson stream (seed 2313), {len(requests)} requests at 200/s: circles, ellipses "
+                                   "(aspect U[1, 4]), 2-material junction disks; N_e log-uniform [256, 16384], "
+                                   "k_e U[1, 50], contrast U[1.2, 2.0]; matrix-free above 8 GB of complex FP32 "
+                                   "matrix (mixed path); the FP64 path stores every matrix",
+                       "identical_requests": True}}
+
+
+def omega_eps_leg(args):
+    """The iteration studies of Sec. 7.1 (unit circle: GMRES iterations vs omega and vs eps_2) and Sec. 7.2
+    (concentric circles: vs omega and vs eps_2 = 1/eps_3; the junction disk: vs N, omega and eps_3) for the
+    proposed ("mod") arrangement and the others the paper compares ("orig": beta = -alpha on the standard rows
+    only; "conv": conventional), each as one batch of all its problems."""
+    torch, P = _load_lib()
+
+    def run_batch(cases, form):
+        res = {}
+        for leg in ("warmup", "timed"):
+            probs = [P.Problem.from_workload(wp, prec="mixed", form=form, tol=args.tol, max_iter=1000)
+                     for _, _, wp in cases]
+            xs = [torch.empty(p.bem_num_unknowns(), dtype=torch.complex128, device="cuda") for p in probs]
+            bt = P.Batch(len(probs), sum(p.bem_num_unknowns() for p in probs), form=form, tol=args.tol,
+                         max_iter=1000)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st, it, rs = bt.bem_batch_solve_planewave(probs, np.zeros(len(probs)), xs)
             torch.cuda.synchronize()
             res[leg] = (time.perf_counter() - t0, it, rs)
             bt.close()
             for p in probs:
                 p.close()
         t, it, rs = res["timed"]
-        line = {"metric": "random-star sweep solves/s (one batch, mixed)", "value": len(stars) / t,
-                "unit": "solves/s", "wall_s": t, "n_problems": len(stars), "iters_mean": float(np.mean(it)),
-                "max_rel_resid": float(np.max(rs)), "tol": args.tol,
-                "config": {"workload": "256 random stars, N_e U[128,2048], k_e U[1,40]"}}
-        print(json.dumps(line), flush=True)
-        return
-    stream = W.cfg_serving_c5(count=args.requests)
-    requests = [(t, wp, 0.0) for t, wp in stream]
-    srv = serve.Server(max_slots=256, pool_unknowns=1 << 22, hbm_budget_bytes=96 << 30, tol=args.tol,
-                       max_iter=args.max_iter)
-    srv.run(requests[:8], time_limit_s=600)                # warm-up (kernel loading, autotuning)
-    st = srv.run(requests, time_limit_s=1200)
-    srv.close()
-    nf = min(len(requests), 40)
-    st64 = serve.serve_fp64_sequential(requests[:nf], tol=args.tol, time_limit_s=1200)
-    line = {"metric": "serving solves/s and latency (continuous batching, mixed) vs FP64 sequential",
-            "mixed": st.summary(), "fp64_sequential_first_%d" % nf: st64.summary(), "tol": args.tol,
-            "config": {"workload": f"Poisson stream, {len(requests)} requests at 200/s: circles, ellipses, "
-                                   "junction disks, N_e log-uniform [256, 16384], k_e U[1, 50]"}}
-    print(json.dumps(line), flush=True)
+        kinds = np.array([c[0] for c in cases])
+        r = {"solves_per_s": len(cases) / t, "wall_s": t, "max_rel_resid": float(np.max(rs)),
+             "iters_vs_omega": [int(v) for v in it[kinds == "omega"]],
+             "iters_vs_eps": [int(v) for v in it[kinds == "eps"]]}
+        if np.any(kinds == "n"):
+            r["iters_vs_n"] = [int(v) for v in it[kinds == "n"]]
+        return r
+    circ = W.cfg_omega_eps_sweep()
+    conc = W.cfg_concentric_sweep()
+    junc = W.cfg_junction_sweep()
+    with ClockSampler(0) as clk:
+        out = {"circle": {f: run_batch(circ, f) for f in ("mod", "conv")},
+               "concentric": {f: run_batch(conc, f) for f in ("mod", "orig", "conv")},
+               "junction": {f: run_batch(junc, f) for f in ("mod", "orig", "conv")}}
+    return {"metric": "omega / eps sweeps of Sec. 7 (one batch per geometry and arrangement, mixed)",
+            "value": out["circle"]["mod"]["solves_per_s"], "unit": "solves/s", "tol": args.tol,
+            "results": out, "clocks": clk.summary(),
+            "circle_omega": [c[1] for c in circ if c[0] == "omega"],
+            "circle_eps_2": [c[1] for c in circ if c[0] == "eps"],
+            "concentric_omega": [c[1] for c in conc if c[0] == "omega"],
+            "concentric_eps_3": [c[1] for c in conc if c[0] == "eps"],
+            "junction_n": [c[1] for c in junc if c[0] == "n"],
+            "junction_omega": [c[1] for c in junc if c[0] == "omega"],
+            "junction_eps_3": [c[1] for c in junc if c[0] == "eps"],
+            "config": {"workload": "unit circle, 600 elements: 64 omega in [0.5, 20] (eps_2 = 2), 64 eps_2 in "
+                                   "[1.1, 10] (omega = 5); concentric circles, 600 + 1200 elements: 32 omega "
+                                   "in [0.5, 10] (eps_i = i), 32 eps_3 in [0.1, 10] with eps_2 = 1/eps_3 "
+                                   "(omega = 5); junction disk (3/4 of the elements on the circle, 1/4 on the "
+                                   "diameter, eps_i = i): N in 266..3198 at omega = 5, 32 omega in [0.5, 10] and "
+                                   "32 eps_3 in [0.1, 10] with eps_2 = 1/eps_3 (omega = 5) at N = 1066; Q = 4, "
+                                   "tolerance 1e-8, mixed precision"}}
 
 
 def main():
@@ -302,24 +385,28 @@ def main():
     ap.add_argument("--prec", default="mixed_tc", choices=["mixed", "mixed_tc"])
     ap.add_argument("--tol", type=float, default=1e-8, help="relative residual target of both paths (paper: 1e-8)")
     ap.add_argument("--fp64-steps", type=int, default=1)
-    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline leg")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle leg (then the accuracy reference is "
+                                                          "the FP64 GPU path at tol 1e-12)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison leg (profiling runs)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg (profiling runs)")
+    ap.add_argument("--no-secondary", action="store_true", help="star: skip the sweep and serving keys")
     ap.add_argument("--n-elem", type=int, default=4096, help="elements of the star (smaller cases for ncu)")
     ap.add_argument("--max-iter", type=int, default=400)
     ap.add_argument("--inner-tol", type=float, default=1e-5, help="inner GMRES tolerance of the mixed path")
     ap.add_argument("--orth-passes", type=int, default=0, help="Gram-Schmidt passes of the mixed path (0 = auto)")
     ap.add_argument("--workload", default="star", choices=["star", "serving", "sweep", "omega_eps"],
-                    help="star: the 64-RHS star (default line); serving: Poisson request stream; "
-                         "sweep: 256 random stars in one batch; omega_eps: Sec. 7.1's omega and eps_2 sweeps "
-                         "of the unit circle, one batch per arrangement")
-    ap.add_argument("--requests", type=int, default=200, help="serving: number of requests")
+                    help="star: the 64-RHS star (default line, with the sweep and serving keys); serving: the "
+                         "Poisson request stream alone; sweep: 256 random stars in one batch alone; omega_eps: the "
+                         "omega and eps sweeps of Sec. 7.1 and 7.2, one batch per arrangement")
+    ap.add_argument("--requests", type=int, default=2000, help="serving: number of requests")
     ap.add_argument("--n-rhs", type=int, default=64, help="star: incident angles per step (64 = the workload)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload != "star":
-        return run_batched_workload(args)
+        leg = {"sweep": sweep_leg, "serving": serving_leg, "omega_eps": omega_eps_leg}[args.workload]
+        print(json.dumps(leg(args)), flush=True)
+        return
 
     import torch
     ws, rank, local = dist_setup(args)
@@ -357,18 +444,16 @@ def main():
     torch.cuda.synchronize()
     barrier(ws)
     torch.cuda.synchronize()
-    times = []
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    iters = []
+    iters, resids = [], []
     with ClockSampler(local) as clk:
-        t_all0 = time.perf_counter()
         for k in range(args.steps):
             evs[k][0].record(stream)
             st, it, rs = step(p, x, ff)
             evs[k][1].record(stream)
             iters.append(it.copy())
+            resids.append(rs.copy())
         torch.cuda.synchronize()
-        t_all = time.perf_counter() - t_all0
     barrier(ws)
     times = [a.elapsed_time(b) for a, b in evs]
     total_ms = barrier_max(ws, sum(times))
@@ -386,9 +471,11 @@ def main():
     p50 = lat[len(lat) // 2]
     p99 = lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)]
 
-    # ---- FP64 path: same step; then a tight FP64 solve as the accuracy reference ----
+    # ---- FP64 path: the same step ----
     fp64 = None
-    acc = {"tol": args.tol, "iters_mixed_max": int(np.max(iters[-1]))}
+    x64 = None
+    acc = {"tol": args.tol, "iters_mixed_max": int(np.max(iters[-1])), "iters_mixed_mean": float(np.mean(iters[-1])),
+           "max_rel_resid_mixed": float(np.max(resids[-1]))}
     if not args.no_fp64:
         p64, x64, ff64 = make("fp64")
         step(p64, x64, ff64)
@@ -403,14 +490,8 @@ def main():
             t64.append(a.elapsed_time(b))
         fp64_ms = statistics.median(t64)
         p64.close()
-        pr = P.Problem.from_workload(wp, prec="fp64", tol=1e-12, max_iter=args.max_iter)
-        xr = torch.empty_like(x64)
-        pr.bem_solve_planewave(ang, xr, stream)
-        pr.close()
-        nrm = torch.linalg.vector_norm(xr, dim=1)
-        acc["reference"] = "FP64 GPU path at tol 1e-12"
-        acc["max_rel_err_mixed"] = (torch.linalg.vector_norm(x_mixed - xr, dim=1) / nrm).max().item()
-        acc["max_rel_err_fp64"] = (torch.linalg.vector_norm(x64 - xr, dim=1) / nrm).max().item()
+        acc["iters_fp64_max"] = int(np.max(it64))
+        acc["iters_fp64_mean"] = float(np.mean(it64))
         fp64 = {"value": N_RHS / (fp64_ms / 1e3), "unit": UNIT, "ms_per_step": fp64_ms,
                 "speedup_mixed_over_fp64": fp64_ms / ms_step, "iters_max": int(np.max(it64))}
 
@@ -445,19 +526,18 @@ def main():
         ach = ASM_WARP_INST_N3072 * scale / avg_s / 1e9
         roof.update({"kernel": "k_assemble (issue-bound: FP64 geometry + double-float Bessel on FP32)", "bound": "alu",
                      "achieved": ach, "peak": ISSUE_PEAK_G, "unit": "G warp instructions/s", "frac": ach / ISSUE_PEAK_G,
-                     # the kernel changed after the capture (occupancy, Bessel clean-up): no current counters
-                     "traffic": None, "traffic_before_last_change": ASM_DRAM_BYTES_N3072 * scale,
+                     "traffic": ASM_DRAM_BYTES_N3072 * scale if ASM_DRAM_BYTES_N3072 else None,
                      "peak_source": "derived: 152 SMs x 4 issue slots/clk x 2.07 GHz"})
     elif ph == "matvec":
-        # one kernel per product: the GEMM (its stream-K reduction is timed as the "reduce" phase)
+        # one kernel per product: the GEMM (its stream-K reduction is timed as the "reduce" phase); the launch
+        # count leaves out the gated launches queued after convergence, which do no work
         avg_s = ph_ms / ph_n / 1e3
         bytes_per = n2 * n2 * 8 + 2 * N_RHS * n2 * 8          # A (2 x FP16 per real entry) + X + Y
         ach = bytes_per / avg_s / 1e9
-        roof.update({"kernel": "k_gemm_tc (tcgen05 FP16x3 multi-RHS GEMM; its stream-K reduction is the reduce phase)", "bound": "hbm",
-                     "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "peak_source": src,
-                     # the kernel changed after the capture (set-up order, 32-bit range split): no current counters
-                     "traffic": None,
-                     "traffic_before_last_change": GEMM_DRAM_BYTES_N3072 * scale if N_RHS > 1 else None})
+        roof.update({"kernel": "k_gemm_tc (tcgen05 FP16x3 multi-RHS GEMM; its stream-K reduction is the reduce phase)",
+                     "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                     "peak_source": src, "algorithmic_bytes_per_launch": bytes_per,
+                     "traffic": GEMM_DRAM_BYTES_N4096 * (nel / 4096.0) ** 2 if GEMM_DRAM_BYTES_N4096 else None})
     else:
         # launches per refinement residual: 11 (12 with a K split) with the tensor-core small terms
         n_gemm = max(1, ph_n // RESID_LAUNCHES_TC)
@@ -486,11 +566,36 @@ def main():
         "gpu_launches": int(sum(v[1] for v in prof.values())) * args.steps,
         "clocks": clk.summary(),
     }
-    if rank == 0 and not args.no_cpu:
-        v, t, sample = oracle_sample(wp, rows=256, lu_ne=2048)
-        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-                                "sample": sample}
+    # ---- CPU oracle (rank 0, N = 1): timed on the whole workload; its LU solution is the accuracy reference ----
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        info, X = oracle_full(wp, ang, args.tol)
+        v = N_RHS / (info["assembly_s"] + info["rhs_and_lu_s"])
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": info["cores"], "kind": "oracle",
+                                "sample": f"the whole workload: assembly of all {n2} rows on {info['cores']} "
+                                          f"host processes + LU solve of {N_RHS} right-hand sides (not "
+                                          "extrapolated); the single-process assembly time is extrapolated from "
+                                          "128 rows; the oracle's GMRES is timed on one column",
+                                "extrapolated": False, **info}
+        Xd = torch.as_tensor(X, device="cuda")
+        nrm = torch.linalg.vector_norm(Xd, dim=1)
+        acc["reference"] = "oracle LU solution (FP64, CPU)"
+        acc["max_rel_err_mixed"] = (torch.linalg.vector_norm(x_mixed - Xd, dim=1) / nrm).max().item()
+        if x64 is not None:
+            acc["max_rel_err_fp64"] = (torch.linalg.vector_norm(x64 - Xd, dim=1) / nrm).max().item()
+    elif x64 is not None:
+        pr = P.Problem.from_workload(wp, prec="fp64", tol=1e-12, max_iter=args.max_iter)
+        xr = torch.empty_like(x64)
+        pr.bem_solve_planewave(ang, xr, stream)
+        pr.close()
+        nrm = torch.linalg.vector_norm(xr, dim=1)
+        acc["reference"] = "FP64 GPU path at tol 1e-12"
+        acc["max_rel_err_mixed"] = (torch.linalg.vector_norm(x_mixed - xr, dim=1) / nrm).max().item()
+        acc["max_rel_err_fp64"] = (torch.linalg.vector_norm(x64 - xr, dim=1) / nrm).max().item()
     p.close()
+    # ---- secondary keys: the batched sweep and the serving stream (rank 0) ----
+    if rank == 0 and not args.no_secondary:
+        line["sweep"] = sweep_leg(args, local)
+        line["serving"] = serving_leg(args, local)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:

@@ -244,7 +244,10 @@ BEM_API bem_status bem_batch_solve_planewave(bem_batch* b, int n, bem_problem* c
 /* Per-phase device timing for measurement.  When enabled, every kernel launch of the problem is bracketed
  * by CUDA events recorded on the stream it runs on; bem_profile_read synchronises those events and returns,
  * per phase, the summed device milliseconds and the number of kernel launches since the last enable.
- * Arrays have BEM_PH_COUNT entries.  Enabling resets the counters; it does not change results. */
+ * Arrays have BEM_PH_COUNT entries.  Enabling resets the counters; it does not change results.  Product
+ * launches of GMRES iterations queued after every system of a block had converged (their gate closed, so
+ * they did no work) are left out of the MATVEC and REDUCE launch counts; their few microseconds stay in the
+ * phase times. */
 typedef enum {
   BEM_PH_GEOMETRY = 0,  /* a1: element geometry */
   BEM_PH_ASSEMBLE = 1,  /* a3-a5: matrix entries */

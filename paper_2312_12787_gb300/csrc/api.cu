@@ -509,6 +509,7 @@ bem_status gmres_run(bem_problem* p, Solver& sv, const double2* r0, double2* x, 
   const int* gate = st.n_active;
   // one iteration: product, orthogonalisation, rotations and scaling of the next basis vector (the kernels read
   // the iteration index from the device; only the non-tensor-core products take the basis vector's address)
+  int launched = 0;   // iterations queued by the host loop below (the graph path does not count them)
   auto iteration = [&](int j) -> cudaError_t {
     void* Vj = static_cast<char*>(st.V) + (size_t)j * nrhs * n2 * tb;
     cudaError_t e;
@@ -645,6 +646,7 @@ bem_status gmres_run(bem_problem* p, Solver& sv, const double2* r0, double2* x, 
     constexpr int kSyncEvery = 4;
     for (int j = 0; j < st.m; ++j) {
       CU(iteration(j));
+      ++launched;
       if ((j + 1) % kSyncEvery == 0) {
         CU(cudaMemcpyAsync(p->h_pin, st.n_active, sizeof(int), cudaMemcpyDeviceToHost, s));
         CU(cudaStreamSynchronize(s));
@@ -668,6 +670,14 @@ bem_status gmres_run(bem_problem* p, Solver& sv, const double2* r0, double2* x, 
   for (int r = 0; r < nrhs; ++r) {
     iters[r] += it[r];
     resid[r] = rs[r];
+  }
+  if (p->prof && launched > 0) {
+    // Iterations queued past the last system's convergence found their gates closed: their product launches
+    // did no work, so the per-launch figures of the product phases count only the launches that did.
+    const int worked = *std::max_element(it.begin(), it.end());
+    const int gated = std::max(0, launched - worked);
+    p->launches[BEM_PH_MATVEC] -= gated;
+    if (use_tc) p->launches[BEM_PH_REDUCE] -= gated;
   }
   return BEM_OK;
 }

@@ -68,6 +68,16 @@ struct VDev {
   int* strict;      // per slot: 1 once a refinement step stagnated (the second pass then always runs)
   int* arrive;      // per slot: first-pass update CTAs done (the last one takes the decision)
   int* n_active;
+  // device-side refinement loop (bem_batch_solve_planewave): per-slot solve state kept on the device
+  int* state;       // 1 iterating, 2 finished
+  int* outer;       // refinement steps done
+  int* itot;        // GMRES iterations over all refinement steps
+  double* bnorm;    // ||b||
+  double* rel;      // relative FP64 residual after the last refinement step
+  int* bodies;      // loop bodies run so far (a hard stop against runaway loops)
+  double otol, itol;  // outer (refinement) and inner tolerances
+  int max_refine;
+  int max_bodies;
 };
 
 __device__ __forceinline__ float2* vbase(const VDev& d, int s) { return d.V + d.u[s] * (long long)(d.m + 1); }
@@ -171,7 +181,8 @@ __global__ void __launch_bounds__(256) kv_update(VDev d, int pass, int cond) {
   __shared__ float2 hs[kMaxM + 1];
   __shared__ float accs[4][kCh][2];
   __shared__ double red[8];
-  const int c = blockIdx.x;
+  // chunks in the reverse of the projection kernel's order: the basis chunks it read last are still in L2
+  const int c = gridDim.x - 1 - blockIdx.x;
   const int s = d.ch_slot[c];
   if (!d.active[s] || (cond && !d.reo[s])) return;   // cond: a conditional pass the slot did not need
   const int n = d.n[s], j = d.j[s];
@@ -436,6 +447,60 @@ __global__ void __launch_bounds__(256) kv_resid(VDev d) {
   }
 }
 
+// ---- device-side refinement loop ----------------------------------------------------------------
+// The host-stepped engine decides on the host, after each graph replay, which inner solves stopped and
+// whether their refined residual meets the tolerance.  For bem_batch_solve_planewave the same decisions run
+// on the device, so that the whole solve is one graph launch: a conditional WHILE node whose body is
+// graph_iters iterations followed by a refinement stage for the slots whose inner solve stopped.
+
+// flag = the slots whose inner solve stopped (iterating, no longer active)
+__global__ void kv_loop_flag(VDev d) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= d.cap) return;
+  d.flag[s] = (d.state[s] == 1 && d.active[s] == 0) ? 1 : 0;
+}
+
+// After kv_norm: the host engine's refine_finished decisions for the flagged slots.  A slot that meets the
+// tolerance (or used its refinement steps) is finished and unflagged; the others keep their flag and get the
+// tolerance of their next inner solve (kv_start_fin / kv_start_scale then restart them).
+__global__ void kv_loop_decide(VDev d) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= d.cap || !d.flag[s]) return;
+  const int it = d.iters[s];
+  const double rn = d.rnorm[s], bn = d.bnorm[s];
+  const double prev = d.outer[s] > 0 ? d.rel[s] : 1.0;
+  d.itot[s] += it;
+  d.outer[s] += 1;
+  const double rel = bn > 0.0 ? rn / bn : 0.0;
+  // a step that used every iteration or cut the residual by less than 4x: Gram-Schmidt twice from now on
+  if (it >= d.m || rel > 0.25 * prev) d.strict[s] = 1;
+  d.rel[s] = rel;
+  if (rel <= d.otol || d.outer[s] >= d.max_refine || !(rel == rel)) {
+    d.state[s] = 2;
+    d.flag[s] = 0;
+  } else {
+    d.tol[s] = fmax(d.itol, 0.3 * d.otol * bn / rn);
+  }
+}
+
+// The loop condition: some slot still iterating (and the body limit not reached).
+__global__ void kv_loop_cond(VDev d, unsigned long long handle) {
+  __shared__ int any;
+  if (threadIdx.x == 0) any = 0;
+  __syncthreads();
+  for (int s = threadIdx.x; s < d.cap; s += blockDim.x)
+    if (d.state[s] == 1) any = 1;
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  const int nb = ++(*d.bodies);
+  if (nb >= d.max_bodies && any) {   // cannot happen within the iteration and refinement limits
+    for (int s = 0; s < d.cap; ++s)
+      if (d.state[s] == 1) { d.state[s] = 2; d.active[s] = 0; }
+    any = 0;
+  }
+  cudaGraphSetConditional((cudaGraphConditionalHandle)handle, any ? 1u : 0u);
+}
+
 }  // namespace
 
 // ================================ host engine ====================================================
@@ -478,6 +543,11 @@ struct BatchEngine {
   int graph_iters = 4;
   bool dirty = true;
   int asm_ty = 0;
+  // device-side refinement loop
+  int *state = nullptr, *outer = nullptr, *itot = nullptr, *bodies = nullptr;
+  double *bnorm = nullptr, *rel = nullptr;
+  cudaGraphExec_t lexec = nullptr;   // the whole-solve graph of the current membership
+  bool noloop = false;               // conditional nodes unavailable: host-stepped replays instead
 };
 
 }  // namespace bem
@@ -532,6 +602,11 @@ VDev view(const BatchEngine& e) {
   d.cbeg = e.cbeg; d.ccnt = e.ccnt; d.ch_slot = e.ch_slot; d.ch_loc = e.ch_loc; d.nchunks = e.nchunks;
   d.rb_slot = e.rb_slot; d.rb_row = e.rb_row; d.nrb = e.nrb;
   d.part = e.part; d.npart = e.npart; d.wpart = e.wpart; d.reo = e.reo; d.strict = e.strict; d.arrive = e.arrive; d.n_active = e.n_active;
+  d.state = e.state; d.outer = e.outer; d.itot = e.itot; d.bnorm = e.bnorm; d.rel = e.rel; d.bodies = e.bodies;
+  d.otol = e.o.tol; d.itol = e.o.inner_tol; d.max_refine = e.o.max_refine;
+  // every inner solve stops within m iterations, i.e. m / graph_iters + 1 bodies, and a slot refines at most
+  // max_refine times; twice that bounds the loop
+  d.max_bodies = 2 * (e.o.max_refine + 1) * (e.m / std::max(1, e.graph_iters) + 2);
   return d;
 }
 
@@ -592,6 +667,10 @@ bem_status rebuild_tables(bem_batch* b) {
   if (e.gexec) {
     cudaGraphExecDestroy(e.gexec);
     e.gexec = nullptr;
+  }
+  if (e.lexec) {
+    cudaGraphExecDestroy(e.lexec);
+    e.lexec = nullptr;
   }
   e.dirty = false;
   return BEM_OK;
@@ -697,6 +776,106 @@ bem_status refine_finished(bem_batch* b) {
   return start_flagged(b, restart);
 }
 
+// The refinement stage of the device loop for the slots whose inner solve stopped (same kernels as
+// refine_finished and start_flagged, with the decisions of kv_loop_decide).
+void enqueue_refine_stage(const BatchEngine& e, const VDev& d) {
+  const int sb = (e.cap + 127) / 128;
+  kv_loop_flag<<<sb, 128, 0, e.st>>>(d);
+  kv_lsq<<<e.cap, kBsThreads, 0, e.st>>>(d);
+  kv_xupdate<<<e.nchunks, 256, 0, e.st>>>(d);
+  kv_split<<<e.nchunks, kCh, 0, e.st>>>(d);
+  kv_resid<<<e.nrb, 256, 0, e.st>>>(d);
+  kv_norm<<<e.cap, 256, 0, e.st>>>(d, 0);
+  kv_loop_decide<<<sb, 128, 0, e.st>>>(d);
+  kv_start_fin<<<sb, 128, 0, e.st>>>(d);
+  kv_start_scale<<<e.nchunks, kCh, 0, e.st>>>(d);
+}
+
+// Iterate every admitted slot to completion as one graph launch (a WHILE node over graph_iters iterations
+// and a refinement stage); the slots' results (state, iterations, residual) are read back at the end.
+// Returns BEM_ECUDA with e.noloop set if conditional graph nodes are not available (the caller falls back
+// to host-stepped replays).
+bem_status run_device_loop(bem_batch* b) {
+  BatchEngine& e = b->e;
+  if (e.dirty) {
+    bem_status st = rebuild_tables(b);
+    if (st != BEM_OK) return st;
+  }
+  if (e.nchunks == 0) return BEM_OK;
+  // the slots' solve state on the device
+  std::vector<int> state(e.cap, 0), outer(e.cap, 0), itot(e.cap, 0), strict(e.cap, 0);
+  std::vector<double> bn(e.cap, 0.0), rel(e.cap, 0.0);
+  for (int s = 0; s < e.cap; ++s) {
+    const BatchSlot& sl = b->slot[s];
+    state[s] = sl.state;
+    outer[s] = sl.outer;
+    itot[s] = sl.iters;
+    strict[s] = sl.strict ? 1 : 0;
+    bn[s] = sl.bnorm;
+    rel[s] = sl.resid;
+  }
+  BCU(cudaMemcpyAsync(e.state, state.data(), e.cap * sizeof(int), cudaMemcpyHostToDevice, e.st));
+  BCU(cudaMemcpyAsync(e.outer, outer.data(), e.cap * sizeof(int), cudaMemcpyHostToDevice, e.st));
+  BCU(cudaMemcpyAsync(e.itot, itot.data(), e.cap * sizeof(int), cudaMemcpyHostToDevice, e.st));
+  BCU(cudaMemcpyAsync(e.strict, strict.data(), e.cap * sizeof(int), cudaMemcpyHostToDevice, e.st));
+  BCU(cudaMemcpyAsync(e.bnorm, bn.data(), e.cap * sizeof(double), cudaMemcpyHostToDevice, e.st));
+  BCU(cudaMemcpyAsync(e.rel, rel.data(), e.cap * sizeof(double), cudaMemcpyHostToDevice, e.st));
+  BCU(cudaMemsetAsync(e.bodies, 0, sizeof(int), e.st));
+  const VDev d = view(e);
+  if (!e.lexec) {
+    cudaGraph_t graph = nullptr;
+    cudaGraphConditionalHandle h = 0;
+    cudaError_t ce = cudaGraphCreate(&graph, 0);
+    if (ce == cudaSuccess) ce = cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault);
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node = nullptr;
+    if (ce == cudaSuccess) ce = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp);
+    if (ce == cudaSuccess) {
+      ce = cudaStreamBeginCaptureToGraph(e.st, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                         cudaStreamCaptureModeThreadLocal);
+      if (ce == cudaSuccess) {
+        for (int it = 0; it < e.graph_iters; ++it) enqueue_iteration(e, d, e.o.orth_passes);
+        enqueue_refine_stage(e, d);
+        kv_loop_cond<<<1, 256, 0, e.st>>>(d, (unsigned long long)h);
+        const cudaError_t le = cudaGetLastError();
+        cudaGraph_t out = nullptr;
+        const cudaError_t ee = cudaStreamEndCapture(e.st, &out);
+        ce = le != cudaSuccess ? le : ee;
+      }
+    }
+    if (ce == cudaSuccess) ce = cudaGraphInstantiate(&e.lexec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) {
+      e.lexec = nullptr;
+      e.noloop = true;
+      (void)cudaGetLastError();
+      return report_error(BEM_ECUDA, "conditional graph nodes unavailable for the batch loop");
+    }
+  }
+  BCU(cudaGraphLaunch(e.lexec, e.st));
+  BCU(cudaMemcpyAsync(state.data(), e.state, e.cap * sizeof(int), cudaMemcpyDeviceToHost, e.st));
+  BCU(cudaMemcpyAsync(outer.data(), e.outer, e.cap * sizeof(int), cudaMemcpyDeviceToHost, e.st));
+  BCU(cudaMemcpyAsync(itot.data(), e.itot, e.cap * sizeof(int), cudaMemcpyDeviceToHost, e.st));
+  BCU(cudaMemcpyAsync(strict.data(), e.strict, e.cap * sizeof(int), cudaMemcpyDeviceToHost, e.st));
+  BCU(cudaMemcpyAsync(rel.data(), e.rel, e.cap * sizeof(double), cudaMemcpyDeviceToHost, e.st));
+  BCU(cudaStreamSynchronize(e.st));
+  for (int s = 0; s < e.cap; ++s) {
+    BatchSlot& sl = b->slot[s];
+    if (sl.state != 1) continue;
+    sl.state = state[s];
+    sl.outer = outer[s];
+    sl.iters = itot[s];
+    sl.strict = strict[s] != 0;
+    sl.resid = rel[s];
+  }
+  e.dirty = true;   // finished slots leave the work lists
+  return BEM_OK;
+}
+
 struct StreamScope {
   BatchEngine& e;
   cudaStream_t caller;
@@ -747,7 +926,8 @@ BEM_API bem_status bem_batch_create(bem_batch** out, const bem_opts* opts, int m
        dalloc(&e.ch_slot, e.max_chunks) && dalloc(&e.ch_loc, e.max_chunks) && dalloc(&e.rb_slot, e.max_rb) &&
        dalloc(&e.rb_row, e.max_rb) && dalloc(&e.part, (size_t)e.max_chunks * (m + 1)) &&
        dalloc(&e.npart, e.max_chunks) && dalloc(&e.wpart, e.max_chunks) && dalloc(&e.reo, cap) && dalloc(&e.strict, cap) && dalloc(&e.arrive, cap) &&
-       dalloc(&e.angles, cap);
+       dalloc(&e.angles, cap) && dalloc(&e.state, cap) && dalloc(&e.outer, cap) && dalloc(&e.itot, cap) &&
+       dalloc(&e.bodies, 1) && dalloc(&e.bnorm, cap) && dalloc(&e.rel, cap);
   ok = ok && cudaMallocHost(&e.h_active, cap * sizeof(int)) == cudaSuccess &&
        cudaMallocHost(&e.h_iters, cap * sizeof(int)) == cudaSuccess &&
        cudaMallocHost(&e.h_rnorm, cap * sizeof(double)) == cudaSuccess &&
@@ -773,9 +953,11 @@ BEM_API void bem_batch_destroy(bem_batch* b) {
   BatchEngine& e = b->e;
   if (e.st) cudaStreamSynchronize(e.st);
   if (e.gexec) cudaGraphExecDestroy(e.gexec);
+  if (e.lexec) cudaGraphExecDestroy(e.lexec);
   void* ptrs[] = {e.dA, e.dAlo, e.dn, e.du, e.V, e.W, e.X, e.R, e.Bv, e.H, e.cs, e.sn, e.g, e.y, e.hcol, e.beta,
                   e.hnext, e.resid, e.tol, e.rnorm, e.active, e.iters, e.jj, e.flag, e.n_active, e.cbeg, e.ccnt,
-                  e.ch_slot, e.ch_loc, e.rb_slot, e.rb_row, e.part, e.npart, e.wpart, e.reo, e.strict, e.arrive, e.angles};
+                  e.ch_slot, e.ch_loc, e.rb_slot, e.rb_row, e.part, e.npart, e.wpart, e.reo, e.strict, e.arrive, e.angles,
+                  e.state, e.outer, e.itot, e.bodies, e.bnorm, e.rel};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (e.h_active) cudaFreeHost(e.h_active);
@@ -961,7 +1143,15 @@ BEM_API bem_status bem_batch_solve_planewave(bem_batch* b, int n, bem_problem* c
       if (s >= 0) { b->slot[s].state = 2; bem_batch_take(b, s, nullptr, stream); }
     return st;
   }
-  int running = 1;
+  // the whole solve as one graph launch (device-side loop); host-stepped replays where that is unavailable
+  bool looped = false;
+  if (!b->e.noloop) {
+    StreamScope scope(b->e, stream);
+    st = run_device_loop(b);
+    if (st == BEM_OK) looped = true;
+    else if (!b->e.noloop) return st;
+  }
+  int running = looped ? 0 : 1;
   for (int guard = 0; running > 0 && guard < 100000; ++guard) {
     st = bem_batch_step(b, &running, stream);
     if (st != BEM_OK) return st;

@@ -67,8 +67,9 @@ class Server:
     """Continuous-batching solver: slots of a bem_batch engine plus an HBM budget for matrices."""
 
     def __init__(self, max_slots=128, pool_unknowns=1 << 21, hbm_budget_bytes=64 << 30, tol=1e-8, max_iter=300,
-                 prec="mixed", quad_order=4, matrix_free_bytes=8e9, mf_max_iter=600):
-        self.opts = dict(prec=prec, tol=tol, max_iter=max_iter, quad_order=quad_order)
+                 prec="mixed", quad_order=4, matrix_free_bytes=8e9, mf_max_iter=600, inner_tol=1e-5, orth_passes=0):
+        self.opts = dict(prec=prec, tol=tol, max_iter=max_iter, quad_order=quad_order, inner_tol=inner_tol,
+                         orth_passes=orth_passes)
         self.batch = _bem.Batch(max_slots, pool_unknowns, **self.opts)
         self.batch_max_slots = max_slots
         self.budget = hbm_budget_bytes

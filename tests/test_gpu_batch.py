@@ -190,3 +190,53 @@ def test_batch_engine_forms_match_oracle_lu(B, torch, form):
     bt.close()
     for p in probs:
         p.close()
+
+
+def test_device_loop_matches_host_stepped_solve(B, torch):
+    """bem_batch_solve_planewave runs the whole batched solve as one graph launch (a conditional loop whose
+    refinement decisions are taken on the device); admitting the same problems and stepping them from the host
+    (bem_batch_step) gives the same solutions and iteration counts."""
+    stars = W.cfg_random_stars_c4(count=6, seed=17, n_min=60, n_max=400)
+    angles = np.linspace(0.2, 3.0, len(stars))
+    pool = sum(wp.n_unknowns for wp in stars)
+    probs = [B.Problem.from_workload(wp, prec="mixed", tol=1e-10) for wp in stars]
+    xs = [torch.empty(p.bem_num_unknowns(), dtype=torch.complex128, device="cuda") for p in probs]
+    bt = B.Batch(8, pool, tol=1e-10, max_iter=300)
+    st, it_loop, rs_loop = bt.bem_batch_solve_planewave(probs, angles, xs)
+    assert st == B.BEM_OK and np.all(rs_loop <= 1e-10), (st, rs_loop)
+    st, slots = bt.bem_batch_admit(probs, angles)
+    assert st == B.BEM_OK
+    while bt.bem_batch_step():
+        pass
+    for k, s in enumerate(slots):
+        state, it, rs = bt.bem_batch_query(int(s))
+        assert state == 2 and it == it_loop[k] and abs(rs - rs_loop[k]) <= 1e-12 * max(rs, 1e-30) + 1e-30
+        x = torch.empty_like(xs[k])
+        bt.bem_batch_take(int(s), x)
+        assert rel(x.cpu().numpy(), xs[k].cpu().numpy()) <= 1e-12
+    bt.close()
+    for p in probs:
+        p.close()
+
+
+def test_junction_study_ordering_and_parity_on_gpu(B, torch):
+    """Sec. 7.2's junction study through the batched engine: on the junction disk (eps_i = i, omega = 5) the
+    modified Calderon arrangement needs the fewest GMRES iterations, then the original one, then the
+    conventional one, at N = 200 and 400; the solutions match the oracle's LU solutions of each arrangement."""
+    cases = [W.junction_material(200, 5.0, 2.0, 3.0), W.junction_material(400, 5.0, 2.0, 3.0)]
+    its = {}
+    for form in ("mod", "orig", "conv"):
+        probs = [B.Problem.from_workload(wp, prec="mixed", form=form, tol=1e-8, max_iter=1000) for wp in cases]
+        xs = [torch.empty(p.bem_num_unknowns(), dtype=torch.complex128, device="cuda") for p in probs]
+        bt = B.Batch(2, sum(p.bem_num_unknowns() for p in probs), form=form, tol=1e-8, max_iter=1000)
+        st, it, rs = bt.bem_batch_solve_planewave(probs, np.zeros(2), xs)
+        assert st == B.BEM_OK and np.all(rs <= 1e-8), (form, st, it, rs)
+        its[form] = it
+        wp = cases[0]
+        xl = O.solve_lu(O.assemble(wp, Q=4, form=form), O.rhs_planewave(wp, 0.0, form=form))
+        assert rel(xs[0].cpu().numpy(), xl) <= SOLUTION_TOL_MIXED, form
+        bt.close()
+        for p in probs:
+            p.close()
+    for k in range(2):
+        assert its["mod"][k] < its["orig"][k] < its["conv"][k], (k, its)

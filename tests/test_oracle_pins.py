@@ -512,3 +512,20 @@ def test_row_parallel_assembly_is_the_serial_assembly():
     for form in ("mod", "conv"):
         assert np.array_equal(O.assemble_parallel(p, Q=4, form=form, workers=3, block=16),
                               O.assemble(p, Q=4, form=form))
+
+
+def test_junction_iteration_study_ordering():
+    """Sec. 7.2, junction disk (three materials meeting at two points, eps_i = i unless stated, tolerance
+    1e-8): the modified Calderon arrangement converges fastest, then the original one, then the conventional
+    Burton-Miller arrangement, at every N, frequency and contrast tried; and the modified count stays flat in N
+    while the conventional one grows."""
+    cases = [(200, 5.0, 2.0, 3.0), (400, 5.0, 2.0, 3.0), (200, 1.0, 2.0, 3.0), (200, 5.0, 0.5, 2.0)]
+    its = {}
+    for case in cases:
+        p = W.junction_material(*case)
+        its[case] = {f: O.gmres(O.assemble(p, Q=4, form=f), O.rhs_planewave(p, 0.0, form=f), tol=1e-8)[1]
+                     for f in ("mod", "orig", "conv")}
+        assert its[case]["mod"] < its[case]["orig"] < its[case]["conv"], (case, its[case])
+    small, big = its[cases[0]], its[cases[1]]
+    assert big["mod"] <= 1.15 * small["mod"]
+    assert big["conv"] >= 1.4 * small["conv"]

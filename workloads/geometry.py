@@ -231,3 +231,29 @@ def cfg_serving_c5(count: int = 2000, seed: int = 2313, rate: float = 200.0,
             p.name = f"junction_{i}"
         out.append((t, p))
     return out
+
+
+def junction_material(n_total: int, omega: float, eps2: float, eps3: float) -> Problem:
+    """The junction disk of Sec. 7.2 with k_d = omega sqrt(eps_d): host eps_1 = 1, left half eps_2, right half
+    eps_3 (domains 1 and 2 here), 3/4 of the elements on the circle and 1/4 on the diameter."""
+    return junction_disk(n_total, k=(omega, omega * math.sqrt(eps2), omega * math.sqrt(eps3)),
+                         eps=(1.0, eps2, eps3))
+
+
+def cfg_junction_sweep(n_fixed: int = 1066, n_values=(266, 400, 533, 800, 1066, 1600, 2132, 3198),
+                       count: int = 32):
+    """The junction-scatterer iteration study of Sec. 7.2 (three materials meeting at two points): the same
+    sweeps as the concentric study on the junction disk, (a) over the number of elements N with eps_i = i and
+    omega = 5 (the N values are a choice), (b) `count` angular frequencies omega in [0.5, 10] with eps_i = i at
+    N = n_fixed, and (c) `count` contrasts eps_2 = 1/eps_3 for eps_3 in [0.1, 10] with omega = 5 at N = n_fixed
+    (the paper fixes N = 1066 for (b) and (c); the omega and eps ranges are read off its setting).
+    Returns [(label, value, Problem)]."""
+    out = []
+    for n in n_values:
+        out.append(("n", float(n), junction_material(int(n), 5.0, 2.0, 3.0)))
+    for w in np.linspace(0.5, 10.0, count):
+        out.append(("omega", float(w), junction_material(n_fixed, float(w), 2.0, 3.0)))
+    for e3 in np.linspace(0.1, 10.0, count):
+        out.append(("eps", float(e3), junction_material(n_fixed, 5.0, 1.0 / float(e3), float(e3))))
+    return out
+
