@@ -181,8 +181,7 @@ __global__ void __launch_bounds__(256) kv_update(VDev d, int pass, int cond) {
   __shared__ float2 hs[kMaxM + 1];
   __shared__ float accs[4][kCh][2];
   __shared__ double red[8];
-  // chunks in the reverse of the projection kernel's order: the basis chunks it read last are still in L2
-  const int c = gridDim.x - 1 - blockIdx.x;
+  const int c = blockIdx.x;
   const int s = d.ch_slot[c];
   if (!d.active[s] || (cond && !d.reo[s])) return;   // cond: a conditional pass the slot did not need
   const int n = d.n[s], j = d.j[s];

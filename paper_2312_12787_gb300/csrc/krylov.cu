@@ -240,9 +240,7 @@ __global__ void __launch_bounds__(CH / 2, sizeof(T) == sizeof(float2) ? 8 : 1) k
   using F = typename Vec<T>::acc_t;
   __shared__ F hs[2 * kHsMax];
   __shared__ double red[CH / 64];
-  // CTAs take (system, chunk) in the reverse of the projection kernel's order: the basis chunks that kernel read
-  // last, still in L2, are read again first
-  const int c = gridDim.x - 1 - blockIdx.x, s = gridDim.y - 1 - blockIdx.y;
+  const int c = blockIdx.x, s = blockIdx.y;
   if (!st.active[s] || (cond && !st.reo[s])) return;   // cond: a conditional pass the system did not need
   const int j = *st.jdev;
   for (int i = threadIdx.x; i <= j; i += CH / 2) {
