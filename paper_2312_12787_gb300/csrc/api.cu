@@ -840,6 +840,8 @@ Quad make_quad_host(int Q) {
   for (int m = 0; m < Q; ++m) {
     q.wh[m] = (float)q.w[m];
     q.wl[m] = (float)(q.w[m] - (double)q.wh[m]);
+    q.th[m] = (float)q.t[m];
+    q.tl[m] = (float)(q.t[m] - (double)q.th[m]);
   }
   return q;
 }

@@ -12,6 +12,7 @@
 // The iteration body is captured once per membership as a CUDA graph of `graph_iters` iterations and
 // replayed on an internal stream that is ordered after the caller's stream by events.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -875,6 +876,10 @@ bem_status run_device_loop(bem_batch* b) {
   return BEM_OK;
 }
 
+// Tile height of the batched assembly chosen by timing, per device (0 = not tuned yet).
+constexpr int kTunedDevs = 64;
+std::atomic<int> g_tuned_ty[kTunedDevs];
+
 struct StreamScope {
   BatchEngine& e;
   cudaStream_t caller;
@@ -1025,19 +1030,33 @@ BEM_API bem_status bem_batch_admit(bem_batch* b, int n, bem_problem* const* prob
     return acc;
   };
   std::vector<long long> pref;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (e.asm_ty == 0 && dev >= 0 && dev < kTunedDevs) e.asm_ty = g_tuned_ty[dev].load(std::memory_order_relaxed);
   if (e.asm_ty == 0) {
+    // Tile height (rows of element pairs per 32-column tile): time 4, 8 and 16 once per device on the first
+    // problems of this batch (about an eighth of its element pairs, at least one problem), keep the fastest.
+    long long pairs = 0, all_pairs = 0;
+    for (const AsmJob& jb : jobs) all_pairs += (long long)jb.n * jb.n;
+    int kjobs = 0;
+    while (kjobs < (int)jobs.size() && (kjobs == 0 || pairs * 8 < all_pairs)) {
+      pairs += (long long)jobs[kjobs].n * jobs[kjobs].n;
+      ++kjobs;
+    }
     const int cand[3] = {4, 8, 16};
     float best = 1e30f;
     int best_ty = 8;
     cudaEvent_t t0, t1;
-    cudaEventCreate(&t0);
-    cudaEventCreate(&t1);
+    BCU(cudaEventCreate(&t0));
+    BCU(cudaEventCreate(&t1));
     for (int c = 0; c < 3; ++c) {
-      const long long tot = prefix_for(cand[c], pref);
+      prefix_for(cand[c], pref);
+      long long tot = 0;
+      for (int i = 0; i < kjobs; ++i) tot += assemble_batched_tiles(jobs[i].n, cand[c]);
       BCU(cudaMemcpyAsync(dpref, pref.data(), pref.size() * sizeof(long long), cudaMemcpyHostToDevice, e.st));
-      cudaEventRecord(t0, e.st);
-      BCU(launch_assemble_batched(djobs, (int)jobs.size(), dpref, tot, q, e.o.form, 1, cand[c], e.st));
-      cudaEventRecord(t1, e.st);
+      BCU(cudaEventRecord(t0, e.st));
+      BCU(launch_assemble_batched(djobs, kjobs, dpref, tot, q, e.o.form, 1, cand[c], e.st));
+      BCU(cudaEventRecord(t1, e.st));
       BCU(cudaEventSynchronize(t1));
       float ms = 0.f;
       cudaEventElapsedTime(&ms, t0, t1);
@@ -1046,7 +1065,9 @@ BEM_API bem_status bem_batch_admit(bem_batch* b, int n, bem_problem* const* prob
     cudaEventDestroy(t0);
     cudaEventDestroy(t1);
     e.asm_ty = best_ty;
-  } else {
+    if (dev >= 0 && dev < kTunedDevs) g_tuned_ty[dev].store(best_ty, std::memory_order_relaxed);
+  }
+  {
     const long long tot = prefix_for(e.asm_ty, pref);
     BCU(cudaMemcpyAsync(dpref, pref.data(), pref.size() * sizeof(long long), cudaMemcpyHostToDevice, e.st));
     BCU(launch_assemble_batched(djobs, (int)jobs.size(), dpref, tot, q, e.o.form, 1, e.asm_ty, e.st));

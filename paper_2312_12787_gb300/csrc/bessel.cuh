@@ -411,6 +411,23 @@ BEM_HD float f32_rsqrt_seed(float v) {
   return 1.0f / sqrtf(v);
 #endif
 }
+BEM_HD float f32_rcp_seed(float v) {
+#if defined(__CUDA_ARCH__)
+  return __frcp_rn(v);
+#else
+  return 1.0f / v;
+#endif
+}
+// a / b for b != 0: the FP32 quotient of the leading parts, corrected once by the double-float remainder
+// a - b q (a Newton step on the quotient; relative error ~2^-46).
+BEM_HD F2 f2_div(F2 a, F2 b) {
+  const float y = f32_rcp_seed(b.h);
+  const float q1 = a.h * y;
+  const F2 rem = f2_sub(a, f2_mulf(b, q1));
+  const float q2 = rem.h * y;
+  return f2_fast_two_sum(q1, q2);
+}
+
 // 1/sqrt(a), a > 0: an FP32 estimate refined by two Newton steps y <- y + y (1 - a y^2) / 2 in double-float
 // (each step squares the relative error: ~1e-7 -> ~1e-14 -> double-float rounding).
 BEM_HD F2 f2_rsqrt(F2 a) {
@@ -549,7 +566,7 @@ BEM_HD void bessel01_asymp_f2x(double x, F2 X, Bessel01F2& b) {
   b.y1 = f2_neg(f2_sub(f2_mul(p1, er), f2_mul(q1, ei)));
 }
 
-// ---- tabulated values and Taylor steps on 2 <= x < 35 --------------------------------------------------
+// ---- tabulated values and Taylor steps on 2 <= x < 128 -------------------------------------------------
 // J0, Y0, J1, Y1 at x_k = 2 + k/32 (computed once on the host with the FP64 routines above, error ~1e-15 of
 // |H|), stored in double-float with 1/x_k.  Between grid points both pairs obey the same first-order system
 // Z0' = -Z1, Z1' = Z0 - Z1/x (DLMF 10.6.2), so with Z0(x_k + h) = sum a_n h^n and Z1(x_k + h) = sum b_n h^n the
@@ -557,11 +574,13 @@ BEM_HD void bessel01_asymp_f2x(double x, F2 X, Bessel01F2& b) {
 //   a_{n+1} = -b_n / (n+1),   b_{n+1} = (a_n - c_n) / (n+1),   c_n = (b_n - c_{n-1}) / x_k,
 // where c_n are the coefficients of Z1/(x_k + h).  With |h| <= 1/64, eight orders leave a remainder below
 // 1e-16; orders 0-3 run in double-float, orders 4-7 (below 3e-9 of the value) in FP32.  This replaces the
-// recurrence of Miller's algorithm (56 steps) and the long expansion near x = 18 by about a fifth of the
-// arithmetic.
+// recurrence of Miller's algorithm (56 steps) and Hankel's expansion up to x = 128 by about a fifth of the
+// arithmetic of the expansion (whose double-float sine, cosine and four Horner sums take ~1000 FP32 operations
+// per evaluation); the table costs 128 bytes per grid point, read through the L1 cache (the lanes of a warp
+// take neighbouring elements, so their arguments share a few grid points).
 constexpr double kTabStep = 1.0 / 32.0;
-constexpr int kTabN = 1057;          // x_k = 2 + k / 32, k = 0 .. 1056: [2, 35]
-constexpr float kTabXMax = 35.0f;    // the table serves 2 <= x < 35
+constexpr int kTabN = 4033;          // x_k = 2 + k / 32, k = 0 .. 4032: [2, 128]
+constexpr float kTabXMax = 128.0f;   // the table serves 2 <= x < 128 (516 KB of device memory)
 // One grid point x_k: for each pair (J0, J1) and (Y0, Y1) the Taylor coefficients of orders 0..3 of Z0 (a_n)
 // and Z1 (b_n) as double-float (a_1 = -b_0 is not stored), c_3 (FP32, the start of the FP32 orders) and
 // 1/x_k (FP32).  The coefficients depend on x_k only, so they are made once on the host in FP64.

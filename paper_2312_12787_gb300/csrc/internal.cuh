@@ -69,6 +69,7 @@ struct Quad {
   double t[kMaxQuad];
   double w[kMaxQuad];
   float wh[kMaxQuad], wl[kMaxQuad];   // weights in double-float
+  float th[kMaxQuad], tl[kMaxQuad];   // nodes in double-float
 };
 
 // One problem of a batched assembly launch.

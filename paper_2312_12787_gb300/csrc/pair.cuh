@@ -4,26 +4,19 @@
 // paragraph), rows placed by the Sec. 6 recipe (eq. calderon_bieb with beta = -alpha, eq. 3dom_calderon_bie
 // with gamma = alpha/eps) or one of the comparison forms.
 //
-// Precision plan (GB300 issues FP64 at 2 operations per clock per SM against 128 for FP32): the node
-// geometry stays FP64 up to the distance r, the phase k r and the direction cosines (an error of k r is an
-// error of the Hankel function's phase, and k r reaches ~100; the cosines cancel for nearly tangent pairs).
-// Everything after that (Bessel values, Gauss weights, the four sums and their combination into entries) is
-// double-float arithmetic on the FP32 pipe.  Accuracy against the FP64 definition: ~1e-14 of the largest
-// entry of a block, ~3e-12 relative on entries above 1e-6 of it.
+// Precision plan (GB300 issues FP64 at 2 operations per clock per SM against 128 for FP32): FP64 forms, once
+// per element pair, the centre-to-centre vector and its projections (the cosines of nearly tangent pairs
+// cancel there, so they keep FP64's extra bits), and per Gauss node only the phase k r (an error of k r is an
+// error of the Hankel function's phase, and k r reaches ~100).  The node distances and direction cosines
+// relative to that vector, the Bessel values, Gauss weights, the four sums and their combination into entries
+// are double-float arithmetic on the FP32 pipe.  Accuracy against the FP64 definition: ~1e-14 of the largest
+// entry of a block, a few 1e-12 relative on entries above 1e-6 of it.
 #pragma once
 
 #include "bessel.cuh"
 #include "internal.cuh"
 
 namespace bem {
-
-BEM_HD double rsqrt_d(double v) {
-#if defined(__CUDA_ARCH__)
-  return rsqrt(v);
-#else
-  return 1.0 / sqrt(v);
-#endif
-}
 
 BEM_HD double2 mul_i(double2 z) { return make_double2(-z.y, z.x); }
 
@@ -136,11 +129,25 @@ BEM_HD void assemble_pair_f2(const ElemDev& e, const DomTab& dom, const Quad& q,
   const double xi = e.mx[i], yi = e.my[i];
   const int Pi = e.P[i], Mi = e.M[i];
   const double mxj = e.mx[j], myj = e.my[j], txj = e.tx[j], tyj = e.ty[j];
-  const double half_h = 0.5 * e.h[j];
   const int Pj = e.P[j], Mj = e.M[j];
   const double nxi = -e.ty[i], nyi = e.tx[i], nxj = -tyj, nyj = txj;
   const F2 HH{e.hhh[j], e.hhl[j]};
   const F2 NN = f2_from_bits(nxi * nxj + nyi * nyj);   // n_i . n_j
+  // Node geometry.  Once per pair in FP64: the vector d = x_i - m_j from element j's centre to the collocation
+  // point, |d| and its projections on tau_j, n_i and n_j.  The node y_m = m_j + s_m tau_j (s_m = t_m h_j / 2)
+  // then has z_m = x_i - y_m = d - s_m tau_j, so per node, in double-float:
+  //   r_m^2 - |d|^2 = s_m (s_m - 2 d.tau_j),   z_m.n_j = d.n_j (tau_j is orthogonal to n_j),
+  //   z_m.n_i = d.n_i - s_m tau_j.n_i.
+  // The phase k r_m needs r_m to FP64's absolute accuracy (k r reaches ~100, and Gauss sums of oscillating
+  // kernels can cancel by three decades): r_m = |d| + c_m with |d| in FP64 and the node's offset
+  // c_m = (r_m^2 - |d|^2) / (r_m + |d|), |c_m| <= h_j / 2, in double-float, so the only error beyond FP64's is
+  // that of c_m, ~2^-46 h_j.
+  const double dx = xi - mxj, dy = yi - myj;
+  const double dd = dx * dx + dy * dy;
+  const double dn = sqrt(dd);
+  const F2 DD = f2_from_bits(dd), DN = f2_from_bits(dn);
+  const F2 DP2 = f2_from_bits(2.0 * (dx * txj + dy * tyj));
+  const F2 DNJ = f2_from_bits(dx * nxj + dy * nyj);
 
   RowEq eq[2];
   float sg[2];
@@ -156,27 +163,29 @@ BEM_HD void assemble_pair_f2(const ElemDev& e, const DomTab& dom, const Quad& q,
     K[half] = F2{dom.kh[d], dom.kl[d]};
     any_bm = any_bm || (eq[half].bm && sg[half] != 0.f);
   }
+  F2 DNI{0.f, 0.f}, TNI{0.f, 0.f};
+  if (any_bm) {
+    DNI = f2_from_bits(dx * nxi + dy * nyi);
+    TNI = f2_from_bits(txj * nxi + tyj * nyi);
+  }
 
   C2 sS[2], sD[2], sDs[2], sN[2];
 #pragma unroll
   for (int half = 0; half < 2; ++half) sS[half] = sD[half] = sDs[half] = sN[half] = c2_zero();
   for (int m = 0; m < q.Q; ++m) {
-    // FP64: node, distance, phase argument and the direction cosines zh . n_i, zh . n_j (these cancel for
-    // nearly tangent pairs, so they keep FP64's extra bits)
-    const double sq = half_h * q.t[m];
-    const double zx0 = xi - (mxj + sq * txj), zy0 = yi - (myj + sq * tyj);
-    const double r2 = zx0 * zx0 + zy0 * zy0;
-    const double ir = rsqrt_d(r2);
-    const double r = r2 * ir;
-    const double ux = zx0 * ir, uy = zy0 * ir;
-    // double-float from here on
-    const F2 IR = f2_from_bits(ir), R = f2_from_bits(r);
-    const F2 CI = f2_from_bits(ux * nxi + uy * nyi);
-    const F2 CJ = f2_from_bits(ux * nxj + uy * nyj);
+    const F2 S = f2_mul(HH, F2{q.th[m], q.tl[m]});
+    const F2 NUM = f2_mul(S, f2_sub(S, DP2));           // r_m^2 - |d|^2
+    const F2 R2 = f2_add(DD, NUM);
+    const F2 IR = f2_rsqrt(R2);
+    const F2 R = f2_mul(R2, IR);
+    const F2 CM = f2_div(NUM, f2_add(R, DN));         // r_m - |d|
+    const double r = dn + ((double)CM.h + (double)CM.l);
+    const F2 CJ = f2_mul(DNJ, IR);
     const F2 WD = f2_mul(HH, F2{q.wh[m], q.wl[m]});
     const F2 WCJ = f2_mul(WD, CJ);
     F2 WCI{0.f, 0.f}, A1{0.f, 0.f}, A0{0.f, 0.f};
     if (any_bm) {
+      const F2 CI = f2_mul(f2_sub(DNI, f2_mul(S, TNI)), IR);
       const F2 CC = f2_mul(CI, CJ);
       WCI = f2_mul(WD, CI);
       A1 = f2_mul(f2_mul(WD, IR), f2_sub(NN, f2_pow2(CC, 2.f)));

@@ -3,8 +3,9 @@
 //
 // stdin: n Q form n_dom, then k[n_dom], eps[n_dom], the Gauss-Legendre nodes t[Q] and weights w[Q] on
 // [-1, 1], then one line per element: ax ay bx by P M (start and end vertex, the domain the normal points out
-// of and the domain it points into).  stdout: the 2n x 2n matrix row by row, "re im" per entry in hexadecimal
-// floating point.  The element geometry below is the per-element step of the element kernel, restated.
+// of and the domain it points into), optionally followed by a pair count and that many "i j" lines.  stdout: the
+// 2n x 2n matrix row by row, "re im" per entry in hexadecimal floating point, or, with a pair list, the four
+// entries (i, j), (i, N+j), (N+i, j), (N+i, N+j) of each listed pair on one line.  The element geometry below is the per-element step of the element kernel, restated.
 #include <cstdio>
 #include <vector>
 
@@ -38,8 +39,10 @@ int main() {
   split(1.0 / dom.k[0], dom.ik1h, dom.ik1l);
   Quad q{};
   q.Q = Q;
-  for (int m = 0; m < Q; ++m)
+  for (int m = 0; m < Q; ++m) {
     if (std::scanf("%lf", &q.t[m]) != 1) return 2;
+    split(q.t[m], q.th[m], q.tl[m]);
+  }
   for (int m = 0; m < Q; ++m) {
     if (std::scanf("%lf", &q.w[m]) != 1) return 2;
     split(q.w[m], q.wh[m], q.wl[m]);
@@ -63,6 +66,22 @@ int main() {
   const ElemDev e{ax.data(), ay.data(), bx.data(), by.data(), mx.data(), my.data(), tx.data(), ty.data(),
                   h.data(), P.data(), M.data(), txh.data(), txl.data(), tyh.data(), tyl.data(), hhh.data(),
                   hhl.data()};
+  // optional: a list of pairs (count, then i j per pair) -> the four entries of each pair, one pair per line
+  int npairs = 0;
+  if (std::scanf("%d", &npairs) == 1) {
+    for (int k = 0; k < npairs; ++k) {
+      int i = 0, j = 0;
+      if (std::scanf("%d %d", &i, &j) != 2 || i < 0 || j < 0 || i >= n || j >= n) return 2;
+      C2 out[2][2];
+      assemble_pair_f2(e, dom, q, form, i, j, out);
+      for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) {
+          const double2 v = c2_to(out[a][b]);
+          std::printf("%a %a%c", v.x, v.y, (a == 1 && b == 1) ? '\n' : ' ');
+        }
+    }
+    return 0;
+  }
   const size_t n2 = 2 * (size_t)n;
   std::vector<double2> A(n2 * n2);
   for (int i = 0; i < n; ++i)

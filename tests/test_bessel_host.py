@@ -1,6 +1,6 @@
 """The library's Bessel routines (bessel.cuh, host-and-device code) built for the host and checked against
 mpmath on every branch: the ascending series (x < 2), the Taylor steps from the tabulated coefficients
-(2 <= x < 35), Hankel's expansion (x >= 35), and the branch boundaries.  Errors are measured relative to
+(2 <= x < 128), Hankel's expansion (x >= 128), and the branch boundaries.  Errors are measured relative to
 |H0| for J0, Y0 and to |H1| for J1, Y1 (the Hankel functions the kernels are made of, Sec. 3.3).
 
 Three paths are checked: bessel01_f2, the double-float path of the assembly and matrix-free kernels;
@@ -42,10 +42,10 @@ def values(tmp_path_factory):
     xs = np.concatenate([
         np.geomspace(1e-3, 1.999, 40),
         [2.0 - 2.0 ** -40, 2.0, 2.0 + 2.0 ** -40],
-        2.0 + np.arange(1, 1056, 3) / 32.0 + rng.uniform(-1 / 64, 1 / 64, 352),   # around the grid points
-        2.0 + (np.arange(0, 1056, 5) + 0.5) / 32.0,                              # half-way between them
-        [18.0, 25.0, 35.0 - 2.0 ** -40, 35.0, 35.0 + 2.0 ** -40],
-        np.geomspace(35.0, 2000.0, 160),
+        2.0 + np.arange(1, 4032, 7) / 32.0 + rng.uniform(-1 / 64, 1 / 64, 576),   # around the grid points
+        2.0 + (np.arange(0, 4032, 11) + 0.5) / 32.0,                             # half-way between them
+        [18.0, 25.0, 35.0, 128.0 - 2.0 ** -40, 128.0, 128.0 + 2.0 ** -40],
+        np.geomspace(128.0, 2000.0, 120),
     ])
     out = subprocess.run([exe], input="\n".join(repr(float(v)) for v in xs), capture_output=True, text=True,
                          check=True).stdout
@@ -64,7 +64,7 @@ def _rel_err(got4, ref):
     return np.max(np.abs(got4 - ref) / scale, axis=1)
 
 
-@pytest.mark.parametrize("lo,hi,bound", [(0.0, 2.0, 3e-15), (2.0, 35.0, 1e-14), (35.0, np.inf, 2.5e-14)])
+@pytest.mark.parametrize("lo,hi,bound", [(0.0, 2.0, 3e-15), (2.0, 128.0, 1e-14), (128.0, np.inf, 2.5e-14)])
 def test_double_float_path_matches_mpmath(values, lo, hi, bound):
     xs, got, ref = values
     sel = (xs >= lo) & (xs < hi)
@@ -80,7 +80,7 @@ def test_fp64_path_matches_mpmath(values, lo, hi, bound):
     assert sel.sum() > 30 and err.max() <= bound, (err.max(), xs[sel][np.argmax(err)])
 
 
-@pytest.mark.parametrize("lo,hi,bound", [(0.0, 2.0, 1e-15), (2.0, 18.0, 2e-15), (18.0, np.inf, 2e-15)])
+@pytest.mark.parametrize("lo,hi,bound", [(0.0, 2.0, 1e-15), (2.0, 18.0, 3e-15), (18.0, np.inf, 2e-15)])
 def test_table_builders_match_mpmath(values, lo, hi, bound):
     xs, got, ref = values
     sel = (xs >= lo) & (xs < hi)

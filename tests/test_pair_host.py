@@ -34,6 +34,29 @@ def harness(tmp_path_factory):
     return exe
 
 
+def _input_lines(wp, Q, form):
+    t, w = np.polynomial.legendre.leggauss(Q)
+    rows = []
+    for s in wp.segments:
+        xy = np.asarray(s.xy, float)
+        ne = len(xy) if s.closed else len(xy) - 1
+        for e in range(ne):
+            a, b = xy[e], xy[(e + 1) % len(xy)]
+            rows.append(" ".join(repr(float(v)) for v in (a[0], a[1], b[0], b[1])) + f" {int(s.P)} {int(s.M)}")
+    head = [f"{len(rows)} {Q} {FORMS[form]} {len(wp.k)}", " ".join(repr(float(v)) for v in wp.k),
+            " ".join(repr(float(v)) for v in wp.eps), " ".join(repr(float(v)) for v in t),
+            " ".join(repr(float(v)) for v in w)]
+    return head + rows
+
+
+def host_pairs(exe, wp, Q, form, pairs):
+    """The four entries of each listed element pair: (npairs, 4) for (i, j), (i, N+j), (N+i, j), (N+i, N+j)."""
+    lines = _input_lines(wp, Q, form) + [str(len(pairs))] + [f"{i} {j}" for i, j in pairs]
+    out = subprocess.run([exe], input="\n".join(lines) + "\n", capture_output=True, text=True, check=True).stdout
+    v = np.array([[float.fromhex(x) for x in ln.split()] for ln in out.strip().splitlines()])
+    return v[:, 0::2] + 1j * v[:, 1::2]
+
+
 def host_matrix(exe, wp, Q, form):
     """Elements from the segments as the C interface forms them (closed: the last vertex joins the first)."""
     t, w = np.polynomial.legendre.leggauss(Q)
@@ -75,3 +98,49 @@ def test_host_entries_match_oracle(harness, name, mk, Q, form):
     ref = O.assemble(wp, Q=Q, form=form)
     blk, rl = block_errors(got, ref)
     assert blk <= ENTRY_BLOCK_TOL and rl <= ENTRY_REL_TOL, (name, blk, rl)
+
+
+def test_cancellation_dominated_entries_are_closer_to_the_exact_rule_than_the_oracle(harness):
+    """Double-layer entries of neighbouring, nearly collinear elements are small because the kernel's cosine
+    (x_i - y).n_j nearly cancels; in FP64 both the oracle (per node) and the library (once per pair, from the
+    centre-to-centre vector) lose digits there, so their disagreement on such entries is not the library's
+    error.  On the star of 1024 elements (k = 20 / 30) the entries that differ most from the oracle, relative to
+    themselves, are each evaluated with the same Gauss rule in 40-digit arithmetic from the same FP64 vertices:
+    the library's value is about as close to it as the oracle's (both ~1e-10 relative there), so the difference
+    between the two is FP64 cancellation and not an error of the library's arithmetic."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 40
+    N, k_in = 1024, 30.0
+    wp = W.Problem(k=[20.0, k_in], eps=[1.0, 2.25], segments=[W.Segment(W.star(N, 0.3, 5), P=0, M=1, closed=True)])
+    pairs = [(i, (i + 1) % N) for i in range(N)] + [(i, (i - 1) % N) for i in range(N)]
+    got = host_pairs(harness, wp, 4, "mod", pairs)[:, 0]             # upper rows, u part: -alpha sigma D
+    el = O.elements(wp)
+    upper = O.assemble_rows(wp, np.arange(N), Q=4, el=el)
+    ii = np.array([p[0] for p in pairs])
+    jj = np.array([p[1] for p in pairs])
+    ref = upper[ii, jj]
+    relerr = np.abs(got - ref) / np.abs(ref)
+    relerr[np.abs(ref) < 1e-6 * np.max(np.abs(upper[:, :N]))] = 0.0
+    t, w = O.gauss_legendre(4)
+    for kk in np.argsort(-relerr)[:3]:
+        i, j = pairs[kk]
+        a = [mp.mpf(float(v)) for v in el.a[j]]
+        b = [mp.mpf(float(v)) for v in el.b[j]]
+        ai = [mp.mpf(float(v)) for v in el.a[i]]
+        bi = [mp.mpf(float(v)) for v in el.b[i]]
+        xi = [(ai[0] + bi[0]) / 2, (ai[1] + bi[1]) / 2]
+        mj = [(a[0] + b[0]) / 2, (a[1] + b[1]) / 2]
+        hj = mp.sqrt((b[0] - a[0]) ** 2 + (b[1] - a[1]) ** 2)
+        tx, ty = (b[0] - a[0]) / hj, (b[1] - a[1]) / hj
+        acc = mp.mpc(0)
+        for q in range(4):
+            y = [mj[0] + hj / 2 * mp.mpf(float(t[q])) * tx, mj[1] + hj / 2 * mp.mpf(float(t[q])) * ty]
+            z = [xi[0] - y[0], xi[1] - y[1]]
+            r = mp.sqrt(z[0] ** 2 + z[1] ** 2)
+            acc += hj / 2 * mp.mpf(float(w[q])) * mp.hankel1(1, k_in * r) * (-z[0] * ty + z[1] * tx) / r
+        # row i is the interior domain's standard equation times -alpha = i/k_1; element j's normal points into
+        # the interior (sigma = -1); D = (i k/4) times the Gauss sum
+        exact = complex((1j / 20.0) * (-1.0) * mp.mpc(0, 0.25) * k_in * acc)
+        e_lib, e_orc = abs(got[kk] - exact) / abs(exact), abs(ref[kk] - exact) / abs(exact)
+        assert e_lib <= 1.5 * e_orc + 1e-13, ((i, j), e_lib, e_orc)
+
