@@ -180,7 +180,10 @@ BEM_API bem_status bem_residual_noalloc(bem_problem* p, int n_rhs, const bem_c64
 
 /* Steps a6..a9: solve A x = b for n_rhs right-hand sides b_dev (n_rhs x 2N) into x_dev.
  * iters_host[r] = total GMRES iterations (matvecs) of column r, resid_host[r] = final relative residual
- * ||b - A x|| / ||b|| computed in FP64 (FP64 path: from the GMRES estimate).  Either may be NULL. */
+ * ||b - A x|| / ||b|| (FP64 path: the GMRES estimate; mixed paths: the FP64 refinement residual, formed in
+ * double-float arithmetic until it is below 1e-4 of ||b|| and from then on updated as r -= A d with the inner
+ * solves' own product of each correction d, whose ~3e-7 relative error enters r at ~3e-7 |A| |d|, far below the
+ * tolerance; tolerances below 1e-11 form every refinement residual in double-float).  Either may be NULL. */
 BEM_API bem_status bem_solve(bem_problem* p, int n_rhs, const bem_c64* b_dev, bem_c64* x_dev, int* iters_host,
                              double* resid_host, void* stream);
 

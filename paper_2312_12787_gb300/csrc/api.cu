@@ -478,7 +478,7 @@ size_t basis_bytes(const Solver& sv) {
 
 // One unrestarted GMRES run from x0 = 0 on r0 (FP64 block), adding the correction into x.
 bem_status gmres_run(bem_problem* p, Solver& sv, const double2* r0, double2* x, const std::vector<double>& tols,
-                     std::vector<int>& iters, std::vector<double>& resid, cudaStream_t s) {
+                     std::vector<int>& iters, std::vector<double>& resid, cudaStream_t s, float2* dout = nullptr) {
   KrylovState& st = sv.st;
   const int n2 = st.n, nrhs = st.nrhs;
   const double tol = tols[0];
@@ -656,7 +656,7 @@ bem_status gmres_run(bem_problem* p, Solver& sv, const double2* r0, double2* x, 
   }
   {
     Phase ph(p, BEM_PH_UPDATE, s, 2);
-    CU(krylov_update_solution(st, x, s));
+    CU(krylov_update_solution(st, x, s, dout));
   }
   std::vector<int> it(nrhs);
   std::vector<double> rs(nrhs);
@@ -692,6 +692,10 @@ bem_status residual_mixed(bem_problem* p, Solver& sv, int nrhs, const double2* x
 // column 2-norms of an FP64 block (host result)
 bem_status column_norms(bem_problem* p, Solver& sv, const double2* v, int nrhs, std::vector<double>& out,
                         cudaStream_t s);
+
+// The refinement residual updated by a correction: r -= A d, with the correction d (complex FP32, in the
+// solver's work block W) multiplied by the inner solves' own product (tensor-core GEMM or FP32 GEMV/GEMM).
+bem_status residual_update(bem_problem* p, Solver& sv, int nrhs, double2* r, cudaStream_t s);
 
 }  // namespace
 
@@ -741,6 +745,32 @@ bem_status residual_mixed(bem_problem* p, Solver& sv, int nrhs, const double2* x
   return BEM_OK;
 }
 
+bem_status residual_update(bem_problem* p, Solver& sv, int nrhs, double2* r, cudaStream_t s) {
+  const int n2 = 2 * p->n;
+  const float2* d = static_cast<const float2*>(sv.st.W);
+  float2* y = static_cast<float2*>(sv.st.V);   // the basis is free between GMRES runs
+  const bool tc = p->o.prec == BEM_PREC_MIXED_TC && nrhs > 1 && matvec_tc_supported(n2, nrhs);
+  int tc_err = 0;
+  {
+    Phase ph(p, BEM_PH_RESIDUAL, s, tc ? 5 : 2);   // [column maxima, operand, GEMM, reduction | product], r -= y
+    if (tc) {
+      const bem_status a = ensure_a16(p, s);
+      if (a != BEM_OK) return a;
+      CU(matvec_tc_clear_error(sv.tcws, n2, nrhs, s));
+      CU(launch_matvec_tc(p->d_A16, n2, nrhs, d, y, sv.tcws, sv.tcws_bytes, s));
+      CU(cudaMemcpyAsync(&tc_err, matvec_tc_error_word(sv.tcws, n2, nrhs), sizeof(int), cudaMemcpyDeviceToHost, s));
+    } else {
+      CU(launch_matvec_c32(static_cast<const float2*>(p->d_A), n2, n2, nrhs, d, y, nullptr, s));
+    }
+    CU(launch_sub_c32(r, y, (size_t)nrhs * n2, s));
+  }
+  if (tc) {
+    CU(cudaStreamSynchronize(s));
+    if (tc_err) return fail(BEM_ETIMEOUT, "tensor-core GEMM wait expired (code %d)", tc_err);
+  }
+  return BEM_OK;
+}
+
 bem_status solve_impl(bem_problem* p, int nrhs, const double2* b, double2* x, int* iters_h, double* resid_h,
                       cudaStream_t s) {
   bem_status st = assemble_impl(p, s);
@@ -767,14 +797,20 @@ bem_status solve_impl(bem_problem* p, int nrhs, const double2* b, double2* x, in
     CU(cudaMemcpyAsync(sv.r, b, (size_t)nrhs * n2 * sizeof(double2), cudaMemcpyDeviceToDevice, s));
     rn = bn;
     std::vector<int> strict(nrhs, 0);
+    std::vector<char> met(nrhs, 0);   // the column met the tolerance; resid[r] keeps its residual from then on
     bool done = false;
     for (int outer = 0; outer < p->o.max_refine && !done; ++outer) {
-      // zero the residual of columns that already meet the tolerance so the inner solve skips them
+      // zero the residual of columns that meet the tolerance so the inner solve skips them
       done = true;
       for (int r = 0; r < nrhs; ++r) {
+        if (met[r]) continue;
         resid[r] = bn[r] > 0 ? rn[r] / bn[r] : 0.0;
-        if (resid[r] <= p->o.tol) CU(cudaMemsetAsync(sv.r + (size_t)r * n2, 0, n2 * sizeof(double2), s));
-        else done = false;
+        if (resid[r] <= p->o.tol) {
+          met[r] = 1;
+          CU(cudaMemsetAsync(sv.r + (size_t)r * n2, 0, n2 * sizeof(double2), s));
+        } else {
+          done = false;
+        }
       }
       if (done) break;
       // each column's inner run only needs to reach what the outer tolerance still asks of it
@@ -783,9 +819,17 @@ bem_status solve_impl(bem_problem* p, int nrhs, const double2* b, double2* x, in
         tols[r] = rn[r] > 0 ? std::max(p->o.inner_tol, 0.3 * p->o.tol * bn[r] / rn[r]) : 1.0;
       const std::vector<int> it_before = iters;
       const std::vector<double> rn_before = rn;
-      st = gmres_run(p, sv, sv.r, x, tols, iters, inner_res, s);
+      // Once the residual is below 1e-4 of ||b||, it is updated, r -= A d, with the inner solves' own product of
+      // the correction d: d is then a small fraction of x (its relative size follows the residual's), so the
+      // product's ~3e-7 relative error enters r at ~3e-7 |A| |d|, far below the tolerance, and the double-float
+      // residual b - (hi + lo) x is formed only until then.  Tolerances below 1e-11 keep exact residuals.
+      double worst = 0.0;
+      for (int r = 0; r < nrhs; ++r)
+        if (!met[r]) worst = std::max(worst, bn[r] > 0 ? rn[r] / bn[r] : 0.0);
+      const bool update = outer > 0 && p->o.tol >= 1e-11 && worst <= 1e-4;
+      st = gmres_run(p, sv, sv.r, x, tols, iters, inner_res, s, update ? static_cast<float2*>(sv.st.W) : nullptr);
       if (st != BEM_OK) return st;
-      st = residual_mixed(p, sv, nrhs, x, b, sv.r, s);
+      st = update ? residual_update(p, sv, nrhs, sv.r, s) : residual_mixed(p, sv, nrhs, x, b, sv.r, s);
       if (st != BEM_OK) return st;
       st = column_norms(p, sv, sv.r, nrhs, rn, s);
       if (st != BEM_OK) return st;
@@ -793,7 +837,7 @@ bem_status solve_impl(bem_problem* p, int nrhs, const double2* b, double2* x, in
       // its FP32 basis under the selective second pass: from now on it runs Gram-Schmidt twice.
       bool changed = false;
       for (int r = 0; r < nrhs; ++r) {
-        if (strict[r] || resid[r] <= p->o.tol) continue;
+        if (strict[r] || met[r]) continue;
         if (iters[r] - it_before[r] >= p->o.max_iter || rn[r] > 0.25 * rn_before[r]) {
           strict[r] = 1;
           changed = true;
@@ -802,7 +846,7 @@ bem_status solve_impl(bem_problem* p, int nrhs, const double2* b, double2* x, in
       if (changed) CU(cudaMemcpyAsync(sv.st.strict, strict.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, s));
     }
     for (int r = 0; r < nrhs; ++r) {
-      resid[r] = bn[r] > 0 ? rn[r] / bn[r] : 0.0;
+      if (!met[r]) resid[r] = bn[r] > 0 ? rn[r] / bn[r] : 0.0;
       if (resid[r] > p->o.tol) result = BEM_ENOCONV;
     }
   }

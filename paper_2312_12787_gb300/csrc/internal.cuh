@@ -188,6 +188,8 @@ cudaError_t launch_convert_c64_c32(const double2* in, float2* out, size_t count,
 cudaError_t launch_convert_c32_c64(const float2* in, double2* out, size_t count, cudaStream_t s);
 // r = b - r (elementwise)
 cudaError_t launch_axpby_neg(const double2* b, double2* r, size_t count, cudaStream_t s);
+// r -= y (r complex FP64, y complex FP32), elementwise
+cudaError_t launch_sub_c32(double2* r, const float2* y, size_t count, cudaStream_t s);
 cudaError_t launch_column_norms(const double2* v, int n, int ncol, double* out, cudaStream_t s);
 
 // GMRES building blocks for nrhs systems sharing one matrix; see krylov.cu.
@@ -235,7 +237,8 @@ cudaError_t krylov_start(const KrylovState& st, const double2* r0, double tol_un
 cudaError_t krylov_orthogonalise(const KrylovState& st, int passes, cudaStream_t s);
 cudaError_t krylov_finish_step(const KrylovState& st, double tol, cudaStream_t s);   // one kernel
 int krylov_orth_launches(const KrylovState& st, int passes);   // kernels of krylov_orthogonalise
-cudaError_t krylov_update_solution(const KrylovState& st, double2* x, cudaStream_t s);
+// x += V y; with dout, the correction V y is also written there in complex FP32.
+cudaError_t krylov_update_solution(const KrylovState& st, double2* x, cudaStream_t s, float2* dout = nullptr);
 
 // For the batch engine: validate, upload geometry and allocate the mixed-precision matrix of p (without
 // assembling it), fill its batched-assembly job and mark the matrix as current.  Also reports the

@@ -475,8 +475,9 @@ __global__ void __launch_bounds__(kBsThreads) k_lsq(KrylovState st) {
 // x += sum_i y_i v_i: CH/2 threads per chunk, each owning one pair of entries and running over all i;
 // products and sums in the basis precision (the correction only needs the inner solve's accuracy), added
 // to the FP64 x.
+// dout (optional): the correction sum_i y_i v_i itself, complex FP32 (the refinement's updated residual).
 template <typename T, int CH>
-__global__ void __launch_bounds__(CH / 2) k_xupdate(KrylovState st, double2* x) {
+__global__ void __launch_bounds__(CH / 2) k_xupdate(KrylovState st, double2* x, float2* dout) {
   using F = typename Vec<T>::acc_t;
   __shared__ F ys[2 * kHsMax];
   const int c = blockIdx.x, s = blockIdx.y;
@@ -488,7 +489,14 @@ __global__ void __launch_bounds__(CH / 2) k_xupdate(KrylovState st, double2* x) 
   }
   __syncthreads();
   const int k = c * CH + 2 * threadIdx.x;
-  if (k >= st.n || mm == 0) return;
+  if (k >= st.n) return;
+  if (mm == 0) {   // no correction (the system had already converged)
+    if (dout) {
+      float2* ds = dout + (size_t)s * st.n + k;
+      ds[0] = ds[1] = make_float2(0.f, 0.f);
+    }
+    return;
+  }
   const size_t stride = (size_t)st.nrhs * st.n;
   const T* V = static_cast<const T*>(st.V) + (size_t)s * st.n + k;
   F ax = 0, ay = 0, bx = 0, by = 0;
@@ -505,6 +513,11 @@ __global__ void __launch_bounds__(CH / 2) k_xupdate(KrylovState st, double2* x) 
   double2* xs = x + (size_t)s * st.n + k;
   xs[0] = make_double2(xs[0].x + (double)ax, xs[0].y + (double)ay);
   xs[1] = make_double2(xs[1].x + (double)bx, xs[1].y + (double)by);
+  if (dout) {
+    float2* ds = dout + (size_t)s * st.n + k;
+    ds[0] = make_float2((float)ax, (float)ay);
+    ds[1] = make_float2((float)bx, (float)by);
+  }
 }
 
 int nchunk_of(int n) { return (n + kCh - 1) / kCh; }
@@ -581,15 +594,15 @@ cudaError_t finish_t(const KrylovState& st, double tol, cudaStream_t s) {
 }
 
 template <typename T>
-cudaError_t xupd_t(const KrylovState& st, double2* x, cudaStream_t s) {
+cudaError_t xupd_t(const KrylovState& st, double2* x, float2* dout, cudaStream_t s) {
   k_lsq<<<st.nrhs, kBsThreads, 0, s>>>(st);
   const int ch = chunk_of(st.n, st.nrhs);
   const dim3 grd((st.n + ch - 1) / ch, st.nrhs);
   switch (ch) {
-    case 512: k_xupdate<T, 512><<<grd, 256, 0, s>>>(st, x); break;
-    case 256: k_xupdate<T, 256><<<grd, 128, 0, s>>>(st, x); break;
-    case 128: k_xupdate<T, 128><<<grd, 64, 0, s>>>(st, x); break;
-    default: k_xupdate<T, 64><<<grd, 32, 0, s>>>(st, x); break;
+    case 512: k_xupdate<T, 512><<<grd, 256, 0, s>>>(st, x, dout); break;
+    case 256: k_xupdate<T, 256><<<grd, 128, 0, s>>>(st, x, dout); break;
+    case 128: k_xupdate<T, 128><<<grd, 64, 0, s>>>(st, x, dout); break;
+    default: k_xupdate<T, 64><<<grd, 32, 0, s>>>(st, x, dout); break;
   }
   return cudaGetLastError();
 }
@@ -612,8 +625,8 @@ int krylov_orth_launches(const KrylovState& st, int passes) {
 cudaError_t krylov_finish_step(const KrylovState& st, double tol, cudaStream_t s) {
   return st.basis_fp32 ? finish_t<float2>(st, tol, s) : finish_t<double2>(st, tol, s);
 }
-cudaError_t krylov_update_solution(const KrylovState& st, double2* x, cudaStream_t s) {
-  return st.basis_fp32 ? xupd_t<float2>(st, x, s) : xupd_t<double2>(st, x, s);
+cudaError_t krylov_update_solution(const KrylovState& st, double2* x, cudaStream_t s, float2* dout) {
+  return st.basis_fp32 ? xupd_t<float2>(st, x, dout, s) : xupd_t<double2>(st, x, dout, s);
 }
 
 }  // namespace bem

@@ -568,6 +568,13 @@ __global__ void k_add_c32(float2* __restrict__ a, const float2* __restrict__ b, 
   }
 }
 
+__global__ void k_sub_c32(double2* r, const float2* y, size_t count) {
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < count; t += (size_t)gridDim.x * blockDim.x) {
+    const float2 v = y[t];
+    r[t] = make_double2(r[t].x - (double)v.x, r[t].y - (double)v.y);
+  }
+}
+
 __global__ void k_b_minus(const double2* b, double2* r, size_t count) {
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < count; t += (size_t)gridDim.x * blockDim.x)
     r[t] = csub(b[t], r[t]);
@@ -596,6 +603,11 @@ static int gemv_c32_grid(int nrhs) {
 
 cudaError_t launch_axpby_neg(const double2* b, double2* r, size_t count, cudaStream_t s) {
   k_b_minus<<<1024, 256, 0, s>>>(b, r, count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sub_c32(double2* r, const float2* y, size_t count, cudaStream_t s) {
+  k_sub_c32<<<1024, 256, 0, s>>>(r, y, count);
   return cudaGetLastError();
 }
 
