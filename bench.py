@@ -39,21 +39,21 @@ sys.path.insert(0, ROOT)
 import workloads as W  # noqa: E402
 
 METRIC = "BEM solves/s (mixed vs FP64 GPU at err<=1e-6)"
-# Roofline inputs from ncu counts of single launches (profiles/assemble_star3072.md, profiles/gemm_tc_star4096_64rhs.md):
-#  * k_assemble issues 2.547e9 warp instructions (sm__inst_executed.sum) on the star r = 1 + 0.3 cos 5t with
-#    N_e = 3072, over both the FP64 pipe (node geometry, phase reduction) and the FP32 pipe (double-float Bessel
-#    arithmetic); neither pipe alone binds, so its roofline is the issue rate: 4 warp instructions per clock per
-#    SM.  Scaled to other sizes by the number of element pairs.  Its DRAM traffic is set once the current kernel
-#    is captured (None: no capture of the current kernel).
-#  * the multi-RHS GEMM streams the FP16 split copy of A once per launch: 2 x 2 bytes per real entry; its DRAM
-#    traffic per launch at N_e = 4096 (None until captured), scaled by the matrix size.
+# Roofline inputs from ncu counts of single launches on the benchmarked star (r = 1 + 0.3 cos 5t, N_e = 4096,
+# 64 right-hand sides; profiles/assemble_star4096.md, profiles/gemm_tc_star4096_64rhs.md):
+#  * k_assemble issues 3.493e9 warp instructions (smsp__inst_executed.sum) over the FP64 pipe (per-pair
+#    geometry, phase k r) and the FP32 pipe (double-float node geometry, Bessel values and Gauss sums); neither
+#    pipe alone binds, so its roofline is the issue rate: 4 warp instructions per clock per SM.  Scaled to other
+#    sizes by the number of element pairs.  DRAM traffic 1.1905 GB written + 1.7 MB read per launch.
+#  * the multi-RHS GEMM streams the FP16 split copy of A once per launch: 2 x 2 bytes per real entry; DRAM
+#    traffic 564.5 MB read + 6.3 MB written per launch, scaled by the matrix size.
 #  * the refinement residual runs 16 FP32 operations per complex multiply-add on the FP32 pipe (four exact
 #    products summed with an offset accumulator, four operations each; the per-run offsets and the
 #    double-float fold are not counted), 128 operations per clock per SM; with the tensor-core product the
 #    small terms hi x_lo + lo x_hi are two FP16x3 GEMMs (11 kernels per residual, 12 with a K split).
-ASM_WARP_INST_N3072 = 2.546915828e9
-ASM_DRAM_BYTES_N3072 = None
-GEMM_DRAM_BYTES_N4096 = None
+ASM_WARP_INST_N4096 = 3.492758832e9
+ASM_DRAM_BYTES_N4096 = 1.1905e9 + 1.662e6
+GEMM_DRAM_BYTES_N4096 = 564.530944e6 + 6.303744e6
 RESID_FP32_OPS_PER_CMAC = 16
 RESID_LAUNCHES_TC = 11
 SM_COUNT, SM_CLOCK_HZ = 152, 2.07e9
@@ -519,14 +519,14 @@ def main():
     models = ("assemble", "matvec", "residual")
     ph, (ph_ms, ph_n) = max(((k, v) for k, v in prof.items() if k in models), key=lambda kv: kv[1][0])
     n2 = 2 * nel
-    scale = (nel / 3072.0) ** 2
+    scale = (nel / 4096.0) ** 2
     roof = {"kernel": ph, "launches": ph_n, "avg_launch_ms": ph_ms / ph_n, "traffic": None}
     if ph == "assemble":
         avg_s = ph_ms / ph_n / 1e3
-        ach = ASM_WARP_INST_N3072 * scale / avg_s / 1e9
+        ach = ASM_WARP_INST_N4096 * scale / avg_s / 1e9
         roof.update({"kernel": "k_assemble (issue-bound: FP64 geometry + double-float Bessel on FP32)", "bound": "alu",
                      "achieved": ach, "peak": ISSUE_PEAK_G, "unit": "G warp instructions/s", "frac": ach / ISSUE_PEAK_G,
-                     "traffic": ASM_DRAM_BYTES_N3072 * scale if ASM_DRAM_BYTES_N3072 else None,
+                     "traffic": ASM_DRAM_BYTES_N4096 * scale, "algorithmic_bytes_per_launch": 64 * nel * nel,
                      "peak_source": "derived: 152 SMs x 4 issue slots/clk x 2.07 GHz"})
     elif ph == "matvec":
         # one kernel per product: the GEMM (its stream-K reduction is timed as the "reduce" phase); the launch
@@ -537,7 +537,9 @@ def main():
         roof.update({"kernel": "k_gemm_tc (tcgen05 FP16x3 multi-RHS GEMM; its stream-K reduction is the reduce phase)",
                      "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
                      "peak_source": src, "algorithmic_bytes_per_launch": bytes_per,
-                     "traffic": GEMM_DRAM_BYTES_N4096 * (nel / 4096.0) ** 2 if GEMM_DRAM_BYTES_N4096 else None})
+                     "traffic": GEMM_DRAM_BYTES_N4096 * scale,
+                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch at N_e = 4096 "
+                                       "(profiles/gemm_tc_star4096_64rhs.md), scaled by the matrix size"})
     else:
         # launches per refinement residual: 11 (12 with a K split) with the tensor-core small terms
         n_gemm = max(1, ph_n // RESID_LAUNCHES_TC)
