@@ -503,29 +503,14 @@ BEM_HD F2 bem_asymp_coef(int which, int m) {
 }
 #undef BEM_ASYMP_TAB
 
-// Hankel's expansion as bessel01_asymp_f2, with 1/sqrt(x) and 1/x from X in double-float.
-BEM_HD void bessel01_asymp_f2x(double x, F2 X, Bessel01F2& b) {
+// Hankel's expansion as bessel01_asymp_f2, with 1/sqrt(x) and 1/x from X in double-float, given the phase
+// reduced by pi/2: x = quad pi/2 + R (mod 2 pi), |R| <= pi/4 (up to ~0.9 the sine and cosine sums below keep
+// their accuracy).
+BEM_HD void bessel01_asymp_f2r(F2 X, F2 R, int quad, Bessel01F2& b) {
   constexpr AsympCoefF2 C = make_asymp_coef_f2();
-  constexpr double kPio2_1 = 0x1.921fb54400000p+0;    // pi/2 = kPio2_1 + kPio2_2 + kPio2_3 + O(1e-37)
-  constexpr double kPio2_2 = 0x1.0b4611a600000p-34;
-  constexpr double kPio2_3 = 0x1.3198a2e037073p-69;
   const F2 rs = f2_rsqrt(X);
   const F2 Y = f2_mul(rs, rs);
   const F2 U = f2_mul(Y, Y);
-  // kq = x 2/pi rounded to an integer: adding 1.5 * 2^52 leaves it in the low bits of t (0 < x < 2^50)
-  const double t = fma(x, kTwoOverPi, 0x1.8p52);
-  const double kq = t - 0x1.8p52;
-  double r = fma(-kq, kPio2_1, x);
-  r = fma(-kq, kPio2_2, r);
-  r = fma(-kq, kPio2_3, r);
-#if defined(__CUDA_ARCH__)
-  const int quad = __double2loint(t) & 3;
-#else
-  unsigned long long tb;
-  memcpy(&tb, &t, sizeof tb);
-  const int quad = (int)(tb & 3u);
-#endif
-  const F2 R = f2_from_bits(r);
   const F2 R2 = f2_mul(R, R);
   F2 sp{C.sh[8], C.sl[8]};
 #pragma unroll
@@ -564,6 +549,36 @@ BEM_HD void bessel01_asymp_f2x(double x, F2 X, Bessel01F2& b) {
   b.y0 = f2_add(f2_mul(p0, ei), f2_mul(q0, er));
   b.j1 = f2_add(f2_mul(p1, ei), f2_mul(q1, er));
   b.y1 = f2_neg(f2_sub(f2_mul(p1, er), f2_mul(q1, ei)));
+}
+
+// pi/2 = kPio2_1 + kPio2_2 + kPio2_3 + O(1e-37) (three-part split for Cody-Waite reduction in FP64)
+constexpr double kPio2_1 = 0x1.921fb54400000p+0;
+constexpr double kPio2_2 = 0x1.0b4611a600000p-34;
+constexpr double kPio2_3 = 0x1.3198a2e037073p-69;
+
+// x = quad pi/2 + r with |r| <= pi/4 for 0 < x < 2^50 (Cody-Waite: kq = x 2/pi rounded to an integer by adding
+// 1.5 * 2^52, which leaves it in the low bits of t).
+BEM_HD double reduce_pio2(double x, int& quad) {
+  const double t = fma(x, kTwoOverPi, 0x1.8p52);
+  const double kq = t - 0x1.8p52;
+  double r = fma(-kq, kPio2_1, x);
+  r = fma(-kq, kPio2_2, r);
+  r = fma(-kq, kPio2_3, r);
+#if defined(__CUDA_ARCH__)
+  quad = __double2loint(t) & 3;
+#else
+  unsigned long long tb;
+  memcpy(&tb, &t, sizeof tb);
+  quad = (int)(tb & 3u);
+#endif
+  return r;
+}
+
+// Hankel's expansion with the phase reduced from the FP64 argument x.
+BEM_HD void bessel01_asymp_f2x(double x, F2 X, Bessel01F2& b) {
+  int quad;
+  const double r = reduce_pio2(x, quad);
+  bessel01_asymp_f2r(X, f2_from_bits(r), quad, b);
 }
 
 // ---- tabulated values and Taylor steps on 2 <= x < 128 -------------------------------------------------
@@ -673,21 +688,87 @@ BEM_HD void taylor_pair(float4 q0, float4 q1, float4 q2, float4 q3, F2 H, F2& ou
   out1 = f2_add(b0, f2_mul(s1, H));
 }
 
-BEM_HD void bessel01_taylor_f2(double x, F2 X, Bessel01F2& b) {
+BEM_HD int tab_index(float xh) {
 #if defined(__CUDA_ARCH__)
-  const int k = __float2int_rn((X.h - 2.f) * 32.f);
+  return __float2int_rn((xh - 2.f) * 32.f);
+#else
+  return (int)lrintf((xh - 2.f) * 32.f);
+#endif
+}
+
+// The Taylor sums at x = x_k + H from grid point k (|H| <= 1/64 up to rounding).
+BEM_HD void bessel01_taylor_f2h(int k, F2 H, Bessel01F2& b) {
+#if defined(__CUDA_ARCH__)
   const float4* ep = reinterpret_cast<const float4*>(&g_bessel_tab[k]);
   const float4 e0 = __ldg(ep), e1 = __ldg(ep + 1), e2 = __ldg(ep + 2), e3 = __ldg(ep + 3);
   const float4 e4 = __ldg(ep + 4), e5 = __ldg(ep + 5), e6 = __ldg(ep + 6), e7 = __ldg(ep + 7);
 #else
-  const int k = (int)lrintf((X.h - 2.f) * 32.f);
   const float4* ep = reinterpret_cast<const float4*>(&bessel_tab_host()[k]);
   const float4 e0 = ep[0], e1 = ep[1], e2 = ep[2], e3 = ep[3], e4 = ep[4], e5 = ep[5], e6 = ep[6], e7 = ep[7];
 #endif
-  const double h = x - (2.0 + k * kTabStep);   // exact: x and the grid point agree to within 1/64
-  const F2 H = f2_from_bits(h);
   taylor_pair(e0, e1, e2, e3, H, b.j0, b.j1);
   taylor_pair(e4, e5, e6, e7, H, b.y0, b.y1);
+}
+
+BEM_HD void bessel01_taylor_f2(double x, F2 X, Bessel01F2& b) {
+  const int k = tab_index(X.h);
+  const double h = x - (2.0 + k * kTabStep);   // exact: x and the grid point agree to within 1/64
+  bessel01_taylor_f2h(k, f2_from_bits(h), b);
+}
+
+// ---- arguments given as an FP64 base plus a small double-float offset -----------------------------------
+// The assembly evaluates x = k r at the Gauss nodes of element j as x = x_b + x_c: x_b = k |d| with d the
+// vector from element j's centre to the collocation point (FP64, once per element pair), and x_c = k c_m with
+// c_m = r_m - |d| (double-float, |c_m| <= h_j / 2).  The FP64 work (the table offset and the reduction by pi/2 of
+// x_b) is then done once per pair; per node only x_c is added in double-float, with an absolute error of
+// ~2^-46 |x_c|, so the argument keeps FP64's absolute accuracy.
+struct BesselArg {
+  double xb;   // x_b
+  int kb;      // grid point of x_b: x_kb = 2 + kb / 32
+  F2 hb;       // x_b - x_kb
+  int qb;      // x_b = qb pi/2 + rb (mod 2 pi)
+  F2 rb;
+};
+
+BEM_HD void bessel_arg_base(double xb, BesselArg& a) {
+  a.xb = xb;
+  // kb = (xb - 2) 32 rounded to an integer (magic-number rounding; |kb| < 2^31 for the arguments that occur)
+  const double t = fma(xb - 2.0, 32.0, 0x1.8p52);
+  const double kd = t - 0x1.8p52;
+#if defined(__CUDA_ARCH__)
+  a.kb = __double2loint(t);
+#else
+  a.kb = (int)kd;
+#endif
+  a.hb = f2_from_bits(xb - fma(kd, kTabStep, 2.0));   // exact: x_kb is a multiple of 1/32
+  a.rb = f2_from_bits(reduce_pio2(xb, a.qb));
+}
+
+// J0, Y0, J1, Y1 at x = a.xb + XC (XC small), X = x in double-float (branch choice and amplitudes).
+BEM_HD void bessel01_f2_at(const BesselArg& a, F2 XC, F2 X, Bessel01F2& b) {
+  if (X.h < (float)BEM_X_SERIES) {
+    bessel01_series_f2(a.xb + ((double)XC.h + (double)XC.l), b);
+  } else if (X.h < kTabXMax) {
+    // x - x_k = (x_b - x_kb) + x_c - (k - kb) / 32 (the last step by a two-sum: when the difference crosses a
+    // power of two its rounding is not exact)
+    const int k = tab_index(X.h);
+    const F2 Hp = f2_add(a.hb, XC);
+    const float dk = (float)(k - a.kb) * (float)kTabStep;
+    const F2 t = f2_two_sum(Hp.h, -dk);
+    const F2 H = f2_fast_two_sum(t.h, t.l + Hp.l);
+    bessel01_taylor_f2h(k, H, b);
+  } else {
+    // the phase x_b reduced by pi/2 plus x_c, reduced once more if x_c carried it past pi/4
+    F2 R = f2_add(a.rb, XC);
+    int quad = a.qb;
+    const float q = rintf(R.h * (float)kTwoOverPi);
+    if (q != 0.f) {
+      constexpr F2 kPio2F2{(float)kPio2_1, (float)(kPio2_1 - (double)(float)kPio2_1 + kPio2_2)};
+      R = f2_sub(R, f2_mulf(kPio2F2, q));
+      quad = (quad + (int)q) & 3;
+    }
+    bessel01_asymp_f2r(X, R, quad, b);
+  }
 }
 
 BEM_HD void bessel01_f2(double x, F2 X, Bessel01F2& b) {

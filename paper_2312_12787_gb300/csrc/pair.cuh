@@ -5,11 +5,11 @@
 // with gamma = alpha/eps) or one of the comparison forms.
 //
 // Precision plan (GB300 issues FP64 at 2 operations per clock per SM against 128 for FP32): FP64 forms, once
-// per element pair, the centre-to-centre vector and its projections (the cosines of nearly tangent pairs
-// cancel there, so they keep FP64's extra bits), and per Gauss node only the phase k r (an error of k r is an
-// error of the Hankel function's phase, and k r reaches ~100).  The node distances and direction cosines
-// relative to that vector, the Bessel values, Gauss weights, the four sums and their combination into entries
-// are double-float arithmetic on the FP32 pipe.  Accuracy against the FP64 definition: ~1e-14 of the largest
+// per element pair, the centre-to-centre vector, its length and projections (the cosines of nearly tangent
+// pairs cancel there, so they keep FP64's extra bits) and the FP64 part of each Bessel argument (an error of
+// k r is an error of the Hankel function's phase, and k r reaches ~100).  The node distances and direction
+// cosines relative to that vector, the node offsets of the Bessel arguments, the Bessel values, Gauss weights,
+// the four sums and their combination into entries are double-float arithmetic on the FP32 pipe.  Accuracy against the FP64 definition: ~1e-14 of the largest
 // entry of a block, a few 1e-12 relative on entries above 1e-6 of it.
 #pragma once
 
@@ -141,7 +141,8 @@ BEM_HD void assemble_pair_f2(const ElemDev& e, const DomTab& dom, const Quad& q,
   // The phase k r_m needs r_m to FP64's absolute accuracy (k r reaches ~100, and Gauss sums of oscillating
   // kernels can cancel by three decades): r_m = |d| + c_m with |d| in FP64 and the node's offset
   // c_m = (r_m^2 - |d|^2) / (r_m + |d|), |c_m| <= h_j / 2, in double-float, so the only error beyond FP64's is
-  // that of c_m, ~2^-46 h_j.
+  // that of c_m, ~2^-46 h_j.  The Bessel routines take k r_m as k |d| (FP64, reduced once per pair) plus k c_m
+  // (double-float), so no FP64 operation is left per node.
   const double dx = xi - mxj, dy = yi - myj;
   const double dd = dx * dx + dy * dy;
   const double dn = sqrt(dd);
@@ -168,6 +169,10 @@ BEM_HD void assemble_pair_f2(const ElemDev& e, const DomTab& dom, const Quad& q,
     DNI = f2_from_bits(dx * nxi + dy * nyi);
     TNI = f2_from_bits(txj * nxi + tyj * nyi);
   }
+  // the Bessel arguments' FP64 part k |d| (table offset and reduction by pi/2 once per pair and domain)
+  BesselArg arg0{}, arg1{};
+  if (sg[0] != 0.f) bessel_arg_base(kk[0] * dn, arg0);
+  if (sg[1] != 0.f) bessel_arg_base(kk[1] * dn, arg1);
 
   C2 sS[2], sD[2], sDs[2], sN[2];
 #pragma unroll
@@ -178,8 +183,7 @@ BEM_HD void assemble_pair_f2(const ElemDev& e, const DomTab& dom, const Quad& q,
     const F2 R2 = f2_add(DD, NUM);
     const F2 IR = f2_rsqrt(R2);
     const F2 R = f2_mul(R2, IR);
-    const F2 CM = f2_div(NUM, f2_add(R, DN));         // r_m - |d|
-    const double r = dn + ((double)CM.h + (double)CM.l);
+    const F2 CM = f2_div(NUM, f2_add(R, DN));         // c_m = r_m - |d|
     const F2 CJ = f2_mul(DNJ, IR);
     const F2 WD = f2_mul(HH, F2{q.wh[m], q.wl[m]});
     const F2 WCJ = f2_mul(WD, CJ);
@@ -195,14 +199,13 @@ BEM_HD void assemble_pair_f2(const ElemDev& e, const DomTab& dom, const Quad& q,
     // and two inlined copies overflow the instruction cache.
     Bessel01F2 bh[2];
     {
-      const double x0 = kk[0] * r, x1 = kk[1] * r;
-      const F2 X0 = f2_mul(K[0], R), X1 = f2_mul(K[1], R);
       Bessel01F2 b0{}, b1{};
 #pragma unroll 1
       for (int h = 0; h < 2; ++h) {
         if ((h ? sg[1] : sg[0]) == 0.f) continue;
+        const F2 Kh = h ? K[1] : K[0];
         Bessel01F2 b;
-        bessel01_f2(h ? x1 : x0, h ? X1 : X0, b);
+        bessel01_f2_at(h ? arg1 : arg0, f2_mul(Kh, CM), f2_mul(Kh, R), b);
         if (h) b1 = b; else b0 = b;
       }
       bh[0] = b0;

@@ -45,12 +45,14 @@ def values(tmp_path_factory):
         2.0 + np.arange(1, 4032, 7) / 32.0 + rng.uniform(-1 / 64, 1 / 64, 576),   # around the grid points
         2.0 + (np.arange(0, 4032, 11) + 0.5) / 32.0,                             # half-way between them
         [18.0, 25.0, 35.0, 128.0 - 2.0 ** -40, 128.0, 128.0 + 2.0 ** -40],
+        2.0 + (np.arange(2, 4032, 13) + 0.5) / 32.0 + 2.0 ** -33,                 # just past half-grid points
+        [8.328125 + 5.16e-11, 2.0 + 0.046875, 2.0 - 1e-9],
         np.geomspace(128.0, 2000.0, 120),
     ])
     out = subprocess.run([exe], input="\n".join(repr(float(v)) for v in xs), capture_output=True, text=True,
                          check=True).stdout
     got = np.array([[float.fromhex(t) for t in line.split()] for line in out.strip().splitlines()])
-    assert got.shape == (len(xs), 13) and np.array_equal(got[:, 0], xs)
+    assert got.shape == (len(xs), 21) and np.array_equal(got[:, 0], xs)
     mpmath.mp.dps = 30
     ref = np.array([[float(mpmath.besselj(0, x)), float(mpmath.bessely(0, x)), float(mpmath.besselj(1, x)),
                      float(mpmath.bessely(1, x))] for x in xs])
@@ -86,3 +88,15 @@ def test_table_builders_match_mpmath(values, lo, hi, bound):
     sel = (xs >= lo) & (xs < hi)
     err = _rel_err(got[sel, 9:13], ref[sel])
     assert sel.sum() > 30 and err.max() <= bound, (err.max(), xs[sel][np.argmax(err)])
+
+
+@pytest.mark.parametrize("lo,hi,bound", [(0.0, 2.0, 3e-15), (2.0, 128.0, 1e-14), (128.0, np.inf, 2.5e-14)])
+def test_split_argument_path_matches_mpmath(values, lo, hi, bound):
+    """The assembly passes x as an FP64 base (per element pair) plus a double-float offset (per node); with the
+    base and the node on different table grid points, near half-grid points and across the branch boundaries."""
+    xs, got, ref = values
+    sel = (xs >= lo) & (xs < hi)
+    for c0 in (13, 17):
+        err = _rel_err(got[sel, c0:c0 + 4], ref[sel])
+        assert sel.sum() > 30 and err.max() <= bound, (c0, err.max(), xs[sel][np.argmax(err)])
+

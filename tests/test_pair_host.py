@@ -88,6 +88,9 @@ CASES = [
     ("junction_mod", lambda: W.junction_disk(60, k=(5.0, 7.5, 10.0)), 4, "mod"),
     ("junction_beta1", lambda: W.junction_disk(60, k=(5.0, 7.5, 10.0)), 4, "beta1"),
     ("equal_density", lambda: W.circle_problem(29, 5.0, 7.5, eps_i=1.0), 4, "mod"),
+    ("concentric83_conv", lambda: W.concentric(41, 83, 2.0), 4, "conv"),
+    ("ellipse250_k40", lambda: W.Problem(k=[40.0, 70.0], eps=[1.0, (70.0 / 40.0) ** 2],
+                                         segments=[W.Segment(W.ellipse(250, 4.0), P=0, M=1, closed=True)]), 4, "mod"),
 ]
 
 
