@@ -224,7 +224,7 @@ typedef struct bem_batch bem_batch;
 BEM_API bem_status bem_batch_create(bem_batch** out, const bem_opts* opts, int max_slots, long long pool_unknowns);
 BEM_API void bem_batch_destroy(bem_batch* b);
 /* Admit n problems, each with one plane wave angles_host[i]: assemble all of them in one launch (tile height
- * chosen by timing 4, 8 and 16 on the first call), form right-hand sides and start their solves.
+ * chosen once per device by timing 4, 8 and 16 on about an eighth of the first admitted batch), form right-hand sides and start their solves.
  * slots_host[i] = slot or -1 when no slot or contiguous pool space was free (BEM_ENOMEM, others admitted).
  * Problems must be MIXED or MIXED_TC with the batch's quad_order and form. */
 BEM_API bem_status bem_batch_admit(bem_batch* b, int n, bem_problem* const* probs, const double* angles_host,
@@ -239,7 +239,10 @@ BEM_API bem_status bem_batch_query(bem_batch* b, int slot, int* state_host, int*
 BEM_API bem_status bem_batch_take(bem_batch* b, int slot, bem_c64* x_dev, void* stream);
 /* Largest contiguous run of free unknowns in the pools (admission check). */
 BEM_API long long bem_batch_free_units(const bem_batch* b);
-/* Admit, iterate to completion and take n problems (they must all fit). */
+/* Admit, iterate to completion and take n problems (they must all fit).  The iterations run as one graph
+ * launch: a conditional loop over a body of iterations and a refinement stage whose decisions (tolerance met,
+ * refinement limit, next inner tolerance) are taken on the device; where conditional graph nodes are
+ * unavailable, replays stepped by the host as in bem_batch_step.  Same results either way. */
 BEM_API bem_status bem_batch_solve_planewave(bem_batch* b, int n, bem_problem* const* probs, const double* angles_host,
                                              bem_c64* const* x_dev, int* iters_host, double* resid_host,
                                              void* stream);
