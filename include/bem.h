@@ -92,14 +92,20 @@ typedef struct {
                          automatic: 2 for the FP64 basis; for the FP32 inner solves of the mixed paths one
                          pass, plus a second one in the iterations where the first shrank the new vector below
                          a tenth of its length (selective reorthogonalisation) */
-  int matrix_free;    /* 1: never store A; every product recomputes the entries in FP64 (FP64 path only).
-                         For matrices that do not fit in device memory; each product costs one assembly. */
+  int matrix_free;    /* 1: do not store A; products recompute the entries (for matrices that do not fit in the
+                         device memory granted to the problem).  FP64: every product recomputes every entry (one
+                         assembly each).  MIXED: the leading element rows that fit in store_bytes are stored as
+                         complex FP32 (their hi part) and only the other rows are recomputed in the FP32 inner
+                         solves; the refinement residual recomputes every entry with FP64 sums (once per solve:
+                         later residuals are updated, see bem_solve).  Not for MIXED_TC. */
+  long long store_bytes;  /* matrix_free MIXED problems: device bytes for stored rows (each element takes two rows
+                         of 2N complex FP32 entries, 32 N bytes); 0 = none.  >= 0. */
 } bem_opts;
 
 typedef struct bem_problem bem_problem;
 
 /* Fill *o with the defaults: quad_order 4, MOD, FP64, max_iter 500, max_refine 6, tol 1e-10,
- * inner_tol 1e-5, orth_passes 0 (automatic), matrix_free 0. */
+ * inner_tol 1e-5, orth_passes 0 (automatic), matrix_free 0, store_bytes 0. */
 BEM_API void bem_default_opts(bem_opts* o);
 
 /* Create an empty problem.  *out receives a library-owned handle (free with bem_problem_destroy).

@@ -42,7 +42,8 @@ class BemError(RuntimeError):
 class bem_opts(ctypes.Structure):
     _fields_ = [("quad_order", ctypes.c_int), ("form", ctypes.c_int), ("prec", ctypes.c_int),
                 ("max_iter", ctypes.c_int), ("max_refine", ctypes.c_int), ("tol", ctypes.c_double),
-                ("inner_tol", ctypes.c_double), ("orth_passes", ctypes.c_int), ("matrix_free", ctypes.c_int)]
+                ("inner_tol", ctypes.c_double), ("orth_passes", ctypes.c_int), ("matrix_free", ctypes.c_int),
+                ("store_bytes", ctypes.c_longlong)]
 
 
 _lib = None
@@ -144,7 +145,7 @@ def bem_default_opts() -> bem_opts:
 
 
 def make_opts(quad_order=4, form="mod", prec="fp64", max_iter=500, max_refine=6, tol=1e-10, inner_tol=1e-5,
-              orth_passes=0, matrix_free=0):
+              orth_passes=0, matrix_free=0, store_bytes=0):
     o = bem_default_opts()
     o.quad_order = quad_order
     o.form = FORMS[form] if isinstance(form, str) else form
@@ -155,6 +156,7 @@ def make_opts(quad_order=4, form="mod", prec="fp64", max_iter=500, max_refine=6,
     o.inner_tol = inner_tol
     o.orth_passes = orth_passes
     o.matrix_free = int(matrix_free)
+    o.store_bytes = int(store_bytes)
     return o
 
 

@@ -75,7 +75,7 @@ bool valid_opts(const bem_opts* o) {
          o->prec <= 2 && o->max_iter >= 1 && o->max_iter <= 1000 && o->max_refine >= 1 && o->max_refine <= 100 &&
          o->tol > 0 && std::isfinite(o->tol) && o->inner_tol > 0 && std::isfinite(o->inner_tol) &&
          (o->orth_passes >= 0 && o->orth_passes <= 2) && (o->matrix_free == 0 || o->matrix_free == 1) &&
-         !(o->matrix_free && o->prec != BEM_PREC_FP64);
+         !(o->matrix_free && o->prec == BEM_PREC_MIXED_TC) && o->store_bytes >= 0;
 }
 
 }  // namespace
@@ -95,6 +95,11 @@ struct bem_problem {
   void* d_A = nullptr;
   void* d_Alo = nullptr;
   size_t A_cap = 0;       // bytes of d_A (and d_Alo when mixed)
+  // matrix-free mixed problems: the leading element rows that fit in opts.store_bytes, stored as complex FP32
+  // (hi) in a compact block (rows i, then rows N + i, of the stored elements i < Es); the rest is recomputed
+  float2* d_Hs = nullptr;
+  size_t Hs_cap = 0;
+  int Es = 0;
   void* d_A16 = nullptr;  // FP16 split copy of the complex FP32 matrix for the tensor-core product
   size_t A16_cap = 0;
   void* d_Alo16 = nullptr;  // the same of the remainder lo (the residual's small terms)
@@ -296,13 +301,49 @@ size_t matrix_bytes(int n, bool mixed) {
   return mixed ? 2 * nn * sizeof(float2) : nn * sizeof(double2);
 }
 
+// Element rows of a matrix-free mixed problem that fit in opts.store_bytes (two rows of 2N complex FP32 each).
+int stored_element_rows(const bem_problem* p) {
+  const size_t per = (size_t)2 * 2 * p->n * sizeof(float2);
+  const size_t rows = (size_t)p->o.store_bytes / per;
+  return (int)std::min<size_t>(rows, (size_t)p->n);
+}
+
+// y = A_hi x (complex FP32, one column) of a matrix-free mixed problem: the stored rows by the FP32 GEMV, the
+// others recomputed (FP64 sums, FP32 result).
+cudaError_t matvec_partial_f32(bem_problem* p, const float2* x, float2* y, cudaStream_t s, const int* gate) {
+  const int n = p->n, n2 = 2 * n, Es = p->Es;
+  cudaError_t e = cudaSuccess;
+  if (Es > 0) {
+    e = launch_matvec_c32_rows(p->d_Hs, n2, n2, Es, 0, 1, x, y, s);
+    if (e == cudaSuccess) e = launch_matvec_c32_rows(p->d_Hs + (size_t)Es * n2, n2, n2, Es, n, 1, x, y, s);
+  }
+  if (e == cudaSuccess)
+    e = launch_matvec_free_f32(p->elem(), n, p->dom, make_quad(p->o.quad_order), p->o.form, Es, x, y, s, gate);
+  return e;
+}
+
 bem_status assemble_impl(bem_problem* p, cudaStream_t s, bool force = false) {
   bem_status st = check_ready(p);
   if (st != BEM_OK) return st;
   st = upload_geometry(p, s);
   if (st != BEM_OK) return st;
   const bool mixed = p->mixed();
-  if (p->o.matrix_free) {      // nothing to store: products recompute the entries
+  if (p->o.matrix_free) {      // products recompute the entries (mixed problems may keep a stored part)
+    if (!force && !p->mat_dirty) return BEM_OK;
+    p->Es = mixed ? stored_element_rows(p) : 0;
+    if (p->Es > 0) {
+      const size_t need = (size_t)2 * p->Es * 2 * p->n * sizeof(float2);
+      if (need > p->Hs_cap) {
+        if (p->d_Hs) dev_free(p->d_Hs);
+        p->d_Hs = nullptr;
+        p->Hs_cap = 0;
+        if (dev_malloc(&p->d_Hs, need) != cudaSuccess) return fail(BEM_ENOMEM, "stored rows: %zu bytes failed", need);
+        p->Hs_cap = need;
+      }
+      Phase ph(p, BEM_PH_ASSEMBLE, s, 1);
+      CU(launch_assemble_rows(p->elem(), p->n, p->dom, make_quad(p->o.quad_order), p->o.form, p->Es, p->d_Hs,
+                              (size_t)2 * p->n, s));
+    }
     p->mat_dirty = false;
     return BEM_OK;
   }
@@ -525,7 +566,12 @@ bem_status gmres_run(bem_problem* p, Solver& sv, const double2* r0, double2* x, 
                            gate, 2);
     } else {
       Phase ph(p, BEM_PH_MATVEC, s, 1);
-      if (p->o.matrix_free) {
+      if (p->o.matrix_free && fp32) {   // stored rows and recomputed rows, column by column
+        e = cudaSuccess;
+        for (int r = 0; r < nrhs && e == cudaSuccess; ++r)
+          e = matvec_partial_f32(p, static_cast<const float2*>(Vj) + (size_t)r * n2,
+                                 static_cast<float2*>(st.W) + (size_t)r * n2, s, gate);
+      } else if (p->o.matrix_free) {
         e = launch_matvec_free(p->elem(), p->n, p->dom, make_quad(p->o.quad_order), p->o.form, nrhs,
                                static_cast<const double2*>(Vj), static_cast<double2*>(st.W), s, gate);
       } else if (!fp32) {
@@ -719,6 +765,12 @@ bem_status column_norms(bem_problem* p, Solver& sv, const double2* v, int nrhs, 
 bem_status residual_mixed(bem_problem* p, Solver& sv, int nrhs, const double2* x, const double2* b, double2* r,
                           cudaStream_t s) {
   const int n2 = 2 * p->n;
+  if (p->o.matrix_free) {   // every entry recomputed, FP64 sums: r = b - A x
+    Phase ph(p, BEM_PH_RESIDUAL, s, nrhs + 1);
+    CU(launch_matvec_free(p->elem(), p->n, p->dom, make_quad(p->o.quad_order), p->o.form, nrhs, x, r, s));
+    CU(launch_axpby_neg(b, r, (size_t)nrhs * n2, s));
+    return BEM_OK;
+  }
   const float2* A = static_cast<const float2*>(p->d_A);
   const float2* Alo = static_cast<const float2*>(p->d_Alo);
   if (p->o.prec == BEM_PREC_MIXED_TC && nrhs > 1 && matvec_tc_supported(n2, nrhs) &&
@@ -759,6 +811,8 @@ bem_status residual_update(bem_problem* p, Solver& sv, int nrhs, double2* r, cud
       CU(matvec_tc_clear_error(sv.tcws, n2, nrhs, s));
       CU(launch_matvec_tc(p->d_A16, n2, nrhs, d, y, sv.tcws, sv.tcws_bytes, s));
       CU(cudaMemcpyAsync(&tc_err, matvec_tc_error_word(sv.tcws, n2, nrhs), sizeof(int), cudaMemcpyDeviceToHost, s));
+    } else if (p->o.matrix_free) {
+      for (int c = 0; c < nrhs; ++c) CU(matvec_partial_f32(p, d + (size_t)c * n2, y + (size_t)c * n2, s, nullptr));
     } else {
       CU(launch_matvec_c32(static_cast<const float2*>(p->d_A), n2, n2, nrhs, d, y, nullptr, s));
     }
@@ -915,6 +969,7 @@ DomTab problem_dom(bem_problem* p) { return p->dom; }
 bem_status problem_prepare_batched(bem_problem* p, cudaStream_t s, AsmJob* job, bem_opts* opts) {
   if (!p) return fail(BEM_EINVAL, "null problem");
   if (!p->mixed()) return fail(BEM_EINVAL, "batched solves need a mixed-precision problem");
+  if (p->o.matrix_free) return fail(BEM_EINVAL, "batched solves store every matrix (no matrix-free problems)");
   bem_status st = check_ready(p);
   if (st != BEM_OK) return st;
   st = upload_geometry(p, s);
@@ -961,6 +1016,7 @@ BEM_API void bem_default_opts(bem_opts* o) {
   o->inner_tol = 1e-5;
   o->orth_passes = 0;
   o->matrix_free = 0;
+  o->store_bytes = 0;
 }
 
 BEM_API bem_status bem_problem_create(bem_problem** out, const bem_opts* opts) {
@@ -982,6 +1038,7 @@ BEM_API void bem_problem_destroy(bem_problem* p) {
   if (p->d_pm) dev_free(p->d_pm);
   if (p->d_A) dev_free(p->d_A);
   if (p->d_Alo) dev_free(p->d_Alo);
+  if (p->d_Hs) dev_free(p->d_Hs);
   if (p->d_A16) dev_free(p->d_A16);
   if (p->d_Alo16) dev_free(p->d_Alo16);
   if (p->ws) dev_free(p->ws);
@@ -1002,7 +1059,9 @@ BEM_API void bem_problem_destroy(bem_problem* p) {
 
 BEM_API bem_status bem_set_opts(bem_problem* p, const bem_opts* opts) {
   if (!p || !valid_opts(opts)) return fail(BEM_EINVAL, "invalid options");
-  if (opts->quad_order != p->o.quad_order || opts->form != p->o.form || opts->prec != p->o.prec) p->mat_dirty = true;
+  if (opts->quad_order != p->o.quad_order || opts->form != p->o.form || opts->prec != p->o.prec ||
+      opts->matrix_free != p->o.matrix_free || opts->store_bytes != p->o.store_bytes)
+    p->mat_dirty = true;
   p->o = *opts;
   return BEM_OK;
 }
@@ -1061,7 +1120,8 @@ BEM_API size_t bem_footprint_bytes(const bem_problem* p, int n_rhs) {
   const bool mixed = p->o.prec != BEM_PREC_FP64;
   const size_t a16 =
       (!p->o.matrix_free && p->o.prec == BEM_PREC_MIXED_TC && n_rhs > 1) ? 2 * matvec_tc_a16_bytes(2 * p->n) : 0;
-  return (p->o.matrix_free ? 0 : matrix_bytes(p->n, mixed)) + a16 + krylov_bytes(2 * p->n, n_rhs, p->o.max_iter, mixed) +
+  const size_t stored = mixed ? (size_t)2 * stored_element_rows(p) * 2 * p->n * sizeof(float2) : 0;
+  return (p->o.matrix_free ? stored : matrix_bytes(p->n, mixed)) + a16 + krylov_bytes(2 * p->n, n_rhs, p->o.max_iter, mixed) +
          (size_t)12 * p->n * 8;
 }
 

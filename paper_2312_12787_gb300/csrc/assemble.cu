@@ -56,10 +56,12 @@ __global__ void k_elements(ElemDev e, int n) {
 
 // Mixed store: the double-float entry (hi, lo) is already the complex FP32 rounding of the entry and the
 // FP32 rounding of its remainder; the FP64 store adds the two parts.
+// lower: the row of the Burton-Miller half of element i is lower + i (n for the whole matrix; the number of
+// stored element rows for a compact block).  With Aloout null the remainder is not stored.
 template <int MIXED>
 __device__ __forceinline__ void store_pair(int n, int i, int j, const C2 (&out)[2][2], void* Aout, void* Aloout,
-                                           size_t lda) {
-  const size_t r0 = (size_t)i * lda, r1 = (size_t)(n + i) * lda;
+                                           size_t lda, int lower) {
+  const size_t r0 = (size_t)i * lda, r1 = (size_t)(lower + i) * lda;
   const size_t idx[4] = {r0 + j, r0 + n + j, r1 + j, r1 + n + j};
   const C2 v[4] = {out[0][0], out[0][1], out[1][0], out[1][1]};
   if (MIXED) {
@@ -68,7 +70,7 @@ __device__ __forceinline__ void store_pair(int n, int i, int j, const C2 (&out)[
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
       A[idx[t]] = make_float2(v[t].x.h, v[t].y.h);
-      L[idx[t]] = make_float2(v[t].x.l, v[t].y.l);
+      if (L) L[idx[t]] = make_float2(v[t].x.l, v[t].y.l);
     }
   } else {
     double2* A = static_cast<double2*>(Aout);
@@ -79,33 +81,45 @@ __device__ __forceinline__ void store_pair(int n, int i, int j, const C2 (&out)[
 
 // Three CTAs per SM (80 registers, some spills): the kernel is bound by dependent FP64 and double-float
 // latencies, and the extra resident warps hide more of them than the spills cost (5 % faster than two).
+// Element rows i < rows (rows = n: the whole matrix; fewer: the stored part of a partly recomputed matrix, rows
+// i and lower + i).
 template <int MIXED>
 __global__ void __launch_bounds__(256, 3) k_assemble(ElemDev e, int n, DomTab dom, Quad q, int form, void* Aout,
-                                                   void* Aloout, size_t lda) {
+                                                   void* Aloout, size_t lda, int rows, int lower) {
   const int j = blockIdx.x * 32 + threadIdx.x;
   const int i = blockIdx.y * 8 + threadIdx.y;
-  if (i >= n || j >= n) return;
+  if (i >= rows || j >= n) return;
   C2 out[2][2];
   assemble_pair_f2(e, dom, q, form, i, j, out);
-  store_pair<MIXED>(n, i, j, out, Aout, Aloout, lda);
+  store_pair<MIXED>(n, i, j, out, Aout, Aloout, lda, lower);
 }
 
 // Matrix-free product y = A x (no stored matrix): each block owns 8 element rows (16 matrix rows i and
 // N + i); the 32 lanes of a warp stride over the element columns j, evaluate the four entries of (i, j) with
 // the assembly's own code and accumulate; a warp reduction gives the two row sums (FP64 products and sums).
 // Three CTAs per SM, as for k_assemble.
-__global__ void __launch_bounds__(256, 3) k_matvec_free(ElemDev e, int n, DomTab dom, Quad q, int form,
-                                                      const double2* __restrict__ x, double2* __restrict__ y,
-                                                      const int* gate) {
+template <typename T> __device__ __forceinline__ double2 ld_c(const T* p);
+template <> __device__ __forceinline__ double2 ld_c<double2>(const double2* p) { return *p; }
+template <> __device__ __forceinline__ double2 ld_c<float2>(const float2* p) {
+  const float2 v = *p;
+  return make_double2(v.x, v.y);
+}
+__device__ __forceinline__ void st_c(double2* p, double2 v) { *p = v; }
+__device__ __forceinline__ void st_c(float2* p, double2 v) { *p = make_float2((float)v.x, (float)v.y); }
+
+// Element rows i0 .. n-1 (all of them for i0 = 0).
+template <typename T>
+__global__ void __launch_bounds__(256, 3) k_matvec_free(ElemDev e, int n, DomTab dom, Quad q, int form, int i0,
+                                                      const T* __restrict__ x, T* __restrict__ y, const int* gate) {
   if (gate && *gate == 0) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int i = blockIdx.x * 8 + warp;
+  const int i = i0 + blockIdx.x * 8 + warp;
   if (i >= n) return;
   double2 up = make_double2(0, 0), lo = make_double2(0, 0);
   for (int j = lane; j < n; j += 32) {
     C2 o2[2][2];
     assemble_pair_f2(e, dom, q, form, i, j, o2);
-    const double2 xu = x[j], xw = x[n + j];
+    const double2 xu = ld_c(x + j), xw = ld_c(x + n + j);
     up = cadd(up, cadd(cmul(c2_to(o2[0][0]), xu), cmul(c2_to(o2[0][1]), xw)));
     lo = cadd(lo, cadd(cmul(c2_to(o2[1][0]), xu), cmul(c2_to(o2[1][1]), xw)));
   }
@@ -117,8 +131,8 @@ __global__ void __launch_bounds__(256, 3) k_matvec_free(ElemDev e, int n, DomTab
     lo.y += __shfl_xor_sync(0xffffffffu, lo.y, o);
   }
   if (lane == 0) {
-    y[i] = up;
-    y[n + i] = lo;
+    st_c(y + i, up);
+    st_c(y + n + i, lo);
   }
 }
 
@@ -144,7 +158,7 @@ __global__ void __launch_bounds__(32 * TY, 768 / (32 * TY)) k_assemble_batched(c
   if (i >= jb.n || j >= jb.n) return;
   C2 out[2][2];
   assemble_pair_f2(jb.e, jb.dom, q, form, i, j, out);
-  store_pair<MIXED>(jb.n, i, j, out, jb.A, jb.Alo, (size_t)2 * jb.n);
+  store_pair<MIXED>(jb.n, i, j, out, jb.A, jb.Alo, (size_t)2 * jb.n, jb.n);
 }
 
 // b[r][half*N + i] for plane wave r (eq. naive_bie right-hand side, placed like the matrix rows).
@@ -323,8 +337,19 @@ cudaError_t launch_assemble(const ElemDev& e, int n, const DomTab& dom, const Qu
   if (const cudaError_t te = ensure_bessel_table(); te != cudaSuccess) return te;
   dim3 blk(32, 8);
   dim3 grd((n + 31) / 32, (n + 7) / 8);
-  if (store_mixed) k_assemble<1><<<grd, blk, 0, s>>>(e, n, dom, q, form, A, Alo, lda);
-  else k_assemble<0><<<grd, blk, 0, s>>>(e, n, dom, q, form, A, Alo, lda);
+  if (store_mixed) k_assemble<1><<<grd, blk, 0, s>>>(e, n, dom, q, form, A, Alo, lda, n, n);
+  else k_assemble<0><<<grd, blk, 0, s>>>(e, n, dom, q, form, A, Alo, lda, n, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_assemble_rows(const ElemDev& e, int n, const DomTab& dom, const Quad& q, int form, int rows,
+                                 float2* H, size_t lda, cudaStream_t s) {
+  if (rows <= 0) return cudaSuccess;
+  if (rows > n) return cudaErrorInvalidValue;
+  if (const cudaError_t te = ensure_bessel_table(); te != cudaSuccess) return te;
+  dim3 blk(32, 8);
+  dim3 grd((n + 31) / 32, (rows + 7) / 8);
+  k_assemble<1><<<grd, blk, 0, s>>>(e, n, dom, q, form, H, nullptr, lda, rows, rows);
   return cudaGetLastError();
 }
 
@@ -332,8 +357,17 @@ cudaError_t launch_matvec_free(const ElemDev& e, int n, const DomTab& dom, const
                                const double2* x, double2* y, cudaStream_t s, const int* gate) {
   if (const cudaError_t te = ensure_bessel_table(); te != cudaSuccess) return te;
   for (int r = 0; r < nrhs; ++r)
-    k_matvec_free<<<(n + 7) / 8, 256, 0, s>>>(e, n, dom, q, form, x + (size_t)r * 2 * n, y + (size_t)r * 2 * n,
-                                              gate);
+    k_matvec_free<double2><<<(n + 7) / 8, 256, 0, s>>>(e, n, dom, q, form, 0, x + (size_t)r * 2 * n,
+                                                       y + (size_t)r * 2 * n, gate);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_matvec_free_f32(const ElemDev& e, int n, const DomTab& dom, const Quad& q, int form, int i0,
+                                   const float2* x, float2* y, cudaStream_t s, const int* gate) {
+  if (i0 >= n) return cudaSuccess;
+  if (i0 < 0) return cudaErrorInvalidValue;
+  if (const cudaError_t te = ensure_bessel_table(); te != cudaSuccess) return te;
+  k_matvec_free<float2><<<(n - i0 + 7) / 8, 256, 0, s>>>(e, n, dom, q, form, i0, x, y, gate);
   return cudaGetLastError();
 }
 

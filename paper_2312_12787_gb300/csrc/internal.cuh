@@ -111,6 +111,14 @@ cudaError_t launch_assemble(const ElemDev& e, int n, const DomTab& dom, const Qu
 // converged; the solver queues several iterations ahead of its convergence check).
 cudaError_t launch_matvec_free(const ElemDev& e, int n, const DomTab& dom, const Quad& q, int form, int nrhs,
                                const double2* x, double2* y, cudaStream_t s, const int* gate = nullptr);
+// The same for complex FP32 x and y (FP64 sums inside) and only the element rows i0 .. n-1 (matrix rows i and
+// n + i): the recomputed part of a partly stored matrix in the FP32 inner solves.
+cudaError_t launch_matvec_free_f32(const ElemDev& e, int n, const DomTab& dom, const Quad& q, int form, int i0,
+                                   const float2* x, float2* y, cudaStream_t s, const int* gate = nullptr);
+// Element rows i < rows of the matrix as complex FP32 (hi only) into a compact block: row i at H + i * lda,
+// row n + i at H + (rows + i) * lda.
+cudaError_t launch_assemble_rows(const ElemDev& e, int n, const DomTab& dom, const Quad& q, int form, int rows,
+                                 float2* H, size_t lda, cudaStream_t s);
 // Tiles of a problem with n elements for tile height ty (4, 8 or 16 rows of element pairs x 32 columns).
 long long assemble_batched_tiles(int n, int ty);
 cudaError_t launch_assemble_batched(const AsmJob* jobs_dev, int njobs, const long long* tile_prefix_dev,
@@ -134,6 +142,10 @@ cudaError_t launch_matvec_c64(const double2* A, size_t lda, int n, int nrhs, con
 // y[r] = A x[r] with A complex FP32 (hi only), x and y complex FP32.
 cudaError_t launch_matvec_c32(const float2* A, size_t lda, int n, int nrhs, const float2* x, float2* y,
                               const int* active, cudaStream_t s, const int* gate = nullptr);
+// The same product for `rows` consecutive stored rows starting at A, written to rows yoff .. yoff + rows - 1 of y
+// (columns of n entries; nrhs 1 or 2).
+cudaError_t launch_matvec_c32_rows(const float2* A, size_t lda, int n, int rows, int yoff, int nrhs, const float2* x,
+                                   float2* y, cudaStream_t s);
 // r = b - (hi + lo) x, with FP64 x, b, r (refinement residual) in double-float arithmetic; ws must hold
 // 2 * nrhs * n float2 (ws_bytes: its size, 0 = exactly that).  The _f64 variant computes the same in FP64 arithmetic.
 // With ws_bytes beyond the x split, the tiled product may split K over CTAs and keep FP64 partials there.

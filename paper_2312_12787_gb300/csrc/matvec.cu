@@ -79,8 +79,10 @@ __global__ void __launch_bounds__(256) k_gemv_f64(ALoad A, size_t lda, int n, co
 // FP64 every 16 steps; the warp sums go to shared memory and are combined in a fixed order (deterministic)
 // once per group of kGvGroup rows.  n must be even (it is: n = 2N); inactive columns are skipped.
 constexpr int kGvGroup = 16;
+// rows (<= n) rows of A from A onwards, written to y at rows yoff .. yoff + rows - 1 (the whole matrix: rows = n,
+// yoff = 0; a stored part of a partly recomputed matrix otherwise).
 template <int NR>
-__global__ void __launch_bounds__(256) k_gemv_c32(const float2* __restrict__ A, size_t lda, int n,
+__global__ void __launch_bounds__(256) k_gemv_c32(const float2* __restrict__ A, size_t lda, int n, int rows, int yoff,
                                                    const float2* __restrict__ x, float2* __restrict__ y,
                                                    const int* __restrict__ active) {
   __shared__ double2 part[kGvGroup][8][NR];
@@ -95,9 +97,9 @@ __global__ void __launch_bounds__(256) k_gemv_c32(const float2* __restrict__ A, 
   if (!any) return;
   const int n2 = n >> 1;   // float4 per row
   const int G = gridDim.x;
-  for (int base = blockIdx.x; base < n; base += kGvGroup * G) {
+  for (int base = blockIdx.x; base < rows; base += kGvGroup * G) {
     int k = 0;
-    for (; k < kGvGroup && base + k * G < n; ++k) {
+    for (; k < kGvGroup && base + k * G < rows; ++k) {
       const int r = base + k * G;
       const float4* row = reinterpret_cast<const float4*>(A + (size_t)r * lda);
       double ax[NR], ay[NR];
@@ -139,7 +141,7 @@ __global__ void __launch_bounds__(256) k_gemv_c32(const float2* __restrict__ A, 
         double2 acc = part[kk][0][s];
 #pragma unroll
         for (int w = 1; w < 8; ++w) acc = cadd(acc, part[kk][w][s]);
-        y[(size_t)s * n + base + kk * G] = make_float2((float)acc.x, (float)acc.y);
+        y[(size_t)s * n + yoff + base + kk * G] = make_float2((float)acc.x, (float)acc.y);
       }
     }
     __syncthreads();
@@ -643,13 +645,24 @@ cudaError_t launch_matvec_c32(const float2* A, size_t lda, int n, int nrhs, cons
     const int grd = std::min(n, gemv_c32_grid(nrhs));
     if (grd <= 0) return cudaErrorInvalidValue;
     if (nrhs == 1)
-      k_gemv_c32<1><<<grd, 256, 0, s>>>(A, lda, n, x, y, active);
+      k_gemv_c32<1><<<grd, 256, 0, s>>>(A, lda, n, n, 0, x, y, active);
     else
-      k_gemv_c32<2><<<grd, 256, 0, s>>>(A, lda, n, x, y, active);
+      k_gemv_c32<2><<<grd, 256, 0, s>>>(A, lda, n, n, 0, x, y, active);
   } else {
     dim3 grd((n + 63) / 64, (nrhs + 63) / 64);
     k_gemm_c32<<<grd, 256, 0, s>>>(A, lda, n, nrhs, x, y, gate);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_matvec_c32_rows(const float2* A, size_t lda, int n, int rows, int yoff, int nrhs, const float2* x,
+                                   float2* y, cudaStream_t s) {
+  if (rows <= 0) return cudaSuccess;
+  if (nrhs < 1 || nrhs > 2 || rows > n || yoff < 0 || yoff + rows > n) return cudaErrorInvalidValue;
+  const int grd = std::min(rows, gemv_c32_grid(nrhs));
+  if (grd <= 0) return cudaErrorInvalidValue;
+  if (nrhs == 1) k_gemv_c32<1><<<grd, 256, 0, s>>>(A, lda, n, rows, yoff, x, y, nullptr);
+  else k_gemv_c32<2><<<grd, 256, 0, s>>>(A, lda, n, rows, yoff, x, y, nullptr);
   return cudaGetLastError();
 }
 

@@ -8,10 +8,12 @@ then iterate together with the ones already on the device; finished solves are t
 their slot, pool space and matrix.  Latency is measured from arrival to the moment the solution is back in a
 device buffer.  All compute runs in libbem; this module only schedules.
 
-Requests whose complex-FP32 matrix would exceed `matrix_free_bytes` (8e9 by default: N_e above ~15.8k) store no
-matrix at all: a worker thread solves them one at a time with the matrix-free FP64 path (every product
-recomputes the entries) on a CUDA stream of its own, while the batch engine keeps iterating the others.  Their
-HBM footprint (the FP64 Krylov basis) is charged to the budget while they run.
+Requests whose complex-FP32 matrix would exceed `matrix_free_bytes` (8e9 by default: N_e above ~15.8k) are
+recomputed above that limit: a worker thread solves them one at a time with the matrix-free mixed path, which keeps
+the leading rows that fit in `matrix_free_bytes` as complex FP32 and recomputes the others in every inner product
+(the refinement residual recomputes every entry with FP64 sums), on a CUDA stream of its own, while the batch
+engine keeps iterating the others.  Their HBM footprint (stored rows and Krylov basis) is charged to the budget
+while they run.
 """
 from __future__ import annotations
 
@@ -57,10 +59,13 @@ def c32_matrix_bytes(wp) -> int:
     return 8 * n2 * n2
 
 
-def mf_footprint_bytes(wp, max_iter) -> int:
-    """Device bytes of a matrix-free FP64 solve: the Krylov basis and the Hessenberg data dominate."""
+def mf_footprint_bytes(wp, max_iter, store_bytes=0) -> int:
+    """Device bytes of a matrix-free mixed solve: the stored rows (whole elements, two rows of 2N complex FP32
+    each, within store_bytes), the FP32 Krylov basis and the Hessenberg data."""
     n2 = wp.n_unknowns
-    return 16 * (max_iter + 1) * n2 + 16 * max_iter * (max_iter + 1) + 64 * n2
+    per_elem = 2 * n2 * 8
+    stored = min(wp.n_elem, int(store_bytes) // per_elem) * per_elem
+    return stored + 8 * (max_iter + 1) * n2 + 16 * max_iter * (max_iter + 1) + 64 * n2
 
 
 class Server:
@@ -76,7 +81,8 @@ class Server:
         self.resident = {}          # slot -> (request id, problem, matrix bytes)
         self.used_bytes = 0
         self.mf_limit = matrix_free_bytes
-        self.mf_opts = dict(prec="fp64", matrix_free=1, tol=tol, max_iter=mf_max_iter, quad_order=quad_order)
+        self.mf_opts = dict(prec="mixed", matrix_free=1, store_bytes=int(matrix_free_bytes), tol=tol,
+                            max_iter=mf_max_iter, quad_order=quad_order, inner_tol=inner_tol, orth_passes=orth_passes)
         self._mf_in = queue.Queue()
         self._mf_out = queue.Queue()
         self._mf_thread = None
@@ -155,7 +161,7 @@ class Server:
                 rid = waiting[0]
                 wp = requests[rid][1]
                 if c32_matrix_bytes(wp) > self.mf_limit:
-                    need = mf_footprint_bytes(wp, self.mf_opts["max_iter"])
+                    need = mf_footprint_bytes(wp, self.mf_opts["max_iter"], self.mf_opts["store_bytes"])
                     if self.used_bytes + need > self.budget:
                         st.deferred += 1
                         break

@@ -7,6 +7,8 @@ import subprocess
 import numpy as np
 import pytest
 
+import workloads as W
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
@@ -75,6 +77,23 @@ def test_host_validation(lib):
     assert p.bem_num_elements() == 3 and p.bem_num_unknowns() == 6
     assert p.bem_footprint_bytes(1) > 6 * 6 * 16
     p.close()
+    # matrix-free: FP64 and MIXED (with stored rows) are valid, MIXED_TC is not; stored bytes must be >= 0
+    with pytest.raises(lib.BemError):
+        P(prec="mixed_tc", matrix_free=1)
+    with pytest.raises(lib.BemError):
+        P(prec="mixed", matrix_free=1, store_bytes=-1)
+    for kw in (dict(prec="fp64", matrix_free=1), dict(prec="mixed", matrix_free=1, store_bytes=1 << 20)):
+        q = P(**kw)
+        q.bem_set_domains([5.0, 7.5], [1.0, 2.25])
+        q.bem_add_segment(W.circle(40), 0, 1, True)
+        if kw["prec"] == "mixed":
+            # stored element rows: 1 MiB / (2 rows x 80 complex FP32) = 819 >= 40, so the whole matrix is kept
+            full = P(prec="mixed")
+            full.bem_set_domains([5.0, 7.5], [1.0, 2.25])
+            full.bem_add_segment(W.circle(40), 0, 1, True)
+            assert q.bem_footprint_bytes(1) < full.bem_footprint_bytes(1)
+            full.close()
+        q.close()
 
 
 def test_workload_generators_shapes():

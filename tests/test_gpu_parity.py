@@ -403,8 +403,8 @@ def test_matrix_free_matvec_residual_and_solve(B, torch):
         pf.bem_get_matrix(torch.empty((n2, n2), dtype=torch.complex128, device="cuda"))
     pf.close()
     ps.close()
-    with pytest.raises(B.BemError):                       # matrix-free is an FP64-path option
-        B.Problem(prec="mixed", matrix_free=1)
+    with pytest.raises(B.BemError):                       # the tensor-core path stores its split copy of A
+        B.Problem(prec="mixed_tc", matrix_free=1)
 
 
 def test_near_field_matches_oracle_and_mie_grid(B, torch):
@@ -510,3 +510,30 @@ def test_mixed_inner_solves_keep_orthogonality(B, torch, name):
     assert st == B.BEM_OK and rs[0] <= 1e-8
     assert it[0] <= 3 * it8[0], (int(it[0]), int(it8[0]))
     assert rel(x[0].cpu().numpy(), x64[0].cpu().numpy()) <= SOLUTION_TOL_MIXED
+
+
+@pytest.mark.parametrize("store_frac", [0.0, 0.5, 1.0])
+def test_matrix_free_mixed_with_stored_rows(B, torch, store_frac):
+    """Matrix-free mixed solves: the leading element rows that fit in store_bytes are kept as complex FP32, the
+    others recomputed in every inner product; the refinement residual recomputes every entry with FP64 sums.
+    Nothing stored, half the rows stored and all rows stored: the solution matches the oracle's LU solution to
+    the mixed bar, and the problem holds less device memory than with its whole matrix stored."""
+    wp = W.Problem(k=[20.0, 30.0], eps=[1.0, 2.25], segments=[W.Segment(W.star(300, 0.3, 5), P=0, M=1, closed=True)])
+    n = wp.n_elem
+    store = int(store_frac * n) * 2 * 2 * n * 8
+    p = B.Problem.from_workload(wp, prec="mixed", matrix_free=1, store_bytes=store, tol=1e-10, max_iter=300)
+    full = B.Problem.from_workload(wp, prec="mixed")
+    assert p.bem_footprint_bytes(1) < full.bem_footprint_bytes(1)
+    full.close()
+    ang = np.array([0.0, 2.1])
+    x = torch.empty((2, 2 * n), dtype=torch.complex128, device="cuda")
+    st, it, rs = p.bem_solve_planewave(ang, x)
+    assert st == B.BEM_OK and np.all(rs <= 1e-10), (st, it, rs)
+    A = O.assemble(wp, Q=4)
+    for r, t in enumerate(ang):
+        xl = O.solve_lu(A, O.rhs_planewave(wp, t))
+        assert rel(x[r].cpu().numpy(), xl) <= SOLUTION_TOL_MIXED, (store_frac, r)
+    with pytest.raises(B.BemError) as e:          # no matrix to read back
+        p.bem_get_matrix(torch.empty((2 * n, 2 * n), dtype=torch.complex128, device="cuda"))
+    assert e.value.status == B.BEM_ESTATE
+    p.close()

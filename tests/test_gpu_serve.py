@@ -58,8 +58,9 @@ def test_serving_defers_when_budget_is_full(P):
 
 
 def test_serving_routes_oversized_requests_matrix_free(P):
-    """Requests whose complex-FP32 matrix exceeds the limit are solved matrix-free on a worker stream while the
-    batch engine serves the rest; every result matches the stored-matrix FP64 solve."""
+    """Requests whose complex-FP32 matrix exceeds the limit are solved matrix-free (rows within the limit stored,
+    the rest recomputed) on a worker stream while the batch engine serves the rest; every result matches the
+    stored-matrix FP64 solve."""
     import torch
     from paper_2312_12787_gb300 import serve
     stream = W.cfg_serving_c5(count=8, seed=21, rate=400.0, n_min=64, n_max=500)
