@@ -10,9 +10,11 @@ is the mixed-precision path (complex FP32 storage and Krylov basis, FP64 refinem
 GPU path runs the same step for comparison (`fp64` key).  The CPU oracle solves the whole workload on
 the host cores (`cpu_baseline`), and its LU solution is the reference of the `accuracy` key.
 
-The same line carries two secondary keys, each with its own clock record and an FP64 comparator on
-identical problems: `sweep` (256 random stars solved as one batch) and `serving` (a Poisson stream of
-2000 requests through the continuous-batching loop, p50/p99 latency).
+The same line carries secondary keys, each with its own clock record: `sweep` (256 random stars solved
+as one batch) and `serving` (a Poisson stream of 2000 requests through the continuous-batching loop,
+p50/p99 latency), both with an FP64 comparator on identical problems, and `sec7_sweeps` (the iteration
+studies of Sec. 7.1 and 7.2: circle, concentric circles and junction disk, GMRES iterations against N,
+omega and eps for the proposed and the compared arrangements, one batch each).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--fp64-steps S]
                        [--workload star|sweep|serving|omega_eps] [--no-secondary] [--requests R]
@@ -598,6 +600,7 @@ def main():
     if rank == 0 and not args.no_secondary:
         line["sweep"] = sweep_leg(args, local)
         line["serving"] = serving_leg(args, local)
+        line["sec7_sweeps"] = omega_eps_leg(args)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
