@@ -79,12 +79,16 @@ __device__ __forceinline__ void store_pair(int n, int i, int j, const C2 (&out)[
   }
 }
 
-// Three CTAs per SM (80 registers, some spills): the kernel is bound by dependent FP64 and double-float
-// latencies, and the extra resident warps hide more of them than the spills cost (5 % faster than two).
+// Resident CTAs per SM of the assembly and matrix-free kernels: two (128 registers, no spills) measured
+// 5.34 ms per launch on the 4096-element star against 5.48 ms with three and 5.52 ms with four (per-pair FP64
+// geometry and Bessel arguments); the kernels are latency-bound, so this is a register-versus-occupancy choice.
+#ifndef BEM_ASM_CTAS_PER_SM
+#define BEM_ASM_CTAS_PER_SM 2
+#endif
 // Element rows i < rows (rows = n: the whole matrix; fewer: the stored part of a partly recomputed matrix, rows
 // i and lower + i).
 template <int MIXED>
-__global__ void __launch_bounds__(256, 3) k_assemble(ElemDev e, int n, DomTab dom, Quad q, int form, void* Aout,
+__global__ void __launch_bounds__(256, BEM_ASM_CTAS_PER_SM) k_assemble(ElemDev e, int n, DomTab dom, Quad q, int form, void* Aout,
                                                    void* Aloout, size_t lda, int rows, int lower) {
   const int j = blockIdx.x * 32 + threadIdx.x;
   const int i = blockIdx.y * 8 + threadIdx.y;
@@ -97,7 +101,7 @@ __global__ void __launch_bounds__(256, 3) k_assemble(ElemDev e, int n, DomTab do
 // Matrix-free product y = A x (no stored matrix): each block owns 8 element rows (16 matrix rows i and
 // N + i); the 32 lanes of a warp stride over the element columns j, evaluate the four entries of (i, j) with
 // the assembly's own code and accumulate; a warp reduction gives the two row sums (FP64 products and sums).
-// Three CTAs per SM, as for k_assemble.
+// Resident CTAs per SM as for k_assemble.
 template <typename T> __device__ __forceinline__ double2 ld_c(const T* p);
 template <> __device__ __forceinline__ double2 ld_c<double2>(const double2* p) { return *p; }
 template <> __device__ __forceinline__ double2 ld_c<float2>(const float2* p) {
@@ -109,7 +113,7 @@ __device__ __forceinline__ void st_c(float2* p, double2 v) { *p = make_float2((f
 
 // Element rows i0 .. n-1 (all of them for i0 = 0).
 template <typename T>
-__global__ void __launch_bounds__(256, 3) k_matvec_free(ElemDev e, int n, DomTab dom, Quad q, int form, int i0,
+__global__ void __launch_bounds__(256, BEM_ASM_CTAS_PER_SM) k_matvec_free(ElemDev e, int n, DomTab dom, Quad q, int form, int i0,
                                                       const T* __restrict__ x, T* __restrict__ y, const int* gate) {
   if (gate && *gate == 0) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
