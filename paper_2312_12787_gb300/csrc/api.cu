@@ -438,6 +438,8 @@ size_t krylov_bytes(int n2, int nrhs, int m, bool fp32) {
   add((size_t)nrhs * 4);                  // reo
   add((size_t)nrhs * 4);                  // strict
   add((size_t)nrhs * 4);                  // arrive
+  add((size_t)nrhs * 4);                  // sync
+  add(4);                                 // err
   add((size_t)nrhs * (m + 1) * 16);       // hcol
   add((size_t)nrhs * 4);                  // active
   add((size_t)nrhs * 4);                  // iters
@@ -497,6 +499,8 @@ Solver carve_solver(bem_problem* p, int nrhs, bool fp32) {
   st.reo = c.take<int>(nrhs);
   st.strict = c.take<int>(nrhs);
   st.arrive = c.take<int>(nrhs);
+  st.sync = c.take<int>(nrhs);
+  st.err = c.take<int>(1);
   st.hcol = c.take<double2>((size_t)nrhs * (m + 1));
   st.active = c.take<int>(nrhs);
   st.iters = c.take<int>(nrhs);
@@ -708,11 +712,13 @@ bem_status gmres_run(bem_problem* p, Solver& sv, const double2* r0, double2* x, 
   std::vector<double> rs(nrhs);
   CU(cudaMemcpyAsync(it.data(), st.iters, nrhs * sizeof(int), cudaMemcpyDeviceToHost, s));
   CU(cudaMemcpyAsync(rs.data(), st.resid, nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
-  int tc_err = 0;
+  int tc_err = 0, orth_err = 0;
   if (use_tc)
     CU(cudaMemcpyAsync(&tc_err, matvec_tc_error_word(sv.tcws, n2, nrhs), sizeof(int), cudaMemcpyDeviceToHost, s));
+  if (krylov_fused(st)) CU(cudaMemcpyAsync(&orth_err, st.err, sizeof(int), cudaMemcpyDeviceToHost, s));
   CU(cudaStreamSynchronize(s));
   if (tc_err) return fail(BEM_ETIMEOUT, "tensor-core GEMM wait expired (code %d)", tc_err);
+  if (orth_err) return fail(BEM_ETIMEOUT, "a per-system barrier wait of the Gram-Schmidt kernel expired");
   for (int r = 0; r < nrhs; ++r) {
     iters[r] += it[r];
     resid[r] = rs[r];

@@ -225,6 +225,9 @@ struct KrylovState {
   int* reo;         // nrhs: 1 if the conditional second Gram-Schmidt pass runs this iteration
   int* strict;      // nrhs: 1 once a refinement step stagnated (the conditional second pass then always runs)
   int* arrive;      // nrhs: CTAs of the first-pass update kernel done (the last one takes the decision)
+  int* sync;        // nrhs: chunk arrivals of the fused projection-update kernel (a per-system barrier; only
+                    // ever incremented, zeroed at the start of a run)
+  int* err;         // 1: nonzero after a bounded wait of the fused kernel ran out (read by the host)
   double2* hcol;    // nrhs x (m+1): projections of the current pass
   int* active;      // nrhs: 1 while iterating
   int* iters;       // nrhs
@@ -249,6 +252,8 @@ cudaError_t krylov_start(const KrylovState& st, const double2* r0, double tol_un
 cudaError_t krylov_orthogonalise(const KrylovState& st, int passes, cudaStream_t s);
 cudaError_t krylov_finish_step(const KrylovState& st, double tol, cudaStream_t s);   // one kernel
 int krylov_orth_launches(const KrylovState& st, int passes);   // kernels of krylov_orthogonalise
+// 1 if krylov_orthogonalise runs the fused projection-update kernel for this state (see krylov.cu).
+int krylov_fused(const KrylovState& st);
 // x += V y; with dout, the correction V y is also written there in complex FP32.
 cudaError_t krylov_update_solution(const KrylovState& st, double2* x, cudaStream_t s, float2* dout = nullptr);
 

@@ -318,6 +318,189 @@ __global__ void __launch_bounds__(CH / 2, sizeof(T) == sizeof(float2) ? 8 : 1) k
   }
 }
 
+// One classical Gram-Schmidt pass, projections and update fused in one cooperative launch.  The two-kernel pass
+// (k_dots, then k_update) reads every chunk of the basis twice, and with all CTAs of the first kernel resident at
+// once the whole basis (64 systems x (j + 1) vectors: 130 MB at j = 30 on the 8192-unknown star) passes through
+// L2 before the second kernel reads it again, so both reads come from HBM.  Here a persistent grid walks the
+// (system, chunk) items in system order: a CTA projects its chunk, waits at a per-system barrier until every
+// chunk of that system has its partial products, sums them (FP64, chunk order) and updates its chunk, whose basis
+// entries it has just read.  Only the CTAs that keep the chunks in flight within `budget` bytes take items (at
+// large j), so the second read can hit L2; the grid is cooperative, so every CTA of a system's barrier is
+// resident.  One launch per pass replaces two (three with the partial-sum kernel), and a conditional second pass
+// that no system needs is one early-exit launch instead of two.
+//
+// Deadlock freedom: items are assigned statically, item q to CTA q mod G, with G >= chunks per system, so the
+// chunks of one system sit on distinct CTAs, and a CTA's earlier items belong to earlier systems; by induction on
+// the system index every barrier completes.  Each wait is bounded (kCgsWaitNs): on expiry the kernel records it in
+// st.err (the host returns BEM_ETIMEOUT) and goes on, and once st.err is set no later wait of the run waits at
+// all, so no CTA can hang and a failed run ends in bounded time.
+constexpr unsigned long long kCgsWaitNs = 500000000ull;   // 0.5 s (a barrier normally completes in microseconds)
+
+__device__ __forceinline__ unsigned long long cgs_time() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+template <typename T, int CH>
+__global__ void __launch_bounds__(kThreads, sizeof(T) == sizeof(float2) ? 4 : 1)
+    k_cgs(KrylovState st, int nchunk, int pass, int mode, long long budget) {
+  using F = typename Vec<T>::acc_t;
+  constexpr int P = CH / 64;
+  __shared__ __align__(16) T ws[CH];
+  __shared__ F hs[2 * kHsMax];
+  __shared__ double red[kThreads / 32];
+  __shared__ int s_last;
+  const int j = *st.jdev;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const size_t stride = (size_t)st.nrhs * st.n;
+  // CTAs in use: at least a system's chunks, at most what keeps the basis chunks in flight within the budget
+  const long long per_item = (long long)CH * (j + 1) * (long long)sizeof(T);
+  int G = gridDim.x;
+  if (nchunk > G) {   // the launcher never does this: a system's chunks must sit on distinct resident CTAs
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicCAS(st.err, 0, 2);
+    return;
+  }
+  const long long fit = budget / per_item;
+  if (fit < G) G = fit > nchunk ? (int)fit : nchunk;
+  if ((int)blockIdx.x >= G) return;
+  const int items = st.nrhs * nchunk;
+  for (int q = blockIdx.x; q < items; q += G) {
+    const int s = q / nchunk, c = q - s * nchunk;
+    if (!st.active[s] || (mode == 1 && !st.reo[s])) continue;   // uniform over the system's chunks
+    const T* W = static_cast<const T*>(st.W) + (size_t)s * st.n;
+    const T* V = static_cast<const T*>(st.V) + (size_t)s * st.n;
+    // ---- projections <v_i, w> over this chunk (as k_dots) ----
+    for (int qq = threadIdx.x; qq < CH / 2; qq += kThreads) {
+      const int k = c * CH + 2 * qq;
+      T a, b;
+      if (k < st.n) {
+        Pair<T>::load(W + k, a, b);
+      } else {
+        a.x = a.y = b.x = b.y = 0;
+      }
+      Pair<T>::store(ws + 2 * qq, a, b);
+    }
+    __syncthreads();
+    if (mode == 0 && warp == 0) {
+      F nw = 0;
+#pragma unroll
+      for (int p = 0; p < P; ++p) {
+        T a, b;
+        Pair<T>::load(ws + 2 * (32 * p + lane), a, b);
+        nw += (F)a.x * (F)a.x + (F)a.y * (F)a.y + (F)b.x * (F)b.x + (F)b.y * (F)b.y;
+      }
+      nw = warp_sum(nw);
+      if (lane == 0) st.wpart[(size_t)s * nchunk + c] = (double)nw;
+    }
+    for (int i = warp; i <= j; i += kThreads / 32) {
+      const T* vi = V + (size_t)i * stride;
+      F px = 0, py = 0;
+      constexpr int kU = P >= 8 ? 4 : 2;
+#pragma unroll kU
+      for (int p = 0; p < P; ++p) {
+        const int qq = 32 * p + lane;
+        const int k = c * CH + 2 * qq;
+        if (k < st.n) {
+          T a, b, w0, w1;
+          Pair<T>::load(vi + k, a, b);
+          Pair<T>::load(ws + 2 * qq, w0, w1);
+          px += (F)a.x * (F)w0.x + (F)a.y * (F)w0.y + (F)b.x * (F)w1.x + (F)b.y * (F)w1.y;
+          py += (F)a.x * (F)w0.y - (F)a.y * (F)w0.x + (F)b.x * (F)w1.y - (F)b.y * (F)w1.x;
+        }
+      }
+      const F hx = warp_sum(px), hy = warp_sum(py);
+      if (lane == 0) st.part[((size_t)s * nchunk + c) * (st.m + 1) + i] = make_double2((double)hx, (double)hy);
+    }
+    // ---- wait until every chunk of system s has written its partial products ----
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      const int old = atomicAdd(st.sync + s, 1);
+      const int target = (old / nchunk + 1) * nchunk;
+      if (*(volatile int*)(st.sync + s) < target && *(volatile int*)st.err == 0) {
+        const unsigned long long t0 = cgs_time();
+        while (*(volatile int*)(st.sync + s) < target) {
+          if (cgs_time() - t0 > kCgsWaitNs || *(volatile int*)st.err != 0) {
+            atomicCAS(st.err, 0, 1);
+            break;
+          }
+        }
+      }
+      __threadfence();
+    }
+    __syncthreads();
+    // ---- h_i = sum over the chunks (FP64, chunk order); chunk 0 records them in column j of H ----
+    for (int i = threadIdx.x; i <= j; i += kThreads) {
+      double2 h = make_double2(0.0, 0.0);
+#pragma unroll 4
+      for (int cc = 0; cc < nchunk; ++cc) h = cadd(h, __ldcg(st.part + ((size_t)s * nchunk + cc) * (st.m + 1) + i));
+      if (c == 0) {
+        st.hcol[(size_t)s * (st.m + 1) + i] = h;
+        double2* Hj = st.H + ((size_t)s * st.m + j) * (st.m + 1);
+        Hj[i] = pass == 0 ? h : cadd(Hj[i], h);
+      }
+      hs[2 * i] = (F)h.x;
+      hs[2 * i + 1] = (F)h.y;
+    }
+    __syncthreads();
+    // ---- w -= sum_i h_i v_i over this chunk (as k_update: a thread owns a pair of entries) ----
+    F nrm_f = 0;
+    const int k = c * CH + 2 * threadIdx.x;
+    if (threadIdx.x < CH / 2 && k < st.n) {
+      const T* Vk = V + k;
+      F ax = 0, ay = 0, bx = 0, by = 0;
+#pragma unroll 8
+      for (int i = 0; i <= j; ++i) {
+        T a, b;
+        Pair<T>::load(Vk + (size_t)i * stride, a, b);
+        const F hx = hs[2 * i], hy = hs[2 * i + 1];
+        ax += hx * (F)a.x - hy * (F)a.y;
+        ay += hx * (F)a.y + hy * (F)a.x;
+        bx += hx * (F)b.x - hy * (F)b.y;
+        by += hx * (F)b.y + hy * (F)b.x;
+      }
+      T* Wk = static_cast<T*>(st.W) + (size_t)s * st.n + k;
+      T w0, w1;
+      Pair<T>::load(ws + 2 * threadIdx.x, w0, w1);
+      w0.x -= ax; w0.y -= ay;
+      w1.x -= bx; w1.y -= by;
+      Pair<T>::store(Wk, w0, w1);
+      nrm_f = w0.x * w0.x + w0.y * w0.y + w1.x * w1.x + w1.y * w1.y;
+    }
+    nrm_f = warp_sum(nrm_f);
+    if (lane == 0) red[warp] = (double)nrm_f;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w8 = 0; w8 < kThreads / 32; ++w8) t += red[w8];
+      st.npart[(size_t)s * nchunk + c] = t;
+      s_last = 0;
+      if (pass == 0) {
+        __threadfence();
+        s_last = atomicAdd(st.arrive + s, 1) == nchunk - 1;
+      }
+    }
+    __syncthreads();
+    if (s_last && threadIdx.x < 32) {
+      // the system's last chunk takes the decision of the conditional second pass (norm-drop test, see k_dots)
+      __threadfence();
+      double before = 0.0, after = 0.0;
+      for (int cc = threadIdx.x; cc < nchunk; cc += 32) {
+        before += __ldcg(st.wpart + (size_t)s * nchunk + cc);
+        after += __ldcg(st.npart + (size_t)s * nchunk + cc);
+      }
+      before = warp_sum(before);
+      after = warp_sum(after);
+      if (threadIdx.x == 0) {
+        st.reo[s] = st.strict[s] || after < 0.01 * before;
+        st.arrive[s] = 0;
+      }
+    }
+    __syncthreads();   // ws, hs and s_last are reused by the next item
+  }
+}
+
 // End of iteration j, one kernel (grid = blocks of kThreads entries x systems):
 //  * every CTA forms ||w|| = h_{j+1,j} from the update kernel's chunk sums and scales its entries of w into
 //    V_{j+1} (and into the FP16 x 3 operand of the next tensor-core product);
@@ -562,6 +745,11 @@ cudaError_t start_t(const KrylovState& st, const double2* r0, cudaStream_t s) {
   k_norm_part<double2><<<grd, kThreads, 0, s>>>(r0, st.n, st.npart, nb);
   cudaError_t e = cudaMemsetAsync(st.n_active, 0, sizeof(int), s);
   if (e != cudaSuccess) return e;
+  if (st.sync) {
+    e = cudaMemsetAsync(st.sync, 0, st.nrhs * sizeof(int), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(st.err, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
+  }
   k_start_finish<<<(st.nrhs + 63) / 64, 64, 0, s>>>(st, nb);
   k_start_scale<T><<<grd, kThreads, 0, s>>>(st, r0);
   return cudaGetLastError();
@@ -569,12 +757,87 @@ cudaError_t start_t(const KrylovState& st, const double2* r0, cudaStream_t s) {
 
 // passes: 1 (classical Gram-Schmidt), 2 (twice, CGS2) or 0 (once, then again only for the systems that the
 // norm-drop test flags).
+// Bytes of basis chunks the fused kernel keeps in flight.  Measured on the 64-system star (Arnoldi phase per
+// step): 32 MB 13.5 ms, 64 MB 9.3 ms, 128 MB 7.86 ms, unlimited 7.96 ms (the two-kernel pass: 8.1 ms).  Fewer
+// CTAs than the device holds cost more memory parallelism than the L2 reuse they buy, so the budget only trims
+// the grid at large j; the fused pass gains by one launch per pass and one early-exit launch less.
+#ifndef BEM_CGS_L2_BUDGET_MB
+#define BEM_CGS_L2_BUDGET_MB 128
+#endif
+constexpr long long kCgsL2Budget = (long long)BEM_CGS_L2_BUDGET_MB << 20;
+
+// Resident CTAs of the fused kernel on this device (0 if its launch cannot be cooperative).
+template <typename T, int CH>
+int cgs_grid() {
+  static std::atomic<int> cache[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+  int g = cache[dev].load(std::memory_order_relaxed);
+  if (g != 0) return g > 0 ? g : 0;
+  int coop = 0, per = 0;
+  if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_cgs<T, CH>, kThreads, 0) != cudaSuccess || per <= 0) {
+    cache[dev].store(-1, std::memory_order_relaxed);
+    return 0;
+  }
+  g = per * sm_count();
+  cache[dev].store(g, std::memory_order_relaxed);
+  return g;
+}
+
+template <typename T, int CH>
+cudaError_t cgs_pass(const KrylovState& st, int pass, int mode, cudaStream_t s) {
+  const int nc = (st.n + CH - 1) / CH;
+  const int G = std::min(cgs_grid<T, CH>(), nc * st.nrhs);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(G);
+  cfg.blockDim = dim3(kThreads);
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_cgs<T, CH>, st, nc, pass, mode, kCgsL2Budget);
+}
+
+// The fused pass is used where its grid can hold every chunk of a system (so its barrier is safe) and the
+// state carries its counters.
+template <typename T, int CH>
+bool cgs_usable(const KrylovState& st) {
+  const int nc = (st.n + CH - 1) / CH;
+  const int G = cgs_grid<T, CH>();
+  return st.sync && st.err && G > 0 && nc <= std::min(G, nc * st.nrhs) && nc <= 64;
+}
+
+template <typename T>
+bool fused_t(const KrylovState& st) {
+  switch (chunk_of(st.n, st.nrhs)) {
+    case 512: return cgs_usable<T, 512>(st);
+    case 256: return cgs_usable<T, 256>(st);
+    case 128: return cgs_usable<T, 128>(st);
+    default: return cgs_usable<T, 64>(st);
+  }
+}
+
 template <typename T>
 cudaError_t orth_t(const KrylovState& st, int passes, cudaStream_t s) {
   const int ch = chunk_of(st.n, st.nrhs);
   const int np = passes == 1 ? 1 : 2;
+  const bool fused = fused_t<T>(st);
   for (int p = 0; p < np; ++p) {
     const int mode = p == 0 ? 0 : (passes == 0 ? 1 : 2);
+    cudaError_t e = cudaSuccess;
+    if (fused) {
+      switch (ch) {
+        case 512: e = cgs_pass<T, 512>(st, p, mode, s); break;
+        case 256: e = cgs_pass<T, 256>(st, p, mode, s); break;
+        case 128: e = cgs_pass<T, 128>(st, p, mode, s); break;
+        default: e = cgs_pass<T, 64>(st, p, mode, s); break;
+      }
+      if (e != cudaSuccess) return e;
+      continue;
+    }
     switch (ch) {
       case 512: orth_pass<T, 512>(st, p, mode, s); break;
       case 256: orth_pass<T, 256>(st, p, mode, s); break;
@@ -617,9 +880,11 @@ cudaError_t krylov_start(const KrylovState& st, const double2* r0, double, cudaS
 cudaError_t krylov_orthogonalise(const KrylovState& st, int passes, cudaStream_t s) {
   return st.basis_fp32 ? orth_t<float2>(st, passes, s) : orth_t<double2>(st, passes, s);
 }
+int krylov_fused(const KrylovState& st) { return st.basis_fp32 ? fused_t<float2>(st) : fused_t<double2>(st); }
 int krylov_orth_launches(const KrylovState& st, int passes) {
   const int ch = chunk_of(st.n, st.nrhs);
   const int nc = (st.n + ch - 1) / ch;
+  if (krylov_fused(st)) return passes == 1 ? 1 : 2;    // one fused launch per pass
   return (passes == 1 ? 1 : 2) * (nc <= 32 ? 2 : 3);   // projections, [reduction,] update per pass
 }
 cudaError_t krylov_finish_step(const KrylovState& st, double tol, cudaStream_t s) {
