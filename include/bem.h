@@ -278,12 +278,19 @@ BEM_API bem_status bem_profile_enable(bem_problem* p, int on);
 BEM_API bem_status bem_profile_read(bem_problem* p, double* ms_host, long long* launches_host);
 
 /* Failure-path testing: the limit, in seconds, of the waits in the main loop of the tensor-core product
- * kernels launched from now on (process-wide; 0 restores the default of 2 s; CUDA graphs that the solver
- * recorded earlier keep the limit they were recorded with).  A wait that runs out records an error word that
- * the host reads after the product (BEM_ETIMEOUT); the kernel then stops issuing work, waits with the default
- * limit for its own copies and MMAs in flight, frees its tensor memory and returns, so the context stays
- * usable.  EINVAL outside [0, 10]. */
+ * kernels and of the per-system barrier waits of the fused GMRES iteration kernel, for kernels launched from now
+ * on (process-wide; 0 restores the defaults of 2 s and 0.5 s; CUDA graphs that a problem recorded earlier keep
+ * the limits they were recorded with).  A tensor-core wait that runs out records an error word that the host
+ * reads after the product (BEM_ETIMEOUT); the kernel then stops issuing work, waits with the default limit for
+ * its own copies and MMAs in flight, frees its tensor memory and returns, so the context stays usable.  A
+ * barrier wait that runs out records an error word and the kernel goes on without waiting (its results are then
+ * meaningless, every access stays in bounds); the solve ends at its iteration limit and returns BEM_ETIMEOUT.
+ * EINVAL outside [0, 10]. */
 BEM_API bem_status bem_test_set_wait_limit(double seconds);
+/* Testing: on = 0 makes solves started from now on run each GMRES iteration's tail as separate kernels
+ * (projections, update, end of iteration: the path of devices without cooperative launches) instead of the
+ * single cooperative kernel; on != 0 restores the default.  Process-wide. */
+BEM_API bem_status bem_test_set_fused_iteration(int on);
 
 /* Thread-local message of the last failure in this thread ("" if none). */
 BEM_API const char* bem_last_error(void);

@@ -28,6 +28,7 @@ EXPORTS = [
     "bem_solve_planewave_host", "bem_near_field", "bem_profile_enable", "bem_profile_read", "bem_last_error", "bem_version",
     "bem_batch_create", "bem_batch_destroy", "bem_batch_admit", "bem_batch_step", "bem_batch_query",
     "bem_batch_take", "bem_batch_free_units", "bem_batch_solve_planewave", "bem_test_set_wait_limit",
+    "bem_test_set_fused_iteration",
 ]
 PHASES = ["geometry", "assemble", "rhs", "matvec", "arnoldi", "givens", "update", "residual", "farfield", "other",
           "reduce"]
@@ -102,6 +103,8 @@ def load(path: str | None = None):
         getattr(L, name).restype = i
     L.bem_test_set_wait_limit.argtypes = [d]
     L.bem_test_set_wait_limit.restype = i
+    L.bem_test_set_fused_iteration.argtypes = [i]
+    L.bem_test_set_fused_iteration.restype = i
     L.bem_last_error.argtypes = []
     L.bem_last_error.restype = ctypes.c_char_p
     L.bem_version.argtypes = []
@@ -367,8 +370,14 @@ class Batch:
 
 
 def bem_test_set_wait_limit(seconds: float) -> None:
-    """Main-loop wait limit of the tensor-core kernels launched from now on (0 = default); for failure tests."""
+    """Wait limit of the tensor-core main loops and of the fused iteration kernel's barriers, for kernels
+    launched from now on (0 = defaults); for failure tests."""
     _check(load().bem_test_set_wait_limit(float(seconds)))
+
+
+def bem_test_set_fused_iteration(on: bool) -> None:
+    """False: later solves run each iteration's tail as separate kernels (the non-cooperative path); for tests."""
+    _check(load().bem_test_set_fused_iteration(1 if on else 0))
 
 
 def bem_version() -> str:

@@ -119,6 +119,7 @@ struct bem_problem {
   const void* ig_ws = nullptr;
   const void* ig_a16 = nullptr;
   int ig_n2 = 0, ig_nrhs = 0, ig_m = 0, ig_passes = -1;
+  bool ig_fused = false;
   cudaStream_t ig_stream = nullptr;
   cudaEvent_t ig_ev[3] = {nullptr, nullptr, nullptr};
   // measurement: event pairs per phase, kernel launches per phase
@@ -438,7 +439,7 @@ size_t krylov_bytes(int n2, int nrhs, int m, bool fp32) {
   add((size_t)nrhs * 4);                  // reo
   add((size_t)nrhs * 4);                  // strict
   add((size_t)nrhs * 4);                  // arrive
-  add((size_t)nrhs * 4);                  // sync
+  add((size_t)nrhs * 4 * kSyncStride);    // sync
   add(4);                                 // err
   add((size_t)nrhs * (m + 1) * 16);       // hcol
   add((size_t)nrhs * 4);                  // active
@@ -499,7 +500,7 @@ Solver carve_solver(bem_problem* p, int nrhs, bool fp32) {
   st.reo = c.take<int>(nrhs);
   st.strict = c.take<int>(nrhs);
   st.arrive = c.take<int>(nrhs);
-  st.sync = c.take<int>(nrhs);
+  st.sync = c.take<int>((size_t)nrhs * kSyncStride);
   st.err = c.take<int>(1);
   st.hcol = c.take<double2>((size_t)nrhs * (m + 1));
   st.active = c.take<int>(nrhs);
@@ -552,6 +553,8 @@ bem_status gmres_run(bem_problem* p, Solver& sv, const double2* r0, double2* x, 
   // systems whose vector the first pass shrank below a tenth of its length (selective reorthogonalisation)
   const int passes = p->o.orth_passes ? p->o.orth_passes : (fp32 ? 0 : 2);
   const int* gate = st.n_active;
+  // decided (and the fused kernel's attributes set) before any graph capture below
+  const bool fused = krylov_fused(st) != 0;
   // one iteration: product, orthogonalisation, rotations and scaling of the next basis vector (the kernels read
   // the iteration index from the device; only the non-tensor-core products take the basis vector's address)
   int launched = 0;   // iterations queued by the host loop below (the graph path does not count them)
@@ -587,6 +590,10 @@ bem_status gmres_run(bem_problem* p, Solver& sv, const double2* r0, double2* x, 
       }
     }
     if (e != cudaSuccess) return e;
+    if (fused) {   // one launch: Gram-Schmidt passes and the end of the iteration
+      Phase ph(p, BEM_PH_ARNOLDI, s, 1);
+      return krylov_fused_step(st, passes, tol, s);
+    }
     {
       Phase ph(p, BEM_PH_ARNOLDI, s, krylov_orth_launches(st, passes));
       e = krylov_orthogonalise(st, passes, s);
@@ -606,7 +613,7 @@ bem_status gmres_run(bem_problem* p, Solver& sv, const double2* r0, double2* x, 
       for (cudaEvent_t& e : p->ig_ev) CU(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     }
     if (p->ig_exec && (p->ig_ws != p->ws || p->ig_a16 != p->d_A16 || p->ig_n2 != n2 || p->ig_nrhs != nrhs ||
-                       p->ig_m != st.m || p->ig_passes != passes)) {
+                       p->ig_m != st.m || p->ig_passes != passes || p->ig_fused != fused)) {
       cudaGraphExecDestroy(p->ig_exec);
       p->ig_exec = nullptr;
     }
@@ -671,6 +678,7 @@ bem_status gmres_run(bem_problem* p, Solver& sv, const double2* r0, double2* x, 
       }
       p->ig_ws = p->ws; p->ig_a16 = p->d_A16; p->ig_n2 = n2; p->ig_nrhs = nrhs; p->ig_m = st.m;
       p->ig_passes = passes;
+      p->ig_fused = fused;
     }
     CU(cudaEventRecord(p->ig_ev[2], s));
     CU(cudaStreamWaitEvent(gs, p->ig_ev[2], 0));
@@ -715,7 +723,7 @@ bem_status gmres_run(bem_problem* p, Solver& sv, const double2* r0, double2* x, 
   int tc_err = 0, orth_err = 0;
   if (use_tc)
     CU(cudaMemcpyAsync(&tc_err, matvec_tc_error_word(sv.tcws, n2, nrhs), sizeof(int), cudaMemcpyDeviceToHost, s));
-  if (krylov_fused(st)) CU(cudaMemcpyAsync(&orth_err, st.err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  if (fused) CU(cudaMemcpyAsync(&orth_err, st.err, sizeof(int), cudaMemcpyDeviceToHost, s));
   CU(cudaStreamSynchronize(s));
   if (tc_err) return fail(BEM_ETIMEOUT, "tensor-core GEMM wait expired (code %d)", tc_err);
   if (orth_err) return fail(BEM_ETIMEOUT, "a per-system barrier wait of the Gram-Schmidt kernel expired");
@@ -1373,6 +1381,12 @@ BEM_API bem_status bem_profile_read(bem_problem* p, double* ms, long long* launc
 BEM_API bem_status bem_test_set_wait_limit(double seconds) {
   if (!(seconds >= 0.0) || seconds > 10.0) return fail(BEM_EINVAL, "wait limit must be in [0, 10] s");
   matvec_tc_set_wait_ns((unsigned long long)(seconds * 1e9));
+  krylov_set_wait_ns((unsigned long long)(seconds * 1e9));
+  return BEM_OK;
+}
+
+BEM_API bem_status bem_test_set_fused_iteration(int on) {
+  krylov_set_fused(on);
   return BEM_OK;
 }
 

@@ -205,6 +205,7 @@ cudaError_t launch_sub_c32(double2* r, const float2* y, size_t count, cudaStream
 cudaError_t launch_column_norms(const double2* v, int n, int ncol, double* out, cudaStream_t s);
 
 // GMRES building blocks for nrhs systems sharing one matrix; see krylov.cu.
+constexpr int kSyncStride = 32;   // ints between the barrier counters of two systems
 struct KrylovState {
   int n;            // unknowns per system
   int nrhs;         // systems
@@ -225,9 +226,9 @@ struct KrylovState {
   int* reo;         // nrhs: 1 if the conditional second Gram-Schmidt pass runs this iteration
   int* strict;      // nrhs: 1 once a refinement step stagnated (the conditional second pass then always runs)
   int* arrive;      // nrhs: CTAs of the first-pass update kernel done (the last one takes the decision)
-  int* sync;        // nrhs: chunk arrivals of the fused projection-update kernel (a per-system barrier; only
-                    // ever incremented, zeroed at the start of a run)
-  int* err;         // 1: nonzero after a bounded wait of the fused kernel ran out (read by the host)
+  int* sync;        // nrhs x kSyncStride: chunk arrivals of the fused iteration kernel (a per-system barrier;
+                    // only ever incremented, zeroed at the start of a run), one 128-byte line per system
+  int* err;         // 1: nonzero after a bounded wait of the fused iteration kernel ran out (read by the host)
   double2* hcol;    // nrhs x (m+1): projections of the current pass
   int* active;      // nrhs: 1 while iterating
   int* iters;       // nrhs
@@ -252,8 +253,13 @@ cudaError_t krylov_start(const KrylovState& st, const double2* r0, double tol_un
 cudaError_t krylov_orthogonalise(const KrylovState& st, int passes, cudaStream_t s);
 cudaError_t krylov_finish_step(const KrylovState& st, double tol, cudaStream_t s);   // one kernel
 int krylov_orth_launches(const KrylovState& st, int passes);   // kernels of krylov_orthogonalise
-// 1 if krylov_orthogonalise runs the fused projection-update kernel for this state (see krylov.cu).
+// Nonzero if the tail of an iteration (both Gram-Schmidt passes, rotations, next basis vector, index advance)
+// runs as one cooperative launch for this state (krylov_fused_step, in place of krylov_orthogonalise and
+// krylov_finish_step); then st.err reports an expired barrier wait.
 int krylov_fused(const KrylovState& st);
+void krylov_set_wait_ns(unsigned long long ns);   // barrier wait limit of the fused kernel (0: default 0.5 s)
+void krylov_set_fused(int on);                     // 0: separate kernels even where the fused one is usable
+cudaError_t krylov_fused_step(const KrylovState& st, int passes, double tol, cudaStream_t s);
 // x += V y; with dout, the correction V y is also written there in complex FP32.
 cudaError_t krylov_update_solution(const KrylovState& st, double2* x, cudaStream_t s, float2* dout = nullptr);
 

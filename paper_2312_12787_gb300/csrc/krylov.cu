@@ -8,11 +8,13 @@
 // run in the basis precision, the per-chunk partial sums are combined in FP64.  The Hessenberg column, g and
 // the residual estimate are FP64; the rotations run in the basis precision.
 //
-// Work split: a vector of n unknowns is cut into chunks (512, 256, 128 or 64 entries, the largest that
-// still gives two CTAs per SM over all systems); one CTA owns one chunk of one system (grid = chunks x
-// systems).  In the projection kernel the chunk of w is staged in shared memory and each warp owns every
-// eighth basis vector; in the update kernel each thread owns a pair of entries over all basis vectors.  One
-// kernel ends each iteration (norm, next basis vector, rotations, iteration index).  The kernels of an
+// Where the device allows cooperative launches, everything after the product is one launch per iteration
+// (k_arnoldi: both passes, rotations, next basis vector, index advance, with per-system barriers between the
+// CTAs of a system).  Otherwise: a vector of n unknowns is cut into chunks (512, 256, 128 or 64 entries, the
+// largest that still gives two CTAs per SM over all systems); one CTA owns one chunk of one system (grid =
+// chunks x systems).  In the projection kernel the chunk of w is staged in shared memory and each warp owns
+// every eighth basis vector; in the update kernel each thread owns a pair of entries over all basis vectors.
+// One kernel ends each iteration (norm, next basis vector, rotations, iteration index).  The kernels of an
 // iteration read the iteration index from the device and use programmatic dependent launch.
 #include <algorithm>
 #include <atomic>
@@ -318,189 +320,6 @@ __global__ void __launch_bounds__(CH / 2, sizeof(T) == sizeof(float2) ? 8 : 1) k
   }
 }
 
-// One classical Gram-Schmidt pass, projections and update fused in one cooperative launch.  The two-kernel pass
-// (k_dots, then k_update) reads every chunk of the basis twice, and with all CTAs of the first kernel resident at
-// once the whole basis (64 systems x (j + 1) vectors: 130 MB at j = 30 on the 8192-unknown star) passes through
-// L2 before the second kernel reads it again, so both reads come from HBM.  Here a persistent grid walks the
-// (system, chunk) items in system order: a CTA projects its chunk, waits at a per-system barrier until every
-// chunk of that system has its partial products, sums them (FP64, chunk order) and updates its chunk, whose basis
-// entries it has just read.  Only the CTAs that keep the chunks in flight within `budget` bytes take items (at
-// large j), so the second read can hit L2; the grid is cooperative, so every CTA of a system's barrier is
-// resident.  One launch per pass replaces two (three with the partial-sum kernel), and a conditional second pass
-// that no system needs is one early-exit launch instead of two.
-//
-// Deadlock freedom: items are assigned statically, item q to CTA q mod G, with G >= chunks per system, so the
-// chunks of one system sit on distinct CTAs, and a CTA's earlier items belong to earlier systems; by induction on
-// the system index every barrier completes.  Each wait is bounded (kCgsWaitNs): on expiry the kernel records it in
-// st.err (the host returns BEM_ETIMEOUT) and goes on, and once st.err is set no later wait of the run waits at
-// all, so no CTA can hang and a failed run ends in bounded time.
-constexpr unsigned long long kCgsWaitNs = 500000000ull;   // 0.5 s (a barrier normally completes in microseconds)
-
-__device__ __forceinline__ unsigned long long cgs_time() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-template <typename T, int CH>
-__global__ void __launch_bounds__(kThreads, sizeof(T) == sizeof(float2) ? 4 : 1)
-    k_cgs(KrylovState st, int nchunk, int pass, int mode, long long budget) {
-  using F = typename Vec<T>::acc_t;
-  constexpr int P = CH / 64;
-  __shared__ __align__(16) T ws[CH];
-  __shared__ F hs[2 * kHsMax];
-  __shared__ double red[kThreads / 32];
-  __shared__ int s_last;
-  const int j = *st.jdev;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const size_t stride = (size_t)st.nrhs * st.n;
-  // CTAs in use: at least a system's chunks, at most what keeps the basis chunks in flight within the budget
-  const long long per_item = (long long)CH * (j + 1) * (long long)sizeof(T);
-  int G = gridDim.x;
-  if (nchunk > G) {   // the launcher never does this: a system's chunks must sit on distinct resident CTAs
-    if (blockIdx.x == 0 && threadIdx.x == 0) atomicCAS(st.err, 0, 2);
-    return;
-  }
-  const long long fit = budget / per_item;
-  if (fit < G) G = fit > nchunk ? (int)fit : nchunk;
-  if ((int)blockIdx.x >= G) return;
-  const int items = st.nrhs * nchunk;
-  for (int q = blockIdx.x; q < items; q += G) {
-    const int s = q / nchunk, c = q - s * nchunk;
-    if (!st.active[s] || (mode == 1 && !st.reo[s])) continue;   // uniform over the system's chunks
-    const T* W = static_cast<const T*>(st.W) + (size_t)s * st.n;
-    const T* V = static_cast<const T*>(st.V) + (size_t)s * st.n;
-    // ---- projections <v_i, w> over this chunk (as k_dots) ----
-    for (int qq = threadIdx.x; qq < CH / 2; qq += kThreads) {
-      const int k = c * CH + 2 * qq;
-      T a, b;
-      if (k < st.n) {
-        Pair<T>::load(W + k, a, b);
-      } else {
-        a.x = a.y = b.x = b.y = 0;
-      }
-      Pair<T>::store(ws + 2 * qq, a, b);
-    }
-    __syncthreads();
-    if (mode == 0 && warp == 0) {
-      F nw = 0;
-#pragma unroll
-      for (int p = 0; p < P; ++p) {
-        T a, b;
-        Pair<T>::load(ws + 2 * (32 * p + lane), a, b);
-        nw += (F)a.x * (F)a.x + (F)a.y * (F)a.y + (F)b.x * (F)b.x + (F)b.y * (F)b.y;
-      }
-      nw = warp_sum(nw);
-      if (lane == 0) st.wpart[(size_t)s * nchunk + c] = (double)nw;
-    }
-    for (int i = warp; i <= j; i += kThreads / 32) {
-      const T* vi = V + (size_t)i * stride;
-      F px = 0, py = 0;
-      constexpr int kU = P >= 8 ? 4 : 2;
-#pragma unroll kU
-      for (int p = 0; p < P; ++p) {
-        const int qq = 32 * p + lane;
-        const int k = c * CH + 2 * qq;
-        if (k < st.n) {
-          T a, b, w0, w1;
-          Pair<T>::load(vi + k, a, b);
-          Pair<T>::load(ws + 2 * qq, w0, w1);
-          px += (F)a.x * (F)w0.x + (F)a.y * (F)w0.y + (F)b.x * (F)w1.x + (F)b.y * (F)w1.y;
-          py += (F)a.x * (F)w0.y - (F)a.y * (F)w0.x + (F)b.x * (F)w1.y - (F)b.y * (F)w1.x;
-        }
-      }
-      const F hx = warp_sum(px), hy = warp_sum(py);
-      if (lane == 0) st.part[((size_t)s * nchunk + c) * (st.m + 1) + i] = make_double2((double)hx, (double)hy);
-    }
-    // ---- wait until every chunk of system s has written its partial products ----
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      __threadfence();
-      const int old = atomicAdd(st.sync + s, 1);
-      const int target = (old / nchunk + 1) * nchunk;
-      if (*(volatile int*)(st.sync + s) < target && *(volatile int*)st.err == 0) {
-        const unsigned long long t0 = cgs_time();
-        while (*(volatile int*)(st.sync + s) < target) {
-          if (cgs_time() - t0 > kCgsWaitNs || *(volatile int*)st.err != 0) {
-            atomicCAS(st.err, 0, 1);
-            break;
-          }
-        }
-      }
-      __threadfence();
-    }
-    __syncthreads();
-    // ---- h_i = sum over the chunks (FP64, chunk order); chunk 0 records them in column j of H ----
-    for (int i = threadIdx.x; i <= j; i += kThreads) {
-      double2 h = make_double2(0.0, 0.0);
-#pragma unroll 4
-      for (int cc = 0; cc < nchunk; ++cc) h = cadd(h, __ldcg(st.part + ((size_t)s * nchunk + cc) * (st.m + 1) + i));
-      if (c == 0) {
-        st.hcol[(size_t)s * (st.m + 1) + i] = h;
-        double2* Hj = st.H + ((size_t)s * st.m + j) * (st.m + 1);
-        Hj[i] = pass == 0 ? h : cadd(Hj[i], h);
-      }
-      hs[2 * i] = (F)h.x;
-      hs[2 * i + 1] = (F)h.y;
-    }
-    __syncthreads();
-    // ---- w -= sum_i h_i v_i over this chunk (as k_update: a thread owns a pair of entries) ----
-    F nrm_f = 0;
-    const int k = c * CH + 2 * threadIdx.x;
-    if (threadIdx.x < CH / 2 && k < st.n) {
-      const T* Vk = V + k;
-      F ax = 0, ay = 0, bx = 0, by = 0;
-#pragma unroll 8
-      for (int i = 0; i <= j; ++i) {
-        T a, b;
-        Pair<T>::load(Vk + (size_t)i * stride, a, b);
-        const F hx = hs[2 * i], hy = hs[2 * i + 1];
-        ax += hx * (F)a.x - hy * (F)a.y;
-        ay += hx * (F)a.y + hy * (F)a.x;
-        bx += hx * (F)b.x - hy * (F)b.y;
-        by += hx * (F)b.y + hy * (F)b.x;
-      }
-      T* Wk = static_cast<T*>(st.W) + (size_t)s * st.n + k;
-      T w0, w1;
-      Pair<T>::load(ws + 2 * threadIdx.x, w0, w1);
-      w0.x -= ax; w0.y -= ay;
-      w1.x -= bx; w1.y -= by;
-      Pair<T>::store(Wk, w0, w1);
-      nrm_f = w0.x * w0.x + w0.y * w0.y + w1.x * w1.x + w1.y * w1.y;
-    }
-    nrm_f = warp_sum(nrm_f);
-    if (lane == 0) red[warp] = (double)nrm_f;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double t = 0.0;
-      for (int w8 = 0; w8 < kThreads / 32; ++w8) t += red[w8];
-      st.npart[(size_t)s * nchunk + c] = t;
-      s_last = 0;
-      if (pass == 0) {
-        __threadfence();
-        s_last = atomicAdd(st.arrive + s, 1) == nchunk - 1;
-      }
-    }
-    __syncthreads();
-    if (s_last && threadIdx.x < 32) {
-      // the system's last chunk takes the decision of the conditional second pass (norm-drop test, see k_dots)
-      __threadfence();
-      double before = 0.0, after = 0.0;
-      for (int cc = threadIdx.x; cc < nchunk; cc += 32) {
-        before += __ldcg(st.wpart + (size_t)s * nchunk + cc);
-        after += __ldcg(st.npart + (size_t)s * nchunk + cc);
-      }
-      before = warp_sum(before);
-      after = warp_sum(after);
-      if (threadIdx.x == 0) {
-        st.reo[s] = st.strict[s] || after < 0.01 * before;
-        st.arrive[s] = 0;
-      }
-    }
-    __syncthreads();   // ws, hs and s_last are reused by the next item
-  }
-}
-
 // End of iteration j, one kernel (grid = blocks of kThreads entries x systems):
 //  * every CTA forms ||w|| = h_{j+1,j} from the update kernel's chunk sums and scales its entries of w into
 //    V_{j+1} (and into the FP16 x 3 operand of the next tensor-core product);
@@ -518,27 +337,33 @@ struct FinishIn {
   double res;
   double tl;
 };
+// The rotations and scalars alone (the fused iteration kernel forms the column itself).
 template <typename C>
-__device__ __forceinline__ void finish_stage(const KrylovState& st, int s, int j, double tol, C* sh_h, C* sh_c,
-                                             C* sh_s, FinishIn* in) {
+__device__ __forceinline__ void stage_rotations(const KrylovState& st, int s, int j, double tol, C* sh_c, C* sh_s,
+                                                FinishIn* in) {
   const int lane = threadIdx.x & 31;
-  const double2* Hj = st.H + ((size_t)s * st.m + j) * (st.m + 1);
   const double2* cs = st.cs + (size_t)s * st.m;
   const double2* sn = st.sn + (size_t)s * st.m;
-  for (int i = lane; i <= j; i += 32) {
-    const double2 h = Hj[i];
-    sh_h[i] = cx<C>(h.x, h.y);
-    if (i < j) {
-      const double2 ci = cs[i], si = sn[i];
-      sh_c[i] = cx<C>(ci.x, ci.y);
-      sh_s[i] = cx<C>(si.x, si.y);
-    }
+  for (int i = lane; i < j; i += 32) {
+    const double2 ci = cs[i], si = sn[i];
+    sh_c[i] = cx<C>(ci.x, ci.y);
+    sh_s[i] = cx<C>(si.x, si.y);
   }
   if (lane == 0) {
     in->gj = st.g[(size_t)s * (st.m + 1) + j];
     in->res = st.resid[s];
     in->tl = st.tolv ? st.tolv[s] : tol;
   }
+}
+template <typename C>
+__device__ __forceinline__ void finish_stage(const KrylovState& st, int s, int j, double tol, C* sh_h, C* sh_c,
+                                             C* sh_s, FinishIn* in) {
+  const double2* Hj = st.H + ((size_t)s * st.m + j) * (st.m + 1);
+  for (int i = threadIdx.x & 31; i <= j; i += 32) {
+    const double2 h = Hj[i];
+    sh_h[i] = cx<C>(h.x, h.y);
+  }
+  stage_rotations(st, s, j, tol, sh_c, sh_s, in);
 }
 
 // One warp, after finish_stage and a barrier: h_{j+1,j} = hn.  The lanes apply the previous rotations to the
@@ -646,6 +471,296 @@ __global__ void __launch_bounds__(kThreads) k_step_end(KrylovState st, int nchun
   }
 }
 
+// ---- One cooperative launch per iteration: orthogonalisation and end of iteration ----
+// As separate kernels, the tail of an iteration (projections, update, a conditional second pass, end of
+// iteration) pays a launch and a grid-wide drain per kernel plus a dependent chain of global round trips in each;
+// at small j these fixed costs dominate (on the 64-system star: 25 us for the first pass at j = 0, where it reads
+// 4 MB, 4.4 us for an empty conditional pass, 10 us for the end of iteration; the fused launch takes 19 us there).
+// One persistent grid walks the (system, chunk) items in system order.  For its item a CTA stages the chunk of w
+// in shared memory, where it stays for the whole iteration, and per Gram-Schmidt pass: writes the chunk's partial
+// projections, waits at a per-system barrier, sums the partials of all chunks (FP64, chunk order), updates its
+// chunk of w, writes the chunk's squared norm and waits at the barrier again.  Every CTA of a system then forms
+// the same norm sums in the same order, so all take the same decision on the second pass (the norm-drop test of
+// k_dots) with no further round trip.  After the last pass each CTA scales its chunk into v_{j+1} and its FP16
+// operand, the chunk-0 CTA applies the rotations (finish_column), and the last CTA of the grid advances the
+// iteration index and sets the graph loop's condition.
+// Chunks are as long as one wave of the grid allows (1024 entries on the star: 512 items on 608 resident CTAs).
+// The update runs over the basis newest vector first: the projections have just streamed the whole basis, and
+// its last-read part is what L2 still holds (on the star, against oldest first: Arnoldi 7.7 against 8.8 ms per
+// step).  Trimming the grid so that each wave's basis chunks fit in L2 was slower (every extra wave repeats the
+// barrier chain with fewer loads in flight: 15.9 ms with 64 MB per wave).
+// Projections: with at least as many basis vectors as warps, warp w takes vectors w, w + 8, ... over the whole
+// chunk; with fewer (small j) each vector is split into NS sub-chunks so that every warp loads, and the
+// sub-chunk sums are combined in shared memory (basis precision, fixed order).  Update: each thread owns
+// CH / 512 pairs of entries over all basis vectors.
+//
+// Deadlock freedom: items are assigned statically, item q to CTA q mod G, with G >= chunks per system, so the
+// chunks of one system sit on distinct CTAs, and a CTA's earlier items belong to earlier systems.  Every CTA of
+// a system passes the same sequence of barriers (its decisions are uniform), so by induction on the system index
+// every barrier completes.  The grid is cooperative, so every CTA is resident.  Each wait is bounded
+// (wait_ns, default kCgsWaitNs): on expiry the kernel records it in st.err (the host returns BEM_ETIMEOUT) and goes on, and once
+// st.err is set no later wait of the run waits at all, so no CTA can hang and a failed run ends in bounded time.
+constexpr unsigned long long kCgsWaitNs = 500000000ull;   // 0.5 s (a barrier normally completes in microseconds)
+std::atomic<unsigned long long> g_cgs_wait_ns{kCgsWaitNs};   // for kernels launched from now on
+std::atomic<int> g_fused_on{1};
+
+__device__ __forceinline__ unsigned long long cgs_time() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// All threads of the CTA: wait until every chunk of system s has arrived.  st.sync[s] only grows (zeroed at the
+// start of a run), and the CTAs of a system pass their barriers in the same order, so barrier number b of the
+// iteration completes when the counter reaches a multiple of nchunk above the arrival.
+// Each system's counter has a cache line of its own, and a waiting thread polls it with a short sleep between
+// reads, so that the polls of one system's CTAs do not queue behind the arrivals of the others at one L2 slice.
+__device__ __forceinline__ void system_barrier(const KrylovState& st, int s, int nchunk, unsigned long long wait_ns) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int* ctr = st.sync + (size_t)s * kSyncStride;
+    __threadfence();
+    const int old = atomicAdd(ctr, 1);
+    const int target = (old / nchunk + 1) * nchunk;
+    if (*(volatile int*)ctr < target && *(volatile int*)st.err == 0) {
+      const unsigned long long t0 = cgs_time();
+      while (*(volatile int*)ctr < target) {
+        __nanosleep(100);
+        if (cgs_time() - t0 > wait_ns || *(volatile int*)st.err != 0) {
+          atomicCAS(st.err, 0, 1);
+          break;
+        }
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+}
+
+constexpr int kArnW = kThreads / 32;   // warps per CTA
+
+// dynamic shared memory: 3 (m + 1) entries of T (the column and the rotations for finish_column)
+template <typename T, int CH>
+__global__ void __launch_bounds__(kThreads, sizeof(T) == sizeof(float2) ? 4 : 1)
+    k_arnoldi(KrylovState st, int nchunk, int passes, double tol, unsigned long long wait_ns) {
+  using F = typename Vec<T>::acc_t;
+  constexpr int NS = CH >= 256 ? CH / 256 : 1;            // sub-chunks of a vector at small j
+  constexpr int PP = CH / 2 > kThreads ? CH / 2 / kThreads : 1;   // update: pairs per thread
+  extern __shared__ __align__(16) unsigned char fin_raw[];
+  T* sh_h = reinterpret_cast<T*>(fin_raw);
+  T* sh_c = sh_h + (st.m + 1);
+  T* sh_s = sh_c + (st.m + 1);
+  __shared__ __align__(16) T ws[CH];   // the chunk of w, for the whole iteration
+  __shared__ F hs[2 * kHsMax];         // projections of the current pass, basis precision
+  __shared__ F tp[2 * kArnW * NS];     // sub-chunk partials at small j
+  __shared__ double red[kArnW];
+  __shared__ F s_hn;
+  __shared__ int s_more;
+  __shared__ FinishIn s_in;
+  const int j = *(volatile const int*)st.jdev;   // read before this CTA's arrival below
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const size_t stride = (size_t)st.nrhs * st.n;
+  const size_t ldp = (size_t)st.m + 1;
+  int G = gridDim.x;
+  if (nchunk > G) {   // the launcher never does this: a system's chunks must sit on distinct CTAs
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicCAS(st.err, 0, 2);
+    G = 0;
+  }
+  const int items = st.nrhs * nchunk;
+  const int ns = j + 1 >= kArnW ? 1 : NS;   // sub-chunks per vector in this iteration
+  const int ntask = (j + 1) * ns;
+  const int sub_pairs = CH / 2 / ns;         // pairs of a projection task
+  for (int q = blockIdx.x; (int)blockIdx.x < G && q < items; q += G) {
+    const int s = q / nchunk, c = q - s * nchunk;
+    if (!st.active[s]) continue;   // the same for every chunk of the system
+    const int k0 = c * CH;
+    const T* V = static_cast<const T*>(st.V) + (size_t)s * st.n + k0;
+    const int nk = min(CH, st.n - k0);   // entries of this chunk (even)
+    {
+      const T* W = static_cast<const T*>(st.W) + (size_t)s * st.n + k0;
+      for (int qq = threadIdx.x; qq < CH / 2; qq += kThreads) {
+        T a, b;
+        if (2 * qq < nk) {
+          Pair<T>::load(W + 2 * qq, a, b);
+        } else {
+          a.x = a.y = b.x = b.y = 0;
+        }
+        Pair<T>::store(ws + 2 * qq, a, b);
+      }
+    }
+    if (c == 0 && warp == kArnW - 1) stage_rotations(st, s, j, tol, sh_c, sh_s, &s_in);
+    __syncthreads();
+    if (passes == 0 && warp == 0) {   // ||w||^2 of the chunk before projection (norm-drop test)
+      F nw = 0;
+      for (int qq = lane; qq < CH / 2; qq += 32) {
+        T a, b;
+        Pair<T>::load(ws + 2 * qq, a, b);
+        nw += (F)a.x * (F)a.x + (F)a.y * (F)a.y + (F)b.x * (F)b.x + (F)b.y * (F)b.y;
+      }
+      nw = warp_sum(nw);
+      if (lane == 0) st.wpart[(size_t)s * nchunk + c] = (double)nw;
+    }
+    for (int pass = 0;; ++pass) {
+      // ---- partial projections <v_i, w> over this chunk ----
+      for (int t = warp; t < ntask; t += kArnW) {
+        const int i = t / ns, sub = t - i * ns;
+        const int p0 = sub * sub_pairs;
+        const T* vi = V + (size_t)i * stride;
+        F px = 0, py = 0;
+#pragma unroll 4
+        for (int pp = p0 + lane; pp < p0 + sub_pairs; pp += 32) {
+          if (2 * pp < nk) {
+            T a, b, w0, w1;
+            Pair<T>::load(vi + 2 * pp, a, b);
+            Pair<T>::load(ws + 2 * pp, w0, w1);
+            px += (F)a.x * (F)w0.x + (F)a.y * (F)w0.y + (F)b.x * (F)w1.x + (F)b.y * (F)w1.y;
+            py += (F)a.x * (F)w0.y - (F)a.y * (F)w0.x + (F)b.x * (F)w1.y - (F)b.y * (F)w1.x;
+          }
+        }
+        const F hx = warp_sum(px), hy = warp_sum(py);
+        if (lane == 0) {
+          if (ns == 1) {
+            st.part[((size_t)s * nchunk + c) * ldp + i] = make_double2((double)hx, (double)hy);
+          } else {
+            tp[2 * t] = hx;
+            tp[2 * t + 1] = hy;
+          }
+        }
+      }
+      if (ns > 1) {
+        __syncthreads();
+        if ((int)threadIdx.x <= j) {
+          F hx = 0, hy = 0;
+          for (int u = 0; u < ns; ++u) {
+            hx += tp[2 * (threadIdx.x * ns + u)];
+            hy += tp[2 * (threadIdx.x * ns + u) + 1];
+          }
+          st.part[((size_t)s * nchunk + c) * ldp + threadIdx.x] = make_double2((double)hx, (double)hy);
+        }
+      }
+      system_barrier(st, s, nchunk, wait_ns);
+      // ---- h_i = sum over the chunks (FP64, chunk order); chunk 0 records the column ----
+      for (int i = threadIdx.x; i <= j; i += kThreads) {
+        double2 h = make_double2(0.0, 0.0);
+#pragma unroll 8
+        for (int cc = 0; cc < nchunk; ++cc) h = cadd(h, __ldcg(st.part + ((size_t)s * nchunk + cc) * ldp + i));
+        hs[2 * i] = (F)h.x;
+        hs[2 * i + 1] = (F)h.y;
+        if (c == 0) {
+          double2* Hj = st.H + ((size_t)s * st.m + j) * ldp;
+          const double2 tot = pass == 0 ? h : cadd(Hj[i], h);
+          Hj[i] = tot;
+          sh_h[i] = cx<T>(tot.x, tot.y);
+        }
+      }
+      __syncthreads();
+      // ---- w -= sum_i h_i v_i over this chunk; squared norm of the result ----
+      F nrm = 0;
+      {
+        F ax[PP], ay[PP], bx[PP], by[PP];
+#pragma unroll
+        for (int r = 0; r < PP; ++r) ax[r] = ay[r] = bx[r] = by[r] = 0;
+#pragma unroll 4
+        for (int ii = 0; ii <= j; ++ii) {   // newest first: those entries are the likeliest still in L2
+          const int i = j - ii;
+          const F hx = hs[2 * i], hy = hs[2 * i + 1];
+          const T* vi = V + (size_t)i * stride;
+#pragma unroll
+          for (int r = 0; r < PP; ++r) {
+            const int e = 2 * (threadIdx.x + r * kThreads);
+            if (e < nk) {
+              T a, b;
+              Pair<T>::load(vi + e, a, b);
+              ax[r] += hx * (F)a.x - hy * (F)a.y;
+              ay[r] += hx * (F)a.y + hy * (F)a.x;
+              bx[r] += hx * (F)b.x - hy * (F)b.y;
+              by[r] += hx * (F)b.y + hy * (F)b.x;
+            }
+          }
+        }
+#pragma unroll
+        for (int r = 0; r < PP; ++r) {
+          const int e = 2 * (threadIdx.x + r * kThreads);
+          if (e < nk) {
+            T w0, w1;
+            Pair<T>::load(ws + e, w0, w1);
+            w0.x -= ax[r]; w0.y -= ay[r];
+            w1.x -= bx[r]; w1.y -= by[r];
+            Pair<T>::store(ws + e, w0, w1);
+            nrm += w0.x * w0.x + w0.y * w0.y + w1.x * w1.x + w1.y * w1.y;
+          }
+        }
+      }
+      nrm = warp_sum(nrm);   // basis precision within the warp, FP64 across warps and chunks
+      if (lane == 0) red[warp] = (double)nrm;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w8 = 0; w8 < kArnW; ++w8) t += red[w8];
+        st.npart[(size_t)s * nchunk + c] = t;
+      }
+      system_barrier(st, s, nchunk, wait_ns);
+      // ---- the system's norms: the same sums in every CTA of the system ----
+      if (warp == 0) {
+        F t = 0;   // ||w|| in the basis precision, as k_step_end
+        double before = 0.0, after = 0.0;
+        for (int cc = lane; cc < nchunk; cc += 32) {
+          const double v = __ldcg(st.npart + (size_t)s * nchunk + cc);
+          t += (F)v;
+          after += v;
+          if (passes == 0) before += __ldcg(st.wpart + (size_t)s * nchunk + cc);
+        }
+        t = warp_sum(t);
+        after = warp_sum(after);
+        before = warp_sum(before);
+        if (lane == 0) {
+          s_hn = sqrt(t);
+          s_more = pass == 0 && (passes == 2 || (passes == 0 && (st.strict[s] || after < 0.01 * before)));
+        }
+      }
+      __syncthreads();
+      if (!s_more) break;
+    }
+    // ---- end of iteration: rotations (chunk 0), next basis vector ----
+    const F hn = s_hn;
+    if (c == 0 && warp == 0) finish_column(st, s, j, (double)hn, sh_h, sh_c, sh_s, &s_in);
+    if (hn > (F)0 && j + 1 < st.m) {
+      const F inv = (F)1 / hn;
+      T* Vn = static_cast<T*>(st.V) + ((size_t)(j + 1) * st.nrhs + s) * st.n + k0;
+      for (int qq = threadIdx.x; qq < CH / 2; qq += kThreads) {
+        const int e = 2 * qq;
+        if (e < nk) {
+          T a, b;
+          Pair<T>::load(ws + e, a, b);
+          a.x *= inv; a.y *= inv;
+          b.x *= inv; b.y *= inv;
+          Pair<T>::store(Vn + e, a, b);
+          if (st.b16hi) {
+            tc_write_b(static_cast<__half*>(st.b16hi), static_cast<__half*>(st.b16lo), st.ldb16, s, k0 + e,
+                       (float)a.x, (float)a.y);
+            tc_write_b(static_cast<__half*>(st.b16hi), static_cast<__half*>(st.b16lo), st.ldb16, s, k0 + e + 1,
+                       (float)b.x, (float)b.y);
+          }
+        }
+      }
+    }
+    __syncthreads();   // ws, hs, tp and the staged rotations are reused by the next item
+  }
+  // every CTA arrives (those without items too); the last one advances the index
+  if (threadIdx.x == 0) {
+    // with a graph loop the last CTA reads the active count: the rotations' decrements must be visible
+    __threadfence();
+    if (atomicAdd(st.arrive_all, 1) == (int)gridDim.x - 1) {
+      *st.arrive_all = 0;
+      *st.jdev = j + 1;
+      if (st.cond_handle) {
+        __threadfence();
+        cudaGraphSetConditional((cudaGraphConditionalHandle)st.cond_handle, atomicAdd(st.n_active, 0) > 0 ? 1u : 0u);
+      }
+    }
+  }
+}
+
 // Least squares: back substitution of the triangularised Hessenberg system, one CTA per system.
 __global__ void __launch_bounds__(kBsThreads) k_lsq(KrylovState st) {
   __shared__ double2 sg[kFinishMaxM], sinv[kFinishMaxM], sy;
@@ -746,7 +861,7 @@ cudaError_t start_t(const KrylovState& st, const double2* r0, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(st.n_active, 0, sizeof(int), s);
   if (e != cudaSuccess) return e;
   if (st.sync) {
-    e = cudaMemsetAsync(st.sync, 0, st.nrhs * sizeof(int), s);
+    e = cudaMemsetAsync(st.sync, 0, (size_t)st.nrhs * kSyncStride * sizeof(int), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(st.err, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
   }
@@ -757,26 +872,22 @@ cudaError_t start_t(const KrylovState& st, const double2* r0, cudaStream_t s) {
 
 // passes: 1 (classical Gram-Schmidt), 2 (twice, CGS2) or 0 (once, then again only for the systems that the
 // norm-drop test flags).
-// Bytes of basis chunks the fused kernel keeps in flight.  Measured on the 64-system star (Arnoldi phase per
-// step): 32 MB 13.5 ms, 64 MB 9.3 ms, 128 MB 7.86 ms, unlimited 7.96 ms (the two-kernel pass: 8.1 ms).  Fewer
-// CTAs than the device holds cost more memory parallelism than the L2 reuse they buy, so the budget only trims
-// the grid at large j; the fused pass gains by one launch per pass and one early-exit launch less.
-#ifndef BEM_CGS_L2_BUDGET_MB
-#define BEM_CGS_L2_BUDGET_MB 128
-#endif
-constexpr long long kCgsL2Budget = (long long)BEM_CGS_L2_BUDGET_MB << 20;
-
-// Resident CTAs of the fused kernel on this device (0 if its launch cannot be cooperative).
+// Resident CTAs of k_arnoldi<T, CH> on this device with the shared memory of the largest Krylov dimension
+// (0 if its launch cannot be cooperative).
 template <typename T, int CH>
-int cgs_grid() {
+int arn_grid() {
   static std::atomic<int> cache[64];
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
   int g = cache[dev].load(std::memory_order_relaxed);
   if (g != 0) return g > 0 ? g : 0;
+  const int dyn = 3 * kHsMax * (int)sizeof(T);
   int coop = 0, per = 0;
   if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_cgs<T, CH>, kThreads, 0) != cudaSuccess || per <= 0) {
+      cudaFuncSetAttribute(k_arnoldi<T, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_arnoldi<T, CH>, kThreads, dyn) != cudaSuccess ||
+      per <= 0) {
+    cudaGetLastError();
     cache[dev].store(-1, std::memory_order_relaxed);
     return 0;
   }
@@ -786,37 +897,56 @@ int cgs_grid() {
 }
 
 template <typename T, int CH>
-cudaError_t cgs_pass(const KrylovState& st, int pass, int mode, cudaStream_t s) {
+int arn_fit(const KrylovState& st, int& best) {   // 1: every item in one wave; best: CH if usable at all
   const int nc = (st.n + CH - 1) / CH;
-  const int G = std::min(cgs_grid<T, CH>(), nc * st.nrhs);
+  const int G = arn_grid<T, CH>();
+  if (G <= 0 || nc > G || nc > krylov_nchunk(st.n)) return 0;
+  best = CH;
+  return (long long)nc * st.nrhs <= G;
+}
+
+// Chunk length of the fused iteration kernel: the shortest of 64 ... 1024 entries whose items all fit in one
+// wave of its grid (one pass of the per-item chain), else the longest usable one; 0 if none is usable (no
+// cooperative launch, the state lacks the barrier counters, or a system's chunks exceed the grid).
+template <typename T>
+int arn_chunk(const KrylovState& st) {
+  if (!st.sync || !st.err || st.m + 1 > kHsMax || !g_fused_on.load(std::memory_order_relaxed)) return 0;
+  int best = 0;
+  if (arn_fit<T, 64>(st, best)) return 64;
+  if (arn_fit<T, 128>(st, best)) return 128;
+  if (arn_fit<T, 256>(st, best)) return 256;
+  if (arn_fit<T, 512>(st, best)) return 512;
+  if (arn_fit<T, 1024>(st, best)) return 1024;
+  return best;
+}
+
+template <typename T, int CH>
+cudaError_t arn_launch(const KrylovState& st, int passes, double tol, cudaStream_t s) {
+  const int nc = (st.n + CH - 1) / CH;
+  const int G = std::min(arn_grid<T, CH>(), nc * st.nrhs);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(G);
   cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = 3 * (size_t)(st.m + 1) * sizeof(T);
   cfg.stream = s;
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeCooperative;
   at[0].val.cooperative = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_cgs<T, CH>, st, nc, pass, mode, kCgsL2Budget);
-}
-
-// The fused pass is used where its grid can hold every chunk of a system (so its barrier is safe) and the
-// state carries its counters.
-template <typename T, int CH>
-bool cgs_usable(const KrylovState& st) {
-  const int nc = (st.n + CH - 1) / CH;
-  const int G = cgs_grid<T, CH>();
-  return st.sync && st.err && G > 0 && nc <= std::min(G, nc * st.nrhs) && nc <= 64;
+  return cudaLaunchKernelEx(&cfg, k_arnoldi<T, CH>, st, nc, passes, tol,
+                            g_cgs_wait_ns.load(std::memory_order_relaxed));
 }
 
 template <typename T>
-bool fused_t(const KrylovState& st) {
-  switch (chunk_of(st.n, st.nrhs)) {
-    case 512: return cgs_usable<T, 512>(st);
-    case 256: return cgs_usable<T, 256>(st);
-    case 128: return cgs_usable<T, 128>(st);
-    default: return cgs_usable<T, 64>(st);
+cudaError_t step_t(const KrylovState& st, int passes, double tol, cudaStream_t s) {
+  switch (arn_chunk<T>(st)) {
+    case 64: return arn_launch<T, 64>(st, passes, tol, s);
+    case 128: return arn_launch<T, 128>(st, passes, tol, s);
+    case 256: return arn_launch<T, 256>(st, passes, tol, s);
+    case 512: return arn_launch<T, 512>(st, passes, tol, s);
+    case 1024: return arn_launch<T, 1024>(st, passes, tol, s);
+    default: return cudaErrorNotSupported;
   }
 }
 
@@ -824,20 +954,8 @@ template <typename T>
 cudaError_t orth_t(const KrylovState& st, int passes, cudaStream_t s) {
   const int ch = chunk_of(st.n, st.nrhs);
   const int np = passes == 1 ? 1 : 2;
-  const bool fused = fused_t<T>(st);
   for (int p = 0; p < np; ++p) {
     const int mode = p == 0 ? 0 : (passes == 0 ? 1 : 2);
-    cudaError_t e = cudaSuccess;
-    if (fused) {
-      switch (ch) {
-        case 512: e = cgs_pass<T, 512>(st, p, mode, s); break;
-        case 256: e = cgs_pass<T, 256>(st, p, mode, s); break;
-        case 128: e = cgs_pass<T, 128>(st, p, mode, s); break;
-        default: e = cgs_pass<T, 64>(st, p, mode, s); break;
-      }
-      if (e != cudaSuccess) return e;
-      continue;
-    }
     switch (ch) {
       case 512: orth_pass<T, 512>(st, p, mode, s); break;
       case 256: orth_pass<T, 256>(st, p, mode, s); break;
@@ -880,11 +998,17 @@ cudaError_t krylov_start(const KrylovState& st, const double2* r0, double, cudaS
 cudaError_t krylov_orthogonalise(const KrylovState& st, int passes, cudaStream_t s) {
   return st.basis_fp32 ? orth_t<float2>(st, passes, s) : orth_t<double2>(st, passes, s);
 }
-int krylov_fused(const KrylovState& st) { return st.basis_fp32 ? fused_t<float2>(st) : fused_t<double2>(st); }
+void krylov_set_wait_ns(unsigned long long ns) { g_cgs_wait_ns.store(ns ? ns : kCgsWaitNs); }
+void krylov_set_fused(int on) { g_fused_on.store(on ? 1 : 0); }
+int krylov_fused(const KrylovState& st) {
+  return st.basis_fp32 ? arn_chunk<float2>(st) : arn_chunk<double2>(st);
+}
+cudaError_t krylov_fused_step(const KrylovState& st, int passes, double tol, cudaStream_t s) {
+  return st.basis_fp32 ? step_t<float2>(st, passes, tol, s) : step_t<double2>(st, passes, tol, s);
+}
 int krylov_orth_launches(const KrylovState& st, int passes) {
   const int ch = chunk_of(st.n, st.nrhs);
   const int nc = (st.n + ch - 1) / ch;
-  if (krylov_fused(st)) return passes == 1 ? 1 : 2;    // one fused launch per pass
   return (passes == 1 ? 1 : 2) * (nc <= 32 ? 2 : 3);   // projections, [reduction,] update per pass
 }
 cudaError_t krylov_finish_step(const KrylovState& st, double tol, cudaStream_t s) {

@@ -1,8 +1,9 @@
 """Failure paths through the C interface: iteration limits (BEM_ENOCONV with the best iterate written) and
 bounded device waits that run out (BEM_ETIMEOUT, with the context still usable afterwards).
 
-No test here faults, traps or hangs the GPU: the timeout is provoked by a short main-loop wait limit of
-the tensor-core product, whose drain waits keep their full limit.
+No test here faults, traps or hangs the GPU: the timeouts are provoked by a short main-loop wait limit of
+the tensor-core product, whose drain waits keep their full limit, and by a short barrier wait limit of the
+fused GMRES iteration kernel, whose waits then give up and let the kernel run on with every access in bounds.
 """
 import numpy as np
 import pytest
@@ -115,4 +116,35 @@ def test_tensor_core_wait_expiry_returns_etimeout_and_the_next_call_succeeds(B):
     assert err < 5e-6
     with pytest.raises(B.BemError):
         B.bem_test_set_wait_limit(-1.0)
+    p.close()
+
+
+def test_gram_schmidt_barrier_expiry_returns_etimeout_and_the_next_solve_succeeds(B):
+    """A barrier wait limit of 1 ns makes the per-system barrier waits of the fused iteration kernel run out:
+    the kernel records the expiry and goes on without waiting (every later wait of the run is skipped), the
+    solve runs to its iteration limit and returns BEM_ETIMEOUT.  A problem created after the default is
+    restored solves to the tolerance (mixed path: no tensor-core waits are involved)."""
+    import torch
+    wp = W.cfg_circle_c1(256)
+    ang = np.array([0.0, 0.7, 1.9])
+    x = torch.zeros((3, 512), dtype=torch.complex128, device="cuda")
+    try:
+        B.bem_test_set_wait_limit(1e-9)
+        p = B.Problem.from_workload(wp, prec="mixed", tol=1e-10, max_iter=30, max_refine=1)
+        with pytest.raises(B.BemError) as e:
+            p.bem_solve_planewave(ang, x)
+        assert e.value.status == B.BEM_ETIMEOUT
+        assert "barrier" in B.bem_last_error()
+        p.close()
+    finally:
+        B.bem_test_set_wait_limit(0.0)
+    torch.cuda.synchronize()
+    p = B.Problem.from_workload(wp, prec="mixed", tol=1e-10)
+    st, it, rs = p.bem_solve_planewave(ang, x)
+    assert st == B.BEM_OK and np.all(rs <= 1e-10)
+    A = O.assemble(wp, Q=4)
+    xs = x.cpu().numpy()
+    for r, t in enumerate(ang):
+        b = O.rhs_planewave(wp, t)
+        assert np.linalg.norm(b - A @ xs[r]) / np.linalg.norm(b) < 1e-9
     p.close()
