@@ -555,22 +555,27 @@ bem_status gmres_run(bem_problem* p, Solver& sv, const double2* r0, double2* x, 
   const int* gate = st.n_active;
   // decided (and the fused kernel's attributes set) before any graph capture below
   const bool fused = krylov_fused(st) != 0;
+  // the fused kernel sums the tensor-core product's stream-K partials itself (no reduction launch)
+  if (use_tc && fused && !matvec_tc_partials(p->d_A16, n2, nrhs, sv.tcws, &st.tc)) st.tc = TcPartials{};
   // one iteration: product, orthogonalisation, rotations and scaling of the next basis vector (the kernels read
   // the iteration index from the device; only the non-tensor-core products take the basis vector's address)
   int launched = 0;   // iterations queued by the host loop below (the graph path does not count them)
   auto iteration = [&](int j) -> cudaError_t {
     void* Vj = static_cast<char*>(st.V) + (size_t)j * nrhs * n2 * tb;
     cudaError_t e;
-    if (use_tc) {   // the GEMM (B = V_j, written by the Krylov kernels), then its stream-K reduction
+    if (use_tc) {   // the GEMM (B = V_j, written by the Krylov kernels), then its stream-K reduction (which the
+                    // fused iteration kernel does itself as it stages w)
       {
         Phase ph(p, BEM_PH_MATVEC, s, 1);
         e = launch_matvec_tc(p->d_A16, n2, nrhs, nullptr, static_cast<float2*>(st.W), sv.tcws, sv.tcws_bytes, s,
                              gate, 1);
       }
       if (e != cudaSuccess) return e;
-      Phase ph(p, BEM_PH_REDUCE, s, 1);
-      e = launch_matvec_tc(p->d_A16, n2, nrhs, nullptr, static_cast<float2*>(st.W), sv.tcws, sv.tcws_bytes, s,
-                           gate, 2);
+      if (!st.tc.part) {
+        Phase ph(p, BEM_PH_REDUCE, s, 1);
+        e = launch_matvec_tc(p->d_A16, n2, nrhs, nullptr, static_cast<float2*>(st.W), sv.tcws, sv.tcws_bytes, s,
+                             gate, 2);
+      }
     } else {
       Phase ph(p, BEM_PH_MATVEC, s, 1);
       if (p->o.matrix_free && fp32) {   // stored rows and recomputed rows, column by column
@@ -737,7 +742,7 @@ bem_status gmres_run(bem_problem* p, Solver& sv, const double2* r0, double2* x, 
     const int worked = *std::max_element(it.begin(), it.end());
     const int gated = std::max(0, launched - worked);
     p->launches[BEM_PH_MATVEC] -= gated;
-    if (use_tc) p->launches[BEM_PH_REDUCE] -= gated;
+    if (use_tc && !st.tc.part) p->launches[BEM_PH_REDUCE] -= gated;
   }
   return BEM_OK;
 }

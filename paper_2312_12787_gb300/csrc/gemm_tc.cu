@@ -18,8 +18,9 @@
 //
 // Work split (stream-K): the (row tile, K-step) pairs of the whole product are cut into G equal contiguous
 // ranges, G a multiple of the SM count with G >= row tiles, so every CTA does the same amount of work and
-// touches at most two row tiles.  Each CTA writes one partial 128 x 128 tile per row tile it touches; a
-// reduction kernel adds the partials of each tile in CTA order (deterministic) and applies the scales.
+// touches at most two row tiles.  Each CTA writes one partial 128 x 128 tile per row tile it touches
+// (column-major, tc_operand.cuh); a reduction kernel, or the GMRES iteration kernel as it stages w, adds the
+// partials of each tile in CTA order (deterministic) and applies the scales.
 //
 // CTA roles (256 threads): warp 0 = TMA producer, warp 1 = TMEM owner and MMA issuer, warps 4-7 =
 // accumulator readers (TMEM lanes 0-127).  3 pipeline stages of 64 KB (A_hi, A_lo, B_hi, B_lo tiles of
@@ -42,8 +43,8 @@ namespace bem {
 
 namespace {
 
-constexpr int kM = 128;              // rows per tile (UMMA M)
-constexpr int kN = 128;              // Bt rows: 64 real parts + 64 imaginary parts
+constexpr int kM = kTcM;             // rows per tile (UMMA M)
+constexpr int kN = kTcN;             // Bt rows: 64 real parts + 64 imaginary parts
 constexpr int kKs = 64;              // FP16 elements per K-step = 128 bytes = one swizzle row
 constexpr int kStages = 3;
 constexpr int kSeg = 4;              // K-steps per accumulation segment (256 K values)
@@ -326,11 +327,12 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_arrive(su32(&bars->acce[b]));
       ++seg;
       if (tile_end) {
-        float4* dst = reinterpret_cast<float4*>(partial + (((size_t)c * 2 + slot) * kM + q * 32 + lane) * kN);
+        // column-major partial tile: for each column the warp's 32 rows are 128 contiguous bytes
+        float* dst = partial + ((size_t)c * 2 + slot) * kM * kN + q * 32 + lane;
 #pragma unroll
-        for (int j = 0; j < kN / 4; ++j) {
-          dst[j] = make_float4(acc[4 * j], acc[4 * j + 1], acc[4 * j + 2], acc[4 * j + 3]);
-          acc[4 * j] = acc[4 * j + 1] = acc[4 * j + 2] = acc[4 * j + 3] = 0.f;
+        for (int j = 0; j < kN; ++j) {
+          dst[(size_t)j * kM] = acc[j];
+          acc[j] = 0.f;
         }
         ++slot;
       }
@@ -428,72 +430,35 @@ __global__ void __launch_bounds__(256) k_tc_prep_a(const float2* __restrict__ A,
 }
 
 // Y[s][r] = (sum of the partials of r's row tile) / (rsc[r] tsc[s]), the real part from column s of D and
-// the imaginary part from column 64 + s.  One CTA per kRedRows rows: the partial rows are read along D's columns
-// (coalesced), summed in CTA order (deterministic), transposed in shared memory and written along r.
-// 8 rows per CTA keep enough CTAs in flight for the loads.
-constexpr int kRedRows = 8;
+// the imaginary part from column 64 + s.  One CTA per kRedRows rows of one row tile; lane = row, so every load
+// of a partial column and every store of Y is 128 contiguous bytes; warp w takes systems w, w + 8, ...; the
+// partials are summed in CTA order (deterministic).
+constexpr int kRedRows = 32;
 __global__ void __launch_bounds__(256) k_tc_reduce(const float* __restrict__ partial, int n, int nrhs, int kpt,
                                                    long long total, int G, const float* __restrict__ rsc,
                                                    const float* __restrict__ tsc, float2* __restrict__ y,
                                                    const int* gate) {
   pdl_enter();
   if (gate && *gate == 0) return;
-  constexpr int kMaxCover = 64;
-  __shared__ float2 tile[kMaxRhs][kRedRows + 1];
-  __shared__ const float* src[kMaxCover];   // partial tiles covering this row tile, in CTA order
+  __shared__ int src[kTcMaxCover];   // partial tiles covering this row tile, in CTA order (2 c + slot)
   __shared__ int nsrc;
   const int r0 = blockIdx.x * kRedRows;
-  const int t = r0 / kM;
-  if (threadIdx.x == 0) {
-    // CTAs whose range [total c / G, total (c+1) / G) meets row tile t's K-steps [t kpt, (t+1) kpt).  32-bit
-    // unsigned divisions where total G fits (every practical size): 64-bit divisions are long sequences.
-    int m = 0;
-    if ((unsigned long long)total * (unsigned long long)G < (1ull << 32)) {
-      const unsigned tot = (unsigned)total, g = (unsigned)G, lo = (unsigned)t * (unsigned)kpt, hi = lo + (unsigned)kpt;
-      unsigned c0 = (lo * g) / tot;
-      while (c0 > 0 && tot * c0 / g > lo) --c0;
-      while (tot * (c0 + 1) / g <= lo) ++c0;
-      for (unsigned c = c0; c < g && m < kMaxCover; ++c) {
-        const unsigned beg = tot * c / g;
-        if (beg >= hi) break;
-        const int slot = (beg / (unsigned)kpt == (unsigned)t) ? 0 : 1;
-        src[m++] = partial + ((size_t)c * 2 + slot) * kM * kN;
-      }
-    } else {
-      const long long lo = (long long)t * kpt, hi = lo + kpt;
-      int c0 = (int)((lo * G) / total);
-      while (c0 > 0 && total * c0 / G > lo) --c0;
-      while (total * (c0 + 1) / G <= lo) ++c0;
-      for (int c = c0; c < G && total * c / G < hi && m < kMaxCover; ++c) {
-        const int slot = ((total * c / G) / kpt == t) ? 0 : 1;
-        src[m++] = partial + ((size_t)c * 2 + slot) * kM * kN;
-      }
-    }
-    nsrc = m;
-  }
+  if (threadIdx.x == 0) nsrc = tc_cover(r0 / kM, kpt, total, G, src, kTcMaxCover);
   __syncthreads();
   const int ns = nsrc;
-#pragma unroll
-  for (int e = threadIdx.x; e < kRedRows * kN; e += 256) {
-    const int rr = e / kN, col = e % kN;
-    const int r = r0 + rr;
-    float v = 0.f;
-    if (r < n) {
-      const size_t off = (size_t)(r % kM) * kN + col;
-      for (int q = 0; q < ns; ++q) v += src[q][off];
+  const int r = r0 + (threadIdx.x & 31);
+  if (r >= n) return;
+  const int rr = r % kM;
+  const float rs = rsc[r];
+  for (int sidx = threadIdx.x >> 5; sidx < nrhs; sidx += 8) {
+    float re = 0.f, im = 0.f;
+    for (int q = 0; q < ns; ++q) {
+      const float* t = partial + (size_t)src[q] * kM * kN + rr;
+      re += t[(size_t)sidx * kM];
+      im += t[(size_t)(64 + sidx) * kM];
     }
-    if (col < 64) tile[col][rr].x = v;
-    else tile[col - 64][rr].y = v;
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < kMaxRhs * kRedRows; e += 256) {
-    const int sidx = e / kRedRows, rr = e % kRedRows;
-    const int r = r0 + rr;
-    if (sidx < nrhs && r < n) {
-      const float inv = 1.f / (rsc[r] * (tsc ? tsc[sidx] : 1.f));   // a power of two: exact
-      const float2 v = tile[sidx][rr];
-      y[(size_t)sidx * n + r] = make_float2(v.x * inv, v.y * inv);
-    }
+    const float inv = 1.f / (rs * (tsc ? tsc[sidx] : 1.f));   // a power of two: exact
+    y[(size_t)sidx * n + r] = make_float2(re * inv, im * inv);
   }
 }
 
@@ -581,6 +546,18 @@ bool matvec_tc_supported(int n, int nrhs) {
 size_t matvec_tc_workspace_bytes(int n, int nrhs) {
   if (nrhs < 2 || nrhs > kMaxRhs || n < kM) return 0;
   return off_err(n) + 64;
+}
+
+bool matvec_tc_partials(const void* a16, int n, int nrhs, void* ws, TcPartials* out) {
+  if (!matvec_tc_supported(n, nrhs) || !out) return false;
+  const size_t ld = ld16(n);
+  out->part = reinterpret_cast<const float*>(static_cast<const char*>(ws) + off_part(n));
+  out->rsc = reinterpret_cast<const float*>(static_cast<const char*>(a16) +
+                                            ((2 * (size_t)n * ld * 2 + 255) & ~(size_t)255));
+  out->kpt = (2 * n + kKs - 1) / kKs;
+  out->total = (long long)((n + kM - 1) / kM) * out->kpt;
+  out->G = grid_of(n);
+  return true;
 }
 
 int* matvec_tc_error_word(void* ws, int n, int nrhs) {

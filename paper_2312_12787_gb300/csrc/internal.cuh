@@ -169,8 +169,6 @@ cudaError_t residual_split_preload();
 // Set-up of the no-allocation residual on the current device (noalloc.cu): looks up its static scratch
 // array and loads its kernels.  Called where the library allocates anyway (assembly of mixed problems).
 bem_status noalloc_setup();
-// tcgen05 tensor-core GEMM Y = A X (A c32, X / Y c32, nrhs <= 64).  Returns cudaErrorNotSupported if the
-// shape is not supported by the kernel.
 // tcgen05 tensor-core GEMM Y = A X (X / Y complex FP32, 2 <= nrhs <= 64) on the FP16 split copy of A that
 // launch_tc_prepare_a makes (matvec_tc_a16_bytes(n) bytes, from the complex FP32 matrix A, n x n).  Returns
 // cudaErrorNotSupported if the shape is not supported.  The kernel records a bounded-wait expiry in an
@@ -194,6 +192,10 @@ size_t matvec_tc_workspace_bytes(int n, int nrhs);
 // Device word where the tensor-core kernel records a bounded-wait expiry (0 = none) inside ws.
 int* matvec_tc_error_word(void* ws, int n, int nrhs);
 bool matvec_tc_supported(int n, int nrhs);
+struct TcPartials;
+// Where a stage-1 product leaves its stream-K partials (layout in tc_operand.cuh), for a consumer that sums them
+// itself instead of the stage-2 reduction; false if the shape is not supported.
+bool matvec_tc_partials(const void* a16, int n, int nrhs, void* ws, TcPartials* out);
 
 // Element-wise conversions between complex FP64 and FP32 blocks; column 2-norms of an FP64 block.
 cudaError_t launch_convert_c64_c32(const double2* in, float2* out, size_t count, cudaStream_t s);
@@ -205,6 +207,16 @@ cudaError_t launch_sub_c32(double2* r, const float2* y, size_t count, cudaStream
 cudaError_t launch_column_norms(const double2* v, int n, int ncol, double* out, cudaStream_t s);
 
 // GMRES building blocks for nrhs systems sharing one matrix; see krylov.cu.
+// The stream-K partials of a tensor-core product (tc_operand.cuh): y[s][r] = (sum over the partial tiles that
+// cover r's row tile, in CTA order) / rsc[r] for a B operand of scale 1.
+struct TcPartials {
+  const float* part = nullptr;   // null: none (the product's result is in the output block)
+  const float* rsc = nullptr;    // row scales of A's FP16 split (powers of two)
+  int kpt = 0;                   // K-steps per row tile
+  int G = 0;                     // CTAs of the product
+  long long total = 0;           // (row tile, K-step) pairs
+};
+
 constexpr int kSyncStride = 32;   // ints between the barrier counters of two systems
 struct KrylovState {
   int n;            // unknowns per system
@@ -245,6 +257,9 @@ struct KrylovState {
   void* b16hi;
   void* b16lo;
   size_t ldb16;
+  // when tc.part is set (fused iteration kernel after a tensor-core product): w is the sum of the product's
+  // stream-K partials, which the kernel adds up itself (W is not written)
+  TcPartials tc;
 };
 int krylov_nchunk(int n);
 cudaError_t krylov_start(const KrylovState& st, const double2* r0, double tol_unused, cudaStream_t s);

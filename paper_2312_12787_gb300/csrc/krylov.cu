@@ -557,6 +557,9 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == sizeof(float2) ? 4 : 1)
   __shared__ F s_hn;
   __shared__ int s_more;
   __shared__ FinishIn s_in;
+  constexpr int NT = CH >= kTcM ? CH / kTcM : 1;   // row tiles of the product per chunk
+  __shared__ int cov[NT][kTcMaxCover];             // their stream-K partial tiles (when st.tc.part is set)
+  __shared__ int ncov[NT];
   const int j = *(volatile const int*)st.jdev;   // read before this CTA's arrival below
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const size_t stride = (size_t)st.nrhs * st.n;
@@ -576,7 +579,41 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == sizeof(float2) ? 4 : 1)
     const int k0 = c * CH;
     const T* V = static_cast<const T*>(st.V) + (size_t)s * st.n + k0;
     const int nk = min(CH, st.n - k0);   // entries of this chunk (even)
-    {
+    if (st.tc.part) {
+      // w = the tensor-core product's stream-K partials of rows k0 .. k0 + nk - 1, summed in CTA order and
+      // scaled by 1 / rsc (the arithmetic of k_tc_reduce, whose launch this replaces)
+      if ((int)threadIdx.x < NT) {
+        const int t = k0 / kTcM + threadIdx.x;
+        ncov[threadIdx.x] = t * kTcM < st.n ? tc_cover(t, st.tc.kpt, st.tc.total, st.tc.G, cov[threadIdx.x],
+                                                       kTcMaxCover)
+                                            : 0;
+      }
+      __syncthreads();
+      for (int qq = threadIdx.x; qq < CH / 2; qq += kThreads) {
+        T a, b;
+        a.x = a.y = b.x = b.y = 0;
+        if (2 * qq < nk) {
+          const int r = k0 + 2 * qq;   // rows r and r + 1 (one row tile: r is even)
+          const int ti = r / kTcM - k0 / kTcM, rr = r % kTcM;
+          float ax = 0.f, ay = 0.f, bx = 0.f, by = 0.f;
+          for (int u = 0; u < ncov[ti]; ++u) {
+            const float* P = st.tc.part + (size_t)cov[ti][u] * kTcM * kTcN + rr;
+            const float2 re = *reinterpret_cast<const float2*>(P + (size_t)s * kTcM);
+            const float2 im = *reinterpret_cast<const float2*>(P + (size_t)(64 + s) * kTcM);
+            ax += re.x;
+            bx += re.y;
+            ay += im.x;
+            by += im.y;
+          }
+          const float ia = 1.f / st.tc.rsc[r], ib = 1.f / st.tc.rsc[r + 1];   // powers of two: exact
+          a.x = ax * ia;
+          a.y = ay * ia;
+          b.x = bx * ib;
+          b.y = by * ib;
+        }
+        Pair<T>::store(ws + 2 * qq, a, b);
+      }
+    } else {
       const T* W = static_cast<const T*>(st.W) + (size_t)s * st.n + k0;
       for (int qq = threadIdx.x; qq < CH / 2; qq += kThreads) {
         T a, b;
