@@ -323,6 +323,23 @@ cudaError_t matvec_partial_f32(bem_problem* p, const float2* x, float2* y, cudaS
   return e;
 }
 
+// Whether any Bessel argument k r of an assembly can reach Hankel's expansion (x >= 128, where the kernel needs the
+// arguments reduced by pi/2): every collocation point and every quadrature node lie in the bounding box of the
+// element end points, so r is at most its diagonal; a margin of 1 below 128 covers the rounding of k r.
+bool asym_reachable(const bem_problem* p) {
+  if (p->ax.empty()) return false;
+  double x0 = p->ax[0], x1 = x0, y0 = p->ay[0], y1 = y0;
+  for (size_t e = 0; e < p->ax.size(); ++e) {
+    x0 = std::min({x0, p->ax[e], p->bx[e]});
+    x1 = std::max({x1, p->ax[e], p->bx[e]});
+    y0 = std::min({y0, p->ay[e], p->by[e]});
+    y1 = std::max({y1, p->ay[e], p->by[e]});
+  }
+  double kmax = 0.0;
+  for (int d = 0; d < p->dom.n; ++d) kmax = std::max(kmax, std::fabs(p->dom.k[d]));
+  return kmax * std::hypot(x1 - x0, y1 - y0) >= 127.0;
+}
+
 bem_status assemble_impl(bem_problem* p, cudaStream_t s, bool force = false) {
   bem_status st = check_ready(p);
   if (st != BEM_OK) return st;
@@ -343,7 +360,7 @@ bem_status assemble_impl(bem_problem* p, cudaStream_t s, bool force = false) {
       }
       Phase ph(p, BEM_PH_ASSEMBLE, s, 1);
       CU(launch_assemble_rows(p->elem(), p->n, p->dom, make_quad(p->o.quad_order), p->o.form, p->Es, p->d_Hs,
-                              (size_t)2 * p->n, s));
+                              (size_t)2 * p->n, s, asym_reachable(p)));
     }
     p->mat_dirty = false;
     return BEM_OK;
@@ -367,7 +384,8 @@ bem_status assemble_impl(bem_problem* p, cudaStream_t s, bool force = false) {
   const Quad q = make_quad(p->o.quad_order);
   {
     Phase ph(p, BEM_PH_ASSEMBLE, s, 1);
-    CU(launch_assemble(p->elem(), p->n, p->dom, q, p->o.form, mixed ? 1 : 0, p->d_A, p->d_Alo, (size_t)2 * p->n, s));
+    CU(launch_assemble(p->elem(), p->n, p->dom, q, p->o.form, mixed ? 1 : 0, p->d_A, p->d_Alo, (size_t)2 * p->n, s,
+                       asym_reachable(p)));
   }
   p->A_mixed = mixed;
   p->mat_dirty = false;

@@ -87,14 +87,16 @@ __device__ __forceinline__ void store_pair(int n, int i, int j, const C2 (&out)[
 #endif
 // Element rows i < rows (rows = n: the whole matrix; fewer: the stored part of a partly recomputed matrix, rows
 // i and lower + i).
-template <int MIXED>
+// ASYM = false: no Bessel argument of the launch reaches Hankel's expansion (decided on the host from the
+// geometry's extent and the largest wavenumber), so the reduction of the arguments by pi/2 is left out.
+template <int MIXED, bool ASYM>
 __global__ void __launch_bounds__(256, BEM_ASM_CTAS_PER_SM) k_assemble(ElemDev e, int n, DomTab dom, Quad q, int form, void* Aout,
                                                    void* Aloout, size_t lda, int rows, int lower) {
   const int j = blockIdx.x * 32 + threadIdx.x;
   const int i = blockIdx.y * 8 + threadIdx.y;
   if (i >= rows || j >= n) return;
   C2 out[2][2];
-  assemble_pair_f2(e, dom, q, form, i, j, out);
+  assemble_pair_f2<ASYM>(e, dom, q, form, i, j, out);
   store_pair<MIXED>(n, i, j, out, Aout, Aloout, lda, lower);
 }
 
@@ -337,23 +339,25 @@ cudaError_t launch_elements(const ElemDev& e, int n, cudaStream_t s) {
 }
 
 cudaError_t launch_assemble(const ElemDev& e, int n, const DomTab& dom, const Quad& q, int form, int store_mixed,
-                            void* A, void* Alo, size_t lda, cudaStream_t s) {
+                            void* A, void* Alo, size_t lda, cudaStream_t s, bool asym) {
   if (const cudaError_t te = ensure_bessel_table(); te != cudaSuccess) return te;
   dim3 blk(32, 8);
   dim3 grd((n + 31) / 32, (n + 7) / 8);
-  if (store_mixed) k_assemble<1><<<grd, blk, 0, s>>>(e, n, dom, q, form, A, Alo, lda, n, n);
-  else k_assemble<0><<<grd, blk, 0, s>>>(e, n, dom, q, form, A, Alo, lda, n, n);
+  if (!store_mixed) k_assemble<0, true><<<grd, blk, 0, s>>>(e, n, dom, q, form, A, Alo, lda, n, n);
+  else if (asym) k_assemble<1, true><<<grd, blk, 0, s>>>(e, n, dom, q, form, A, Alo, lda, n, n);
+  else k_assemble<1, false><<<grd, blk, 0, s>>>(e, n, dom, q, form, A, Alo, lda, n, n);
   return cudaGetLastError();
 }
 
 cudaError_t launch_assemble_rows(const ElemDev& e, int n, const DomTab& dom, const Quad& q, int form, int rows,
-                                 float2* H, size_t lda, cudaStream_t s) {
+                                 float2* H, size_t lda, cudaStream_t s, bool asym) {
   if (rows <= 0) return cudaSuccess;
   if (rows > n) return cudaErrorInvalidValue;
   if (const cudaError_t te = ensure_bessel_table(); te != cudaSuccess) return te;
   dim3 blk(32, 8);
   dim3 grd((n + 31) / 32, (rows + 7) / 8);
-  k_assemble<1><<<grd, blk, 0, s>>>(e, n, dom, q, form, H, nullptr, lda, rows, rows);
+  if (asym) k_assemble<1, true><<<grd, blk, 0, s>>>(e, n, dom, q, form, H, nullptr, lda, rows, rows);
+  else k_assemble<1, false><<<grd, blk, 0, s>>>(e, n, dom, q, form, H, nullptr, lda, rows, rows);
   return cudaGetLastError();
 }
 

@@ -730,7 +730,9 @@ struct BesselArg {
   F2 rb;
 };
 
-BEM_HD void bessel_arg_base(double xb, BesselArg& a) {
+// asym = false: the caller knows that no argument x_b + x_c reaches Hankel's expansion (x >= kTabXMax), so the
+// reduction by pi/2 (five FP64 operations) is skipped and rb, qb are zero.
+BEM_HD void bessel_arg_base(double xb, BesselArg& a, bool asym = true) {
   a.xb = xb;
   // kb = (xb - 2) 32 rounded to an integer (magic-number rounding; |kb| < 2^31 for the arguments that occur)
   const double t = fma(xb - 2.0, 32.0, 0x1.8p52);
@@ -741,7 +743,12 @@ BEM_HD void bessel_arg_base(double xb, BesselArg& a) {
   a.kb = (int)kd;
 #endif
   a.hb = f2_from_bits(xb - fma(kd, kTabStep, 2.0));   // exact: x_kb is a multiple of 1/32
-  a.rb = f2_from_bits(reduce_pio2(xb, a.qb));
+  if (asym) {
+    a.rb = f2_from_bits(reduce_pio2(xb, a.qb));
+  } else {
+    a.rb = F2{0.f, 0.f};
+    a.qb = 0;
+  }
 }
 
 // J0, Y0, J1, Y1 at x = a.xb + XC (XC small), X = x in double-float (branch choice and amplitudes).

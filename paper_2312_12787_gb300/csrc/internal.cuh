@@ -104,8 +104,10 @@ __host__ __device__ __forceinline__ float2 cdotc(float2 a, float2 b) {
 
 // ---- launchers (each returns cudaGetLastError() of its launch) -----------------------------------
 cudaError_t launch_elements(const ElemDev& e, int n, cudaStream_t s);
+// asym = false: the caller has checked that no Bessel argument reaches Hankel's expansion (asym_reachable in
+// api.cu), so the mixed-store kernel leaves out the reduction of the arguments by pi/2.
 cudaError_t launch_assemble(const ElemDev& e, int n, const DomTab& dom, const Quad& q, int form, int store_mixed,
-                            void* A, void* Alo, size_t lda, cudaStream_t s);
+                            void* A, void* Alo, size_t lda, cudaStream_t s, bool asym = true);
 // y = A x without a stored matrix (entries recomputed in FP64), n elements, nrhs columns of 2n.
 // `gate` (optional, device int): when it reads 0 the product is skipped (every system of the block has
 // converged; the solver queues several iterations ahead of its convergence check).
@@ -118,7 +120,7 @@ cudaError_t launch_matvec_free_f32(const ElemDev& e, int n, const DomTab& dom, c
 // Element rows i < rows of the matrix as complex FP32 (hi only) into a compact block: row i at H + i * lda,
 // row n + i at H + (rows + i) * lda.
 cudaError_t launch_assemble_rows(const ElemDev& e, int n, const DomTab& dom, const Quad& q, int form, int rows,
-                                 float2* H, size_t lda, cudaStream_t s);
+                                 float2* H, size_t lda, cudaStream_t s, bool asym = true);
 // Tiles of a problem with n elements for tile height ty (4, 8 or 16 rows of element pairs x 32 columns).
 long long assemble_batched_tiles(int n, int ty);
 cudaError_t launch_assemble_batched(const AsmJob* jobs_dev, int njobs, const long long* tile_prefix_dev,

@@ -133,6 +133,36 @@ template <> struct Pair<double2> {
   __device__ static __forceinline__ void store(double2* p, double2 a, double2 b) { p[0] = a; p[1] = b; }
 };
 
+// Loads with an L2 eviction policy (createpolicy / ld.global.L2::cache_hint, PTX ISA 7.4+).
+__device__ __forceinline__ unsigned long long l2_evict_last() {
+  unsigned long long p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ unsigned long long l2_evict_first() {
+  unsigned long long p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+
+template <typename T> struct PairHint;
+template <> struct PairHint<float2> {
+  __device__ static __forceinline__ void load(const float2* p, float2& a, float2& b, unsigned long long pol) {
+    float4 v;
+    asm volatile("ld.global.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "l"(p), "l"(pol));
+    a = make_float2(v.x, v.y);
+    b = make_float2(v.z, v.w);
+  }
+};
+template <> struct PairHint<double2> {
+  __device__ static __forceinline__ void load(const double2* p, double2& a, double2& b, unsigned long long pol) {
+    asm volatile("ld.global.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;" : "=d"(a.x), "=d"(a.y) : "l"(p), "l"(pol));
+    asm volatile("ld.global.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;" : "=d"(b.x), "=d"(b.y) : "l"(p + 1), "l"(pol));
+  }
+};
+
 // Partial projections <v_i, w> over one chunk of CH entries: warp w takes basis vectors i = w, w+8, ...;
 // lane l holds the pairs k = chunk start + 2 (32 p + l), p < CH/64, so each load instruction of the warp
 // moves 512 (FP32) or 1024 (FP64) contiguous bytes.  Products, lane sums and the warp reduction in the basis
@@ -538,6 +568,11 @@ __device__ __forceinline__ void system_barrier(const KrylovState& st, int s, int
 }
 
 constexpr int kArnW = kThreads / 32;   // warps per CTA
+// L2 bytes of basis chunks that the projections mark evict-last for the update's second read.  Star, 64 systems,
+// per step (Arnoldi phase): no hints 7.0 ms; every load evict-first 7.4; 32 MB kept 6.94, 64 MB 6.84, 96 MB
+// 6.82, 128 MB 6.98 (another box: 96 MB 6.97); leaving the older vectors or the update at normal priority
+// instead of evict-first gave the same or worse (7.0, 7.2).
+constexpr long long kArnKeepBytes = 96ll << 20;
 
 // dynamic shared memory: 3 (m + 1) entries of T (the column and the rotations for finish_column)
 template <typename T, int CH>
@@ -570,6 +605,13 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == sizeof(float2) ? 4 : 1)
     G = 0;
   }
   const int items = st.nrhs * nchunk;
+  // The projections mark the newest `keep` vectors of each chunk evict-last in L2 (the update reads them first)
+  // and the others evict-first, so that the update's second read finds the kept ones there; the update's own
+  // loads are evict-first (nothing reads them again before the next iteration's projections).
+  const unsigned long long pol_last = l2_evict_last(), pol_first = l2_evict_first();
+  const int items_live = min(items, G);
+  const long long keep_ll = items_live > 0 ? kArnKeepBytes / ((long long)items_live * CH * (long long)sizeof(T)) : 0;
+  const int keep = (int)min(keep_ll, (long long)(j + 1));
   const int ns = j + 1 >= kArnW ? 1 : NS;   // sub-chunks per vector in this iteration
   const int ntask = (j + 1) * ns;
   const int sub_pairs = CH / 2 / ns;         // pairs of a projection task
@@ -648,7 +690,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == sizeof(float2) ? 4 : 1)
         for (int pp = p0 + lane; pp < p0 + sub_pairs; pp += 32) {
           if (2 * pp < nk) {
             T a, b, w0, w1;
-            Pair<T>::load(vi + 2 * pp, a, b);
+            PairHint<T>::load(vi + 2 * pp, a, b, i > j - keep ? pol_last : pol_first);
             Pair<T>::load(ws + 2 * pp, w0, w1);
             px += (F)a.x * (F)w0.x + (F)a.y * (F)w0.y + (F)b.x * (F)w1.x + (F)b.y * (F)w1.y;
             py += (F)a.x * (F)w0.y - (F)a.y * (F)w0.x + (F)b.x * (F)w1.y - (F)b.y * (F)w1.x;
@@ -707,7 +749,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == sizeof(float2) ? 4 : 1)
             const int e = 2 * (threadIdx.x + r * kThreads);
             if (e < nk) {
               T a, b;
-              Pair<T>::load(vi + e, a, b);
+              PairHint<T>::load(vi + e, a, b, pol_first);   // not read again this iteration
               ax[r] += hx * (F)a.x - hy * (F)a.y;
               ay[r] += hx * (F)a.y + hy * (F)a.x;
               bx[r] += hx * (F)b.x - hy * (F)b.y;

@@ -120,6 +120,9 @@ BEM_HD void self_pair(const ElemDev& e, const DomTab& dom, int form, int i, C2 (
 // where sS, sD, sDs, sN are the Gauss sums of H0, (zh.n_j) H1, (zh.n_i) H1 and
 // H1/r (n_i.n_j - 2 (zh.n_i)(zh.n_j)) + k H0 (zh.n_i)(zh.n_j) over the element j (zh = (x_i - y)/r).
 // out[half][0] multiplies u_j, out[half][1] multiplies w_j in row half*N + i.
+// kAsym = false: the caller guarantees that no argument k r of the launch reaches Hankel's expansion
+// (k (|d| + h_j / 2) < kTabXMax - 1 for every pair), so the reduction of the arguments by pi/2 is left out.
+template <bool kAsym = true>
 BEM_HD void assemble_pair_f2(const ElemDev& e, const DomTab& dom, const Quad& q, int form, int i, int j,
                              C2 (&out)[2][2]) {
   if (i == j) {
@@ -169,10 +172,11 @@ BEM_HD void assemble_pair_f2(const ElemDev& e, const DomTab& dom, const Quad& q,
     DNI = f2_from_bits(dx * nxi + dy * nyi);
     TNI = f2_from_bits(txj * nxi + tyj * nyi);
   }
-  // the Bessel arguments' FP64 part k |d| (table offset and reduction by pi/2 once per pair and domain)
+  // the Bessel arguments' FP64 part k |d| (table offset and, where the expansion can be reached, reduction by
+  // pi/2, once per pair and domain)
   BesselArg arg0{}, arg1{};
-  if (sg[0] != 0.f) bessel_arg_base(kk[0] * dn, arg0);
-  if (sg[1] != 0.f) bessel_arg_base(kk[1] * dn, arg1);
+  if (sg[0] != 0.f) bessel_arg_base(kk[0] * dn, arg0, kAsym);
+  if (sg[1] != 0.f) bessel_arg_base(kk[1] * dn, arg1, kAsym);
 
   C2 sS[2], sD[2], sDs[2], sN[2];
 #pragma unroll

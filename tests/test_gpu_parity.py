@@ -71,8 +71,16 @@ def test_assembly_forms_match_oracle(B, torch, form):
         assert blk <= ENTRY_BLOCK_TOL and rl <= ENTRY_REL_TOL, (form, blk, rl)
 
 
-def test_assembly_mixed_split_matches_oracle(B, torch):
-    wp = W.Problem(k=[20.0, 30.0], eps=[1.0, 2.25], segments=[W.Segment(W.star(300, 0.3, 5), P=0, M=1, closed=True)])
+@pytest.mark.parametrize("name,mk", [
+    # k times the bounding-box diagonal below 127: the kernel without the reduction by pi/2
+    ("star300", lambda: W.Problem(k=[20.0, 30.0], eps=[1.0, 2.25],
+                                  segments=[W.Segment(W.star(300, 0.3, 5), P=0, M=1, closed=True)])),
+    # far above it (arguments up to ~280 reach Hankel's expansion): the kernel with the reduction
+    ("ellipse250_k40", lambda: W.Problem(k=[40.0, 70.0], eps=[1.0, (70.0 / 40.0) ** 2],
+                                         segments=[W.Segment(W.ellipse(250, 4.0), P=0, M=1, closed=True)])),
+], ids=["star300", "ellipse250_k40"])
+def test_assembly_mixed_split_matches_oracle(B, torch, name, mk):
+    wp = mk()
     ref = O.assemble(wp, Q=4)
     m = gpu_matrix(B, torch, wp, prec="mixed")
     blk, rl = block_errors(m["full"], ref)
