@@ -907,7 +907,7 @@ bem_status solve_impl(bem_problem* p, int nrhs, const double2* b, double2* x, in
       // each column's inner run only needs to reach what the outer tolerance still asks of it
       std::vector<double> inner_res(nrhs), tols(nrhs);
       for (int r = 0; r < nrhs; ++r)
-        tols[r] = rn[r] > 0 ? std::max(p->o.inner_tol, 0.3 * p->o.tol * bn[r] / rn[r]) : 1.0;
+        tols[r] = rn[r] > 0 ? std::max(p->o.inner_tol, kRefineMargin * p->o.tol * bn[r] / rn[r]) : 1.0;
       const std::vector<int> it_before = iters;
       const std::vector<double> rn_before = rn;
       // Once the residual is below 1e-4 of ||b||, it is updated, r -= A d, with the inner solves' own product of

@@ -479,7 +479,7 @@ __global__ void kv_loop_decide(VDev d) {
     d.state[s] = 2;
     d.flag[s] = 0;
   } else {
-    d.tol[s] = fmax(d.itol, 0.3 * d.otol * bn / rn);
+    d.tol[s] = fmax(d.itol, kRefineMargin * d.otol * bn / rn);
   }
 }
 
@@ -769,7 +769,7 @@ bem_status refine_finished(bem_batch* b) {
       sl.state = 2;
       e.dirty = true;
     } else {
-      b->htol[s] = std::max(e.o.inner_tol, 0.3 * e.o.tol * sl.bnorm / e.h_rnorm[s]);
+      b->htol[s] = std::max(e.o.inner_tol, kRefineMargin * e.o.tol * sl.bnorm / e.h_rnorm[s]);
       restart.push_back(s);
     }
   }

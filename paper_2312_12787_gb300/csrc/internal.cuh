@@ -220,6 +220,13 @@ struct TcPartials {
 };
 
 constexpr int kSyncStride = 32;   // ints between the barrier counters of two systems
+
+// Mixed refinement: each inner solve is asked for kRefineMargin x (the residual reduction that the outer
+// tolerance still needs).  The inner solves' residual estimates match the updated residuals closely (on the
+// 64-system star the final residuals land at margin x tol: 3.0e-9, 5.0e-9, 7.0e-9, 9.0e-9 for 0.3, 0.5, 0.7,
+// 0.9), so the margin only guards against an optimistic estimate; a column that still misses the tolerance gets
+// another refinement step.  0.9 against 0.3: 116 against 121 iterations, 27.1 against 28.2 ms per step.
+constexpr double kRefineMargin = 0.9;
 struct KrylovState {
   int n;            // unknowns per system
   int nrhs;         // systems
