@@ -1030,6 +1030,7 @@ bem_status problem_prepare_batched(bem_problem* p, cudaStream_t s, AsmJob* job, 
   job->dom = p->dom;
   job->A = p->d_A;
   job->Alo = p->d_Alo;
+  job->asym = asym_reachable(p) ? 1 : 0;
   p->A_mixed = 1;
   p->mat_dirty = false;
   p->a16_dirty = true;

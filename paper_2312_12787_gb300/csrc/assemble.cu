@@ -144,9 +144,10 @@ __global__ void __launch_bounds__(256, BEM_ASM_CTAS_PER_SM) k_matvec_free(ElemDe
 
 // Many problems in one launch: blockIdx.x walks a list of 32 x TY tiles of all problems (problem found by
 // binary search in the tile prefix sums); each problem keeps its own elements, domain table and matrices.
-// About 24 resident warps per SM, as for k_assemble.
-template <int MIXED, int TY>
-__global__ void __launch_bounds__(32 * TY, 768 / (32 * TY)) k_assemble_batched(const AsmJob* __restrict__ jobs, int njobs,
+// 16 resident warps per SM (128 registers a thread), as for k_assemble: at 24 warps (85 registers) the pair code
+// spills.  ASYM as for k_assemble, for the whole batch.
+template <int MIXED, int TY, bool ASYM>
+__global__ void __launch_bounds__(32 * TY, 512 / (32 * TY)) k_assemble_batched(const AsmJob* __restrict__ jobs, int njobs,
                                                               const long long* __restrict__ tile_prefix, Quad q,
                                                               int form) {
   const long long t = blockIdx.x;
@@ -163,7 +164,7 @@ __global__ void __launch_bounds__(32 * TY, 768 / (32 * TY)) k_assemble_batched(c
   const int i = ty * TY + threadIdx.y;
   if (i >= jb.n || j >= jb.n) return;
   C2 out[2][2];
-  assemble_pair_f2(jb.e, jb.dom, q, form, i, j, out);
+  assemble_pair_f2<ASYM>(jb.e, jb.dom, q, form, i, j, out);
   store_pair<MIXED>(jb.n, i, j, out, jb.A, jb.Alo, (size_t)2 * jb.n, jb.n);
 }
 
@@ -383,15 +384,16 @@ long long assemble_batched_tiles(int n, int ty) { return (long long)((n + 31) / 
 
 cudaError_t launch_assemble_batched(const AsmJob* jobs_dev, int njobs, const long long* tile_prefix_dev,
                                    long long total_tiles, const Quad& q, int form, int store_mixed, int ty,
-                                   cudaStream_t s) {
+                                   cudaStream_t s, bool asym) {
   if (total_tiles <= 0) return cudaSuccess;
   if (total_tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
+  if (!store_mixed) return cudaErrorNotSupported;   // the batch engine stores the mixed form only
   if (const cudaError_t te = ensure_bessel_table(); te != cudaSuccess) return te;
   const unsigned grid = (unsigned)total_tiles;
 #define BEM_ASM_CASE(TYV)                                                                                  \
   case TYV:                                                                                                \
-    if (store_mixed) k_assemble_batched<1, TYV><<<grid, dim3(32, TYV), 0, s>>>(jobs_dev, njobs, tile_prefix_dev, q, form); \
-    else k_assemble_batched<0, TYV><<<grid, dim3(32, TYV), 0, s>>>(jobs_dev, njobs, tile_prefix_dev, q, form); \
+    if (asym) k_assemble_batched<1, TYV, true><<<grid, dim3(32, TYV), 0, s>>>(jobs_dev, njobs, tile_prefix_dev, q, form); \
+    else k_assemble_batched<1, TYV, false><<<grid, dim3(32, TYV), 0, s>>>(jobs_dev, njobs, tile_prefix_dev, q, form); \
     break;
   switch (ty) {
     BEM_ASM_CASE(4)

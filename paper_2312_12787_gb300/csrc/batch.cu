@@ -1016,17 +1016,28 @@ BEM_API bem_status bem_batch_admit(bem_batch* b, int n, bem_problem* const* prob
     slots_out[i] = s;
   }
   if (jobs.empty()) return all ? BEM_OK : report_error(BEM_ENOMEM, "no slot or pool space free");
-  // ---- one launch assembles every admitted problem; the tile height is tuned on first use ----
+  // ---- the admitted problems' matrices: the problems whose Bessel arguments stay below Hankel's expansion
+  // first, then the others, one launch per group (the first group's kernel leaves out the reduction of the
+  // arguments by pi/2); the tile height is tuned on first use ----
+  std::vector<AsmJob> ajobs;
+  ajobs.reserve(jobs.size());
+  for (const AsmJob& jb : jobs)
+    if (!jb.asym) ajobs.push_back(jb);
+  const int nplain = (int)ajobs.size();
+  for (const AsmJob& jb : jobs)
+    if (jb.asym) ajobs.push_back(jb);
+  const int group_first[2] = {0, nplain}, group_count[2] = {nplain, (int)ajobs.size() - nplain};
   AsmJob* djobs = nullptr;
   long long* dpref = nullptr;
-  BCU(cudaMallocAsync(&djobs, jobs.size() * sizeof(AsmJob), e.st));
-  BCU(cudaMallocAsync(&dpref, jobs.size() * sizeof(long long), e.st));
-  BCU(cudaMemcpyAsync(djobs, jobs.data(), jobs.size() * sizeof(AsmJob), cudaMemcpyHostToDevice, e.st));
+  BCU(cudaMallocAsync(&djobs, ajobs.size() * sizeof(AsmJob), e.st));
+  BCU(cudaMallocAsync(&dpref, ajobs.size() * sizeof(long long), e.st));
+  BCU(cudaMemcpyAsync(djobs, ajobs.data(), ajobs.size() * sizeof(AsmJob), cudaMemcpyHostToDevice, e.st));
   const Quad q = make_quad_host(e.o.quad_order);
-  auto prefix_for = [&](int ty, std::vector<long long>& pref) {
-    pref.resize(jobs.size());
+  // tile prefix sums of jobs [first, first + count), from 0; returns the tiles of the range
+  auto prefix_for = [&](int ty, int first, int count, std::vector<long long>& pref) {
+    pref.resize(count);
     long long acc = 0;
-    for (size_t i = 0; i < jobs.size(); ++i) { pref[i] = acc; acc += assemble_batched_tiles(jobs[i].n, ty); }
+    for (int i = 0; i < count; ++i) { pref[i] = acc; acc += assemble_batched_tiles(ajobs[first + i].n, ty); }
     return acc;
   };
   std::vector<long long> pref;
@@ -1035,12 +1046,14 @@ BEM_API bem_status bem_batch_admit(bem_batch* b, int n, bem_problem* const* prob
   if (e.asm_ty == 0 && dev >= 0 && dev < kTunedDevs) e.asm_ty = g_tuned_ty[dev].load(std::memory_order_relaxed);
   if (e.asm_ty == 0) {
     // Tile height (rows of element pairs per 32-column tile): time 4, 8 and 16 once per device on the first
-    // problems of this batch (about an eighth of its element pairs, at least one problem), keep the fastest.
+    // problems of the larger group of this batch (about an eighth of its element pairs, at least one problem),
+    // keep the fastest.
+    const int g = group_count[0] >= group_count[1] ? 0 : 1;
     long long pairs = 0, all_pairs = 0;
-    for (const AsmJob& jb : jobs) all_pairs += (long long)jb.n * jb.n;
+    for (int i = 0; i < group_count[g]; ++i) all_pairs += (long long)ajobs[group_first[g] + i].n * ajobs[group_first[g] + i].n;
     int kjobs = 0;
-    while (kjobs < (int)jobs.size() && (kjobs == 0 || pairs * 8 < all_pairs)) {
-      pairs += (long long)jobs[kjobs].n * jobs[kjobs].n;
+    while (kjobs < group_count[g] && (kjobs == 0 || pairs * 8 < all_pairs)) {
+      pairs += (long long)ajobs[group_first[g] + kjobs].n * ajobs[group_first[g] + kjobs].n;
       ++kjobs;
     }
     const int cand[3] = {4, 8, 16};
@@ -1050,12 +1063,10 @@ BEM_API bem_status bem_batch_admit(bem_batch* b, int n, bem_problem* const* prob
     BCU(cudaEventCreate(&t0));
     BCU(cudaEventCreate(&t1));
     for (int c = 0; c < 3; ++c) {
-      prefix_for(cand[c], pref);
-      long long tot = 0;
-      for (int i = 0; i < kjobs; ++i) tot += assemble_batched_tiles(jobs[i].n, cand[c]);
+      const long long tot = prefix_for(cand[c], group_first[g], kjobs, pref);
       BCU(cudaMemcpyAsync(dpref, pref.data(), pref.size() * sizeof(long long), cudaMemcpyHostToDevice, e.st));
       BCU(cudaEventRecord(t0, e.st));
-      BCU(launch_assemble_batched(djobs, kjobs, dpref, tot, q, e.o.form, 1, cand[c], e.st));
+      BCU(launch_assemble_batched(djobs + group_first[g], kjobs, dpref, tot, q, e.o.form, 1, cand[c], e.st, g == 1));
       BCU(cudaEventRecord(t1, e.st));
       BCU(cudaEventSynchronize(t1));
       float ms = 0.f;
@@ -1067,10 +1078,14 @@ BEM_API bem_status bem_batch_admit(bem_batch* b, int n, bem_problem* const* prob
     e.asm_ty = best_ty;
     if (dev >= 0 && dev < kTunedDevs) g_tuned_ty[dev].store(best_ty, std::memory_order_relaxed);
   }
-  {
-    const long long tot = prefix_for(e.asm_ty, pref);
-    BCU(cudaMemcpyAsync(dpref, pref.data(), pref.size() * sizeof(long long), cudaMemcpyHostToDevice, e.st));
-    BCU(launch_assemble_batched(djobs, (int)jobs.size(), dpref, tot, q, e.o.form, 1, e.asm_ty, e.st));
+  std::vector<long long> gpref[2];
+  for (int g = 0; g < 2; ++g) {
+    if (group_count[g] == 0) continue;
+    const long long tot = prefix_for(e.asm_ty, group_first[g], group_count[g], gpref[g]);
+    BCU(cudaMemcpyAsync(dpref + group_first[g], gpref[g].data(), gpref[g].size() * sizeof(long long),
+                        cudaMemcpyHostToDevice, e.st));
+    BCU(launch_assemble_batched(djobs + group_first[g], group_count[g], dpref + group_first[g], tot, q, e.o.form, 1,
+                                e.asm_ty, e.st, g == 1));
   }
   BCU(cudaStreamSynchronize(e.st));   // pref / jobs are host-local
   cudaFreeAsync(djobs, e.st);

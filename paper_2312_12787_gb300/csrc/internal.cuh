@@ -79,6 +79,7 @@ struct AsmJob {
   DomTab dom;
   void* A;         // hi (mixed) or full (FP64) matrix, 2n x 2n row-major
   void* Alo;       // remainder (mixed) or null
+  int asym;        // 1 if a Bessel argument of this problem can reach Hankel's expansion (x >= 128)
 };
 
 // ---- complex helpers ---------------------------------------------------------------------------
@@ -123,9 +124,10 @@ cudaError_t launch_assemble_rows(const ElemDev& e, int n, const DomTab& dom, con
                                  float2* H, size_t lda, cudaStream_t s, bool asym = true);
 // Tiles of a problem with n elements for tile height ty (4, 8 or 16 rows of element pairs x 32 columns).
 long long assemble_batched_tiles(int n, int ty);
+// Mixed store only (store_mixed = 0 returns cudaErrorNotSupported); asym = false when no job's asym is set.
 cudaError_t launch_assemble_batched(const AsmJob* jobs_dev, int njobs, const long long* tile_prefix_dev,
                                    long long total_tiles, const Quad& q, int form, int store_mixed, int ty,
-                                   cudaStream_t s);
+                                   cudaStream_t s, bool asym = true);
 cudaError_t launch_rhs_planewave(const ElemDev& e, int n, const DomTab& dom, int form, int nrhs,
                                  const double* angles_dev, double2* b, cudaStream_t s);
 // scratch: 2 * nang * n complex entries (the per-angle element sums).
