@@ -265,13 +265,16 @@ typedef enum {
   BEM_PH_ASSEMBLE = 1,  /* a3-a5: matrix entries */
   BEM_PH_RHS = 2,       /* a2 */
   BEM_PH_MATVEC = 3,    /* a6 / a11: GEMV, SIMT GEMM or tensor-core GEMM */
-  BEM_PH_ARNOLDI = 4,   /* a7: projections, updates, norms */
-  BEM_PH_GIVENS = 5,    /* a8: Hessenberg column, rotations, residual estimate, basis scaling */
+  BEM_PH_ARNOLDI = 4,   /* a7: projections, updates, norms; where the iteration tail is one cooperative launch,
+                           also the rotations, the next basis vector and the stream-K sums of the product */
+  BEM_PH_GIVENS = 5,    /* a8: Hessenberg column, rotations, residual estimate, basis scaling (start of a run;
+                           every iteration only on the separate-kernel path) */
   BEM_PH_UPDATE = 6,    /* a9: least squares and x += V y */
   BEM_PH_RESIDUAL = 7,  /* a9: refinement residual b - (hi + lo) x (its norms count as OTHER) */
   BEM_PH_FARFIELD = 8,  /* a10 */
   BEM_PH_OTHER = 9,     /* conversions, copies, column norms, the FP16 split copy of A */
-  BEM_PH_REDUCE = 10,   /* a11: stream-K reduction of the tensor-core GEMM inside GMRES (the GEMM is MATVEC) */
+  BEM_PH_REDUCE = 10,   /* a11: stream-K reduction of the tensor-core GEMM inside GMRES (the GEMM is MATVEC);
+                           none where the cooperative iteration kernel sums the partials itself */
   BEM_PH_COUNT = 11
 } bem_phase;
 BEM_API bem_status bem_profile_enable(bem_problem* p, int on);

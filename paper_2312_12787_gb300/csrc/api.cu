@@ -648,7 +648,7 @@ bem_status gmres_run(bem_problem* p, Solver& sv, const double2* r0, double2* x, 
       cudaError_t ce = cudaErrorNotSupported;
       if (!p->ig_noloop) {
         // One graph for the whole inner solve: a WHILE node whose body is kLoopIters iterations; the
-        // end-of-iteration kernel sets the loop condition to (some system still iterating), so the host does
+        // iteration's last kernel sets the loop condition to (some system still iterating), so the host does
         // not poll and at most kLoopIters - 1 gated iterations run past convergence (one iteration per body
         // made each pass through the loop cost more than the iterations it saved).
         cudaGraph_t graph = nullptr;
