@@ -3,7 +3,9 @@
 // double- and hypersingular operators (paper Sec. 3.3, eq. fundamental_sol: G = (i/4) H0^(1)(k r)).
 //
 // Written from the published mathematics (NIST DLMF), not from any library's internals:
-//   * x < BEM_X_SERIES:   ascending power series, DLMF 10.2.2 (J_n) and 10.8.1 (Y_n, n = 0, 1).
+//   * x < BEM_X_SERIES:   ascending power series, DLMF 10.2.2 (J_n) and 10.8.1 (Y_n, n = 0, 1).  (The
+//                         double-float path of the kernels takes the series only below 1 and Taylor steps from a
+//                         table on 1 <= x < 128, below.)
 //   * x < BEM_X_ASYMP:    Miller's backward recurrence for J_n (DLMF 3.6(vi), 10.74(iv)), normalised by
 //                         1 = J0 + 2 sum J_2k (DLMF 10.12.4), and the Neumann expansions
 //                         Y0 = (2/pi)(ln(x/2)+gamma) J0 - (4/pi) sum_k (-1)^k J_2k / k  (a Neumann expansion, DLMF 10.23(ii))
@@ -459,12 +461,15 @@ constexpr SeriesCoef make_series_coef() {
 
 // The ascending series of bessel01_series with tabulated coefficients, in FP64 (x < 2, a few per cent of
 // the evaluations), converted to double-float.
+// The double-float path takes the series only below kTabXMin = 1 (the table serves 1 <= x < 128): t = x^2/4 <= 1/4,
+// so terms m = 0 .. 9 suffice (the first one left out, t^10/(10!)^2 H_10, is below 2e-20).
+constexpr int kSeriesTermsF2 = 10;
 BEM_HD void bessel01_series_f2(double x, Bessel01F2& b) {
   constexpr SeriesCoef C = make_series_coef();
   const double t = 0.25 * x * x;
   double e0 = 1.0, e1 = 1.0, sj0 = 1.0, sj1 = 1.0, sy0 = 0.0, sy1 = 1.0;
 #pragma unroll   // a fixed count: constant indices make the coefficients immediates (no table in memory)
-  for (int m = 1; m < kSeriesTerms; ++m) {
+  for (int m = 1; m < kSeriesTermsF2; ++m) {
     e0 *= -t * C.inv_mm[m];
     e1 *= -t * C.inv_mm1[m];
     sj0 += e0;
@@ -581,21 +586,25 @@ BEM_HD void bessel01_asymp_f2x(double x, F2 X, Bessel01F2& b) {
   bessel01_asymp_f2r(X, f2_from_bits(r), quad, b);
 }
 
-// ---- tabulated values and Taylor steps on 2 <= x < 128 -------------------------------------------------
-// J0, Y0, J1, Y1 at x_k = 2 + k/32 (computed once on the host with the FP64 routines above, error ~1e-15 of
+// ---- tabulated values and Taylor steps on 1 <= x < 128 -------------------------------------------------
+// J0, Y0, J1, Y1 at x_k = 1 + k/32 (computed once on the host with the FP64 routines above, error ~1e-15 of
 // |H|), stored in double-float with 1/x_k.  Between grid points both pairs obey the same first-order system
 // Z0' = -Z1, Z1' = Z0 - Z1/x (DLMF 10.6.2), so with Z0(x_k + h) = sum a_n h^n and Z1(x_k + h) = sum b_n h^n the
 // Taylor coefficients follow from
 //   a_{n+1} = -b_n / (n+1),   b_{n+1} = (a_n - c_n) / (n+1),   c_n = (b_n - c_{n-1}) / x_k,
 // where c_n are the coefficients of Z1/(x_k + h).  With |h| <= 1/64, eight orders leave a remainder below
-// 1e-16; orders 0-3 run in double-float, orders 4-7 (below 3e-9 of the value) in FP32.  This replaces the
+// 1e-16 from x = 2 on and below ~4e-15 at x = 1 (the derivatives of Y_n grow like n!/x^n toward the origin:
+// (h/x)^8 = 64^-8); orders 0-3 run in double-float, orders 4-7 (below 3e-9 of the value from x = 2 on, ~1e-7 at
+// x = 1) in FP32.  This replaces the
 // recurrence of Miller's algorithm (56 steps) and Hankel's expansion up to x = 128 by about a fifth of the
 // arithmetic of the expansion (whose double-float sine, cosine and four Horner sums take ~1000 FP32 operations
 // per evaluation); the table costs 128 bytes per grid point, read through the L1 cache (the lanes of a warp
 // take neighbouring elements, so their arguments share a few grid points).
 constexpr double kTabStep = 1.0 / 32.0;
-constexpr int kTabN = 4033;          // x_k = 2 + k / 32, k = 0 .. 4032: [2, 128]
-constexpr float kTabXMax = 128.0f;   // the table serves 2 <= x < 128 (516 KB of device memory)
+constexpr double kTabX0 = 1.0;       // first grid point
+constexpr int kTabN = 4065;          // x_k = 1 + k / 32, k = 0 .. 4064: [1, 128]
+constexpr float kTabXMin = 1.0f;     // the table serves 1 <= x < 128 (520 KB of device memory); the series below
+constexpr float kTabXMax = 128.0f;
 // One grid point x_k: for each pair (J0, J1) and (Y0, Y1) the Taylor coefficients of orders 0..3 of Z0 (a_n)
 // and Z1 (b_n) as double-float (a_1 = -b_0 is not stored), c_3 (FP32, the start of the FP32 orders) and
 // 1/x_k (FP32).  The coefficients depend on x_k only, so they are made once on the host in FP64.
@@ -641,9 +650,10 @@ inline const BesselTabEntry* bessel_tab_host() {
   static const std::vector<BesselTabEntry> tab = [] {
     std::vector<BesselTabEntry> t(kTabN);
     for (int k = 0; k < kTabN; ++k) {
-      const double x = 2.0 + k * kTabStep;
+      const double x = kTabX0 + k * kTabStep;
       Bessel01 b;
-      if (x < BEM_X_ASYMP) bessel01_miller(x, b);
+      if (x < BEM_X_SERIES) bessel01_series(x, b);
+      else if (x < BEM_X_ASYMP) bessel01_miller(x, b);
       else bessel01_asymp(x, b);
       taylor_coefs_host(x, b.j0, b.j1, t[k].j);
       taylor_coefs_host(x, b.y0, b.y1, t[k].y);
@@ -690,9 +700,9 @@ BEM_HD void taylor_pair(float4 q0, float4 q1, float4 q2, float4 q3, F2 H, F2& ou
 
 BEM_HD int tab_index(float xh) {
 #if defined(__CUDA_ARCH__)
-  return __float2int_rn((xh - 2.f) * 32.f);
+  return __float2int_rn((xh - (float)kTabX0) * 32.f);
 #else
-  return (int)lrintf((xh - 2.f) * 32.f);
+  return (int)lrintf((xh - (float)kTabX0) * 32.f);
 #endif
 }
 
@@ -712,7 +722,7 @@ BEM_HD void bessel01_taylor_f2h(int k, F2 H, Bessel01F2& b) {
 
 BEM_HD void bessel01_taylor_f2(double x, F2 X, Bessel01F2& b) {
   const int k = tab_index(X.h);
-  const double h = x - (2.0 + k * kTabStep);   // exact: x and the grid point agree to within 1/64
+  const double h = x - (kTabX0 + k * kTabStep);   // exact: x and the grid point agree to within 1/64
   bessel01_taylor_f2h(k, f2_from_bits(h), b);
 }
 
@@ -724,7 +734,7 @@ BEM_HD void bessel01_taylor_f2(double x, F2 X, Bessel01F2& b) {
 // ~2^-46 |x_c|, so the argument keeps FP64's absolute accuracy.
 struct BesselArg {
   double xb;   // x_b
-  int kb;      // grid point of x_b: x_kb = 2 + kb / 32
+  int kb;      // grid point of x_b: x_kb = 1 + kb / 32
   F2 hb;       // x_b - x_kb
   int qb;      // x_b = qb pi/2 + rb (mod 2 pi)
   F2 rb;
@@ -734,15 +744,15 @@ struct BesselArg {
 // reduction by pi/2 (five FP64 operations) is skipped and rb, qb are zero.
 BEM_HD void bessel_arg_base(double xb, BesselArg& a, bool asym = true) {
   a.xb = xb;
-  // kb = (xb - 2) 32 rounded to an integer (magic-number rounding; |kb| < 2^31 for the arguments that occur)
-  const double t = fma(xb - 2.0, 32.0, 0x1.8p52);
+  // kb = (xb - 1) 32 rounded to an integer (magic-number rounding; |kb| < 2^31 for the arguments that occur)
+  const double t = fma(xb - kTabX0, 32.0, 0x1.8p52);
   const double kd = t - 0x1.8p52;
 #if defined(__CUDA_ARCH__)
   a.kb = __double2loint(t);
 #else
   a.kb = (int)kd;
 #endif
-  a.hb = f2_from_bits(xb - fma(kd, kTabStep, 2.0));   // exact: x_kb is a multiple of 1/32
+  a.hb = f2_from_bits(xb - fma(kd, kTabStep, kTabX0));   // exact: x_kb is a multiple of 1/32
   if (asym) {
     a.rb = f2_from_bits(reduce_pio2(xb, a.qb));
   } else {
@@ -753,7 +763,7 @@ BEM_HD void bessel_arg_base(double xb, BesselArg& a, bool asym = true) {
 
 // J0, Y0, J1, Y1 at x = a.xb + XC (XC small), X = x in double-float (branch choice and amplitudes).
 BEM_HD void bessel01_f2_at(const BesselArg& a, F2 XC, F2 X, Bessel01F2& b) {
-  if (X.h < (float)BEM_X_SERIES) {
+  if (X.h < kTabXMin) {
     bessel01_series_f2(a.xb + ((double)XC.h + (double)XC.l), b);
   } else if (X.h < kTabXMax) {
     // x - x_k = (x_b - x_kb) + x_c - (k - kb) / 32 (the last step by a two-sum: when the difference crosses a
@@ -779,7 +789,7 @@ BEM_HD void bessel01_f2_at(const BesselArg& a, F2 XC, F2 X, Bessel01F2& b) {
 }
 
 BEM_HD void bessel01_f2(double x, F2 X, Bessel01F2& b) {
-  if (X.h < (float)BEM_X_SERIES) {
+  if (X.h < kTabXMin) {
     bessel01_series_f2(x, b);
   } else if (X.h < kTabXMax) {
     bessel01_taylor_f2(x, X, b);
