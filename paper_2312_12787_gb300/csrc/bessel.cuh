@@ -461,9 +461,9 @@ constexpr SeriesCoef make_series_coef() {
 
 // The ascending series of bessel01_series with tabulated coefficients, in FP64 (x < 2, a few per cent of
 // the evaluations), converted to double-float.
-// The double-float path takes the series only below kTabXMin = 1 (the table serves 1 <= x < 128): t = x^2/4 <= 1/4,
-// so terms m = 0 .. 9 suffice (the first one left out, t^10/(10!)^2 H_10, is below 2e-20).
-constexpr int kSeriesTermsF2 = 10;
+// The double-float path takes the series only below kTabXMin = 1/4 (the table serves 1/4 <= x < 128):
+// t = x^2/4 <= 1/64, so terms m = 0 .. 6 suffice (the first one left out, t^7/(7!)^2 H_7, is below 2e-20).
+constexpr int kSeriesTermsF2 = 7;
 BEM_HD void bessel01_series_f2(double x, Bessel01F2& b) {
   constexpr SeriesCoef C = make_series_coef();
   const double t = 0.25 * x * x;
@@ -586,25 +586,31 @@ BEM_HD void bessel01_asymp_f2x(double x, F2 X, Bessel01F2& b) {
   bessel01_asymp_f2r(X, f2_from_bits(r), quad, b);
 }
 
-// ---- tabulated values and Taylor steps on 1 <= x < 128 -------------------------------------------------
-// J0, Y0, J1, Y1 at x_k = 1 + k/32 (computed once on the host with the FP64 routines above, error ~1e-15 of
-// |H|), stored in double-float with 1/x_k.  Between grid points both pairs obey the same first-order system
+// ---- tabulated values and Taylor steps on 1/4 <= x < 128 -----------------------------------------------
+// J0, Y0, J1, Y1 at the grid points (computed once on the host with the FP64 routines above, error ~1e-15 of
+// |H|), stored in double-float with 1/x_k: x = 1/4 + k/128 for entries k = 0 .. 95 and x = 1 + (k - 96)/32 from
+// entry 96 on, so that every step |h| <= half a grid spacing keeps |h| / x <= 1/64.  All grid points are
+// multiples of 1/128.  Between grid points both pairs obey the same first-order system
 // Z0' = -Z1, Z1' = Z0 - Z1/x (DLMF 10.6.2), so with Z0(x_k + h) = sum a_n h^n and Z1(x_k + h) = sum b_n h^n the
 // Taylor coefficients follow from
 //   a_{n+1} = -b_n / (n+1),   b_{n+1} = (a_n - c_n) / (n+1),   c_n = (b_n - c_{n-1}) / x_k,
-// where c_n are the coefficients of Z1/(x_k + h).  With |h| <= 1/64, eight orders leave a remainder below
-// 1e-16 from x = 2 on and below ~4e-15 at x = 1 (the derivatives of Y_n grow like n!/x^n toward the origin:
+// where c_n are the coefficients of Z1/(x_k + h).  Eight orders leave a remainder below 1e-16 from x = 2 on and
+// below ~4e-15 where |h| / x reaches 1/64 (the derivatives of Y_n grow like n!/x^n toward the origin:
 // (h/x)^8 = 64^-8); orders 0-3 run in double-float, orders 4-7 (below 3e-9 of the value from x = 2 on, ~1e-7 at
-// x = 1) in FP32.  This replaces the
+// |h| / x = 1/64) in FP32.  This replaces the
 // recurrence of Miller's algorithm (56 steps) and Hankel's expansion up to x = 128 by about a fifth of the
 // arithmetic of the expansion (whose double-float sine, cosine and four Horner sums take ~1000 FP32 operations
 // per evaluation); the table costs 128 bytes per grid point, read through the L1 cache (the lanes of a warp
 // take neighbouring elements, so their arguments share a few grid points).
-constexpr double kTabStep = 1.0 / 32.0;
-constexpr double kTabX0 = 1.0;       // first grid point
-constexpr int kTabN = 4065;          // x_k = 1 + k / 32, k = 0 .. 4064: [1, 128]
-constexpr float kTabXMin = 1.0f;     // the table serves 1 <= x < 128 (520 KB of device memory); the series below
-constexpr float kTabXMax = 128.0f;
+constexpr double kTabStep = 1.0 / 32.0;   // spacing from x = 1 on
+constexpr double kTabX0 = 1.0;            // where the 1/32 spacing starts (entry kTabFine)
+constexpr int kTabFine = 96;              // entries of the 1/128 spacing on [1/4, 1)
+constexpr int kTabN = kTabFine + 4065;    // then x = 1 + k / 32, k = 0 .. 4064: [1, 128]
+constexpr float kTabXMin = 0.25f;         // the table serves 1/4 <= x < 128 (532 KB of device memory); the series
+constexpr float kTabXMax = 128.0f;        // below, Hankel's expansion above
+// Grid point of entry k in units of 1/128 (an integer).
+BEM_HD int tab_g128(int k) { return k < kTabFine ? 32 + k : 128 + 4 * (k - kTabFine); }
+BEM_HD double tab_x(int k) { return (double)tab_g128(k) * (1.0 / 128.0); }
 // One grid point x_k: for each pair (J0, J1) and (Y0, Y1) the Taylor coefficients of orders 0..3 of Z0 (a_n)
 // and Z1 (b_n) as double-float (a_1 = -b_0 is not stored), c_3 (FP32, the start of the FP32 orders) and
 // 1/x_k (FP32).  The coefficients depend on x_k only, so they are made once on the host in FP64.
@@ -650,7 +656,7 @@ inline const BesselTabEntry* bessel_tab_host() {
   static const std::vector<BesselTabEntry> tab = [] {
     std::vector<BesselTabEntry> t(kTabN);
     for (int k = 0; k < kTabN; ++k) {
-      const double x = kTabX0 + k * kTabStep;
+      const double x = tab_x(k);
       Bessel01 b;
       if (x < BEM_X_SERIES) bessel01_series(x, b);
       else if (x < BEM_X_ASYMP) bessel01_miller(x, b);
@@ -698,11 +704,14 @@ BEM_HD void taylor_pair(float4 q0, float4 q1, float4 q2, float4 q3, F2 H, F2& ou
   out1 = f2_add(b0, f2_mul(s1, H));
 }
 
+// Nearest grid entry of x (kTabXMin <= xh < kTabXMax).
 BEM_HD int tab_index(float xh) {
 #if defined(__CUDA_ARCH__)
-  return __float2int_rn((xh - (float)kTabX0) * 32.f);
+  return xh < (float)kTabX0 ? __float2int_rn((xh - kTabXMin) * 128.f)
+                            : kTabFine + __float2int_rn((xh - (float)kTabX0) * 32.f);
 #else
-  return (int)lrintf((xh - (float)kTabX0) * 32.f);
+  return xh < (float)kTabX0 ? (int)lrintf((xh - kTabXMin) * 128.f)
+                            : kTabFine + (int)lrintf((xh - (float)kTabX0) * 32.f);
 #endif
 }
 
@@ -722,7 +731,7 @@ BEM_HD void bessel01_taylor_f2h(int k, F2 H, Bessel01F2& b) {
 
 BEM_HD void bessel01_taylor_f2(double x, F2 X, Bessel01F2& b) {
   const int k = tab_index(X.h);
-  const double h = x - (kTabX0 + k * kTabStep);   // exact: x and the grid point agree to within 1/64
+  const double h = x - tab_x(k);   // exact: x and the grid point agree to within 1/64 of x
   bessel01_taylor_f2h(k, f2_from_bits(h), b);
 }
 
@@ -766,11 +775,11 @@ BEM_HD void bessel01_f2_at(const BesselArg& a, F2 XC, F2 X, Bessel01F2& b) {
   if (X.h < kTabXMin) {
     bessel01_series_f2(a.xb + ((double)XC.h + (double)XC.l), b);
   } else if (X.h < kTabXMax) {
-    // x - x_k = (x_b - x_kb) + x_c - (k - kb) / 32 (the last step by a two-sum: when the difference crosses a
-    // power of two its rounding is not exact)
+    // x - x_k = (x_b - x_kb) + x_c - (x_k - x_kb) (the last step by a two-sum: when the difference crosses a
+    // power of two its rounding is not exact); x_k - x_kb is a multiple of 1/128, exact in FP32
     const int k = tab_index(X.h);
     const F2 Hp = f2_add(a.hb, XC);
-    const float dk = (float)(k - a.kb) * (float)kTabStep;
+    const float dk = (float)(tab_g128(k) - (128 + 4 * a.kb)) * (1.f / 128.f);
     const F2 t = f2_two_sum(Hp.h, -dk);
     const F2 H = f2_fast_two_sum(t.h, t.l + Hp.l);
     bessel01_taylor_f2h(k, H, b);

@@ -1,7 +1,7 @@
 """The library's Bessel routines (bessel.cuh, host-and-device code) built for the host and checked against
-mpmath on every branch: the ascending series (x < 1 on the double-float path, x < 2 on the FP64 path), the
-Taylor steps from the tabulated coefficients (1 <= x < 128), Hankel's expansion (x >= 128), and the branch
-boundaries.  Errors are measured relative to
+mpmath on every branch: the ascending series (x < 1/4 on the double-float path, x < 2 on the FP64 path), the
+Taylor steps from the tabulated coefficients (1/4 <= x < 128: spacing 1/128 below 1, 1/32 above), Hankel's
+expansion (x >= 128), and the branch boundaries.  Errors are measured relative to
 |H0| for J0, Y0 and to |H1| for J1, Y1 (the Hankel functions the kernels are made of, Sec. 3.3).
 
 Three paths are checked: bessel01_f2, the double-float path of the assembly and matrix-free kernels;
@@ -54,6 +54,11 @@ def values(tmp_path_factory):
         1.0 + np.arange(0, 32) / 32.0 + rng.uniform(-1 / 64, 1 / 64, 32),
         1.0 + (np.arange(0, 32) + 0.5) / 32.0,
         np.geomspace(0.5, 0.999, 12),
+        # the fine segment, 1/4 <= x < 1 (spacing 1/128), and the series below it
+        [0.25 - 2.0 ** -40, 0.25, 0.25 + 2.0 ** -40, 1.0 - 1 / 256, 1.0 - 1 / 256 - 2.0 ** -33],
+        0.25 + np.arange(0, 96) / 128.0 + rng.uniform(-1 / 256, 1 / 256, 96),
+        0.25 + (np.arange(0, 96) + 0.5) / 128.0,
+        np.geomspace(1e-3, 0.249, 24),
     ])
     out = subprocess.run([exe], input="\n".join(repr(float(v)) for v in xs), capture_output=True, text=True,
                          check=True).stdout
@@ -72,8 +77,8 @@ def _rel_err(got4, ref):
     return np.max(np.abs(got4 - ref) / scale, axis=1)
 
 
-@pytest.mark.parametrize("lo,hi,bound", [(0.0, 1.0, 3e-15), (1.0, 2.0, 1e-14), (2.0, 128.0, 1e-14),
-                                         (128.0, np.inf, 2.5e-14)])
+@pytest.mark.parametrize("lo,hi,bound", [(0.0, 0.25, 3e-15), (0.25, 1.0, 1e-14), (1.0, 2.0, 1e-14),
+                                         (2.0, 128.0, 1e-14), (128.0, np.inf, 2.5e-14)])
 def test_double_float_path_matches_mpmath(values, lo, hi, bound):
     xs, got, ref = values
     sel = (xs >= lo) & (xs < hi)
@@ -97,8 +102,8 @@ def test_table_builders_match_mpmath(values, lo, hi, bound):
     assert sel.sum() > 30 and err.max() <= bound, (err.max(), xs[sel][np.argmax(err)])
 
 
-@pytest.mark.parametrize("lo,hi,bound", [(0.0, 1.0, 3e-15), (1.0, 2.0, 1e-14), (2.0, 128.0, 1e-14),
-                                         (128.0, np.inf, 2.5e-14)])
+@pytest.mark.parametrize("lo,hi,bound", [(0.0, 0.25, 3e-15), (0.25, 1.0, 1e-14), (1.0, 2.0, 1e-14),
+                                         (2.0, 128.0, 1e-14), (128.0, np.inf, 2.5e-14)])
 def test_split_argument_path_matches_mpmath(values, lo, hi, bound):
     """The assembly passes x as an FP64 base (per element pair) plus a double-float offset (per node); with the
     base and the node on different table grid points, near half-grid points and across the branch boundaries."""
