@@ -43,18 +43,18 @@ import workloads as W  # noqa: E402
 METRIC = "BEM solves/s (mixed vs FP64 GPU at err<=1e-6)"
 # Roofline inputs from ncu counts of single launches on the benchmarked star (r = 1 + 0.3 cos 5t, N_e = 4096,
 # 64 right-hand sides; profiles/assemble_star4096.md, profiles/gemm_tc_star4096_64rhs.md):
-#  * k_assemble issues 3.369e9 warp instructions (smsp__inst_executed.sum) over the FP64 pipe (per-pair
+#  * k_assemble issues 3.342e9 warp instructions (smsp__inst_executed.sum) over the FP64 pipe (per-pair
 #    geometry, phase k r) and the FP32 pipe (double-float node geometry, Bessel values and Gauss sums); neither
 #    pipe alone binds, so its roofline is the issue rate: 4 warp instructions per clock per SM.  Scaled to other
-#    sizes by the number of element pairs.  DRAM traffic 1.0167 GB written + 1.2 MB read per launch.
+#    sizes by the number of element pairs.  DRAM traffic 1.0159 GB written + 0.95 MB read per launch.
 #  * the multi-RHS GEMM streams the FP16 split copy of A once per launch: 2 x 2 bytes per real entry; DRAM
 #    traffic 562.4 MB read + 6.8 MB written per launch, scaled by the matrix size.
 #  * the refinement residual runs 16 FP32 operations per complex multiply-add on the FP32 pipe (four exact
 #    products summed with an offset accumulator, four operations each; the per-run offsets and the
 #    double-float fold are not counted), 128 operations per clock per SM; with the tensor-core product the
 #    small terms hi x_lo + lo x_hi are two FP16x3 GEMMs (11 kernels per residual, 12 with a K split).
-ASM_WARP_INST_N4096 = 3.369155222e9
-ASM_DRAM_BYTES_N4096 = 1.016702e9 + 1.228544e6
+ASM_WARP_INST_N4096 = 3.34192383e9
+ASM_DRAM_BYTES_N4096 = 1.015926e9 + 0.951808e6
 GEMM_DRAM_BYTES_N4096 = 562.432e6 + 6.828032e6
 RESID_FP32_OPS_PER_CMAC = 16
 RESID_LAUNCHES_TC = 11
