@@ -459,8 +459,8 @@ constexpr SeriesCoef make_series_coef() {
   return c;
 }
 
-// The ascending series of bessel01_series with tabulated coefficients, in FP64 (x < 2, a few per cent of
-// the evaluations), converted to double-float.
+// The ascending series of bessel01_series with tabulated coefficients, in FP64, converted to double-float (only
+// for the arguments below the table: a few neighbouring elements of each collocation point).
 // The double-float path takes the series only below kTabXMin = 1/4 (the table serves 1/4 <= x < 128):
 // t = x^2/4 <= 1/64, so terms m = 0 .. 6 suffice (the first one left out, t^7/(7!)^2 H_7, is below 2e-20).
 constexpr int kSeriesTermsF2 = 7;
