@@ -587,6 +587,11 @@ def main():
         "accuracy": acc,
         "phases_ms": {k: round(v[0], 3) for k, v in prof.items() if v[1]},   # one profiled step
         "roofline": roof,
+        # the assembly kernel's own rate: Gauss nodes x the (two) domains of every element pair of one interface
+        "assembly": ({"ms_per_launch": prof["assemble"][0] / prof["assemble"][1],
+                      "hankel_pairs_per_launch": 4 * 2 * nel * nel,
+                      "hankel_pairs_per_s": 4 * 2 * nel * nel / (prof["assemble"][0] / prof["assemble"][1] / 1e3)}
+                     if prof.get("assemble", (0, 0))[1] else None),
         "e2e": e2e,
         "gpu_launches": int(sum(v[1] for v in prof.values())) * args.steps,
         "clocks": clk.summary(),
