@@ -87,6 +87,7 @@ struct bem_problem {
   std::vector<int> P, M;
   int n = 0;
   bool geom_dirty = true;
+  double bbox_diag = -1.0;   // diagonal of the elements' bounding box (< 0: not yet computed for this geometry)
   bool mat_dirty = true;
   // device geometry: ax ay bx by mx my tx ty h (9n doubles), their double-float copies (6n floats), P M
   double* d_geom = nullptr;
@@ -309,6 +310,26 @@ int stored_element_rows(const bem_problem* p) {
   return (int)std::min<size_t>(rows, (size_t)p->n);
 }
 
+// Whether any Bessel argument k r of an assembly can reach Hankel's expansion (x >= 128, where the kernel needs the
+// arguments reduced by pi/2): every collocation point and every quadrature node lie in the bounding box of the
+// element end points, so r is at most its diagonal; a margin of 1 below 128 covers the rounding of k r.
+bool asym_reachable(bem_problem* p) {
+  if (p->ax.empty()) return false;
+  if (p->bbox_diag < 0.0) {   // once per geometry
+    double x0 = p->ax[0], x1 = x0, y0 = p->ay[0], y1 = y0;
+    for (size_t e = 0; e < p->ax.size(); ++e) {
+      x0 = std::min({x0, p->ax[e], p->bx[e]});
+      x1 = std::max({x1, p->ax[e], p->bx[e]});
+      y0 = std::min({y0, p->ay[e], p->by[e]});
+      y1 = std::max({y1, p->ay[e], p->by[e]});
+    }
+    p->bbox_diag = std::hypot(x1 - x0, y1 - y0);
+  }
+  double kmax = 0.0;
+  for (int d = 0; d < p->dom.n; ++d) kmax = std::max(kmax, std::fabs(p->dom.k[d]));
+  return kmax * p->bbox_diag >= 127.0;
+}
+
 // y = A_hi x (complex FP32, one column) of a matrix-free mixed problem: the stored rows by the FP32 GEMV, the
 // others recomputed (FP64 sums, FP32 result).
 cudaError_t matvec_partial_f32(bem_problem* p, const float2* x, float2* y, cudaStream_t s, const int* gate) {
@@ -319,25 +340,9 @@ cudaError_t matvec_partial_f32(bem_problem* p, const float2* x, float2* y, cudaS
     if (e == cudaSuccess) e = launch_matvec_c32_rows(p->d_Hs + (size_t)Es * n2, n2, n2, Es, n, 1, x, y, s);
   }
   if (e == cudaSuccess)
-    e = launch_matvec_free_f32(p->elem(), n, p->dom, make_quad(p->o.quad_order), p->o.form, Es, x, y, s, gate);
+    e = launch_matvec_free_f32(p->elem(), n, p->dom, make_quad(p->o.quad_order), p->o.form, Es, x, y, s, gate,
+                               asym_reachable(p));
   return e;
-}
-
-// Whether any Bessel argument k r of an assembly can reach Hankel's expansion (x >= 128, where the kernel needs the
-// arguments reduced by pi/2): every collocation point and every quadrature node lie in the bounding box of the
-// element end points, so r is at most its diagonal; a margin of 1 below 128 covers the rounding of k r.
-bool asym_reachable(const bem_problem* p) {
-  if (p->ax.empty()) return false;
-  double x0 = p->ax[0], x1 = x0, y0 = p->ay[0], y1 = y0;
-  for (size_t e = 0; e < p->ax.size(); ++e) {
-    x0 = std::min({x0, p->ax[e], p->bx[e]});
-    x1 = std::max({x1, p->ax[e], p->bx[e]});
-    y0 = std::min({y0, p->ay[e], p->by[e]});
-    y1 = std::max({y1, p->ay[e], p->by[e]});
-  }
-  double kmax = 0.0;
-  for (int d = 0; d < p->dom.n; ++d) kmax = std::max(kmax, std::fabs(p->dom.k[d]));
-  return kmax * std::hypot(x1 - x0, y1 - y0) >= 127.0;
 }
 
 bem_status assemble_impl(bem_problem* p, cudaStream_t s, bool force = false) {
@@ -603,7 +608,8 @@ bem_status gmres_run(bem_problem* p, Solver& sv, const double2* r0, double2* x, 
                                  static_cast<float2*>(st.W) + (size_t)r * n2, s, gate);
       } else if (p->o.matrix_free) {
         e = launch_matvec_free(p->elem(), p->n, p->dom, make_quad(p->o.quad_order), p->o.form, nrhs,
-                               static_cast<const double2*>(Vj), static_cast<double2*>(st.W), s, gate);
+                               static_cast<const double2*>(Vj), static_cast<double2*>(st.W), s, gate,
+                               asym_reachable(p));
       } else if (!fp32) {
         e = launch_matvec_c64(static_cast<const double2*>(p->d_A), n2, n2, nrhs, static_cast<const double2*>(Vj),
                               static_cast<double2*>(st.W), s, gate);
@@ -804,7 +810,8 @@ bem_status residual_mixed(bem_problem* p, Solver& sv, int nrhs, const double2* x
   const int n2 = 2 * p->n;
   if (p->o.matrix_free) {   // every entry recomputed, FP64 sums: r = b - A x
     Phase ph(p, BEM_PH_RESIDUAL, s, nrhs + 1);
-    CU(launch_matvec_free(p->elem(), p->n, p->dom, make_quad(p->o.quad_order), p->o.form, nrhs, x, r, s));
+    CU(launch_matvec_free(p->elem(), p->n, p->dom, make_quad(p->o.quad_order), p->o.form, nrhs, x, r, s, nullptr,
+                          asym_reachable(p)));
     CU(launch_axpby_neg(b, r, (size_t)nrhs * n2, s));
     return BEM_OK;
   }
@@ -1146,6 +1153,7 @@ BEM_API bem_status bem_add_segment(bem_problem* p, int n_vert, const double* xy,
   }
   p->n += ne;
   p->geom_dirty = true;
+  p->bbox_diag = -1.0;
   p->mat_dirty = true;
   return BEM_OK;
 }
@@ -1195,7 +1203,8 @@ BEM_API bem_status bem_matvec(bem_problem* p, int n_rhs, const bem_c64* x_dev, b
   double2* y = reinterpret_cast<double2*>(y_dev);
   if (p->o.matrix_free) {
     Phase ph(p, BEM_PH_MATVEC, s, n_rhs);
-    CU(launch_matvec_free(p->elem(), p->n, p->dom, make_quad(p->o.quad_order), p->o.form, n_rhs, x, y, s));
+    CU(launch_matvec_free(p->elem(), p->n, p->dom, make_quad(p->o.quad_order), p->o.form, n_rhs, x, y, s, nullptr,
+                          asym_reachable(p)));
     return BEM_OK;
   }
   if (!p->mixed()) {
@@ -1250,7 +1259,8 @@ BEM_API bem_status bem_residual(bem_problem* p, int n_rhs, const bem_c64* x_dev,
   if (p->o.matrix_free) {
     Phase ph(p, BEM_PH_RESIDUAL, s, 2);
     // r = b - A x with recomputed entries: product into r, then r = b - r
-    CU(launch_matvec_free(p->elem(), p->n, p->dom, make_quad(p->o.quad_order), p->o.form, n_rhs, x, r, s));
+    CU(launch_matvec_free(p->elem(), p->n, p->dom, make_quad(p->o.quad_order), p->o.form, n_rhs, x, r, s, nullptr,
+                          asym_reachable(p)));
     CU(launch_axpby_neg(b, r, (size_t)n_rhs * n2, s));
     return BEM_OK;
   }

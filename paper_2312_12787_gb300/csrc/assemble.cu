@@ -113,8 +113,8 @@ template <> __device__ __forceinline__ double2 ld_c<float2>(const float2* p) {
 __device__ __forceinline__ void st_c(double2* p, double2 v) { *p = v; }
 __device__ __forceinline__ void st_c(float2* p, double2 v) { *p = make_float2((float)v.x, (float)v.y); }
 
-// Element rows i0 .. n-1 (all of them for i0 = 0).
-template <typename T>
+// Element rows i0 .. n-1 (all of them for i0 = 0).  ASYM as for k_assemble.
+template <typename T, bool ASYM>
 __global__ void __launch_bounds__(256, BEM_ASM_CTAS_PER_SM) k_matvec_free(ElemDev e, int n, DomTab dom, Quad q, int form, int i0,
                                                       const T* __restrict__ x, T* __restrict__ y, const int* gate) {
   if (gate && *gate == 0) return;
@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(256, BEM_ASM_CTAS_PER_SM) k_matvec_free(ElemDe
   double2 up = make_double2(0, 0), lo = make_double2(0, 0);
   for (int j = lane; j < n; j += 32) {
     C2 o2[2][2];
-    assemble_pair_f2(e, dom, q, form, i, j, o2);
+    assemble_pair_f2<ASYM>(e, dom, q, form, i, j, o2);
     const double2 xu = ld_c(x + j), xw = ld_c(x + n + j);
     up = cadd(up, cadd(cmul(c2_to(o2[0][0]), xu), cmul(c2_to(o2[0][1]), xw)));
     lo = cadd(lo, cadd(cmul(c2_to(o2[1][0]), xu), cmul(c2_to(o2[1][1]), xw)));
@@ -363,20 +363,24 @@ cudaError_t launch_assemble_rows(const ElemDev& e, int n, const DomTab& dom, con
 }
 
 cudaError_t launch_matvec_free(const ElemDev& e, int n, const DomTab& dom, const Quad& q, int form, int nrhs,
-                               const double2* x, double2* y, cudaStream_t s, const int* gate) {
+                               const double2* x, double2* y, cudaStream_t s, const int* gate, bool asym) {
   if (const cudaError_t te = ensure_bessel_table(); te != cudaSuccess) return te;
-  for (int r = 0; r < nrhs; ++r)
-    k_matvec_free<double2><<<(n + 7) / 8, 256, 0, s>>>(e, n, dom, q, form, 0, x + (size_t)r * 2 * n,
-                                                       y + (size_t)r * 2 * n, gate);
+  for (int r = 0; r < nrhs; ++r) {
+    const double2* xr = x + (size_t)r * 2 * n;
+    double2* yr = y + (size_t)r * 2 * n;
+    if (asym) k_matvec_free<double2, true><<<(n + 7) / 8, 256, 0, s>>>(e, n, dom, q, form, 0, xr, yr, gate);
+    else k_matvec_free<double2, false><<<(n + 7) / 8, 256, 0, s>>>(e, n, dom, q, form, 0, xr, yr, gate);
+  }
   return cudaGetLastError();
 }
 
 cudaError_t launch_matvec_free_f32(const ElemDev& e, int n, const DomTab& dom, const Quad& q, int form, int i0,
-                                   const float2* x, float2* y, cudaStream_t s, const int* gate) {
+                                   const float2* x, float2* y, cudaStream_t s, const int* gate, bool asym) {
   if (i0 >= n) return cudaSuccess;
   if (i0 < 0) return cudaErrorInvalidValue;
   if (const cudaError_t te = ensure_bessel_table(); te != cudaSuccess) return te;
-  k_matvec_free<float2><<<(n - i0 + 7) / 8, 256, 0, s>>>(e, n, dom, q, form, i0, x, y, gate);
+  if (asym) k_matvec_free<float2, true><<<(n - i0 + 7) / 8, 256, 0, s>>>(e, n, dom, q, form, i0, x, y, gate);
+  else k_matvec_free<float2, false><<<(n - i0 + 7) / 8, 256, 0, s>>>(e, n, dom, q, form, i0, x, y, gate);
   return cudaGetLastError();
 }
 

@@ -112,12 +112,15 @@ cudaError_t launch_assemble(const ElemDev& e, int n, const DomTab& dom, const Qu
 // y = A x without a stored matrix (entries recomputed in FP64), n elements, nrhs columns of 2n.
 // `gate` (optional, device int): when it reads 0 the product is skipped (every system of the block has
 // converged; the solver queues several iterations ahead of its convergence check).
+// asym as for launch_assemble.
 cudaError_t launch_matvec_free(const ElemDev& e, int n, const DomTab& dom, const Quad& q, int form, int nrhs,
-                               const double2* x, double2* y, cudaStream_t s, const int* gate = nullptr);
+                               const double2* x, double2* y, cudaStream_t s, const int* gate = nullptr,
+                               bool asym = true);
 // The same for complex FP32 x and y (FP64 sums inside) and only the element rows i0 .. n-1 (matrix rows i and
 // n + i): the recomputed part of a partly stored matrix in the FP32 inner solves.
 cudaError_t launch_matvec_free_f32(const ElemDev& e, int n, const DomTab& dom, const Quad& q, int form, int i0,
-                                   const float2* x, float2* y, cudaStream_t s, const int* gate = nullptr);
+                                   const float2* x, float2* y, cudaStream_t s, const int* gate = nullptr,
+                                   bool asym = true);
 // Element rows i < rows of the matrix as complex FP32 (hi only) into a compact block: row i at H + i * lda,
 // row n + i at H + (rows + i) * lda.
 cudaError_t launch_assemble_rows(const ElemDev& e, int n, const DomTab& dom, const Quad& q, int form, int rows,

@@ -383,10 +383,19 @@ def test_full_size_junction_disk_c3(B, torch):
     assert rel(xf.cpu().numpy()[0], xl) <= SOLUTION_TOL_FP64
 
 
-def test_matrix_free_matvec_residual_and_solve(B, torch):
+@pytest.mark.parametrize("name,mk,solve", [
+    # k times the bounding-box diagonal below 127: the kernels without the reduction by pi/2
+    ("star300", lambda: W.Problem(k=[20.0, 30.0], eps=[1.0, 2.25],
+                                  segments=[W.Segment(W.star(300, 0.3, 5), P=0, M=1, closed=True)]), True),
+    # arguments up to ~280 reach Hankel's expansion: the kernels with the reduction (products and residual only:
+    # 2.6 elements per interior wavelength is too coarse a mesh for a meaningful solve)
+    ("ellipse250_k40", lambda: W.Problem(k=[40.0, 70.0], eps=[1.0, (70.0 / 40.0) ** 2],
+                                         segments=[W.Segment(W.ellipse(250, 4.0), P=0, M=1, closed=True)]), False),
+], ids=["star300", "ellipse250_k40"])
+def test_matrix_free_matvec_residual_and_solve(B, torch, name, mk, solve):
     """Matrix-free products (entries recomputed, nothing stored) against the stored FP64 matrix, the
     residual against the oracle, and the matrix-free solve against the oracle's LU solution."""
-    wp = W.Problem(k=[20.0, 30.0], eps=[1.0, 2.25], segments=[W.Segment(W.star(300, 0.3, 5), P=0, M=1, closed=True)])
+    wp = mk()
     pf = B.Problem.from_workload(wp, prec="fp64", matrix_free=1, tol=1e-12)
     ps = B.Problem.from_workload(wp, prec="fp64")
     n2 = pf.bem_num_unknowns()
@@ -403,10 +412,11 @@ def test_matrix_free_matvec_residual_and_solve(B, torch):
     pf.bem_residual(x, torch.as_tensor(b, device="cuda"), r, n_rhs=2)
     ref = b - (A @ x.cpu().numpy().T).T
     assert np.max(np.abs(r.cpu().numpy() - ref)) <= 1e-12 * np.max(np.abs(A)) * np.max(np.abs(x.cpu().numpy())) * n2
-    xs = torch.empty((1, n2), dtype=torch.complex128, device="cuda")
-    st, it, rs = pf.bem_solve_planewave([0.0], xs)
-    assert st == B.BEM_OK
-    assert rel(xs[0].cpu().numpy(), O.solve_lu(A, b[0])) <= SOLUTION_TOL_FP64
+    if solve:
+        xs = torch.empty((1, n2), dtype=torch.complex128, device="cuda")
+        st, it, rs = pf.bem_solve_planewave([0.0], xs)
+        assert st == B.BEM_OK
+        assert rel(xs[0].cpu().numpy(), O.solve_lu(A, b[0])) <= SOLUTION_TOL_FP64
     with pytest.raises(B.BemError):
         pf.bem_get_matrix(torch.empty((n2, n2), dtype=torch.complex128, device="cuda"))
     pf.close()
@@ -518,6 +528,23 @@ def test_mixed_inner_solves_keep_orthogonality(B, torch, name):
     assert st == B.BEM_OK and rs[0] <= 1e-8
     assert it[0] <= 3 * it8[0], (int(it[0]), int(it8[0]))
     assert rel(x[0].cpu().numpy(), x64[0].cpu().numpy()) <= SOLUTION_TOL_MIXED
+
+
+def test_matrix_free_mixed_reaching_the_expansion(B, torch):
+    """Mixed matrix-free solve where Bessel arguments reach Hankel's expansion (an ellipse of aspect 4 with
+    k = 40 / 70, arguments up to ~280: the recomputing kernels keep the reduction by pi/2), half of the rows
+    stored, against the same problem with its whole matrix stored: both solve to 1e-8, so their solutions agree
+    to ~cond x 1e-8."""
+    wp = W.Problem(k=[40.0, 70.0], eps=[1.0, (70.0 / 40.0) ** 2],
+                   segments=[W.Segment(W.ellipse(600, 4.0), P=0, M=1, closed=True)])
+    n = wp.n_elem
+    x = torch.empty((2, 1, 2 * n), dtype=torch.complex128, device="cuda")
+    for k, kw in enumerate((dict(matrix_free=1, store_bytes=(n // 2) * 2 * 2 * n * 8), {})):
+        p = B.Problem.from_workload(wp, prec="mixed", tol=1e-8, max_iter=600, **kw)
+        st, it, rs = p.bem_solve_planewave(np.array([0.3]), x[k])
+        assert st == B.BEM_OK and rs[0] <= 1e-8, (kw, st, it, rs)
+        p.close()
+    assert rel(x[0, 0].cpu().numpy(), x[1, 0].cpu().numpy()) <= 1e-6
 
 
 @pytest.mark.parametrize("store_frac", [0.0, 0.5, 1.0])
