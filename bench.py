@@ -48,14 +48,16 @@ METRIC = "BEM solves/s (mixed vs FP64 GPU at err<=1e-6)"
 #    pipe alone binds, so its roofline is the issue rate: 4 warp instructions per clock per SM.  Scaled to other
 #    sizes by the number of element pairs.  DRAM traffic 1.0159 GB written + 0.95 MB read per launch.
 #  * the multi-RHS GEMM streams the FP16 split copy of A once per launch: 2 x 2 bytes per real entry; DRAM
-#    traffic 562.4 MB read + 6.8 MB written per launch, scaled by the matrix size.
+#    traffic 565.0 MB read + 6.7 MB written per launch (a relaxed launch, A's and Bt's hi parts only: 274.0 +
+#    6.3 MB), scaled by the matrix size.
 #  * the refinement residual runs 16 FP32 operations per complex multiply-add on the FP32 pipe (four exact
 #    products summed with an offset accumulator, four operations each; the per-run offsets and the
 #    double-float fold are not counted), 128 operations per clock per SM; with the tensor-core product the
 #    small terms hi x_lo + lo x_hi are two FP16x3 GEMMs (11 kernels per residual, 12 with a K split).
 ASM_WARP_INST_N4096 = 3.34192383e9
 ASM_DRAM_BYTES_N4096 = 1.015926e9 + 0.951808e6
-GEMM_DRAM_BYTES_N4096 = 562.432e6 + 6.828032e6
+GEMM_DRAM_BYTES_N4096 = 564.993024e6 + 6.675712e6
+GEMM_DRAM_BYTES_RELAXED_N4096 = 273.995776e6 + 6.288384e6
 RESID_FP32_OPS_PER_CMAC = 16
 RESID_LAUNCHES_TC = 11
 SM_COUNT, SM_CLOCK_HZ = 152, 2.07e9
@@ -554,15 +556,25 @@ def main():
     elif ph == "matvec":
         # one kernel per product: the GEMM (its stream-K reduction is timed as the "reduce" phase); the launch
         # count leaves out the gated launches queued after convergence, which do no work
+        # relaxed launches (inexact GMRES: A's FP16 remainder dropped) stream half of A's bytes; the algorithmic
+        # bytes and the traffic are the averages over the profiled step's full and relaxed launches
         avg_s = ph_ms / ph_n / 1e3
-        bytes_per = n2 * n2 * 8 + 2 * N_RHS * n2 * 8          # A (2 x FP16 per real entry) + X + Y
+        n_rel = min(ph_n, prof.get("relaxed", (0.0, 0))[1])
+        full_b = n2 * n2 * 8 + 2 * N_RHS * n2 * 8             # A (2 x FP16 per real entry) + X + Y
+        rel_b = n2 * n2 * 4 + 2 * N_RHS * n2 * 8              # A's FP16 hi part + X + Y
+        bytes_per = ((ph_n - n_rel) * full_b + n_rel * rel_b) / ph_n
         ach = bytes_per / avg_s / 1e9
+        traffic = None
+        if GEMM_DRAM_BYTES_RELAXED_N4096 is not None:
+            traffic = ((ph_n - n_rel) * GEMM_DRAM_BYTES_N4096 + n_rel * GEMM_DRAM_BYTES_RELAXED_N4096) / ph_n * scale
         roof.update({"kernel": "k_gemm_tc (tcgen05 FP16x3 multi-RHS GEMM; its stream-K reduction is the reduce phase)",
                      "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
                      "peak_source": src, "algorithmic_bytes_per_launch": bytes_per,
-                     "traffic": GEMM_DRAM_BYTES_N4096 * scale,
-                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch at N_e = 4096 "
-                                       "(profiles/gemm_tc_star4096_64rhs.md), scaled by the matrix size"})
+                     "relaxed_launches": n_rel, "full_launches": ph_n - n_rel,
+                     "traffic": traffic,
+                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one full and one relaxed "
+                                       "launch at N_e = 4096 (profiles/gemm_tc_star4096_64rhs.md), averaged like the "
+                                       "algorithmic bytes and scaled by the matrix size"})
     else:
         # launches per refinement residual: 11 (12 with a K split) with the tensor-core small terms
         n_gemm = max(1, ph_n // RESID_LAUNCHES_TC)
@@ -585,7 +597,7 @@ def main():
         "latency_ms": {"p50": p50, "p99": p99, "unit": "ms per 64-solve batch"},
         "fp64": fp64,
         "accuracy": acc,
-        "phases_ms": {k: round(v[0], 3) for k, v in prof.items() if v[1]},   # one profiled step
+        "phases_ms": {k: round(v[0], 3) for k, v in prof.items() if v[1] and k != "relaxed"},   # one profiled step
         "roofline": roof,
         # the assembly kernel's own rate: Gauss nodes x the (two) domains of every element pair of one interface
         "assembly": ({"ms_per_launch": prof["assemble"][0] / prof["assemble"][1],
@@ -593,7 +605,7 @@ def main():
                       "hankel_pairs_per_s": 4 * 2 * nel * nel / (prof["assemble"][0] / prof["assemble"][1] / 1e3)}
                      if prof.get("assemble", (0, 0))[1] else None),
         "e2e": e2e,
-        "gpu_launches": int(sum(v[1] for v in prof.values())) * args.steps,
+        "gpu_launches": int(sum(v[1] for k, v in prof.items() if k != "relaxed")) * args.steps,
         "clocks": clk.summary(),
     }
     # ---- CPU oracle (rank 0, N = 1): timed on the whole workload; its LU solution is the accuracy reference ----

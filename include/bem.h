@@ -275,7 +275,9 @@ typedef enum {
   BEM_PH_OTHER = 9,     /* conversions, copies, column norms, the FP16 split copy of A */
   BEM_PH_REDUCE = 10,   /* a11: stream-K reduction of the tensor-core GEMM inside GMRES (the GEMM is MATVEC);
                            none where the cooperative iteration kernel sums the partials itself */
-  BEM_PH_COUNT = 11
+  BEM_PH_RELAXED = 11,  /* launch count only (time 0): the MATVEC launches of the tensor-core GEMM that ran relaxed,
+                           with A's FP16 remainder dropped (half of A's bytes) */
+  BEM_PH_COUNT = 12
 } bem_phase;
 BEM_API bem_status bem_profile_enable(bem_problem* p, int on);
 BEM_API bem_status bem_profile_read(bem_problem* p, double* ms_host, long long* launches_host);

@@ -31,7 +31,7 @@ EXPORTS = [
     "bem_test_set_fused_iteration",
 ]
 PHASES = ["geometry", "assemble", "rhs", "matvec", "arnoldi", "givens", "update", "residual", "farfield", "other",
-          "reduce"]
+          "reduce", "relaxed"]
 
 
 class BemError(RuntimeError):

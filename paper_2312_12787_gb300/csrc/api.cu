@@ -470,6 +470,8 @@ size_t krylov_bytes(int n2, int nrhs, int m, bool fp32) {
   add((size_t)nrhs * 8);                  // resid
   add((size_t)nrhs * 8);                  // tolv
   add(4);                                 // n_active
+  add((size_t)nrhs * 4);                  // relaxed
+  add(4);                                 // n_unrelaxed
   add(4);                                 // jdev
   add(4);                                 // arrive_all
   // mixed extras: residual r (FP64), rhs copy of the inner solve (FP32 not needed), tc workspace
@@ -531,6 +533,8 @@ Solver carve_solver(bem_problem* p, int nrhs, bool fp32) {
   st.resid = c.take<double>(nrhs);
   st.tolv = c.take<double>(nrhs);
   st.n_active = c.take<int>(1);
+  st.relaxed = c.take<int>(nrhs);
+  st.n_unrelaxed = c.take<int>(1);
   st.jdev = c.take<int>(1);
   st.arrive_all = c.take<int>(1);
   sv.r = c.take<double2>((size_t)nrhs * n2);
@@ -591,7 +595,7 @@ bem_status gmres_run(bem_problem* p, Solver& sv, const double2* r0, double2* x, 
       {
         Phase ph(p, BEM_PH_MATVEC, s, 1);
         e = launch_matvec_tc(p->d_A16, n2, nrhs, nullptr, static_cast<float2*>(st.W), sv.tcws, sv.tcws_bytes, s,
-                             gate, 1);
+                             gate, 1, kRelaxFactor > 0.0 ? st.n_unrelaxed : nullptr);
       }
       if (e != cudaSuccess) return e;
       if (!st.tc.part) {
@@ -749,9 +753,10 @@ bem_status gmres_run(bem_problem* p, Solver& sv, const double2* r0, double2* x, 
   std::vector<double> rs(nrhs);
   CU(cudaMemcpyAsync(it.data(), st.iters, nrhs * sizeof(int), cudaMemcpyDeviceToHost, s));
   CU(cudaMemcpyAsync(rs.data(), st.resid, nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
-  int tc_err = 0, orth_err = 0;
+  int tc_words[2] = {0, 0}, orth_err = 0;   // error word, relaxed launches
   if (use_tc)
-    CU(cudaMemcpyAsync(&tc_err, matvec_tc_error_word(sv.tcws, n2, nrhs), sizeof(int), cudaMemcpyDeviceToHost, s));
+    CU(cudaMemcpyAsync(tc_words, matvec_tc_error_word(sv.tcws, n2, nrhs), 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+  const int tc_err = tc_words[0];
   if (fused) CU(cudaMemcpyAsync(&orth_err, st.err, sizeof(int), cudaMemcpyDeviceToHost, s));
   CU(cudaStreamSynchronize(s));
   if (tc_err) return fail(BEM_ETIMEOUT, "tensor-core GEMM wait expired (code %d)", tc_err);
@@ -767,6 +772,10 @@ bem_status gmres_run(bem_problem* p, Solver& sv, const double2* r0, double2* x, 
     const int gated = std::max(0, launched - worked);
     p->launches[BEM_PH_MATVEC] -= gated;
     if (use_tc && !st.tc.part) p->launches[BEM_PH_REDUCE] -= gated;
+  }
+  if (p->prof && use_tc) {
+    // the run's relaxed products (counted on the device; the error word's neighbour is cleared per run)
+    p->launches[BEM_PH_RELAXED] += tc_words[1];
   }
   return BEM_OK;
 }

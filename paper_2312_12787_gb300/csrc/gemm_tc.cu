@@ -185,7 +185,8 @@ struct SegWalk {
 __global__ void __launch_bounds__(kThreads, 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap mapAh, const __grid_constant__ CUtensorMap mapAl,
               const __grid_constant__ CUtensorMap mapBh, const __grid_constant__ CUtensorMap mapBl, int n,
-              int kpt, long long total, float* partial, int* err, const int* gate, unsigned long long wait_ns) {
+              int kpt, long long total, float* partial, int* err, const int* gate, unsigned long long wait_ns,
+              const int* relax) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   Bars* bars = reinterpret_cast<Bars*>(smem + kStages * kStage);
@@ -233,6 +234,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
     return;
   }
+  // relaxed product: the FP16 remainders of A and of Bt are neither loaded nor multiplied, only hi x hi (uniform
+  // for the grid); counted in the word after the error word
+  const bool hi_only = relax && *relax == 0;
+  if (hi_only && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(err + 1, 1);
   int issued = 0;   // TMA stages issued by the producer thread
 
   if (warp == 0) {
@@ -245,13 +250,13 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (*(volatile int*)err) break;
         unsigned char* base = smem + st * kStage;
         const uint32_t fb = su32(&bars->full[st]);
-        mbar_expect_tx(fb, 4 * kTile);
+        mbar_expect_tx(fb, (hi_only ? 2 : 4) * kTile);
         const int g = kb + it;
         const int x = (g % kpt) * kKs, y = (g / kpt) * kM;
         tma_load_2d(su32(base), &mapAh, x, y, fb);
-        tma_load_2d(su32(base + kTile), &mapAl, x, y, fb);
+        if (!hi_only) tma_load_2d(su32(base + kTile), &mapAl, x, y, fb);
         tma_load_2d(su32(base + 2 * kTile), &mapBh, x, 0, fb);
-        tma_load_2d(su32(base + 3 * kTile), &mapBl, x, 0, fb);
+        if (!hi_only) tma_load_2d(su32(base + 3 * kTile), &mapBl, x, 0, fb);
         issued = it + 1;
       }
     }
@@ -284,8 +289,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint64_t off = (uint64_t)((k * 32) >> 4);   // 16 FP16 = 32 bytes along the swizzled row
             const uint32_t acc0 = (it == beg && k == 0) ? 0u : 1u;
             mma_f16(d1, dah + off, dbh + off, acc0);
-            mma_f16(d2, dal + off, dbh + off, acc0);
-            mma_f16(d2, dah + off, dbl + off, 1u);
+            if (!hi_only) {
+              mma_f16(d2, dal + off, dbh + off, acc0);
+              mma_f16(d2, dah + off, dbl + off, 1u);
+            }
           }
           mma_commit(su32(&bars->empty[st]));
         }
@@ -319,9 +326,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         tmem_ld32(ta + (uint32_t)(cc * 32), v);                  // D1
 #pragma unroll
         for (int i = 0; i < 32; ++i) acc[cc * 32 + i] += v[i];
-        tmem_ld32(ta + (uint32_t)(kN + cc * 32), v);             // D2, lo terms times 2^11
+        if (!hi_only) {   // D2 (lo terms times 2^11) is not written by a relaxed product
+          tmem_ld32(ta + (uint32_t)(kN + cc * 32), v);
 #pragma unroll
-        for (int i = 0; i < 32; ++i) acc[cc * 32 + i] = fmaf(v[i], 1.f / kTcLoScale, acc[cc * 32 + i]);
+          for (int i = 0; i < 32; ++i) acc[cc * 32 + i] = fmaf(v[i], 1.f / kTcLoScale, acc[cc * 32 + i]);
+        }
       }
       tc_fence_before();
       mbar_arrive(su32(&bars->acce[b]));
@@ -568,7 +577,7 @@ int* matvec_tc_error_word(void* ws, int n, int nrhs) {
 cudaError_t matvec_tc_clear_error(void* ws, int n, int nrhs, cudaStream_t s) {
   int* err = matvec_tc_error_word(ws, n, nrhs);
   if (!err) return cudaErrorInvalidValue;
-  return cudaMemsetAsync(err, 0, sizeof(int), s);
+  return cudaMemsetAsync(err, 0, 2 * sizeof(int), s);   // the error word and the relaxed-launch count
 }
 
 size_t matvec_tc_a16_bytes(int n) { return ((2 * (size_t)n * ld16(n) * 2 + 255) & ~(size_t)255) + (size_t)n * 4; }
@@ -584,7 +593,7 @@ cudaError_t launch_tc_prepare_a(const float2* A, int n, void* a16, cudaStream_t 
 }
 
 cudaError_t launch_matvec_tc(const void* a16, int n, int nrhs, const float2* x, float2* y, void* ws,
-                             size_t ws_bytes, cudaStream_t s, const int* gate, int stage) {
+                             size_t ws_bytes, cudaStream_t s, const int* gate, int stage, const int* relax) {
   if (!matvec_tc_supported(n, nrhs)) return cudaErrorNotSupported;
   if (ws_bytes < matvec_tc_workspace_bytes(n, nrhs)) return cudaErrorInvalidValue;
   const size_t ld = ld16(n);
@@ -621,7 +630,7 @@ cudaError_t launch_matvec_tc(const void* a16, int n, int nrhs, const float2* x, 
     k_tc_prep_b<<<dim3((n + 255) / 256, kMaxRhs), 256, 0, s>>>(x, n, nrhs, cmax, bhi, blo, ld, tsc, gate);
   }
   cudaError_t e = launch_pdl(k_gemm_tc, dim3(G), dim3(kThreads), kSmemBytes, s, mAh, mAl, mBh, mBl, n, kpt, total,
-                             part, err, gate, g_wait_ns.load(std::memory_order_relaxed));
+                             part, err, gate, g_wait_ns.load(std::memory_order_relaxed), relax);
   if (e != cudaSuccess || stage == 1) return e;
   return launch_pdl(k_tc_reduce, dim3((n + kRedRows - 1) / kRedRows), dim3(256), 0, s, part, n, nrhs, kpt, total, G,
                     rsc, x ? tsc : static_cast<const float*>(nullptr), y, gate);

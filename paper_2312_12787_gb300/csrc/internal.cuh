@@ -184,8 +184,12 @@ bem_status noalloc_setup();
 // x == nullptr: the block's B operand is already in ws in the FP16 x 3 format with scale 1 (the Krylov kernels
 // write it for unit-norm basis vectors; matvec_tc_b_operand gives its place).  stage 0: the whole product;
 // 1: operand preparation and the GEMM; 2: the stream-K reduction of a stage-1 call with the same arguments.
+// relax (optional, device int): when it reads 0 the product multiplies the FP16 hi parts of A and Bt alone (half
+// of A's bytes and of Bt's, a relative error of ~2^-11 of the largest entries): the relaxed products of inexact
+// GMRES.
 cudaError_t launch_matvec_tc(const void* a16, int n, int nrhs, const float2* x, float2* y, void* ws,
-                             size_t ws_bytes, cudaStream_t s, const int* gate = nullptr, int stage = 0);
+                             size_t ws_bytes, cudaStream_t s, const int* gate = nullptr, int stage = 0,
+                             const int* relax = nullptr);
 void matvec_tc_b_operand(void* ws, int n, void** bhi, void** blo, size_t* ldb);
 size_t matvec_tc_b_bytes(int n);
 // One-time settings of the tensor-core kernel (shared-memory limit); call before recording it in a graph.
@@ -196,7 +200,8 @@ cudaError_t matvec_tc_clear_error(void* ws, int n, int nrhs, cudaStream_t s);
 size_t matvec_tc_a16_bytes(int n);
 cudaError_t launch_tc_prepare_a(const float2* A, int n, void* a16, cudaStream_t s);
 size_t matvec_tc_workspace_bytes(int n, int nrhs);
-// Device word where the tensor-core kernel records a bounded-wait expiry (0 = none) inside ws.
+// Device word where the tensor-core kernel records a bounded-wait expiry (0 = none) inside ws; the next word
+// counts the relaxed launches (both cleared by matvec_tc_clear_error).
 int* matvec_tc_error_word(void* ws, int n, int nrhs);
 bool matvec_tc_supported(int n, int nrhs);
 struct TcPartials;
@@ -225,6 +230,15 @@ struct TcPartials {
 };
 
 constexpr int kSyncStride = 32;   // ints between the barrier counters of two systems
+
+// Relaxed products in the tensor-core inner solves (inexact GMRES: once the residual has fallen, the product may
+// be less accurate in inverse proportion, Simoncini and Szyld 2003; Bouras and Fraysse 2005): when every active
+// system of the block is within kRelaxFactor of its inner tolerance, the product multiplies the FP16 hi parts of A
+// and of the basis block alone (half of the bytes, a relative error of ~2^-11 of the largest entries).  The outer
+// refinement's residuals use the full product, so a relaxation too early costs iterations, never accuracy.
+// 64-system star, per step: factor 0 (off) 26.25 ms; 10: 25.87 ms (116 iterations, final residual 9.0e-9, the
+// last ~10 iterations of each inner solve relaxed: 71 against 94 us per product); 30: 26.65 ms (117, 9.2e-9).
+constexpr double kRelaxFactor = 10.0;
 
 // Mixed refinement: each inner solve is asked for kRefineMargin x (the residual reduction that the outer
 // tolerance still needs).  The inner solves' residual estimates match the updated residuals closely (on the
@@ -261,6 +275,11 @@ struct KrylovState {
   double* resid;    // nrhs: estimated relative residual
   const double* tolv;  // nrhs per-system tolerances (overrides the scalar tol when non-null)
   int* n_active;    // device count of active systems (the gate of queued iterations)
+  // Relaxed products (inexact GMRES): relaxed[s] is set once system s's residual estimate is within
+  // kRelaxFactor of its tolerance (or it stopped); n_unrelaxed counts the systems not yet there.  While it is 0
+  // the tensor-core product may drop A's FP16 remainder (see launch_matvec_tc).
+  int* relaxed;     // nrhs
+  int* n_unrelaxed;
   int* jdev;        // current iteration index (set by the start kernel, advanced after each iteration)
   int* arrive_all;  // systems whose end-of-iteration CTAs are all done (the last one advances jdev)
   // when non-zero: the cudaGraphConditionalHandle of the graph's loop over iterations; the end-of-iteration

@@ -96,6 +96,8 @@ __global__ void k_start_finish(KrylovState st, int nblk) {
   st.resid[s] = beta > 0.0 ? 1.0 : 0.0;
   st.hnext[s] = beta;
   if (beta > 0.0) atomicAdd(st.n_active, 1);   // zeroed by the launcher
+  st.relaxed[s] = beta > 0.0 ? 0 : 1;
+  if (beta > 0.0) atomicAdd(st.n_unrelaxed, 1);   // zeroed by the launcher
   st.arrive[s] = 0;
   st.reo[s] = 0;
   if (s == 0) {
@@ -426,7 +428,12 @@ __device__ __forceinline__ void finish_column(const KrylovState& st, int s, int 
   st.resid[s] = res;
   st.iters[s] = j + 1;
   st.hnext[s] = hn;
-  if (res <= in->tl || j + 1 >= st.m || hn == 0.0) {
+  const bool stop = res <= in->tl || j + 1 >= st.m || hn == 0.0;
+  if (!st.relaxed[s] && (stop || res <= kRelaxFactor * in->tl)) {
+    st.relaxed[s] = 1;
+    atomicSub(st.n_unrelaxed, 1);
+  }
+  if (stop) {
     st.active[s] = 0;
     atomicSub(st.n_active, 1);   // the gate of the queued iterations closes with the last system
   }
@@ -938,6 +945,7 @@ cudaError_t start_t(const KrylovState& st, const double2* r0, cudaStream_t s) {
   dim3 grd(nb, st.nrhs);
   k_norm_part<double2><<<grd, kThreads, 0, s>>>(r0, st.n, st.npart, nb);
   cudaError_t e = cudaMemsetAsync(st.n_active, 0, sizeof(int), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(st.n_unrelaxed, 0, sizeof(int), s);
   if (e != cudaSuccess) return e;
   if (st.sync) {
     e = cudaMemsetAsync(st.sync, 0, (size_t)st.nrhs * kSyncStride * sizeof(int), s);
