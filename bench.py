@@ -48,7 +48,7 @@ METRIC = "BEM solves/s (mixed vs FP64 GPU at err<=1e-6)"
 #    pipe alone binds, so its roofline is the issue rate: 4 warp instructions per clock per SM.  Scaled to other
 #    sizes by the number of element pairs.  DRAM traffic 1.0159 GB written + 0.95 MB read per launch.
 #  * the multi-RHS GEMM streams the FP16 split copy of A once per launch: 2 x 2 bytes per real entry; DRAM
-#    traffic 565.0 MB read + 6.7 MB written per launch (a relaxed launch, A's and Bt's hi parts only: 274.0 +
+#    traffic 564.2 MB read + 6.4 MB written per launch (a relaxed launch, A's and Bt's hi parts only: 274.0 +
 #    6.3 MB), scaled by the matrix size.
 #  * the refinement residual runs 16 FP32 operations per complex multiply-add on the FP32 pipe (four exact
 #    products summed with an offset accumulator, four operations each; the per-run offsets and the
@@ -56,7 +56,7 @@ METRIC = "BEM solves/s (mixed vs FP64 GPU at err<=1e-6)"
 #    small terms hi x_lo + lo x_hi are two FP16x3 GEMMs (11 kernels per residual, 12 with a K split).
 ASM_WARP_INST_N4096 = 3.34192383e9
 ASM_DRAM_BYTES_N4096 = 1.015926e9 + 0.951808e6
-GEMM_DRAM_BYTES_N4096 = 564.993024e6 + 6.675712e6
+GEMM_DRAM_BYTES_N4096 = 564.2304e6 + 6.43072e6
 GEMM_DRAM_BYTES_RELAXED_N4096 = 273.995776e6 + 6.288384e6
 RESID_FP32_OPS_PER_CMAC = 16
 RESID_LAUNCHES_TC = 11
