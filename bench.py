@@ -234,6 +234,60 @@ def run_reference(args):
 # GPU legs
 # ------------------------------------------------------------------------------------------------
 
+def roofline(prof, nel, hbm, src):
+    """Roofline entry of the dominant kernel: the phase with the most device time among those with a model.
+
+    prof maps a phase name to (milliseconds, launches) of one profiled step (the "relaxed" entry counts the
+    tensor-core products that multiplied the FP16 hi parts alone); nel is the element count of the workload;
+    hbm the HBM peak in GB/s and src where it comes from."""
+    models = ("assemble", "matvec", "residual")
+    ph, (ph_ms, ph_n) = max(((k, v) for k, v in prof.items() if k in models), key=lambda kv: kv[1][0])
+    n2 = 2 * nel
+    scale = (nel / 4096.0) ** 2
+    roof = {"kernel": ph, "launches": ph_n, "avg_launch_ms": ph_ms / ph_n, "traffic": None}
+    if ph == "assemble":
+        avg_s = ph_ms / ph_n / 1e3
+        ach = ASM_WARP_INST_N4096 * scale / avg_s / 1e9
+        roof.update({"kernel": "k_assemble (issue-bound: FP64 geometry + double-float Bessel on FP32)", "bound": "alu",
+                     "achieved": ach, "peak": ISSUE_PEAK_G, "unit": "G warp instructions/s", "frac": ach / ISSUE_PEAK_G,
+                     "traffic": ASM_DRAM_BYTES_N4096 * scale, "algorithmic_bytes_per_launch": 64 * nel * nel,
+                     "peak_source": "derived: 152 SMs x 4 issue slots/clk x 2.07 GHz"})
+    elif ph == "matvec":
+        # one kernel per product: the GEMM (its stream-K reduction is timed as the "reduce" phase); the launch
+        # count leaves out the gated launches queued after convergence, which do no work
+        # relaxed launches (inexact GMRES: A's FP16 remainder dropped) stream half of A's bytes; the algorithmic
+        # bytes and the traffic are the averages over the profiled step's full and relaxed launches
+        avg_s = ph_ms / ph_n / 1e3
+        n_rel = min(ph_n, prof.get("relaxed", (0.0, 0))[1])
+        full_b = n2 * n2 * 8 + 2 * N_RHS * n2 * 8             # A (2 x FP16 per real entry) + X + Y
+        rel_b = n2 * n2 * 4 + 2 * N_RHS * n2 * 8              # A's FP16 hi part + X + Y
+        bytes_per = ((ph_n - n_rel) * full_b + n_rel * rel_b) / ph_n
+        ach = bytes_per / avg_s / 1e9
+        traffic = None
+        if GEMM_DRAM_BYTES_RELAXED_N4096 is not None:
+            traffic = ((ph_n - n_rel) * GEMM_DRAM_BYTES_N4096 + n_rel * GEMM_DRAM_BYTES_RELAXED_N4096) / ph_n * scale
+        roof.update({"kernel": "k_gemm_tc (tcgen05 FP16x3 multi-RHS GEMM; its stream-K reduction is the reduce phase)",
+                     "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                     "peak_source": src, "algorithmic_bytes_per_launch": bytes_per,
+                     "relaxed_launches": n_rel, "full_launches": ph_n - n_rel,
+                     "traffic": traffic,
+                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one full and one relaxed "
+                                       "launch at N_e = 4096 (profiles/gemm_tc_star4096_64rhs.md), averaged like the "
+                                       "algorithmic bytes and scaled by the matrix size"})
+    else:
+        # launches per refinement residual: 11 (12 with a K split) with the tensor-core small terms
+        n_gemm = max(1, ph_n // RESID_LAUNCHES_TC)
+        avg_s = ph_ms / n_gemm / 1e3
+        ops = RESID_FP32_OPS_PER_CMAC * n2 * n2 * N_RHS
+        ach = ops / avg_s / 1e12
+        roof.update({"kernel": "k_resid_df_gemm (double-float residual: exact products on the FP32 pipe)", "bound": "alu",
+                     "launches": n_gemm, "avg_launch_ms": ph_ms / n_gemm, "achieved": ach, "peak": FP32_PEAK_T,
+                     "unit": "T FP32 operations/s", "frac": ach / FP32_PEAK_T,
+                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz"})
+
+    return roof
+
+
 def _load_lib():
     import torch
     import paper_2312_12787_gb300 as P
@@ -539,52 +593,9 @@ def main():
         e2e = {"value": N_RHS / (statistics.median(e2e_ms) / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h}
 
-    # ---- roofline of the dominant kernel (the phase with the most device time among those with a model) ----
     hbm, src = _peaks()
-    models = ("assemble", "matvec", "residual")
-    ph, (ph_ms, ph_n) = max(((k, v) for k, v in prof.items() if k in models), key=lambda kv: kv[1][0])
+    roof = roofline(prof, nel, hbm, src)
     n2 = 2 * nel
-    scale = (nel / 4096.0) ** 2
-    roof = {"kernel": ph, "launches": ph_n, "avg_launch_ms": ph_ms / ph_n, "traffic": None}
-    if ph == "assemble":
-        avg_s = ph_ms / ph_n / 1e3
-        ach = ASM_WARP_INST_N4096 * scale / avg_s / 1e9
-        roof.update({"kernel": "k_assemble (issue-bound: FP64 geometry + double-float Bessel on FP32)", "bound": "alu",
-                     "achieved": ach, "peak": ISSUE_PEAK_G, "unit": "G warp instructions/s", "frac": ach / ISSUE_PEAK_G,
-                     "traffic": ASM_DRAM_BYTES_N4096 * scale, "algorithmic_bytes_per_launch": 64 * nel * nel,
-                     "peak_source": "derived: 152 SMs x 4 issue slots/clk x 2.07 GHz"})
-    elif ph == "matvec":
-        # one kernel per product: the GEMM (its stream-K reduction is timed as the "reduce" phase); the launch
-        # count leaves out the gated launches queued after convergence, which do no work
-        # relaxed launches (inexact GMRES: A's FP16 remainder dropped) stream half of A's bytes; the algorithmic
-        # bytes and the traffic are the averages over the profiled step's full and relaxed launches
-        avg_s = ph_ms / ph_n / 1e3
-        n_rel = min(ph_n, prof.get("relaxed", (0.0, 0))[1])
-        full_b = n2 * n2 * 8 + 2 * N_RHS * n2 * 8             # A (2 x FP16 per real entry) + X + Y
-        rel_b = n2 * n2 * 4 + 2 * N_RHS * n2 * 8              # A's FP16 hi part + X + Y
-        bytes_per = ((ph_n - n_rel) * full_b + n_rel * rel_b) / ph_n
-        ach = bytes_per / avg_s / 1e9
-        traffic = None
-        if GEMM_DRAM_BYTES_RELAXED_N4096 is not None:
-            traffic = ((ph_n - n_rel) * GEMM_DRAM_BYTES_N4096 + n_rel * GEMM_DRAM_BYTES_RELAXED_N4096) / ph_n * scale
-        roof.update({"kernel": "k_gemm_tc (tcgen05 FP16x3 multi-RHS GEMM; its stream-K reduction is the reduce phase)",
-                     "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                     "peak_source": src, "algorithmic_bytes_per_launch": bytes_per,
-                     "relaxed_launches": n_rel, "full_launches": ph_n - n_rel,
-                     "traffic": traffic,
-                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one full and one relaxed "
-                                       "launch at N_e = 4096 (profiles/gemm_tc_star4096_64rhs.md), averaged like the "
-                                       "algorithmic bytes and scaled by the matrix size"})
-    else:
-        # launches per refinement residual: 11 (12 with a K split) with the tensor-core small terms
-        n_gemm = max(1, ph_n // RESID_LAUNCHES_TC)
-        avg_s = ph_ms / n_gemm / 1e3
-        ops = RESID_FP32_OPS_PER_CMAC * n2 * n2 * N_RHS
-        ach = ops / avg_s / 1e12
-        roof.update({"kernel": "k_resid_df_gemm (double-float residual: exact products on the FP32 pipe)", "bound": "alu",
-                     "launches": n_gemm, "avg_launch_ms": ph_ms / n_gemm, "achieved": ach, "peak": FP32_PEAK_T,
-                     "unit": "T FP32 operations/s", "frac": ach / FP32_PEAK_T,
-                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz"})
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
