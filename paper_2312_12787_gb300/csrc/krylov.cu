@@ -547,21 +547,42 @@ __device__ __forceinline__ unsigned long long cgs_time() {
   return t;
 }
 
+// GPU-scope release / acquire accesses of the barrier counters.  A CTA's writes made before a __syncthreads
+// become visible with thread 0's release arrival after it, and a CTA whose thread 0 has read an arrival with an
+// acquire load sees, after its next __syncthreads, everything the arriving CTA wrote before arriving (the
+// ordering of a release pattern is cumulative over what the barrier ordered before it).  Against a full fence
+// before a relaxed atomic and after the wait: 1.41 against 1.87 us per barrier of 64 systems x 8 CTAs.
+__device__ __forceinline__ int ld_acquire_gpu(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ int atom_add_release_gpu(int* p, int v) {
+  int old;
+  asm volatile("atom.add.release.gpu.global.s32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+__device__ __forceinline__ int atom_add_acq_rel_gpu(int* p, int v) {
+  int old;
+  asm volatile("atom.add.acq_rel.gpu.global.s32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+
 // All threads of the CTA: wait until every chunk of system s has arrived.  st.sync[s] only grows (zeroed at the
 // start of a run), and the CTAs of a system pass their barriers in the same order, so barrier number b of the
 // iteration completes when the counter reaches a multiple of nchunk above the arrival.
 // Each system's counter has a cache line of its own, and a waiting thread polls it with a short sleep between
 // reads, so that the polls of one system's CTAs do not queue behind the arrivals of the others at one L2 slice.
+// The data exchanged through a barrier (the chunk sums) is read with L2 loads (__ldcg).
 __device__ __forceinline__ void system_barrier(const KrylovState& st, int s, int nchunk, unsigned long long wait_ns) {
   __syncthreads();
   if (threadIdx.x == 0) {
     int* ctr = st.sync + (size_t)s * kSyncStride;
-    __threadfence();
-    const int old = atomicAdd(ctr, 1);
+    const int old = atom_add_release_gpu(ctr, 1);
     const int target = (old / nchunk + 1) * nchunk;
-    if (*(volatile int*)ctr < target && *(volatile int*)st.err == 0) {
+    if (ld_acquire_gpu(ctr) < target && *(volatile int*)st.err == 0) {
       const unsigned long long t0 = cgs_time();
-      while (*(volatile int*)ctr < target) {
+      while (ld_acquire_gpu(ctr) < target) {
         __nanosleep(100);
         if (cgs_time() - t0 > wait_ns || *(volatile int*)st.err != 0) {
           atomicCAS(st.err, 0, 1);
@@ -569,7 +590,6 @@ __device__ __forceinline__ void system_barrier(const KrylovState& st, int s, int
         }
       }
     }
-    __threadfence();
   }
   __syncthreads();
 }
@@ -832,17 +852,15 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == sizeof(float2) ? 4 : 1)
     }
     __syncthreads();   // ws, hs, tp and the staged rotations are reused by the next item
   }
-  // every CTA arrives (those without items too); the last one advances the index
+  // every CTA arrives (those without items too, after the __syncthreads that ends the item loop); the last one
+  // advances the index.  With a graph loop the last CTA reads the active count: its acquire-release arrival
+  // makes the rotations' decrements, which other CTAs made before arriving, visible to it.
   if (threadIdx.x == 0) {
-    // with a graph loop the last CTA reads the active count: the rotations' decrements must be visible
-    __threadfence();
-    if (atomicAdd(st.arrive_all, 1) == (int)gridDim.x - 1) {
+    if (atom_add_acq_rel_gpu(st.arrive_all, 1) == (int)gridDim.x - 1) {
       *st.arrive_all = 0;
       *st.jdev = j + 1;
-      if (st.cond_handle) {
-        __threadfence();
+      if (st.cond_handle)
         cudaGraphSetConditional((cudaGraphConditionalHandle)st.cond_handle, atomicAdd(st.n_active, 0) > 0 ? 1u : 0u);
-      }
     }
   }
 }
